@@ -1,0 +1,120 @@
+"""Path-based Hessian bound (Thm. 1) and its baselines, plain FP64.
+
+Steps, in the paper's order (Sec. III-A):
+
+1. Tube set -> box X (Eq. 18a box ``c + diag(sigma) E``, or a zonotope ``c + G E`` reduced to its interval
+   hull ``c +- ||G||_{1,r}`` with the row-wise l1 norm of Sec. II and Eq. 21), hulled with the nominal
+   point so that ``alpha~ in X`` as Thm. 1 requires.
+2. Displacement set Delta = X (-) alpha~ (Eq. 12).
+3. For each output row l and each structurally nonzero Hessian entry (j <= k):
+   evaluate [H_{l,kj}] over the prefix set X^(j) (coordinates 0..j range over X, the rest are fixed at
+   the nominal; Sec. III-A, "coordinate-wise path"), multiply by Delta_j * Delta_k (j < k) or by
+   1/2 Delta_k^2 (j = k, the interval of squares), and sum the terms one by one (Eq. 15).
+
+``ih_expand`` (Eq. 13) evaluates every entry over the full X; ``ih_classic`` (Eq. 12) forms the interval
+quadratic form 1/2 Delta^T ([H](X) Delta). ``gamma_map`` is the zonotope map of Sec. III-C.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .dynamics import iv_add, iv_mul, iv_scale, iv_sqr
+
+
+def box_from_set(nominal: np.ndarray, radii=None, G=None, center=None):
+    """Interval hull of the tube set, hulled with the nominal point. Returns (lo, hi) FP64 [n]."""
+    a = np.asarray(nominal, np.float64)
+    c = a if center is None else np.asarray(center, np.float64)
+    if G is not None:
+        half = np.abs(np.asarray(G, np.float64)).sum(axis=1)      # ||G||_{1,r}
+    else:
+        half = np.asarray(radii, np.float64)
+    lo = np.minimum(c - half, a)
+    hi = np.maximum(c + half, a)
+    return lo, hi
+
+
+def prefix_box(lo: np.ndarray, hi: np.ndarray, nominal: np.ndarray, j: int):
+    """X^(j): coordinates 0..j range over [lo, hi], coordinates > j are fixed at the nominal."""
+    plo = np.array(nominal, np.float64)
+    phi = np.array(nominal, np.float64)
+    plo[: j + 1] = lo[: j + 1]
+    phi[: j + 1] = hi[: j + 1]
+    return plo, phi
+
+
+def pbh(dyn, nominal: np.ndarray, lo: np.ndarray, hi: np.ndarray):
+    """Thm. 1 enclosure [R_lo, R_hi] of the linearization error of every output row."""
+    a = np.asarray(nominal, np.float64)
+    D = [(lo[i] - a[i], hi[i] - a[i]) for i in range(dyn.n)]
+    R_lo = np.zeros(dyn.n_x)
+    R_hi = np.zeros(dyn.n_x)
+    for row in range(dyn.n_x):
+        R = (0.0, 0.0)
+        for j, k, fn in dyn.hessian_terms(row):
+            plo, phi = prefix_box(lo, hi, a, min(j, k))
+            Hv = fn(plo, phi)
+            if j == k:
+                term = iv_scale(0.5, iv_mul(Hv, iv_sqr(D[k])))
+            else:
+                term = iv_mul(Hv, iv_mul(D[j], D[k]))
+            R = iv_add(R, term)
+        R_lo[row], R_hi[row] = R
+    return R_lo, R_hi
+
+
+def ih_expand(dyn, nominal, lo, hi):
+    """Eq. 13: the same expansion with every Hessian entry over the full box X."""
+    a = np.asarray(nominal, np.float64)
+    D = [(lo[i] - a[i], hi[i] - a[i]) for i in range(dyn.n)]
+    R_lo = np.zeros(dyn.n_x)
+    R_hi = np.zeros(dyn.n_x)
+    for row in range(dyn.n_x):
+        R = (0.0, 0.0)
+        for j, k, fn in dyn.hessian_terms(row):
+            Hv = fn(lo, hi)
+            if j == k:
+                term = iv_scale(0.5, iv_mul(Hv, iv_sqr(D[k])))
+            else:
+                term = iv_mul(Hv, iv_mul(D[j], D[k]))
+            R = iv_add(R, term)
+        R_lo[row], R_hi[row] = R
+    return R_lo, R_hi
+
+
+def ih_classic(dyn, nominal, lo, hi):
+    """Eq. 12: 1/2 Delta^T ([H](X) Delta) with interval matrix-vector then interval dot products."""
+    a = np.asarray(nominal, np.float64)
+    D = [(lo[i] - a[i], hi[i] - a[i]) for i in range(dyn.n)]
+    R_lo = np.zeros(dyn.n_x)
+    R_hi = np.zeros(dyn.n_x)
+    for row in range(dyn.n_x):
+        Hfull = {}
+        for j, k, fn in dyn.hessian_terms(row):
+            Hv = fn(lo, hi)
+            Hfull[(j, k)] = Hv
+            Hfull[(k, j)] = Hv
+        idx = sorted({p for jk in Hfull for p in jk})
+        R = (0.0, 0.0)
+        for p in idx:
+            v = (0.0, 0.0)
+            for q in idx:
+                if (p, q) in Hfull:
+                    v = iv_add(v, iv_mul(Hfull[(p, q)], D[q]))
+            R = iv_add(R, iv_mul(D[p], v))
+        R_lo[row], R_hi[row] = iv_scale(0.5, R)
+    return R_lo, R_hi
+
+
+def gamma_map(r_lo: np.ndarray, r_hi: np.ndarray, pad: float = 0.0):
+    """Zonotope of an interval bound (Sec. III-C): c = (lo+hi)/2, R = diag((hi-lo)/2) (+ diagonal padding)."""
+    c = 0.5 * (np.asarray(r_lo, np.float64) + np.asarray(r_hi, np.float64))
+    rad = 0.5 * (np.asarray(r_hi, np.float64) - np.asarray(r_lo, np.float64)) + pad
+    return c, rad
+
+
+def pbh_workload_row(dyn, nominal, radii=None, G=None, center=None):
+    """Convenience: set -> box -> Thm. 1 for one timestep. Returns (R_lo, R_hi, J, lo, hi)."""
+    lo, hi = box_from_set(nominal, radii=radii, G=G, center=center)
+    R_lo, R_hi = pbh(dyn, nominal, lo, hi)
+    return R_lo, R_hi, dyn.jacobian(nominal), lo, hi

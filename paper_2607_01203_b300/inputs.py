@@ -1,0 +1,243 @@
+"""Seeded synthetic workloads for certified linearization-error bounds (LEBs).
+
+This module is the single source of inputs for both the CUDA path and the FP64
+oracle. It holds none of the bound arithmetic: it only draws random numbers and
+rolls nominal trajectories forward with the model equations, so that every
+timestep has a plausible nominal point (x~_k, u~_k) and a tube set around it.
+
+All randomness is NumPy ``Generator(PCG64(...))`` seeded from ``SEED_BASE + config``
+(and, for per-trajectory arrays, the trajectory index), drawn in FP64 and rounded
+to FP32 once. Both sides receive the same FP32 arrays.
+
+Workloads (shapes follow the paper's systems, App. A, at synthetic sizes):
+
+* ``planar_quad``     6-state planar quadrotor (App. A "Planar Quadrotor"), box sets.
+* ``relu_mlp``        residual ReLU MLP 8->64->64->6 dynamics, box sets.
+* ``quad_chain``      28 planar quadrotors joined by neighbour springs (n_x=168, n_u=56),
+                      ragged horizons, zonotope tube sets with 2*n_x generators (Eq. 18a / 21).
+* ``tanh_mlp``        residual tanh MLP 224->512->512->512->168 dynamics, box sets.
+* ``proposer_data``   state/control/radius triples on quad-chain rollouts for the learned
+                      bound proposer.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+SEED_BASE = 1000
+
+# Planar quadrotor constants of the synthetic workloads (App. A equations).
+QUAD = dict(mass=1.0, inertia=0.01, arm=0.1, g=9.81, dt=0.05)
+
+
+def _rng(*keys: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence(list(keys))))
+
+
+# ----------------------------------------------------------------------------------------------
+# model equations used only to roll nominal trajectories forward (App. A, forward Euler)
+# ----------------------------------------------------------------------------------------------
+def _quad_chain_step(x: np.ndarray, u: np.ndarray, n_quads: int, p: dict, spring_k: float) -> np.ndarray:
+    """One forward-Euler step of ``n_quads`` planar quadrotors with neighbour springs."""
+    q = x.reshape(n_quads, 6)
+    uu = u.reshape(n_quads, 2)
+    px, py, phi, vx, vy, om = (q[:, i] for i in range(6))
+    S = uu[:, 0] + uu[:, 1]
+    fx = np.zeros(n_quads)
+    fy = np.zeros(n_quads)
+    if n_quads > 1 and spring_k != 0.0:
+        fx[1:] += px[:-1] - px[1:]
+        fx[:-1] += px[1:] - px[:-1]
+        fy[1:] += py[:-1] - py[1:]
+        fy[:-1] += py[1:] - py[:-1]
+    m, dt = p["mass"], p["dt"]
+    xd = np.stack([
+        vx, vy, om,
+        -(S / m) * np.sin(phi) + (spring_k / m) * fx,
+        (S / m) * np.cos(phi) - p["g"] + (spring_k / m) * fy,
+        (p["arm"] / p["inertia"]) * (uu[:, 1] - uu[:, 0]),
+    ], axis=1)
+    return (q + dt * xd).reshape(-1)
+
+
+def _mlp_step(x: np.ndarray, u: np.ndarray, Ws, bs, act: str) -> np.ndarray:
+    h = np.concatenate([x, u])
+    for i, (W, b) in enumerate(zip(Ws, bs)):
+        h = W.astype(np.float64) @ h + b.astype(np.float64)
+        if i + 1 < len(Ws):
+            h = np.maximum(h, 0.0) if act == "relu" else np.tanh(h)
+    return x + h
+
+
+def _rollout(step, x0: np.ndarray, U: np.ndarray) -> np.ndarray:
+    """States x_0..x_{N-1} visited under controls U[0..N-1] (the nominal points of each step)."""
+    X = np.empty((U.shape[0], x0.shape[0]))
+    x = x0.astype(np.float64)
+    for k in range(U.shape[0]):
+        X[k] = x
+        x = step(x, U[k].astype(np.float64))
+    return X
+
+
+def _mlp_weights(rng: np.random.Generator, widths, scale: float = 0.5):
+    Ws, bs = [], []
+    for fan_in, fan_out in zip(widths[:-1], widths[1:]):
+        Ws.append((rng.standard_normal((fan_out, fan_in)) * (scale / np.sqrt(fan_in))).astype(np.float32))
+        bs.append(np.zeros(fan_out, np.float32))
+    return Ws, bs
+
+
+# ----------------------------------------------------------------------------------------------
+@dataclasses.dataclass
+class Workload:
+    """One batch of LEB problems. Arrays are FP32, row-major, timesteps flattened over trajectories."""
+    name: str
+    kind: str                       # "planar_quad_chain" | "mlp"
+    n_x: int
+    n_u: int
+    x_nom: np.ndarray               # [T, n_x]
+    u_nom: np.ndarray               # [T, n_u]
+    traj_offsets: np.ndarray        # [n_traj + 1] int32 CSR over T
+    set_kind: str                   # "box" | "zono"
+    radii: np.ndarray | None = None     # [T, n] box half-widths (box sets), centred at the nominal
+    G: np.ndarray | None = None         # [T, n, p] zonotope generators (zono sets), centred at the nominal
+    params: dict | None = None          # analytic model constants (FP64 reals)
+    n_quads: int = 0
+    spring_k: float = 0.0
+    Ws: list | None = None              # MLP weights [out, in] FP32
+    bs: list | None = None
+    act: str = ""
+    residual: bool = True
+
+    @property
+    def T(self) -> int:
+        return int(self.x_nom.shape[0])
+
+    @property
+    def n(self) -> int:
+        return self.n_x + self.n_u
+
+    def nominal(self) -> np.ndarray:
+        return np.concatenate([self.x_nom, self.u_nom], axis=1)
+
+
+def planar_quad(seed: int = SEED_BASE + 1, N: int = 20) -> Workload:
+    """Planar quadrotor, n_x=6, n_u=2, horizon N, box radii U[0.01, 0.1] per state/input."""
+    rng = _rng(seed)
+    U = rng.uniform(3.0, 7.0, size=(N, 2))
+    X = _rollout(lambda x, u: _quad_chain_step(x, u, 1, QUAD, 0.0), np.zeros(6), U)
+    radii = rng.uniform(0.01, 0.1, size=(N, 8))
+    return Workload("planar_quad", "planar_quad_chain", 6, 2, X.astype(np.float32), U.astype(np.float32),
+                    np.array([0, N], np.int32), "box", radii=radii.astype(np.float32),
+                    params=dict(QUAD), n_quads=1, spring_k=0.0)
+
+
+def relu_mlp(seed: int = SEED_BASE + 2, N: int = 20, widths=(8, 64, 64, 6), radius_range=(0.01, 0.1)) -> Workload:
+    """Residual ReLU MLP x+ = x + MLP([x, u]); weights 0.5*N(0, 1/fan_in), zero biases."""
+    rng = _rng(seed)
+    Ws, bs = _mlp_weights(rng, widths)
+    n_x = widths[-1]
+    n_u = widths[0] - n_x
+    U = rng.uniform(3.0, 7.0, size=(N, n_u))
+    X = _rollout(lambda x, u: _mlp_step(x, u, Ws, bs, "relu"), np.zeros(n_x), U)
+    radii = rng.uniform(*radius_range, size=(N, widths[0]))
+    return Workload("relu_mlp", "mlp", n_x, n_u, X.astype(np.float32), U.astype(np.float32),
+                    np.array([0, N], np.int32), "box", radii=radii.astype(np.float32),
+                    Ws=Ws, bs=bs, act="relu")
+
+
+def quad_chain(seed: int = SEED_BASE + 3, n_traj: int = 256, horizon=(20, 60), n_quads: int = 28,
+               spring_k: float = 0.5, gen_std: float = 0.01, n_gen: int | None = None,
+               with_G: bool = True) -> Workload:
+    """Chain of planar quadrotors with neighbour springs; zonotope sets c + G*xi, G ~ N(0, gen_std^2).
+
+    ``horizon`` is either an int (fixed N) or an inclusive range (lo, hi) drawn per trajectory.
+    Generators are drawn per trajectory from their own stream, so any timestep can be regenerated
+    alone (``quad_chain_G``).
+    """
+    rng = _rng(seed)
+    n_x, n_u = 6 * n_quads, 2 * n_quads
+    n_gen = 2 * n_x if n_gen is None else n_gen
+    if isinstance(horizon, int):
+        H = np.full(n_traj, horizon, np.int64)
+    else:
+        H = rng.integers(horizon[0], horizon[1] + 1, size=n_traj)
+    offs = np.zeros(n_traj + 1, np.int64)
+    offs[1:] = np.cumsum(H)
+    T = int(offs[-1])
+    X = np.empty((T, n_x), np.float32)
+    U = np.empty((T, n_u), np.float32)
+    for b in range(n_traj):
+        Ub = rng.uniform(3.0, 7.0, size=(H[b], n_u))
+        Xb = _rollout(lambda x, u: _quad_chain_step(x, u, n_quads, QUAD, spring_k), np.zeros(n_x), Ub)
+        X[offs[b]:offs[b + 1]] = Xb
+        U[offs[b]:offs[b + 1]] = Ub
+    w = Workload("quad_chain", "planar_quad_chain", n_x, n_u, X, U, offs.astype(np.int32), "zono",
+                 params=dict(QUAD), n_quads=n_quads, spring_k=spring_k)
+    w.params["gen_std"] = gen_std
+    w.params["n_gen"] = n_gen
+    w.params["seed"] = seed
+    if with_G:
+        G = np.empty((T, n_x + n_u, n_gen), np.float32)
+        for b in range(n_traj):
+            G[offs[b]:offs[b + 1]] = quad_chain_G(seed, b, int(H[b]), n_x + n_u, n_gen, gen_std)
+        w.G = G
+    return w
+
+
+def quad_chain_G(seed: int, traj: int, horizon: int, n: int, n_gen: int, gen_std: float) -> np.ndarray:
+    """Zonotope generators of one trajectory, [horizon, n, n_gen] FP32."""
+    g = _rng(seed, 7, traj)
+    return (g.standard_normal((horizon, n, n_gen), dtype=np.float32) * np.float32(gen_std)).astype(np.float32)
+
+
+def tanh_mlp(seed: int = SEED_BASE + 4, n_traj: int = 128, N: int = 50, widths=(224, 512, 512, 512, 168),
+             radius_range=(0.005, 0.05)) -> Workload:
+    """Residual tanh MLP dynamics; box radii U[0.005, 0.05] per state/input."""
+    rng = _rng(seed)
+    Ws, bs = _mlp_weights(rng, widths)
+    n_x = widths[-1]
+    n_u = widths[0] - n_x
+    T = n_traj * N
+    X = np.empty((T, n_x), np.float32)
+    U = np.empty((T, n_u), np.float32)
+    for b in range(n_traj):
+        Ub = rng.uniform(3.0, 7.0, size=(N, n_u))
+        X[b * N:(b + 1) * N] = _rollout(lambda x, u: _mlp_step(x, u, Ws, bs, "tanh"), np.zeros(n_x), Ub)
+        U[b * N:(b + 1) * N] = Ub
+    radii = rng.uniform(*radius_range, size=(T, widths[0])).astype(np.float32)
+    offs = (np.arange(n_traj + 1) * N).astype(np.int32)
+    return Workload("tanh_mlp", "mlp", n_x, n_u, X, U, offs, "box", radii=radii, Ws=Ws, bs=bs, act="tanh")
+
+
+def proposer_data(seed: int = SEED_BASE + 5, n_rollouts: int = 2000, N: int = 50, n_quads: int = 28,
+                  spring_k: float = 0.5, state_radius=(0.01, 0.1), control_radius: float = 0.05) -> Workload:
+    """Quad-chain rollouts with box sets: state radii U[0.01, 0.1], control radii fixed."""
+    rng = _rng(seed)
+    n_x, n_u = 6 * n_quads, 2 * n_quads
+    T = n_rollouts * N
+    X = np.empty((T, n_x), np.float32)
+    U = np.empty((T, n_u), np.float32)
+    for b in range(n_rollouts):
+        Ub = rng.uniform(3.0, 7.0, size=(N, n_u))
+        X[b * N:(b + 1) * N] = _rollout(lambda x, u: _quad_chain_step(x, u, n_quads, QUAD, spring_k),
+                                        np.zeros(n_x), Ub)
+        U[b * N:(b + 1) * N] = Ub
+    radii = np.empty((T, n_x + n_u), np.float32)
+    radii[:, :n_x] = rng.uniform(*state_radius, size=(T, n_x))
+    radii[:, n_x:] = control_radius
+    offs = (np.arange(n_rollouts + 1) * N).astype(np.int32)
+    return Workload("proposer_data", "planar_quad_chain", n_x, n_u, X, U, offs, "box", radii=radii,
+                    params=dict(QUAD), n_quads=n_quads, spring_k=spring_k)
+
+
+def subset(w: Workload, rows: np.ndarray) -> Workload:
+    """The same workload restricted to the given timestep rows (one trajectory per row)."""
+    rows = np.asarray(rows)
+    d = dataclasses.replace(w)
+    d.x_nom = np.ascontiguousarray(w.x_nom[rows])
+    d.u_nom = np.ascontiguousarray(w.u_nom[rows])
+    d.radii = None if w.radii is None else np.ascontiguousarray(w.radii[rows])
+    d.G = None if w.G is None else np.ascontiguousarray(w.G[rows])
+    d.traj_offsets = np.arange(len(rows) + 1, dtype=np.int32)
+    return d
