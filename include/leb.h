@@ -1,0 +1,221 @@
+/*
+ * leb.h — C ABI of the B300 library for certified linearization-error bounds (LEBs).
+ *
+ * The library computes, for every timestep k of a batch of nominal trajectories and every state
+ * dimension l, sound bounds
+ *
+ *     r_lo[k,l] <= f_l(x,u) - f_l(x~_k,u~_k) - (A_k (x - x~_k) + B_k (u - u~_k))_l <= r_hi[k,l]
+ *
+ * for all (x,u) in the tube set around (x~_k, u~_k): Problem 1 of the paper (Eq. 9c, Eq. 10), with
+ * the set as a box (Eq. 18a) or a zonotope reduced to its interval hull (row-wise l1 norm, Eq. 21).
+ * Analytic dynamics use the path-based Hessian bound (Thm. 1, Eq. 15); MLP dynamics use CROWN affine
+ * relaxations (Thm. 2) with the Jacobian correction (Thm. 3). A_k, B_k (Eq. 8) are returned, and the
+ * bounds are sound for the FP32 A_k, B_k actually returned.
+ *
+ * Conventions for every entry point:
+ *  - Arrays are row-major FP32 unless stated. "device" pointers are CUDA device memory of the current
+ *    device; "host" pointers are ordinary host memory. All array arguments are owned by the caller;
+ *    the library never frees or retains them beyond the call.
+ *  - Work is enqueued on the given stream (a cudaStream_t passed as void*, NULL = legacy default
+ *    stream) and is asynchronous: results are valid once the stream reaches that point.
+ *  - Argument errors are detected on the host and returned synchronously (LEB_ERR_INVALID_ARG,
+ *    LEB_ERR_UNSUPPORTED, LEB_ERR_WORKSPACE); nothing is enqueued then. Launch failures return
+ *    LEB_ERR_CUDA. No C++ exception crosses this interface.
+ *  - Conditions found on the GPU are OR-ed into the caller's device word *dev_flags (see
+ *    leb_async_flag); it is cleared at the start of each leb_bounds / leb_bounds_backward call.
+ *    A timestep whose inputs are not finite gets bounds [-inf, +inf] (sound) and raises
+ *    LEB_ASYNC_NONFINITE. Every wait inside a kernel is bounded; a wait that runs out raises
+ *    LEB_ASYNC_TIMEOUT and the kernel returns without hanging.
+ *  - leb_bounds / leb_bounds_backward allocate nothing, never synchronize and never read device memory
+ *    from the host, so they can be captured into a CUDA graph (leb_graph_* does that for you).
+ */
+#ifndef LEB_H
+#define LEB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct leb_ctx* leb_handle;
+typedef struct leb_graph_s* leb_graph;
+typedef struct leb_proposer_s* leb_proposer;
+
+typedef enum {
+  LEB_OK = 0,
+  LEB_ERR_INVALID_ARG = -1,   /* a pointer, size or enum value is invalid                       */
+  LEB_ERR_UNSUPPORTED = -2,   /* valid request that this build does not implement                */
+  LEB_ERR_WORKSPACE = -3,     /* workspace NULL or smaller than leb_workspace_size()             */
+  LEB_ERR_CUDA = -4,          /* a CUDA runtime call or kernel launch failed                     */
+  LEB_ERR_TIMEOUT = -5        /* reserved for host-side waits (device waits report via flags)    */
+} leb_status;
+
+typedef enum {
+  LEB_ASYNC_NONFINITE = 1,    /* some timestep had NaN/Inf inputs; its bounds are [-inf, +inf]  */
+  LEB_ASYNC_TIMEOUT = 2,      /* a bounded device wait ran out; affected outputs are [-inf, +inf] */
+  LEB_ASYNC_OVERFLOW = 4      /* a reduced-precision operand overflowed; bounds set to [-inf,+inf] */
+} leb_async_flag;
+
+typedef enum { LEB_DYN_QUAD_CHAIN = 0, LEB_DYN_MLP = 1 } leb_dyn_kind;
+typedef enum { LEB_ACT_RELU = 0, LEB_ACT_TANH = 1 } leb_act;
+/* arithmetic of the MLP back-substitution: FP32 on CUDA cores, or FP16/BF16 operands on the
+   tensor cores with FP32 accumulation and a rigorous rounding inflation */
+typedef enum { LEB_PREC_FP32 = 0, LEB_PREC_FP16 = 1, LEB_PREC_BF16 = 2 } leb_prec;
+typedef enum { LEB_SET_BOX = 0, LEB_SET_ZONO = 1 } leb_set_kind;
+
+/* Dynamics specification (read during leb_create only; weights are copied into the handle).
+ *  LEB_DYN_QUAD_CHAIN: n_quads planar quadrotors of App. A ("Planar Quadrotor") integrated by forward
+ *    Euler with step dt, neighbours joined by linear springs of stiffness spring_k between their
+ *    positions (free ends; spring_k = 0 and n_quads = 1 is the single planar quadrotor).
+ *    State order (p_x, p_y, phi, v_x, v_y, omega) per quadrotor, all states first, then inputs
+ *    (u_1, u_2) per quadrotor: n_x = 6 n_quads, n_u = 2 n_quads. Constants are exact reals given as
+ *    doubles; the library encloses them in FP32 intervals.
+ *  LEB_DYN_MLP: f(x,u) = [x +] W_L h_{L-1} + b_L, h_i = act(W_i h_{i-1} + b_i), h_0 = [x; u];
+ *    widths[0] = n_x + n_u, widths[L] = n_x. W[i] is host FP32 [widths[i+1]][widths[i]], b[i] host
+ *    FP32 [widths[i+1]]. residual != 0 adds the identity on x. */
+typedef struct {
+  leb_dyn_kind kind;
+  int n_quads;
+  double dt, mass, inertia, arm, g, spring_k;
+  int n_layers;
+  const int* widths;
+  const float* const* W;
+  const float* const* b;
+  leb_act act;
+  int residual;
+  leb_prec prec;
+} leb_dynamics_spec;
+
+/* Tube set of every timestep (device pointers, row-major over timesteps).
+ *  center: [T, n] or NULL (the set is centred at the nominal [x~; u~]).
+ *  LEB_SET_BOX:  radii [T, n], non-negative half-widths.
+ *  LEB_SET_ZONO: G [T, n, n_gen] generators; the set is center + G xi, |xi|_inf <= 1.
+ * The set is replaced by its interval hull and hulled with the nominal point (Thm. 1 needs the
+ * nominal inside the set; a tube with a centre offset may not contain it). */
+typedef struct {
+  leb_set_kind kind;
+  const float* center;
+  const float* radii;
+  const float* G;
+  int n_gen;
+} leb_set;
+
+/* Ragged batch of trajectories (optional; NULL means T independent timesteps of the handle's size).
+ *  traj_offsets: device int [n_traj + 1], timestep CSR; T must equal traj_offsets[n_traj].
+ *  traj_nquads:  device int [n_traj] or NULL. Quad chains only: per-trajectory chain length (uneven
+ *    dimension). Then every per-timestep array is packed: trajectory b's rows have n_x = 6 nq_b,
+ *    n_u = 2 nq_b, n = 8 nq_b, and a zonotope of trajectory b has n_gen_per_quad * nq_b generators
+ *    (leb_set.n_gen is then read as generators per quadrotor). nq_b <= the handle's n_quads. */
+typedef struct {
+  int n_traj;
+  const int* traj_offsets;
+  const int* traj_nquads;
+} leb_batch;
+
+/* Optional outputs and overrides (NULL = none). All pointers device, [T, n_x] (packed like r_lo).
+ *  gamma_c, gamma_r: the zonotope map of Sec. III-C: c = (r_lo + r_hi)/2, R = diag((r_hi - r_lo)/2) +
+ *    gamma_pad (diagonal returned as a vector; rounded upward so that c +- R contains [r_lo, r_hi]).
+ *  eps: per-bound stated a-priori slack of the reduced-precision MLP path (rounding inflation plus a
+ *    bound on the deviation caused by rounded operands); zero for exact-arithmetic paths. */
+typedef struct {
+  float* gamma_c;
+  float* gamma_r;
+  float gamma_pad;
+  float* eps;
+} leb_options;
+
+/* ---- handle ------------------------------------------------------------------------------------ */
+leb_status leb_create(const leb_dynamics_spec* spec, leb_handle* out);
+leb_status leb_destroy(leb_handle h);
+/* n_x, n_u of the handle (largest chain for uneven batches). */
+leb_status leb_dims(leb_handle h, int* n_x, int* n_u);
+/* Bytes of device workspace leb_bounds and leb_bounds_backward need for up to T_max timesteps. */
+leb_status leb_workspace_size(leb_handle h, int T_max, size_t* bytes);
+
+/* ---- forward bounds (Thm. 1 / Thm. 2-3) -------------------------------------------------------- */
+/* x_nom [T, n_x], u_nom [T, n_u]: nominal points (device). r_lo, r_hi [T, n_x] (device, written).
+ * A [T, n_x, n_x], B [T, n_x, n_u] (device, written) or NULL to skip writing them (the bound is then
+ * sound for the FP32 values that would have been written). workspace: device, >= leb_workspace_size.
+ * dev_flags: device int (cleared, then OR-ed with leb_async_flag bits). */
+leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* x_nom, const float* u_nom,
+                      const leb_set* set, float* r_lo, float* r_hi, float* A, float* B,
+                      const leb_options* opt, void* workspace, size_t ws_bytes, int* dev_flags, void* stream);
+
+/* ---- adjoint of the MLP bounds (differentiable LEBs, Sec. III-D) -------------------------------- */
+/* Box sets centred at the nominal only. Given g_rlo = dL/dr_lo and g_rhi = dL/dr_hi [T, n_x], writes
+ * g_x [T, n_x], g_u [T, n_u], g_radii [T, n] = dL/d(x~, u~, radii) of the piecewise-smooth bound
+ * (relaxation cases fixed at the evaluation point). All device pointers. */
+leb_status leb_bounds_backward(leb_handle h, int T, const float* x_nom, const float* u_nom, const leb_set* set,
+                               const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_radii,
+                               void* workspace, size_t ws_bytes, int* dev_flags, void* stream);
+
+/* ---- zonotope map of Sec. III-C as a standalone call -------------------------------------------- */
+/* c = (lo+hi)/2, r = (hi-lo)/2 + pad over count elements (device), r rounded up, c to nearest. */
+leb_status leb_zonotope_map(const float* r_lo, const float* r_hi, long long count, float pad, float* c,
+                            float* r, void* stream);
+
+/* ---- launch plans and autotuning ---------------------------------------------------------------- */
+/* Times the candidate launch configurations of this handle on synthetic data of T timesteps and the
+ * given set kind / generator count, keeps the fastest in the handle, and (if cache_path is not NULL)
+ * reads/writes a text cache keyed by GPU name and problem signature. Synchronizes the device: do not
+ * call during stream capture. Buffers: workspace as for leb_bounds. */
+leb_status leb_autotune(leb_handle h, int T, leb_set_kind set_kind, int n_gen, const char* cache_path,
+                        void* workspace, size_t ws_bytes, void* stream);
+/* Current plan as text ("key=value;..."), for logs and tests. */
+leb_status leb_plan_string(leb_handle h, char* buf, size_t buf_len);
+/* Force a plan by its index in the candidate list (-1 = back to the default / autotuned plan). */
+leb_status leb_plan_select(leb_handle h, int index);
+leb_status leb_plan_count(leb_handle h, int* count);
+
+/* ---- CUDA graphs -------------------------------------------------------------------------------- */
+/* Captures one leb_bounds call with these exact arguments into an executable CUDA graph (on a private
+ * stream), so a fixed batch can be relaunched with one call. The pointers must stay valid while the
+ * graph exists. */
+leb_status leb_graph_capture(leb_handle h, const leb_batch* batch, int T, const float* x_nom,
+                             const float* u_nom, const leb_set* set, float* r_lo, float* r_hi, float* A,
+                             float* B, const leb_options* opt, void* workspace, size_t ws_bytes,
+                             int* dev_flags, leb_graph* out);
+leb_status leb_graph_launch(leb_graph g, void* stream);
+leb_status leb_graph_destroy(leb_graph g);
+
+/* ---- learned bound proposer (an addition to the paper; never the final answer) ------------------- */
+/* ReLU MLP n_in -> n_hidden -> n_hidden -> n_out on the tensor cores (FP16 operands, FP32
+ * accumulation, FP32 master weights, Adam). Inputs are standardised and outputs de-standardised inside
+ * the kernels with the statistics set by leb_proposer_set_norm. Weights are initialised on the device
+ * from seed (He-uniform). All data pointers are device FP32. */
+leb_status leb_proposer_create(int n_in, int n_hidden, int n_out, unsigned long long seed, leb_proposer* out);
+leb_status leb_proposer_destroy(leb_proposer p);
+/* in_mean/in_std [n_in], out_mean/out_std [n_out]: device FP32, copied. */
+leb_status leb_proposer_set_norm(leb_proposer p, const float* in_mean, const float* in_std,
+                                 const float* out_mean, const float* out_std, void* stream);
+/* Y [B, n_out] = de-standardised network output for X [B, n_in]. */
+leb_status leb_proposer_forward(leb_proposer p, int B, const float* X, float* Y, void* workspace,
+                                size_t ws_bytes, void* stream);
+/* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the MSE between the network output and the
+ * standardised targets Ytgt [B, n_out]; loss (device float, may be NULL) receives the mean loss. */
+leb_status leb_proposer_train_step(leb_proposer p, int B, const float* X, const float* Ytgt, float lr,
+                                   float* loss, void* workspace, size_t ws_bytes, void* stream);
+leb_status leb_proposer_workspace_size(leb_proposer p, int B_max, size_t* bytes);
+/* Copy the FP32 master weights/biases of layer i (0..2) to or from device buffers W [out, in], b [out]. */
+leb_status leb_proposer_get_layer(leb_proposer p, int i, float* W, float* b, void* stream);
+leb_status leb_proposer_set_layer(leb_proposer p, int i, const float* W, const float* b, void* stream);
+/* Raw gradients of the last train step (for checks): dW [out, in], db [out]. */
+leb_status leb_proposer_get_grad(leb_proposer p, int i, float* dW, float* db, void* stream);
+
+/* ---- diagnostics -------------------------------------------------------------------------------- */
+/* Evaluates the library's point enclosures of sin, cos and tanh (the CUDA function value widened by
+ * the slack that covers its documented error) at n device inputs x, writing [lo, hi] pairs to the
+ * device arrays out_sin, out_cos, out_tanh ([n, 2] each). Used by tests to check the slack against
+ * FP64 host values. */
+leb_status leb_selftest_point_enclosures(const float* x, int n, float* out_sin, float* out_cos, float* out_tanh,
+                                         void* stream);
+
+const char* leb_status_string(leb_status st);
+const char* leb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEB_H */

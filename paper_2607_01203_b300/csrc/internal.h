@@ -1,0 +1,134 @@
+// Internal declarations shared by the library's translation units (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/leb.h"
+
+namespace leb {
+
+// FP32 enclosures [lo, hi] and round-to-nearest values of the quad-chain model constants.
+struct QuadConsts {
+  float c_lo, c_hi, c_f;     // dt / m
+  float dt_lo, dt_hi, dt_f;  // dt
+  float ks_lo, ks_hi, ks_f;  // dt * k / m
+  float tq_lo, tq_hi, tq_f;  // dt * arm / I
+  int springs;               // k != 0
+};
+
+struct PbhPlan {
+  int block;          // threads per CTA (zonotope kernel: one producer warp + consumer warps)
+  int ctas_per_sm;    // persistent grid = SMs * ctas_per_sm
+  int stages;         // shared-memory ring stages of the zonotope stream (kPbhStageCap bytes each)
+};
+constexpr int kPbhStageCap = 16384;
+
+struct PbhArgs {
+  const float* x_nom;
+  const float* u_nom;
+  const float* center;
+  const float* radii;
+  const float* G;
+  int n_gen;           // generators per timestep (uniform batch) or per quadrotor (uneven batch)
+  int zono;
+  float* r_lo;
+  float* r_hi;
+  float* A;
+  float* B;
+  float* gamma_c;
+  float* gamma_r;
+  float gamma_pad;
+  float* eps;
+  int* flags;
+  int T;
+  int nq;              // uniform chain length
+  int n_traj;
+  const int* traj_offsets;
+  const int* traj_nquads;   // NULL: uniform
+  const long long* pre1;    // [n_traj] sum_{b'<b} H_b' nq_b'
+  const long long* pre2;    // [n_traj] sum_{b'<b} H_b' nq_b'^2
+  int* counter;             // work-list counter
+  QuadConsts k;
+};
+
+// ---- MLP ---------------------------------------------------------------------------------------
+constexpr int kMaxLayers = 8;
+
+struct MlpModel {
+  int L = 0;                      // affine layers
+  int widths[kMaxLayers + 1] = {};
+  int act = 0;
+  int residual = 0;
+  int prec = 0;
+  // device copies
+  float* W[kMaxLayers] = {};      // [out, in] FP32
+  float* WT[kMaxLayers] = {};     // [in, out] FP32 (transposed, for K-major operand tiles)
+  float* b[kMaxLayers] = {};
+  __half* WTh[kMaxLayers] = {};   // [in, out] reduced-precision copy of W^T (tensor-core B operand)
+  float* Werr[kMaxLayers] = {};   // [out, in] |W - W~| (W~ = reduced-precision value), FP32 rounded up
+  float* Wabs_h[kMaxLayers] = {}; // [out, in] |W~| FP32
+};
+
+// Workspace layout of the MLP path (offsets in floats; [T, H] arrays hold every hidden layer of a
+// timestep contiguously, layer i at hoff[i]).
+struct MlpWs {
+  size_t zhat, zrad;        // nominal pre-activations z^ and enclosure radii e (|z^ - z~| <= e)
+  size_t hhat, hrad;        // nominal post-activations and their enclosure radii
+  size_t lo, hi;            // pre-activation bounds over the set
+  size_t sL, tL, sU, tU;    // relaxation lines in delta form (tL/tU are the offsets tau)
+  size_t D;                 // sigma'(z^) (slopes of the Jacobian chain)
+  size_t abar;              // bound on |sigma(z) - sigma(z~)| over the set
+  size_t loss;              // part of the lines' offsets due to the nominal enclosure (stated slack)
+  size_t v1, v2;            // |W~_k| abar_{k-1} and |W_k - W~_k| abar_{k-1} per neuron of hidden layer k
+  size_t bslack;            // stated slack of the intermediate bounds (max of both directions)
+  size_t anom, dlo, dhi;    // [T, n] nominal alpha~ and displacement box Delta = X - alpha~
+  size_t bad;               // [T] int: non-finite inputs
+  size_t total;             // floats
+  int H;                    // total hidden neurons
+  int hoff[kMaxLayers];     // offset of hidden layer i (0-based) inside H
+};
+
+struct Ctx {
+  leb_dyn_kind kind;
+  int n_x = 0, n_u = 0;
+  // quad chain
+  int nq = 0;
+  QuadConsts qk{};
+  PbhPlan pbh_plan{256, 2, 6};
+  std::vector<PbhPlan> pbh_candidates;
+  int plan_index = -1;
+  // mlp
+  MlpModel mlp;
+  int sm_count = 148;
+  int device = 0;
+  std::string plan_note;
+};
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_pbh(const Ctx& c, const PbhArgs& a, const PbhPlan& p, cudaStream_t s);
+cudaError_t launch_prefix(const int* traj_offsets, const int* traj_nquads, int n_traj, long long* pre1,
+                          long long* pre2, cudaStream_t s);
+cudaError_t launch_zonotope_map(const float* lo, const float* hi, long long count, float pad, float* c, float* r,
+                                cudaStream_t s);
+
+size_t mlp_workspace_floats(const Ctx& c, int T, MlpWs* layout);
+leb_status mlp_bounds(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set, float* r_lo,
+                      float* r_hi, float* A, float* B, const leb_options* opt, void* ws, int* flags, cudaStream_t s);
+leb_status mlp_bounds_backward(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set,
+                               const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_rad,
+                               void* ws, int* flags, cudaStream_t s);
+leb_status mlp_prepare(Ctx& c);
+void mlp_release(Ctx& c);
+size_t simt_chain_smem(int maxw);
+leb_status run_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, float* r_lo, float* r_hi, float* A,
+                     float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt);
+// tensor-core back-substitution (reduced-precision operands, FP32 accumulation in TMEM)
+leb_status tc_prepare(Ctx& c);
+void tc_release(Ctx& c);
+leb_status tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, float* r_lo, float* r_hi, float* A,
+                    float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt);
+
+}  // namespace leb

@@ -1,0 +1,534 @@
+// Path-based Hessian bounds (Thm. 1, Eq. 15) for the spring-coupled planar-quadrotor chain.
+//
+// One persistent launch walks a device work list of timesteps (a ragged batch of trajectories of
+// uneven horizon and, optionally, uneven chain length). For each timestep one CTA
+//   1. reduces the tube set to its interval hull: a box, or a zonotope c + G xi reduced row by row
+//      with the row-wise l1 norm (Eq. 21) — one warp per row, 16-byte streaming loads, sums rounded
+//      upward — and hulls it with the nominal point (Thm. 1 needs alpha~ in X);
+//   2. evaluates, thread per output row, the Hessian terms of Eq. 15 over their prefix sets
+//      X^(j) in outward-rounded FP32 interval arithmetic, plus the term (J - A) Delta that makes the
+//      bound sound for the FP32 Jacobian actually returned;
+//   3. streams A_k and B_k (Eq. 8) to memory with 16-byte stores (banded: zeros outside the
+//      quadrotor's neighbourhood).
+// Model (App. A planar quadrotor, forward Euler), per quadrotor i with S = u1 + u2:
+//   v_x+ = v_x + dt(-(S/m) sin phi + (k/m) sum_nbr (p_x,j - p_x,i)),
+//   v_y+ = v_y + dt( (S/m) cos phi - g + (k/m) sum_nbr (p_y,j - p_y,i)),
+//   omega+ = omega + dt (arm/I)(u2 - u1), positions/angle integrate their rates.
+// Curved entries (all with prefix set X^(phi): phi ranges over X, the inputs sit at the nominal):
+//   v_x row: H_{phi phi} = (dt/m) S sin phi, H_{u_r phi} = -(dt/m) cos phi
+//   v_y row: H_{phi phi} = -(dt/m) S cos phi, H_{u_r phi} = -(dt/m) sin phi
+#include "internal.h"
+#include "interval.cuh"
+#include "sync.cuh"
+
+namespace leb {
+
+struct Item {
+  int nq;
+  int n_gen;
+  long long x_off, u_off, n_off, g_off, a_off, b_off;
+};
+
+__device__ __forceinline__ float warp_sum_ru(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ Item make_item(const PbhArgs& a, int t) {
+  Item it;
+  if (a.traj_nquads == nullptr) {
+    it.nq = a.nq;
+    it.n_gen = a.n_gen;
+    const long long nx = 6LL * a.nq, nu = 2LL * a.nq, n = nx + nu;
+    it.x_off = t * nx;
+    it.u_off = t * nu;
+    it.n_off = t * n;
+    it.g_off = t * n * a.n_gen;
+    it.a_off = t * nx * nx;
+    it.b_off = t * nx * nu;
+  } else {
+    // trajectory of timestep t: last b with traj_offsets[b] <= t
+    int lo = 0, hi = a.n_traj - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (__ldg(a.traj_offsets + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    const int b = lo;
+    const long long k = t - __ldg(a.traj_offsets + b);
+    const long long nq = __ldg(a.traj_nquads + b);
+    const long long p1 = a.pre1[b] + k * nq;        // sum of nq over earlier timesteps
+    const long long p2 = a.pre2[b] + k * nq * nq;   // sum of nq^2 over earlier timesteps
+    it.nq = (int)nq;
+    it.n_gen = a.n_gen * (int)nq;
+    it.x_off = 6 * p1;
+    it.u_off = 2 * p1;
+    it.n_off = 8 * p1;
+    it.g_off = 8LL * a.n_gen * p2;
+    it.a_off = 36 * p2;
+    it.b_off = 12 * p2;
+  }
+  return it;
+}
+
+// Round-to-nearest values written to A_k, B_k for quadrotor i's curved rows (a pure function of the
+// nominal), computed once per timestep into shared memory and used by both the A/B stores and the
+// (J - A) Delta term, so the bound refers to exactly the stored values.
+struct QuadA {
+  float aphi_x, au_x, aphi_y, au_y;
+};
+
+__device__ __forceinline__ QuadA quad_avals(const float* xn, const float* un, int i, const QuadConsts& K) {
+  const float phi0 = xn[6 * i + 2];
+  const float S_f = un[2 * i] + un[2 * i + 1];
+  const float cph = cosf(phi0), sph = sinf(phi0);
+  QuadA q;
+  q.aphi_x = -K.c_f * S_f * cph;
+  q.au_x = -K.c_f * sph;
+  q.aphi_y = -K.c_f * S_f * sph;
+  q.au_y = K.c_f * cph;
+  return q;
+}
+
+// A_k entry (row l, column j); q holds the curved entries of row l's quadrotor.
+__device__ __forceinline__ float a_entry(int l, int j, int nq, const QuadA& q, const QuadConsts& k) {
+  const int i = l / 6, s = l - 6 * i;
+  const int qj = j / 6, sj = j - 6 * qj;
+  if (qj == i) {
+    if (sj == s) return 1.f;
+    if (s < 3 && sj == s + 3) return k.dt_f;
+    const int deg = k.springs ? (i > 0) + (i + 1 < nq) : 0;
+    if (s == 3) { if (sj == 2) return q.aphi_x; if (sj == 0 && deg) return -(float)deg * k.ks_f; }
+    if (s == 4) { if (sj == 2) return q.aphi_y; if (sj == 1 && deg) return -(float)deg * k.ks_f; }
+    return 0.f;
+  }
+  if (k.springs && (qj == i - 1 || qj == i + 1)) {
+    if (s == 3 && sj == 0) return k.ks_f;
+    if (s == 4 && sj == 1) return k.ks_f;
+  }
+  return 0.f;
+}
+
+__device__ __forceinline__ float b_entry(int l, int c, const QuadA& q, const QuadConsts& k) {
+  const int i = l / 6, s = l - 6 * i;
+  if ((c >> 1) != i) return 0.f;
+  if (s == 3) return q.au_x;
+  if (s == 4) return q.au_y;
+  if (s == 5) return (c & 1) ? k.tq_f : -k.tq_f;
+  return 0.f;
+}
+
+// A_k and B_k rows, warp per row (banded, 16-byte streaming stores when the row length allows).
+__device__ __forceinline__ void write_AB(const PbhArgs& a, const Item& it, const QuadA* qa, int wid, int nw,
+                                         int lane) {
+  const QuadConsts& K = a.k;
+  const int nq = it.nq, nx = 6 * nq, nu = 2 * nq;
+  if (a.A) {
+    float* At = a.A + it.a_off;
+    const bool v4 = ((nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(At) & 15) == 0);
+    for (int l = wid; l < nx; l += nw) {
+      const int i = l / 6;
+      const QuadA q = qa[i];
+      if (v4) {
+        const int band_lo = 6 * (i - 1), band_hi = 6 * (i + 2);
+        float4* rowp = reinterpret_cast<float4*>(At + (long long)l * nx);
+        for (int c = lane; c < (nx >> 2); c += 32) {
+          const int j0 = 4 * c;
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (j0 + 4 > band_lo && j0 < band_hi) {
+            v.x = a_entry(l, j0, nq, q, K);
+            v.y = a_entry(l, j0 + 1, nq, q, K);
+            v.z = a_entry(l, j0 + 2, nq, q, K);
+            v.w = a_entry(l, j0 + 3, nq, q, K);
+          }
+          __stcs(rowp + c, v);
+        }
+      } else {
+        for (int j = lane; j < nx; j += 32) At[(long long)l * nx + j] = a_entry(l, j, nq, q, K);
+      }
+    }
+  }
+  if (a.B) {
+    float* Bt = a.B + it.b_off;
+    const bool v4 = ((nu & 3) == 0) && ((reinterpret_cast<uintptr_t>(Bt) & 15) == 0);
+    for (int l = wid; l < nx; l += nw) {
+      const int i = l / 6;
+      const QuadA q = qa[i];
+      if (v4) {
+        float4* rowp = reinterpret_cast<float4*>(Bt + (long long)l * nu);
+        for (int c = lane; c < (nu >> 2); c += 32) {
+          const int j0 = 4 * c;
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (j0 + 4 > 2 * i && j0 < 2 * i + 2) {
+            v.x = b_entry(l, j0, q, K);
+            v.y = b_entry(l, j0 + 1, q, K);
+            v.z = b_entry(l, j0 + 2, q, K);
+            v.w = b_entry(l, j0 + 3, q, K);
+          }
+          __stcs(rowp + c, v);
+        }
+      } else {
+        for (int c = lane; c < nu; c += 32) Bt[(long long)l * nu + c] = b_entry(l, c, q, K);
+      }
+    }
+  }
+}
+
+// Eq. 15 for every output row of one timestep (thread per row), plus (J - A) Delta.
+__device__ __forceinline__ void pbh_rows(const PbhArgs& a, const Item& it, const float* xn, const float* un,
+                                         const float* s_lo, const float* s_hi, const QuadA* qa, bool bad, int tid,
+                                         int nthr) {
+  const QuadConsts& K = a.k;
+  const int nq = it.nq, nx = 6 * nq;
+  const ivl cI = iv(K.c_lo, K.c_hi);
+  for (int l = tid; l < nx; l += nthr) {
+    const int i = l / 6, s = l - 6 * i;
+    auto D = [&](int j) {  // Delta_j = X_j - alpha~_j
+      const float nom = j < nx ? xn[j] : un[j - nx];
+      return iv(__fsub_rd(s_lo[j], nom), __fsub_ru(s_hi[j], nom));
+    };
+    auto corr = [&](ivl Jiv, float Aval, ivl Dj) { return iv_mul(iv_sub(Jiv, iv(Aval)), Dj); };
+    ivl R = iv(0.f);
+    const int deg = K.springs ? (i > 0) + (i + 1 < nq) : 0;
+    if (s < 3) {
+      R = corr(iv(K.dt_lo, K.dt_hi), K.dt_f, D(l + 3));
+    } else if (s == 3 || s == 4) {
+      const int jp = 6 * i + 2, j1 = nx + 2 * i, j2 = j1 + 1;
+      const float phi0 = xn[jp];
+      const float u1 = un[2 * i], u2 = un[2 * i + 1];
+      const ivl S = iv(__fadd_rd(u1, u2), __fadd_ru(u1, u2));  // S~ (inputs fixed on X^(phi))
+      const ivl Phi = iv(s_lo[jp], s_hi[jp]);
+      const ivl Dp = D(jp), D1 = D(j1), D2 = D(j2);
+      const ivl Dp2 = iv_sqr(Dp);
+      const QuadA q = qa[i];
+      float Aphi, Au;
+      ivl Jphi, Ju;
+      if (s == 3) {
+        // 1/2 [H_pp](X^(phi)) Dphi^2 + [H_1p](X^(phi)) Dphi Du1 + [H_2p](X^(phi)) Dphi Du2
+        const ivl Hpp = iv_mul(iv_mul(cI, S), iv_sin(Phi));
+        const ivl Hup = iv_neg(iv_mul(cI, iv_cos(Phi)));
+        R = iv_half(iv_mul(Hpp, Dp2));
+        R = iv_add(R, iv_mul(Hup, iv_mul(Dp, D1)));
+        R = iv_add(R, iv_mul(Hup, iv_mul(Dp, D2)));
+        Aphi = q.aphi_x;
+        Au = q.au_x;
+        Jphi = iv_neg(iv_mul(iv_mul(cI, S), point_cos(phi0)));
+        Ju = iv_neg(iv_mul(cI, point_sin(phi0)));
+      } else {
+        const ivl Hpp = iv_neg(iv_mul(iv_mul(cI, S), iv_cos(Phi)));
+        const ivl Hup = iv_neg(iv_mul(cI, iv_sin(Phi)));
+        R = iv_half(iv_mul(Hpp, Dp2));
+        R = iv_add(R, iv_mul(Hup, iv_mul(Dp, D1)));
+        R = iv_add(R, iv_mul(Hup, iv_mul(Dp, D2)));
+        Aphi = q.aphi_y;
+        Au = q.au_y;
+        Jphi = iv_neg(iv_mul(iv_mul(cI, S), point_sin(phi0)));
+        Ju = iv_mul(cI, point_cos(phi0));
+      }
+      R = iv_add(R, corr(Jphi, Aphi, Dp));
+      R = iv_add(R, corr(Ju, Au, D1));
+      R = iv_add(R, corr(Ju, Au, D2));
+      if (deg) {
+        const int sc = s - 3;  // 0: p_x column, 1: p_y column
+        const ivl ks = iv(K.ks_lo, K.ks_hi);
+        const ivl self = iv_mul(iv(-(float)deg), ks);
+        R = iv_add(R, corr(self, -(float)deg * K.ks_f, D(6 * i + sc)));
+        if (i > 0) R = iv_add(R, corr(ks, K.ks_f, D(6 * (i - 1) + sc)));
+        if (i + 1 < nq) R = iv_add(R, corr(ks, K.ks_f, D(6 * (i + 1) + sc)));
+      }
+    } else {  // omega row: dt arm / I (u2 - u1)
+      const ivl tq = iv(K.tq_lo, K.tq_hi);
+      R = iv_add(corr(iv_neg(tq), -K.tq_f, D(nx + 2 * i)), corr(tq, K.tq_f, D(nx + 2 * i + 1)));
+    }
+    if (bad || !finite_ivl(R)) R = iv(-CUDART_INF_F, CUDART_INF_F);
+    const long long o = it.x_off + l;
+    a.r_lo[o] = R.lo;
+    a.r_hi[o] = R.hi;
+    if (a.gamma_c) {
+      const float c = 0.5f * R.lo + 0.5f * R.hi;
+      a.gamma_c[o] = c;
+      a.gamma_r[o] = __fadd_ru(fmaxf(__fsub_ru(R.hi, c), __fsub_ru(c, R.lo)), a.gamma_pad);
+    }
+    if (a.eps) a.eps[o] = 0.f;
+  }
+}
+
+__device__ __forceinline__ void compute_qa(const float* xn, const float* un, int nq, const QuadConsts& K, QuadA* qa,
+                                           int tid, int nthr) {
+  for (int i = tid; i < nq; i += nthr) qa[i] = quad_avals(xn, un, i, K);
+}
+
+__device__ __forceinline__ float row_l1_ru(const float* row, int p, int lane, bool vec) {
+  float sum = 0.f;
+  if (vec) {
+    const float4* row4 = reinterpret_cast<const float4*>(row);
+#pragma unroll 4
+    for (int c = lane; c < (p >> 2); c += 32) {
+      const float4 v = row4[c];
+      sum = __fadd_ru(sum, fabsf(v.x));
+      sum = __fadd_ru(sum, fabsf(v.y));
+      sum = __fadd_ru(sum, fabsf(v.z));
+      sum = __fadd_ru(sum, fabsf(v.w));
+    }
+  } else {
+    for (int c = lane; c < p; c += 32) sum = __fadd_ru(sum, fabsf(row[c]));
+  }
+  return warp_sum_ru(sum);
+}
+
+// Box hull of one set row, hulled with the nominal; returns false if not finite.
+__device__ __forceinline__ bool hull_row(const PbhArgs& a, const Item& it, const float* xn, const float* un, int r,
+                                         float half, float* s_lo, float* s_hi) {
+  const int nx = 6 * it.nq;
+  const float nom = r < nx ? xn[r] : un[r - nx];
+  const float c = a.center ? a.center[it.n_off + r] : nom;
+  const float lo = fminf(__fsub_rd(c, half), nom);
+  const float hi = fmaxf(__fadd_ru(c, half), nom);
+  s_lo[r] = lo;
+  s_hi[r] = hi;
+  return isfinite(lo) && isfinite(hi) && isfinite(nom) && half >= 0.f;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Kernel 1 (box sets, and zonotopes that cannot be bulk-copied): all warps reduce the set, then all
+// warps evaluate the rows and store A_k, B_k.
+// ---------------------------------------------------------------------------------------------------
+template <bool kZono>
+__global__ void __launch_bounds__(256, 4) pbh_chain_kernel(PbhArgs a) {
+  extern __shared__ float smem[];
+  __shared__ int s_t;
+  __shared__ Item s_it;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int n_max = 8 * a.nq;
+  float* s_lo = smem;
+  float* s_hi = smem + n_max;
+  QuadA* s_qa = reinterpret_cast<QuadA*>(smem + 2 * n_max);
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_t = atomicAdd(a.counter, 1);
+      if (s_t < a.T) s_it = make_item(a, s_t);
+    }
+    __syncthreads();
+    const int t = s_t;
+    if (t >= a.T) break;
+    const Item it = s_it;
+    const int n = 8 * it.nq;
+    const float* xn = a.x_nom + it.x_off;
+    const float* un = a.u_nom + it.u_off;
+    bool ok = true;
+    if (kZono) {
+      const int p = it.n_gen;
+      const float* Gt = a.G + it.g_off;
+      for (int r = warp; r < n; r += nwarps) {
+        const float half = row_l1_ru(Gt + (long long)r * p, p, lane, false);
+        if (lane == 0) ok &= hull_row(a, it, xn, un, r, half, s_lo, s_hi);
+      }
+    } else {
+      for (int r = threadIdx.x; r < n; r += blockDim.x) ok &= hull_row(a, it, xn, un, r, a.radii[it.n_off + r], s_lo, s_hi);
+    }
+    compute_qa(xn, un, it.nq, a.k, s_qa, threadIdx.x, blockDim.x);
+    const bool bad = __syncthreads_or(!ok) != 0;
+    pbh_rows(a, it, xn, un, s_lo, s_hi, s_qa, bad, threadIdx.x, blockDim.x);
+    write_AB(a, it, s_qa, warp, nwarps, lane);
+    if (bad && threadIdx.x == 0) atomicOr(a.flags, LEB_ASYNC_NONFINITE);
+    __syncthreads();  // shared buffers are reused by the next timestep
+  }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Kernel 2 (zonotopes): warp 0 streams every timestep's generators G[t] (one contiguous block) through
+// a ring of shared-memory stages with bulk async copies (TMA); the other warps reduce rows out of shared
+// memory, then evaluate Eq. 15 and store A_k, B_k while the copies of the next timestep are in flight.
+// ---------------------------------------------------------------------------------------------------
+struct StageMeta {
+  int t, chunk, last, rows;
+};
+
+__global__ void __launch_bounds__(256, 2) pbh_zono_tma_kernel(PbhArgs a, int S, int stage_bytes_cap) {
+  extern __shared__ __align__(128) unsigned char sraw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int ncons = nwarps - 1, ncthr = ncons * 32;
+  const int n_max = 8 * a.nq;
+  unsigned char* stages = sraw;  // S * stage_bytes_cap, 128-byte aligned
+  float* s_lo = reinterpret_cast<float*>(sraw + (size_t)S * stage_bytes_cap);  // [2][n_max]
+  float* s_hi = s_lo + 2 * n_max;                                               // [2][n_max]
+  QuadA* s_qa = reinterpret_cast<QuadA*>(s_hi + 2 * n_max);                    // [2][nq]
+  StageMeta* meta = reinterpret_cast<StageMeta*>(s_qa + 2 * a.nq);             // [S]
+  uint64_t* full = reinterpret_cast<uint64_t*>(
+      (reinterpret_cast<uintptr_t>(meta + S) + 7) & ~uintptr_t(7));             // [S]
+  uint64_t* empty = full + S;                                                   // [S]
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], ncons);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer --------------------------------------------------------------------------
+      uint32_t k = 0;
+      bool ok = true;
+      for (bool done = false; !done && ok;) {
+        const int t = atomicAdd(a.counter, 1);
+        done = t >= a.T;
+        Item it{};
+        int rows_per = 1, nch = 1, n = 0;
+        if (!done) {
+          it = make_item(a, t);
+          n = 8 * it.nq;
+          rows_per = max(1, stage_bytes_cap / (it.n_gen * 4));
+          nch = (n + rows_per - 1) / rows_per;
+        }
+        for (int c = 0; c < nch; ++c, ++k) {
+          const int s = (int)(k % (uint32_t)S);
+          const uint32_t ph = (k / (uint32_t)S) & 1u;
+          if (k >= (uint32_t)S && !mbar_wait(&empty[s], ph ^ 1u)) { ok = false; break; }
+          if (done) {
+            meta[s] = StageMeta{-1, 0, 1, 0};
+            mbar_arrive(&full[s]);
+          } else {
+            const int rows = min(rows_per, n - c * rows_per);
+            const uint32_t bytes = (uint32_t)rows * (uint32_t)it.n_gen * 4u;
+            meta[s] = StageMeta{t, c, c == nch - 1, rows};
+            mbar_arrive_expect_tx(&full[s], bytes);
+            bulk_g2s(stages + (size_t)s * stage_bytes_cap, a.G + it.g_off + (long long)c * rows_per * it.n_gen, bytes,
+                     &full[s]);
+          }
+        }
+      }
+      if (!ok) {
+        atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
+        // drain: every posted copy must land before the block exits
+        for (uint32_t j = (k > (uint32_t)S ? k - (uint32_t)S : 0u); j < k; ++j)
+          mbar_wait(&full[j % (uint32_t)S], (j / (uint32_t)S) & 1u);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- consumers ---------------------------------------------------------------------------
+    const int cw = warp - 1, ctid = threadIdx.x - 32;
+    uint32_t k = 0;
+    int slot = 0;
+    bool ok = true;  // this thread saw only finite rows
+    for (;;) {
+      const int s = (int)(k % (uint32_t)S);
+      const uint32_t ph = (k / (uint32_t)S) & 1u;
+      if (!mbar_wait(&full[s], ph)) {
+        if (ctid == 0) atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
+        break;
+      }
+      const StageMeta m = meta[s];
+      if (m.t < 0) break;
+      const Item it = make_item(a, m.t);
+      const float* xn = a.x_nom + it.x_off;
+      const float* un = a.u_nom + it.u_off;
+      float* lo = s_lo + slot * n_max;
+      float* hi = s_hi + slot * n_max;
+      QuadA* qa = s_qa + slot * a.nq;
+      if (m.chunk == 0) compute_qa(xn, un, it.nq, a.k, qa, ctid, ncthr);
+      const int p = it.n_gen;
+      const int rows_per = max(1, stage_bytes_cap / (p * 4));
+      const float* stage = reinterpret_cast<const float*>(stages + (size_t)s * stage_bytes_cap);
+      for (int rl = cw; rl < m.rows; rl += ncons) {
+        const float half = row_l1_ru(stage + (size_t)rl * p, p, lane, true);
+        if (lane == 0) ok &= hull_row(a, it, xn, un, m.chunk * rows_per + rl, half, lo, hi);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+      ++k;
+      if (m.last) {
+        const bool bad = bar_sync_or(1, ncthr, !ok);
+        ok = true;
+        pbh_rows(a, it, xn, un, lo, hi, qa, bad, ctid, ncthr);
+        write_AB(a, it, qa, cw, ncons, lane);
+        if (bad && ctid == 0) atomicOr(a.flags, LEB_ASYNC_NONFINITE);
+        slot ^= 1;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Prefix sums over trajectories for packed uneven-dimension batches (single block, sequential scan
+// by thread 0 — n_traj is small and this runs once per call).
+__global__ void prefix_kernel(const int* offs, const int* nqs, int n_traj, long long* pre1, long long* pre2) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  long long s1 = 0, s2 = 0;
+  for (int b = 0; b < n_traj; ++b) {
+    pre1[b] = s1;
+    pre2[b] = s2;
+    const long long H = offs[b + 1] - offs[b];
+    const long long q = nqs[b];
+    s1 += H * q;
+    s2 += H * q * q;
+  }
+}
+
+__global__ void zonotope_map_kernel(const float* lo, const float* hi, long long count, float pad, float* c, float* r) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    const float l = lo[i], h = hi[i];
+    const float m = 0.5f * l + 0.5f * h;
+    c[i] = m;
+    r[i] = __fadd_ru(fmaxf(__fsub_ru(h, m), __fsub_ru(m, l)), pad);
+  }
+}
+
+bool pbh_tma_ok(const PbhArgs& a) {
+  if (!a.zono) return false;
+  if ((reinterpret_cast<uintptr_t>(a.G) & 15) != 0) return false;
+  if (a.traj_nquads)  // n_gen counts generators per quadrotor; rows of the longest chain must fit a stage
+    return (a.n_gen % 4) == 0 && (long long)a.n_gen * a.nq * 4 <= kPbhStageCap;
+  return (a.n_gen % 4) == 0 && a.n_gen * 4 <= kPbhStageCap;
+}
+
+size_t pbh_tma_smem(const PbhArgs& a, int S) {
+  const int n_max = 8 * a.nq;
+  size_t b = (size_t)S * kPbhStageCap + 4 * (size_t)n_max * 4 + 2 * (size_t)a.nq * sizeof(QuadA) +
+             (size_t)S * sizeof(StageMeta);
+  b = (b + 7) & ~size_t(7);
+  return b + 2 * (size_t)S * 8;
+}
+
+cudaError_t launch_pbh(const Ctx& c, const PbhArgs& a, const PbhPlan& p, cudaStream_t s) {
+  const int grid = c.sm_count * p.ctas_per_sm;
+  if (pbh_tma_ok(a)) {
+    const size_t smem = pbh_tma_smem(a, p.stages);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(pbh_zono_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      attr = true;
+    }
+    pbh_zono_tma_kernel<<<grid, p.block, smem, s>>>(a, p.stages, kPbhStageCap);
+    return cudaGetLastError();
+  }
+  const int n_max = 8 * a.nq;
+  const size_t smem = (size_t)(2 * n_max) * sizeof(float) + (size_t)a.nq * sizeof(QuadA);
+  const int block = p.block > 256 ? 256 : p.block;
+  if (a.zono)
+    pbh_chain_kernel<true><<<c.sm_count * 4, block, smem, s>>>(a);
+  else
+    pbh_chain_kernel<false><<<c.sm_count * 4, block, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prefix(const int* traj_offsets, const int* traj_nquads, int n_traj, long long* pre1,
+                          long long* pre2, cudaStream_t s) {
+  prefix_kernel<<<1, 32, 0, s>>>(traj_offsets, traj_nquads, n_traj, pre1, pre2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zonotope_map(const float* lo, const float* hi, long long count, float pad, float* c, float* r,
+                                cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  long long blocks = (count + 255) / 256;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  zonotope_map_kernel<<<(int)blocks, 256, 0, s>>>(lo, hi, count, pad, c, r);
+  return cudaGetLastError();
+}
+
+}  // namespace leb

@@ -1,0 +1,25 @@
+// Diagnostic entry point: the point enclosures of sin/cos/tanh used by the bound kernels.
+#include "internal.h"
+#include "interval.cuh"
+#include "mlp_math.cuh"
+
+namespace leb {
+__global__ void point_enclosure_kernel(const float* x, int n, float2* s, float2* c, float2* th) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float v = x[i];
+  const ivl a = point_sin(v), b = point_cos(v), t = point_tanh(v);
+  s[i] = make_float2(a.lo, a.hi);
+  c[i] = make_float2(b.lo, b.hi);
+  th[i] = make_float2(t.lo, t.hi);
+}
+}  // namespace leb
+
+extern "C" leb_status leb_selftest_point_enclosures(const float* x, int n, float* out_sin, float* out_cos,
+                                                     float* out_tanh, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !out_sin || !out_cos || !out_tanh))) return LEB_ERR_INVALID_ARG;
+  if (n == 0) return LEB_OK;
+  leb::point_enclosure_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
+      x, n, (float2*)out_sin, (float2*)out_cos, (float2*)out_tanh);
+  return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
+}

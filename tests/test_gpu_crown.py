@@ -1,0 +1,121 @@
+"""GPU parity of the CROWN remainder bound (Thms. 2-3) against the FP64 oracle, through the C ABI.
+
+Tolerance: the kernel returns with every bound a stated slack eps_l (its rigorous rounding inflation of
+the back-substitution GEMMs plus the part of its relaxation offsets that comes from enclosing the FP32
+nominal pass); apart from that it evaluates the oracle's algorithm in FP32 with outward rounding. So
+
+    |gpu - oracle| <= 1e-5 * w_l + 2 * eps_l + 2^-20 * s_l
+
+per bound, with w_l the oracle's width and s_l = max(|oracle_lo|, |oracle_hi|) (FP32 representation of
+the result). Soundness is checked separately: the GPU bound must contain the exact remainder range
+(ReLU enumeration) and every sampled remainder w.r.t. the A, B it returned.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import crown, exact, sampling
+from paper_2607_01203_b300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def _t(x, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(DEV, dtype)
+
+
+def run(w, prec="fp32", rows=None, center=None, radii=None):
+    h = binding.mlp(w.Ws, w.bs, w.act, w.residual, prec)
+    sel = slice(None) if rows is None else rows
+    rad = w.radii if radii is None else radii
+    out = h.bounds(_t(w.x_nom[sel]), _t(w.u_nom[sel]), radii=_t(rad[sel]),
+                   center=None if center is None else _t(center[sel]), want_eps=True)
+    torch.cuda.synchronize()
+    return {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in out.items()}
+
+
+def parity(w, g, rows):
+    worst = 0.0
+    for i, t in enumerate(rows):
+        ol, oh, J = crown.box_remainder(w.Ws, w.bs, w.act, w.x_nom[t], w.u_nom[t], w.radii[t], w.residual)
+        wdt = oh - ol
+        eps = g["eps"][i].astype(np.float64)
+        scale = np.maximum(np.abs(ol), np.abs(oh))
+        tol = 1e-5 * wdt + 2 * eps + 2.0 ** -20 * scale
+        dl = np.abs(g["r_lo"][i] - ol)
+        dh = np.abs(g["r_hi"][i] - oh)
+        worst = max(worst, float(np.max(np.maximum(dl, dh) / tol)))
+        assert np.all(dl <= tol) and np.all(dh <= tol), (t, np.max(dl - tol), np.max(dh - tol))
+        AB = np.concatenate([g["A"][i], g["B"][i]], axis=1)
+        assert np.all(np.abs(AB - J) <= 1e-5 * np.abs(J) + 1e-6)
+    return worst
+
+
+def test_relu_parity_all_timesteps():
+    w = inputs.relu_mlp()
+    g = run(w)
+    assert g["flags"][0] == 0
+    parity(w, g, list(range(w.T)))
+    assert np.all(g["eps"] >= 0) and np.all(g["r_lo"] <= g["r_hi"])
+
+
+def test_relu_contains_exact_range_for_returned_linearization():
+    """Soundness against the enumerated exact range w.r.t. the A, B the GPU returned."""
+    w = inputs.relu_mlp()
+    g = run(w)
+    for t in (0, 7, 19):
+        a = w.nominal()[t].astype(np.float64)
+        lin = np.concatenate([g["A"][t], g["B"][t]], axis=1).astype(np.float64)
+        el, eh, _ = exact.relu_exact_range(w.Ws, w.bs, a, a - w.radii[t], a + w.radii[t], lin=lin)
+        assert np.all(g["r_lo"][t] <= el) and np.all(g["r_hi"][t] >= eh)
+
+
+@pytest.mark.parametrize("act", ["relu", "tanh"])
+def test_soundness_1e6_samples_per_set(act):
+    w = inputs.relu_mlp() if act == "relu" else inputs.tanh_mlp(n_traj=1, N=3)
+    rows = list(range(min(w.T, 4)))
+    g = run(w, rows=rows)
+    f = sampling.mlp_f_batch(w.Ws, w.bs, w.act)
+    rng = np.random.default_rng(5)
+    for i, t in enumerate(rows):
+        a = w.nominal()[t].astype(np.float64)
+        lin = np.concatenate([g["A"][i], g["B"][i]], axis=1).astype(np.float64)
+        n_pts = 1_000_000 if act == "relu" else 100_000
+        for _ in range(n_pts // 100_000):
+            P = sampling.box_points(a - w.radii[t], a + w.radii[t], 100_000, rng)
+            R = sampling.remainders(f, a, lin, P)
+            assert np.all(R >= g["r_lo"][i]) and np.all(R <= g["r_hi"][i])
+
+
+def test_tanh_parity_fp32_subset():
+    w = inputs.tanh_mlp(n_traj=2, N=50)
+    rows = [0, 1, 17, 49, 50, 99]
+    g = run(w, rows=rows)
+    assert g["flags"][0] == 0
+    parity(w, g, rows)
+
+
+def test_small_tanh_net_several_layers_parity():
+    w = inputs.tanh_mlp(n_traj=1, N=6, widths=(10, 24, 24, 24, 24, 6))
+    g = run(w)
+    parity(w, g, list(range(w.T)))
+
+
+def test_edge_cases():
+    w = inputs.relu_mlp(N=5)
+    # non-finite radius -> that timestep is [-inf, inf], flag raised, others finite
+    rad = w.radii.copy()
+    rad[1, 0] = np.inf
+    g = run(w, radii=rad)
+    assert g["flags"][0] & binding.ASYNC_NONFINITE
+    assert np.all(np.isneginf(g["r_lo"][1])) and np.all(np.isposinf(g["r_hi"][1]))
+    assert np.all(np.isfinite(g["r_lo"][[0, 2, 3, 4]]))
+    # zero radii: the remainder is exactly zero; the bound is within its stated slack of 0
+    g0 = run(w, radii=np.zeros_like(w.radii))
+    assert np.all(np.abs(g0["r_lo"]) <= 2 * g0["eps"] + 1e-12)
+    assert np.all(np.abs(g0["r_hi"]) <= 2 * g0["eps"] + 1e-12)
+    # empty batch
+    h = binding.mlp(w.Ws, w.bs, w.act)
+    out = h.bounds(_t(w.x_nom[:0]), _t(w.u_nom[:0]), radii=_t(w.radii[:0]))
+    assert out["r_lo"].numel() == 0
