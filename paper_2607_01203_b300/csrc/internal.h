@@ -70,6 +70,7 @@ struct MlpModel {
   __half* WTh[kMaxLayers] = {};   // [in, out] reduced-precision copy of W^T (tensor-core B operand)
   float* Werr[kMaxLayers] = {};   // [out, in] |W - W~| (W~ = reduced-precision value), FP32 rounded up
   float* Wabs_h[kMaxLayers] = {}; // [out, in] |W~| FP32
+  void* tc = nullptr;             // tensor-core state (rounded transposed weights, TMA descriptors)
 };
 
 // Workspace layout of the MLP path (offsets in floats; [T, H] arrays hold every hidden layer of a
@@ -84,6 +85,8 @@ struct MlpWs {
   size_t loss;              // part of the lines' offsets due to the nominal enclosure (stated slack)
   size_t v1, v2;            // |W~_k| abar_{k-1} and |W_k - W~_k| abar_{k-1} per neuron of hidden layer k
   size_t bslack;            // stated slack of the intermediate bounds (max of both directions)
+  size_t winf;              // [T, H] tensor-core inflation weight per neuron (see crown_tc.cu)
+  size_t ucon;              // [T, L-1] tensor-core inflation constant per layer (operand underflow)
   size_t anom, dlo, dhi;    // [T, n] nominal alpha~ and displacement box Delta = X - alpha~
   size_t bad;               // [T] int: non-finite inputs
   size_t total;             // floats
@@ -97,7 +100,7 @@ struct Ctx {
   // quad chain
   int nq = 0;
   QuadConsts qk{};
-  PbhPlan pbh_plan{256, 2, 6};
+  PbhPlan pbh_plan{256, 3, 4};
   std::vector<PbhPlan> pbh_candidates;
   int plan_index = -1;
   // mlp
@@ -124,11 +127,12 @@ leb_status mlp_prepare(Ctx& c);
 void mlp_release(Ctx& c);
 size_t simt_chain_smem(int maxw);
 leb_status run_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, float* r_lo, float* r_hi, float* A,
-                     float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt);
+                     float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags);
 // tensor-core back-substitution (reduced-precision operands, FP32 accumulation in TMEM)
 leb_status tc_prepare(Ctx& c);
 void tc_release(Ctx& c);
+float gamma_tc(int K);  // accumulation bound of K exact products in FP32 (unit roundoff 2^-23)
 leb_status tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, float* r_lo, float* r_hi, float* A,
-                    float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt);
+                    float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags);
 
 }  // namespace leb

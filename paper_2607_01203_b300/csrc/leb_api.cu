@@ -43,8 +43,8 @@ size_t pbh_ws_bytes(int T_max) { return kWsHeader + 2 * sizeof(long long) * (siz
 void default_pbh_candidates(Ctx& c) {
   c.pbh_candidates.clear();
   // (CTAs per SM, ring stages) pairs that fit the 228 KB of shared memory of an SM
-  const int cfg[][2] = {{1, 12}, {2, 6}, {2, 5}, {3, 4}};
-  for (int block : {256, 384, 512})
+  const int cfg[][2] = {{1, 12}, {2, 6}, {2, 5}, {3, 4}, {3, 3}, {4, 3}};
+  for (int block : {128, 192, 256})
     for (const auto& cs : cfg)
       if (block * cs[0] <= 2048) c.pbh_candidates.push_back(PbhPlan{block, cs[0], cs[1]});
 }

@@ -23,6 +23,7 @@
 #include "internal.h"
 #include "interval.cuh"
 #include "mlp_math.cuh"
+#include <cuda_bf16.h>
 
 namespace leb {
 
@@ -59,6 +60,8 @@ size_t mlp_workspace_floats(const Ctx& c, int T, MlpWs* w) {
   w->dlo = take(Tn);
   w->dhi = take(Tn);
   w->bslack = take(TH);
+  w->winf = take(TH);
+  w->ucon = take((size_t)T * (m.L > 1 ? m.L - 1 : 1));
   w->bad = take(T);
   w->total = o;
   return o;
@@ -176,6 +179,8 @@ struct NomArgs {
   float* hhat;
   float* hrad;
   float* v1;
+  float* v2;            // |W - W~| abar (reduced-precision handles only)
+  int op_fmt;           // -1: none, 0: FP16, 1: BF16 rounding of W for v2
   float* lo;
   float* hi;
   float gam;            // gamma for the blocked dot product (chunk + chunk count + bias)
@@ -197,11 +202,11 @@ __global__ void __launch_bounds__(256) mlp_nominal_kernel(NomArgs a) {
   // compensated dot products (TwoProduct via FMA + TwoSum, Ogita-Rump-Oishi "Dot2"): the value is
   // as accurate as if computed in twice the working precision, with the rigorous bound
   // |res - exact| <= u |res| + 2 gamma_K^2 sum |w| |x| (slack of 2 covers res vs exact in the first term)
-  float sum[4][4], cmp[4][4], err[4][4], vv[4][4], blo[4][4], bhi[4][4];
+  float sum[4][4], cmp[4][4], err[4][4], vv[4][4], vw[4][4], blo[4][4], bhi[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) sum[i][j] = cmp[i][j] = err[i][j] = vv[i][j] = blo[i][j] = bhi[i][j] = 0.f;
+    for (int j = 0; j < 4; ++j) sum[i][j] = cmp[i][j] = err[i][j] = vv[i][j] = vw[i][j] = blo[i][j] = bhi[i][j] = 0.f;
 
   for (int k0 = 0; k0 < a.K; k0 += kKC) {
     // load the input tile (transposed: s_x[k][t]) and the weight tile (s_w[k][c])
@@ -236,9 +241,14 @@ __global__ void __launch_bounds__(256) mlp_nominal_kernel(NomArgs a) {
     __syncthreads();
 #pragma unroll 2
     for (int kk = 0; kk < kKC; ++kk) {
-      float w[4], x[4], q[4], ab[4];
+      float w[4], x[4], q[4], ab[4], we[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) w[j] = s_w[kk][4 * tx + j];
+      for (int j = 0; j < 4; ++j) {
+        w[j] = s_w[kk][4 * tx + j];
+        if (a.op_fmt == 0) we[j] = fabsf(w[j] - __half2float(__float2half_rn(w[j])));
+        else if (a.op_fmt == 1) we[j] = fabsf(w[j] - __bfloat162float(__float2bfloat16_rn(w[j])));
+        else we[j] = 0.f;
+      }
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         x[i] = s_in[kk][4 * ty + i];
@@ -259,6 +269,7 @@ __global__ void __launch_bounds__(256) mlp_nominal_kernel(NomArgs a) {
           cmp[i][j] = __fadd_rn(cmp[i][j], __fadd_rn(pe, se));
           err[i][j] = __fmaf_ru(fabsf(w[j]), q[i], err[i][j]);
           vv[i][j] = __fmaf_ru(fabsf(w[j]), ab[i], vv[i][j]);
+          vw[i][j] = __fmaf_ru(we[j], ab[i], vw[i][j]);
         }
       if (a.first) {
 #pragma unroll
@@ -295,6 +306,7 @@ __global__ void __launch_bounds__(256) mlp_nominal_kernel(NomArgs a) {
       a.zhat[o] = zh;
       a.zrad[o] = e;
       a.v1[o] = vv[i][j];
+      if (a.v2) a.v2[o] = vw[i][j];
       if (a.first) {
         a.lo[o] = __fadd_rd(__fsub_rd(zh, e), blo[i][j]);
         a.hi[o] = __fadd_ru(__fadd_ru(zh, e), bhi[i][j]);
@@ -318,9 +330,23 @@ __global__ void __launch_bounds__(256) mlp_nominal_kernel(NomArgs a) {
 // ---------------------------------------------------------------------------------------------------
 // 3. relaxation of one hidden layer (elementwise over [T, width])
 // ---------------------------------------------------------------------------------------------------
+// Tensor-core inflation weights of one hidden layer (reduced-precision handles only): the stage that
+// multiplies by W_i sees operands a_j = Lambda_j s_j rounded to the operand format, W_i rounded the same
+// way and FP32 accumulation. Per neuron j its rounding error on Lambda' dh_{i-1} is at most
+//   |a_j| w_j  with  w_j = c1 v1'_j + (1 + 2^-23) v2_j,   c1 = u_op + 1.01 2^-24 + gamma_K (1 + u_op),
+// v1' = |W~| abar (from |W| abar with |W~| <= |W| (1 + 2 u_op)), v2 = |W - W~| abar, plus the per-layer
+// constant ucon = u_sub (1 + gamma_K) sum_j v1'_j for operands that round into the subnormal range.
+struct TcWeights {
+  float* winf;
+  float* ucon;
+  int ldu;
+  float c1, v1scale, usub, gam;
+};
+
 __global__ void mlp_relax_kernel(int T, int width, int ld, int off, int act, const float* lo, const float* hi,
                                  const float* zhat, const float* zrad, const float* bslack, float* sL, float* tL,
-                                 float* sU, float* tU, float* D, float* abar, float* loss) {
+                                 float* sU, float* tU, float* D, float* abar, float* loss, const float* v1,
+                                 const float* v2, TcWeights tw, int layer) {
   const long long total = (long long)T * width;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     const long long t = e / width;
@@ -335,8 +361,19 @@ __global__ void mlp_relax_kernel(int T, int width, int ld, int off, int act, con
     abar[o] = r.abar;
     // stated slack per unit coefficient: the nominal-enclosure part of the offsets, plus the change of
     // the lines when [l, u] moves by the nominal radius and by the bounds' own stated slack
+    // (first order: an endpoint moving by w shifts a line's offset by at most |sigma' - s| w there)
     const float widen = __fadd_ru(zrad[o], bslack ? bslack[o] : 0.f);
-    loss[o] = __fmaf_ru(4.f, widen, r.loss);
+    const float lo_ = lo[o], hi_ = hi[o];
+    const float sens = __fadd_ru(gprime_mag(act, r.sL, lo_, hi_), gprime_mag(act, r.sU, lo_, hi_));
+    // FP32 slopes differ from exact ones: a chord slope carries the tanhf error / width, i.e. a line
+    // offset error of about 2^-21 over the interval (tanh); a ReLU chord about 2^-22 (u - l)
+    const float slope_dev = act == kActTanh ? 9.5367432e-07f : __fmul_ru(2.3841858e-07f, __fsub_ru(hi_, lo_));
+    loss[o] = __fadd_ru(__fmaf_ru(2.f * sens, widen, r.loss), slope_dev);
+    if (tw.winf) {
+      const float v1s = __fmul_ru(v1[o], tw.v1scale);
+      tw.winf[o] = __fmaf_ru(tw.c1, v1s, __fmul_ru(1.0000001f, v2[o]));
+      atomicAdd(tw.ucon + t * tw.ldu + layer, __fmul_ru(tw.usub * (1.f + tw.gam), v1s));
+    }
   }
 }
 
@@ -618,9 +655,26 @@ leb_status mlp_bounds(Ctx& c, int T, const float* x_nom, const float* u_nom, con
   MlpWs L;
   mlp_workspace_floats(c, T, &L);
   float* ws = (float*)((char*)ws_base + 256);
+  const bool tc = m.prec != LEB_PREC_FP32;
+  auto tcw = [&](int layer) {
+    TcWeights w{};
+    if (!tc) return w;
+    const float uop = m.prec == LEB_PREC_FP16 ? 4.8828125e-04f : 3.90625e-03f;  // 2^-11 / 2^-8
+    const float g = gamma_tc(m.widths[layer + 1]);
+    w.winf = ws + L.winf;
+    w.ucon = ws + L.ucon;
+    w.ldu = m.L - 1;
+    w.c1 = std::nextafterf(uop + 1.01f * 5.9604645e-08f + g * (1.f + uop), INFINITY);
+    w.v1scale = std::nextafterf(1.f + 2.f * uop, INFINITY);
+    w.usub = m.prec == LEB_PREC_FP16 ? 2.9802322e-08f : 4.6e-41f;  // half the smallest subnormal spacing
+    w.gam = g;
+    return w;
+  };
   const int n = m.widths[0], n_x = c.n_x, n_u = c.n_u;
   int* bad = (int*)(ws + L.bad);
   if (cudaMemsetAsync(ws + L.bslack, 0, (size_t)T * L.H * sizeof(float), s) != cudaSuccess) return LEB_ERR_CUDA;
+  if (tc && cudaMemsetAsync(ws + L.ucon, 0, (size_t)T * (m.L - 1) * sizeof(float), s) != cudaSuccess)
+    return LEB_ERR_CUDA;
   mlp_prep_kernel<<<T, 256, 0, s>>>(T, n_x, n_u, x_nom, u_nom, *set, ws + L.anom, ws + L.dlo, ws + L.dhi, bad, flags);
   if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
 
@@ -645,6 +699,8 @@ leb_status mlp_bounds(Ctx& c, int T, const float* x_nom, const float* u_nom, con
     na.hhat = ws + L.hhat + L.hoff[i];
     na.hrad = ws + L.hrad + L.hoff[i];
     na.v1 = ws + L.v1 + L.hoff[i];
+    na.v2 = m.prec == LEB_PREC_FP32 ? nullptr : ws + L.v2 + L.hoff[i];
+    na.op_fmt = m.prec == LEB_PREC_FP16 ? 0 : (m.prec == LEB_PREC_BF16 ? 1 : -1);
     na.lo = ws + L.lo + L.hoff[i];
     na.hi = ws + L.hi + L.hoff[i];
     {
@@ -664,29 +720,29 @@ leb_status mlp_bounds(Ctx& c, int T, const float* x_nom, const float* u_nom, con
       const int blocks = (int)std::min<long long>(((long long)T * na.N + 255) / 256, 148LL * 32);
       mlp_relax_kernel<<<blocks, 256, 0, s>>>(T, na.N, L.H, L.hoff[0], m.act, ws + L.lo, ws + L.hi, ws + L.zhat,
                                               ws + L.zrad, nullptr, ws + L.sL, ws + L.tL, ws + L.sU, ws + L.tU,
-                                              ws + L.D, ws + L.abar, ws + L.loss);
+                                              ws + L.D, ws + L.abar, ws + L.loss, ws + L.v1, ws + L.v2, tcw(0), 0);
       if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
       continue;
     }
     mlp_nominal_kernel<<<grid, 256, 0, s>>>(na);
     if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
     // bounds of hidden layer i by back-substitution, then its relaxation
-    leb_status st = run_chain(c, T, i, L, ws, nullptr, nullptr, nullptr, nullptr, nullptr, s, bad, opt);
+    leb_status st = run_chain(c, T, i, L, ws, nullptr, nullptr, nullptr, nullptr, nullptr, s, bad, opt, flags);
     if (st != LEB_OK) return st;
     const int blocks = (int)std::min<long long>(((long long)T * na.N + 255) / 256, 148LL * 32);
     mlp_relax_kernel<<<blocks, 256, 0, s>>>(T, na.N, L.H, L.hoff[i], m.act, ws + L.lo, ws + L.hi, ws + L.zhat,
                                             ws + L.zrad, ws + L.bslack, ws + L.sL, ws + L.tL, ws + L.sU, ws + L.tU,
-                                            ws + L.D, ws + L.abar, ws + L.loss);
+                                            ws + L.D, ws + L.abar, ws + L.loss, ws + L.v1, ws + L.v2, tcw(i), i);
     if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
   }
   // output rows: lower, upper and Jacobian chains -> r_lo, r_hi, A, B
-  return run_chain(c, T, m.L - 1, L, ws, r_lo, r_hi, A, B, opt ? opt->eps : nullptr, s, bad, opt);
+  return run_chain(c, T, m.L - 1, L, ws, r_lo, r_hi, A, B, opt ? opt->eps : nullptr, s, bad, opt, flags);
 }
 
 leb_status run_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, float* r_lo, float* r_hi, float* A,
-                     float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt) {
+                     float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags) {
   const MlpModel& m = c.mlp;
-  if (m.prec != LEB_PREC_FP32) return tc_chain(c, T, target, L, ws, r_lo, r_hi, A, B, eps, s, bad, opt);
+  if (m.prec != LEB_PREC_FP32) return tc_chain(c, T, target, L, ws, r_lo, r_hi, A, B, eps, s, bad, opt, flags);
   ChainArgs a{};
   a.m = view(m);
   a.T = T;

@@ -2,10 +2,6 @@
 // paths land).
 #include "internal.h"
 namespace leb {
-leb_status tc_prepare(Ctx&) { return LEB_ERR_UNSUPPORTED; }
-void tc_release(Ctx&) {}
-leb_status tc_chain(const Ctx&, int, int, const MlpWs&, float*, float*, float*, float*, float*, float*, cudaStream_t,
-                    const int*, const leb_options*) { return LEB_ERR_UNSUPPORTED; }
 leb_status mlp_bounds_backward(Ctx&, int, const float*, const float*, const leb_set*, const float*, const float*,
                                float*, float*, float*, void*, int*, cudaStream_t) { return LEB_ERR_UNSUPPORTED; }
 }  // namespace leb

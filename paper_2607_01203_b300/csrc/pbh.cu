@@ -90,166 +90,173 @@ __device__ __forceinline__ QuadA quad_avals(const float* xn, const float* un, in
   return q;
 }
 
-// A_k entry (row l, column j); q holds the curved entries of row l's quadrotor.
-__device__ __forceinline__ float a_entry(int l, int j, int nq, const QuadA& q, const QuadConsts& k) {
+// Nonzeros of row l of A_k (at most 6) and of B_k (at most 2) in fixed slots (column -1 = unused):
+// warp-uniform lists, so a warp writes a row with 16-byte stores of zeros into which it drops the few
+// nonzeros (no divergence, no dynamically indexed local arrays).
+struct RowNz {
+  int c0, c1, c2, c3, c4, c5;
+  float v0, v1, v2, v3, v4, v5;
+};
+
+__device__ __forceinline__ RowNz a_row(int l, int nq, const QuadA& q, const QuadConsts& K) {
   const int i = l / 6, s = l - 6 * i;
-  const int qj = j / 6, sj = j - 6 * qj;
-  if (qj == i) {
-    if (sj == s) return 1.f;
-    if (s < 3 && sj == s + 3) return k.dt_f;
-    const int deg = k.springs ? (i > 0) + (i + 1 < nq) : 0;
-    if (s == 3) { if (sj == 2) return q.aphi_x; if (sj == 0 && deg) return -(float)deg * k.ks_f; }
-    if (s == 4) { if (sj == 2) return q.aphi_y; if (sj == 1 && deg) return -(float)deg * k.ks_f; }
-    return 0.f;
-  }
-  if (k.springs && (qj == i - 1 || qj == i + 1)) {
-    if (s == 3 && sj == 0) return k.ks_f;
-    if (s == 4 && sj == 1) return k.ks_f;
-  }
-  return 0.f;
+  const bool curved = (s == 3 || s == 4);
+  const int deg = (K.springs && curved) ? (i > 0) + (i + 1 < nq) : 0;
+  const int sc = s - 3;
+  RowNz r;
+  r.c0 = l;
+  r.v0 = 1.f;
+  r.c1 = s < 3 ? l + 3 : -1;
+  r.v1 = K.dt_f;
+  r.c2 = curved ? 6 * i + 2 : -1;
+  r.v2 = s == 3 ? q.aphi_x : q.aphi_y;
+  r.c3 = deg ? 6 * i + sc : -1;
+  r.v3 = -(float)deg * K.ks_f;
+  r.c4 = (deg && i > 0) ? 6 * (i - 1) + sc : -1;
+  r.v4 = K.ks_f;
+  r.c5 = (deg && i + 1 < nq) ? 6 * (i + 1) + sc : -1;
+  r.v5 = K.ks_f;
+  return r;
 }
 
-__device__ __forceinline__ float b_entry(int l, int c, const QuadA& q, const QuadConsts& k) {
+__device__ __forceinline__ RowNz b_row(int l, const QuadA& q, const QuadConsts& K) {
   const int i = l / 6, s = l - 6 * i;
-  if ((c >> 1) != i) return 0.f;
-  if (s == 3) return q.au_x;
-  if (s == 4) return q.au_y;
-  if (s == 5) return (c & 1) ? k.tq_f : -k.tq_f;
-  return 0.f;
+  RowNz r;
+  const bool any = s >= 3;
+  r.c0 = any ? 2 * i : -1;
+  r.c1 = any ? 2 * i + 1 : -1;
+  r.v0 = s == 3 ? q.au_x : (s == 4 ? q.au_y : -K.tq_f);
+  r.v1 = s == 3 ? q.au_x : (s == 4 ? q.au_y : K.tq_f);
+  r.c2 = r.c3 = r.c4 = r.c5 = -1;
+  r.v2 = r.v3 = r.v4 = r.v5 = 0.f;
+  return r;
 }
 
-// A_k and B_k rows, warp per row (banded, 16-byte streaming stores when the row length allows).
+__device__ __forceinline__ void drop(float4& v, int base, int col, float val) {
+  const int d = col - base;
+  if (d == 0) v.x = val;
+  if (d == 1) v.y = val;
+  if (d == 2) v.z = val;
+  if (d == 3) v.w = val;
+}
+
+__device__ __forceinline__ void store_row(float* row, int len, const RowNz& nz, int lane) {
+  if (((len & 3) == 0) && ((reinterpret_cast<uintptr_t>(row) & 15) == 0)) {
+    float4* r4 = reinterpret_cast<float4*>(row);
+    for (int c = lane; c < (len >> 2); c += 32) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      const int b = 4 * c;
+      drop(v, b, nz.c0, nz.v0);
+      drop(v, b, nz.c1, nz.v1);
+      drop(v, b, nz.c2, nz.v2);
+      drop(v, b, nz.c3, nz.v3);
+      drop(v, b, nz.c4, nz.v4);
+      drop(v, b, nz.c5, nz.v5);
+      __stcs(r4 + c, v);
+    }
+  } else {
+    for (int c = lane; c < len; c += 32) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      drop(v, c, nz.c0, nz.v0);
+      drop(v, c, nz.c1, nz.v1);
+      drop(v, c, nz.c2, nz.v2);
+      drop(v, c, nz.c3, nz.v3);
+      drop(v, c, nz.c4, nz.v4);
+      drop(v, c, nz.c5, nz.v5);
+      row[c] = v.x;
+    }
+  }
+}
+
+// A_k and B_k rows, warp per row.
 __device__ __forceinline__ void write_AB(const PbhArgs& a, const Item& it, const QuadA* qa, int wid, int nw,
                                          int lane) {
   const QuadConsts& K = a.k;
   const int nq = it.nq, nx = 6 * nq, nu = 2 * nq;
-  if (a.A) {
-    float* At = a.A + it.a_off;
-    const bool v4 = ((nx & 3) == 0) && ((reinterpret_cast<uintptr_t>(At) & 15) == 0);
-    for (int l = wid; l < nx; l += nw) {
-      const int i = l / 6;
-      const QuadA q = qa[i];
-      if (v4) {
-        const int band_lo = 6 * (i - 1), band_hi = 6 * (i + 2);
-        float4* rowp = reinterpret_cast<float4*>(At + (long long)l * nx);
-        for (int c = lane; c < (nx >> 2); c += 32) {
-          const int j0 = 4 * c;
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (j0 + 4 > band_lo && j0 < band_hi) {
-            v.x = a_entry(l, j0, nq, q, K);
-            v.y = a_entry(l, j0 + 1, nq, q, K);
-            v.z = a_entry(l, j0 + 2, nq, q, K);
-            v.w = a_entry(l, j0 + 3, nq, q, K);
-          }
-          __stcs(rowp + c, v);
-        }
-      } else {
-        for (int j = lane; j < nx; j += 32) At[(long long)l * nx + j] = a_entry(l, j, nq, q, K);
-      }
-    }
-  }
-  if (a.B) {
-    float* Bt = a.B + it.b_off;
-    const bool v4 = ((nu & 3) == 0) && ((reinterpret_cast<uintptr_t>(Bt) & 15) == 0);
-    for (int l = wid; l < nx; l += nw) {
-      const int i = l / 6;
-      const QuadA q = qa[i];
-      if (v4) {
-        float4* rowp = reinterpret_cast<float4*>(Bt + (long long)l * nu);
-        for (int c = lane; c < (nu >> 2); c += 32) {
-          const int j0 = 4 * c;
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (j0 + 4 > 2 * i && j0 < 2 * i + 2) {
-            v.x = b_entry(l, j0, q, K);
-            v.y = b_entry(l, j0 + 1, q, K);
-            v.z = b_entry(l, j0 + 2, q, K);
-            v.w = b_entry(l, j0 + 3, q, K);
-          }
-          __stcs(rowp + c, v);
-        }
-      } else {
-        for (int c = lane; c < nu; c += 32) Bt[(long long)l * nu + c] = b_entry(l, c, q, K);
-      }
-    }
+  for (int l = wid; l < nx; l += nw) {
+    const QuadA q = qa[l / 6];
+    if (a.A) store_row(a.A + it.a_off + (long long)l * nx, nx, a_row(l, nq, q, K), lane);
+    if (a.B) store_row(a.B + it.b_off + (long long)l * nu, nu, b_row(l, q, K), lane);
   }
 }
 
-// Eq. 15 for every output row of one timestep (thread per row), plus (J - A) Delta.
+__device__ __forceinline__ void emit_row(const PbhArgs& a, const Item& it, int l, ivl R, bool bad) {
+  if (bad || !finite_ivl(R)) R = iv(-CUDART_INF_F, CUDART_INF_F);
+  const long long o = it.x_off + l;
+  a.r_lo[o] = R.lo;
+  a.r_hi[o] = R.hi;
+  if (a.gamma_c) {
+    const float c = 0.5f * R.lo + 0.5f * R.hi;
+    a.gamma_c[o] = c;
+    a.gamma_r[o] = __fadd_ru(fmaxf(__fsub_ru(R.hi, c), __fsub_ru(c, R.lo)), a.gamma_pad);
+  }
+  if (a.eps) a.eps[o] = 0.f;
+}
+
+// Eq. 15 for every output row of one timestep, plus (J - A) Delta. Items 0..nq-1: the two curved rows
+// (v_x, v_y) of quadrotor i, which share their trigonometric enclosures; items nq..5nq-1: the four
+// linear rows of each quadrotor (only the Jacobian-rounding term).
 __device__ __forceinline__ void pbh_rows(const PbhArgs& a, const Item& it, const float* xn, const float* un,
                                          const float* s_lo, const float* s_hi, const QuadA* qa, bool bad, int tid,
                                          int nthr) {
   const QuadConsts& K = a.k;
   const int nq = it.nq, nx = 6 * nq;
   const ivl cI = iv(K.c_lo, K.c_hi);
-  for (int l = tid; l < nx; l += nthr) {
-    const int i = l / 6, s = l - 6 * i;
-    auto D = [&](int j) {  // Delta_j = X_j - alpha~_j
-      const float nom = j < nx ? xn[j] : un[j - nx];
-      return iv(__fsub_rd(s_lo[j], nom), __fsub_ru(s_hi[j], nom));
-    };
-    auto corr = [&](ivl Jiv, float Aval, ivl Dj) { return iv_mul(iv_sub(Jiv, iv(Aval)), Dj); };
-    ivl R = iv(0.f);
-    const int deg = K.springs ? (i > 0) + (i + 1 < nq) : 0;
-    if (s < 3) {
-      R = corr(iv(K.dt_lo, K.dt_hi), K.dt_f, D(l + 3));
-    } else if (s == 3 || s == 4) {
+  auto D = [&](int j) {  // Delta_j = X_j - alpha~_j
+    const float nom = j < nx ? xn[j] : un[j - nx];
+    return iv(__fsub_rd(s_lo[j], nom), __fsub_ru(s_hi[j], nom));
+  };
+  auto corr = [&](ivl Jiv, float Aval, ivl Dj) { return iv_mul(iv_sub(Jiv, iv(Aval)), Dj); };
+  for (int item = tid; item < 5 * nq; item += nthr) {
+    if (item < nq) {
+      const int i = item;
       const int jp = 6 * i + 2, j1 = nx + 2 * i, j2 = j1 + 1;
       const float phi0 = xn[jp];
       const float u1 = un[2 * i], u2 = un[2 * i + 1];
       const ivl S = iv(__fadd_rd(u1, u2), __fadd_ru(u1, u2));  // S~ (inputs fixed on X^(phi))
       const ivl Phi = iv(s_lo[jp], s_hi[jp]);
       const ivl Dp = D(jp), D1 = D(j1), D2 = D(j2);
-      const ivl Dp2 = iv_sqr(Dp);
+      const ivl Dp2 = iv_sqr(Dp), Dp1 = iv_mul(Dp, D1), Dpu2 = iv_mul(Dp, D2);
+      const ivl sinP = iv_sin(Phi), cosP = iv_cos(Phi);
+      const ivl sin0 = point_sin(phi0), cos0 = point_cos(phi0);
+      const ivl cS = iv_mul(cI, S);
       const QuadA q = qa[i];
-      float Aphi, Au;
-      ivl Jphi, Ju;
-      if (s == 3) {
-        // 1/2 [H_pp](X^(phi)) Dphi^2 + [H_1p](X^(phi)) Dphi Du1 + [H_2p](X^(phi)) Dphi Du2
-        const ivl Hpp = iv_mul(iv_mul(cI, S), iv_sin(Phi));
-        const ivl Hup = iv_neg(iv_mul(cI, iv_cos(Phi)));
-        R = iv_half(iv_mul(Hpp, Dp2));
-        R = iv_add(R, iv_mul(Hup, iv_mul(Dp, D1)));
-        R = iv_add(R, iv_mul(Hup, iv_mul(Dp, D2)));
-        Aphi = q.aphi_x;
-        Au = q.au_x;
-        Jphi = iv_neg(iv_mul(iv_mul(cI, S), point_cos(phi0)));
-        Ju = iv_neg(iv_mul(cI, point_sin(phi0)));
-      } else {
-        const ivl Hpp = iv_neg(iv_mul(iv_mul(cI, S), iv_cos(Phi)));
-        const ivl Hup = iv_neg(iv_mul(cI, iv_sin(Phi)));
-        R = iv_half(iv_mul(Hpp, Dp2));
-        R = iv_add(R, iv_mul(Hup, iv_mul(Dp, D1)));
-        R = iv_add(R, iv_mul(Hup, iv_mul(Dp, D2)));
-        Aphi = q.aphi_y;
-        Au = q.au_y;
-        Jphi = iv_neg(iv_mul(iv_mul(cI, S), point_sin(phi0)));
-        Ju = iv_mul(cI, point_cos(phi0));
+      const int deg = K.springs ? (i > 0) + (i + 1 < nq) : 0;
+      for (int row = 0; row < 2; ++row) {
+        // v_x: 1/2 [(dt/m) S sin](X^(phi)) Dphi^2 - [(dt/m) cos](X^(phi)) Dphi (Du1 + Du2 termwise)
+        // v_y: -1/2 [(dt/m) S cos](X^(phi)) Dphi^2 - [(dt/m) sin](X^(phi)) Dphi (Du1, Du2 termwise)
+        const ivl Hpp = row == 0 ? iv_mul(cS, sinP) : iv_neg(iv_mul(cS, cosP));
+        const ivl Hup = iv_neg(iv_mul(cI, row == 0 ? cosP : sinP));
+        ivl R = iv_half(iv_mul(Hpp, Dp2));
+        R = iv_add(R, iv_mul(Hup, Dp1));
+        R = iv_add(R, iv_mul(Hup, Dpu2));
+        const ivl Jphi = iv_neg(iv_mul(cS, row == 0 ? cos0 : sin0));
+        const ivl Ju = row == 0 ? iv_neg(iv_mul(cI, sin0)) : iv_mul(cI, cos0);
+        R = iv_add(R, corr(Jphi, row == 0 ? q.aphi_x : q.aphi_y, Dp));
+        R = iv_add(R, corr(Ju, row == 0 ? q.au_x : q.au_y, D1));
+        R = iv_add(R, corr(Ju, row == 0 ? q.au_x : q.au_y, D2));
+        if (deg) {
+          const ivl ks = iv(K.ks_lo, K.ks_hi);
+          const ivl self = iv_mul(iv(-(float)deg), ks);
+          R = iv_add(R, corr(self, -(float)deg * K.ks_f, D(6 * i + row)));
+          if (i > 0) R = iv_add(R, corr(ks, K.ks_f, D(6 * (i - 1) + row)));
+          if (i + 1 < nq) R = iv_add(R, corr(ks, K.ks_f, D(6 * (i + 1) + row)));
+        }
+        emit_row(a, it, 6 * i + 3 + row, R, bad);
       }
-      R = iv_add(R, corr(Jphi, Aphi, Dp));
-      R = iv_add(R, corr(Ju, Au, D1));
-      R = iv_add(R, corr(Ju, Au, D2));
-      if (deg) {
-        const int sc = s - 3;  // 0: p_x column, 1: p_y column
-        const ivl ks = iv(K.ks_lo, K.ks_hi);
-        const ivl self = iv_mul(iv(-(float)deg), ks);
-        R = iv_add(R, corr(self, -(float)deg * K.ks_f, D(6 * i + sc)));
-        if (i > 0) R = iv_add(R, corr(ks, K.ks_f, D(6 * (i - 1) + sc)));
-        if (i + 1 < nq) R = iv_add(R, corr(ks, K.ks_f, D(6 * (i + 1) + sc)));
+    } else {
+      const int e = item - nq, i = e >> 2, k = e & 3;
+      const int s = k < 3 ? k : 5;
+      const int l = 6 * i + s;
+      ivl R;
+      if (s < 3) {
+        R = corr(iv(K.dt_lo, K.dt_hi), K.dt_f, D(l + 3));
+      } else {  // omega row: dt arm / I (u2 - u1)
+        const ivl tq = iv(K.tq_lo, K.tq_hi);
+        R = iv_add(corr(iv_neg(tq), -K.tq_f, D(nx + 2 * i)), corr(tq, K.tq_f, D(nx + 2 * i + 1)));
       }
-    } else {  // omega row: dt arm / I (u2 - u1)
-      const ivl tq = iv(K.tq_lo, K.tq_hi);
-      R = iv_add(corr(iv_neg(tq), -K.tq_f, D(nx + 2 * i)), corr(tq, K.tq_f, D(nx + 2 * i + 1)));
+      emit_row(a, it, l, R, bad);
     }
-    if (bad || !finite_ivl(R)) R = iv(-CUDART_INF_F, CUDART_INF_F);
-    const long long o = it.x_off + l;
-    a.r_lo[o] = R.lo;
-    a.r_hi[o] = R.hi;
-    if (a.gamma_c) {
-      const float c = 0.5f * R.lo + 0.5f * R.hi;
-      a.gamma_c[o] = c;
-      a.gamma_r[o] = __fadd_ru(fmaxf(__fsub_ru(R.hi, c), __fsub_ru(c, R.lo)), a.gamma_pad);
-    }
-    if (a.eps) a.eps[o] = 0.f;
   }
 }
 
@@ -342,10 +349,10 @@ __global__ void __launch_bounds__(256, 4) pbh_chain_kernel(PbhArgs a) {
 // memory, then evaluate Eq. 15 and store A_k, B_k while the copies of the next timestep are in flight.
 // ---------------------------------------------------------------------------------------------------
 struct StageMeta {
-  int t, chunk, last, rows;
+  int t, chunk, last, rows, rows_per, pad0, pad1, pad2;
 };
 
-__global__ void __launch_bounds__(256, 2) pbh_zono_tma_kernel(PbhArgs a, int S, int stage_bytes_cap) {
+__global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, int stage_bytes_cap) {
   extern __shared__ __align__(128) unsigned char sraw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int ncons = nwarps - 1, ncthr = ncons * 32;
@@ -389,12 +396,12 @@ __global__ void __launch_bounds__(256, 2) pbh_zono_tma_kernel(PbhArgs a, int S, 
           const uint32_t ph = (k / (uint32_t)S) & 1u;
           if (k >= (uint32_t)S && !mbar_wait(&empty[s], ph ^ 1u)) { ok = false; break; }
           if (done) {
-            meta[s] = StageMeta{-1, 0, 1, 0};
+            meta[s] = StageMeta{-1, 0, 1, 0, 1, 0, 0, 0};
             mbar_arrive(&full[s]);
           } else {
             const int rows = min(rows_per, n - c * rows_per);
             const uint32_t bytes = (uint32_t)rows * (uint32_t)it.n_gen * 4u;
-            meta[s] = StageMeta{t, c, c == nch - 1, rows};
+            meta[s] = StageMeta{t, c, c == nch - 1, rows, rows_per, 0, 0, 0};
             mbar_arrive_expect_tx(&full[s], bytes);
             bulk_g2s(stages + (size_t)s * stage_bytes_cap, a.G + it.g_off + (long long)c * rows_per * it.n_gen, bytes,
                      &full[s]);
@@ -414,6 +421,7 @@ __global__ void __launch_bounds__(256, 2) pbh_zono_tma_kernel(PbhArgs a, int S, 
     const int cw = warp - 1, ctid = threadIdx.x - 32;
     uint32_t k = 0;
     int slot = 0;
+    Item it{};
     bool ok = true;  // this thread saw only finite rows
     for (;;) {
       const int s = (int)(k % (uint32_t)S);
@@ -424,7 +432,7 @@ __global__ void __launch_bounds__(256, 2) pbh_zono_tma_kernel(PbhArgs a, int S, 
       }
       const StageMeta m = meta[s];
       if (m.t < 0) break;
-      const Item it = make_item(a, m.t);
+      if (m.chunk == 0) it = make_item(a, m.t);  // the item changes only at a timestep's first chunk
       const float* xn = a.x_nom + it.x_off;
       const float* un = a.u_nom + it.u_off;
       float* lo = s_lo + slot * n_max;
@@ -432,7 +440,7 @@ __global__ void __launch_bounds__(256, 2) pbh_zono_tma_kernel(PbhArgs a, int S, 
       QuadA* qa = s_qa + slot * a.nq;
       if (m.chunk == 0) compute_qa(xn, un, it.nq, a.k, qa, ctid, ncthr);
       const int p = it.n_gen;
-      const int rows_per = max(1, stage_bytes_cap / (p * 4));
+      const int rows_per = m.rows_per;
       const float* stage = reinterpret_cast<const float*>(stages + (size_t)s * stage_bytes_cap);
       for (int rl = cw; rl < m.rows; rl += ncons) {
         const float half = row_l1_ru(stage + (size_t)rl * p, p, lane, true);
