@@ -87,6 +87,9 @@ struct MlpWs {
   size_t bslack;            // stated slack of the intermediate bounds (max of both directions)
   size_t winf;              // [T, H] tensor-core inflation weight per neuron (see crown_tc.cu)
   size_t ucon;              // [T, L-1] tensor-core inflation constant per layer (operand underflow)
+  size_t gsL, gsU, gtL, gtU, gD, gz, gl, gu;  // [T, H] adjoint accumulators
+  size_t grho;              // [T, n] adjoint of the radii
+  size_t gscr;              // [T, max width] adjoint scratch
   size_t anom, dlo, dhi;    // [T, n] nominal alpha~ and displacement box Delta = X - alpha~
   size_t bad;               // [T] int: non-finite inputs
   size_t total;             // floats
@@ -127,7 +130,11 @@ leb_status mlp_prepare(Ctx& c);
 void mlp_release(Ctx& c);
 size_t simt_chain_smem(int maxw);
 leb_status run_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, float* r_lo, float* r_hi, float* A,
-                     float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags);
+                     float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags,
+                     bool simt);
+// prep, enclosed nominal pass, bounds and relaxation of every hidden layer (chains on CUDA cores if simt)
+leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set, void* ws,
+                              int* flags, cudaStream_t s, bool simt, const leb_options* opt);
 // tensor-core back-substitution (reduced-precision operands, FP32 accumulation in TMEM)
 leb_status tc_prepare(Ctx& c);
 void tc_release(Ctx& c);

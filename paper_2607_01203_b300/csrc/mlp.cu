@@ -56,6 +56,18 @@ size_t mlp_workspace_floats(const Ctx& c, int T, MlpWs* w) {
   w->loss = take(TH);
   w->v1 = take(TH);
   w->v2 = take(TH);
+  int maxw = 0;
+  for (int i = 0; i <= m.L; ++i) maxw = maxw > m.widths[i] ? maxw : m.widths[i];
+  w->gsL = take(TH);
+  w->gsU = take(TH);
+  w->gtL = take(TH);
+  w->gtU = take(TH);
+  w->gD = take(TH);
+  w->gz = take(TH);
+  w->gl = take(TH);
+  w->gu = take(TH);
+  w->grho = take(Tn);
+  w->gscr = take((size_t)T * maxw);
   w->anom = take(Tn);
   w->dlo = take(Tn);
   w->dhi = take(Tn);
@@ -648,14 +660,13 @@ leb_status launch_simt_chain(const Ctx& c, const ChainArgs& a, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
 }
 
-leb_status mlp_bounds(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set, float* r_lo,
-                      float* r_hi, float* A, float* B, const leb_options* opt, void* ws_base, int* flags,
-                      cudaStream_t s) {
+leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set,
+                              void* ws_base, int* flags, cudaStream_t s, bool simt, const leb_options* opt) {
   const MlpModel& m = c.mlp;
   MlpWs L;
   mlp_workspace_floats(c, T, &L);
   float* ws = (float*)((char*)ws_base + 256);
-  const bool tc = m.prec != LEB_PREC_FP32;
+  const bool tc = !simt && m.prec != LEB_PREC_FP32;
   auto tcw = [&](int layer) {
     TcWeights w{};
     if (!tc) return w;
@@ -727,7 +738,7 @@ leb_status mlp_bounds(Ctx& c, int T, const float* x_nom, const float* u_nom, con
     mlp_nominal_kernel<<<grid, 256, 0, s>>>(na);
     if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
     // bounds of hidden layer i by back-substitution, then its relaxation
-    leb_status st = run_chain(c, T, i, L, ws, nullptr, nullptr, nullptr, nullptr, nullptr, s, bad, opt, flags);
+    leb_status st = run_chain(c, T, i, L, ws, nullptr, nullptr, nullptr, nullptr, nullptr, s, bad, opt, flags, simt);
     if (st != LEB_OK) return st;
     const int blocks = (int)std::min<long long>(((long long)T * na.N + 255) / 256, 148LL * 32);
     mlp_relax_kernel<<<blocks, 256, 0, s>>>(T, na.N, L.H, L.hoff[i], m.act, ws + L.lo, ws + L.hi, ws + L.zhat,
@@ -735,14 +746,28 @@ leb_status mlp_bounds(Ctx& c, int T, const float* x_nom, const float* u_nom, con
                                             ws + L.D, ws + L.abar, ws + L.loss, ws + L.v1, ws + L.v2, tcw(i), i);
     if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
   }
+  return LEB_OK;
+}
+
+leb_status mlp_bounds(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set, float* r_lo,
+                      float* r_hi, float* A, float* B, const leb_options* opt, void* ws_base, int* flags,
+                      cudaStream_t s) {
+  const bool simt = c.mlp.prec == LEB_PREC_FP32;
+  leb_status st = mlp_forward_hidden(c, T, x_nom, u_nom, set, ws_base, flags, s, simt, opt);
+  if (st != LEB_OK) return st;
+  MlpWs L;
+  mlp_workspace_floats(c, T, &L);
+  float* ws = (float*)((char*)ws_base + 256);
   // output rows: lower, upper and Jacobian chains -> r_lo, r_hi, A, B
-  return run_chain(c, T, m.L - 1, L, ws, r_lo, r_hi, A, B, opt ? opt->eps : nullptr, s, bad, opt, flags);
+  return run_chain(c, T, c.mlp.L - 1, L, ws, r_lo, r_hi, A, B, opt ? opt->eps : nullptr, s, (int*)(ws + L.bad), opt,
+                   flags, simt);
 }
 
 leb_status run_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, float* r_lo, float* r_hi, float* A,
-                     float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags) {
+                     float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags,
+                     bool simt) {
   const MlpModel& m = c.mlp;
-  if (m.prec != LEB_PREC_FP32) return tc_chain(c, T, target, L, ws, r_lo, r_hi, A, B, eps, s, bad, opt, flags);
+  if (!simt) return tc_chain(c, T, target, L, ws, r_lo, r_hi, A, B, eps, s, bad, opt, flags);
   ChainArgs a{};
   a.m = view(m);
   a.T = T;

@@ -2,8 +2,6 @@
 // paths land).
 #include "internal.h"
 namespace leb {
-leb_status mlp_bounds_backward(Ctx&, int, const float*, const float*, const leb_set*, const float*, const float*,
-                               float*, float*, float*, void*, int*, cudaStream_t) { return LEB_ERR_UNSUPPORTED; }
 }  // namespace leb
 extern "C" {
 leb_status leb_proposer_create(int, int, int, unsigned long long, leb_proposer* out) { if (out) *out = nullptr; return LEB_ERR_UNSUPPORTED; }
