@@ -204,6 +204,24 @@ leb_status leb_proposer_set_layer(leb_proposer p, int i, const float* W, const f
 /* Raw gradients of the last train step (for checks): dW [out, in], db [out]. */
 leb_status leb_proposer_get_grad(leb_proposer p, int i, float* dW, float* db, void* stream);
 
+/* ---- allocation-free bounds (quad chains) --------------------------------------------------------- */
+/* The same bounds as leb_bounds for LEB_DYN_QUAD_CHAIN handles, without a workspace argument: for callers
+ * that cannot allocate device memory when they need bounds (a control loop whose memory is fixed after
+ * start-up, or an integration that only hands over inputs and outputs). This is an addition of this
+ * library; the paper has no counterpart.
+ * The scratch (the work-list counter and, for uneven batches, two 8-byte prefix sums per trajectory) is a
+ * 64 KiB array inside the library that every GPU loading the library keeps until the process exits.
+ * Uneven-dimension batches may have at most leb_bounds_static_max_traj() trajectories; more return
+ * LEB_ERR_WORKSPACE. MLP handles return LEB_ERR_UNSUPPORTED. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress): make that first call before any stream capture. All
+ * calls share the array and clear its counter themselves; calls that overlap on the GPU (issued on
+ * different streams or from different host threads without ordering) race on it. Nothing is allocated
+ * or freed. Other arguments and outputs as leb_bounds (no leb_options). */
+leb_status leb_bounds_static(leb_handle h, const leb_batch* batch, int T, const float* x_nom, const float* u_nom,
+                             const leb_set* set, float* r_lo, float* r_hi, float* A, float* B, int* dev_flags,
+                             void* stream);
+int leb_bounds_static_max_traj(void);
+
 /* ---- diagnostics -------------------------------------------------------------------------------- */
 /* Evaluates the library's point enclosures of sin, cos and tanh (the CUDA function value widened by
  * the slack that covers its documented error) at n device inputs x, writing [lo, hi] pairs to the

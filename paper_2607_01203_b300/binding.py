@@ -57,7 +57,7 @@ EXPORTS = [
     "leb_graph_capture", "leb_graph_launch", "leb_graph_destroy", "leb_proposer_create", "leb_proposer_destroy",
     "leb_proposer_set_norm", "leb_proposer_forward", "leb_proposer_train_step", "leb_proposer_workspace_size",
     "leb_proposer_get_layer", "leb_proposer_set_layer", "leb_proposer_get_grad", "leb_selftest_point_enclosures",
-    "leb_status_string", "leb_version",
+    "leb_bounds_static", "leb_bounds_static_max_traj", "leb_status_string", "leb_version",
 ]
 
 
@@ -102,6 +102,9 @@ def lib():
         L.leb_proposer_set_layer.argtypes = [vp, i32, vp, vp, vp]
         L.leb_proposer_get_grad.argtypes = [vp, i32, vp, vp, vp]
         L.leb_selftest_point_enclosures.argtypes = [vp, i32, vp, vp, vp, vp]
+        L.leb_bounds_static.argtypes = [vp, C.POINTER(BatchDesc), i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp, vp, vp,
+                                        vp]
+        L.leb_bounds_static_max_traj.argtypes = []
         _lib = L
     return _lib
 
