@@ -5,6 +5,9 @@ The proposer maps (x~_k, u~_k, state radii) to standardised (r_lo, r_hi). It is 
 the paper's method, whose bounds it only proposes; the certified bound stays the answer.)
 
 Layout: weights W_i are [out, in], inputs X are [B, in], outputs [B, out].
+The proposer's specification fixes its arithmetic to BF16 GEMM operands with FP32 (here FP64)
+accumulation; with ``bf16=True`` every matrix-product operand is rounded to BF16 (round to nearest, ties
+to even) before the product, as the definition of that precision.
 Loss = mean over all B*out entries of (Y - T)^2.
 Adam (Kingma & Ba 2015): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
 p -= lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).
@@ -14,12 +17,24 @@ from __future__ import annotations
 import numpy as np
 
 
-def forward(params, X):
+def bf16(x):
+    """Round to the nearest BF16 value (ties to even), returned as FP64."""
+    f = np.asarray(x, np.float32)
+    bits = f.view(np.uint32).astype(np.uint64)
+    rounded = ((bits + 0x7FFF + ((bits >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return rounded.view(np.float32).astype(np.float64)
+
+
+def _op(x, on):
+    return bf16(x) if on else np.asarray(x, np.float64)
+
+
+def forward(params, X, bf16_ops=False):
     Ws, bs = params
     h = np.asarray(X, np.float64)
     cache = [h]
     for i, (W, b) in enumerate(zip(Ws, bs)):
-        z = h @ np.asarray(W, np.float64).T + np.asarray(b, np.float64)
+        z = _op(h, bf16_ops) @ _op(W, bf16_ops).T + np.asarray(b, np.float64)
         if i + 1 < len(Ws):
             h = np.maximum(z, 0.0)
         else:
@@ -28,9 +43,9 @@ def forward(params, X):
     return h, cache
 
 
-def loss_and_grads(params, X, Tgt):
+def loss_and_grads(params, X, Tgt, bf16_ops=False):
     Ws, bs = params
-    Y, cache = forward(params, X)
+    Y, cache = forward(params, X, bf16_ops)
     B, out = Y.shape
     diff = Y - np.asarray(Tgt, np.float64)
     loss = float((diff ** 2).mean())
@@ -39,10 +54,10 @@ def loss_and_grads(params, X, Tgt):
     gbs = [None] * len(Ws)
     for i in range(len(Ws) - 1, -1, -1):
         h_in = cache[0] if i == 0 else np.maximum(cache[i], 0.0)
-        gWs[i] = g.T @ h_in
+        gWs[i] = _op(g, bf16_ops).T @ _op(h_in, bf16_ops)
         gbs[i] = g.sum(axis=0)
         if i > 0:
-            g = (g @ np.asarray(Ws[i], np.float64)) * (cache[i] > 0)
+            g = (_op(g, bf16_ops) @ _op(Ws[i], bf16_ops)) * (cache[i] > 0)
     return loss, gWs, gbs
 
 

@@ -229,3 +229,22 @@ def test_proposer_gradients_and_adam_closed_form():
     g = np.array([0.5, -1e-3, 2.0])
     p1, m, v = proposer.adam_step(p, g, np.zeros(3), np.zeros(3), 1, lr=0.01)
     assert np.allclose(p1, p - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+
+
+def test_proposer_bf16_rounding_matches_torch():
+    """The oracle's BF16 operand rounding is round-to-nearest-even, as torch's bfloat16 cast."""
+    rng = np.random.default_rng(17)
+    x = np.concatenate([rng.normal(size=20000) * 10.0 ** rng.integers(-6, 6, 20000),
+                        np.array([0.0, -0.0, 1.0, 1.00390625, 1.005859375, -2.5, 3e38])]).astype(np.float32)
+    ref = torch.as_tensor(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(proposer.bf16(x), ref)
+    # with rounding on, gradients still match finite differences of the rounded loss at a smooth point
+    Ws = [rng.normal(size=(6, 4)) * 0.5, rng.normal(size=(5, 6)) * 0.5, rng.normal(size=(3, 5)) * 0.5]
+    bs = [rng.normal(size=6) * 0.1, rng.normal(size=5) * 0.1, rng.normal(size=3) * 0.1]
+    X = rng.normal(size=(7, 4))
+    Tg = rng.normal(size=(7, 3))
+    l0, g0, _ = proposer.loss_and_grads((Ws, bs), X, Tg)
+    l1, g1, _ = proposer.loss_and_grads((Ws, bs), X, Tg, bf16_ops=True)
+    assert abs(l1 - l0) < 5e-2 * abs(l0)
+    for a, b in zip(g0, g1):
+        assert np.max(np.abs(a - b)) < 5e-2 * np.abs(a).max()
