@@ -181,8 +181,8 @@ leb_status leb_graph_launch(leb_graph g, void* stream);
 leb_status leb_graph_destroy(leb_graph g);
 
 /* ---- learned bound proposer (an addition to the paper; never the final answer) ------------------- */
-/* ReLU MLP n_in -> n_hidden -> n_hidden -> n_out on the tensor cores (FP16 operands, FP32
- * accumulation, FP32 master weights, Adam). Inputs are standardised and outputs de-standardised inside
+/* ReLU MLP n_in -> n_hidden -> n_hidden -> n_out (GEMM operands rounded to BF16, FP32 accumulation,
+ * FP32 master weights, Adam). Inputs are standardised and outputs de-standardised inside
  * the kernels with the statistics set by leb_proposer_set_norm. Weights are initialised on the device
  * from seed (He-uniform). All data pointers are device FP32. */
 leb_status leb_proposer_create(int n_in, int n_hidden, int n_out, unsigned long long seed, leb_proposer* out);
@@ -190,11 +190,20 @@ leb_status leb_proposer_destroy(leb_proposer p);
 /* in_mean/in_std [n_in], out_mean/out_std [n_out]: device FP32, copied. */
 leb_status leb_proposer_set_norm(leb_proposer p, const float* in_mean, const float* in_std,
                                  const float* out_mean, const float* out_std, void* stream);
+/* Marks inputs that are angles (mask [n_in] host ints, 1 = angle): they are wrapped to [-pi, pi)
+ * before standardisation, a canonical form of the same input for quantities periodic in that angle. */
+leb_status leb_proposer_set_periodic(leb_proposer p, const int* mask);
+/* Sets the standardisation statistics to the column means and standard deviations of a training set
+ * X [B, n_in], Y [B, n_out] (device; angle inputs wrapped first). Each output's standard deviation is
+ * floored at 1e-2 of the largest one, so outputs that are zero up to rounding (the bounds of linear
+ * rows) are not scaled up into noise that outweighs the real targets in the loss. */
+leb_status leb_proposer_fit_norm(leb_proposer p, int B, const float* X, const float* Y, void* stream);
 /* Y [B, n_out] = de-standardised network output for X [B, n_in]. */
 leb_status leb_proposer_forward(leb_proposer p, int B, const float* X, float* Y, void* workspace,
                                 size_t ws_bytes, void* stream);
-/* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the MSE between the network output and the
- * standardised targets Ytgt [B, n_out]; loss (device float, may be NULL) receives the mean loss. */
+/* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the mean-squared error between the network
+ * output and the targets Ytgt [B, n_out] (given in original units; standardised inside with out_mean,
+ * out_std); loss (device float, may be NULL) receives the mean squared error in standardised units. */
 leb_status leb_proposer_train_step(leb_proposer p, int B, const float* X, const float* Ytgt, float lr,
                                    float* loss, void* workspace, size_t ws_bytes, void* stream);
 leb_status leb_proposer_workspace_size(leb_proposer p, int B_max, size_t* bytes);

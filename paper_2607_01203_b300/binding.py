@@ -57,7 +57,7 @@ EXPORTS = [
     "leb_graph_capture", "leb_graph_launch", "leb_graph_destroy", "leb_proposer_create", "leb_proposer_destroy",
     "leb_proposer_set_norm", "leb_proposer_forward", "leb_proposer_train_step", "leb_proposer_workspace_size",
     "leb_proposer_get_layer", "leb_proposer_set_layer", "leb_proposer_get_grad", "leb_selftest_point_enclosures",
-    "leb_bounds_static", "leb_bounds_static_max_traj", "leb_status_string", "leb_version",
+    "leb_bounds_static", "leb_bounds_static_max_traj", "leb_proposer_fit_norm", "leb_proposer_set_periodic", "leb_status_string", "leb_version",
 ]
 
 
@@ -105,6 +105,8 @@ def lib():
         L.leb_bounds_static.argtypes = [vp, C.POINTER(BatchDesc), i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp, vp, vp,
                                         vp]
         L.leb_bounds_static_max_traj.argtypes = []
+        L.leb_proposer_fit_norm.argtypes = [vp, i32, vp, vp, vp]
+        L.leb_proposer_set_periodic.argtypes = [vp, C.POINTER(i32)]
         _lib = L
     return _lib
 

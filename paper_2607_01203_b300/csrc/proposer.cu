@@ -1,0 +1,433 @@
+// Learned LEB proposer: a ReLU MLP n_in -> H -> H -> n_out that maps (x~_k, u~_k, state radii) to
+// standardised (r_lo, r_hi). It only proposes bounds; the certified kernels stay the final answer and
+// the judge of its error. (An addition to the paper's method.)
+//
+// Training and inference run in this file's kernels: GEMMs with operands rounded to BF16 and FP32
+// accumulation, bias/ReLU epilogues, mean-squared-error gradient, column sums for the bias gradients,
+// and a fused Adam update of the FP32 master weights.
+#include <cmath>
+#include <cuda_bf16.h>
+#include <new>
+#include <vector>
+#include <algorithm>
+
+#include "internal.h"
+
+struct leb_proposer_s {
+  int n_in = 0, H = 0, n_out = 0;
+  float* W[3] = {};
+  float* b[3] = {};
+  float* gW[3] = {};
+  float* gb[3] = {};
+  float* mW[3] = {};
+  float* vW[3] = {};
+  float* mb[3] = {};
+  float* vb[3] = {};
+  float* norm = nullptr;  // in_mean [n_in], in_std [n_in], out_mean [n_out], out_std [n_out]
+  int* periodic = nullptr;  // [n_in] 1: the input is an angle, wrapped to [-pi, pi) before standardising
+  int step = 0;
+};
+
+namespace leb {
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// C[M, N] = op(A) op(B) (+ bias[N]) (ReLU) or (* (Mask > 0)); operands rounded to BF16, FP32 accumulate.
+// op(A)[m, k] = tA ? A[k * lda + m] : A[m * lda + k];  op(B)[k, n] = tB ? B[n * ldb + k] : B[k * ldb + n].
+// epi: 0 store, 1 + bias, 2 + bias then ReLU, 3 multiply by (Mask[m, n] > 0).
+__global__ void __launch_bounds__(256) prop_gemm_kernel(int M, int N, int K, const float* A, int lda, int tA,
+                                                        const float* B, int ldb, int tB, float* C, int ldc,
+                                                        const float* bias, const float* Mask, int epi) {
+  __shared__ float sa[16][68];
+  __shared__ float sb[16][68];
+  const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      int mm, kk;
+      if (tA) { kk = e / 64; mm = e - kk * 64; }
+      else { mm = e / 16; kk = e - mm * 16; }
+      const int m = m0 + mm, k = k0 + kk;
+      float v = 0.f;
+      if (m < M && k < K) v = tA ? A[(long long)k * lda + m] : A[(long long)m * lda + k];
+      sa[kk][mm] = bf16r(v);
+      int nn, kb;
+      if (tB) { nn = e / 16; kb = e - nn * 16; }
+      else { kb = e / 64; nn = e - kb * 64; }
+      const int n = n0 + nn, k2 = k0 + kb;
+      float w = 0.f;
+      if (n < N && k2 < K) w = tB ? B[(long long)n * ldb + k2] : B[(long long)k2 * ldb + n];
+      sb[kb][nn] = bf16r(w);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = sa[kk][4 * ty + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = sb[kk][4 * tx + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + 4 * ty + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + 4 * tx + j;
+      if (n >= N) continue;
+      float v = acc[i][j];
+      if (epi == 1 || epi == 2) v += bias[n];
+      if (epi == 2) v = fmaxf(v, 0.f);
+      if (epi == 3) v = Mask[(long long)m * ldc + n] > 0.f ? v : 0.f;
+      C[(long long)m * ldc + n] = v;
+    }
+  }
+}
+
+__device__ __forceinline__ float wrap_pi(float x) {
+  const float two_pi = 6.283185307179586f;
+  float r = fmodf(x + 3.141592653589793f, two_pi);
+  if (r < 0.f) r += two_pi;
+  return r - 3.141592653589793f;
+}
+
+__global__ void prop_standardize_kernel(long long total, int n, const float* X, const int* periodic, const float* mean,
+                                        const float* stdv, float* Xs) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e % n);
+    const float x = periodic[j] ? wrap_pi(X[e]) : X[e];
+    Xs[e] = (x - mean[j]) / stdv[j];
+  }
+}
+
+__global__ void prop_destandardize_kernel(long long total, int n, const float* y, const float* mean, const float* stdv,
+                                          float* Y) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e % n);
+    Y[e] = fmaf(y[e], stdv[j], mean[j]);
+  }
+}
+
+// dy = 2 (y - t) / (B n) with t the standardised target; loss += mean (y - t)^2
+__global__ void prop_mse_kernel(long long total, int n, const float* y, const float* Y, const float* mean,
+                                const float* stdv, float* dy, float* loss) {
+  float part = 0.f;
+  const float scale = 2.f / (float)total;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e % n);
+    const float tgt = (Y[e] - mean[j]) / stdv[j];
+    const float d = y[e] - tgt;
+    dy[e] = scale * d;
+    part = fmaf(d, d, part);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (loss && (threadIdx.x & 31) == 0) atomicAdd(loss, part / (float)total);
+}
+
+__global__ void prop_colsum_kernel(int M, int N, const float* G, float* out) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.f;
+  for (int m = 0; m < M; ++m) s += G[(long long)m * N + n];
+  out[n] = s;
+}
+
+// column mean and standard deviation (two passes, FP64 accumulation); std floored at 1e-6 (+ tiny)
+__global__ void prop_colstats_kernel(int M, int N, const float* X, const int* periodic, float* mean, float* stdv) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const bool wrap = periodic && periodic[n];
+  double s = 0.0;
+  for (int m = 0; m < M; ++m) s += wrap ? wrap_pi(X[(long long)m * N + n]) : X[(long long)m * N + n];
+  const double mu = s / M;
+  double v = 0.0;
+  for (int m = 0; m < M; ++m) {
+    const double d = (wrap ? wrap_pi(X[(long long)m * N + n]) : X[(long long)m * N + n]) - mu;
+    v += d * d;
+  }
+  mean[n] = (float)mu;
+  stdv[n] = (float)fmax(sqrt(v / M), 1e-6 * (fabs(mu) + 1e-30)) + 1e-30f;
+}
+
+// out_std[j] = max(out_std[j], rel * max_j out_std): one block. Outputs whose spread is far below the
+// others' (bounds that are zero up to rounding) are standardised by the floor, so their rounding noise
+// does not weigh in the loss like a real target.
+__global__ void prop_std_floor_kernel(int N, float* stdv, float rel) {
+  __shared__ float red[256];
+  float m = 0.f;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) m = fmaxf(m, stdv[j]);
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  const float f = rel * red[0];
+  for (int j = threadIdx.x; j < N; j += blockDim.x) stdv[j] = fmaxf(stdv[j], f);
+}
+
+__global__ void prop_adam_kernel(long long total, float* p, const float* g, float* m, float* v, float lr, float b1,
+                                 float b2, float eps, float c1, float c2) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const float gg = g[e];
+    const float mm = b1 * m[e] + (1.f - b1) * gg;
+    const float vv = b2 * v[e] + (1.f - b2) * gg * gg;
+    m[e] = mm;
+    v[e] = vv;
+    p[e] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+  }
+}
+
+// He-uniform initialisation from a counter-based hash (splitmix64 of seed and index).
+__device__ __forceinline__ unsigned long long splitmix(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+__global__ void prop_init_kernel(long long total, float* W, float bound, unsigned long long seed) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long r = splitmix(seed ^ (unsigned long long)e * 0xD1B54A32D192ED03ull);
+    const float u = (float)(r >> 40) * (1.f / 16777216.f);  // [0, 1)
+    W[e] = (2.f * u - 1.f) * bound;
+  }
+}
+
+namespace {
+
+inline int blocks_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 148LL * 16); }
+
+cudaError_t gemm(cudaStream_t s, int M, int N, int K, const float* A, int lda, int tA, const float* B, int ldb, int tB,
+                 float* C, int ldc, const float* bias, const float* Mask, int epi) {
+  dim3 grid((M + 63) / 64, (N + 63) / 64);
+  prop_gemm_kernel<<<grid, 256, 0, s>>>(M, N, K, A, lda, tA, B, ldb, tB, C, ldc, bias, Mask, epi);
+  return cudaGetLastError();
+}
+
+// workspace (floats): Xs [B, n_in], h0 [B, H], h1 [B, H], y [B, n_out], dy [B, n_out], d1 [B, H], d0 [B, H]
+size_t ws_floats(const leb_proposer_s* p, int B) {
+  return (size_t)B * (p->n_in + 4 * p->H + 2 * p->n_out) + 64;
+}
+
+}  // namespace
+}  // namespace leb
+
+using namespace leb;
+
+extern "C" {
+
+leb_status leb_proposer_create(int n_in, int n_hidden, int n_out, unsigned long long seed, leb_proposer* out) {
+  if (!out || n_in < 1 || n_hidden < 1 || n_out < 1 || n_in > 65536 || n_hidden > 65536 || n_out > 65536)
+    return LEB_ERR_INVALID_ARG;
+  *out = nullptr;
+  leb_proposer p = new (std::nothrow) leb_proposer_s();
+  if (!p) return LEB_ERR_CUDA;
+  p->n_in = n_in;
+  p->H = n_hidden;
+  p->n_out = n_out;
+  const int ins[3] = {n_in, n_hidden, n_hidden}, outs[3] = {n_hidden, n_hidden, n_out};
+  bool ok = true;
+  for (int i = 0; i < 3 && ok; ++i) {
+    const size_t nw = (size_t)ins[i] * outs[i], nb = outs[i];
+    for (float** q : {&p->W[i], &p->gW[i], &p->mW[i], &p->vW[i]}) ok = ok && cudaMalloc(q, nw * 4) == cudaSuccess;
+    for (float** q : {&p->b[i], &p->gb[i], &p->mb[i], &p->vb[i]}) ok = ok && cudaMalloc(q, nb * 4) == cudaSuccess;
+    if (!ok) break;
+    ok = cudaMemset(p->mW[i], 0, nw * 4) == cudaSuccess && cudaMemset(p->vW[i], 0, nw * 4) == cudaSuccess &&
+         cudaMemset(p->mb[i], 0, nb * 4) == cudaSuccess && cudaMemset(p->vb[i], 0, nb * 4) == cudaSuccess &&
+         cudaMemset(p->b[i], 0, nb * 4) == cudaSuccess;
+    const float bound = std::sqrt(6.f / (float)ins[i]);
+    prop_init_kernel<<<blocks_for((long long)nw), 256>>>((long long)nw, p->W[i], bound, seed * 7919ull + i);
+    ok = ok && cudaGetLastError() == cudaSuccess;
+  }
+  ok = ok && cudaMalloc(&p->norm, (size_t)2 * (n_in + n_out) * 4) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->periodic, (size_t)n_in * sizeof(int)) == cudaSuccess &&
+       cudaMemset(p->periodic, 0, (size_t)n_in * sizeof(int)) == cudaSuccess;
+  if (ok) {
+    // identity normalisation until set
+    std::vector<float> h(2 * (n_in + n_out), 0.f);
+    for (int j = 0; j < n_in; ++j) h[n_in + j] = 1.f;
+    for (int j = 0; j < n_out; ++j) h[2 * n_in + n_out + j] = 1.f;
+    ok = cudaMemcpy(p->norm, h.data(), h.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  if (!ok || cudaDeviceSynchronize() != cudaSuccess) {
+    leb_proposer_destroy(p);
+    return LEB_ERR_CUDA;
+  }
+  *out = p;
+  return LEB_OK;
+}
+
+leb_status leb_proposer_destroy(leb_proposer p) {
+  if (!p) return LEB_ERR_INVALID_ARG;
+  for (int i = 0; i < 3; ++i)
+    for (float* q : {p->W[i], p->gW[i], p->mW[i], p->vW[i], p->b[i], p->gb[i], p->mb[i], p->vb[i]}) cudaFree(q);
+  cudaFree(p->norm);
+  cudaFree(p->periodic);
+  delete p;
+  return LEB_OK;
+}
+
+leb_status leb_proposer_set_norm(leb_proposer p, const float* in_mean, const float* in_std, const float* out_mean,
+                                 const float* out_std, void* stream) {
+  if (!p || !in_mean || !in_std || !out_mean || !out_std) return LEB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t a = (size_t)p->n_in * 4, b = (size_t)p->n_out * 4;
+  bool ok = cudaMemcpyAsync(p->norm, in_mean, a, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+            cudaMemcpyAsync(p->norm + p->n_in, in_std, a, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+            cudaMemcpyAsync(p->norm + 2 * p->n_in, out_mean, b, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+            cudaMemcpyAsync(p->norm + 2 * p->n_in + p->n_out, out_std, b, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+  return ok ? LEB_OK : LEB_ERR_CUDA;
+}
+
+leb_status leb_proposer_fit_norm(leb_proposer p, int B, const float* X, const float* Y, void* stream) {
+  if (!p || B < 1 || !X || !Y) return LEB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  prop_colstats_kernel<<<(p->n_in + 127) / 128, 128, 0, s>>>(B, p->n_in, X, p->periodic, p->norm, p->norm + p->n_in);
+  prop_colstats_kernel<<<(p->n_out + 127) / 128, 128, 0, s>>>(B, p->n_out, Y, nullptr, p->norm + 2 * p->n_in,
+                                                              p->norm + 2 * p->n_in + p->n_out);
+  prop_std_floor_kernel<<<1, 256, 0, s>>>(p->n_out, p->norm + 2 * p->n_in + p->n_out, 1e-2f);
+  return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
+}
+
+leb_status leb_proposer_set_periodic(leb_proposer p, const int* mask) {
+  if (!p || !mask) return LEB_ERR_INVALID_ARG;
+  return cudaMemcpy(p->periodic, mask, (size_t)p->n_in * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess
+             ? LEB_OK
+             : LEB_ERR_CUDA;
+}
+
+leb_status leb_proposer_workspace_size(leb_proposer p, int B_max, size_t* bytes) {
+  if (!p || !bytes || B_max < 0) return LEB_ERR_INVALID_ARG;
+  *bytes = ws_floats(p, B_max) * sizeof(float);
+  return LEB_OK;
+}
+
+static leb_status forward_impl(leb_proposer p, int B, const float* X, float* ws, cudaStream_t s) {
+  const int n_in = p->n_in, H = p->H, n_out = p->n_out;
+  float* Xs = ws;
+  float* h0 = Xs + (size_t)B * n_in;
+  float* h1 = h0 + (size_t)B * H;
+  float* y = h1 + (size_t)B * H;
+  prop_standardize_kernel<<<blocks_for((long long)B * n_in), 256, 0, s>>>((long long)B * n_in, n_in, X, p->periodic,
+                                                                            p->norm, p->norm + n_in, Xs);
+  if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
+  // h0 = relu(Xs W0^T + b0), h1 = relu(h0 W1^T + b1), y = h1 W2^T + b2   (W_i [out, in])
+  if (gemm(s, B, H, n_in, Xs, n_in, 0, p->W[0], n_in, 1, h0, H, p->b[0], nullptr, 2) != cudaSuccess ||
+      gemm(s, B, H, H, h0, H, 0, p->W[1], H, 1, h1, H, p->b[1], nullptr, 2) != cudaSuccess ||
+      gemm(s, B, n_out, H, h1, H, 0, p->W[2], H, 1, y, n_out, p->b[2], nullptr, 1) != cudaSuccess)
+    return LEB_ERR_CUDA;
+  return LEB_OK;
+}
+
+leb_status leb_proposer_forward(leb_proposer p, int B, const float* X, float* Y, void* workspace, size_t ws_bytes,
+                                void* stream) {
+  if (!p || B < 0 || (B > 0 && (!X || !Y))) return LEB_ERR_INVALID_ARG;
+  if (!workspace || ws_bytes < ws_floats(p, B) * sizeof(float)) return LEB_ERR_WORKSPACE;
+  if (B == 0) return LEB_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* ws = (float*)workspace;
+  leb_status st = forward_impl(p, B, X, ws, s);
+  if (st != LEB_OK) return st;
+  const float* y = ws + (size_t)B * (p->n_in + 2 * p->H);
+  const long long tot = (long long)B * p->n_out;
+  prop_destandardize_kernel<<<blocks_for(tot), 256, 0, s>>>(tot, p->n_out, y, p->norm + 2 * p->n_in,
+                                                             p->norm + 2 * p->n_in + p->n_out, Y);
+  return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
+}
+
+leb_status leb_proposer_train_step(leb_proposer p, int B, const float* X, const float* Ytgt, float lr, float* loss,
+                                   void* workspace, size_t ws_bytes, void* stream) {
+  if (!p || B < 1 || !X || !Ytgt || !(lr > 0.f)) return LEB_ERR_INVALID_ARG;
+  if (!workspace || ws_bytes < ws_floats(p, B) * sizeof(float)) return LEB_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* ws = (float*)workspace;
+  leb_status st = forward_impl(p, B, X, ws, s);
+  if (st != LEB_OK) return st;
+  const int n_in = p->n_in, H = p->H, n_out = p->n_out;
+  float* Xs = ws;
+  float* h0 = Xs + (size_t)B * n_in;
+  float* h1 = h0 + (size_t)B * H;
+  float* y = h1 + (size_t)B * H;
+  float* dy = y + (size_t)B * n_out;
+  float* d1 = dy + (size_t)B * n_out;
+  float* d0 = d1 + (size_t)B * H;
+  if (loss && cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) return LEB_ERR_CUDA;
+  const long long tot = (long long)B * n_out;
+  prop_mse_kernel<<<blocks_for(tot), 256, 0, s>>>(tot, n_out, y, Ytgt, p->norm + 2 * n_in, p->norm + 2 * n_in + n_out,
+                                                   dy, loss);
+  if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
+  // layer 2: dW2 = dy^T h1, db2 = sum dy, d1 = (dy W2) o (h1 > 0)
+  if (gemm(s, n_out, H, B, dy, n_out, 1, h1, H, 0, p->gW[2], H, nullptr, nullptr, 0) != cudaSuccess) return LEB_ERR_CUDA;
+  prop_colsum_kernel<<<(n_out + 255) / 256, 256, 0, s>>>(B, n_out, dy, p->gb[2]);
+  if (gemm(s, B, H, n_out, dy, n_out, 0, p->W[2], H, 0, d1, H, nullptr, h1, 3) != cudaSuccess) return LEB_ERR_CUDA;
+  // layer 1
+  if (gemm(s, H, H, B, d1, H, 1, h0, H, 0, p->gW[1], H, nullptr, nullptr, 0) != cudaSuccess) return LEB_ERR_CUDA;
+  prop_colsum_kernel<<<(H + 255) / 256, 256, 0, s>>>(B, H, d1, p->gb[1]);
+  if (gemm(s, B, H, H, d1, H, 0, p->W[1], H, 0, d0, H, nullptr, h0, 3) != cudaSuccess) return LEB_ERR_CUDA;
+  // layer 0
+  if (gemm(s, H, n_in, B, d0, H, 1, Xs, n_in, 0, p->gW[0], n_in, nullptr, nullptr, 0) != cudaSuccess) return LEB_ERR_CUDA;
+  prop_colsum_kernel<<<(H + 255) / 256, 256, 0, s>>>(B, H, d0, p->gb[0]);
+  if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
+  // Adam
+  p->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)p->step), c2 = 1.f - std::pow(b2, (float)p->step);
+  const int ins[3] = {n_in, H, H}, outs[3] = {H, H, n_out};
+  for (int i = 0; i < 3; ++i) {
+    const long long nw = (long long)ins[i] * outs[i];
+    prop_adam_kernel<<<blocks_for(nw), 256, 0, s>>>(nw, p->W[i], p->gW[i], p->mW[i], p->vW[i], lr, b1, b2, 1e-8f, c1, c2);
+    prop_adam_kernel<<<blocks_for(outs[i]), 256, 0, s>>>(outs[i], p->b[i], p->gb[i], p->mb[i], p->vb[i], lr, b1, b2,
+                                                          1e-8f, c1, c2);
+  }
+  return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
+}
+
+static leb_status layer_dims(leb_proposer p, int i, int* in, int* out) {
+  if (!p || i < 0 || i > 2) return LEB_ERR_INVALID_ARG;
+  const int ins[3] = {p->n_in, p->H, p->H}, outs[3] = {p->H, p->H, p->n_out};
+  *in = ins[i];
+  *out = outs[i];
+  return LEB_OK;
+}
+
+leb_status leb_proposer_get_layer(leb_proposer p, int i, float* W, float* b, void* stream) {
+  int in, out;
+  if (layer_dims(p, i, &in, &out) != LEB_OK || !W || !b) return LEB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  return (cudaMemcpyAsync(W, p->W[i], (size_t)in * out * 4, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+          cudaMemcpyAsync(b, p->b[i], (size_t)out * 4, cudaMemcpyDeviceToDevice, s) == cudaSuccess)
+             ? LEB_OK
+             : LEB_ERR_CUDA;
+}
+
+leb_status leb_proposer_set_layer(leb_proposer p, int i, const float* W, const float* b, void* stream) {
+  int in, out;
+  if (layer_dims(p, i, &in, &out) != LEB_OK || !W || !b) return LEB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  return (cudaMemcpyAsync(p->W[i], W, (size_t)in * out * 4, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+          cudaMemcpyAsync(p->b[i], b, (size_t)out * 4, cudaMemcpyDeviceToDevice, s) == cudaSuccess)
+             ? LEB_OK
+             : LEB_ERR_CUDA;
+}
+
+leb_status leb_proposer_get_grad(leb_proposer p, int i, float* dW, float* db, void* stream) {
+  int in, out;
+  if (layer_dims(p, i, &in, &out) != LEB_OK || !dW || !db) return LEB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  return (cudaMemcpyAsync(dW, p->gW[i], (size_t)in * out * 4, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+          cudaMemcpyAsync(db, p->gb[i], (size_t)out * 4, cudaMemcpyDeviceToDevice, s) == cudaSuccess)
+             ? LEB_OK
+             : LEB_ERR_CUDA;
+}
+
+}  // extern "C"
