@@ -1,17 +1,22 @@
 """Benchmark of the certified LEB hot path on B300 (one JSON line on rank 0).
 
-A step is one pass of the hot path over one batch of seeded synthetic input:
-  * plain form: path-based Hessian bounds (Thm. 1) for the 28-quadrotor spring chain
-    (n_x = 168, n_u = 56), 256 trajectories x N = 50 (T = 12800 timesteps), zonotope tube sets with
-    2 n_x = 336 generators, A_k and B_k written;
-  * batched / tensor-core form: CROWN (Thm. 2-3) bounds of the residual tanh MLP 224->512->512->512->168,
-    128 trajectories x N = 50 (T = 6400), box sets, FP16 tensor-core back-substitution (when built);
-  * the adjoint of the MLP bounds (backward, when built) and the proposer inference (when built).
-``value`` = certified timestep-bounds per second over the forward forms (whole job, all ranks).
+A step is one pass of the whole hot path over one batch of seeded synthetic input, four forms in turn:
+  * plain form (pbh): path-based Hessian bounds (Thm. 1) for the 28-quadrotor spring chain
+    (n_x = 168, n_u = 56), 256 trajectories x N = 50 (T = 12800), zonotope tube sets with 2 n_x = 336
+    generators, A_k and B_k written;
+  * batched / tensor-core form (crown): CROWN + Jacobian correction (Thms. 2-3) for the residual tanh MLP
+    224->512->512->512->168, 128 trajectories x N = 50 (T = 6400), box sets, FP16 tensor-core
+    back-substitution with rigorous inflation, A_k and B_k written;
+  * backward: the adjoint d(r_lo, r_hi)/d(x~, u~, radii) of the crown form's bounds with random cotangents;
+  * proposer: the learned proposer's inference on 12800 quad-chain inputs (trained once at start-up on
+    10^5 certified bounds; its training step, error and the certified kernel's time on the same inputs
+    are reported beside it).
+``value`` = certified timestep-bounds per second of the whole step (pbh + crown timesteps over the time
+of all four forms), summed over ranks.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--forms pbh,crown,...]
-For N > 1 it runs under torchrun, one independent replica per GPU (the bound of every timestep is
-independent, so the path shards with no data exchange; only the timing uses a barrier and a max).
+For N > 1 it runs under torchrun, one independent replica per GPU (every timestep's bound is independent,
+so the path shards with no data exchange; only the timing uses a barrier and a max).
 """
 from __future__ import annotations
 
@@ -32,15 +37,52 @@ sys.path.insert(0, ROOT)
 METRIC = "certified LEB timestep-bounds/s at n_x=168, N=50; backward µs; % of roofline"
 UNIT = "timestep-bounds/s"
 
+# algorithmic work per unit (derivations beside each form)
+PBH_BYTES_PER_TS = 4 * (224 * 336 + 168 + 56 + 2 * 168 + 168 * 168 + 168 * 56)   # 453,824
+MLP_WIDTHS = (224, 512, 512, 512, 168)
+PROPOSER_FLOP = 2 * (392 * 256 + 256 * 256 + 256 * 336)                           # 503,808 per sample
+
+
+def crown_flop_per_ts(w=MLP_WIDTHS):
+    """Back-substitution FLOPs per timestep: every chain row times every weight it passes through.
+    Intermediate bounds of hidden layer i (2 width_i rows) pass W_{i-1} .. W_0; the output chain has
+    3 n_x rows (lower, upper, Jacobian) and passes W_{L-2} .. W_0."""
+    L = len(w) - 1
+    tot = 0
+    for i in range(2, L):                       # hidden layers whose bounds need back-substitution
+        rows = 2 * w[i]
+        tot += rows * sum(2 * w[k + 1] * w[k] for k in range(i - 1))
+    tot += 3 * w[L] * sum(2 * w[k + 1] * w[k] for k in range(L - 1))
+    return tot
+
+
+def hidden_flop_per_ts(w=MLP_WIDTHS):
+    """The part of crown_flop_per_ts spent on the hidden layers' intermediate bounds."""
+    L = len(w) - 1
+    return sum(2 * w[i] * sum(2 * w[k + 1] * w[k] for k in range(i - 1)) for i in range(2, L))
+
+
+def adjoint_flop_per_ts(w=MLP_WIDTHS):
+    """Adjoint FLOPs per timestep: the hidden layers' bounds recomputed, then every chain (output and
+    intermediate) recomputed forward and run backward, twice its forward work."""
+    return hidden_flop_per_ts(w) + 2 * crown_flop_per_ts(w)
+
 
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             p = json.load(fh)
         return {"hbm_gbs": p["hbm_gbs"], "bf16_tflops": p["bf16_tflops"],
-                "bf16_tflops_sustained": p.get("bf16_tflops_sustained", p["bf16_tflops"]), "src": "measured"}
+                "bf16_tflops_sustained": p.get("bf16_tflops_sustained", p["bf16_tflops"]),
+                "sm_max_mhz": p.get("sm_max_mhz", 2032.0), "src": "measured"}
     except Exception:
-        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "src": "fallback"}
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0,
+                "src": "fallback"}
+
+
+def fp32_simt_peak_tflops(pk):
+    """FP32 FMA peak of the CUDA cores: 148 SMs x 128 lanes x 2 FLOP x max SM clock."""
+    return 148 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
 
 
 # ------------------------------------------------------------------------------------------------
@@ -78,7 +120,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
+        sm, smax, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
@@ -87,89 +129,85 @@ class ClockSampler:
             try:
                 sm.append(float(parts[0]))
                 smax.append(float(parts[1]))
+                pw.append(float(parts[2]))
             except ValueError:
                 continue
             for nm, v in zip(names, parts[4:8]):
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(pw) if pw else None}
 
 
 # ------------------------------------------------------------------------------------------------
-class PbhForm:
-    """Plain form: PBH over the chain batch (zonotope sets), A and B written."""
-    name = "plain_pbh"
+class Form:
+    """One form of the hot path: set-up (untimed), run (one pass), its timed main kernel and extras."""
+    name = ""
+    handle = None
+    which = 0  # entry point of the library's timer records: 0 leb_bounds, 1 leb_bounds_backward
+
+    def units(self):
+        return 0
+
+
+class PbhForm(Form):
+    """Plain form: PBH over the chain batch (zonotope sets), A and B written.
+
+    Algorithmic bytes per timestep: the generators read once (224 x 336 x 4 = 301,056 B), x~, u~ read,
+    r_lo, r_hi and A (168 x 168), B (168 x 56) written, all FP32: 453,824 B."""
+    name = "pbh"
 
     def __init__(self, torch, dev, quick=False):
         from paper_2607_01203_b300 import binding, inputs
         self.torch = torch
-        n_traj = 16 if quick else 256
-        self.w = inputs.quad_chain(n_traj=n_traj, horizon=50)
+        self.w = inputs.quad_chain(n_traj=16 if quick else 256, horizon=50)
         w = self.w
         self.T = w.T
-        self.h = binding.quad_chain(28, **w.params, spring_k=w.spring_k)
+        self.handle = binding.quad_chain(28, **w.params, spring_k=w.spring_k)
         self.x = torch.as_tensor(w.x_nom).to(dev)
         self.u = torch.as_tensor(w.u_nom).to(dev)
         self.G = torch.as_tensor(w.G).to(dev)
-        self.out = self.h.bounds(self.x, self.u, G=self.G)
+        self.out = self.handle.bounds(self.x, self.u, G=self.G)
         torch.cuda.synchronize()
-        n, p, nx, nu = 224, w.G.shape[-1], 168, 56
-        self.bytes_per_ts = 4 * (n * p + nx + nu + 2 * nx + nx * nx + nx * nu)
-        self.kernel_ms = []
-        self.kernels_per_call = 1
+        self.desc = f"28-quadrotor spring chain n_x=168 n_u=56, {self.T // 50} traj x N=50, zonotope 224x336"
 
-    def run(self, timed=False):
-        torch = self.torch
-        if timed:
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-        self.h.bounds(self.x, self.u, G=self.G, out=self.out)
-        if timed:
-            e1.record()
-            self.kernel_events.append((e0, e1))
+    def run(self):
+        self.handle.bounds(self.x, self.u, G=self.G, out=self.out)
 
     def units(self):
         return self.T
 
-    def roofline(self, pk):
-        ms = statistics.mean(self.kernel_ms)
-        achieved = self.bytes_per_ts * self.T / (ms * 1e-3) / 1e9
+    def roofline(self, pk, ms, launches, kernel):
+        achieved = PBH_BYTES_PER_TS * self.T / (ms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
-                "peak_src": pk["src"] + " hbm_gbs (STREAM-style copy)", "kernel": "pbh_chain_kernel<zono>",
-                "kernel_ms": round(ms, 4), "bytes_per_timestep": self.bytes_per_ts, "timesteps": self.T}
+                "peak_src": pk["src"] + " hbm_gbs (STREAM-style copy)", "kernel": kernel,
+                "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
+                "bytes_per_unit": PBH_BYTES_PER_TS, "units_per_launch": self.T // max(launches, 1)}
 
     def e2e(self, steps):
-        """Same metric through the C ABI from pinned HOST buffers, copies inside the timed region."""
+        """The same work through the C ABI from pinned host buffers, copies inside the timed region."""
         torch = self.torch
         hx = torch.as_tensor(self.w.x_nom).pin_memory()
         hu = torch.as_tensor(self.w.u_nom).pin_memory()
         hG = torch.as_tensor(self.w.G).pin_memory()
-        out_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in self.out.items()
-                 if torch.is_tensor(v) and k in ("r_lo", "r_hi", "A", "B")}
+        out_h = {k: torch.empty(self.out[k].shape).pin_memory() for k in ("r_lo", "r_hi", "A", "B")}
         dx, du, dG = torch.empty_like(self.x), torch.empty_like(self.u), torch.empty_like(self.G)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(steps):
+
+        def one():
             dx.copy_(hx, non_blocking=True)
             du.copy_(hu, non_blocking=True)
             dG.copy_(hG, non_blocking=True)
-            o = self.h.bounds(dx, du, G=dG, out=self.out)
+            o = self.handle.bounds(dx, du, G=dG, out=self.out)
             for k, v in out_h.items():
                 v.copy_(o[k], non_blocking=True)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        h2d = hx.numel() * 4 + hu.numel() * 4 + hG.numel() * 4
+        ms = timed_loop(torch, one, steps)
+        h2d = (hx.numel() + hu.numel() + hG.numel()) * 4
         d2h = sum(v.numel() * 4 for v in out_h.values())
         return ms, h2d, d2h
 
-    def cpu_baseline(self, budget_s=12.0):
-        """The FP64 oracle (as it stands) on a bounded sample of the same workload."""
+    def oracle_seconds_per_unit(self, budget_s):
+        """The FP64 oracle as it stands on a sample of this batch's timesteps: seconds per timestep."""
         from oracle import dynamics, pbh
         w = self.w
         dyn = dynamics.QuadChain(28, **w.params, spring_k=w.spring_k)
@@ -182,46 +220,297 @@ class PbhForm:
             pbh.pbh(dyn, a, lo, hi)
             dyn.jacobian(a)
             done += 1
-        el = time.perf_counter() - t0
-        return {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": f"{done} timesteps of the chain batch (PBH, zonotope hull, Jacobian) in {el:.1f} s"}
+        return (time.perf_counter() - t0) / done, done
 
 
-FORMS = {"pbh": PbhForm}
+class CrownForm(Form):
+    """Batched / tensor-core form: CROWN + Jacobian correction of the residual tanh MLP, FP16 tensor-core
+    back-substitution, A and B written.
+
+    Algorithmic FLOPs per timestep: every chain row times every weight it passes (crown_flop_per_ts):
+    1.651 GFLOP for 224->512->512->512->168."""
+    name = "crown"
+
+    def __init__(self, torch, dev, quick=False):
+        from paper_2607_01203_b300 import binding, inputs
+        self.torch = torch
+        self.w = inputs.tanh_mlp(n_traj=8 if quick else 128, N=50)
+        w = self.w
+        self.T = w.T
+        self.handle = binding.mlp(w.Ws, w.bs, w.act, w.residual, "fp16")
+        self.x = torch.as_tensor(w.x_nom).to(dev)
+        self.u = torch.as_tensor(w.u_nom).to(dev)
+        self.r = torch.as_tensor(w.radii).to(dev)
+        self.out = self.handle.bounds(self.x, self.u, radii=self.r)
+        torch.cuda.synchronize()
+        self.desc = f"residual tanh MLP 224-512-512-512-168, {self.T // 50} traj x N=50, box sets, FP16 TC"
+
+    def run(self):
+        self.handle.bounds(self.x, self.u, radii=self.r, out=self.out)
+
+    def units(self):
+        return self.T
+
+    def roofline(self, pk, ms, launches, kernel):
+        flop = crown_flop_per_ts() * self.T
+        achieved = flop / (ms * 1e-3) / 1e12
+        return {"bound": "tensor", "achieved": round(achieved, 1), "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                "frac": round(achieved / pk["bf16_tflops"], 4), "traffic": None,
+                "peak_src": pk["src"] + " bf16_tflops (cuBLAS bf16 burst; FP16 dense rate is the same)",
+                "kernel": kernel, "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
+                "flop_per_unit": crown_flop_per_ts(), "units_per_step": self.T}
+
+    def e2e(self, steps):
+        torch = self.torch
+        hx, hu, hr = (torch.as_tensor(a).pin_memory() for a in (self.w.x_nom, self.w.u_nom, self.w.radii))
+        out_h = {k: torch.empty(self.out[k].shape).pin_memory() for k in ("r_lo", "r_hi", "A", "B")}
+        dx, du, dr = torch.empty_like(self.x), torch.empty_like(self.u), torch.empty_like(self.r)
+
+        def one():
+            dx.copy_(hx, non_blocking=True)
+            du.copy_(hu, non_blocking=True)
+            dr.copy_(hr, non_blocking=True)
+            o = self.handle.bounds(dx, du, radii=dr, out=self.out)
+            for k, v in out_h.items():
+                v.copy_(o[k], non_blocking=True)
+        ms = timed_loop(torch, one, steps)
+        return ms, (hx.numel() + hu.numel() + hr.numel()) * 4, sum(v.numel() * 4 for v in out_h.values())
+
+    def oracle_seconds_per_unit(self, budget_s):
+        from oracle import crown
+        w = self.w
+        t0 = time.perf_counter()
+        done = 0
+        while done < 1 or (time.perf_counter() - t0 < budget_s and done < w.T):
+            t = (done * 97) % w.T
+            crown.box_remainder(w.Ws, w.bs, w.act, w.x_nom[t], w.u_nom[t], w.radii[t], w.residual)
+            done += 1
+        return (time.perf_counter() - t0) / done, done
+
+
+class BackwardForm(Form):
+    """The adjoint of the crown form's bounds (random cotangents), reported in µs per call.
+
+    Algorithmic FLOPs per timestep (adjoint_flop_per_ts): the hidden bounds recomputed (1.007 GFLOP),
+    then every chain recomputed and run backward (2 x 1.651 GFLOP): 4.31 GFLOP."""
+    name = "backward"
+    which = 1
+
+    def __init__(self, torch, dev, quick=False, crown=None):
+        self.torch = torch
+        c = crown if crown is not None else CrownForm(torch, dev, quick)
+        self.c = c
+        self.handle = c.handle
+        self.T = c.T
+        g = torch.Generator(device="cpu").manual_seed(7)
+        self.glo = torch.randn(self.T, 168, generator=g).to(dev)
+        self.ghi = torch.randn(self.T, 168, generator=g).to(dev)
+        self.handle.bounds_backward(c.x, c.u, c.r, self.glo, self.ghi)
+        torch.cuda.synchronize()
+        self.desc = "adjoint of the crown form (cotangents N(0,1))"
+
+    def run(self):
+        self.handle.bounds_backward(self.c.x, self.c.u, self.c.r, self.glo, self.ghi)
+
+    def roofline(self, pk, ms, launches, kernel):
+        flop = adjoint_flop_per_ts() * self.T
+        achieved = flop / (ms * 1e-3) / 1e12
+        tc = "tc" in kernel
+        peak = pk["bf16_tflops"] if tc else fp32_simt_peak_tflops(pk)
+        return {"bound": "tensor" if tc else "alu", "achieved": round(achieved, 2), "peak": round(peak, 1),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_src": (pk["src"] + " bf16_tflops") if tc else
+                "FP32 FMA peak derived: 148 SM x 128 lanes x 2 FLOP x max SM clock (MEASURED_PEAKS sm_max_mhz)",
+                "kernel": kernel, "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
+                "flop_per_unit": adjoint_flop_per_ts(), "units_per_step": self.T}
+
+    def e2e(self, steps):
+        torch = self.torch
+        c = self.c
+        hs = [torch.as_tensor(a).pin_memory() for a in (c.w.x_nom, c.w.u_nom, c.w.radii)]
+        hg = [self.glo.cpu().pin_memory(), self.ghi.cpu().pin_memory()]
+        ds = [torch.empty_like(c.x), torch.empty_like(c.u), torch.empty_like(c.r)]
+        dg = [torch.empty_like(self.glo), torch.empty_like(self.ghi)]
+        outs = [torch.empty(self.T, 168).pin_memory(), torch.empty(self.T, 56).pin_memory(),
+                torch.empty(self.T, 224).pin_memory()]
+
+        def one():
+            for d, h in zip(ds + dg, hs + hg):
+                d.copy_(h, non_blocking=True)
+            gx, gu, gr, _ = self.handle.bounds_backward(ds[0], ds[1], ds[2], dg[0], dg[1])
+            for o, g in zip(outs, (gx, gu, gr)):
+                o.copy_(g, non_blocking=True)
+        ms = timed_loop(torch, one, steps)
+        return ms, sum(h.numel() * 4 for h in hs + hg), sum(o.numel() * 4 for o in outs)
+
+    def oracle_seconds_per_unit(self, budget_s):
+        from oracle import crown
+        w = self.c.w
+        g = np.random.default_rng(7).normal(size=(2, 168))
+        t0 = time.perf_counter()
+        done = 0
+        while done < 1 or (time.perf_counter() - t0 < budget_s and done < w.T):
+            t = (done * 97) % w.T
+            crown.box_remainder_vjp(w.Ws, w.bs, w.act, w.x_nom[t], w.u_nom[t], w.radii[t], g[0], g[1], w.residual)
+            done += 1
+        return (time.perf_counter() - t0) / done, done
+
+
+class ProposerForm(Form):
+    """Learned proposer inference on 12800 quad-chain inputs (x~, u~, state radii), beside the certified
+    PBH kernel on the same box sets. Trained at start-up (untimed) on 10^5 certified bounds.
+
+    Algorithmic FLOPs per sample: 2 (392 x 256 + 256 x 256 + 256 x 336) = 503,808."""
+    name = "proposer"
+
+    def __init__(self, torch, dev, quick=False):
+        from paper_2607_01203_b300 import inputs
+        from paper_2607_01203_b300.proposer import Proposer, certified_dataset, chain_angle_columns
+        self.torch = torch
+        w = inputs.proposer_data(n_rollouts=200 if quick else 2000)
+        X, Y, self.cert = certified_dataset(w)
+        n_tr = int(0.9 * X.shape[0])
+        self.p = Proposer(seed=1)
+        self.p.set_periodic(chain_angle_columns())
+        self.p.fit_norm(X[:n_tr], Y[:n_tr])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        epochs = 5 if quick else 50
+        self.p.fit(X[:n_tr], Y[:n_tr], epochs=epochs, batch=256, lr=1e-3)
+        torch.cuda.synchronize()
+        steps = epochs * (n_tr // 256)
+        self.train_ms_per_step = 1e3 * (time.perf_counter() - t0) / steps
+        # proposal error on the held-out 10 % (curved rows v_x, v_y; the others are zero up to rounding)
+        curved = torch.tensor([6 * i + s for i in range(28) for s in (3, 4)], device=dev)
+        P = self.p.forward(X[n_tr:])
+        Yv = Y[n_tr:]
+        lo_p, hi_p, lo_c, hi_c = P[:, curved], P[:, curved + 168], Yv[:, curved], Yv[:, curved + 168]
+        wmean = (hi_c - lo_c).mean()
+        self.err = ((lo_p - lo_c).abs().mean() + (hi_p - hi_c).abs().mean()).item() / 2 / wmean.item()
+        self.under = ((lo_p > lo_c) | (hi_p < hi_c)).float().mean().item()
+        # inference batch: 12800 fresh inputs
+        t = inputs.proposer_data(seed=1777, n_rollouts=256)
+        self.T = t.T
+        self.xt = torch.as_tensor(t.x_nom).to(dev)
+        self.ut = torch.as_tensor(t.u_nom).to(dev)
+        self.rt = torch.as_tensor(t.radii).to(dev)
+        self.X = torch.cat([self.xt, self.ut, self.rt[:, :168]], 1).contiguous()
+        self.Y = self.p.forward(self.X)
+        self.cert_out = self.cert.bounds(self.xt, self.ut, radii=self.rt, want_AB=False)
+        torch.cuda.synchronize()
+        self.desc = "proposer 392-256-256-336 inference, 12800 quad-chain box inputs"
+
+    def run(self):
+        self.Y = self.p.forward(self.X)
+
+    def certified_ms(self, reps=20):
+        """The certified PBH kernel on the same inputs (box sets, bounds only), ms per call."""
+        torch = self.torch
+        return timed_loop(torch, lambda: self.cert.bounds(self.xt, self.ut, radii=self.rt, want_AB=False,
+                                                          out=self.cert_out), reps)
+
+    def roofline(self, pk, ms, launches, kernel):
+        flop = PROPOSER_FLOP * self.T
+        achieved = flop / (ms * 1e-3) / 1e12
+        peak = fp32_simt_peak_tflops(pk)
+        return {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_src": "FP32 FMA peak derived: 148 SM x 128 lanes x 2 FLOP x max SM clock",
+                "kernel": kernel, "kernel_ms": round(ms, 4), "launches_per_step": launches,
+                "flop_per_unit": PROPOSER_FLOP, "units_per_step": self.T}
+
+    def e2e(self, steps):
+        torch = self.torch
+        hX = self.X.cpu().pin_memory()
+        hY = torch.empty(self.T, 336).pin_memory()
+        dX = torch.empty_like(self.X)
+
+        def one():
+            dX.copy_(hX, non_blocking=True)
+            hY.copy_(self.p.forward(dX), non_blocking=True)
+        ms = timed_loop(torch, one, steps)
+        return ms, hX.numel() * 4, hY.numel() * 4
+
+
+def timed_loop(torch, fn, steps):
+    """CUDA-event time per call of fn on the current stream (after one untimed call)."""
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def count_launches(torch, fn):
+    """Kernels launched by one call of fn, from the CUDA activity trace: (ours, all)."""
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        torch.cuda.synchronize()
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
+        names = [e.name for e in prof.events() if e.device_type.name == "CUDA"]
+        kern = [n for n in names if not n.startswith(("Memcpy", "Memset", "[memory]"))]
+        ours = [n for n in kern if "leb::" in n]
+        return len(ours), len(kern), sorted(set(ours))
+    except Exception as e:  # profiler unavailable: no claim
+        return None, None, [f"profiler unavailable: {type(e).__name__}"]
 
 
 # ------------------------------------------------------------------------------------------------
 def reference_arm(args):
-    """The oracle as the reference arm, on the host cores, same metric/unit/config."""
+    """The FP64 oracle as the reference arm, on the host cores: the same step (pbh + crown timesteps
+    over the time of pbh, crown and the adjoint), each step a bounded sample of every form."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import torch  # noqa: F401  (keeps the import cost out of the timed region)
+    import torch
     from paper_2607_01203_b300 import inputs
-    from oracle import dynamics, pbh
-    w = inputs.quad_chain(n_traj=4, horizon=50)
-    dyn = dynamics.QuadChain(28, **w.params, spring_k=w.spring_k)
-    per_step = 8
-    times = []
+    from oracle import crown, dynamics, pbh
+    wq = inputs.quad_chain(n_traj=4, horizon=50)
+    dyn = dynamics.QuadChain(28, **wq.params, spring_k=wq.spring_k)
+    wm = inputs.tanh_mlp(n_traj=2, N=50)
+    g = np.random.default_rng(7).normal(size=(2, 168))
+    n_pbh, n_crown, n_bwd = 16, 2, 1
+    T_pbh, T_mlp = 12800, 6400
+    est = []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        for i in range(per_step):
-            t = (s * per_step + i) % w.T
-            a = w.nominal()[t].astype(np.float64)
-            lo, hi = pbh.box_from_set(a, G=w.G[t])
+        for i in range(n_pbh):
+            t = (s * n_pbh + i) % wq.T
+            a = wq.nominal()[t].astype(np.float64)
+            lo, hi = pbh.box_from_set(a, G=wq.G[t])
             pbh.pbh(dyn, a, lo, hi)
             dyn.jacobian(a)
+        t1 = time.perf_counter()
+        for i in range(n_crown):
+            t = (s * n_crown + i) % wm.T
+            crown.box_remainder(wm.Ws, wm.bs, wm.act, wm.x_nom[t], wm.u_nom[t], wm.radii[t], wm.residual)
+        t2 = time.perf_counter()
+        for i in range(n_bwd):
+            t = (s * n_bwd + i) % wm.T
+            crown.box_remainder_vjp(wm.Ws, wm.bs, wm.act, wm.x_nom[t], wm.u_nom[t], wm.radii[t], g[0], g[1],
+                                    wm.residual)
+        t3 = time.perf_counter()
         if s >= args.warmup:
-            times.append(time.perf_counter() - t0)
-    el = sum(times)
-    v = per_step * args.steps / el
+            # time the oracle would take for one full step of the same workload
+            est.append((t1 - t0) / n_pbh * T_pbh + (t2 - t1) / n_crown * T_mlp + (t3 - t2) / n_bwd * T_mlp)
+    step_s = statistics.mean(est)
+    v = (T_pbh + T_mlp) / step_s
+    cores = torch.get_num_threads()
+    sample = (f"per step {n_pbh} PBH timesteps (1 core), {n_crown} CROWN and {n_bwd} adjoint timesteps "
+              f"(torch, {cores} threads) of the bench workloads, scaled to a full step")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "quad-chain PBH (28 planar quadrotors, n_x=168, zonotope 224x336), "
-                                   "FP64 oracle on a sample of 8 timesteps per step", "parallelism": "host"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} timesteps per step of the 256x50 chain workload"},
+            "config": {"workload": "pbh 256x50 quad chain (zonotope) + crown 128x50 tanh MLP + adjoint, "
+                                   "FP64 oracle on a bounded sample per step", "parallelism": "host"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -229,11 +518,11 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--forms", default=",".join(FORMS))
-    ap.add_argument("--quick", action="store_true", help="small batch (smoke runs, not a bench value)")
+    ap.add_argument("--forms", default="pbh,crown,backward,proposer")
+    ap.add_argument("--quick", action="store_true", help="small batches (smoke runs, not a bench value)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -249,13 +538,35 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     pk = peaks()
-    forms = [FORMS[f](torch, dev, quick=args.quick) for f in args.forms.split(",") if f]
-    for f in forms:
-        f.kernel_events = []
-    for _ in range(args.warmup):
+    names = [f for f in args.forms.split(",") if f]
+    forms = []
+    crown = None
+    for nm in names:
+        if nm == "pbh":
+            forms.append(PbhForm(torch, dev, args.quick))
+        elif nm == "crown":
+            crown = CrownForm(torch, dev, args.quick)
+            forms.append(crown)
+        elif nm == "backward":
+            forms.append(BackwardForm(torch, dev, args.quick, crown))
+        elif nm == "proposer":
+            forms.append(ProposerForm(torch, dev, args.quick))
+        else:
+            raise SystemExit(f"unknown form {nm}")
+    handles = {id(f.handle): f.handle for f in forms if f.handle is not None}
+
+    def step():
         for f in forms:
             f.run()
+    for _ in range(args.warmup):
+        step()
     torch.cuda.synchronize()
+    # L2: without the pbh form nothing else streams > 126 MB per step, so a flush runs between steps
+    flush = None if "pbh" in names else torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    # per-form device time and main-kernel time, measured live on the launching (current) stream
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in forms]
+          for _ in range(args.steps)]
+    kern = {f.name: [0.0, 0, ""] for f in forms}
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -264,52 +575,105 @@ def main():
     time.sleep(0.3)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    for h in handles.values():
+        h.timing(True)
     e0.record()
-    for _ in range(args.steps):
-        for f in forms:
-            f.run(timed=True)
+    for k in range(args.steps):
+        for i, f in enumerate(forms):
+            ev[k][i][0].record()
+            f.run()
+            ev[k][i][1].record()
+        if flush is not None and k + 1 < args.steps:
+            flush.zero_()
     e1.record()
     torch.cuda.synchronize()
     clocks = sampler.stop()
     if world > 1:
         dist.barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([ms], device=dev)
+    form_ms = {f.name: statistics.mean(ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps))
+               for i, f in enumerate(forms)}
+    step_ms = sum(form_ms.values())
+    wall_ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([step_ms], device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
+    for h in handles.values():
+        h.timing(False)
+    # main-kernel times per step, from the event pairs recorded around their launches in the timed region
+    kt = {}
     for f in forms:
-        f.kernel_ms = [a.elapsed_time(b) for a, b in f.kernel_events]
+        if f.handle is not None:
+            ms, n, name = f.handle.timing_read(f.which)
+            kt[f.name] = (ms / args.steps, n // args.steps, name)
+        else:
+            kt[f.name] = (form_ms[f.name], 1, "proposer forward (prop_gemm_kernel x3 + elementwise)")
     units = sum(f.units() for f in forms) * world
     value = units / (ms_max * 1e-3)
-    dominant = max(forms, key=lambda f: statistics.mean(f.kernel_ms))
     out_forms = {}
+    roof = {}
     for f in forms:
-        out_forms[f.name] = {"timesteps": f.units(), "ms": round(statistics.mean(f.kernel_ms), 4),
-                             "value": f.units() / (statistics.mean(f.kernel_ms) * 1e-3), "roofline": f.roofline(pk)}
+        ms, n, name = kt[f.name]
+        roof[f.name] = f.roofline(pk, ms, n or 1, name)
+        d = {"ms": round(form_ms[f.name], 4), "units": f.units(), "workload": f.desc, "roofline": roof[f.name]}
+        if f.units():
+            d["value"] = round(f.units() / (form_ms[f.name] * 1e-3), 1)
+        if f.name == "backward":
+            d["us_per_call"] = round(1e3 * form_ms[f.name], 1)
+        if f.name == "proposer":
+            cms = f.certified_ms()
+            d.update({"proposal_error_vs_certified": round(f.err, 4), "under_cover_fraction": round(f.under, 4),
+                      "train_step_ms_batch256": round(f.train_ms_per_step, 4),
+                      "certified_pbh_box_ms_same_inputs": round(cms, 4),
+                      "speedup_vs_certified": round(cms / form_ms["proposer"], 3)})
+        out_forms[f.name] = d
+    # dominant kernel: the largest share of the step
+    dom = max(forms, key=lambda f: kt[f.name][0])
+    # end to end through the public API from pinned host memory
     e2e_ms, h2d, d2h = 0.0, 0, 0
     for f in forms:
-        m, a, b = f.e2e(max(2, min(5, args.steps)))
+        m, a, b = f.e2e(1 if f.name == "backward" else max(2, min(5, args.steps)))
         e2e_ms += m
         h2d += a
         d2h += b
+        out_forms[f.name]["e2e_ms"] = round(m, 4)
+    ours, allk, kn = count_launches(torch, step)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "+".join(f.name for f in forms) + (" (quick)" if args.quick else ""),
-                       "pbh": "28-quadrotor spring chain n_x=168 n_u=56, 256 traj x N=50, zonotope 224x336",
-                       "l2": "inputs larger than L2 (3.85 GB of generators per step)",
+                       **{f.name: f.desc for f in forms},
+                       "l2": ("each step streams the 3.85 GB of PBH generators, more than the 126 MB L2"
+                              if flush is None else "512 MB L2 flush between steps, outside the form timers"),
                        "parallelism": f"replicas x{world}"},
-            "roofline": dominant.roofline(pk), "forms": out_forms,
+            "roofline": roof[dom.name], "forms": out_forms,
             "e2e": {"value": units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps * sum(f.kernels_per_call for f in forms), "clocks": clocks}
+            "gpu_launches": None if ours is None else ours * args.steps,
+            "gpu_launches_detail": {"per_step_ours": ours, "per_step_all_kernels": allk, "kernels": kn},
+            "wall_ms_per_step": round(wall_ms, 3), "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = dominant.cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(forms, torch)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def cpu_baseline(forms, torch):
+    """The oracle as it stands on a bounded sample of each form, scaled to the step's metric."""
+    budget = {"pbh": 6.0, "crown": 6.0, "backward": 8.0}
+    step_s, units, parts = 0.0, 0, []
+    for f in forms:
+        if f.name not in budget:
+            continue
+        spu, n = f.oracle_seconds_per_unit(budget[f.name])
+        step_s += spu * f.T
+        units += f.units()
+        parts.append(f"{f.name}: {n} timesteps ({spu * 1e3:.1f} ms each)")
+    return {"value": units / step_s if step_s else None, "unit": UNIT,
+            "cores": f"pbh 1; crown/backward {torch.get_num_threads()} (torch threads)", "kind": "oracle",
+            "sample": "; ".join(parts) + " — scaled to one full step"}
 
 
 if __name__ == "__main__":

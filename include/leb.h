@@ -242,6 +242,18 @@ leb_status leb_selftest_point_enclosures(const float* x, int n, float* out_sin, 
 const char* leb_status_string(leb_status st);
 const char* leb_version(void);
 
+/* ---- measurement -------------------------------------------------------------------------------- */
+/* Event timing of the path's main kernels (no counterpart in the paper). While on, every launch of a
+ * main kernel of the handle (the PBH kernel for quad chains; the back-substitution chain kernels and
+ * the adjoint chain kernels for MLPs) is bracketed by a CUDA event pair on the stream it runs on and
+ * tagged with the entry point that launched it (0: leb_bounds, 1: leb_bounds_backward). Launches on a
+ * capturing stream are not recorded. leb_timing(h, 1) clears the records and starts recording;
+ * leb_timing(h, 0) stops. leb_timing_read waits for the recorded launches of entry point `which` (-1:
+ * all), returns their summed duration in ms, their count and the name of the last of them (kernel may be
+ * NULL); it keeps the records. Not thread-safe: one host thread per handle while timing. */
+leb_status leb_timing(leb_handle h, int on);
+leb_status leb_timing_read(leb_handle h, int which, double* ms, int* launches, char* kernel, size_t kernel_len);
+
 #ifdef __cplusplus
 }
 #endif

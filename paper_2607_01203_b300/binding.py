@@ -57,7 +57,7 @@ EXPORTS = [
     "leb_graph_capture", "leb_graph_launch", "leb_graph_destroy", "leb_proposer_create", "leb_proposer_destroy",
     "leb_proposer_set_norm", "leb_proposer_forward", "leb_proposer_train_step", "leb_proposer_workspace_size",
     "leb_proposer_get_layer", "leb_proposer_set_layer", "leb_proposer_get_grad", "leb_selftest_point_enclosures",
-    "leb_bounds_static", "leb_bounds_static_max_traj", "leb_proposer_fit_norm", "leb_proposer_set_periodic", "leb_status_string", "leb_version",
+    "leb_bounds_static", "leb_bounds_static_max_traj", "leb_proposer_fit_norm", "leb_proposer_set_periodic", "leb_timing", "leb_timing_read", "leb_status_string", "leb_version",
 ]
 
 
@@ -107,6 +107,8 @@ def lib():
         L.leb_bounds_static_max_traj.argtypes = []
         L.leb_proposer_fit_norm.argtypes = [vp, i32, vp, vp, vp]
         L.leb_proposer_set_periodic.argtypes = [vp, C.POINTER(i32)]
+        L.leb_timing.argtypes = [vp, i32]
+        L.leb_timing_read.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(i32), C.c_char_p, sz]
         _lib = L
     return _lib
 
@@ -168,6 +170,17 @@ class Handle:
         buf = C.create_string_buffer(512)
         check(lib().leb_plan_string(self.h, buf, 512), "leb_plan_string")
         return buf.value.decode()
+
+    def timing(self, on: bool):
+        """Event timing of the main kernel's launches (see leb_timing)."""
+        check(lib().leb_timing(self.h, int(bool(on))), "leb_timing")
+
+    def timing_read(self, which: int = -1):
+        """(summed ms, launches, last kernel name) of the timed launches of leb_bounds (which=0),
+        leb_bounds_backward (1) or both (-1) since timing was switched on."""
+        ms, n, name = C.c_double(), C.c_int(), C.create_string_buffer(64)
+        check(lib().leb_timing_read(self.h, int(which), C.byref(ms), C.byref(n), name, 64), "leb_timing_read")
+        return ms.value, n.value, name.value.decode()
 
     def plan_count(self) -> int:
         n = C.c_int()

@@ -428,6 +428,7 @@ static leb_status launch_chain_bwd(const Ctx& c, int T, int target, const MlpWs&
   a.grho = ws + L.grho;
   const size_t smem = bwd_chain_smem(c, target, nullptr);
   dim3 grid(T, (a.rows_total + kBwdRB - 1) / kBwdRB);
+  timer_begin(c, s, "mlp_chain_bwd_kernel");
   if (maxw <= 256) {
     cudaFuncSetAttribute(mlp_chain_bwd_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     mlp_chain_bwd_kernel<1><<<grid, 256, smem, s>>>(a);
@@ -438,6 +439,7 @@ static leb_status launch_chain_bwd(const Ctx& c, int T, int target, const MlpWs&
     cudaFuncSetAttribute(mlp_chain_bwd_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     mlp_chain_bwd_kernel<4><<<grid, 256, smem, s>>>(a);
   }
+  timer_end(c, s);
   return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
 }
 

@@ -601,7 +601,9 @@ leb_status tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, 
   const int items = T * a.tiles_per_t;
   const int grid = items < c.sm_count ? items : c.sm_count;
   if (grid == 0) return LEB_OK;
+  timer_begin(c, s, "crown_tc_kernel");
   crown_tc_kernel<<<grid, kTcThreads, kTcSmem, s>>>(a);
+  timer_end(c, s);
   return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
 }
 

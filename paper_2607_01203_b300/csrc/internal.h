@@ -97,6 +97,17 @@ struct MlpWs {
   int hoff[kMaxLayers];     // offset of hidden layer i (0-based) inside H
 };
 
+// Optional event timing of the path's main kernel (leb_timing / leb_timing_read): an event pair per
+// recorded launch, on the launching stream.
+struct KernelTimer {
+  bool on = false;
+  int phase = 0;                    // entry point being run: 0 leb_bounds, 1 leb_bounds_backward
+  std::vector<cudaEvent_t> ev;      // start/stop pairs, reused after a reset
+  std::vector<int> rec_phase;       // per recorded pair
+  std::vector<std::string> rec_name;
+  int used = 0;                     // pairs recorded since the last reset
+};
+
 struct Ctx {
   leb_dyn_kind kind;
   int n_x = 0, n_u = 0;
@@ -111,7 +122,12 @@ struct Ctx {
   int sm_count = 148;
   int device = 0;
   std::string plan_note;
+  mutable KernelTimer timer;
 };
+
+// Record the start / stop event of a timed launch (no-ops when timing is off or the stream captures).
+void timer_begin(const Ctx& c, cudaStream_t s, const char* kernel);
+void timer_end(const Ctx& c, cudaStream_t s);
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_pbh(const Ctx& c, const PbhArgs& a, const PbhPlan& p, cudaStream_t s);

@@ -51,7 +51,75 @@ void default_pbh_candidates(Ctx& c) {
 
 }  // namespace
 
+namespace leb {
+
+static bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &st) != cudaSuccess || st != cudaStreamCaptureStatusNone;
+}
+
+void timer_begin(const Ctx& c, cudaStream_t s, const char* kernel) {
+  KernelTimer& t = c.timer;
+  if (!t.on || capturing(s)) return;
+  if ((size_t)(2 * t.used + 2) > t.ev.size()) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess) return;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return;
+    }
+    t.ev.push_back(a);
+    t.ev.push_back(b);
+    t.rec_phase.push_back(0);
+    t.rec_name.emplace_back();
+  }
+  t.rec_phase[t.used] = t.phase;
+  t.rec_name[t.used] = kernel;
+  cudaEventRecord(t.ev[2 * t.used], s);
+}
+
+void timer_end(const Ctx& c, cudaStream_t s) {
+  KernelTimer& t = c.timer;
+  if (!t.on || capturing(s) || (size_t)(2 * t.used + 2) > t.ev.size()) return;
+  cudaEventRecord(t.ev[2 * t.used + 1], s);
+  ++t.used;
+}
+
+}  // namespace leb
+
 extern "C" {
+
+
+leb_status leb_timing(leb_handle h, int on) {
+  if (!h) return LEB_ERR_INVALID_ARG;
+  if (on) h->timer.used = 0;
+  h->timer.on = on != 0;
+  return LEB_OK;
+}
+
+leb_status leb_timing_read(leb_handle h, int which, double* ms, int* launches, char* kernel, size_t kernel_len) {
+  if (!h || !ms || !launches || which < -1 || which > 1) return LEB_ERR_INVALID_ARG;
+  KernelTimer& t = h->timer;
+  double total = 0.0;
+  int n = 0;
+  const char* name = "";
+  for (int i = 0; i < t.used; ++i) {
+    if (which >= 0 && t.rec_phase[i] != which) continue;
+    if (cudaEventSynchronize(t.ev[2 * i + 1]) != cudaSuccess) return LEB_ERR_CUDA;
+    float e = 0.f;
+    if (cudaEventElapsedTime(&e, t.ev[2 * i], t.ev[2 * i + 1]) != cudaSuccess) return LEB_ERR_CUDA;
+    total += e;
+    ++n;
+    name = t.rec_name[i].c_str();
+  }
+  *ms = total;
+  *launches = n;
+  if (kernel && kernel_len) {
+    std::strncpy(kernel, name, kernel_len - 1);
+    kernel[kernel_len - 1] = 0;
+  }
+  return LEB_OK;
+}
 
 const char* leb_version(void) { return "leb-b300 0.1 (sm_103a)"; }
 
@@ -170,6 +238,7 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
                       const leb_set* set, float* r_lo, float* r_hi, float* A, float* B, const leb_options* opt,
                       void* workspace, size_t ws_bytes, int* dev_flags, void* stream) {
   if (!h || !set || T < 0 || !dev_flags) return LEB_ERR_INVALID_ARG;
+  h->timer.phase = 0;
   if (T > 0 && (!x_nom || !u_nom || !r_lo || !r_hi)) return LEB_ERR_INVALID_ARG;
   if (set->kind != LEB_SET_BOX && set->kind != LEB_SET_ZONO) return LEB_ERR_INVALID_ARG;
   if (T > 0 && set->kind == LEB_SET_BOX && !set->radii) return LEB_ERR_INVALID_ARG;
@@ -222,7 +291,10 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
     const PbhPlan& p = (h->plan_index >= 0 && h->plan_index < (int)h->pbh_candidates.size())
                            ? h->pbh_candidates[h->plan_index]
                            : h->pbh_plan;
-    if (launch_pbh(*h, a, p, s) != cudaSuccess) return LEB_ERR_CUDA;
+    timer_begin(*h, s, a.zono ? "pbh_zonotope" : "pbh_box");
+    const cudaError_t e = launch_pbh(*h, a, p, s);
+    timer_end(*h, s);
+    if (e != cudaSuccess) return LEB_ERR_CUDA;
     return LEB_OK;
   }
   // MLP dynamics
@@ -237,6 +309,7 @@ leb_status leb_bounds_backward(leb_handle h, int T, const float* x_nom, const fl
                                const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_radii,
                                void* workspace, size_t ws_bytes, int* dev_flags, void* stream) {
   if (!h || !set || T < 0 || !dev_flags) return LEB_ERR_INVALID_ARG;
+  h->timer.phase = 1;
   if (h->kind != LEB_DYN_MLP) return LEB_ERR_UNSUPPORTED;
   if (set->kind != LEB_SET_BOX || set->center) return LEB_ERR_UNSUPPORTED;
   if (T > 0 && (!x_nom || !u_nom || !set->radii || !g_rlo || !g_rhi || !g_x || !g_u || !g_radii))

@@ -652,11 +652,13 @@ static int pick_cg(int maxw) { return maxw <= 256 ? 1 : (maxw <= 512 ? 2 : 4); }
 leb_status launch_simt_chain(const Ctx& c, const ChainArgs& a, cudaStream_t s) {
   const size_t smem = simt_chain_smem(a.maxw);
   dim3 grid(a.T, (a.rows_total + a.RB - 1) / a.RB);
+  timer_begin(c, s, "mlp_chain_simt_kernel");
   switch (pick_cg(a.maxw)) {
     case 1: mlp_chain_simt_kernel<1><<<grid, 256, smem, s>>>(a); break;
     case 2: mlp_chain_simt_kernel<2><<<grid, 256, smem, s>>>(a); break;
     default: mlp_chain_simt_kernel<4><<<grid, 256, smem, s>>>(a); break;
   }
+  timer_end(c, s);
   return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
 }
 
