@@ -447,10 +447,15 @@ leb_status mlp_bounds_backward(Ctx& c, int T, const float* x_nom, const float* u
                                const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_rad, void* ws_base,
                                int* flags, cudaStream_t s) {
   const MlpModel& m = c.mlp;
+  // reduced-precision handles with a tensor-core adjoint: chains on the tensor cores, and the hidden
+  // bounds recomputed by the tensor-core chains without their rounding inflation, i.e. the algorithm's
+  // bounds up to operand rounding (the inflation is a constant slack for the derivative); otherwise
+  // everything on CUDA cores in FP32
+  const bool tc = m.adj != nullptr;
   int stot = 0;
-  if (bwd_chain_smem(c, m.L - 1, &stot) > 227 * 1024) return LEB_ERR_UNSUPPORTED;
-  // 1. forward recompute on CUDA cores (every hidden layer's bounds and lines)
-  leb_status st = mlp_forward_hidden(c, T, x_nom, u_nom, set, ws_base, flags, s, true, nullptr);
+  if (!tc && bwd_chain_smem(c, m.L - 1, &stot) > 227 * 1024) return LEB_ERR_UNSUPPORTED;
+  // 1. forward recompute (every hidden layer's bounds and lines)
+  leb_status st = mlp_forward_hidden(c, T, x_nom, u_nom, set, ws_base, flags, s, !tc, nullptr, tc);
   if (st != LEB_OK) return st;
   MlpWs L;
   mlp_workspace_floats(c, T, &L);
@@ -460,8 +465,12 @@ leb_status mlp_bounds_backward(Ctx& c, int T, const float* x_nom, const float* u
   for (size_t off : {L.gsL, L.gsU, L.gtL, L.gtU, L.gD, L.gz, L.gl, L.gu})
     if (cudaMemsetAsync(ws + off, 0, TH * sizeof(float), s) != cudaSuccess) return LEB_ERR_CUDA;
   if (cudaMemsetAsync(ws + L.grho, 0, (size_t)T * n * sizeof(float), s) != cudaSuccess) return LEB_ERR_CUDA;
+  auto chain = [&](int target, const float* glo, const float* ghi) {
+    return tc ? adj_tc_chain(c, T, target, L, ws, set->radii, glo, ghi, flags, s)
+              : launch_chain_bwd(c, T, target, L, ws, set->radii, glo, ghi, s);
+  };
   // 2. output chains
-  st = launch_chain_bwd(c, T, m.L - 1, L, ws, set->radii, g_rlo, g_rhi, s);
+  st = chain(m.L - 1, g_rlo, g_rhi);
   if (st != LEB_OK) return st;
   // 3. hidden layers top-down
   for (int i = m.L - 2; i >= 0; --i) {
@@ -472,7 +481,7 @@ leb_status mlp_bounds_backward(Ctx& c, int T, const float* x_nom, const float* u
                                                 ws + L.gu, ws + L.gz);
     if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
     if (i > 0) {
-      st = launch_chain_bwd(c, T, i, L, ws, set->radii, nullptr, nullptr, s);
+      st = chain(i, nullptr, nullptr);
       if (st != LEB_OK) return st;
     } else {
       // layer 0: l = z~ - |W_0| rho, u = z~ + |W_0| rho  ->  d rho += |W_0|^T (g_u - g_l)

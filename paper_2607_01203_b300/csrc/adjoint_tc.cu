@@ -1,0 +1,631 @@
+// Adjoint of the CROWN remainder bound (differentiable LEBs, Sec. III-D) on the tensor cores: the chain
+// part of the reverse pass for reduced-precision (FP16 / BF16) handles.
+//
+// For one back-substitution target (the output rows, or the lower/upper rows of hidden layer `target`)
+// and 128 chain rows of one timestep, a CTA
+//   1. recomputes the chain forward:  lambda_{k-1} = (lambda_k o s_k) W_k,  k = target-1 .. 0,
+//      starting from lambda_{target-1} = rows of W_target, keeping each lambda_k (k >= 0) in a per-CTA
+//      scratch area (it stays in L2);
+//   2. forms G_{-1} = dr / d lambda_{-1} from -|M| rho (lower) and +|M| rho (upper), M = lambda_{-1}
+//      minus the Jacobian row of the same state for output rows, and the direct radius gradient;
+//   3. runs the chain backward:  Ga_k = G_{k-1} W_k^T,  G_k = Ga_k o s_k + g tau_k,  summing per neuron
+//      over the chain rows d/ds_sel += Ga_k lambda_k, d/dtau_sel += g lambda_k (lower/upper rows) and
+//      d/dD += Ga_k lambda_k (Jacobian rows).
+// The slopes are those of the relaxation case selected at the evaluation point (sign of lambda_k), as
+// automatic differentiation of the same algorithm would take them.
+//
+// Layout (transposed with respect to the forward chain kernel): the products are computed as
+//   lambda_{k-1}^T = W_k^T (lambda_k o s_k)^T   and   Ga_k^T = W_k G_{k-1}^T,
+// so the weights are the streamed A operand (128 neurons x 64 K tiles by TMA, a ring of kAdjStages) and
+// the per-row operand is the resident B operand (128 rows x K, K-major, 128-byte swizzle). TMEM holds
+// D[neuron][row]: lane = neuron inside an M-tile of 128, column = 128 * M-tile + row. Every epilogue
+// thread owns one neuron, so every sum over chain rows is a register sum, and the role of a row (lower,
+// upper, Jacobian) is the same across a warp.
+//
+// Output rows are carried in difference form: the lower and upper rows hold delta = lambda - lambda^J
+// (their operand lambda o s_sel - lambda^J o sigma'(z~) is formed in FP32 from the row and the Jacobian
+// row of the same state, which sit in the same thread), so M = delta_{-1} comes out of the tensor cores
+// with the operand format's relative precision instead of as a difference of two rounded chains, whose
+// cancellation would flip sign(M) wherever the relaxation slopes are close to sigma'(z~).
+//
+// G is scaled by 1 / max |g| of the tile's rows before it is rounded to the operand format (so FP16 does
+// not overflow for large cotangents); the sums are scaled back when they are added to global memory.
+#include <cmath>
+#include <cstdio>
+#include <type_traits>
+
+#include "internal.h"
+#include "tc_ptx.cuh"
+
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+namespace leb {
+
+constexpr int kAdjEpiWarps = 16;                    // 4 M-tiles x 4 TMEM lane quarters
+constexpr int kAdjThreads = 32 * (2 + kAdjEpiWarps);
+constexpr int kAdjStages = 6;                       // weight-tile ring
+constexpr int kAdjATile = 128 * 64 * 2;             // 128 neurons x 64 K x 2 bytes
+constexpr int kAdjBRegion = 128 * 512 * 2;          // 128 rows x K <= 512 x 2 bytes
+constexpr int kAdjSmall = 1024 + 32 + 256 + 512 + 16 * 8;   // row data and barriers
+constexpr int kAdjSmem = 1024 + kAdjBRegion + kAdjStages * kAdjATile + kAdjSmall;
+static_assert(kAdjSmem <= 227 * 1024, "adjoint tensor-core shared memory");
+
+struct AdjTcArgs {
+  CUtensorMap fwd[kMaxLayers];   // W_k^T [widths[k] rows, widths[k+1] cols] (operand format), box {64, 128}
+  CUtensorMap bwd[kMaxLayers];   // W_k   [widths[k+1] rows, widths[k] cols] (operand format), box {64, 128}
+  int L;
+  int widths[kMaxLayers + 1];
+  int fmt;                       // 0 FP16, 1 BF16
+  int T, target, nroles, rows_total, rows_per_tile, tiles_per_t;
+  int H;
+  int hoff[kMaxLayers];
+  int soff[kMaxLayers];          // scratch offset (in neurons) of lambda_k, k = 0 .. target-2
+  int stot;                      // neurons per CTA scratch row block
+  const float* W_target;         // FP32 [widths[target+1], widths[target]]
+  const float *sL, *sU, *tL, *tU, *D;   // [T, H]
+  const float* radii;            // [T, n]
+  const float *g_lo, *g_hi;      // output target: [T, n_x]
+  const float *gl, *gu;          // hidden target: [T, H]
+  float *gsL, *gsU, *gtL, *gtU, *gD, *grho;
+  float* scratch;                // gridDim.x x stot x 128 floats
+  int* flags;
+};
+
+__device__ __forceinline__ uint16_t op_round(float x, int fmt) {
+  if (fmt == 0) return __half_as_ushort(__float2half_rn(x));
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+// Byte offset of element (row r, column j) in the K-major, 128-byte-swizzled B operand: 64-column blocks
+// of 128 rows x 128 bytes; the 16-byte chunk index inside a row is XORed with r mod 8.
+__device__ __forceinline__ uint32_t b_off(int r, int j) {
+  return (uint32_t)((j >> 6) * 16384 + r * 128 + ((((j & 63) >> 3) ^ (r & 7)) << 4) + ((j & 7) << 1));
+}
+
+__global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid_constant__ AdjTcArgs a) {
+  extern __shared__ uint8_t sraw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sraw) + 1023) & ~uintptr_t(1023));
+  uint8_t* Bop = base;                                   // per-row operand
+  uint8_t* ring = base + kAdjBRegion;                    // weight tiles
+  float* gws = reinterpret_cast<float*>(ring + kAdjStages * kAdjATile);   // [2][128] row cotangents
+  float* wmax = gws + 256;                                                 // [2][4] per-warp max |g|
+  uint8_t* roles = reinterpret_cast<uint8_t*>(wmax + 8);                   // [2][128] role, 3 = no row
+  int16_t* idxs = reinterpret_cast<int16_t*>(roles + 256);                 // [2][128] state / neuron index
+  uint64_t* bars = reinterpret_cast<uint64_t*>(idxs + 256);
+  uint64_t* full = bars;                      // [kAdjStages]
+  uint64_t* empty = bars + kAdjStages;        // [kAdjStages]
+  uint64_t* a_full = bars + 2 * kAdjStages;   // operand written by the epilogue
+  uint64_t* acc_full = a_full + 1;            // accumulators complete
+  uint64_t* drain = acc_full + 1;
+  uint64_t* ebar = drain + 1;                 // epilogue-warps barrier
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_items = a.T * a.tiles_per_t;
+  const int target = a.target;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kAdjStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(a_full, kAdjEpiWarps);
+    mbar_init(acc_full, 1);
+    mbar_init(drain, 1);
+    mbar_init(ebar, kAdjEpiWarps);
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  if (warp == 1) tmem_alloc(&tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  // stage s of an item: s < target: forward stage k = target-1-s; else backward stage k = s - target
+  const int n_stages = 2 * target;
+  auto stage_shape = [&](int s, int& M, int& K, const CUtensorMap*& map) {
+    if (s < target) {
+      const int k = target - 1 - s;
+      M = a.widths[k];
+      K = a.widths[k + 1];
+      map = &a.fwd[k];
+    } else {
+      const int k = s - target;
+      M = a.widths[k + 1];
+      K = a.widths[k];
+      map = &a.bwd[k];
+    }
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------------ TMA producer (weight tiles)
+    if (lane == 0) {
+      for (int k = 0; k < target; ++k) {
+        tma_prefetch_desc(&a.fwd[k]);
+        tma_prefetch_desc(&a.bwd[k]);
+      }
+      uint32_t kb = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+        for (int s = 0; s < n_stages && ok; ++s) {
+          int M, K;
+          const CUtensorMap* map;
+          stage_shape(s, M, K, map);
+          const int nM = (M + 127) / 128, nK = (K + 63) / 64;
+          for (int kc = 0; kc < nK && ok; ++kc)
+            for (int c = 0; c < nM; ++c, ++kb) {
+              const int slot = (int)(kb % kAdjStages);
+              if (kb >= (uint32_t)kAdjStages && !mbar_wait(&empty[slot], ((kb / kAdjStages) - 1) & 1u)) {
+                ok = false;
+                break;
+              }
+              if (*(volatile int*)&s_abort) { ok = false; break; }
+              mbar_arrive_expect_tx(&full[slot], (uint32_t)kAdjATile);
+              tma_load_2d(ring + (size_t)slot * kAdjATile, map, kc * 64, c * 128, &full[slot]);
+            }
+        }
+      }
+      if (!ok) {
+        s_abort = 1;
+        atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
+      }
+      // every issued load must land before the block exits
+      for (uint32_t j = (kb > (uint32_t)kAdjStages ? kb - kAdjStages : 0u); j < kb; ++j)
+        mbar_wait(&full[j % kAdjStages], (j / kAdjStages) & 1u);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t ring_base = smem_u32(ring), b_base = smem_u32(Bop);
+      const uint32_t idesc = idesc_f16(128, 128, a.fmt);
+      uint32_t kb = 0, na = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+        for (int s = 0; s < n_stages && ok; ++s) {
+          int M, K;
+          const CUtensorMap* map;
+          stage_shape(s, M, K, map);
+          const int nM = (M + 127) / 128, nK = (K + 63) / 64;
+          if (!mbar_wait(a_full, na & 1u)) { ok = false; break; }
+          ++na;
+          tc_fence_after();
+          for (int kc = 0; kc < nK && ok; ++kc)
+            for (int c = 0; c < nM; ++c, ++kb) {
+              const int slot = (int)(kb % kAdjStages);
+              if (!mbar_wait(&full[slot], (kb / kAdjStages) & 1u)) { ok = false; break; }
+              tc_fence_after();
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t ad = sw128_desc(ring_base + slot * kAdjATile + kk * 32);
+                const uint64_t bd = sw128_desc(b_base + kc * 16384 + kk * 32);
+                tc_mma_f16(tmem + (uint32_t)(c * 128), ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+              }
+              tc_commit(&empty[slot]);
+            }
+          tc_commit(acc_full);
+        }
+      }
+      if (!ok) {
+        s_abort = 1;
+        atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
+      }
+      tc_commit(drain);
+      mbar_wait(drain, 0);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------------ epilogue warps
+    const int q = warp & 3;                    // TMEM lane quarter
+    const int mt = (warp - 2) >> 2;            // M-tile: neurons 128 mt .. 128 mt + 127
+    const int nrn = mt * 128 + q * 32 + lane;  // the neuron this thread owns (and the TMEM lane)
+    const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * 128);
+    const int etid = threadIdx.x - 64;
+    float* scr = a.scratch + (size_t)blockIdx.x * a.stot * 128;
+    const int n = a.widths[0];
+    const bool output = target == a.L - 1;
+    uint32_t nacc = 0, nbar = 0;
+    int gb = 0;
+    bool ok = true;
+    auto epi_sync = [&]() -> bool {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(ebar);
+      const bool res = mbar_wait(ebar, nbar & 1u);
+      ++nbar;
+      return res;
+    };
+    auto operand_ready = [&]() {
+      tc_fence_before();
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(a_full);
+    };
+    auto wait_acc = [&]() -> bool {
+      if (!mbar_wait(acc_full, nacc & 1u)) return false;
+      ++nacc;
+      tc_fence_after();
+      return true;
+    };
+
+    for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+      const int t = item / a.tiles_per_t, tile = item - t * a.tiles_per_t;
+      const int row0 = tile * a.rows_per_tile;
+      const int nrows = min(a.rows_per_tile, a.rows_total - row0);   // valid rows of this tile
+      // ---- row cotangents of the tile and their scale ---------------------------------------------
+      float* gw = gws + gb * 128;
+      const uint8_t* rrole = roles + gb * 128;
+      const int16_t* ridx = idxs + gb * 128;
+      if (etid < 128) {
+        float g = 0.f;
+        int role = 3, idx = 0;
+        if (etid < nrows) {
+          const int grow = row0 + etid;
+          role = grow % a.nroles;
+          idx = grow / a.nroles;
+          if (output) {
+            const int nx = a.widths[a.L];
+            g = role == 0 ? a.g_lo[(long long)t * nx + idx] : (role == 1 ? a.g_hi[(long long)t * nx + idx] : 0.f);
+          } else {
+            const long long o = (long long)t * a.H + a.hoff[target] + idx;
+            g = role == 0 ? a.gl[o] : a.gu[o];
+          }
+        }
+        gw[etid] = g;
+        roles[gb * 128 + etid] = (uint8_t)role;
+        idxs[gb * 128 + etid] = (int16_t)idx;
+        float m = fabsf(g);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
+        if (lane == 0) wmax[gb * 4 + (etid >> 5)] = m;
+      }
+      if (!epi_sync()) { ok = false; break; }
+      float gmax = fmaxf(fmaxf(wmax[gb * 4], wmax[gb * 4 + 1]), fmaxf(wmax[gb * 4 + 2], wmax[gb * 4 + 3]));
+      const float gscale = (gmax > 0.f && isfinite(gmax)) ? gmax : 1.f;
+      const float ginv = 1.f / gscale;
+      gb ^= 1;
+
+      // ---- prologue: B = (W_target rows o s_{target-1}) for neurons j < widths[target] ----------------
+      {
+        const int K = a.widths[target], Kp = (K + 63) & ~63;
+        if (nrn < Kp) {
+          const bool live = nrn < K;
+          const long long o = (long long)t * a.H + a.hoff[target - 1] + nrn;
+          const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f, dd = live ? a.D[o] : 0.f;
+          for (int r = 0; r < 128; ++r) {
+            float v = 0.f;
+            const int role = rrole[r];
+            if (live && role != 3) {
+              const float lam = __ldg(a.W_target + (long long)ridx[r] * K + nrn);
+              if (role == 2) {
+                v = lam * dd;
+              } else {
+                const float sv = ((role == 0) == (lam >= 0.f)) ? sl : su;
+                v = output ? fmaf(lam, sv, -lam * dd) : lam * sv;   // delta = 0 at the start of the chain
+              }
+            }
+            *reinterpret_cast<uint16_t*>(Bop + b_off(r, nrn)) = op_round(v, a.fmt);
+          }
+        }
+        operand_ready();
+      }
+      // ---- forward stages k = target-1 .. 1: lambda_{k-1} -> scratch, next operand ------------------
+      // rows in whole groups: (lower, upper, Jacobian) triples of output rows, (lower, upper) pairs
+      auto fwd_stage = [&](auto nr_c, int k) {
+        constexpr int nr = decltype(nr_c)::value, gsize = 16 * nr;
+        const int N = a.widths[k];             // neurons of hidden layer k-1 (rows of this product)
+        const int Np = (N + 63) & ~63;
+        if (!(nrn < Np && mt * 128 < N)) return;
+        const bool live = nrn < N;
+        const long long o = (long long)t * a.H + a.hoff[k - 1] + (live ? nrn : 0);
+        const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f, dd = live ? a.D[o] : 0.f;
+        float* lrow = scr + (size_t)(a.soff[k - 1] + (live ? nrn : 0)) * 128;
+        for (int r0 = 0; r0 < 128; r0 += gsize) {
+          const int nch = min(nr, (128 - r0) >> 4);   // 16-column TMEM chunks inside the tile's 128 rows
+          float d[gsize], lam[gsize];
+#pragma unroll
+          for (int h = 0; h < nr; ++h) {
+            if (h < nch) tmem_ld16(t_lane + (uint32_t)(r0 + 16 * h), d + 16 * h);
+            else
+#pragma unroll
+              for (int e = 0; e < 16; ++e) d[16 * h + e] = 0.f;
+          }
+#pragma unroll
+          for (int e = 0; e < gsize; e += nr) {
+            const int r = r0 + e;
+            float v[nr];
+            const bool row_ok = live && r < 128 && rrole[r] != 3;
+            if (nr == 3) {
+              const float lj = d[e + 2], ll = d[e] + lj, lu = d[e + 1] + lj;
+              lam[e] = ll;
+              lam[e + 1] = lu;
+              lam[e + nr - 1] = lj;
+              const float jd = lj * dd;
+              v[0] = row_ok ? fmaf(ll, ll >= 0.f ? sl : su, -jd) : 0.f;
+              v[1] = row_ok ? fmaf(lu, lu >= 0.f ? su : sl, -jd) : 0.f;
+              v[nr - 1] = row_ok ? jd : 0.f;
+            } else {
+              lam[e] = d[e];
+              lam[e + 1] = d[e + 1];
+              v[0] = row_ok ? d[e] * (d[e] >= 0.f ? sl : su) : 0.f;
+              v[1] = row_ok ? d[e + 1] * (d[e + 1] >= 0.f ? su : sl) : 0.f;
+            }
+#pragma unroll
+            for (int p = 0; p < nr; ++p)
+              if (r + p < 128) *reinterpret_cast<uint16_t*>(Bop + b_off(r + p, nrn)) = op_round(v[p], a.fmt);
+          }
+          if (live)
+#pragma unroll
+            for (int e = 0; e < gsize; e += 4)
+              if (e < 16 * nch)
+                *reinterpret_cast<float4*>(lrow + r0 + e) = make_float4(lam[e], lam[e + 1], lam[e + 2], lam[e + 3]);
+        }
+      };
+      for (int k = target - 1; k >= 1 && ok; --k) {
+        if (!wait_acc()) { ok = false; break; }
+        if (output) fwd_stage(std::integral_constant<int, 3>(), k);
+        else fwd_stage(std::integral_constant<int, 2>(), k);
+        operand_ready();
+      }
+      if (!ok) break;
+      // ---- G_{-1} from lambda_{-1} (TMEM, neurons = inputs m < n) -----------------------------------
+      {
+        if (!wait_acc()) { ok = false; break; }
+        const int np = (n + 63) & ~63;
+        if (mt * 128 < np) {
+          const bool live = nrn < n;
+          const float rho = live ? a.radii[(long long)t * n + nrn] : 0.f;
+          float grho = 0.f;
+          // whole (lower, upper, Jacobian) triples or (lower, upper) pairs per group of TMEM columns
+          auto group = [&](auto nr_c) {
+            constexpr int nr = decltype(nr_c)::value, gsize = 16 * nr;
+            for (int r0 = 0; r0 < 128; r0 += gsize) {
+              const int nch = min(nr, (128 - r0) >> 4);
+              float lam[gsize];
+#pragma unroll
+              for (int h = 0; h < nr; ++h) {
+                if (h < nch) tmem_ld16(t_lane + (uint32_t)(r0 + 16 * h), lam + 16 * h);
+                else
+#pragma unroll
+                  for (int e = 0; e < 16; ++e) lam[16 * h + e] = 0.f;
+              }
+#pragma unroll
+              for (int e = 0; e < gsize; e += nr) {
+                const int r = r0 + e;
+                float G0 = 0.f, G1 = 0.f;
+                if (live && r + nr - 1 < nrows) {
+                  const float glo = gw[r] * ginv, ghi = gw[r + 1] * ginv;
+                  const float mlo = lam[e], mhi = lam[e + 1];   // output rows: delta = lambda - lambda^J
+                  const float sgl = mlo > 0.f ? 1.f : (mlo < 0.f ? -1.f : 0.f);
+                  const float sgh = mhi > 0.f ? 1.f : (mhi < 0.f ? -1.f : 0.f);
+                  G0 = -glo * sgl * rho;
+                  G1 = ghi * sgh * rho;
+                  grho += ghi * fabsf(mhi) - glo * fabsf(mlo);
+                }
+                if (r < 128) *reinterpret_cast<uint16_t*>(Bop + b_off(r, nrn)) = op_round(G0, a.fmt);
+                if (r + 1 < 128) *reinterpret_cast<uint16_t*>(Bop + b_off(r + 1, nrn)) = op_round(G1, a.fmt);
+                if (nr == 3 && r + 2 < 128)
+                  *reinterpret_cast<uint16_t*>(Bop + b_off(r + 2, nrn)) = op_round(-(G0 + G1), a.fmt);
+              }
+            }
+          };
+          if (output) group(std::integral_constant<int, 3>());
+          else group(std::integral_constant<int, 2>());
+          if (live && grho != 0.f) atomicAdd(a.grho + (long long)t * n + nrn, grho * gscale);
+        }
+        operand_ready();
+      }
+      // ---- backward stages k = 0 .. target-1 -------------------------------------------------------
+      for (int k = 0; k < target && ok; ++k) {
+        if (!wait_acc()) { ok = false; break; }
+        const int N = a.widths[k + 1];            // neurons of hidden layer k
+        const bool last = k == target - 1;
+        const int Np = (N + 63) & ~63;
+        if (nrn < Np && mt * 128 < N) {
+          const bool live = nrn < N;
+          const long long o = (long long)t * a.H + a.hoff[k] + (live ? nrn : 0);
+          const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f;
+          const float tl = live ? a.tL[o] : 0.f, tu = live ? a.tU[o] : 0.f, dd = live ? a.D[o] : 0.f;
+          const float* lrow = last ? nullptr : scr + (size_t)(a.soff[k] + (live ? nrn : 0)) * 128;
+          float gsl = 0.f, gsu = 0.f, gtl = 0.f, gtu = 0.f, gd = 0.f;
+          for (int r0 = 0; r0 < 128; r0 += 16) {
+            float ga[16], lam[16];
+            tmem_ld16(t_lane + (uint32_t)r0, ga);
+            if (!last && live) {
+#pragma unroll
+              for (int e = 0; e < 16; e += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(lrow + r0 + e);
+                lam[e] = v.x; lam[e + 1] = v.y; lam[e + 2] = v.z; lam[e + 3] = v.w;
+              }
+            }
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const int r = r0 + e;
+              float G = 0.f;
+              const int role = rrole[r];
+              if (live && role != 3) {
+                const float l = last ? __ldg(a.W_target + (long long)ridx[r] * a.widths[target] + nrn) : lam[e];
+                if (role == 2) {
+                  gd = fmaf(ga[e], l, gd);
+                  G = ga[e] * dd;
+                } else {
+                  const float g = gw[r] * ginv;
+                  if ((role == 0) == (l >= 0.f)) {
+                    gsl = fmaf(ga[e], l, gsl);
+                    gtl = fmaf(g, l, gtl);
+                    G = fmaf(ga[e], sl, g * tl);
+                  } else {
+                    gsu = fmaf(ga[e], l, gsu);
+                    gtu = fmaf(g, l, gtu);
+                    G = fmaf(ga[e], su, g * tu);
+                  }
+                }
+              }
+              if (!last) *reinterpret_cast<uint16_t*>(Bop + b_off(r, nrn)) = op_round(G, a.fmt);
+            }
+          }
+          if (live) {
+            if (gsl != 0.f) atomicAdd(a.gsL + o, gsl * gscale);
+            if (gsu != 0.f) atomicAdd(a.gsU + o, gsu * gscale);
+            if (gtl != 0.f) atomicAdd(a.gtL + o, gtl * gscale);
+            if (gtu != 0.f) atomicAdd(a.gtU + o, gtu * gscale);
+            if (gd != 0.f) atomicAdd(a.gD + o, gd * gscale);
+          }
+        }
+        if (!last) operand_ready();
+      }
+      if (!ok) break;
+      tc_fence_before();
+      if (*(volatile int*)&s_abort) ok = false;
+    }
+    if (!ok) {
+      s_abort = 1;
+      if (lane == 0) atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, 512);
+}
+
+// ---------------------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------------------
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 adj_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+__global__ void round_copy_kernel(const float* W, long long count, uint16_t* out, int fmt) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count; e += (long long)gridDim.x * blockDim.x)
+    out[e] = op_round(W[e], fmt);
+}
+
+struct AdjState {
+  uint16_t* W[kMaxLayers] = {};   // W_k rounded to the operand format, row-major [widths[k+1], widths[k]]
+  CUtensorMap fwd[kMaxLayers];
+  CUtensorMap bwd[kMaxLayers];
+};
+
+bool encode(CUtensorMap* map, const void* ptr, int rows, int cols, int fmt) {
+  auto enc = adj_encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {64, 128};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(map, fmt == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+             const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+leb_status adj_tc_prepare(Ctx& c) {
+  MlpModel& m = c.mlp;
+  if (!m.tc || m.L < 2) return LEB_ERR_UNSUPPORTED;
+  for (int i = 0; i < m.L; ++i)
+    if (m.widths[i] > 512 || m.widths[i] % 32 != 0) return LEB_ERR_UNSUPPORTED;
+  const int fmt = m.prec == LEB_PREC_BF16 ? 1 : 0;
+  AdjState* st = new AdjState();
+  m.adj = st;
+  for (int k = 0; k + 1 < m.L; ++k) {
+    const int rows = m.widths[k + 1], cols = m.widths[k];
+    if (cudaMalloc(&st->W[k], (size_t)rows * cols * 2) != cudaSuccess) return LEB_ERR_CUDA;
+    round_copy_kernel<<<256, 256>>>(m.W[k], (long long)rows * cols, st->W[k], fmt);
+    if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
+    if (!encode(&st->bwd[k], st->W[k], rows, cols, fmt)) return LEB_ERR_UNSUPPORTED;
+    if (!encode(&st->fwd[k], tc_weight_t(c, k), cols, rows, fmt)) return LEB_ERR_UNSUPPORTED;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return LEB_ERR_CUDA;
+  if (cudaFuncSetAttribute(adjoint_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmem) != cudaSuccess)
+    return LEB_ERR_CUDA;
+  return LEB_OK;
+}
+
+void adj_tc_release(Ctx& c) {
+  AdjState* st = reinterpret_cast<AdjState*>(c.mlp.adj);
+  if (!st) return;
+  for (int k = 0; k < kMaxLayers; ++k) cudaFree(st->W[k]);
+  delete st;
+  c.mlp.adj = nullptr;
+}
+
+size_t adj_tc_scratch_floats(const Ctx& c) {
+  const MlpModel& m = c.mlp;
+  size_t stot = 0;
+  for (int k = 0; k + 2 < m.L; ++k) stot += m.widths[k + 1];   // lambda_0 .. lambda_{L-3}
+  return (size_t)c.sm_count * stot * 128;
+}
+
+leb_status adj_tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, const float* radii,
+                        const float* g_lo, const float* g_hi, int* flags, cudaStream_t s) {
+  const MlpModel& m = c.mlp;
+  AdjState* st = reinterpret_cast<AdjState*>(m.adj);
+  if (!st) return LEB_ERR_UNSUPPORTED;
+  AdjTcArgs a;
+  memset(&a, 0, sizeof(a));
+  for (int k = 0; k + 1 < m.L; ++k) {
+    a.fwd[k] = st->fwd[k];
+    a.bwd[k] = st->bwd[k];
+  }
+  a.L = m.L;
+  for (int i = 0; i <= m.L; ++i) a.widths[i] = m.widths[i];
+  a.fmt = m.prec == LEB_PREC_BF16 ? 1 : 0;
+  a.T = T;
+  a.target = target;
+  const bool output = target == m.L - 1;
+  a.nroles = output ? 3 : 2;
+  a.rows_total = a.nroles * m.widths[target + 1];
+  a.rows_per_tile = output ? 126 : 128;
+  a.tiles_per_t = (a.rows_total + a.rows_per_tile - 1) / a.rows_per_tile;
+  a.H = L.H;
+  for (int i = 0; i + 1 < m.L; ++i) a.hoff[i] = L.hoff[i];
+  int o = 0;
+  for (int k = 0; k + 2 <= target; ++k) {
+    a.soff[k] = o;
+    o += m.widths[k + 1];
+  }
+  a.stot = o > 0 ? o : 1;
+  a.W_target = m.W[target];
+  a.sL = ws + L.sL;
+  a.sU = ws + L.sU;
+  a.tL = ws + L.tL;
+  a.tU = ws + L.tU;
+  a.D = ws + L.D;
+  a.radii = radii;
+  a.g_lo = g_lo;
+  a.g_hi = g_hi;
+  a.gl = ws + L.gl;
+  a.gu = ws + L.gu;
+  a.gsL = ws + L.gsL;
+  a.gsU = ws + L.gsU;
+  a.gtL = ws + L.gtL;
+  a.gtU = ws + L.gtU;
+  a.gD = ws + L.gD;
+  a.grho = ws + L.grho;
+  a.scratch = ws + L.adj;
+  a.flags = flags;
+  const int items = T * a.tiles_per_t;
+  const int grid = items < c.sm_count ? items : c.sm_count;
+  if (grid == 0) return LEB_OK;
+  timer_begin(c, s, "adjoint_tc_kernel");
+  adjoint_tc_kernel<<<grid, kAdjThreads, kAdjSmem, s>>>(a);
+  timer_end(c, s);
+  return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
+}
+
+}  // namespace leb

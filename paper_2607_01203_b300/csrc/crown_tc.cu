@@ -56,6 +56,7 @@ struct TcArgs {
   float *lo, *hi, *bslack;
   float *r_lo, *r_hi, *A, *B, *eps, *gamma_c, *gamma_r;
   float gamma_pad;
+  int tight;                     // 1: no rounding inflation (the adjoint's recompute; not a sound bound)
   int* flags;
 };
 
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
         float* st = stat + (r * 4 + cq) * 4;
         st[0] = dn ? __fadd_rd(sum0, sum1) : __fadd_ru(sum0, sum1);
         st[1] = dn ? __fadd_rd(beta0, beta1) : __fadd_ru(beta0, beta1);
-        st[2] = __fadd_ru(__fadd_ru(infl0, infl1), cq == 0 ? ucon : 0.f);
+        st[2] = a.tight ? 0.f : __fadd_ru(__fadd_ru(infl0, infl1), cq == 0 ? ucon : 0.f);
         if (!epi_sync()) { ok = false; break; }
         if (cq == 0 && bound_row) {
           const float* s0 = stat + (r * 4) * 4;
@@ -536,7 +537,13 @@ leb_status tc_prepare(Ctx& c) {
   return LEB_OK;
 }
 
+const void* tc_weight_t(const Ctx& c, int k) {
+  const TcState* st = tc_state(c);
+  return st ? st->WT[k] : nullptr;
+}
+
 void tc_release(Ctx& c) {
+  adj_tc_release(c);
   TcState* st = tc_state(c);
   if (!st) return;
   for (int k = 0; k < kMaxLayers; ++k) cudaFree(st->WT[k]);
@@ -553,7 +560,7 @@ float gamma_tc(int K) {
 }
 
 leb_status tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, float* r_lo, float* r_hi, float* A,
-                    float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags) {
+                    float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags, bool tight) {
   const MlpModel& m = c.mlp;
   TcState* st = tc_state(c);
   if (!st) return LEB_ERR_UNSUPPORTED;
@@ -598,6 +605,7 @@ leb_status tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, 
   a.gamma_r = opt ? opt->gamma_r : nullptr;
   a.gamma_pad = opt ? opt->gamma_pad : 0.f;
   a.flags = flags;
+  a.tight = tight ? 1 : 0;
   const int items = T * a.tiles_per_t;
   const int grid = items < c.sm_count ? items : c.sm_count;
   if (grid == 0) return LEB_OK;

@@ -71,6 +71,7 @@ struct MlpModel {
   float* Werr[kMaxLayers] = {};   // [out, in] |W - W~| (W~ = reduced-precision value), FP32 rounded up
   float* Wabs_h[kMaxLayers] = {}; // [out, in] |W~| FP32
   void* tc = nullptr;             // tensor-core state (rounded transposed weights, TMA descriptors)
+  void* adj = nullptr;            // tensor-core adjoint state (rounded weights, TMA descriptors)
 };
 
 // Workspace layout of the MLP path (offsets in floats; [T, H] arrays hold every hidden layer of a
@@ -90,6 +91,7 @@ struct MlpWs {
   size_t gsL, gsU, gtL, gtU, gD, gz, gl, gu;  // [T, H] adjoint accumulators
   size_t grho;              // [T, n] adjoint of the radii
   size_t gscr;              // [T, max width] adjoint scratch
+  size_t adj;               // tensor-core adjoint: per-CTA lambda store (0 floats for FP32 handles)
   size_t anom, dlo, dhi;    // [T, n] nominal alpha~ and displacement box Delta = X - alpha~
   size_t bad;               // [T] int: non-finite inputs
   size_t total;             // floats
@@ -147,15 +149,25 @@ void mlp_release(Ctx& c);
 size_t simt_chain_smem(int maxw);
 leb_status run_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, float* r_lo, float* r_hi, float* A,
                      float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags,
-                     bool simt);
-// prep, enclosed nominal pass, bounds and relaxation of every hidden layer (chains on CUDA cores if simt)
+                     bool simt, bool tight = false);
+// prep, enclosed nominal pass, bounds and relaxation of every hidden layer (chains on CUDA cores if simt).
+// tight: tensor-core chains without the rounding inflation (not sound; the adjoint's recompute of the
+// algorithm's bounds).
 leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set, void* ws,
-                              int* flags, cudaStream_t s, bool simt, const leb_options* opt);
+                              int* flags, cudaStream_t s, bool simt, const leb_options* opt, bool tight = false);
 // tensor-core back-substitution (reduced-precision operands, FP32 accumulation in TMEM)
 leb_status tc_prepare(Ctx& c);
 void tc_release(Ctx& c);
 float gamma_tc(int K);  // accumulation bound of K exact products in FP32 (unit roundoff 2^-23)
 leb_status tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, float* r_lo, float* r_hi, float* A,
-                    float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags);
+                    float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags,
+                    bool tight = false);
+const void* tc_weight_t(const Ctx& c, int k);   // W_k^T in the operand format, [widths[k], widths[k+1]]
+// tensor-core adjoint chains (reduced-precision handles)
+leb_status adj_tc_prepare(Ctx& c);
+void adj_tc_release(Ctx& c);
+size_t adj_tc_scratch_floats(const Ctx& c);
+leb_status adj_tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, const float* radii,
+                        const float* g_lo, const float* g_hi, int* flags, cudaStream_t s);
 
 }  // namespace leb

@@ -68,6 +68,7 @@ size_t mlp_workspace_floats(const Ctx& c, int T, MlpWs* w) {
   w->gu = take(TH);
   w->grho = take(Tn);
   w->gscr = take((size_t)T * maxw);
+  w->adj = take(m.adj ? adj_tc_scratch_floats(c) : 0);
   w->anom = take(Tn);
   w->dlo = take(Tn);
   w->dhi = take(Tn);
@@ -631,7 +632,17 @@ leb_status mlp_prepare(Ctx& c) {
       cudaFuncSetAttribute(mlp_chain_simt_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaFuncSetAttribute(mlp_chain_simt_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return LEB_ERR_CUDA;
-  if (c.mlp.prec != LEB_PREC_FP32) return tc_prepare(c);
+  if (c.mlp.prec != LEB_PREC_FP32) {
+    const leb_status st = tc_prepare(c);
+    if (st != LEB_OK) return st;
+    // the tensor-core adjoint is optional: shapes it does not support keep the CUDA-core adjoint
+    const leb_status sa = adj_tc_prepare(c);
+    if (sa == LEB_ERR_UNSUPPORTED) {
+      adj_tc_release(c);
+      return LEB_OK;
+    }
+    return sa;
+  }
   return LEB_OK;
 }
 
@@ -663,7 +674,7 @@ leb_status launch_simt_chain(const Ctx& c, const ChainArgs& a, cudaStream_t s) {
 }
 
 leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set,
-                              void* ws_base, int* flags, cudaStream_t s, bool simt, const leb_options* opt) {
+                              void* ws_base, int* flags, cudaStream_t s, bool simt, const leb_options* opt, bool tight) {
   const MlpModel& m = c.mlp;
   MlpWs L;
   mlp_workspace_floats(c, T, &L);
@@ -740,7 +751,8 @@ leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_
     mlp_nominal_kernel<<<grid, 256, 0, s>>>(na);
     if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
     // bounds of hidden layer i by back-substitution, then its relaxation
-    leb_status st = run_chain(c, T, i, L, ws, nullptr, nullptr, nullptr, nullptr, nullptr, s, bad, opt, flags, simt);
+    leb_status st = run_chain(c, T, i, L, ws, nullptr, nullptr, nullptr, nullptr, nullptr, s, bad, opt, flags, simt,
+                              tight);
     if (st != LEB_OK) return st;
     const int blocks = (int)std::min<long long>(((long long)T * na.N + 255) / 256, 148LL * 32);
     mlp_relax_kernel<<<blocks, 256, 0, s>>>(T, na.N, L.H, L.hoff[i], m.act, ws + L.lo, ws + L.hi, ws + L.zhat,
@@ -767,9 +779,9 @@ leb_status mlp_bounds(Ctx& c, int T, const float* x_nom, const float* u_nom, con
 
 leb_status run_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, float* r_lo, float* r_hi, float* A,
                      float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags,
-                     bool simt) {
+                     bool simt, bool tight) {
   const MlpModel& m = c.mlp;
-  if (!simt) return tc_chain(c, T, target, L, ws, r_lo, r_hi, A, B, eps, s, bad, opt, flags);
+  if (!simt) return tc_chain(c, T, target, L, ws, r_lo, r_hi, A, B, eps, s, bad, opt, flags, tight);
   ChainArgs a{};
   a.m = view(m);
   a.T = T;
