@@ -577,6 +577,7 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     for h in handles.values():
         h.timing(True)
+    torch.cuda.nvtx.range_push("timed")    # profilers can restrict a capture to this range
     e0.record()
     for k in range(args.steps):
         for i, f in enumerate(forms):
@@ -586,6 +587,7 @@ def main():
         if flush is not None and k + 1 < args.steps:
             flush.zero_()
     e1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clocks = sampler.stop()
     if world > 1:

@@ -19,8 +19,8 @@
 // so the weights are the streamed A operand (128 neurons x 64 K tiles by TMA, a ring of kAdjStages) and
 // the per-row operand is the resident B operand (128 rows x K, K-major, 128-byte swizzle). TMEM holds
 // D[neuron][row]: lane = neuron inside an M-tile of 128, column = 128 * M-tile + row. Every epilogue
-// thread owns one neuron, so every sum over chain rows is a register sum, and the role of a row (lower,
-// upper, Jacobian) is the same across a warp.
+// thread owns two neurons (M-tiles m and m + 2 of one TMEM lane), so every sum over chain rows is a
+// register sum, and the role of a row (lower, upper, Jacobian) is the same across a warp.
 //
 // Output rows are carried in difference form: the lower and upper rows hold delta = lambda - lambda^J
 // (their operand lambda o s_sel - lambda^J o sigma'(z~) is formed in FP32 from the row and the Jacobian
@@ -42,12 +42,12 @@
 
 namespace leb {
 
-constexpr int kAdjEpiWarps = 16;                    // 4 M-tiles x 4 TMEM lane quarters
+constexpr int kAdjEpiWarps = 8;                     // 2 M-tile pairs x 4 TMEM lane quarters
 constexpr int kAdjThreads = 32 * (2 + kAdjEpiWarps);
 constexpr int kAdjStages = 6;                       // weight-tile ring
 constexpr int kAdjATile = 128 * 64 * 2;             // 128 neurons x 64 K x 2 bytes
 constexpr int kAdjBRegion = 128 * 512 * 2;          // 128 rows x K <= 512 x 2 bytes
-constexpr int kAdjSmall = 1024 + 32 + 256 + 512 + 16 * 8;   // row data and barriers
+constexpr int kAdjSmall = 1024 + 32 + 16 * 8;   // row cotangents, their scale, barriers
 constexpr int kAdjSmem = 1024 + kAdjBRegion + kAdjStages * kAdjATile + kAdjSmall;
 static_assert(kAdjSmem <= 227 * 1024, "adjoint tensor-core shared memory");
 
@@ -90,9 +90,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
   uint8_t* ring = base + kAdjBRegion;                    // weight tiles
   float* gws = reinterpret_cast<float*>(ring + kAdjStages * kAdjATile);   // [2][128] row cotangents
   float* wmax = gws + 256;                                                 // [2][4] per-warp max |g|
-  uint8_t* roles = reinterpret_cast<uint8_t*>(wmax + 8);                   // [2][128] role, 3 = no row
-  int16_t* idxs = reinterpret_cast<int16_t*>(roles + 256);                 // [2][128] state / neuron index
-  uint64_t* bars = reinterpret_cast<uint64_t*>(idxs + 256);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wmax + 8);
   uint64_t* full = bars;                      // [kAdjStages]
   uint64_t* empty = bars + kAdjStages;        // [kAdjStages]
   uint64_t* a_full = bars + 2 * kAdjStages;   // operand written by the epilogue
@@ -219,10 +217,12 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
     __syncwarp();
   } else {
     // ------------------------------------------------------------------ epilogue warps
+    // Each thread owns two neurons, nrn[0] in M-tile mt and nrn[1] = nrn[0] + 256 in M-tile mt + 2 (same
+    // TMEM lane), and works on both side by side.
     const int q = warp & 3;                    // TMEM lane quarter
-    const int mt = (warp - 2) >> 2;            // M-tile: neurons 128 mt .. 128 mt + 127
-    const int nrn = mt * 128 + q * 32 + lane;  // the neuron this thread owns (and the TMEM lane)
-    const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * 128);
+    const int mt = (warp - 2) >> 2;            // 0 or 1
+    const int nrn0 = mt * 128 + q * 32 + lane;
+    const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * 128);   // + 256 for nrn[1]
     const int etid = threadIdx.x - 64;
     float* scr = a.scratch + (size_t)blockIdx.x * a.stot * 128;
     const int n = a.widths[0];
@@ -249,22 +249,246 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       tc_fence_after();
       return true;
     };
+    auto put = [&](int r, int j, float v) { *reinterpret_cast<uint16_t*>(Bop + b_off(r, j)) = op_round(v, a.fmt); };
+
+    // Rows of a tile come in groups of NR (output: lower, upper, Jacobian; hidden: lower, upper) and a
+    // tile starts on a group, so the role of row r0 + e with r0 a multiple of 8 NR is e mod NR: a
+    // compile-time constant in the unrolled loops. Rows past the tile's valid rows carry zero cotangents
+    // and a zero first operand, so every value derived from them is zero.
+    auto run_item = [&](auto nr_c, int t, int row0, int nrows, const float* gw, float ginv, float gscale) -> bool {
+      constexpr int NR = decltype(nr_c)::value;
+      constexpr int GS = 8 * NR;                 // rows per group: whole groups of NR, whole 8-column loads
+      const int Kt = a.widths[target];
+      // ---- prologue: B = (W_target rows o s_{target-1}) (difference form for output rows) ----------
+      {
+        const int Kp = (Kt + 63) & ~63;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int j = nrn0 + 256 * u;
+          if (j < Kp) {
+            const bool live = j < Kt;
+            const long long o = (long long)t * a.H + a.hoff[target - 1] + (live ? j : 0);
+            const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f, dd = live ? a.D[o] : 0.f;
+            const float* wcol = a.W_target + (live ? j : 0);
+            for (int r = 0; r < 128; r += NR) {
+              float lam = 0.f;
+              if (live && r + NR - 1 < nrows) lam = __ldg(wcol + (long long)((row0 + r) / NR) * Kt);
+              const float jd = lam * dd;
+              const float vl = lam * (lam >= 0.f ? sl : su), vu = lam * (lam >= 0.f ? su : sl);
+              if (NR == 3) {
+                put(r, j, vl - jd);
+                put(r + 1, j, vu - jd);
+                if (r + 2 < 128) put(r + 2, j, jd);
+              } else {
+                put(r, j, vl);
+                put(r + 1, j, vu);
+              }
+            }
+          }
+        }
+        operand_ready();
+      }
+      // ---- forward stages k = target-1 .. 1 --------------------------------------------------------
+      for (int k = target - 1; k >= 1; --k) {
+        if (!wait_acc()) return false;
+        const int N = a.widths[k];             // neurons of hidden layer k-1 (rows of this product)
+        const int Np = (N + 63) & ~63;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int j = nrn0 + 256 * u;
+          if (j >= Np) continue;
+          const bool live = j < N;
+          const long long o = (long long)t * a.H + a.hoff[k - 1] + (live ? j : 0);
+          const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f, dd = live ? a.D[o] : 0.f;
+          float* lrow = scr + (size_t)(a.soff[k - 1] + (live ? j : 0)) * 128;
+          const uint32_t tl = t_lane + 256u * u;
+#pragma unroll 1
+          for (int r0 = 0; r0 < 128; r0 += GS) {
+            const int nch = min(NR, (128 - r0) >> 3);
+            float d[GS];
+#pragma unroll
+            for (int h = 0; h < NR; ++h)
+              if (h < nch) tmem_ld8_nowait(tl + (uint32_t)(r0 + 8 * h), d + 8 * h);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < GS; e += NR) {
+              if (NR == 3) {
+                const float lj = d[e + 2];
+                d[e] += lj;                     // lambda of the lower row
+                d[e + 1] += lj;                 // lambda of the upper row
+                const float jd = lj * dd;
+                if (r0 + e < 128) put(r0 + e, j, fmaf(d[e], d[e] >= 0.f ? sl : su, -jd));
+                if (r0 + e + 1 < 128) put(r0 + e + 1, j, fmaf(d[e + 1], d[e + 1] >= 0.f ? su : sl, -jd));
+                if (r0 + e + 2 < 128) put(r0 + e + 2, j, jd);
+              } else {
+                put(r0 + e, j, d[e] * (d[e] >= 0.f ? sl : su));
+                put(r0 + e + 1, j, d[e + 1] * (d[e + 1] >= 0.f ? su : sl));
+              }
+            }
+            if (live)
+#pragma unroll
+              for (int e = 0; e < GS; e += 4)
+                if (r0 + e < 128)
+                  *reinterpret_cast<float4*>(lrow + r0 + e) = make_float4(d[e], d[e + 1], d[e + 2], d[e + 3]);
+          }
+        }
+        operand_ready();
+      }
+      // ---- G_{-1} from lambda_{-1} (neurons = inputs m < n) --------------------------------------------
+      {
+        if (!wait_acc()) return false;
+        const int np = (n + 63) & ~63;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int j = nrn0 + 256 * u;
+          if (j >= np) continue;
+          const bool live = j < n;
+          const float rho = live ? a.radii[(long long)t * n + j] : 0.f;
+          const uint32_t tl = t_lane + 256u * u;
+          float grho = 0.f;
+#pragma unroll 1
+          for (int r0 = 0; r0 < 128; r0 += GS) {
+            const int nch = min(NR, (128 - r0) >> 3);
+            float d[GS];
+#pragma unroll
+            for (int h = 0; h < NR; ++h)
+              if (h < nch) tmem_ld8_nowait(tl + (uint32_t)(r0 + 8 * h), d + 8 * h);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < GS; e += NR) {
+              const int r = r0 + e;
+              if (r >= 128) break;
+              // output rows: d = delta = lambda - lambda^J (M itself); hidden rows: d = lambda = M
+              const float glo = gw[r] * ginv, ghi = gw[r + 1] * ginv;
+              const float mlo = d[e], mhi = d[e + 1];
+              const float G0 = mlo > 0.f ? -glo * rho : (mlo < 0.f ? glo * rho : 0.f);
+              const float G1 = mhi > 0.f ? ghi * rho : (mhi < 0.f ? -ghi * rho : 0.f);
+              grho = fmaf(ghi, fabsf(mhi), fmaf(-glo, fabsf(mlo), grho));
+              put(r, j, G0);
+              put(r + 1, j, G1);
+              if (NR == 3 && r + 2 < 128) put(r + 2, j, -(G0 + G1));
+            }
+          }
+          if (live && grho != 0.f) atomicAdd(a.grho + (long long)t * n + j, grho * gscale);
+        }
+        operand_ready();
+      }
+      // ---- backward stages k = 0 .. target-1 -------------------------------------------------------
+      for (int k = 0; k < target; ++k) {
+        if (!wait_acc()) return false;
+        const int N = a.widths[k + 1];            // neurons of hidden layer k
+        const bool last = k == target - 1;
+        const int Np = (N + 63) & ~63;
+        const int nu = nrn0 + 256 < Np ? 2 : (nrn0 < Np ? 1 : 0);   // neurons of this thread in the layer
+        if (nu > 0) {
+          bool live[2];
+          long long o[2];
+          float sl[2], su[2], tlv[2], tu[2], dd[2];
+          const float* lrow[2];
+          const float* wcol[2];
+          float gsl[2] = {0.f, 0.f}, gsu[2] = {0.f, 0.f}, gtl[2] = {0.f, 0.f}, gtu[2] = {0.f, 0.f}, gd[2] = {0.f, 0.f};
+          float wv[2] = {0.f, 0.f};   // lambda_{target-1} of the current row group (last stage)
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int j = nrn0 + 256 * u;
+            live[u] = u < nu && j < N;
+            o[u] = (long long)t * a.H + a.hoff[k] + (live[u] ? j : 0);
+            sl[u] = live[u] ? a.sL[o[u]] : 0.f;
+            su[u] = live[u] ? a.sU[o[u]] : 0.f;
+            tlv[u] = live[u] ? a.tL[o[u]] : 0.f;
+            tu[u] = live[u] ? a.tU[o[u]] : 0.f;
+            dd[u] = live[u] ? a.D[o[u]] : 0.f;
+            lrow[u] = scr + (size_t)((last ? 0 : a.soff[k]) + (live[u] ? j : 0)) * 128;
+            wcol[u] = a.W_target + (live[u] ? j : 0);
+          }
+          // 8-row chunks; the roles of a chunk's rows as bit masks (bit e: row rb + e): Jacobian rows, and
+          // rows whose lower line is chosen when lambda >= 0 (lower-bound rows)
+#pragma unroll 1
+          for (int rb = 0; rb < 128; rb += 8) {
+            const int off = rb % NR;       // role of row rb (tiles start on a row group)
+            // role-0 rows: e = -off mod NR (+ NR, ...); Jacobian rows (NR = 3): e = 2 - off mod 3 (+ 3, ...)
+            const uint32_t lm = NR == 3 ? (0x49u << ((3 - off) % 3)) & 0xFFu : (off == 0 ? 0x55u : 0xAAu);
+            const uint32_t jm = NR == 3 ? (0x49u << ((5 - off) % 3)) & 0xFFu : 0u;
+            float ga[2][8], lam[2][8], g[8];
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+              if (u < nu) tmem_ld8_nowait(t_lane + 256u * u + (uint32_t)rb, ga[u]);
+            if (!last) {
+#pragma unroll
+              for (int u = 0; u < 2; ++u)
+                if (u < nu)
+#pragma unroll
+                  for (int e = 0; e < 8; e += 4) {
+                    const float4 v = *reinterpret_cast<const float4*>(lrow[u] + rb + e);
+                    lam[u][e] = v.x; lam[u][e + 1] = v.y; lam[u][e + 2] = v.z; lam[u][e + 3] = v.w;
+                  }
+            } else {
+              // lambda_{target-1}: the W_target row of each row's state, loaded at the group's first row
+              // (role 0) and carried to the group's other rows, also across chunks
+#pragma unroll
+              for (int u = 0; u < 2; ++u)
+                if (u < nu)
+#pragma unroll
+                  for (int e = 0; e < 8; ++e) {
+                    if ((lm >> e) & 1u) {
+                      const int r = rb + e;
+                      wv[u] = (live[u] && r + NR - 1 < nrows) ? __ldg(wcol[u] + (long long)((row0 + r) / NR) * Kt)
+                                                              : 0.f;
+                    }
+                    lam[u][e] = wv[u];
+                  }
+            }
+#pragma unroll
+            for (int e = 0; e < 8; e += 4) {
+              const float4 v = *reinterpret_cast<const float4*>(gw + rb + e);
+              g[e] = v.x * ginv; g[e + 1] = v.y * ginv; g[e + 2] = v.z * ginv; g[e + 3] = v.w * ginv;
+            }
+            tmem_wait_ld();
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              if (u >= nu) continue;
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                const bool isJ = (jm >> e) & 1u, isL = (lm >> e) & 1u;
+                const float l = lam[u][e], x = ga[u][e];
+                const bool useL = isL == (l >= 0.f);
+                const float p1 = x * l, p2 = g[e] * l;
+                const bool cl = !isJ && useL, cu = !isJ && !useL;
+                gsl[u] += cl ? p1 : 0.f;
+                gtl[u] += cl ? p2 : 0.f;
+                gsu[u] += cu ? p1 : 0.f;
+                gtu[u] += cu ? p2 : 0.f;
+                gd[u] += isJ ? p1 : 0.f;
+                const float G = isJ ? x * dd[u] : fmaf(x, useL ? sl[u] : su[u], g[e] * (useL ? tlv[u] : tu[u]));
+                if (!last) put(rb + e, nrn0 + 256 * u, G);
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+            if (live[u]) {
+              if (gsl[u] != 0.f) atomicAdd(a.gsL + o[u], gsl[u] * gscale);
+              if (gsu[u] != 0.f) atomicAdd(a.gsU + o[u], gsu[u] * gscale);
+              if (gtl[u] != 0.f) atomicAdd(a.gtL + o[u], gtl[u] * gscale);
+              if (gtu[u] != 0.f) atomicAdd(a.gtU + o[u], gtu[u] * gscale);
+              if (gd[u] != 0.f) atomicAdd(a.gD + o[u], gd[u] * gscale);
+            }
+        }
+        if (!last) operand_ready();
+      }
+      return true;
+    };
 
     for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
       const int t = item / a.tiles_per_t, tile = item - t * a.tiles_per_t;
       const int row0 = tile * a.rows_per_tile;
       const int nrows = min(a.rows_per_tile, a.rows_total - row0);   // valid rows of this tile
-      // ---- row cotangents of the tile and their scale ---------------------------------------------
+      // ---- row cotangents of the tile (0 past the valid rows) and their scale ----------------------
       float* gw = gws + gb * 128;
-      const uint8_t* rrole = roles + gb * 128;
-      const int16_t* ridx = idxs + gb * 128;
       if (etid < 128) {
         float g = 0.f;
-        int role = 3, idx = 0;
         if (etid < nrows) {
-          const int grow = row0 + etid;
-          role = grow % a.nroles;
-          idx = grow / a.nroles;
+          const int grow = row0 + etid, role = grow % a.nroles, idx = grow / a.nroles;
           if (output) {
             const int nx = a.widths[a.L];
             g = role == 0 ? a.g_lo[(long long)t * nx + idx] : (role == 1 ? a.g_hi[(long long)t * nx + idx] : 0.f);
@@ -274,208 +498,18 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
           }
         }
         gw[etid] = g;
-        roles[gb * 128 + etid] = (uint8_t)role;
-        idxs[gb * 128 + etid] = (int16_t)idx;
         float m = fabsf(g);
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
+        for (int dlt = 16; dlt > 0; dlt >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, dlt));
         if (lane == 0) wmax[gb * 4 + (etid >> 5)] = m;
       }
       if (!epi_sync()) { ok = false; break; }
-      float gmax = fmaxf(fmaxf(wmax[gb * 4], wmax[gb * 4 + 1]), fmaxf(wmax[gb * 4 + 2], wmax[gb * 4 + 3]));
+      const float gmax = fmaxf(fmaxf(wmax[gb * 4], wmax[gb * 4 + 1]), fmaxf(wmax[gb * 4 + 2], wmax[gb * 4 + 3]));
       const float gscale = (gmax > 0.f && isfinite(gmax)) ? gmax : 1.f;
       const float ginv = 1.f / gscale;
       gb ^= 1;
-
-      // ---- prologue: B = (W_target rows o s_{target-1}) for neurons j < widths[target] ----------------
-      {
-        const int K = a.widths[target], Kp = (K + 63) & ~63;
-        if (nrn < Kp) {
-          const bool live = nrn < K;
-          const long long o = (long long)t * a.H + a.hoff[target - 1] + nrn;
-          const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f, dd = live ? a.D[o] : 0.f;
-          for (int r = 0; r < 128; ++r) {
-            float v = 0.f;
-            const int role = rrole[r];
-            if (live && role != 3) {
-              const float lam = __ldg(a.W_target + (long long)ridx[r] * K + nrn);
-              if (role == 2) {
-                v = lam * dd;
-              } else {
-                const float sv = ((role == 0) == (lam >= 0.f)) ? sl : su;
-                v = output ? fmaf(lam, sv, -lam * dd) : lam * sv;   // delta = 0 at the start of the chain
-              }
-            }
-            *reinterpret_cast<uint16_t*>(Bop + b_off(r, nrn)) = op_round(v, a.fmt);
-          }
-        }
-        operand_ready();
-      }
-      // ---- forward stages k = target-1 .. 1: lambda_{k-1} -> scratch, next operand ------------------
-      // rows in whole groups: (lower, upper, Jacobian) triples of output rows, (lower, upper) pairs
-      auto fwd_stage = [&](auto nr_c, int k) {
-        constexpr int nr = decltype(nr_c)::value, gsize = 16 * nr;
-        const int N = a.widths[k];             // neurons of hidden layer k-1 (rows of this product)
-        const int Np = (N + 63) & ~63;
-        if (!(nrn < Np && mt * 128 < N)) return;
-        const bool live = nrn < N;
-        const long long o = (long long)t * a.H + a.hoff[k - 1] + (live ? nrn : 0);
-        const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f, dd = live ? a.D[o] : 0.f;
-        float* lrow = scr + (size_t)(a.soff[k - 1] + (live ? nrn : 0)) * 128;
-        for (int r0 = 0; r0 < 128; r0 += gsize) {
-          const int nch = min(nr, (128 - r0) >> 4);   // 16-column TMEM chunks inside the tile's 128 rows
-          float d[gsize], lam[gsize];
-#pragma unroll
-          for (int h = 0; h < nr; ++h) {
-            if (h < nch) tmem_ld16(t_lane + (uint32_t)(r0 + 16 * h), d + 16 * h);
-            else
-#pragma unroll
-              for (int e = 0; e < 16; ++e) d[16 * h + e] = 0.f;
-          }
-#pragma unroll
-          for (int e = 0; e < gsize; e += nr) {
-            const int r = r0 + e;
-            float v[nr];
-            const bool row_ok = live && r < 128 && rrole[r] != 3;
-            if (nr == 3) {
-              const float lj = d[e + 2], ll = d[e] + lj, lu = d[e + 1] + lj;
-              lam[e] = ll;
-              lam[e + 1] = lu;
-              lam[e + nr - 1] = lj;
-              const float jd = lj * dd;
-              v[0] = row_ok ? fmaf(ll, ll >= 0.f ? sl : su, -jd) : 0.f;
-              v[1] = row_ok ? fmaf(lu, lu >= 0.f ? su : sl, -jd) : 0.f;
-              v[nr - 1] = row_ok ? jd : 0.f;
-            } else {
-              lam[e] = d[e];
-              lam[e + 1] = d[e + 1];
-              v[0] = row_ok ? d[e] * (d[e] >= 0.f ? sl : su) : 0.f;
-              v[1] = row_ok ? d[e + 1] * (d[e + 1] >= 0.f ? su : sl) : 0.f;
-            }
-#pragma unroll
-            for (int p = 0; p < nr; ++p)
-              if (r + p < 128) *reinterpret_cast<uint16_t*>(Bop + b_off(r + p, nrn)) = op_round(v[p], a.fmt);
-          }
-          if (live)
-#pragma unroll
-            for (int e = 0; e < gsize; e += 4)
-              if (e < 16 * nch)
-                *reinterpret_cast<float4*>(lrow + r0 + e) = make_float4(lam[e], lam[e + 1], lam[e + 2], lam[e + 3]);
-        }
-      };
-      for (int k = target - 1; k >= 1 && ok; --k) {
-        if (!wait_acc()) { ok = false; break; }
-        if (output) fwd_stage(std::integral_constant<int, 3>(), k);
-        else fwd_stage(std::integral_constant<int, 2>(), k);
-        operand_ready();
-      }
-      if (!ok) break;
-      // ---- G_{-1} from lambda_{-1} (TMEM, neurons = inputs m < n) -----------------------------------
-      {
-        if (!wait_acc()) { ok = false; break; }
-        const int np = (n + 63) & ~63;
-        if (mt * 128 < np) {
-          const bool live = nrn < n;
-          const float rho = live ? a.radii[(long long)t * n + nrn] : 0.f;
-          float grho = 0.f;
-          // whole (lower, upper, Jacobian) triples or (lower, upper) pairs per group of TMEM columns
-          auto group = [&](auto nr_c) {
-            constexpr int nr = decltype(nr_c)::value, gsize = 16 * nr;
-            for (int r0 = 0; r0 < 128; r0 += gsize) {
-              const int nch = min(nr, (128 - r0) >> 4);
-              float lam[gsize];
-#pragma unroll
-              for (int h = 0; h < nr; ++h) {
-                if (h < nch) tmem_ld16(t_lane + (uint32_t)(r0 + 16 * h), lam + 16 * h);
-                else
-#pragma unroll
-                  for (int e = 0; e < 16; ++e) lam[16 * h + e] = 0.f;
-              }
-#pragma unroll
-              for (int e = 0; e < gsize; e += nr) {
-                const int r = r0 + e;
-                float G0 = 0.f, G1 = 0.f;
-                if (live && r + nr - 1 < nrows) {
-                  const float glo = gw[r] * ginv, ghi = gw[r + 1] * ginv;
-                  const float mlo = lam[e], mhi = lam[e + 1];   // output rows: delta = lambda - lambda^J
-                  const float sgl = mlo > 0.f ? 1.f : (mlo < 0.f ? -1.f : 0.f);
-                  const float sgh = mhi > 0.f ? 1.f : (mhi < 0.f ? -1.f : 0.f);
-                  G0 = -glo * sgl * rho;
-                  G1 = ghi * sgh * rho;
-                  grho += ghi * fabsf(mhi) - glo * fabsf(mlo);
-                }
-                if (r < 128) *reinterpret_cast<uint16_t*>(Bop + b_off(r, nrn)) = op_round(G0, a.fmt);
-                if (r + 1 < 128) *reinterpret_cast<uint16_t*>(Bop + b_off(r + 1, nrn)) = op_round(G1, a.fmt);
-                if (nr == 3 && r + 2 < 128)
-                  *reinterpret_cast<uint16_t*>(Bop + b_off(r + 2, nrn)) = op_round(-(G0 + G1), a.fmt);
-              }
-            }
-          };
-          if (output) group(std::integral_constant<int, 3>());
-          else group(std::integral_constant<int, 2>());
-          if (live && grho != 0.f) atomicAdd(a.grho + (long long)t * n + nrn, grho * gscale);
-        }
-        operand_ready();
-      }
-      // ---- backward stages k = 0 .. target-1 -------------------------------------------------------
-      for (int k = 0; k < target && ok; ++k) {
-        if (!wait_acc()) { ok = false; break; }
-        const int N = a.widths[k + 1];            // neurons of hidden layer k
-        const bool last = k == target - 1;
-        const int Np = (N + 63) & ~63;
-        if (nrn < Np && mt * 128 < N) {
-          const bool live = nrn < N;
-          const long long o = (long long)t * a.H + a.hoff[k] + (live ? nrn : 0);
-          const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f;
-          const float tl = live ? a.tL[o] : 0.f, tu = live ? a.tU[o] : 0.f, dd = live ? a.D[o] : 0.f;
-          const float* lrow = last ? nullptr : scr + (size_t)(a.soff[k] + (live ? nrn : 0)) * 128;
-          float gsl = 0.f, gsu = 0.f, gtl = 0.f, gtu = 0.f, gd = 0.f;
-          for (int r0 = 0; r0 < 128; r0 += 16) {
-            float ga[16], lam[16];
-            tmem_ld16(t_lane + (uint32_t)r0, ga);
-            if (!last && live) {
-#pragma unroll
-              for (int e = 0; e < 16; e += 4) {
-                const float4 v = *reinterpret_cast<const float4*>(lrow + r0 + e);
-                lam[e] = v.x; lam[e + 1] = v.y; lam[e + 2] = v.z; lam[e + 3] = v.w;
-              }
-            }
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const int r = r0 + e;
-              float G = 0.f;
-              const int role = rrole[r];
-              if (live && role != 3) {
-                const float l = last ? __ldg(a.W_target + (long long)ridx[r] * a.widths[target] + nrn) : lam[e];
-                if (role == 2) {
-                  gd = fmaf(ga[e], l, gd);
-                  G = ga[e] * dd;
-                } else {
-                  const float g = gw[r] * ginv;
-                  if ((role == 0) == (l >= 0.f)) {
-                    gsl = fmaf(ga[e], l, gsl);
-                    gtl = fmaf(g, l, gtl);
-                    G = fmaf(ga[e], sl, g * tl);
-                  } else {
-                    gsu = fmaf(ga[e], l, gsu);
-                    gtu = fmaf(g, l, gtu);
-                    G = fmaf(ga[e], su, g * tu);
-                  }
-                }
-              }
-              if (!last) *reinterpret_cast<uint16_t*>(Bop + b_off(r, nrn)) = op_round(G, a.fmt);
-            }
-          }
-          if (live) {
-            if (gsl != 0.f) atomicAdd(a.gsL + o, gsl * gscale);
-            if (gsu != 0.f) atomicAdd(a.gsU + o, gsu * gscale);
-            if (gtl != 0.f) atomicAdd(a.gtL + o, gtl * gscale);
-            if (gtu != 0.f) atomicAdd(a.gtU + o, gtu * gscale);
-            if (gd != 0.f) atomicAdd(a.gD + o, gd * gscale);
-          }
-        }
-        if (!last) operand_ready();
-      }
+      ok = output ? run_item(std::integral_constant<int, 3>(), t, row0, nrows, gw, ginv, gscale)
+                  : run_item(std::integral_constant<int, 2>(), t, row0, nrows, gw, ginv, gscale);
       if (!ok) break;
       tc_fence_before();
       if (*(volatile int*)&s_abort) ok = false;
