@@ -72,15 +72,27 @@ struct AdjTcArgs {
   int* flags;
 };
 
+__device__ __forceinline__ uint32_t pack2(float x, float y, int fmt) {
+  if (fmt == 0) {
+    const __half2 h = __floats2half2_rn(x, y);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
 __device__ __forceinline__ uint16_t op_round(float x, int fmt) {
   if (fmt == 0) return __half_as_ushort(__float2half_rn(x));
   return __bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
 
-// Byte offset of element (row r, column j) in the K-major, 128-byte-swizzled B operand: 64-column blocks
-// of 128 rows x 128 bytes; the 16-byte chunk index inside a row is XORed with r mod 8.
-__device__ __forceinline__ uint32_t b_off(int r, int j) {
-  return (uint32_t)((j >> 6) * 16384 + r * 128 + ((((j & 63) >> 3) ^ (r & 7)) << 4) + ((j & 7) << 1));
+// The per-row operand B (N = 128 chain rows x K neurons) is MN-major with 128-byte swizzle: atom
+// (row block rb = r / 64, neuron group g = j / 8) at rb * kAdjLbo + g * 1024 holds neuron j's 64 rows as
+// 128 contiguous bytes at (j mod 8) * 128, the 16-byte chunk index XORed with j mod 8. Byte offset of the
+// 8 rows r0 .. r0 + 7 (r0 a multiple of 8) of neuron j:
+constexpr uint32_t kAdjLbo = 64 * 1024;   // 64 neuron groups x 1 KB
+__device__ __forceinline__ uint32_t b_off8(int r0, int j) {
+  return (uint32_t)((r0 >> 6) * kAdjLbo + (j >> 3) * 1024 + (j & 7) * 128 + ((((r0 & 63) >> 3) ^ (j & 7)) << 4));
 }
 
 __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid_constant__ AdjTcArgs a) {
@@ -179,7 +191,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t ring_base = smem_u32(ring), b_base = smem_u32(Bop);
-      const uint32_t idesc = idesc_f16(128, 128, a.fmt);
+      const uint32_t idesc = idesc_f16_bmn(128, 128, a.fmt);
       uint32_t kb = 0, na = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
@@ -199,7 +211,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
 #pragma unroll
               for (int kk = 0; kk < 4; ++kk) {
                 const uint64_t ad = sw128_desc(ring_base + slot * kAdjATile + kk * 32);
-                const uint64_t bd = sw128_desc(b_base + kc * 16384 + kk * 32);
+                const uint64_t bd = sw128_mn_desc(b_base + (uint32_t)(kc * 8 + kk * 2) * 1024u, kAdjLbo, 1024u);
                 tc_mma_f16(tmem + (uint32_t)(c * 128), ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
               }
               tc_commit(&empty[slot]);
@@ -249,7 +261,15 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       tc_fence_after();
       return true;
     };
-    auto put = [&](int r, int j, float v) { *reinterpret_cast<uint16_t*>(Bop + b_off(r, j)) = op_round(v, a.fmt); };
+    // 8 consecutive rows r0 .. r0 + 7 of neuron j into the operand (one 16-byte store)
+    auto put8 = [&](int r0, int j, const float* v) {
+      uint4 q;
+      q.x = pack2(v[0], v[1], a.fmt);
+      q.y = pack2(v[2], v[3], a.fmt);
+      q.z = pack2(v[4], v[5], a.fmt);
+      q.w = pack2(v[6], v[7], a.fmt);
+      *reinterpret_cast<uint4*>(Bop + b_off8(r0, j)) = q;
+    };
 
     // Rows of a tile come in groups of NR (output: lower, upper, Jacobian; hidden: lower, upper) and a
     // tile starts on a group, so the role of row r0 + e with r0 a multiple of 8 NR is e mod NR: a
@@ -270,19 +290,25 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
             const long long o = (long long)t * a.H + a.hoff[target - 1] + (live ? j : 0);
             const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f, dd = live ? a.D[o] : 0.f;
             const float* wcol = a.W_target + (live ? j : 0);
-            for (int r = 0; r < 128; r += NR) {
-              float lam = 0.f;
-              if (live && r + NR - 1 < nrows) lam = __ldg(wcol + (long long)((row0 + r) / NR) * Kt);
-              const float jd = lam * dd;
-              const float vl = lam * (lam >= 0.f ? sl : su), vu = lam * (lam >= 0.f ? su : sl);
-              if (NR == 3) {
-                put(r, j, vl - jd);
-                put(r + 1, j, vu - jd);
-                if (r + 2 < 128) put(r + 2, j, jd);
-              } else {
-                put(r, j, vl);
-                put(r + 1, j, vu);
+            float wv = 0.f;   // the W_target entry of the current row group, carried across chunks
+#pragma unroll 1
+            for (int rb = 0; rb < 128; rb += 8) {
+              const int off = rb % NR;
+              const uint32_t lm = NR == 3 ? (0x49u << ((3 - off) % 3)) & 0xFFu : (off == 0 ? 0x55u : 0xAAu);
+              const uint32_t jm = NR == 3 ? (0x49u << ((5 - off) % 3)) & 0xFFu : 0u;
+              float v[8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                const bool isL = (lm >> e) & 1u, isJ = (jm >> e) & 1u;
+                if (isL) {
+                  const int r = rb + e;
+                  wv = (live && r + NR - 1 < nrows) ? __ldg(wcol + (long long)((row0 + r) / NR) * Kt) : 0.f;
+                }
+                const float lam = wv, jd = NR == 3 ? lam * dd : 0.f;
+                const bool useL = isL == (lam >= 0.f);
+                v[e] = isJ ? jd : fmaf(lam, useL ? sl : su, -jd);
               }
+              put8(rb, j, v);
             }
           }
         }
@@ -307,9 +333,14 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
             const int nch = min(NR, (128 - r0) >> 3);
             float d[GS];
 #pragma unroll
-            for (int h = 0; h < NR; ++h)
+            for (int h = 0; h < NR; ++h) {
               if (h < nch) tmem_ld8_nowait(tl + (uint32_t)(r0 + 8 * h), d + 8 * h);
+              else
+#pragma unroll
+                for (int e = 0; e < 8; ++e) d[8 * h + e] = 0.f;   // rows past the tile
+            }
             tmem_wait_ld();
+            float v[GS];
 #pragma unroll
             for (int e = 0; e < GS; e += NR) {
               if (NR == 3) {
@@ -317,14 +348,17 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
                 d[e] += lj;                     // lambda of the lower row
                 d[e + 1] += lj;                 // lambda of the upper row
                 const float jd = lj * dd;
-                if (r0 + e < 128) put(r0 + e, j, fmaf(d[e], d[e] >= 0.f ? sl : su, -jd));
-                if (r0 + e + 1 < 128) put(r0 + e + 1, j, fmaf(d[e + 1], d[e + 1] >= 0.f ? su : sl, -jd));
-                if (r0 + e + 2 < 128) put(r0 + e + 2, j, jd);
+                v[e] = fmaf(d[e], d[e] >= 0.f ? sl : su, -jd);
+                v[e + 1] = fmaf(d[e + 1], d[e + 1] >= 0.f ? su : sl, -jd);
+                v[e + NR - 1] = jd;
               } else {
-                put(r0 + e, j, d[e] * (d[e] >= 0.f ? sl : su));
-                put(r0 + e + 1, j, d[e + 1] * (d[e + 1] >= 0.f ? su : sl));
+                v[e] = d[e] * (d[e] >= 0.f ? sl : su);
+                v[e + 1] = d[e + 1] * (d[e + 1] >= 0.f ? su : sl);
               }
             }
+#pragma unroll
+            for (int h = 0; h < NR; ++h)
+              if (h < nch) put8(r0 + 8 * h, j, v + 8 * h);
             if (live)
 #pragma unroll
               for (int e = 0; e < GS; e += 4)
@@ -351,23 +385,31 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
             const int nch = min(NR, (128 - r0) >> 3);
             float d[GS];
 #pragma unroll
-            for (int h = 0; h < NR; ++h)
+            for (int h = 0; h < NR; ++h) {
               if (h < nch) tmem_ld8_nowait(tl + (uint32_t)(r0 + 8 * h), d + 8 * h);
+              else
+#pragma unroll
+                for (int e = 0; e < 8; ++e) d[8 * h + e] = 0.f;   // rows past the tile
+            }
             tmem_wait_ld();
+            float v[GS];
 #pragma unroll
             for (int e = 0; e < GS; e += NR) {
               const int r = r0 + e;
-              if (r >= 128) break;
-              // output rows: d = delta = lambda - lambda^J (M itself); hidden rows: d = lambda = M
-              const float glo = gw[r] * ginv, ghi = gw[r + 1] * ginv;
+              // output rows: d = delta = lambda - lambda^J (M itself); hidden rows: d = lambda = M.
+              // Rows past 128 (the last group) only hold zeros and are not stored.
+              const float glo = r < 128 ? gw[r] * ginv : 0.f, ghi = r + 1 < 128 ? gw[r + 1] * ginv : 0.f;
               const float mlo = d[e], mhi = d[e + 1];
               const float G0 = mlo > 0.f ? -glo * rho : (mlo < 0.f ? glo * rho : 0.f);
               const float G1 = mhi > 0.f ? ghi * rho : (mhi < 0.f ? -ghi * rho : 0.f);
               grho = fmaf(ghi, fabsf(mhi), fmaf(-glo, fabsf(mlo), grho));
-              put(r, j, G0);
-              put(r + 1, j, G1);
-              if (NR == 3 && r + 2 < 128) put(r + 2, j, -(G0 + G1));
+              v[e] = G0;
+              v[e + 1] = G1;
+              if (NR == 3) v[e + NR - 1] = -(G0 + G1);
             }
+#pragma unroll
+            for (int h = 0; h < NR; ++h)
+              if (h < nch) put8(r0 + 8 * h, j, v + 8 * h);
           }
           if (live && grho != 0.f) atomicAdd(a.grho + (long long)t * n + j, grho * gscale);
         }
@@ -447,6 +489,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
               if (u >= nu) continue;
+              float gv[8];
 #pragma unroll
               for (int e = 0; e < 8; ++e) {
                 const bool isJ = (jm >> e) & 1u, isL = (lm >> e) & 1u;
@@ -459,9 +502,9 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
                 gsu[u] += cu ? p1 : 0.f;
                 gtu[u] += cu ? p2 : 0.f;
                 gd[u] += isJ ? p1 : 0.f;
-                const float G = isJ ? x * dd[u] : fmaf(x, useL ? sl[u] : su[u], g[e] * (useL ? tlv[u] : tu[u]));
-                if (!last) put(rb + e, nrn0 + 256 * u, G);
+                gv[e] = isJ ? x * dd[u] : fmaf(x, useL ? sl[u] : su[u], g[e] * (useL ? tlv[u] : tu[u]));
               }
+              if (!last) put8(rb, nrn0 + 256 * u, gv);
             }
           }
 #pragma unroll

@@ -23,11 +23,28 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t smem_addr) {
   return d;
 }
 
+// Shared-memory matrix descriptor of an MN-major operand with 128-byte swizzle: atoms of 64 MN elements
+// (128 contiguous bytes) x 8 K rows (128 bytes apart); lbo = byte stride between atoms along MN,
+// sbo = byte stride between 8-row groups along K; version 1, layout type 2.
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t smem_addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
 // Instruction descriptor of kind::f16: D = FP32 (bits [4,6) = 1), A/B format (bits [7,10), [10,13):
 // 0 = FP16, 1 = BF16), both K-major (bits 15, 16 = 0), N >> 3 in [17,23), M >> 4 in [24,29).
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int ab_fmt) {
   return (1u << 4) | ((uint32_t)ab_fmt << 7) | ((uint32_t)ab_fmt << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
+}
+// The same with B MN-major (bit 16).
+__host__ __device__ constexpr uint32_t idesc_f16_bmn(int M, int N, int ab_fmt) {
+  return idesc_f16(M, N, ab_fmt) | (1u << 16);
 }
 
 __device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
