@@ -68,7 +68,7 @@ struct AdjTcArgs {
   const float *g_lo, *g_hi;      // output target: [T, n_x]
   const float *gl, *gu;          // hidden target: [T, H]
   float *gsL, *gsU, *gtL, *gtU, *gD, *grho;
-  float* scratch;                // gridDim.x x stot x 128 floats
+  __half* scratch;               // gridDim.x x stot x 128 lambdas, FP16
   int* flags;
 };
 
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
     const int nrn0 = mt * 128 + q * 32 + lane;
     const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * 128);   // + 256 for nrn[1]
     const int etid = threadIdx.x - 64;
-    float* scr = a.scratch + (size_t)blockIdx.x * a.stot * 128;
+    __half* scr = a.scratch + (size_t)blockIdx.x * a.stot * 128;
     const int n = a.widths[0];
     const bool output = target == a.L - 1;
     uint32_t nacc = 0, nbar = 0;
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
                   wv = (live && r + NR - 1 < nrows) ? __ldg(wcol + (long long)((row0 + r) / NR) * Kt) : 0.f;
                 }
                 const float lam = wv, jd = NR == 3 ? lam * dd : 0.f;
-                const bool useL = isL == (lam >= 0.f);
+                const bool useL = isL == !signbit(lam);
                 v[e] = isJ ? jd : fmaf(lam, useL ? sl : su, -jd);
               }
               put8(rb, j, v);
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
           const bool live = j < N;
           const long long o = (long long)t * a.H + a.hoff[k - 1] + (live ? j : 0);
           const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f, dd = live ? a.D[o] : 0.f;
-          float* lrow = scr + (size_t)(a.soff[k - 1] + (live ? j : 0)) * 128;
+          __half* lrow = scr + (size_t)(a.soff[k - 1] + (live ? j : 0)) * 128;
           const uint32_t tl = t_lane + 256u * u;
 #pragma unroll 1
           for (int r0 = 0; r0 < 128; r0 += GS) {
@@ -340,20 +340,29 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
                 for (int e = 0; e < 8; ++e) d[8 * h + e] = 0.f;   // rows past the tile
             }
             tmem_wait_ld();
+            if (NR == 3)
+#pragma unroll
+              for (int e = 0; e < GS; e += NR) {
+                d[e] += d[e + 2];               // lambda of the lower row
+                d[e + 1] += d[e + 2];           // lambda of the upper row
+              }
+            // lambda is kept in FP16 for the backward pass, and the line choice (sign of lambda) is made
+            // on that stored value here and there alike
+            __half lh[GS];
+#pragma unroll
+            for (int e = 0; e < GS; ++e) lh[e] = __float2half_rn(d[e]);
             float v[GS];
 #pragma unroll
             for (int e = 0; e < GS; e += NR) {
+              const bool nl = !(__half_as_ushort(lh[e]) & 0x8000u), nu_ = !(__half_as_ushort(lh[e + 1]) & 0x8000u);
               if (NR == 3) {
-                const float lj = d[e + 2];
-                d[e] += lj;                     // lambda of the lower row
-                d[e + 1] += lj;                 // lambda of the upper row
-                const float jd = lj * dd;
-                v[e] = fmaf(d[e], d[e] >= 0.f ? sl : su, -jd);
-                v[e + 1] = fmaf(d[e + 1], d[e + 1] >= 0.f ? su : sl, -jd);
+                const float jd = d[e + 2] * dd;
+                v[e] = fmaf(d[e], nl ? sl : su, -jd);
+                v[e + 1] = fmaf(d[e + 1], nu_ ? su : sl, -jd);
                 v[e + NR - 1] = jd;
               } else {
-                v[e] = d[e] * (d[e] >= 0.f ? sl : su);
-                v[e + 1] = d[e + 1] * (d[e + 1] >= 0.f ? su : sl);
+                v[e] = d[e] * (nl ? sl : su);
+                v[e + 1] = d[e + 1] * (nu_ ? su : sl);
               }
             }
 #pragma unroll
@@ -361,9 +370,15 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
               if (h < nch) put8(r0 + 8 * h, j, v + 8 * h);
             if (live)
 #pragma unroll
-              for (int e = 0; e < GS; e += 4)
-                if (r0 + e < 128)
-                  *reinterpret_cast<float4*>(lrow + r0 + e) = make_float4(d[e], d[e + 1], d[e + 2], d[e + 3]);
+              for (int h = 0; h < NR; ++h)
+                if (h < nch) {
+                  uint4 q4;
+                  q4.x = (uint32_t)__half_as_ushort(lh[8 * h]) | ((uint32_t)__half_as_ushort(lh[8 * h + 1]) << 16);
+                  q4.y = (uint32_t)__half_as_ushort(lh[8 * h + 2]) | ((uint32_t)__half_as_ushort(lh[8 * h + 3]) << 16);
+                  q4.z = (uint32_t)__half_as_ushort(lh[8 * h + 4]) | ((uint32_t)__half_as_ushort(lh[8 * h + 5]) << 16);
+                  q4.w = (uint32_t)__half_as_ushort(lh[8 * h + 6]) | ((uint32_t)__half_as_ushort(lh[8 * h + 7]) << 16);
+                  *reinterpret_cast<uint4*>(lrow + r0 + 8 * h) = q4;
+                }
           }
         }
         operand_ready();
@@ -416,6 +431,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
         operand_ready();
       }
       // ---- backward stages k = 0 .. target-1 -------------------------------------------------------
+      // The thread's two neurons go side by side through packed FP32x2 arithmetic.
       for (int k = 0; k < target; ++k) {
         if (!wait_acc()) return false;
         const int N = a.widths[k + 1];            // neurons of hidden layer k
@@ -426,10 +442,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
           bool live[2];
           long long o[2];
           float sl[2], su[2], tlv[2], tu[2], dd[2];
-          const float* lrow[2];
+          const __half* lrow[2];
           const float* wcol[2];
-          float gsl[2] = {0.f, 0.f}, gsu[2] = {0.f, 0.f}, gtl[2] = {0.f, 0.f}, gtu[2] = {0.f, 0.f}, gd[2] = {0.f, 0.f};
-          float wv[2] = {0.f, 0.f};   // lambda_{target-1} of the current row group (last stage)
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             const int j = nrn0 + 256 * u;
@@ -443,70 +457,98 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
             lrow[u] = scr + (size_t)((last ? 0 : a.soff[k]) + (live[u] ? j : 0)) * 128;
             wcol[u] = a.W_target + (live[u] ? j : 0);
           }
-          // 8-row chunks; the roles of a chunk's rows as bit masks (bit e: row rb + e): Jacobian rows, and
+          const float2 dd2 = make_float2(dd[0], dd[1]);
+          float2 SL = make_float2(0.f, 0.f), SU = SL, TL = SL, TU = SL, GD = SL;
+          float2 wv = SL;   // lambda_{target-1} of the current row group (last stage), carried across chunks
+          // 16-row chunks; the roles of a chunk's rows as bit masks (bit e: row rb + e): Jacobian rows, and
           // rows whose lower line is chosen when lambda >= 0 (lower-bound rows)
 #pragma unroll 1
-          for (int rb = 0; rb < 128; rb += 8) {
+          for (int rb = 0; rb < 128; rb += 16) {
             const int off = rb % NR;       // role of row rb (tiles start on a row group)
             // role-0 rows: e = -off mod NR (+ NR, ...); Jacobian rows (NR = 3): e = 2 - off mod 3 (+ 3, ...)
-            const uint32_t lm = NR == 3 ? (0x49u << ((3 - off) % 3)) & 0xFFu : (off == 0 ? 0x55u : 0xAAu);
-            const uint32_t jm = NR == 3 ? (0x49u << ((5 - off) % 3)) & 0xFFu : 0u;
-            float ga[2][8], lam[2][8], g[8];
-#pragma unroll
-            for (int u = 0; u < 2; ++u)
-              if (u < nu) tmem_ld8_nowait(t_lane + 256u * u + (uint32_t)rb, ga[u]);
+            const uint32_t lm = NR == 3 ? (0x9249u << ((3 - off) % 3)) & 0xFFFFu : (off == 0 ? 0x5555u : 0xAAAAu);
+            const uint32_t jm = NR == 3 ? (0x9249u << ((5 - off) % 3)) & 0xFFFFu : 0u;
+            float ga0[16], ga1[16], l0[16], l1[16], g[16];
+            tmem_ld16_nowait(t_lane + (uint32_t)rb, ga0);
+            if (nu > 1) tmem_ld16_nowait(t_lane + 256u + (uint32_t)rb, ga1);
             if (!last) {
 #pragma unroll
-              for (int u = 0; u < 2; ++u)
-                if (u < nu)
+              for (int e = 0; e < 16; e += 8) {
+                const uint4 v = *reinterpret_cast<const uint4*>(lrow[0] + rb + e);
+                const uint4 w = nu > 1 ? *reinterpret_cast<const uint4*>(lrow[1] + rb + e) : make_uint4(0u, 0u, 0u, 0u);
+                const uint32_t vv[4] = {v.x, v.y, v.z, v.w}, ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-                  for (int e = 0; e < 8; e += 4) {
-                    const float4 v = *reinterpret_cast<const float4*>(lrow[u] + rb + e);
-                    lam[u][e] = v.x; lam[u][e + 1] = v.y; lam[u][e + 2] = v.z; lam[u][e + 3] = v.w;
-                  }
+                for (int h = 0; h < 4; ++h) {
+                  const float2 a2 = __half22float2(*reinterpret_cast<const __half2*>(&vv[h]));
+                  const float2 b2 = __half22float2(*reinterpret_cast<const __half2*>(&ww[h]));
+                  l0[e + 2 * h] = a2.x; l0[e + 2 * h + 1] = a2.y;
+                  l1[e + 2 * h] = b2.x; l1[e + 2 * h + 1] = b2.y;
+                }
+              }
             } else {
               // lambda_{target-1}: the W_target row of each row's state, loaded at the group's first row
               // (role 0) and carried to the group's other rows, also across chunks
 #pragma unroll
-              for (int u = 0; u < 2; ++u)
-                if (u < nu)
-#pragma unroll
-                  for (int e = 0; e < 8; ++e) {
-                    if ((lm >> e) & 1u) {
-                      const int r = rb + e;
-                      wv[u] = (live[u] && r + NR - 1 < nrows) ? __ldg(wcol[u] + (long long)((row0 + r) / NR) * Kt)
-                                                              : 0.f;
-                    }
-                    lam[u][e] = wv[u];
-                  }
+              for (int e = 0; e < 16; ++e) {
+                if ((lm >> e) & 1u) {
+                  const int r = rb + e;
+                  const bool grp = r + NR - 1 < nrows;
+                  const long long wo = (long long)((row0 + r) / NR) * Kt;
+                  wv.x = (live[0] && grp) ? __ldg(wcol[0] + wo) : 0.f;
+                  wv.y = (live[1] && grp) ? __ldg(wcol[1] + wo) : 0.f;
+                }
+                l0[e] = wv.x;
+                l1[e] = wv.y;
+              }
             }
 #pragma unroll
-            for (int e = 0; e < 8; e += 4) {
+            for (int e = 0; e < 16; e += 4) {
               const float4 v = *reinterpret_cast<const float4*>(gw + rb + e);
               g[e] = v.x * ginv; g[e + 1] = v.y * ginv; g[e + 2] = v.z * ginv; g[e + 3] = v.w * ginv;
             }
             tmem_wait_ld();
+            if (nu < 2)
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              if (u >= nu) continue;
-              float gv[8];
+              for (int e = 0; e < 16; ++e) ga1[e] = 0.f;
+            float G0[16], G1[16];
 #pragma unroll
-              for (int e = 0; e < 8; ++e) {
-                const bool isJ = (jm >> e) & 1u, isL = (lm >> e) & 1u;
-                const float l = lam[u][e], x = ga[u][e];
-                const bool useL = isL == (l >= 0.f);
-                const float p1 = x * l, p2 = g[e] * l;
-                const bool cl = !isJ && useL, cu = !isJ && !useL;
-                gsl[u] += cl ? p1 : 0.f;
-                gtl[u] += cl ? p2 : 0.f;
-                gsu[u] += cu ? p1 : 0.f;
-                gtu[u] += cu ? p2 : 0.f;
-                gd[u] += isJ ? p1 : 0.f;
-                gv[e] = isJ ? x * dd[u] : fmaf(x, useL ? sl[u] : su[u], g[e] * (useL ? tlv[u] : tu[u]));
+            for (int e = 0; e < 16; ++e) {
+              const bool isJ = (jm >> e) & 1u, isL = (lm >> e) & 1u;
+              const float2 x = make_float2(ga0[e], ga1[e]), l = make_float2(l0[e], l1[e]);
+              const float2 gg = make_float2(g[e], g[e]);
+              const float2 p1 = __fmul2_rn(x, l), p2 = __fmul2_rn(gg, l);
+              // lower line chosen (sg) / upper line chosen (ng); both 0 on Jacobian rows. The choice is
+              // the sign bit of the stored lambda, as in the forward recompute.
+              const bool u0 = isL == !signbit(l.x), u1 = isL == !signbit(l.y);
+              const float2 sg = make_float2(!isJ && u0 ? 1.f : 0.f, !isJ && u1 ? 1.f : 0.f);
+              const float2 ng = make_float2(!isJ && !u0 ? 1.f : 0.f, !isJ && !u1 ? 1.f : 0.f);
+              SL = __ffma2_rn(sg, p1, SL);
+              SU = __ffma2_rn(ng, p1, SU);
+              TL = __ffma2_rn(sg, p2, TL);
+              TU = __ffma2_rn(ng, p2, TU);
+              float2 G;
+              if (isJ) {
+                GD = __fadd2_rn(GD, p1);
+                G = __fmul2_rn(x, dd2);
+              } else {
+                const float2 sv = make_float2(u0 ? sl[0] : su[0], u1 ? sl[1] : su[1]);
+                const float2 tv = make_float2(u0 ? tlv[0] : tu[0], u1 ? tlv[1] : tu[1]);
+                G = __ffma2_rn(x, sv, __fmul2_rn(gg, tv));
               }
-              if (!last) put8(rb, nrn0 + 256 * u, gv);
+              G0[e] = G.x;
+              G1[e] = G.y;
+            }
+            if (!last) {
+              put8(rb, nrn0, G0);
+              put8(rb + 8, nrn0, G0 + 8);
+              if (nu > 1) {
+                put8(rb, nrn0 + 256, G1);
+                put8(rb + 8, nrn0 + 256, G1 + 8);
+              }
             }
           }
+          const float gsl[2] = {SL.x, SL.y}, gsu[2] = {SU.x, SU.y}, gtl[2] = {TL.x, TL.y}, gtu[2] = {TU.x, TU.y};
+          const float gd[2] = {GD.x, GD.y};
 #pragma unroll
           for (int u = 0; u < 2; ++u)
             if (live[u]) {
@@ -645,7 +687,7 @@ size_t adj_tc_scratch_floats(const Ctx& c) {
   const MlpModel& m = c.mlp;
   size_t stot = 0;
   for (int k = 0; k + 2 < m.L; ++k) stot += m.widths[k + 1];   // lambda_0 .. lambda_{L-3}
-  return (size_t)c.sm_count * stot * 128;
+  return (size_t)c.sm_count * stot * 64;   // FP16: two per float
 }
 
 leb_status adj_tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, const float* radii,
@@ -694,7 +736,7 @@ leb_status adj_tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* 
   a.gtU = ws + L.gtU;
   a.gD = ws + L.gD;
   a.grho = ws + L.grho;
-  a.scratch = ws + L.adj;
+  a.scratch = reinterpret_cast<__half*>(ws + L.adj);
   a.flags = flags;
   const int items = T * a.tiles_per_t;
   const int grid = items < c.sm_count ? items : c.sm_count;
