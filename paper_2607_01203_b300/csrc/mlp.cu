@@ -203,23 +203,31 @@ struct NomArgs {
 
 constexpr int kNomBT = 64, kNomBN = 64;
 
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ float2 abs2(float2 v) { return make_float2(fabsf(v.x), fabsf(v.y)); }
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+
 __global__ void __launch_bounds__(256) mlp_nominal_kernel(NomArgs a) {
-  __shared__ float s_in[kKC][kNomBT + 4];
-  __shared__ float s_q[kKC][kNomBT + 4];
-  __shared__ float s_ab[kKC][kNomBT + 4];
-  __shared__ float s_dl[kKC][kNomBT + 4];
-  __shared__ float s_dh[kKC][kNomBT + 4];
-  __shared__ float s_w[kKC][kNomBN + 4];
+  __shared__ __align__(16) float s_in[kKC][kNomBT + 4];
+  __shared__ __align__(16) float s_q[kKC][kNomBT + 4];
+  __shared__ __align__(16) float s_ab[kKC][kNomBT + 4];
+  __shared__ __align__(16) float s_dl[kKC][kNomBT + 4];
+  __shared__ __align__(16) float s_dh[kKC][kNomBT + 4];
+  __shared__ __align__(16) float s_w[kKC][kNomBN + 4];
+  __shared__ __align__(16) float s_we[kKC][kNomBN + 4];   // |W - W~| (operand rounding of the weight)
   const int t0 = blockIdx.x * kNomBT, c0 = blockIdx.y * kNomBN;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // thread owns t = t0 + 4ty.., c = c0 + 4tx..
   // compensated dot products (TwoProduct via FMA + TwoSum, Ogita-Rump-Oishi "Dot2"): the value is
   // as accurate as if computed in twice the working precision, with the rigorous bound
-  // |res - exact| <= u |res| + 2 gamma_K^2 sum |w| |x| (slack of 2 covers res vs exact in the first term)
-  float sum[4][4], cmp[4][4], err[4][4], vv[4][4], vw[4][4], blo[4][4], bhi[4][4];
+  // |res - exact| <= u |res| + 2 gamma_K^2 sum |w| |x| (slack of 2 covers res vs exact in the first term).
+  // The thread's 4 x 4 outputs run as 4 x 2 pairs of columns in packed FP32x2 arithmetic (each
+  // component rounds exactly as the scalar operation would).
+  float2 sum[4][2], cmp[4][2], err[4][2], vv[4][2], vw[4][2], blo[4][2], bhi[4][2];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) sum[i][j] = cmp[i][j] = err[i][j] = vv[i][j] = vw[i][j] = blo[i][j] = bhi[i][j] = 0.f;
+    for (int j = 0; j < 2; ++j)
+      sum[i][j] = cmp[i][j] = err[i][j] = vv[i][j] = vw[i][j] = blo[i][j] = bhi[i][j] = make_float2(0.f, 0.f);
 
   for (int k0 = 0; k0 < a.K; k0 += kKC) {
     // load the input tile (transposed: s_x[k][t]) and the weight tile (s_w[k][c])
@@ -249,49 +257,53 @@ __global__ void __launch_bounds__(256) mlp_nominal_kernel(NomArgs a) {
     for (int e = threadIdx.x; e < kKC * kNomBN; e += 256) {
       const int cc = e / kKC, kk = e - cc * kKC;
       const int c = c0 + cc, k = k0 + kk;
-      s_w[kk][cc] = (c < a.N && k < a.K) ? a.W[(long long)c * a.K + k] : 0.f;
+      const float w = (c < a.N && k < a.K) ? a.W[(long long)c * a.K + k] : 0.f;
+      s_w[kk][cc] = w;
+      float we = 0.f;
+      if (a.op_fmt == 0) we = fabsf(w - __half2float(__float2half_rn(w)));
+      else if (a.op_fmt == 1) we = fabsf(w - __bfloat162float(__float2bfloat16_rn(w)));
+      s_we[kk][cc] = we;
     }
     __syncthreads();
 #pragma unroll 2
     for (int kk = 0; kk < kKC; ++kk) {
-      float w[4], x[4], q[4], ab[4], we[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        w[j] = s_w[kk][4 * tx + j];
-        if (a.op_fmt == 0) we[j] = fabsf(w[j] - __half2float(__float2half_rn(w[j])));
-        else if (a.op_fmt == 1) we[j] = fabsf(w[j] - __bfloat162float(__float2bfloat16_rn(w[j])));
-        else we[j] = 0.f;
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        x[i] = s_in[kk][4 * ty + i];
-        q[i] = s_q[kk][4 * ty + i];
-        ab[i] = s_ab[kk][4 * ty + i];
-      }
+      const float4 w4 = *reinterpret_cast<const float4*>(&s_w[kk][4 * tx]);
+      const float4 e4 = *reinterpret_cast<const float4*>(&s_we[kk][4 * tx]);
+      const float4 x4 = *reinterpret_cast<const float4*>(&s_in[kk][4 * ty]);
+      const float4 q4 = *reinterpret_cast<const float4*>(&s_q[kk][4 * ty]);
+      const float4 a4 = *reinterpret_cast<const float4*>(&s_ab[kk][4 * ty]);
+      const float2 w2[2] = {make_float2(w4.x, w4.y), make_float2(w4.z, w4.w)};
+      const float2 wa2[2] = {abs2(w2[0]), abs2(w2[1])};
+      const float2 we2[2] = {make_float2(e4.x, e4.y), make_float2(e4.z, e4.w)};
+      const float x[4] = {x4.x, x4.y, x4.z, x4.w}, q[4] = {q4.x, q4.y, q4.z, q4.w};
+      const float ab[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < 2; ++j) {
           // explicit round-to-nearest intrinsics: the error-free transformations must not be contracted
-          const float pr = __fmul_rn(w[j], x[i]);
-          const float pe = fmaf(w[j], x[i], -pr);      // exact: w x = pr + pe
-          const float t1 = __fadd_rn(sum[i][j], pr);   // TwoSum(sum, pr) = t1 + se exactly
-          const float z = __fsub_rn(t1, sum[i][j]);
-          const float se = __fadd_rn(__fsub_rn(sum[i][j], __fsub_rn(t1, z)), __fsub_rn(pr, z));
+          const float2 xx = dup2(x[i]);
+          const float2 pr = __fmul2_rn(w2[j], xx);
+          const float2 pe = __ffma2_rn(w2[j], xx, neg2(pr));                 // exact: w x = pr + pe
+          const float2 t1 = __fadd2_rn(sum[i][j], pr);                       // TwoSum(sum, pr) = t1 + se
+          const float2 z = __fadd2_rn(t1, neg2(sum[i][j]));
+          const float2 se = __fadd2_rn(__fadd2_rn(sum[i][j], neg2(__fadd2_rn(t1, neg2(z)))), __fadd2_rn(pr, neg2(z)));
           sum[i][j] = t1;
-          cmp[i][j] = __fadd_rn(cmp[i][j], __fadd_rn(pe, se));
-          err[i][j] = __fmaf_ru(fabsf(w[j]), q[i], err[i][j]);
-          vv[i][j] = __fmaf_ru(fabsf(w[j]), ab[i], vv[i][j]);
-          vw[i][j] = __fmaf_ru(we[j], ab[i], vw[i][j]);
+          cmp[i][j] = __fadd2_rn(cmp[i][j], __fadd2_rn(pe, se));
+          err[i][j] = __ffma2_ru(wa2[j], dup2(q[i]), err[i][j]);
+          vv[i][j] = __ffma2_ru(wa2[j], dup2(ab[i]), vv[i][j]);
+          vw[i][j] = __ffma2_ru(we2[j], dup2(ab[i]), vw[i][j]);
         }
       if (a.first) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const float dl = s_dl[kk][4 * ty + i], dh = s_dh[kk][4 * ty + i];
+          const float2 dl = dup2(s_dl[kk][4 * ty + i]), dh = dup2(s_dh[kk][4 * ty + i]);
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            blo[i][j] = __fadd_rd(blo[i][j], fminf(__fmul_rd(w[j], dl), __fmul_rd(w[j], dh)));
-            bhi[i][j] = __fadd_ru(bhi[i][j], fmaxf(__fmul_ru(w[j], dl), __fmul_ru(w[j], dh)));
+          for (int j = 0; j < 2; ++j) {
+            const float2 l1 = __fmul2_rd(w2[j], dl), l2 = __fmul2_rd(w2[j], dh);
+            const float2 h1 = __fmul2_ru(w2[j], dl), h2 = __fmul2_ru(w2[j], dh);
+            blo[i][j] = __fadd2_rd(blo[i][j], make_float2(fminf(l1.x, l2.x), fminf(l1.y, l2.y)));
+            bhi[i][j] = __fadd2_ru(bhi[i][j], make_float2(fmaxf(h1.x, h2.x), fmaxf(h1.y, h2.y)));
           }
         }
       }
@@ -307,22 +319,29 @@ __global__ void __launch_bounds__(256) mlp_nominal_kernel(NomArgs a) {
       const int c = c0 + 4 * tx + j;
       if (c >= a.N) continue;
       const float bias = a.b[c];
+      const float sm = (j & 1) ? sum[i][j >> 1].y : sum[i][j >> 1].x;
+      const float cm = (j & 1) ? cmp[i][j >> 1].y : cmp[i][j >> 1].x;
+      const float er = (j & 1) ? err[i][j >> 1].y : err[i][j >> 1].x;
+      const float v1 = (j & 1) ? vv[i][j >> 1].y : vv[i][j >> 1].x;
+      const float v2 = (j & 1) ? vw[i][j >> 1].y : vw[i][j >> 1].x;
+      const float bl = (j & 1) ? blo[i][j >> 1].y : blo[i][j >> 1].x;
+      const float bh = (j & 1) ? bhi[i][j >> 1].y : bhi[i][j >> 1].x;
       // add the bias as one more compensated term, then round the compensated sum once
-      const float t1 = __fadd_rn(sum[i][j], bias);
-      const float z = __fsub_rn(t1, sum[i][j]);
-      const float se = __fadd_rn(__fsub_rn(sum[i][j], __fsub_rn(t1, z)), __fsub_rn(bias, z));
-      const float zh = __fadd_rn(t1, __fadd_rn(cmp[i][j], se));
+      const float t1 = __fadd_rn(sm, bias);
+      const float z = __fsub_rn(t1, sm);
+      const float se = __fadd_rn(__fsub_rn(sm, __fsub_rn(t1, z)), __fsub_rn(bias, z));
+      const float zh = __fadd_rn(t1, __fadd_rn(cm, se));
       // |zh - z~| <= u |zh| (final rounding, doubled) + gam2 (sum |w||x| + |b|) + sum |w| rad
-      float e = __fmaf_ru(a.gam, fabsf(bias), err[i][j]);
+      float e = __fmaf_ru(a.gam, fabsf(bias), er);
       e = __fmaf_ru(1.2e-7f, fabsf(zh), e);
       const long long o = (long long)t * a.ld_out + c;
       a.zhat[o] = zh;
       a.zrad[o] = e;
-      a.v1[o] = vv[i][j];
-      if (a.v2) a.v2[o] = vw[i][j];
+      a.v1[o] = v1;
+      if (a.v2) a.v2[o] = v2;
       if (a.first) {
-        a.lo[o] = __fadd_rd(__fsub_rd(zh, e), blo[i][j]);
-        a.hi[o] = __fadd_ru(__fadd_ru(zh, e), bhi[i][j]);
+        a.lo[o] = __fadd_rd(__fsub_rd(zh, e), bl);
+        a.hi[o] = __fadd_ru(__fadd_ru(zh, e), bh);
       }
       // post-activation of the nominal and its enclosure radius
       float hh, hr;
