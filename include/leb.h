@@ -47,7 +47,7 @@ typedef enum {
   LEB_OK = 0,
   LEB_ERR_INVALID_ARG = -1,   /* a pointer, size or enum value is invalid                       */
   LEB_ERR_UNSUPPORTED = -2,   /* valid request that this build does not implement                */
-  LEB_ERR_WORKSPACE = -3,     /* workspace NULL or smaller than leb_workspace_size()             */
+  LEB_ERR_WORKSPACE = -3,     /* workspace NULL, not 256-byte aligned, or too small             */
   LEB_ERR_CUDA = -4,          /* a CUDA runtime call or kernel launch failed                     */
   LEB_ERR_TIMEOUT = -5        /* reserved for host-side waits (device waits report via flags)    */
 } leb_status;
@@ -137,7 +137,8 @@ leb_status leb_workspace_size(leb_handle h, int T_max, size_t* bytes);
 /* ---- forward bounds (Thm. 1 / Thm. 2-3) -------------------------------------------------------- */
 /* x_nom [T, n_x], u_nom [T, n_u]: nominal points (device). r_lo, r_hi [T, n_x] (device, written).
  * A [T, n_x, n_x], B [T, n_x, n_u] (device, written) or NULL to skip writing them (the bound is then
- * sound for the FP32 values that would have been written). workspace: device, >= leb_workspace_size.
+ * sound for the FP32 values that would have been written). workspace: device, 256-byte aligned,
+ * >= leb_workspace_size.
  * dev_flags: device int (cleared, then OR-ed with leb_async_flag bits). */
 leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* x_nom, const float* u_nom,
                       const leb_set* set, float* r_lo, float* r_hi, float* A, float* B,

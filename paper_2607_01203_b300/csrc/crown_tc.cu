@@ -5,19 +5,33 @@
 // upper, Jacobian} so that the three rows of a state dimension share a tile) and carries it through
 // every back-substitution stage on chip:
 //   A_k = Lambda o s_k (sign-selected slopes, FP16 or BF16, 128 x K in shared memory, 128-byte swizzle)
-//   Lambda' = A_k W_k  (tcgen05.mma, FP32 accumulators in TMEM: 128 lanes x N <= 512 columns)
-// Warp roles: warp 0 streams W_k^T tiles with TMA (ring of NSB stages), warp 1 allocates TMEM and one of
-// its threads issues the MMAs, warps 2..9 run the epilogue (two warps per TMEM lane quarter, each on one
-// half of the columns): they read Lambda' out of TMEM, apply the next layer's selected slopes, accumulate
-// the offsets beta and the rounding inflation, and write the next A operand; after the last stage they
-// concretise over the displacement box.
+//   Lambda' = A_k W_k  (tcgen05.mma, FP32 accumulators in TMEM)
+// Upper-bound rows carry the negated chain (-Lambda^U): an upper bound of Lambda^U h is minus a lower
+// bound of (-Lambda^U) h, so every bound row runs the lower-bound arithmetic (lower line where the
+// coefficient is >= 0, every sum rounded down) and the upper bound is negated at the end. Lower and
+// upper rows of a warp then execute the same instructions.
+//
+// Pipeline. A stage's product (N <= 512 columns) is issued as one or two jobs of <= 256 columns; jobs
+// alternate between the two halves of TMEM (columns 0-255 and 256-511), so the epilogue of one job runs
+// while the tensor cores compute the next. The epilogue turns a job's columns into K-blocks (64 columns)
+// of the next stage's operand and writes each block as soon as the current stage's last job has read the
+// old block there (one "free" barrier per block, committed by the tensor cores); the next stage's first
+// job starts on a block as soon as it is written (one "ready" barrier per block). The next timestep's
+// prologue (its first operand) is built before the current timestep's final concretisation, so the
+// tensor cores start the next tile while the epilogue concretises.
+// Warp roles: warp 0 streams W_k^T tiles (128 rows x 64 K) with TMA through a ring of kTcNSB stages,
+// warp 1 allocates TMEM and one of its threads issues the MMAs, warps 2..17 run the epilogue (four warps
+// per TMEM lane quarter, each on one 16-column chunk of every 64-column block).
 //
 // Rigour of the reduced-precision GEMM (per stage, per row): with A~ the rounded operand, W~ the rounded
 // weights and the FP32 accumulation error bounded by gamma_K |A~| |W~| (u = 2^-23, i.e. without assuming
 // round-to-nearest accumulation), the computed Lambda' differs from the exact (Lambda o s) W_k by at most
 //   gamma_K |A~| |W~| + |A~ - Lambda o s| |W~| + |Lambda o s| |W~ - W|,
-// and its effect on Lambda' dh_{k-1} is bounded with the per-neuron vectors v1 = |W| abar and
-// v2 = |W - W~| abar (|W~| <= |W| (1 + 2^-10)); the sum is subtracted from (added to) the bound.
+// and its effect on Lambda' dh_{k-1} is bounded by sum_j |Lambda_j s_j| w_j with the per-neuron weight
+// w_j (from v1 = |W| abar and v2 = |W - W~| abar, |W~| <= |W| (1 + 2^-10)). The weight is folded into the
+// offsets: with tau'_L = tau_L - |s_L| w (rounded down) and tau'_U = tau_U + |s_U| w (rounded up),
+// Lambda_j tau'_sel <= Lambda_j tau_sel - |Lambda_j s_sel| w_j for either sign of Lambda_j, so the one
+// rounded-down accumulation of Lambda_j tau'_sel carries both the relaxation offsets and the inflation.
 #include <cmath>
 #include <cstdio>
 
@@ -31,18 +45,24 @@
 
 namespace leb {
 
-constexpr int kTcEpiWarps = 16;                 // 4 per TMEM lane quarter, 16-column chunks round-robin
+constexpr int kTcEpiWarps = 16;                 // 4 per TMEM lane quarter, one 16-column chunk of each block
 constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
-constexpr int kTcNSB = 2;                       // B ring stages
-constexpr int kTcBStage = 256 * 128;            // 256 rows x 64 K x 2 bytes
-constexpr int kTcARegion = 128 * 512 * 2;       // 128 rows x 512 K x 2 bytes
-constexpr int kTcVec = 512 * 24;                // per-neuron vectors of one stage: float4 + float2
-constexpr int kTcStat = 128 * 4 * 4 * 4;        // [row][column quarter][4]
-constexpr int kTcSmem = 1024 + kTcARegion + kTcNSB * kTcBStage + 2 * kTcVec + kTcStat + 256;
+constexpr int kTcNSB = 4;                       // B ring stages
+constexpr int kTcBRows = 128;                   // N rows of one B tile
+constexpr int kTcBStage = kTcBRows * 128;       // 128 rows x 64 K x 2 bytes
+constexpr int kTcARegion = 128 * 512 * 2;       // 128 rows x 512 K x 2 bytes (8 blocks of 16 KB)
+constexpr int kTcVecBuf = 512 * 16 + 512 * 4 + 512 * 4;   // per-neuron vectors: {sL, sU, tau'L, tau'U}, D, w
+constexpr int kTcStat = 128 * 4 * 3 * 4;        // [row][column group][3]
+constexpr int kTcVals = 2 * 128 * 4;            // [128] final values, [128] stated slack
+constexpr int kTcXch = 4 * 2 * 2 * 16 * 4;      // [column group][buffer][slot][16] Jacobian values
+constexpr int kTcNBar = 2 * kTcNSB + 8 + 8 + 2 + 2 + 1 + 1 + 4;
+constexpr int kTcSmem = 1024 + kTcARegion + kTcNSB * kTcBStage + 2 * kTcVecBuf + kTcStat + kTcVals + kTcXch +
+                        kTcNBar * 8;
 static_assert(kTcSmem <= 227 * 1024, "tensor-core chain shared memory");
 
 struct TcArgs {
-  CUtensorMap tmap[kMaxLayers];  // W_k^T in FP16/BF16: [widths[k] rows, widths[k+1] cols], box {64, Nbox}
+  CUtensorMap tmap[kMaxLayers];  // W_k^T in FP16/BF16: [widths[k] rows, widths[k+1] cols], box {64, brows[k]}
+  int brows[kMaxLayers];         // rows of a B tile of W_k^T: min(128, widths[k])
   int L;
   int widths[kMaxLayers + 1];
   int residual;
@@ -53,7 +73,7 @@ struct TcArgs {
   const float* W_target;
   const float *zhat, *zrad, *sL, *tL, *sU, *tU, *D, *winf, *ucon, *dlo, *dhi;
   const int* bad;
-  float *lo, *hi, *bslack;
+  float *lo, *hi;
   float *r_lo, *r_hi, *A, *B, *eps, *gamma_c, *gamma_r;
   float gamma_pad;
   int tight;                     // 1: no rounding inflation (the adjoint's recompute; not a sound bound)
@@ -79,53 +99,79 @@ __device__ __forceinline__ uint32_t pack2(float x, float y, int fmt) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// Row pass over 16 columns (row role: 0 lower, 1 upper, 2 Jacobian). sv[j] = {sL, sU, tauL, tauU},
-// sw[j] = {inflation weight of neuron j, sigma'(z^_j)} of the hidden layer Lambda acts on.
-__device__ __forceinline__ void row_pass16(int role, int j0, const float lam[16], const float4* sv, const float2* sw,
-                                           int fmt, uint32_t packed[8], float& beta0, float& beta1, float& infl0,
-                                           float& infl1) {
-  float av[16];
-  if (role == 2) {
+// Row pass over 16 columns j0..j0+15 of a chain row (lam: this row's coefficients on the neurons of the
+// hidden layer whose vectors are staged). sv[j] = {sL, sU, tau'L, tau'U}, sd[j] = sigma'(z^_j),
+// sw[j] = inflation weight. Bound rows take the lower line where lam >= 0, else the upper line; Jacobian
+// rows (OUT only) take sigma'. Writes the next operand lam o s (packed pairs) and accumulates
+// beta += lam tau' rounded down (and, EPS, the inflation sum |lam s| w rounded up, for the stated slack).
+template <bool OUT, bool EPS>
+__device__ __forceinline__ void row_pass16(const float lam[16], int j0, const float4* __restrict__ sv,
+                                           const float* __restrict__ sd, const float* __restrict__ sw, bool isJ,
+                                           int fmt, uint32_t packed[8], float2& beta, float2& infl) {
 #pragma unroll
-    for (int e = 0; e < 16; ++e) av[e] = lam[e] * sw[j0 + e].y;
-  } else {
-    const bool lower = role == 0;
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const float4 v = sv[j0 + e];
-      const float w = sw[j0 + e].x;
-      const float l = lam[e];
-      const bool use_lower = lower == (l >= 0.f);
-      const float s = use_lower ? v.x : v.y;
-      const float tau = use_lower ? v.z : v.w;
-      av[e] = l * s;
-      if (e & 1) {
-        beta1 = lower ? __fmaf_rd(l, tau, beta1) : __fmaf_ru(l, tau, beta1);
-        infl1 = __fmaf_ru(fabsf(av[e]), w, infl1);
-      } else {
-        beta0 = lower ? __fmaf_rd(l, tau, beta0) : __fmaf_ru(l, tau, beta0);
-        infl0 = __fmaf_ru(fabsf(av[e]), w, infl0);
-      }
+  for (int e = 0; e < 16; e += 2) {
+    const float4 v0 = sv[j0 + e], v1 = sv[j0 + e + 1];
+    const float2 l = make_float2(lam[e], lam[e + 1]);
+    const bool p0 = l.x >= 0.f, p1 = l.y >= 0.f;
+    float2 s = make_float2(p0 ? v0.x : v0.y, p1 ? v1.x : v1.y);
+    const float2 tau = make_float2(p0 ? v0.z : v0.w, p1 ? v1.z : v1.w);
+    if (OUT) {
+      const float2 d = *reinterpret_cast<const float2*>(sd + j0 + e);
+      s.x = isJ ? d.x : s.x;
+      s.y = isJ ? d.y : s.y;
     }
+    const float2 av = __fmul2_rn(l, s);
+    beta = __ffma2_rd(l, tau, beta);
+    if (EPS) {
+      const float2 w = *reinterpret_cast<const float2*>(sw + j0 + e);
+      infl = __ffma2_ru(make_float2(fabsf(av.x), fabsf(av.y)), w, infl);
+    }
+    packed[e >> 1] = pack2(av.x, av.y, fmt);
   }
-#pragma unroll
-  for (int e = 0; e < 8; ++e) packed[e] = pack2(av[2 * e], av[2 * e + 1], fmt);
 }
 
+// Role of a tile row.
+struct RowInfo {
+  bool valid;    // inside the tile and the target's rows
+  bool bound;    // lower or upper bound row
+  bool isJ;      // Jacobian row (output target)
+  bool neg;      // upper bound row: the chain is carried negated
+  int idx;       // neuron (hidden target) or state (output target)
+};
+
+__device__ __forceinline__ RowInfo row_info(const TcArgs& a, int tile, int r) {
+  RowInfo ri;
+  const int grow = tile * a.rows_per_tile + r;
+  ri.valid = r < a.rows_per_tile && grow < a.rows_total;
+  const int role = ri.valid ? grow % a.nroles : 3;
+  ri.idx = ri.valid ? grow / a.nroles : 0;
+  ri.bound = role < 2;
+  ri.isJ = role == 2;
+  ri.neg = role == 1;
+  return ri;
+}
+
+template <bool OUT, bool EPS>
 __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_constant__ TcArgs a) {
   extern __shared__ uint8_t sraw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sraw) + 1023) & ~uintptr_t(1023));
-  uint8_t* Asm = base;                                     // A operand (and the J-row buffer at the end)
+  uint8_t* Asm = base;                                     // A operand
   uint8_t* Bsm = base + kTcARegion;                        // B ring
-  uint8_t* Vsm = Bsm + kTcNSB * kTcBStage;                 // 2 x per-neuron vectors (double buffered)
-  float* stat = reinterpret_cast<float*>(Vsm + 2 * kTcVec);  // [128][4][4]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(stat) + kTcStat);
-  uint64_t* b_full = bars;                 // [kTcNSB]
-  uint64_t* b_empty = bars + kTcNSB;       // [kTcNSB]
-  uint64_t* a_full = bars + 2 * kTcNSB;    // operand written by the epilogue
-  uint64_t* acc_full = a_full + 1;         // accumulator complete
-  uint64_t* drain = acc_full + 1;
-  uint64_t* ebar = drain + 1;              // epilogue-warps barrier (bounded waits)
+  uint8_t* Vsm = Bsm + kTcNSB * kTcBStage;                 // 2 x per-neuron vectors
+  float* stat = reinterpret_cast<float*>(Vsm + 2 * kTcVecBuf);   // [128][4][3]
+  float* vals = stat + 128 * 12;                           // [128]
+  float* slk = vals + 128;                                 // [128]
+  float* xch = slk + 128;                                  // [4][2][2][16]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(xch + 4 * 2 * 2 * 16);
+  uint64_t* b_full = bars;                 // [kTcNSB]  B tile landed
+  uint64_t* b_empty = bars + kTcNSB;       // [kTcNSB]  B tile consumed
+  uint64_t* a_ready = bars + 2 * kTcNSB;   // [8]  operand block written by the epilogue
+  uint64_t* a_free = a_ready + 8;          // [8]  operand block read by the current stage's last job
+  uint64_t* acc_full = a_free + 8;         // [2]  TMEM half holds a finished job
+  uint64_t* acc_free = acc_full + 2;       // [2]  TMEM half read by the epilogue
+  uint64_t* drain = acc_free + 2;
+  uint64_t* ebar = drain + 1;              // epilogue-warps barrier
+  uint64_t* xbar = ebar + 1;               // [4]  per column group (Jacobian exchange)
   __shared__ uint32_t tmem_slot;
   __shared__ int s_abort;
 
@@ -138,10 +184,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       mbar_init(&b_full[s], 1);
       mbar_init(&b_empty[s], 1);
     }
-    mbar_init(a_full, kTcEpiWarps);
-    mbar_init(acc_full, 1);
+    for (int b = 0; b < 8; ++b) {
+      mbar_init(&a_ready[b], kTcEpiWarps);
+      mbar_init(&a_free[b], 1);
+    }
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(&acc_full[h], 1);
+      mbar_init(&acc_free[h], kTcEpiWarps);
+    }
     mbar_init(drain, 1);
     mbar_init(ebar, kTcEpiWarps);
+    for (int c = 0; c < 4; ++c) mbar_init(&xbar[c], 4);
     mbar_fence_init();
     s_abort = 0;
   }
@@ -151,6 +204,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
+  // Jobs of stage k (the product with W_k, N = widths[k] columns): one job if N <= 256, else two, split
+  // at a multiple of 64 so that every job of a hidden stage covers whole operand blocks.
+  auto stage_split = [&](int k) -> int {
+    const int N = a.widths[k];
+    return N > 256 ? 64 * ((N + 127) / 128) : N;
+  };
+
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
@@ -159,17 +219,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       bool ok = true;
       for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
         for (int k = target - 1; k >= 0 && ok; --k) {
-          const int K = a.widths[k + 1], N = a.widths[k];
-          const int nh = N > 256 ? 2 : 1, nbox = N / nh;
-          const int nkc = (K + 63) / 64;
-          for (int kc = 0; kc < nkc && ok; ++kc)
-            for (int h = 0; h < nh; ++h, ++kb) {
-              const int s = (int)(kb % kTcNSB);
-              if (kb >= (uint32_t)kTcNSB && !mbar_wait(&b_empty[s], ((kb / kTcNSB) - 1) & 1u)) { ok = false; break; }
-              if (*(volatile int*)&s_abort) { ok = false; break; }
-              mbar_arrive_expect_tx(&b_full[s], (uint32_t)nbox * 128u);
-              tma_load_2d(Bsm + (size_t)s * kTcBStage, &a.tmap[k], kc * 64, h * nbox, &b_full[s]);
-            }
+          const int N = a.widths[k], nK = a.widths[k + 1] / 64, split = stage_split(k);
+          for (int h = 0; h < (N > split ? 2 : 1) && ok; ++h) {
+            const int c0 = h ? split : 0, nc = h ? N - split : split;
+            const int nbt = (nc + kTcBRows - 1) / kTcBRows;
+            for (int kc = 0; kc < nK && ok; ++kc)
+              for (int bt = 0; bt < nbt; ++bt, ++kb) {
+                const int s = (int)(kb % kTcNSB);
+                if (kb >= (uint32_t)kTcNSB && !mbar_wait(&b_empty[s], ((kb / kTcNSB) - 1) & 1u)) { ok = false; break; }
+                if (*(volatile int*)&s_abort) { ok = false; break; }
+                mbar_arrive_expect_tx(&b_full[s], (uint32_t)a.brows[k] * 128u);
+                tma_load_2d(Bsm + (size_t)s * kTcBStage, &a.tmap[k], kc * 64, c0 + bt * kTcBRows, &b_full[s]);
+              }
+          }
         }
       }
       if (!ok) {
@@ -185,31 +247,47 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       const uint32_t a_base = smem_u32(Asm), b_base = smem_u32(Bsm);
-      uint32_t kb = 0, na = 0;
+      uint32_t kb = 0, jc = 0, rpar = 0, fpar = 0, used = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
         for (int k = target - 1; k >= 0 && ok; --k) {
-          const int K = a.widths[k + 1], N = a.widths[k];
-          const int nh = N > 256 ? 2 : 1, nbox = N / nh;
-          const int nkc = (K + 63) / 64;
-          const uint32_t idesc = idesc_f16(128, nbox, a.fmt);
-          if (!mbar_wait(a_full, na & 1u)) { ok = false; break; }
-          ++na;
-          tc_fence_after();
-          for (int kc = 0; kc < nkc && ok; ++kc)
-            for (int h = 0; h < nh; ++h, ++kb) {
-              const int s = (int)(kb % kTcNSB);
-              if (!mbar_wait(&b_full[s], (kb / kTcNSB) & 1u)) { ok = false; break; }
-              tc_fence_after();
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t ad = sw128_desc(a_base + kc * 16384 + kk * 32);
-                const uint64_t bd = sw128_desc(b_base + s * kTcBStage + kk * 32);
-                tc_mma_f16(tmem + (uint32_t)(h * nbox), ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-              }
-              tc_commit(&b_empty[s]);
+          const int N = a.widths[k], nK = a.widths[k + 1] / 64, split = stage_split(k);
+          const int nh = N > split ? 2 : 1;
+          for (int h = 0; h < nh && ok; ++h, ++jc) {
+            const int nc = h ? N - split : split;
+            const int nbt = (nc + kTcBRows - 1) / kTcBRows;
+            const uint32_t hb = jc & 1u;
+            if ((used >> hb) & 1u) {
+              if (!mbar_wait(&acc_free[hb], (fpar >> hb) & 1u)) { ok = false; break; }
+              fpar ^= 1u << hb;
             }
-          tc_commit(acc_full);
+            used |= 1u << hb;
+            tc_fence_after();
+            for (int kc = 0; kc < nK && ok; ++kc) {
+              if (h == 0) {
+                if (!mbar_wait(&a_ready[kc], (rpar >> kc) & 1u)) { ok = false; break; }
+                rpar ^= 1u << kc;
+                tc_fence_after();
+              }
+              for (int bt = 0; bt < nbt; ++bt, ++kb) {
+                const int s = (int)(kb % kTcNSB);
+                if (!mbar_wait(&b_full[s], (kb / kTcNSB) & 1u)) { ok = false; break; }
+                tc_fence_after();
+                const int nn = min(kTcBRows, nc - bt * kTcBRows);
+                const uint32_t idesc = idesc_f16(128, nn, a.fmt);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                  const uint64_t ad = sw128_desc(a_base + kc * 16384 + kk * 32);
+                  const uint64_t bd = sw128_desc(b_base + s * kTcBStage + kk * 32);
+                  tc_mma_f16(tmem + hb * 256u + (uint32_t)(bt * kTcBRows), ad, bd, idesc,
+                             (kc > 0 || kk > 0) ? 1u : 0u);
+                }
+                tc_commit(&b_empty[s]);
+              }
+              if (h == nh - 1) tc_commit(&a_free[kc]);
+            }
+            tc_commit(&acc_full[hb]);
+          }
         }
       }
       if (!ok) {
@@ -224,14 +302,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     // ---------------------------------------------------------------- epilogue warps
     const int ew = warp - 2;
     const int q = warp & 3;                 // TMEM lane quarter of this warp
-    const int cq = ew >> 2;                 // 16-column chunks cq, cq + 4, ...
+    const int cq = ew >> 2;                 // 16-column chunk of every 64-column block
     const int r = q * 32 + lane;            // tile row = TMEM lane
     const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16);
-    const int ethr = kTcEpiWarps * 32, etid = threadIdx.x - 64;
-    uint32_t nacc = 0, nbar = 0;
-    int vbuf = 0;
+    const int etid = threadIdx.x - 64;
+    const int n = a.widths[0];
+    const int n_x = a.widths[a.L];
+    const bool tight = a.tight != 0;
+    uint32_t nbar = 0, cpar = 0, apend = 0, apar = 0, xph = 0;
+    uint32_t jc = 0;
+    int vb = 0;                             // vector buffer installed next
     bool ok = true;
-    // all epilogue warps meet here; false if the wait ran out (then every later step is skipped)
+
     auto epi_sync = [&]() -> bool {
       __syncwarp();
       if (lane == 0) mbar_arrive(ebar);
@@ -239,216 +321,333 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       ++nbar;
       return res;
     };
-    // stage the per-neuron vectors of hidden layer hl of timestep t (or, hl < 0, the box) into buffer b
-    auto stage_vectors = [&](int t, int hl, int b) {
-      float4* sv = reinterpret_cast<float4*>(Vsm + b * kTcVec);
-      float2* sw = reinterpret_cast<float2*>(Vsm + b * kTcVec + 512 * 16);
-      if (hl >= 0) {
-        const int width = a.widths[hl + 1], wp = (width + 63) & ~63;
-        const long long o = (long long)t * a.H + a.hoff[hl];
-        for (int j = etid; j < wp; j += ethr) {
-          if (j < width) {
-            sv[j] = make_float4(a.sL[o + j], a.sU[o + j], a.tL[o + j], a.tU[o + j]);
-            sw[j] = make_float2(a.winf[o + j], a.D[o + j]);
-          } else {
-            sv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-            sw[j] = make_float2(0.f, 0.f);
-          }
-        }
-      } else {
-        const int n = a.widths[0];
-        const long long o = (long long)t * n;
-        for (int j = etid; j < n; j += ethr) sw[j] = make_float2(a.dlo[o + j], a.dhi[o + j]);
+    auto vbuf = [&](int b, const float4*& sv, const float*& sd, const float*& sw) {
+      uint8_t* p = Vsm + b * kTcVecBuf;
+      sv = reinterpret_cast<const float4*>(p);
+      sd = reinterpret_cast<const float*>(p + 512 * 16);
+      sw = reinterpret_cast<const float*>(p + 512 * 20);
+    };
+    // prefetched per-neuron values of the next vector set (neuron etid): sL, sU, tL, tU, w, D
+    float pf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int pf_width = 0, pf_wp = 0;
+    auto prefetch = [&](int t, int hl) {
+      const int width = a.widths[hl + 1];
+      pf_width = width;
+      pf_wp = (width + 63) & ~63;
+      if (etid < width) {
+        const long long o = (long long)t * a.H + a.hoff[hl] + etid;
+        pf[0] = a.sL[o];
+        pf[1] = a.sU[o];
+        pf[2] = a.tL[o];
+        pf[3] = a.tU[o];
+        pf[4] = tight ? 0.f : a.winf[o];
+        pf[5] = a.D[o];
       }
     };
-
-    for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
-      const int t = item / a.tiles_per_t, tile = item - t * a.tiles_per_t;
-      const int grow = tile * a.rows_per_tile + r;
-      const bool valid = r < a.rows_per_tile && grow < a.rows_total;
-      const int role = valid ? grow % a.nroles : 0;
-      const int idx = valid ? grow / a.nroles : 0;
-      float beta0 = 0.f, beta1 = 0.f, infl0 = 0.f, infl1 = 0.f, ucon = 0.f;
-
-      // ---- prologue: A for the stage that multiplies by W_{target-1}: W_target rows o slopes -------
-      {
-        const int K = a.widths[target], Kp = (K + 63) & ~63;
-        stage_vectors(t, target - 1, vbuf);
-        if (!epi_sync()) { ok = false; break; }
-        const float4* sv = reinterpret_cast<const float4*>(Vsm + vbuf * kTcVec);
-        const float2* sw = reinterpret_cast<const float2*>(Vsm + vbuf * kTcVec + 512 * 16);
-        const float* Wrow = a.W_target + (long long)idx * K;
-        for (int j0 = 16 * cq; j0 < Kp; j0 += 64) {
-          float lam[16];
-          if (valid && j0 + 16 <= K) {
-#pragma unroll
-            for (int e = 0; e < 16; e += 4) {
-              const float4 w4 = __ldg(reinterpret_cast<const float4*>(Wrow + j0 + e));
-              lam[e] = w4.x; lam[e + 1] = w4.y; lam[e + 2] = w4.z; lam[e + 3] = w4.w;
-            }
-          } else {
-#pragma unroll
-            for (int e = 0; e < 16; ++e) lam[e] = (valid && j0 + e < K) ? __ldg(Wrow + j0 + e) : 0.f;
-          }
-          uint32_t packed[8];
-          row_pass16(valid ? role : 2, j0, lam, sv, sw, a.fmt, packed, beta0, beta1, infl0, infl1);
-          store_a16(Asm, r, j0, packed);
+    // write the prefetched set into buffer vb (last read two sets ago: free since the last install)
+    auto install = [&]() -> bool {
+      uint8_t* p = Vsm + vb * kTcVecBuf;
+      float4* sv = reinterpret_cast<float4*>(p);
+      float* sd = reinterpret_cast<float*>(p + 512 * 16);
+      float* sw = reinterpret_cast<float*>(p + 512 * 20);
+      if (etid < pf_wp) {
+        if (etid < pf_width) {
+          const float w = pf[4];
+          const float tl = tight ? pf[2] : __fmaf_rd(-fabsf(pf[0]), w, pf[2]);
+          const float tu = tight ? pf[3] : __fmaf_ru(fabsf(pf[1]), w, pf[3]);
+          sv[etid] = make_float4(pf[0], pf[1], tl, tu);
+          sd[etid] = pf[5];
+          sw[etid] = w;
+        } else {
+          sv[etid] = make_float4(0.f, 0.f, 0.f, 0.f);
+          sd[etid] = 0.f;
+          sw[etid] = 0.f;
         }
-        // (the per-layer constant was summed with round-to-nearest atomics: 1.001 covers their rounding)
-        if (valid && role != 2) ucon = __fmaf_ru(1.001f, a.ucon[(long long)t * (a.L - 1) + target - 1], ucon);
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(a_full);
-        vbuf ^= 1;
       }
-      // ---- stages -------------------------------------------------------------------------------
-      for (int k = target - 1; k >= 0 && ok; --k) {
-        // stage the vectors of the next pass while the tensor cores work
-        stage_vectors(t, k - 1, vbuf);
-        if (!epi_sync()) { ok = false; break; }
-        if (!mbar_wait(acc_full, nacc & 1u)) { ok = false; break; }
-        ++nacc;
-        tc_fence_after();
-        const float4* sv = reinterpret_cast<const float4*>(Vsm + vbuf * kTcVec);
-        const float2* sw = reinterpret_cast<const float2*>(Vsm + vbuf * kTcVec + 512 * 16);
-        const int N = a.widths[k];
-        if (k > 0) {
-          const int Np = (N + 63) & ~63;
-          for (int j0 = 16 * cq; j0 < Np; j0 += 64) {
-            float lam[16];
-            if (j0 < N) tmem_ld16(t_lane + (uint32_t)j0, lam);
-            else
+      const bool res = epi_sync();
+      vb ^= 1;
+      return res;
+    };
+    // the set after the one just installed for (t, hl): the next hidden layer down, or the next item's
+    // prologue set
+    auto prefetch_next = [&](int t, int hl, int next_item) {
+      if (hl >= 1) prefetch(t, hl - 1);
+      else if (next_item < n_items) prefetch(next_item / a.tiles_per_t, target - 1);
+    };
+    auto wait_free = [&](int b) -> bool {
+      if ((apend >> b) & 1u) {
+        if (!mbar_wait(&a_free[b], (apar >> b) & 1u)) return false;
+        apar ^= 1u << b;
+        apend &= ~(1u << b);
+      }
+      return true;
+    };
+    auto block_ready = [&](int b) {
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&a_ready[b]);
+    };
+    auto wait_acc = [&](uint32_t hb) -> bool {
+      if (!mbar_wait(&acc_full[hb], (cpar >> hb) & 1u)) return false;
+      cpar ^= 1u << hb;
+      tc_fence_after();
+      return true;
+    };
+    auto release_acc = [&](uint32_t hb) {
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_free[hb]);
+    };
+    auto ucon_of = [&](int t, int hl) -> float {
+      return tight ? 0.f : __fmul_ru(1.001f, a.ucon[(long long)t * (a.L - 1) + hl]);
+    };
+
+    // prologue of an item: operand = W_target rows (negated for upper rows) o slopes of layer target-1
+    auto prologue = [&](int t, const RowInfo& ri, int vcur, float2& beta, float2& infl, float& ucon) -> bool {
+      const float4* sv;
+      const float* sd;
+      const float* sw;
+      vbuf(vcur, sv, sd, sw);
+      const int K = a.widths[target], nK = K / 64;
+      const float* Wrow = a.W_target + (long long)ri.idx * K;
+      const float sg = ri.neg ? -1.f : 1.f;
+      for (int b = 0; b < nK; ++b) {
+        const int j0 = 64 * b + 16 * cq;
+        float lam[16];
+        if (ri.valid) {
 #pragma unroll
-              for (int e = 0; e < 16; ++e) lam[e] = 0.f;
-            uint32_t packed[8];
-            row_pass16(valid ? role : 2, j0, lam, sv, sw, a.fmt, packed, beta0, beta1, infl0, infl1);
-            store_a16(Asm, r, j0, packed);
+          for (int e = 0; e < 16; e += 4) {
+            const float4 w4 = __ldg(reinterpret_cast<const float4*>(Wrow + j0 + e));
+            lam[e] = sg * w4.x; lam[e + 1] = sg * w4.y; lam[e + 2] = sg * w4.z; lam[e + 3] = sg * w4.w;
           }
-          if (valid && role != 2) ucon = __fmaf_ru(1.001f, a.ucon[(long long)t * (a.L - 1) + k - 1], ucon);
-          tc_fence_before();
-          fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(a_full);
-          vbuf ^= 1;
-          continue;
-        }
-        // ---- last stage: concretise over the displacement box (sw = {dlo, dhi}) ------------------
-        const int n = N;  // = widths[0]
-        const bool output = target == a.L - 1;
-        const int n_x = a.widths[a.L];
-        float* Jbuf = reinterpret_cast<float*>(Asm);  // [42][n + 1] Jacobian rows of this tile
-        const int jstride = n + 1;
-        const int l0 = output ? tile * (a.rows_per_tile / 3) : 0;
-        if (output) {
-          // Jacobian rows of an output tile go to shared memory first (TMEM loads are warp-collective,
-          // so every lane loads and only the Jacobian lanes store)
-          for (int j0 = 16 * cq; j0 < n; j0 += 64) {
-            float lam[16];
-            tmem_ld16(t_lane + (uint32_t)j0, lam);
-            if (valid && role == 2)
+        } else {
 #pragma unroll
-              for (int e = 0; e < 16; ++e) Jbuf[(idx - l0) * jstride + j0 + e] = lam[e];
-          }
-          if (!epi_sync()) { ok = false; break; }
+          for (int e = 0; e < 16; ++e) lam[e] = 0.f;
         }
-        const bool bound_row = valid && role != 2;
-        const bool dn = role == 0;
-        const float* Jr = Jbuf + (output && bound_row ? idx - l0 : 0) * jstride;
-        float sum0 = 0.f, sum1 = 0.f;
-        for (int j0 = 16 * cq; j0 < n; j0 += 64) {
-          float lam[16];
-          tmem_ld16(t_lane + (uint32_t)j0, lam);
-          if (bound_row) {
+        uint32_t packed[8];
+        row_pass16<OUT, EPS>(lam, j0, sv, sd, sw, ri.isJ, a.fmt, packed, beta, infl);
+        if (!wait_free(b)) return false;
+        store_a16(Asm, r, j0, packed);
+        block_ready(b);
+      }
+      if (ri.bound) ucon = __fadd_ru(ucon, ucon_of(t, target - 1));
+      return true;
+    };
+
+    // one job of a hidden stage k >= 1: TMEM half hb holds columns [c0, c0 + nc) of Lambda'; write them as
+    // operand blocks of stage k - 1 (vectors of hidden layer k - 1 in buffer vcur)
+    auto stage_job = [&](const RowInfo& ri, uint32_t hb, int c0, int nc, int vcur, float2& beta, float2& infl) -> bool {
+      if (!wait_acc(hb)) return false;
+      const float4* sv;
+      const float* sd;
+      const float* sw;
+      vbuf(vcur, sv, sd, sw);
+      const uint32_t tb = t_lane + hb * 256u + (uint32_t)(16 * cq);
+      for (int bb = 0; bb < nc / 64; ++bb) {
+        float lam[16];
+        tmem_ld16(tb + (uint32_t)(64 * bb), lam);
+        const int j0 = c0 + 64 * bb + 16 * cq;
+        uint32_t packed[8];
+        row_pass16<OUT, EPS>(lam, j0, sv, sd, sw, ri.isJ, a.fmt, packed, beta, infl);
+        const int b = (c0 >> 6) + bb;
+        if (!wait_free(b)) return false;
+        store_a16(Asm, r, j0, packed);
+        block_ready(b);
+      }
+      release_acc(hb);
+      return true;
+    };
+
+    // one job of the final stage: concretise columns [c0, c0 + nc) over the displacement box
+    auto conc_job = [&](int t, const RowInfo& ri, uint32_t hb, int c0, int nc, float2& sum) -> bool {
+      if (!wait_acc(hb)) return false;
+      const uint32_t tb = t_lane + hb * 256u;
+      const float* dlo = a.dlo + (long long)t * n;
+      const float* dhi = a.dhi + (long long)t * n;
+      // Jacobian rows: lanes whose lower/upper row needs the Jacobian row of the same state from the next
+      // lane quarter (rows 30, 31 and 63 of a 126-row tile) read it from the exchange buffer
+      const int role = ri.isJ ? 2 : (ri.neg ? 1 : 0);
+      const int src = lane + 2 - role;
+      const bool importer = OUT && ri.bound && src >= 32;
+      const bool exporter = OUT && ri.isJ && lane < 2;
+      const int dcol = (OUT && a.residual && ri.bound) ? ri.idx : -1;   // diagonal column of the state
+      for (int j0 = c0 + 16 * cq; j0 < c0 + nc; j0 += 64) {
+        float lam[16];
+        tmem_ld16(tb + (uint32_t)(j0 - c0), lam);
+        float jl[16], jh[16];
+        if (OUT) {
+          float* xb = xch + ((cq * 2 + (int)(xph & 1u)) * 2) * 16;
+          if (exporter)
+#pragma unroll
+            for (int e = 0; e < 16; e += 4)
+              *reinterpret_cast<float4*>(xb + (q - 1) * 16 + e) = make_float4(lam[e], lam[e + 1], lam[e + 2], lam[e + 3]);
+          if (ri.isJ && ri.valid) {
+            // this Jacobian row chunk -> A (residual: + I) and B
+            const int l = ri.idx;
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-              const int j = j0 + e;
-              const float2 d = sw[j];  // the box contains the nominal: dlo <= 0 <= dhi
-              float mlo = lam[e], mhi = lam[e];
-              if (output) {
-                const float jv = Jr[j];
-                if (a.residual && j == idx) {
-                  const float aret = 1.f + jv;
-                  mlo = __fadd_rd(__fsub_rd(lam[e], aret), 1.f);
-                  mhi = __fadd_ru(__fsub_ru(lam[e], aret), 1.f);
-                } else {
-                  mlo = __fsub_rd(lam[e], jv);
-                  mhi = __fsub_ru(lam[e], jv);
-                }
+              const int m = j0 + e;
+              if (m < n_x) {
+                if (a.A) a.A[((long long)t * n_x + l) * n_x + m] = (a.residual && m == l) ? 1.f + lam[e] : lam[e];
+              } else if (a.B) {
+                a.B[((long long)t * n_x + l) * (n - n_x) + (m - n_x)] = lam[e];
               }
-              // [mlo, mhi] x [dlo, dhi] with dlo <= 0 <= dhi: min = min(mlo dhi, mhi dlo), max = max(mhi dhi, mlo dlo)
-              float term;
-              if (dn) term = fminf(__fmul_rd(mlo, d.y), __fmul_rd(mhi, d.x));
-              else term = fmaxf(__fmul_ru(mhi, d.y), __fmul_ru(mlo, d.x));
-              if (e & 1) sum1 = dn ? __fadd_rd(sum1, term) : __fadd_ru(sum1, term);
-              else sum0 = dn ? __fadd_rd(sum0, term) : __fadd_ru(sum0, term);
             }
           }
-        }
-        tc_fence_before();
-        // combine the four column quarters of each row
-        float* st = stat + (r * 4 + cq) * 4;
-        st[0] = dn ? __fadd_rd(sum0, sum1) : __fadd_ru(sum0, sum1);
-        st[1] = dn ? __fadd_rd(beta0, beta1) : __fadd_ru(beta0, beta1);
-        st[2] = a.tight ? 0.f : __fadd_ru(__fadd_ru(infl0, infl1), cq == 0 ? ucon : 0.f);
-        if (!epi_sync()) { ok = false; break; }
-        if (cq == 0 && bound_row) {
-          const float* s0 = stat + (r * 4) * 4;
-          float tot = s0[0], beta = s0[1], infl = s0[2];
-          for (int c = 1; c < 4; ++c) {
-            tot = dn ? __fadd_rd(tot, s0[4 * c]) : __fadd_ru(tot, s0[4 * c]);
-            beta = dn ? __fadd_rd(beta, s0[4 * c + 1]) : __fadd_ru(beta, s0[4 * c + 1]);
-            infl = __fadd_ru(infl, s0[4 * c + 2]);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&xbar[cq]);
+          if (!mbar_wait(&xbar[cq], xph & 1u)) return false;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) jl[e] = __shfl_sync(0xffffffffu, lam[e], src & 31);
+          if (importer)
+#pragma unroll
+            for (int e = 0; e < 16; ++e) jl[e] = xb[q * 16 + e];
+          ++xph;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) jh[e] = jl[e];
+          if ((unsigned)(dcol - j0) < 16u) {
+            // the returned A has 1 + J on the diagonal: J_eff = fl(1 + J) - 1, enclosed
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              if (j0 + e == dcol) {
+                const float aret = 1.f + jl[e];
+                jl[e] = __fsub_rd(aret, 1.f);
+                jh[e] = __fsub_ru(aret, 1.f);
+              }
           }
-          float val = dn ? __fsub_rd(__fadd_rd(tot, beta), infl) : __fadd_ru(__fadd_ru(tot, beta), infl);
-          const bool nonfinite = !isfinite(val);
-          const bool badrow = a.bad[t] != 0 || nonfinite;
-          const float slack = __fmul_ru(2.f, infl);
-          if (!output) {
-            const long long o = (long long)t * a.H + a.hoff[target] + idx;
-            const float zh = a.zhat[o], e = a.zrad[o];
-            val = dn ? __fadd_rd(__fsub_rd(zh, e), val) : __fadd_ru(__fadd_ru(zh, e), val);
-            if (badrow) val = dn ? -CUDART_INF_F : CUDART_INF_F;
-            if (dn) a.lo[o] = val; else a.hi[o] = val;
-            atomicMax(reinterpret_cast<int*>(a.bslack + o), __float_as_int(isfinite(slack) ? slack : 3.0e38f));
-          } else {
-            if (badrow) val = dn ? -CUDART_INF_F : CUDART_INF_F;
-            const long long o = (long long)t * n_x + idx;
-            if (dn) a.r_lo[o] = val; else a.r_hi[o] = val;
-            stat[(r * 4) * 4 + 3] = val;   // final value, read by the slack/Gamma pass below
-            stat[(r * 4) * 4 + 2] = slack;
-          }
-          if (nonfinite && a.bad[t] == 0) atomicOr(a.flags, LEB_ASYNC_OVERFLOW);
         }
-        if (output) {
-          if (!epi_sync()) { ok = false; break; }
-          // Jacobian rows of this tile -> A, B (coalesced), stated slack and Gamma map per state row
-          const int nl = min(a.rows_per_tile / 3, n_x - l0);
-          for (int e = etid; e < nl * n; e += ethr) {
-            const int ll = e / n, m = e - ll * n;
-            const float jv = Jbuf[ll * jstride + m];
-            const int l = l0 + ll;
-            if (m < n_x) {
-              if (a.A) a.A[((long long)t * n_x + l) * n_x + m] = (a.residual && m == l) ? 1.f + jv : jv;
-            } else if (a.B) {
-              a.B[((long long)t * n_x + l) * (n - n_x) + (m - n_x)] = jv;
+        if (ri.bound) {
+          float dl[16], dh[16];
+#pragma unroll
+          for (int e = 0; e < 16; e += 4) {
+            const float4 x = __ldg(reinterpret_cast<const float4*>(dlo + j0 + e));
+            const float4 y = __ldg(reinterpret_cast<const float4*>(dhi + j0 + e));
+            dl[e] = x.x; dl[e + 1] = x.y; dl[e + 2] = x.z; dl[e + 3] = x.w;
+            dh[e] = y.x; dh[e + 1] = y.y; dh[e + 2] = y.z; dh[e + 3] = y.w;
+          }
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            float mlo = lam[e], mhi = lam[e];
+            if (OUT) {
+              // lower rows: M = lam - J; upper rows (lam = -Lambda^U): M = lam + J
+              const float pl = ri.neg ? jl[e] : -jh[e], ph = ri.neg ? jh[e] : -jl[e];
+              mlo = __fadd_rd(lam[e], pl);
+              mhi = __fadd_ru(lam[e], ph);
             }
-          }
-          for (int ll = etid; ll < nl; ll += ethr) {
-            const float* sl = stat + (3 * ll * 4) * 4;
-            const float* su = stat + ((3 * ll + 1) * 4) * 4;
-            const long long o = (long long)t * n_x + l0 + ll;
-            if (a.eps) a.eps[o] = fmaxf(sl[2], su[2]);
-            if (a.gamma_c) {
-              const float lo = sl[3], hi = su[3];
-              const float c = 0.5f * lo + 0.5f * hi;
-              a.gamma_c[o] = c;
-              a.gamma_r[o] = __fadd_ru(fmaxf(__fsub_ru(hi, c), __fsub_ru(c, lo)), a.gamma_pad);
-            }
+            // [mlo, mhi] x [dlo, dhi] with dlo <= 0 <= dhi: min = min(mlo dhi, mhi dlo)
+            const float term = fminf(__fmul_rd(mlo, dh[e]), __fmul_rd(mhi, dl[e]));
+            if (e & 1) sum.y = __fadd_rd(sum.y, term);
+            else sum.x = __fadd_rd(sum.x, term);
           }
         }
-        // the next item's prologue overwrites Asm (J rows), the vectors and TMEM: everyone must be done
-        if (!epi_sync()) { ok = false; break; }
       }
+      release_acc(hb);
+      return true;
+    };
+
+    // combine the column groups of every row and write the bounds of an item
+    auto finalize = [&](int t, int tile, const RowInfo& ri, float2 sum, float2 beta, float2 infl,
+                        float ucon) -> bool {
+      float* st = stat + (r * 4 + cq) * 3;
+      st[0] = __fadd_rd(sum.x, sum.y);
+      st[1] = __fadd_rd(beta.x, beta.y);
+      st[2] = EPS ? __fadd_ru(infl.x, infl.y) : 0.f;
+      if (!epi_sync()) return false;
+      if (cq == 0 && ri.bound) {
+        const float* s0 = stat + r * 12;
+        float tot = s0[0], bsum = s0[1], isum = s0[2];
+        for (int c = 1; c < 4; ++c) {
+          tot = __fadd_rd(tot, s0[3 * c]);
+          bsum = __fadd_rd(bsum, s0[3 * c + 1]);
+          isum = __fadd_ru(isum, s0[3 * c + 2]);
+        }
+        // lower bound of this row's (possibly negated) chain value; the inflation is inside beta
+        const float val = __fsub_rd(__fadd_rd(tot, bsum), ucon);
+        const bool nonfinite = !isfinite(val);
+        const bool badrow = a.bad[t] != 0 || nonfinite;
+        if (!OUT) {
+          const long long o = (long long)t * a.H + a.hoff[target] + ri.idx;
+          const float zh = a.zhat[o], e = a.zrad[o];
+          if (!ri.neg) a.lo[o] = badrow ? -CUDART_INF_F : __fadd_rd(__fsub_rd(zh, e), val);
+          else a.hi[o] = badrow ? CUDART_INF_F : __fsub_ru(__fadd_ru(zh, e), val);
+        } else {
+          const long long o = (long long)t * n_x + ri.idx;
+          const float v = badrow ? (ri.neg ? CUDART_INF_F : -CUDART_INF_F) : (ri.neg ? -val : val);
+          if (ri.neg) a.r_hi[o] = v; else a.r_lo[o] = v;
+          vals[r] = v;
+          slk[r] = EPS ? __fmul_ru(2.f, __fadd_ru(isum, ucon)) : 0.f;
+        }
+        if (nonfinite && a.bad[t] == 0) atomicOr(a.flags, LEB_ASYNC_OVERFLOW);
+      }
+      if (OUT) {
+        if (!epi_sync()) return false;
+        const int l0 = tile * (a.rows_per_tile / 3);
+        const int nl = min(a.rows_per_tile / 3, n_x - l0);
+        for (int ll = etid; ll < nl; ll += kTcEpiWarps * 32) {
+          const long long o = (long long)t * n_x + l0 + ll;
+          if (EPS && a.eps) a.eps[o] = fmaxf(slk[3 * ll], slk[3 * ll + 1]);
+          if (a.gamma_c) {
+            const float lo = vals[3 * ll], hi = vals[3 * ll + 1];
+            const float c = 0.5f * lo + 0.5f * hi;
+            a.gamma_c[o] = c;
+            a.gamma_r[o] = __fadd_ru(fmaxf(__fsub_ru(hi, c), __fsub_ru(c, lo)), a.gamma_pad);
+          }
+        }
+      }
+      // the next finalisation overwrites stat / vals
+      return epi_sync();
+    };
+
+    const float2 z2 = make_float2(0.f, 0.f);
+    int item = blockIdx.x;
+    float2 beta = z2, infl = z2;
+    float ucon = 0.f;
+    if (item < n_items) {
+      // first item's prologue
+      const int t0 = item / a.tiles_per_t;
+      prefetch(t0, target - 1);
+      const int v0 = vb;
+      ok = install();
+      prefetch_next(t0, target - 1, item + gridDim.x);
+      if (ok) ok = prologue(t0, row_info(a, item - t0 * a.tiles_per_t, r), v0, beta, infl, ucon);
+    }
+    for (; item < n_items && ok; item += gridDim.x) {
+      const int t = item / a.tiles_per_t, tile = item - t * a.tiles_per_t;
+      const int next = item + gridDim.x;
+      const RowInfo ri = row_info(a, tile, r);
+      // hidden stages k = target-1 .. 1 (vectors of layer k-1)
+      for (int k = target - 1; k >= 1 && ok; --k) {
+        const int vcur = vb;
+        if (!install()) { ok = false; break; }
+        prefetch_next(t, k - 1, next);
+        apend |= (1u << (a.widths[k + 1] / 64)) - 1u;   // stage k's reads of the operand it consumes
+        if (ri.bound) ucon = __fadd_ru(ucon, ucon_of(t, k - 1));
+        const int N = a.widths[k], split = stage_split(k);
+        for (int h = 0; h < (N > split ? 2 : 1) && ok; ++h, ++jc)
+          ok = stage_job(ri, jc & 1u, h ? split : 0, h ? N - split : split, vcur, beta, infl);
+      }
+      if (!ok) break;
+      // the next item's prologue, built while the tensor cores run this item's final stage
+      apend |= (1u << (a.widths[1] / 64)) - 1u;
+      float2 beta_n = z2, infl_n = z2;
+      float ucon_n = 0.f;
+      if (next < n_items) {
+        const int tn = next / a.tiles_per_t;
+        const int vcur = vb;
+        if (!install()) { ok = false; break; }
+        prefetch_next(tn, target - 1, next + gridDim.x);
+        if (!prologue(tn, row_info(a, next - tn * a.tiles_per_t, r), vcur, beta_n, infl_n, ucon_n)) { ok = false; break; }
+      }
+      // final stage: concretise over the box
+      float2 sum = z2;
+      const int N0 = a.widths[0], split0 = stage_split(0);
+      for (int h = 0; h < (N0 > split0 ? 2 : 1) && ok; ++h, ++jc)
+        ok = conc_job(t, ri, jc & 1u, h ? split0 : 0, h ? N0 - split0 : split0, sum);
+      if (!ok) break;
+      if (!finalize(t, tile, ri, sum, beta, infl, ucon)) { ok = false; break; }
+      beta = beta_n;
+      infl = infl_n;
+      ucon = ucon_n;
       if (*(volatile int*)&s_abort) ok = false;
     }
     if (!ok) {
@@ -521,10 +720,9 @@ leb_status tc_prepare(Ctx& c) {
     if (cudaMalloc(&st->WT[k], (size_t)K * N * 2) != cudaSuccess) return LEB_ERR_CUDA;
     transpose_round_kernel<<<256, 256>>>(m.W[k], K, N, st->WT[k], fmt);
     if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
-    const int nh = N > 256 ? 2 : 1;
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)N};
     cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)(N / nh)};
+    cuuint32_t box[2] = {64, (cuuint32_t)(N < kTcBRows ? N : kTcBRows)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(&st->maps[k], fmt == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                      st->WT[k], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -532,7 +730,12 @@ leb_status tc_prepare(Ctx& c) {
     if (r != CUDA_SUCCESS) return LEB_ERR_UNSUPPORTED;
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return LEB_ERR_CUDA;
-  if (cudaFuncSetAttribute(crown_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) != cudaSuccess)
+  if (cudaFuncSetAttribute(crown_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(crown_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(crown_tc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) !=
+          cudaSuccess)
     return LEB_ERR_CUDA;
   return LEB_OK;
 }
@@ -566,7 +769,10 @@ leb_status tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, 
   if (!st) return LEB_ERR_UNSUPPORTED;
   TcArgs a;
   memset(&a, 0, sizeof(a));
-  for (int k = 0; k + 1 < m.L; ++k) a.tmap[k] = st->maps[k];
+  for (int k = 0; k + 1 < m.L; ++k) {
+    a.tmap[k] = st->maps[k];
+    a.brows[k] = m.widths[k] < kTcBRows ? m.widths[k] : kTcBRows;
+  }
   a.L = m.L;
   for (int i = 0; i <= m.L; ++i) a.widths[i] = m.widths[i];
   a.residual = m.residual;
@@ -595,7 +801,6 @@ leb_status tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, 
   a.bad = bad;
   a.lo = ws + L.lo;
   a.hi = ws + L.hi;
-  a.bslack = ws + L.bslack;
   a.r_lo = r_lo;
   a.r_hi = r_hi;
   a.A = A;
@@ -610,7 +815,9 @@ leb_status tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, 
   const int grid = items < c.sm_count ? items : c.sm_count;
   if (grid == 0) return LEB_OK;
   timer_begin(c, s, "crown_tc_kernel");
-  crown_tc_kernel<<<grid, kTcThreads, kTcSmem, s>>>(a);
+  if (!output) crown_tc_kernel<false, false><<<grid, kTcThreads, kTcSmem, s>>>(a);
+  else if (eps) crown_tc_kernel<true, true><<<grid, kTcThreads, kTcSmem, s>>>(a);
+  else crown_tc_kernel<true, false><<<grid, kTcThreads, kTcSmem, s>>>(a);
   timer_end(c, s);
   return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
 }

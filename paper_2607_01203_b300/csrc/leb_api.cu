@@ -245,7 +245,7 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
   if (T > 0 && set->kind == LEB_SET_ZONO && (!set->G || set->n_gen < 1)) return LEB_ERR_INVALID_ARG;
   if (opt && ((opt->gamma_c == nullptr) != (opt->gamma_r == nullptr))) return LEB_ERR_INVALID_ARG;
   if (opt && !(opt->gamma_pad >= 0.f)) return LEB_ERR_INVALID_ARG;
-  if (!workspace) return LEB_ERR_WORKSPACE;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return LEB_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(dev_flags, 0, sizeof(int), s) != cudaSuccess) return LEB_ERR_CUDA;
   if (T == 0) return LEB_OK;
@@ -314,7 +314,7 @@ leb_status leb_bounds_backward(leb_handle h, int T, const float* x_nom, const fl
   if (set->kind != LEB_SET_BOX || set->center) return LEB_ERR_UNSUPPORTED;
   if (T > 0 && (!x_nom || !u_nom || !set->radii || !g_rlo || !g_rhi || !g_x || !g_u || !g_radii))
     return LEB_ERR_INVALID_ARG;
-  if (!workspace) return LEB_ERR_WORKSPACE;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return LEB_ERR_WORKSPACE;
   MlpWs lay;
   const size_t need = kWsHeader + mlp_workspace_floats(*h, T, &lay) * sizeof(float);
   if (ws_bytes < need) return LEB_ERR_WORKSPACE;
