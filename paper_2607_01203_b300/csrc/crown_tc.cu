@@ -20,8 +20,9 @@
 // prologue (its first operand) is built before the current timestep's final concretisation, so the
 // tensor cores start the next tile while the epilogue concretises.
 // Warp roles: warp 0 streams W_k^T tiles (128 rows x 64 K) with TMA through a ring of kTcNSB stages,
-// warp 1 allocates TMEM and one of its threads issues the MMAs, warps 2..17 run the epilogue (four warps
-// per TMEM lane quarter, each on one 16-column chunk of every 64-column block).
+// warp 1 allocates TMEM and one of its threads issues the MMAs, warps 2..9 run the epilogue (two warps
+// per TMEM lane quarter, each on one 32-column half of every 64-column block, the next block's TMEM
+// load in flight while a block is processed; the per-neuron vectors of the next pass arrive by cp.async).
 //
 // Rigour of the reduced-precision GEMM (per stage, per row): with A~ the rounded operand, W~ the rounded
 // weights and the FP32 accumulation error bounded by gamma_K |A~| |W~| (u = 2^-23, i.e. without assuming
@@ -45,17 +46,17 @@
 
 namespace leb {
 
-constexpr int kTcEpiWarps = 16;                 // 4 per TMEM lane quarter, one 16-column chunk of each block
+constexpr int kTcEpiWarps = 8;                  // 2 per TMEM lane quarter, 32 columns of every 64-column block each
 constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
-constexpr int kTcNSB = 4;                       // B ring stages
-constexpr int kTcBRows = 128;                   // N rows of one B tile
-constexpr int kTcBStage = kTcBRows * 128;       // 128 rows x 64 K x 2 bytes
+constexpr int kTcNSB = 2;                       // B ring stages
+constexpr int kTcBRows = 256;                   // N rows of one B tile (the MMA's N)
+constexpr int kTcBStage = kTcBRows * 128;       // 256 rows x 64 K x 2 bytes
 constexpr int kTcARegion = 128 * 512 * 2;       // 128 rows x 512 K x 2 bytes (8 blocks of 16 KB)
 constexpr int kTcVecBuf = 512 * 16 + 512 * 4 + 512 * 4;   // per-neuron vectors: {sL, sU, tau'L, tau'U}, D, w
-constexpr int kTcStat = 128 * 4 * 3 * 4;        // [row][column group][3]
+constexpr int kTcStat = 128 * 2 * 3 * 4;        // [row][column group][3]
 constexpr int kTcVals = 2 * 128 * 4;            // [128] final values, [128] stated slack
-constexpr int kTcXch = 4 * 2 * 2 * 16 * 4;      // [column group][buffer][slot][16] Jacobian values
-constexpr int kTcNBar = 2 * kTcNSB + 8 + 8 + 2 + 2 + 1 + 1 + 4;
+constexpr int kTcXch = 2 * 2 * 2 * 32 * 4;      // [column group][buffer][slot][32] Jacobian values
+constexpr int kTcNBar = 2 * kTcNSB + 8 + 8 + 2 + 2 + 1 + 1 + 2;
 constexpr int kTcSmem = 1024 + kTcARegion + kTcNSB * kTcBStage + 2 * kTcVecBuf + kTcStat + kTcVals + kTcXch +
                         kTcNBar * 8;
 static_assert(kTcSmem <= 227 * 1024, "tensor-core chain shared memory");
@@ -80,18 +81,22 @@ struct TcArgs {
   int* flags;
 };
 
-// Store 16 operand values (row r, columns j0..j0+15, packed pairs) into the 128-byte-swizzled K-major tile.
-__device__ __forceinline__ void store_a16(uint8_t* A, int r, int j0, const uint32_t packed[8]) {
+// Store 32 operand values (row r, columns j0..j0+31, packed pairs) into the 128-byte-swizzled K-major tile
+// (j0 a multiple of 32: one half of a 64-column block).
+__device__ __forceinline__ void store_a32(uint8_t* A, int r, int j0, const uint32_t packed[16]) {
   const int kb = j0 >> 6;                 // K block of 64 columns (16 KB each)
-  const int c = (j0 & 63) >> 3;           // first 16-byte chunk inside the 128-byte row
+  const int c = (j0 & 63) >> 3;           // first 16-byte chunk inside the 128-byte row (0 or 4)
   uint8_t* rowp = A + kb * 16384 + r * 128;
   const int sw = r & 7;
-  *reinterpret_cast<uint4*>(rowp + ((c ^ sw) << 4)) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-  *reinterpret_cast<uint4*>(rowp + (((c + 1) ^ sw) << 4)) = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    *reinterpret_cast<uint4*>(rowp + (((c + i) ^ sw) << 4)) =
+        make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2], packed[4 * i + 3]);
 }
 
-__device__ __forceinline__ uint32_t pack2(float x, float y, int fmt) {
-  if (fmt == 0) {
+template <int FMT>
+__device__ __forceinline__ uint32_t pack2(float x, float y) {
+  if (FMT == 0) {
     const __half2 h = __floats2half2_rn(x, y);
     return *reinterpret_cast<const uint32_t*>(&h);
   }
@@ -104,10 +109,10 @@ __device__ __forceinline__ uint32_t pack2(float x, float y, int fmt) {
 // sw[j] = inflation weight. Bound rows take the lower line where lam >= 0, else the upper line; Jacobian
 // rows (OUT only) take sigma'. Writes the next operand lam o s (packed pairs) and accumulates
 // beta += lam tau' rounded down (and, EPS, the inflation sum |lam s| w rounded up, for the stated slack).
-template <bool OUT, bool EPS>
+template <bool OUT, bool EPS, int FMT>
 __device__ __forceinline__ void row_pass16(const float lam[16], int j0, const float4* __restrict__ sv,
                                            const float* __restrict__ sd, const float* __restrict__ sw, bool isJ,
-                                           int fmt, uint32_t packed[8], float2& beta, float2& infl) {
+                                           uint32_t packed[8], float2& beta, float2& infl) {
 #pragma unroll
   for (int e = 0; e < 16; e += 2) {
     const float4 v0 = sv[j0 + e], v1 = sv[j0 + e + 1];
@@ -126,7 +131,7 @@ __device__ __forceinline__ void row_pass16(const float lam[16], int j0, const fl
       const float2 w = *reinterpret_cast<const float2*>(sw + j0 + e);
       infl = __ffma2_ru(make_float2(fabsf(av.x), fabsf(av.y)), w, infl);
     }
-    packed[e >> 1] = pack2(av.x, av.y, fmt);
+    packed[e >> 1] = pack2<FMT>(av.x, av.y);
   }
 }
 
@@ -151,18 +156,29 @@ __device__ __forceinline__ RowInfo row_info(const TcArgs& a, int tile, int r) {
   return ri;
 }
 
-template <bool OUT, bool EPS>
+// 32 TMEM columns of this warp's lane quarter (two asynchronous x16 loads; tmem_wait_ld completes them).
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, float v[32]) {
+  tmem_ld16_async(taddr, v);
+  tmem_ld16_async(taddr + 16u, v + 16);
+}
+__device__ __forceinline__ void tmem_wait32(float v[32]) {
+  tmem_wait_ld();
+  tmem_regs_fence16(v);
+  tmem_regs_fence16(v + 16);
+}
+
+template <bool OUT, bool EPS, int FMT>
 __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_constant__ TcArgs a) {
   extern __shared__ uint8_t sraw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sraw) + 1023) & ~uintptr_t(1023));
   uint8_t* Asm = base;                                     // A operand
   uint8_t* Bsm = base + kTcARegion;                        // B ring
   uint8_t* Vsm = Bsm + kTcNSB * kTcBStage;                 // 2 x per-neuron vectors
-  float* stat = reinterpret_cast<float*>(Vsm + 2 * kTcVecBuf);   // [128][4][3]
-  float* vals = stat + 128 * 12;                           // [128]
+  float* stat = reinterpret_cast<float*>(Vsm + 2 * kTcVecBuf);   // [128][2][3]
+  float* vals = stat + 128 * 6;                            // [128]
   float* slk = vals + 128;                                 // [128]
-  float* xch = slk + 128;                                  // [4][2][2][16]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(xch + 4 * 2 * 2 * 16);
+  float* xch = slk + 128;                                  // [2][2][2][32]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(xch + 2 * 2 * 2 * 32);
   uint64_t* b_full = bars;                 // [kTcNSB]  B tile landed
   uint64_t* b_empty = bars + kTcNSB;       // [kTcNSB]  B tile consumed
   uint64_t* a_ready = bars + 2 * kTcNSB;   // [8]  operand block written by the epilogue
@@ -171,7 +187,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
   uint64_t* acc_free = acc_full + 2;       // [2]  TMEM half read by the epilogue
   uint64_t* drain = acc_free + 2;
   uint64_t* ebar = drain + 1;              // epilogue-warps barrier
-  uint64_t* xbar = ebar + 1;               // [4]  per column group (Jacobian exchange)
+  uint64_t* xbar = ebar + 1;               // [2]  per column group (Jacobian exchange)
   __shared__ uint32_t tmem_slot;
   __shared__ int s_abort;
 
@@ -194,7 +210,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     }
     mbar_init(drain, 1);
     mbar_init(ebar, kTcEpiWarps);
-    for (int c = 0; c < 4; ++c) mbar_init(&xbar[c], 4);
+    for (int c = 0; c < 2; ++c) mbar_init(&xbar[c], 4);
     mbar_fence_init();
     s_abort = 0;
   }
@@ -274,7 +290,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
                 if (!mbar_wait(&b_full[s], (kb / kTcNSB) & 1u)) { ok = false; break; }
                 tc_fence_after();
                 const int nn = min(kTcBRows, nc - bt * kTcBRows);
-                const uint32_t idesc = idesc_f16(128, nn, a.fmt);
+                const uint32_t idesc = idesc_f16(128, nn, FMT);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
                   const uint64_t ad = sw128_desc(a_base + kc * 16384 + kk * 32);
@@ -302,16 +318,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     // ---------------------------------------------------------------- epilogue warps
     const int ew = warp - 2;
     const int q = warp & 3;                 // TMEM lane quarter of this warp
-    const int cq = ew >> 2;                 // 16-column chunk of every 64-column block
+    const int cq = ew >> 2;                 // 32-column half of every 64-column block
     const int r = q * 32 + lane;            // tile row = TMEM lane
     const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16);
     const int etid = threadIdx.x - 64;
+    constexpr int kEThreads = kTcEpiWarps * 32;
     const int n = a.widths[0];
     const int n_x = a.widths[a.L];
     const bool tight = a.tight != 0;
     uint32_t nbar = 0, cpar = 0, apend = 0, apar = 0, xph = 0;
     uint32_t jc = 0;
     int vb = 0;                             // vector buffer installed next
+    int pf_width = 0;                       // width of the vector set being prefetched into buffer vb
     bool ok = true;
 
     auto epi_sync = [&]() -> bool {
@@ -321,47 +339,57 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       ++nbar;
       return res;
     };
-    auto vbuf = [&](int b, const float4*& sv, const float*& sd, const float*& sw) {
+    auto vptr = [&](int b, float4*& sv, float*& sd, float*& sw) {
       uint8_t* p = Vsm + b * kTcVecBuf;
-      sv = reinterpret_cast<const float4*>(p);
-      sd = reinterpret_cast<const float*>(p + 512 * 16);
-      sw = reinterpret_cast<const float*>(p + 512 * 20);
+      sv = reinterpret_cast<float4*>(p);
+      sd = reinterpret_cast<float*>(p + 512 * 16);
+      sw = reinterpret_cast<float*>(p + 512 * 20);
     };
-    // prefetched per-neuron values of the next vector set (neuron etid): sL, sU, tL, tU, w, D
-    float pf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int pf_width = 0, pf_wp = 0;
+    // Asynchronous copy of the raw vectors of hidden layer hl of timestep t into buffer vb:
+    // sv[j] = {sL, sU, tL, tU}, sd[j] = D, sw[j] = w. The buffer was last read two sets ago.
     auto prefetch = [&](int t, int hl) {
       const int width = a.widths[hl + 1];
       pf_width = width;
-      pf_wp = (width + 63) & ~63;
-      if (etid < width) {
-        const long long o = (long long)t * a.H + a.hoff[hl] + etid;
-        pf[0] = a.sL[o];
-        pf[1] = a.sU[o];
-        pf[2] = a.tL[o];
-        pf[3] = a.tU[o];
-        pf[4] = tight ? 0.f : a.winf[o];
-        pf[5] = a.D[o];
+      float4* sv;
+      float* sd;
+      float* sw;
+      vptr(vb, sv, sd, sw);
+      const long long o0 = (long long)t * a.H + a.hoff[hl];
+      for (int j = etid; j < width; j += kEThreads) {
+        const long long o = o0 + j;
+        float* e4 = reinterpret_cast<float*>(sv + j);
+        cp_async4(e4, a.sL + o);
+        cp_async4(e4 + 1, a.sU + o);
+        cp_async4(e4 + 2, a.tL + o);
+        cp_async4(e4 + 3, a.tU + o);
+        cp_async4(sd + j, a.D + o);
+        if (!tight) cp_async4(sw + j, a.winf + o);
       }
+      cp_async_commit();
     };
-    // write the prefetched set into buffer vb (last read two sets ago: free since the last install)
+    // complete the prefetched set in buffer vb: fold the inflation weight into the offsets, zero the
+    // padding up to a multiple of 64, make it visible to every epilogue warp
     auto install = [&]() -> bool {
-      uint8_t* p = Vsm + vb * kTcVecBuf;
-      float4* sv = reinterpret_cast<float4*>(p);
-      float* sd = reinterpret_cast<float*>(p + 512 * 16);
-      float* sw = reinterpret_cast<float*>(p + 512 * 20);
-      if (etid < pf_wp) {
-        if (etid < pf_width) {
-          const float w = pf[4];
-          const float tl = tight ? pf[2] : __fmaf_rd(-fabsf(pf[0]), w, pf[2]);
-          const float tu = tight ? pf[3] : __fmaf_ru(fabsf(pf[1]), w, pf[3]);
-          sv[etid] = make_float4(pf[0], pf[1], tl, tu);
-          sd[etid] = pf[5];
-          sw[etid] = w;
+      cp_async_wait_all();
+      float4* sv;
+      float* sd;
+      float* sw;
+      vptr(vb, sv, sd, sw);
+      const int wp = (pf_width + 63) & ~63;
+      for (int j = etid; j < wp; j += kEThreads) {
+        if (j < pf_width) {
+          if (!tight) {
+            const float4 v = sv[j];
+            const float w = sw[j];
+            sv[j].z = __fmaf_rd(-fabsf(v.x), w, v.z);
+            sv[j].w = __fmaf_ru(fabsf(v.y), w, v.w);
+          } else {
+            sw[j] = 0.f;
+          }
         } else {
-          sv[etid] = make_float4(0.f, 0.f, 0.f, 0.f);
-          sd[etid] = 0.f;
-          sw[etid] = 0.f;
+          sv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+          sd[j] = 0.f;
+          sw[j] = 0.f;
         }
       }
       const bool res = epi_sync();
@@ -401,58 +429,89 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     auto ucon_of = [&](int t, int hl) -> float {
       return tight ? 0.f : __fmul_ru(1.001f, a.ucon[(long long)t * (a.L - 1) + hl]);
     };
+    // row pass of 16 columns j0..j0+15 into packed[8]
+    auto pass16 = [&](const float lam[16], int j0, int vcur, const RowInfo& ri, uint32_t packed[8], float2& beta,
+                      float2& infl) {
+      float4* sv;
+      float* sd;
+      float* sw;
+      vptr(vcur, sv, sd, sw);
+      row_pass16<OUT, EPS, FMT>(lam, j0, sv, sd, sw, ri.isJ, packed, beta, infl);
+    };
+    // this warp's 32 columns of operand block b -> shared memory, then the block is announced
+    auto put32 = [&](int j0, int b, const uint32_t packed[16]) -> bool {
+      if (!wait_free(b)) return false;
+      store_a32(Asm, r, j0, packed);
+      block_ready(b);
+      return true;
+    };
 
     // prologue of an item: operand = W_target rows (negated for upper rows) o slopes of layer target-1
-    auto prologue = [&](int t, const RowInfo& ri, int vcur, float2& beta, float2& infl, float& ucon) -> bool {
-      const float4* sv;
-      const float* sd;
-      const float* sw;
-      vbuf(vcur, sv, sd, sw);
-      const int K = a.widths[target], nK = K / 64;
-      const float* Wrow = a.W_target + (long long)ri.idx * K;
-      const float sg = ri.neg ? -1.f : 1.f;
-      for (int b = 0; b < nK; ++b) {
-        const int j0 = 64 * b + 16 * cq;
-        float lam[16];
+    auto prologue = [&](int t, const RowInfo& ri, int vcur, float2 (&beta)[2], float2 (&infl)[2],
+                        float& ucon) -> bool {
+      const int K = a.widths[target], nb = K / 64;
+      const float* Wrow = a.W_target + (long long)ri.idx * K + 32 * cq;
+      const float2 sg = ri.neg ? make_float2(-1.f, -1.f) : make_float2(1.f, 1.f);
+      // 16-column halves h = 2 bb + hh of this warp's 32 columns of block bb; the next half's weights are
+      // loaded while a half is processed
+      auto ldw = [&](float v[16], int h) {
         if (ri.valid) {
+          const float* src = Wrow + 64 * (h >> 1) + 16 * (h & 1);
 #pragma unroll
           for (int e = 0; e < 16; e += 4) {
-            const float4 w4 = __ldg(reinterpret_cast<const float4*>(Wrow + j0 + e));
-            lam[e] = sg * w4.x; lam[e + 1] = sg * w4.y; lam[e + 2] = sg * w4.z; lam[e + 3] = sg * w4.w;
+            const float4 w4 = __ldg(reinterpret_cast<const float4*>(src + e));
+            const float2 x = __fmul2_rn(make_float2(w4.x, w4.y), sg), y = __fmul2_rn(make_float2(w4.z, w4.w), sg);
+            v[e] = x.x; v[e + 1] = x.y; v[e + 2] = y.x; v[e + 3] = y.y;
           }
         } else {
 #pragma unroll
-          for (int e = 0; e < 16; ++e) lam[e] = 0.f;
+          for (int e = 0; e < 16; ++e) v[e] = 0.f;
         }
-        uint32_t packed[8];
-        row_pass16<OUT, EPS>(lam, j0, sv, sd, sw, ri.isJ, a.fmt, packed, beta, infl);
-        if (!wait_free(b)) return false;
-        store_a16(Asm, r, j0, packed);
-        block_ready(b);
+      };
+      float A0[16], A1[16];
+      uint32_t packed[16];
+      ldw(A0, 0);
+      for (int bb = 0; bb < nb; ++bb) {
+        const int j0 = 64 * bb + 32 * cq;
+        ldw(A1, 2 * bb + 1);
+        pass16(A0, j0, vcur, ri, packed, beta[0], infl[0]);
+        if (bb + 1 < nb) ldw(A0, 2 * bb + 2);
+        pass16(A1, j0 + 16, vcur, ri, packed + 8, beta[1], infl[1]);
+        if (!put32(j0, bb, packed)) return false;
       }
       if (ri.bound) ucon = __fadd_ru(ucon, ucon_of(t, target - 1));
       return true;
     };
 
     // one job of a hidden stage k >= 1: TMEM half hb holds columns [c0, c0 + nc) of Lambda'; write them as
-    // operand blocks of stage k - 1 (vectors of hidden layer k - 1 in buffer vcur)
-    auto stage_job = [&](const RowInfo& ri, uint32_t hb, int c0, int nc, int vcur, float2& beta, float2& infl) -> bool {
+    // operand blocks of stage k - 1 (vectors of hidden layer k - 1 in buffer vcur). The next block's TMEM
+    // load is in flight while a block is processed.
+    auto stage_job = [&](const RowInfo& ri, uint32_t hb, int c0, int nc, int vcur, float2 (&beta)[2],
+                         float2 (&infl)[2]) -> bool {
       if (!wait_acc(hb)) return false;
-      const float4* sv;
-      const float* sd;
-      const float* sw;
-      vbuf(vcur, sv, sd, sw);
-      const uint32_t tb = t_lane + hb * 256u + (uint32_t)(16 * cq);
-      for (int bb = 0; bb < nc / 64; ++bb) {
-        float lam[16];
-        tmem_ld16(tb + (uint32_t)(64 * bb), lam);
-        const int j0 = c0 + 64 * bb + 16 * cq;
-        uint32_t packed[8];
-        row_pass16<OUT, EPS>(lam, j0, sv, sd, sw, ri.isJ, a.fmt, packed, beta, infl);
-        const int b = (c0 >> 6) + bb;
-        if (!wait_free(b)) return false;
-        store_a16(Asm, r, j0, packed);
-        block_ready(b);
+      const uint32_t tb = t_lane + hb * 256u + (uint32_t)(32 * cq);
+      const int nb = nc / 64, b0 = c0 >> 6;
+      float A0[16], A1[16];
+      uint32_t packed[16];
+      tmem_ld16_async(tb, A0);
+      tmem_wait_ld();
+      tmem_regs_fence16(A0);
+      for (int bb = 0; bb < nb; ++bb) {
+        const int j0 = c0 + 64 * bb + 32 * cq;
+        tmem_ld16_async(tb + (uint32_t)(64 * bb + 16), A1);
+        pass16(A0, j0, vcur, ri, packed, beta[0], infl[0]);
+        tmem_wait_ld();
+        tmem_regs_fence16(A1);
+        if (bb + 1 < nb) tmem_ld16_async(tb + (uint32_t)(64 * (bb + 1)), A0);
+        pass16(A1, j0 + 16, vcur, ri, packed + 8, beta[1], infl[1]);
+        if (!put32(j0, b0 + bb, packed)) {
+          tmem_wait_ld();
+          return false;
+        }
+        if (bb + 1 < nb) {
+          tmem_wait_ld();
+          tmem_regs_fence16(A0);
+        }
       }
       release_acc(hb);
       return true;
@@ -464,103 +523,96 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       const uint32_t tb = t_lane + hb * 256u;
       const float* dlo = a.dlo + (long long)t * n;
       const float* dhi = a.dhi + (long long)t * n;
-      // Jacobian rows: lanes whose lower/upper row needs the Jacobian row of the same state from the next
-      // lane quarter (rows 30, 31 and 63 of a 126-row tile) read it from the exchange buffer
+      // Jacobian rows: the lower/upper rows of a state whose Jacobian row sits in the next lane quarter
+      // (rows 30, 31 and 63 of a 126-row tile) read it from the exchange buffer, the others by shuffle
       const int role = ri.isJ ? 2 : (ri.neg ? 1 : 0);
       const int src = lane + 2 - role;
       const bool importer = OUT && ri.bound && src >= 32;
       const bool exporter = OUT && ri.isJ && lane < 2;
       const int dcol = (OUT && a.residual && ri.bound) ? ri.idx : -1;   // diagonal column of the state
-      for (int j0 = c0 + 16 * cq; j0 < c0 + nc; j0 += 64) {
-        float lam[16];
-        tmem_ld16(tb + (uint32_t)(j0 - c0), lam);
-        float jl[16], jh[16];
+      auto chunk = [&](const float lam[32], int j0) -> bool {
+        const float* xb = xch;
         if (OUT) {
-          float* xb = xch + ((cq * 2 + (int)(xph & 1u)) * 2) * 16;
+          float* xw = xch + ((cq * 2 + (int)(xph & 1u)) * 2) * 32;
+          xb = xw;
           if (exporter)
 #pragma unroll
-            for (int e = 0; e < 16; e += 4)
-              *reinterpret_cast<float4*>(xb + (q - 1) * 16 + e) = make_float4(lam[e], lam[e + 1], lam[e + 2], lam[e + 3]);
+            for (int e = 0; e < 32; e += 4)
+              *reinterpret_cast<float4*>(xw + (q - 1) * 32 + e) = make_float4(lam[e], lam[e + 1], lam[e + 2], lam[e + 3]);
           if (ri.isJ && ri.valid) {
             // this Jacobian row chunk -> A (residual: + I) and B
             const int l = ri.idx;
+            float* Ar = a.A ? a.A + ((long long)t * n_x + l) * n_x : nullptr;
+            float* Br = a.B ? a.B + ((long long)t * n_x + l) * (n - n_x) : nullptr;
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
+            for (int e = 0; e < 32; ++e) {
               const int m = j0 + e;
               if (m < n_x) {
-                if (a.A) a.A[((long long)t * n_x + l) * n_x + m] = (a.residual && m == l) ? 1.f + lam[e] : lam[e];
-              } else if (a.B) {
-                a.B[((long long)t * n_x + l) * (n - n_x) + (m - n_x)] = lam[e];
+                if (Ar) Ar[m] = (a.residual && m == l) ? 1.f + lam[e] : lam[e];
+              } else if (Br) {
+                Br[m - n_x] = lam[e];
               }
             }
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(&xbar[cq]);
           if (!mbar_wait(&xbar[cq], xph & 1u)) return false;
-#pragma unroll
-          for (int e = 0; e < 16; ++e) jl[e] = __shfl_sync(0xffffffffu, lam[e], src & 31);
-          if (importer)
-#pragma unroll
-            for (int e = 0; e < 16; ++e) jl[e] = xb[q * 16 + e];
           ++xph;
-#pragma unroll
-          for (int e = 0; e < 16; ++e) jh[e] = jl[e];
-          if ((unsigned)(dcol - j0) < 16u) {
-            // the returned A has 1 + J on the diagonal: J_eff = fl(1 + J) - 1, enclosed
-#pragma unroll
-            for (int e = 0; e < 16; ++e)
-              if (j0 + e == dcol) {
-                const float aret = 1.f + jl[e];
-                jl[e] = __fsub_rd(aret, 1.f);
-                jh[e] = __fsub_ru(aret, 1.f);
-              }
-          }
         }
-        if (ri.bound) {
-          float dl[16], dh[16];
 #pragma unroll
-          for (int e = 0; e < 16; e += 4) {
-            const float4 x = __ldg(reinterpret_cast<const float4*>(dlo + j0 + e));
-            const float4 y = __ldg(reinterpret_cast<const float4*>(dhi + j0 + e));
-            dl[e] = x.x; dl[e + 1] = x.y; dl[e + 2] = x.z; dl[e + 3] = x.w;
-            dh[e] = y.x; dh[e + 1] = y.y; dh[e + 2] = y.z; dh[e + 3] = y.w;
-          }
+        for (int e4 = 0; e4 < 32; e4 += 4) {
+          const float4 dl4 = __ldg(reinterpret_cast<const float4*>(dlo + j0 + e4));
+          const float4 dh4 = __ldg(reinterpret_cast<const float4*>(dhi + j0 + e4));
+          const float dl[4] = {dl4.x, dl4.y, dl4.z, dl4.w}, dh[4] = {dh4.x, dh4.y, dh4.z, dh4.w};
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
+          for (int u = 0; u < 4; ++u) {
+            const int e = e4 + u;
             float mlo = lam[e], mhi = lam[e];
             if (OUT) {
+              float jv = __shfl_sync(0xffffffffu, lam[e], src & 31);
+              if (importer) jv = xb[q * 32 + e];
+              float jl = jv, jh = jv;
+              if (j0 + e == dcol) {
+                // the returned A has 1 + J on the diagonal: J_eff = fl(1 + J) - 1, enclosed
+                const float aret = 1.f + jv;
+                jl = __fsub_rd(aret, 1.f);
+                jh = __fsub_ru(aret, 1.f);
+              }
               // lower rows: M = lam - J; upper rows (lam = -Lambda^U): M = lam + J
-              const float pl = ri.neg ? jl[e] : -jh[e], ph = ri.neg ? jh[e] : -jl[e];
+              const float pl = ri.neg ? jl : -jh, ph = ri.neg ? jh : -jl;
               mlo = __fadd_rd(lam[e], pl);
               mhi = __fadd_ru(lam[e], ph);
             }
             // [mlo, mhi] x [dlo, dhi] with dlo <= 0 <= dhi: min = min(mlo dhi, mhi dlo)
-            const float term = fminf(__fmul_rd(mlo, dh[e]), __fmul_rd(mhi, dl[e]));
-            if (e & 1) sum.y = __fadd_rd(sum.y, term);
+            const float term = fminf(__fmul_rd(mlo, dh[u]), __fmul_rd(mhi, dl[u]));
+            if (u & 1) sum.y = __fadd_rd(sum.y, term);
             else sum.x = __fadd_rd(sum.x, term);
           }
         }
+        return true;
+      };
+      // 32-column chunks j0 = c0 + 32 cq + 64 c
+      for (int j0 = c0 + 32 * cq; j0 < c0 + nc; j0 += 64) {
+        float L0[32];
+        tmem_ld32_async(tb + (uint32_t)(j0 - c0), L0);
+        tmem_wait32(L0);
+        if (!chunk(L0, j0)) return false;
       }
       release_acc(hb);
       return true;
     };
 
     // combine the column groups of every row and write the bounds of an item
-    auto finalize = [&](int t, int tile, const RowInfo& ri, float2 sum, float2 beta, float2 infl,
-                        float ucon) -> bool {
-      float* st = stat + (r * 4 + cq) * 3;
+    auto finalize = [&](int t, int tile, const RowInfo& ri, float2 sum, const float2 (&beta)[2],
+                        const float2 (&infl)[2], float ucon) -> bool {
+      float* st = stat + (r * 2 + cq) * 3;
       st[0] = __fadd_rd(sum.x, sum.y);
-      st[1] = __fadd_rd(beta.x, beta.y);
-      st[2] = EPS ? __fadd_ru(infl.x, infl.y) : 0.f;
+      st[1] = __fadd_rd(__fadd_rd(beta[0].x, beta[0].y), __fadd_rd(beta[1].x, beta[1].y));
+      st[2] = EPS ? __fadd_ru(__fadd_ru(infl[0].x, infl[0].y), __fadd_ru(infl[1].x, infl[1].y)) : 0.f;
       if (!epi_sync()) return false;
       if (cq == 0 && ri.bound) {
-        const float* s0 = stat + r * 12;
-        float tot = s0[0], bsum = s0[1], isum = s0[2];
-        for (int c = 1; c < 4; ++c) {
-          tot = __fadd_rd(tot, s0[3 * c]);
-          bsum = __fadd_rd(bsum, s0[3 * c + 1]);
-          isum = __fadd_ru(isum, s0[3 * c + 2]);
-        }
+        const float* s0 = stat + r * 6;
+        const float tot = __fadd_rd(s0[0], s0[3]), bsum = __fadd_rd(s0[1], s0[4]), isum = __fadd_ru(s0[2], s0[5]);
         // lower bound of this row's (possibly negated) chain value; the inflation is inside beta
         const float val = __fsub_rd(__fadd_rd(tot, bsum), ucon);
         const bool nonfinite = !isfinite(val);
@@ -583,7 +635,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
         if (!epi_sync()) return false;
         const int l0 = tile * (a.rows_per_tile / 3);
         const int nl = min(a.rows_per_tile / 3, n_x - l0);
-        for (int ll = etid; ll < nl; ll += kTcEpiWarps * 32) {
+        for (int ll = etid; ll < nl; ll += kEThreads) {
           const long long o = (long long)t * n_x + l0 + ll;
           if (EPS && a.eps) a.eps[o] = fmaxf(slk[3 * ll], slk[3 * ll + 1]);
           if (a.gamma_c) {
@@ -600,7 +652,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
 
     const float2 z2 = make_float2(0.f, 0.f);
     int item = blockIdx.x;
-    float2 beta = z2, infl = z2;
+    float2 beta[2] = {z2, z2}, infl[2] = {z2, z2};
     float ucon = 0.f;
     if (item < n_items) {
       // first item's prologue
@@ -629,14 +681,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       if (!ok) break;
       // the next item's prologue, built while the tensor cores run this item's final stage
       apend |= (1u << (a.widths[1] / 64)) - 1u;
-      float2 beta_n = z2, infl_n = z2;
+      float2 beta_n[2] = {z2, z2}, infl_n[2] = {z2, z2};
       float ucon_n = 0.f;
       if (next < n_items) {
         const int tn = next / a.tiles_per_t;
         const int vcur = vb;
         if (!install()) { ok = false; break; }
         prefetch_next(tn, target - 1, next + gridDim.x);
-        if (!prologue(tn, row_info(a, next - tn * a.tiles_per_t, r), vcur, beta_n, infl_n, ucon_n)) { ok = false; break; }
+        if (!prologue(tn, row_info(a, next - tn * a.tiles_per_t, r), vcur, beta_n, infl_n, ucon_n)) {
+          ok = false;
+          break;
+        }
       }
       // final stage: concretise over the box
       float2 sum = z2;
@@ -645,11 +700,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
         ok = conc_job(t, ri, jc & 1u, h ? split0 : 0, h ? N0 - split0 : split0, sum);
       if (!ok) break;
       if (!finalize(t, tile, ri, sum, beta, infl, ucon)) { ok = false; break; }
-      beta = beta_n;
-      infl = infl_n;
+      beta[0] = beta_n[0];
+      beta[1] = beta_n[1];
+      infl[0] = infl_n[0];
+      infl[1] = infl_n[1];
       ucon = ucon_n;
       if (*(volatile int*)&s_abort) ok = false;
     }
+    cp_async_wait_all();
     if (!ok) {
       s_abort = 1;
       if (lane == 0) atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
@@ -730,13 +788,12 @@ leb_status tc_prepare(Ctx& c) {
     if (r != CUDA_SUCCESS) return LEB_ERR_UNSUPPORTED;
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return LEB_ERR_CUDA;
-  if (cudaFuncSetAttribute(crown_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(crown_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(crown_tc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) !=
-          cudaSuccess)
-    return LEB_ERR_CUDA;
+  const void* kernels[] = {(const void*)crown_tc_kernel<false, false, 0>, (const void*)crown_tc_kernel<true, false, 0>,
+                           (const void*)crown_tc_kernel<true, true, 0>,   (const void*)crown_tc_kernel<false, false, 1>,
+                           (const void*)crown_tc_kernel<true, false, 1>,  (const void*)crown_tc_kernel<true, true, 1>};
+  for (const void* k : kernels)
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) != cudaSuccess)
+      return LEB_ERR_CUDA;
   return LEB_OK;
 }
 
@@ -815,9 +872,15 @@ leb_status tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, 
   const int grid = items < c.sm_count ? items : c.sm_count;
   if (grid == 0) return LEB_OK;
   timer_begin(c, s, "crown_tc_kernel");
-  if (!output) crown_tc_kernel<false, false><<<grid, kTcThreads, kTcSmem, s>>>(a);
-  else if (eps) crown_tc_kernel<true, true><<<grid, kTcThreads, kTcSmem, s>>>(a);
-  else crown_tc_kernel<true, false><<<grid, kTcThreads, kTcSmem, s>>>(a);
+  if (a.fmt == 0) {
+    if (!output) crown_tc_kernel<false, false, 0><<<grid, kTcThreads, kTcSmem, s>>>(a);
+    else if (eps) crown_tc_kernel<true, true, 0><<<grid, kTcThreads, kTcSmem, s>>>(a);
+    else crown_tc_kernel<true, false, 0><<<grid, kTcThreads, kTcSmem, s>>>(a);
+  } else {
+    if (!output) crown_tc_kernel<false, false, 1><<<grid, kTcThreads, kTcSmem, s>>>(a);
+    else if (eps) crown_tc_kernel<true, true, 1><<<grid, kTcThreads, kTcSmem, s>>>(a);
+    else crown_tc_kernel<true, false, 1><<<grid, kTcThreads, kTcSmem, s>>>(a);
+  }
   timer_end(c, s);
   return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
 }
