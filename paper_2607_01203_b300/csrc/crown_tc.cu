@@ -52,7 +52,7 @@ constexpr int kTcNSB = 2;                       // B ring stages
 constexpr int kTcBRows = 256;                   // N rows of one B tile (the MMA's N)
 constexpr int kTcBStage = kTcBRows * 128;       // 256 rows x 64 K x 2 bytes
 constexpr int kTcARegion = 128 * 512 * 2;       // 128 rows x 512 K x 2 bytes (8 blocks of 16 KB)
-constexpr int kTcVecBuf = 512 * 16 + 512 * 4 + 512 * 4;   // per-neuron vectors: {sL, sU, tau'L, tau'U}, D, w
+constexpr int kTcVecBuf = 512 * 24 + 512 * 4;   // per-neuron line slots {s, tau'} x {lower, upper, Jacobian}, w
 constexpr int kTcStat = 128 * 2 * 3 * 4;        // [row][column group][3]
 constexpr int kTcVals = 2 * 128 * 4;            // [128] final values, [128] stated slack
 constexpr int kTcXch = 2 * 2 * 2 * 32 * 4;      // [column group][buffer][slot][32] Jacobian values
@@ -105,28 +105,28 @@ __device__ __forceinline__ uint32_t pack2(float x, float y) {
 }
 
 // Row pass over 16 columns j0..j0+15 of a chain row (lam: this row's coefficients on the neurons of the
-// hidden layer whose vectors are staged). sv[j] = {sL, sU, tau'L, tau'U}, sd[j] = sigma'(z^_j),
-// sw[j] = inflation weight. Bound rows take the lower line where lam >= 0, else the upper line; Jacobian
-// rows (OUT only) take sigma'. Writes the next operand lam o s (packed pairs) and accumulates
-// beta += lam tau' rounded down (and, EPS, the inflation sum |lam s| w rounded up, for the stated slack).
+// hidden layer whose vectors are staged). Neuron j has three line slots sl[3 j + k] = {slope, offset}:
+// k = 0 the lower line {sL, tau'L}, k = 1 the upper line {sU, tau'U}, k = 2 the Jacobian {sigma'(z^), 0}.
+// A bound row takes the lower line where lam >= 0 and the upper line where lam < 0, i.e. k = sign bit of
+// lam (smask = 1, jsel = 0); a Jacobian row always takes k = 2 (smask = 0, jsel = 2). One 8-byte load per
+// element carries the selected slope and offset. Writes the next operand lam o s (packed pairs) and
+// accumulates beta += lam tau' rounded down (and, EPS, the inflation sum |lam s| w rounded up, sw[j] = w).
 template <bool OUT, bool EPS, int FMT>
-__device__ __forceinline__ void row_pass16(const float lam[16], int j0, const float4* __restrict__ sv,
-                                           const float* __restrict__ sd, const float* __restrict__ sw, bool isJ,
+__device__ __forceinline__ void row_pass16(const float lam[16], int j0, const float2* __restrict__ sl,
+                                           const float* __restrict__ sw, uint32_t smask, uint32_t jsel,
                                            uint32_t packed[8], float2& beta, float2& infl) {
+  const float2* base = sl + 3 * j0 + (OUT ? jsel : 0u);
 #pragma unroll
   for (int e = 0; e < 16; e += 2) {
-    const float4 v0 = sv[j0 + e], v1 = sv[j0 + e + 1];
     const float2 l = make_float2(lam[e], lam[e + 1]);
-    const bool p0 = l.x >= 0.f, p1 = l.y >= 0.f;
-    float2 s = make_float2(p0 ? v0.x : v0.y, p1 ? v1.x : v1.y);
-    const float2 tau = make_float2(p0 ? v0.z : v0.w, p1 ? v1.z : v1.w);
+    uint32_t k0 = __float_as_uint(l.x) >> 31, k1 = __float_as_uint(l.y) >> 31;
     if (OUT) {
-      const float2 d = *reinterpret_cast<const float2*>(sd + j0 + e);
-      s.x = isJ ? d.x : s.x;
-      s.y = isJ ? d.y : s.y;
+      k0 &= smask;
+      k1 &= smask;
     }
-    const float2 av = __fmul2_rn(l, s);
-    beta = __ffma2_rd(l, tau, beta);
+    const float2 v0 = base[3 * e + k0], v1 = base[3 * (e + 1) + k1];
+    const float2 av = __fmul2_rn(l, make_float2(v0.x, v1.x));
+    beta = __ffma2_rd(l, make_float2(v0.y, v1.y), beta);
     if (EPS) {
       const float2 w = *reinterpret_cast<const float2*>(sw + j0 + e);
       infl = __ffma2_ru(make_float2(fabsf(av.x), fabsf(av.y)), w, infl);
@@ -339,30 +339,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       ++nbar;
       return res;
     };
-    auto vptr = [&](int b, float4*& sv, float*& sd, float*& sw) {
+    auto vptr = [&](int b, float2*& sl, float*& sw) {
       uint8_t* p = Vsm + b * kTcVecBuf;
-      sv = reinterpret_cast<float4*>(p);
-      sd = reinterpret_cast<float*>(p + 512 * 16);
-      sw = reinterpret_cast<float*>(p + 512 * 20);
+      sl = reinterpret_cast<float2*>(p);
+      sw = reinterpret_cast<float*>(p + 512 * 24);
     };
     // Asynchronous copy of the raw vectors of hidden layer hl of timestep t into buffer vb:
-    // sv[j] = {sL, sU, tL, tU}, sd[j] = D, sw[j] = w. The buffer was last read two sets ago.
+    // slots {sL, tL}, {sU, tU}, {D, -} and sw[j] = w. The buffer was last read two sets ago.
     auto prefetch = [&](int t, int hl) {
       const int width = a.widths[hl + 1];
       pf_width = width;
-      float4* sv;
-      float* sd;
+      float2* sl;
       float* sw;
-      vptr(vb, sv, sd, sw);
+      vptr(vb, sl, sw);
       const long long o0 = (long long)t * a.H + a.hoff[hl];
       for (int j = etid; j < width; j += kEThreads) {
         const long long o = o0 + j;
-        float* e4 = reinterpret_cast<float*>(sv + j);
-        cp_async4(e4, a.sL + o);
-        cp_async4(e4 + 1, a.sU + o);
-        cp_async4(e4 + 2, a.tL + o);
-        cp_async4(e4 + 3, a.tU + o);
-        cp_async4(sd + j, a.D + o);
+        float* e6 = reinterpret_cast<float*>(sl + 3 * j);
+        cp_async4(e6, a.sL + o);
+        cp_async4(e6 + 1, a.tL + o);
+        cp_async4(e6 + 2, a.sU + o);
+        cp_async4(e6 + 3, a.tU + o);
+        cp_async4(e6 + 4, a.D + o);
         if (!tight) cp_async4(sw + j, a.winf + o);
       }
       cp_async_commit();
@@ -371,24 +369,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     // padding up to a multiple of 64, make it visible to every epilogue warp
     auto install = [&]() -> bool {
       cp_async_wait_all();
-      float4* sv;
-      float* sd;
+      float2* sl;
       float* sw;
-      vptr(vb, sv, sd, sw);
+      vptr(vb, sl, sw);
       const int wp = (pf_width + 63) & ~63;
       for (int j = etid; j < wp; j += kEThreads) {
         if (j < pf_width) {
           if (!tight) {
-            const float4 v = sv[j];
             const float w = sw[j];
-            sv[j].z = __fmaf_rd(-fabsf(v.x), w, v.z);
-            sv[j].w = __fmaf_ru(fabsf(v.y), w, v.w);
+            const float2 lo = sl[3 * j], up = sl[3 * j + 1];
+            sl[3 * j].y = __fmaf_rd(-fabsf(lo.x), w, lo.y);
+            sl[3 * j + 1].y = __fmaf_ru(fabsf(up.x), w, up.y);
           } else {
             sw[j] = 0.f;
           }
+          sl[3 * j + 2].y = 0.f;
         } else {
-          sv[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-          sd[j] = 0.f;
+          sl[3 * j] = make_float2(0.f, 0.f);
+          sl[3 * j + 1] = make_float2(0.f, 0.f);
+          sl[3 * j + 2] = make_float2(0.f, 0.f);
           sw[j] = 0.f;
         }
       }
@@ -432,11 +431,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     // row pass of 16 columns j0..j0+15 into packed[8]
     auto pass16 = [&](const float lam[16], int j0, int vcur, const RowInfo& ri, uint32_t packed[8], float2& beta,
                       float2& infl) {
-      float4* sv;
-      float* sd;
+      float2* sl;
       float* sw;
-      vptr(vcur, sv, sd, sw);
-      row_pass16<OUT, EPS, FMT>(lam, j0, sv, sd, sw, ri.isJ, packed, beta, infl);
+      vptr(vcur, sl, sw);
+      row_pass16<OUT, EPS, FMT>(lam, j0, sl, sw, ri.isJ ? 0u : 1u, ri.isJ ? 2u : 0u, packed, beta, infl);
     };
     // this warp's 32 columns of operand block b -> shared memory, then the block is announced
     auto put32 = [&](int j0, int b, const uint32_t packed[16]) -> bool {
