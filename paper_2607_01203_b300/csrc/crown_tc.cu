@@ -528,6 +528,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       const bool importer = OUT && ri.bound && src >= 32;
       const bool exporter = OUT && ri.isJ && lane < 2;
       const int dcol = (OUT && a.residual && ri.bound) ? ri.idx : -1;   // diagonal column of the state
+      // A and B rows start on 16-byte boundaries when n_x and n_u are multiples of 4 (A, B, the workspace
+      // and every device buffer the binding allocates are 16-byte aligned)
+      const bool vec_ab = (n_x % 4 == 0) && ((n - n_x) % 4 == 0) &&
+                          ((reinterpret_cast<uintptr_t>(a.A) | reinterpret_cast<uintptr_t>(a.B)) & 15u) == 0;
       auto chunk = [&](const float lam[32], int j0) -> bool {
         const float* xb = xch;
         if (OUT) {
@@ -538,17 +542,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
             for (int e = 0; e < 32; e += 4)
               *reinterpret_cast<float4*>(xw + (q - 1) * 32 + e) = make_float4(lam[e], lam[e + 1], lam[e + 2], lam[e + 3]);
           if (ri.isJ && ri.valid) {
-            // this Jacobian row chunk -> A (residual: + I) and B
+            // this Jacobian row chunk -> A (residual: + I) and B, four columns per store where the rows allow
             const int l = ri.idx;
             float* Ar = a.A ? a.A + ((long long)t * n_x + l) * n_x : nullptr;
             float* Br = a.B ? a.B + ((long long)t * n_x + l) * (n - n_x) : nullptr;
+            if (vec_ab) {
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              const int m = j0 + e;
-              if (m < n_x) {
-                if (Ar) Ar[m] = (a.residual && m == l) ? 1.f + lam[e] : lam[e];
-              } else if (Br) {
-                Br[m - n_x] = lam[e];
+              for (int e = 0; e < 32; e += 4) {
+                const int m = j0 + e;
+                float4 v = make_float4(lam[e], lam[e + 1], lam[e + 2], lam[e + 3]);
+                if (m < n_x) {
+                  if (a.residual && (unsigned)(l - m) < 4u) {
+                    const int d = l - m;
+                    v.x += d == 0 ? 1.f : 0.f;
+                    v.y += d == 1 ? 1.f : 0.f;
+                    v.z += d == 2 ? 1.f : 0.f;
+                    v.w += d == 3 ? 1.f : 0.f;
+                  }
+                  if (Ar) *reinterpret_cast<float4*>(Ar + m) = v;
+                } else if (Br) {
+                  *reinterpret_cast<float4*>(Br + (m - n_x)) = v;
+                }
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < 32; ++e) {
+                const int m = j0 + e;
+                if (m < n_x) {
+                  if (Ar) Ar[m] = (a.residual && m == l) ? 1.f + lam[e] : lam[e];
+                } else if (Br) {
+                  Br[m - n_x] = lam[e];
+                }
               }
             }
           }
