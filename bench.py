@@ -42,6 +42,20 @@ PBH_BYTES_PER_TS = 4 * (224 * 336 + 168 + 56 + 2 * 168 + 168 * 168 + 168 * 56)  
 MLP_WIDTHS = (224, 512, 512, 512, 168)
 PROPOSER_FLOP = 2 * (392 * 256 + 256 * 256 + 256 * 336)                           # 503,808 per sample
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch and timestep of each form's timed
+# kernels, from one ncu capture of the small-batch bench (--quick: 16 x 50 quad-chain timesteps, 8 x 50
+# tanh-MLP timesteps); traffic grows in proportion to the timesteps a launch processes, so a launch of T
+# timesteps moves T times this. Summary and command: profiles/dram_traffic_bench_kernels_quick.md.
+DRAM_BYTES_PER_TS_LAUNCH = {
+    "pbh": 311_519_744 / 800,                  # pbh_zono_tma_kernel
+    "crown": 44_803_072 / (3 * 400),           # crown_tc_kernel, mean over its 3 launches
+    "backward": 86_559_744 / (5 * 400),        # 2 tight crown_tc_kernel + 3 adjoint_tc_kernel launches, mean
+}
+
+
+def dram_traffic(form, units_per_launch):
+    return round(DRAM_BYTES_PER_TS_LAUNCH[form] * units_per_launch)
+
 
 def crown_flop_per_ts(w=MLP_WIDTHS):
     """Back-substitution FLOPs per timestep: every chain row times every weight it passes through.
@@ -180,7 +194,7 @@ class PbhForm(Form):
     def roofline(self, pk, ms, launches, kernel):
         achieved = PBH_BYTES_PER_TS * self.T / (ms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
+                "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": dram_traffic("pbh", self.T),
                 "peak_src": pk["src"] + " hbm_gbs (STREAM-style copy)", "kernel": kernel,
                 "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
                 "bytes_per_unit": PBH_BYTES_PER_TS, "units_per_launch": self.T // max(launches, 1)}
@@ -255,7 +269,7 @@ class CrownForm(Form):
         flop = crown_flop_per_ts() * self.T
         achieved = flop / (ms * 1e-3) / 1e12
         return {"bound": "tensor", "achieved": round(achieved, 1), "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                "frac": round(achieved / pk["bf16_tflops"], 4), "traffic": None,
+                "frac": round(achieved / pk["bf16_tflops"], 4), "traffic": dram_traffic("crown", self.T),
                 "peak_src": pk["src"] + " bf16_tflops (cuBLAS bf16 burst; FP16 dense rate is the same)",
                 "kernel": kernel, "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
                 "flop_per_unit": crown_flop_per_ts(), "units_per_step": self.T}
@@ -318,7 +332,7 @@ class BackwardForm(Form):
         tc = "tc" in kernel
         peak = pk["bf16_tflops"] if tc else fp32_simt_peak_tflops(pk)
         return {"bound": "tensor" if tc else "alu", "achieved": round(achieved, 2), "peak": round(peak, 1),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": dram_traffic("backward", self.T),
                 "peak_src": (pk["src"] + " bf16_tflops") if tc else
                 "FP32 FMA peak derived: 148 SM x 128 lanes x 2 FLOP x max SM clock (MEASURED_PEAKS sm_max_mhz)",
                 "kernel": kernel, "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
