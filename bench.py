@@ -1,6 +1,6 @@
 """Benchmark of the certified LEB hot path on B300 (one JSON line on rank 0).
 
-A step is one pass of the whole hot path over one batch of seeded synthetic input, four forms in turn:
+A step is one pass of the whole hot path over one batch of seeded synthetic input, five forms in turn:
   * plain form (pbh): path-based Hessian bounds (Thm. 1) for the 28-quadrotor spring chain
     (n_x = 168, n_u = 56), 256 trajectories x N = 50 (T = 12800), zonotope tube sets with 2 n_x = 336
     generators, A_k and B_k written;
@@ -10,9 +10,12 @@ A step is one pass of the whole hot path over one batch of seeded synthetic inpu
   * backward: the adjoint d(r_lo, r_hi)/d(x~, u~, radii) of the crown form's bounds with random cotangents;
   * proposer: the learned proposer's inference on 12800 quad-chain inputs (trained once at start-up on
     10^5 certified bounds; its training step, error and the certified kernel's time on the same inputs
-    are reported beside it).
+    are reported beside it);
+  * pbh_grad: the adjoint of the PBH bound of the same chain (256 x 50 timesteps, box sets, random
+    cotangents), with the nominal refinement of Table II (projected gradient descent on the PBH width
+    against random sampling) measured once at start-up and reported beside it.
 ``value`` = certified timestep-bounds per second of the whole step (pbh + crown timesteps over the time
-of all four forms), summed over ranks.
+of all five forms), summed over ranks.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--forms pbh,crown,...]
 For N > 1 it runs under torchrun, one independent replica per GPU (every timestep's bound is independent,
@@ -446,6 +449,84 @@ class ProposerForm(Form):
         return ms, hX.numel() * 4, hY.numel() * 4
 
 
+class PbhGradForm(Form):
+    """Adjoint of the PBH bound (differentiable LEBs, Sec. III-D) of the 28-quadrotor chain, 256 x 50
+    timesteps with box sets (state radii U[0.01, 0.1], control radii 0.05), random cotangents. Beside it,
+    once at start-up (untimed), the nominal refinement of Table II: projected gradient descent on the PBH
+    width within eps = 0.05 of 1280 nominal points against random sampling with as many bound evaluations.
+
+    Bytes per timestep: the rows it reads (x~ 168, u~ 56, radii 224, two cotangent rows of 168) and
+    writes (g_x 168, g_u 56, g_radii 224), FP32, every sector of them touched: 4,928 B."""
+    name = "pbh_grad"
+    which = 1
+    BYTES_PER_TS = 4 * (168 + 56 + 224 + 2 * 168 + 168 + 56 + 224)
+
+    def __init__(self, torch, dev, quick=False):
+        from paper_2607_01203_b300 import binding, inputs
+        self.torch = torch
+        self.w = inputs.proposer_data(seed=1779, n_rollouts=16 if quick else 256)
+        w = self.w
+        self.T = w.T
+        self.handle = binding.quad_chain(w.n_quads, **w.params, spring_k=w.spring_k)
+        self.x = torch.as_tensor(w.x_nom).to(dev)
+        self.u = torch.as_tensor(w.u_nom).to(dev)
+        self.r = torch.as_tensor(w.radii).to(dev)
+        g = torch.Generator(device="cpu").manual_seed(3)
+        self.glo = torch.randn(self.T, 168, generator=g).to(dev)
+        self.ghi = torch.randn(self.T, 168, generator=g).to(dev)
+        self.handle.bounds_backward(self.x, self.u, self.r, self.glo, self.ghi)
+        torch.cuda.synchronize()
+        self.pgd = self._table2(torch, dev, 1280 if not quick else 320)
+        self.desc = f"PBH adjoint, 28-quadrotor chain n_x=168 n_u=56, {self.T // 50} traj x N=50, box sets"
+
+    def _table2(self, torch, dev, n, eps=0.05, steps=10):
+        x0, u0, r = self.x[:n].contiguous(), self.u[:n].contiguous(), self.r[:n].contiguous()
+        h = self.handle
+        h.refine_nominal_pgd(x0, u0, r, eps=eps, lr=eps / 5, steps=steps)
+        torch.cuda.synchronize()
+        ms = timed_loop(torch, lambda: h.refine_nominal_pgd(x0, u0, r, eps=eps, lr=eps / 5, steps=steps), 3)
+        _, _, w0, w1, _ = h.refine_nominal_pgd(x0, u0, r, eps=eps, lr=eps / 5, steps=steps)
+        K = 2 * steps + 1
+        g = torch.Generator(device=dev).manual_seed(11)
+        xs = (x0[:, None, :] + eps * (2 * torch.rand(n, K, 168, device=dev, generator=g) - 1)).reshape(-1, 168)
+        us = (u0[:, None, :] + eps * (2 * torch.rand(n, K, 56, device=dev, generator=g) - 1)).reshape(-1, 56)
+        rs = r[:, None, :].expand(n, K, 224).reshape(-1, 224).contiguous()
+        o = h.bounds(xs.contiguous(), us.contiguous(), radii=rs, want_AB=False)
+        ws = (o["r_hi"] - o["r_lo"]).sum(1).view(n, K).min(1).values
+        torch.cuda.synchronize()
+        per = 1.0 / 28   # mean over the 28 quadrotors' curved rows, like a per-system width
+        return {"timesteps": n, "eps": eps, "steps": steps, "mean_width_initial": round(float(w0.mean()) * per, 6),
+                "mean_width_sampling": round(float(ws.mean()) * per, 6), "mean_width_pgd": round(float(w1.mean()) * per, 6),
+                "pgd_better_pct": round(100.0 * float((w1 < ws).float().mean()), 1), "pgd_ms_per_call": round(ms, 3)}
+
+    def run(self):
+        self.handle.bounds_backward(self.x, self.u, self.r, self.glo, self.ghi)
+
+    def roofline(self, pk, ms, launches, kernel):
+        achieved = self.BYTES_PER_TS * self.T / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
+                "peak_src": pk["src"] + " hbm_gbs (STREAM-style copy)", "kernel": kernel,
+                "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
+                "bytes_per_unit": self.BYTES_PER_TS, "units_per_launch": self.T // max(launches, 1)}
+
+    def e2e(self, steps):
+        torch = self.torch
+        hx, hu, hr = (a.cpu().pin_memory() for a in (self.x, self.u, self.r))
+        hgl, hgh = self.glo.cpu().pin_memory(), self.ghi.cpu().pin_memory()
+        dx, du, dr, dgl, dgh = (torch.empty_like(a) for a in (self.x, self.u, self.r, self.glo, self.ghi))
+        outs = [torch.empty(self.T, k).pin_memory() for k in (168, 56, 224)]
+
+        def one():
+            for d, hsrc in ((dx, hx), (du, hu), (dr, hr), (dgl, hgl), (dgh, hgh)):
+                d.copy_(hsrc, non_blocking=True)
+            g = self.handle.bounds_backward(dx, du, dr, dgl, dgh)
+            for o, gg in zip(outs, g[:3]):
+                o.copy_(gg, non_blocking=True)
+        ms = timed_loop(torch, one, steps)
+        return ms, sum(a.numel() * 4 for a in (hx, hu, hr, hgl, hgh)), sum(o.numel() * 4 for o in outs)
+
+
 def timed_loop(torch, fn, steps):
     """CUDA-event time per call of fn on the current stream (after one untimed call)."""
     fn()
@@ -535,7 +616,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--forms", default="pbh,crown,backward,proposer")
+    ap.add_argument("--forms", default="pbh,crown,backward,proposer,pbh_grad")
     ap.add_argument("--quick", action="store_true", help="small batches (smoke runs, not a bench value)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -565,6 +646,8 @@ def main():
             forms.append(BackwardForm(torch, dev, args.quick, crown))
         elif nm == "proposer":
             forms.append(ProposerForm(torch, dev, args.quick))
+        elif nm == "pbh_grad":
+            forms.append(PbhGradForm(torch, dev, args.quick))
         else:
             raise SystemExit(f"unknown form {nm}")
     handles = {id(f.handle): f.handle for f in forms if f.handle is not None}
@@ -634,8 +717,10 @@ def main():
         d = {"ms": round(form_ms[f.name], 4), "units": f.units(), "workload": f.desc, "roofline": roof[f.name]}
         if f.units():
             d["value"] = round(f.units() / (form_ms[f.name] * 1e-3), 1)
-        if f.name == "backward":
+        if f.name in ("backward", "pbh_grad"):
             d["us_per_call"] = round(1e3 * form_ms[f.name], 1)
+        if f.name == "pbh_grad":
+            d["nominal_refinement_table2"] = f.pgd
         if f.name == "proposer":
             cms = f.certified_ms()
             d.update({"proposal_error_vs_certified": round(f.err, 4), "under_cover_fraction": round(f.under, 4),

@@ -144,13 +144,30 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
                       const leb_set* set, float* r_lo, float* r_hi, float* A, float* B,
                       const leb_options* opt, void* workspace, size_t ws_bytes, int* dev_flags, void* stream);
 
-/* ---- adjoint of the MLP bounds (differentiable LEBs, Sec. III-D) -------------------------------- */
-/* Box sets centred at the nominal only. Given g_rlo = dL/dr_lo and g_rhi = dL/dr_hi [T, n_x], writes
- * g_x [T, n_x], g_u [T, n_u], g_radii [T, n] = dL/d(x~, u~, radii) of the piecewise-smooth bound
- * (relaxation cases fixed at the evaluation point). All device pointers. */
+/* ---- adjoint of the bounds (differentiable LEBs, Sec. III-D) ------------------------------------ */
+/* Box sets centred at the nominal only (set->center NULL), uniform batches. Given g_rlo = dL/dr_lo and
+ * g_rhi = dL/dr_hi [T, n_x], writes g_x [T, n_x], g_u [T, n_u], g_radii [T, n] = dL/d(x~, u~, radii) of
+ * the piecewise-smooth bound with every case fixed at the evaluation point: the relaxation case of each
+ * neuron (MLP handles, Thms. 2-3) or the selected endpoint of each interval (quad-chain handles, Thm. 1).
+ * All device pointers. */
 leb_status leb_bounds_backward(leb_handle h, int T, const float* x_nom, const float* u_nom, const leb_set* set,
                                const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_radii,
                                void* workspace, size_t ws_bytes, int* dev_flags, void* stream);
+
+/* ---- nominal refinement by projected gradient descent (Sec. IV, Table II) ------------------------ */
+/* Minimises, per timestep, the summed width sum_l (r_hi - r_lo) of the Thm. 1 bound over nominal points in
+ * the box |x - x0| <= eps, |u - u0| <= eps (componentwise), for box sets of the given radii centred at the
+ * nominal. Each of `steps` steps moves every coordinate by lr against the sign of its gradient
+ * (leb_bounds_backward with cotangents -1 on r_lo, +1 on r_hi) and projects onto the box; the iterate with
+ * the smallest width is returned per timestep. Quad-chain handles, uniform batches.
+ * x0 [T, n_x], u0 [T, n_u], radii [T, n]: device inputs. x_opt [T, n_x], u_opt [T, n_u]: device outputs
+ * (best iterate). w_init, w_best [T]: device outputs (width at x0, u0 and at the best iterate), each may
+ * be NULL. workspace: device, 256-byte aligned, >= leb_refine_workspace_size(h, T). Errors as leb_bounds;
+ * eps, lr must be finite and >= 0. Synchronizes nothing; launches 4 + 4 steps kernels. */
+leb_status leb_refine_nominal_pgd(leb_handle h, int T, const float* x0, const float* u0, const float* radii,
+                                  float eps, float lr, int steps, float* x_opt, float* u_opt, float* w_init,
+                                  float* w_best, void* workspace, size_t ws_bytes, int* dev_flags, void* stream);
+leb_status leb_refine_workspace_size(leb_handle h, int T_max, size_t* bytes);
 
 /* ---- zonotope map of Sec. III-C as a standalone call -------------------------------------------- */
 /* c = (lo+hi)/2, r = (hi-lo)/2 + pad over count elements (device), r rounded up, c to nearest. */

@@ -7,7 +7,9 @@ points by projected gradient descent on the PBH bound's width (Sec. IV, Table II
 piecewise-smooth function of the nominal point and the tube radii: interval endpoints are minima and
 maxima of endpoint values, and the range of sin / cos over an interval is either an endpoint value or an
 interior extremum (+-1). Its gradient here is that of the same algorithm with every such selection
-fixed at the evaluation point, i.e. what automatic differentiation of Thm. 1 gives. It is obtained by
+fixed at the evaluation point, i.e. what automatic differentiation of Thm. 1 gives; where two candidates
+of a minimum or maximum are exactly equal (a kink) it is the average of their derivatives (torch's
+convention for min / max). It is obtained by
 evaluating Thm. 1 once more with FP64 torch tensors (the same steps as ``oracle.pbh.pbh``: box set
 centred at the nominal, displacement set, prefix sets X^(j), one interval term per structurally nonzero
 Hessian entry, Eq. 15) and back-propagating through it.

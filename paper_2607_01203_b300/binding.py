@@ -58,6 +58,7 @@ EXPORTS = [
     "leb_proposer_set_norm", "leb_proposer_forward", "leb_proposer_train_step", "leb_proposer_workspace_size",
     "leb_proposer_get_layer", "leb_proposer_set_layer", "leb_proposer_get_grad", "leb_selftest_point_enclosures",
     "leb_bounds_static", "leb_bounds_static_max_traj", "leb_proposer_fit_norm", "leb_proposer_set_periodic", "leb_timing", "leb_timing_read", "leb_status_string", "leb_version",
+    "leb_refine_nominal_pgd", "leb_refine_workspace_size",
 ]
 
 
@@ -109,6 +110,9 @@ def lib():
         L.leb_proposer_set_periodic.argtypes = [vp, C.POINTER(i32)]
         L.leb_timing.argtypes = [vp, i32]
         L.leb_timing_read.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(i32), C.c_char_p, sz]
+        L.leb_refine_nominal_pgd.argtypes = [vp, i32, vp, vp, vp, C.c_float, C.c_float, i32, vp, vp, vp, vp, vp, sz,
+                                             vp, vp]
+        L.leb_refine_workspace_size.argtypes = [vp, i32, C.POINTER(sz)]
         _lib = L
     return _lib
 
@@ -278,6 +282,26 @@ class Handle:
                                         _ptr(g_rhi.contiguous()), _ptr(g_x), _ptr(g_u), _ptr(g_r), _ptr(ws),
                                         ws.numel(), _ptr(flags), _stream()), "leb_bounds_backward")
         return g_x, g_u, g_r, flags
+
+    def refine_nominal_pgd(self, x0, u0, radii, eps: float, lr: float, steps: int):
+        """Projected gradient descent of every timestep's nominal point on the summed PBH width inside
+        the box |x - x0|, |u - u0| <= eps (leb_refine_nominal_pgd). Returns (x_opt, u_opt, w_init, w_best,
+        flags), device tensors."""
+        dev = x0.device
+        T = int(x0.shape[0])
+        f32 = dict(device=dev, dtype=torch.float32)
+        x_opt = torch.empty(T, self.n_x, **f32)
+        u_opt = torch.empty(T, self.n_u, **f32)
+        w0 = torch.empty(T, **f32)
+        w1 = torch.empty(T, **f32)
+        flags = torch.zeros(1, device=dev, dtype=torch.int32)
+        b = C.c_size_t()
+        check(lib().leb_refine_workspace_size(self.h, max(T, 1), C.byref(b)), "leb_refine_workspace_size")
+        ws = torch.empty(max(b.value, 256), dtype=torch.uint8, device=dev)
+        check(lib().leb_refine_nominal_pgd(self.h, T, _ptr(x0), _ptr(u0), _ptr(radii), float(eps), float(lr),
+                                           int(steps), _ptr(x_opt), _ptr(u_opt), _ptr(w0), _ptr(w1), _ptr(ws),
+                                           ws.numel(), _ptr(flags), _stream()), "leb_refine_nominal_pgd")
+        return x_opt, u_opt, w0, w1, flags
 
 
 def quad_chain(n_quads: int, mass: float, inertia: float, arm: float, g: float, dt: float, spring_k: float = 0.0,

@@ -163,6 +163,19 @@ leb_status tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, 
                     float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags,
                     bool tight = false);
 const void* tc_weight_t(const Ctx& c, int k);   // W_k^T in the operand format, [widths[k], widths[k+1]]
+// adjoint of the PBH bound of the quadrotor chain (box sets centred at the nominal); g_lo == nullptr:
+// cotangents -1 on r_lo and +1 on r_hi (the gradient of the summed width)
+leb_status pbh_bounds_backward(const Ctx& c, int T, const float* x_nom, const float* u_nom, const float* radii,
+                               const float* g_lo, const float* g_hi, float* g_x, float* g_u, float* g_rad, int* flags,
+                               cudaStream_t s);
+// projected-gradient pieces of leb_refine_nominal_pgd: per-timestep width and best iterate, a signed step
+// projected onto the box around the start, and an OR of a flag word into another
+leb_status pgd_track(const Ctx& c, int T, const float* r_lo, const float* r_hi, const float* x_cur,
+                     const float* u_cur, float* best, float* x_opt, float* u_opt, float* w_init, bool first,
+                     cudaStream_t s);
+leb_status pgd_step(const Ctx& c, long long count, float* v, const float* g, const float* v0, float lr, float eps,
+                    cudaStream_t s);
+leb_status or_flags(int* dst, const int* src, cudaStream_t s);
 // tensor-core adjoint chains (reduced-precision handles)
 leb_status adj_tc_prepare(Ctx& c);
 void adj_tc_release(Ctx& c);

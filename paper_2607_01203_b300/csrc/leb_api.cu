@@ -310,11 +310,16 @@ leb_status leb_bounds_backward(leb_handle h, int T, const float* x_nom, const fl
                                void* workspace, size_t ws_bytes, int* dev_flags, void* stream) {
   if (!h || !set || T < 0 || !dev_flags) return LEB_ERR_INVALID_ARG;
   h->timer.phase = 1;
-  if (h->kind != LEB_DYN_MLP) return LEB_ERR_UNSUPPORTED;
   if (set->kind != LEB_SET_BOX || set->center) return LEB_ERR_UNSUPPORTED;
   if (T > 0 && (!x_nom || !u_nom || !set->radii || !g_rlo || !g_rhi || !g_x || !g_u || !g_radii))
     return LEB_ERR_INVALID_ARG;
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return LEB_ERR_WORKSPACE;
+  if (h->kind == LEB_DYN_QUAD_CHAIN) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(dev_flags, 0, sizeof(int), s) != cudaSuccess) return LEB_ERR_CUDA;
+    return pbh_bounds_backward(*h, T, x_nom, u_nom, set->radii, g_rlo, g_rhi, g_x, g_u, g_radii, dev_flags, s);
+  }
+  if (h->kind != LEB_DYN_MLP) return LEB_ERR_UNSUPPORTED;
   MlpWs lay;
   const size_t need = kWsHeader + mlp_workspace_floats(*h, T, &lay) * sizeof(float);
   if (ws_bytes < need) return LEB_ERR_WORKSPACE;
@@ -322,6 +327,83 @@ leb_status leb_bounds_backward(leb_handle h, int T, const float* x_nom, const fl
   if (cudaMemsetAsync(dev_flags, 0, sizeof(int), s) != cudaSuccess) return LEB_ERR_CUDA;
   if (T == 0) return LEB_OK;
   return mlp_bounds_backward(*h, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, workspace, dev_flags, s);
+}
+
+// ---- nominal refinement (projected gradient descent on the PBH width) ----------------------------
+namespace {
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+// [leb_bounds workspace | inner flags | x | u | r_lo | r_hi | g_x | g_u | g_radii | best width]
+struct RefineWs {
+  size_t bounds, flags, x, u, rlo, rhi, gx, gu, gr, best, total;
+};
+RefineWs refine_layout(const Ctx& c, int T) {
+  RefineWs w;
+  const size_t nx = c.n_x, nu = c.n_u, Tz = (size_t)T;
+  size_t o = 0;
+  auto take = [&](size_t b) { const size_t r = o; o += align256(b); return r; };
+  w.bounds = take(pbh_ws_bytes(0));
+  w.flags = take(sizeof(int));
+  w.x = take(Tz * nx * 4);
+  w.u = take(Tz * nu * 4);
+  w.rlo = take(Tz * nx * 4);
+  w.rhi = take(Tz * nx * 4);
+  w.gx = take(Tz * nx * 4);
+  w.gu = take(Tz * nu * 4);
+  w.gr = take(Tz * (nx + nu) * 4);
+  w.best = take(Tz * 4);
+  w.total = o;
+  return w;
+}
+}  // namespace
+
+leb_status leb_refine_workspace_size(leb_handle h, int T_max, size_t* bytes) {
+  if (!h || !bytes || T_max < 0) return LEB_ERR_INVALID_ARG;
+  if (h->kind != LEB_DYN_QUAD_CHAIN) return LEB_ERR_UNSUPPORTED;
+  *bytes = refine_layout(*h, T_max).total;
+  return LEB_OK;
+}
+
+leb_status leb_refine_nominal_pgd(leb_handle h, int T, const float* x0, const float* u0, const float* radii,
+                                  float eps, float lr, int steps, float* x_opt, float* u_opt, float* w_init,
+                                  float* w_best, void* workspace, size_t ws_bytes, int* dev_flags, void* stream) {
+  if (!h || T < 0 || steps < 0 || !dev_flags) return LEB_ERR_INVALID_ARG;
+  if (h->kind != LEB_DYN_QUAD_CHAIN) return LEB_ERR_UNSUPPORTED;
+  if (!(eps >= 0.f) || !(lr >= 0.f) || !std::isfinite(eps) || !std::isfinite(lr)) return LEB_ERR_INVALID_ARG;
+  if (T > 0 && (!x0 || !u0 || !radii || !x_opt || !u_opt)) return LEB_ERR_INVALID_ARG;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return LEB_ERR_WORKSPACE;
+  const RefineWs L = refine_layout(*h, T);
+  if (ws_bytes < L.total) return LEB_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(dev_flags, 0, sizeof(int), s) != cudaSuccess) return LEB_ERR_CUDA;
+  if (T == 0) return LEB_OK;
+  char* ws = (char*)workspace;
+  int* inner = (int*)(ws + L.flags);
+  float *x = (float*)(ws + L.x), *u = (float*)(ws + L.u), *rlo = (float*)(ws + L.rlo), *rhi = (float*)(ws + L.rhi);
+  float *gx = (float*)(ws + L.gx), *gu = (float*)(ws + L.gu), *gr = (float*)(ws + L.gr), *best = (float*)(ws + L.best);
+  const size_t nx = h->n_x, nu = h->n_u;
+  if (cudaMemcpyAsync(x, x0, (size_t)T * nx * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(u, u0, (size_t)T * nu * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return LEB_ERR_CUDA;
+  leb_set set{};
+  set.kind = LEB_SET_BOX;
+  set.center = nullptr;
+  set.radii = radii;
+  leb_status st;
+  for (int it = 0; it <= steps; ++it) {
+    st = leb_bounds(h, nullptr, T, x, u, &set, rlo, rhi, nullptr, nullptr, nullptr, ws + L.bounds, pbh_ws_bytes(0),
+                    inner, stream);
+    if (st != LEB_OK) return st;
+    if ((st = or_flags(dev_flags, inner, s)) != LEB_OK) return st;
+    if ((st = pgd_track(*h, T, rlo, rhi, x, u, best, x_opt, u_opt, w_init, it == 0, s)) != LEB_OK) return st;
+    if (it == steps) break;
+    if ((st = pbh_bounds_backward(*h, T, x, u, radii, nullptr, nullptr, gx, gu, gr, dev_flags, s)) != LEB_OK)
+      return st;
+    if ((st = pgd_step(*h, (long long)T * nx, x, gx, x0, lr, eps, s)) != LEB_OK) return st;
+    if ((st = pgd_step(*h, (long long)T * nu, u, gu, u0, lr, eps, s)) != LEB_OK) return st;
+  }
+  if (w_best && cudaMemcpyAsync(w_best, best, (size_t)T * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return LEB_ERR_CUDA;
+  return LEB_OK;
 }
 
 leb_status leb_zonotope_map(const float* r_lo, const float* r_hi, long long count, float pad, float* c, float* r,
