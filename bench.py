@@ -1,6 +1,6 @@
 """Benchmark of the certified LEB hot path on B300 (one JSON line on rank 0).
 
-A step is one pass of the whole hot path over one batch of seeded synthetic input, five forms in turn:
+A step is one pass of the whole hot path over one batch of seeded synthetic input, six forms in turn:
   * plain form (pbh): path-based Hessian bounds (Thm. 1) for the 28-quadrotor spring chain
     (n_x = 168, n_u = 56), 256 trajectories x N = 50 (T = 12800), zonotope tube sets with 2 n_x = 336
     generators, A_k and B_k written;
@@ -13,9 +13,12 @@ A step is one pass of the whole hot path over one batch of seeded synthetic inpu
     are reported beside it);
   * pbh_grad: the adjoint of the PBH bound of the same chain (256 x 50 timesteps, box sets, random
     cotangents), with the nominal refinement of Table II (projected gradient descent on the PBH width
-    against random sampling) measured once at start-up and reported beside it.
-``value`` = certified timestep-bounds per second of the whole step (pbh + crown timesteps over the time
-of all five forms), summed over ranks.
+    against random sampling) measured once at start-up and reported beside it;
+  * pbh_sys: PBH for the paper's own 168-state system, 14 3-D quadrotors with the centroid
+    spring-damper (256 x 50 timesteps, box sets, A_k and B_k written), with the runtime at the Table I
+    shapes (satellite, one 3-D quadrotor) measured once at start-up and reported beside it.
+``value`` = certified timestep-bounds per second of the whole step (pbh + crown + pbh_sys timesteps, all
+at n_x = 168, over the time of all six forms), summed over ranks.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--forms pbh,crown,...]
 For N > 1 it runs under torchrun, one independent replica per GPU (every timestep's bound is independent,
@@ -527,6 +530,93 @@ class PbhGradForm(Form):
         return ms, sum(a.numel() * 4 for a in (hx, hu, hr, hgl, hgh)), sum(o.numel() * 4 for o in outs)
 
 
+class PbhSysForm(Form):
+    """The paper's own 168-state system (App. A): 14 3-D quadrotors coupled by the centroid spring-damper
+    (alpha = 0.75, gamma = 0.25), PBH with box sets of half-width 0.05, 256 trajectories x N = 50, A and B
+    written. Beside it, once at start-up (untimed), the runtime of PBH at the shapes of Table I (the
+    satellite, n_x = 7, and one 3-D quadrotor, n_x = 12) for 1, 10^3 and 10^6 nominal points per launch.
+
+    Bytes per timestep: x~ (168), u~ (56) and radii (224) read; r_lo, r_hi (2 x 168), A (168 x 168) and
+    B (168 x 56) written, FP32: 153,664 B."""
+    name = "pbh_sys"
+    BYTES_PER_TS = 4 * (168 + 56 + 224 + 2 * 168 + 168 * 168 + 168 * 56)
+
+    def __init__(self, torch, dev, quick=False):
+        from paper_2607_01203_b300 import binding, inputs
+        self.torch = torch
+        self.w = inputs.quad3d(T=(16 if quick else 256) * 50, n_quads=14, eps=0.05, coupled=True, N=50)
+        w = self.w
+        self.T = w.T
+        self.handle = binding.quad3d(14, **w.params)
+        self.x = torch.as_tensor(w.x_nom).to(dev)
+        self.u = torch.as_tensor(w.u_nom).to(dev)
+        self.r = torch.as_tensor(w.radii).to(dev)
+        self.out = self.handle.bounds(self.x, self.u, radii=self.r)
+        torch.cuda.synchronize()
+        self.table1 = self._table1(torch, dev, binding, inputs, quick)
+        self.desc = f"14 coupled 3-D quadrotors n_x=168 n_u=56, {self.T // 50} traj x N=50, box sets eps=0.05"
+
+    @staticmethod
+    def _table1(torch, dev, binding, inputs, quick):
+        res = {}
+        for label, w, mk in (("satellite_nx7", inputs.satellite(T=10 ** 6, eps=0.1), binding.satellite),
+                             ("quadrotor_nx12", inputs.quad3d(T=10 ** 6, eps=0.1), binding.quad3d)):
+            h = mk(**w.params)
+            x, u, r = (torch.as_tensor(a).to(dev) for a in (w.x_nom, w.u_nom, w.radii))
+            row = {}
+            for T in ((1, 1000) if quick else (1, 1000, 10 ** 6)):
+                xs, us, rs = x[:T].contiguous(), u[:T].contiguous(), r[:T].contiguous()
+                o = h.bounds(xs, us, radii=rs)
+                ms = timed_loop(torch, lambda: h.bounds(xs, us, radii=rs, out=o), 20 if T < 10 ** 6 else 5)
+                row[f"T={T}"] = {"ms_per_launch": round(ms, 4), "timestep_bounds_per_s": round(T / (ms * 1e-3), 1)}
+            res[label] = row
+        return res
+
+    def run(self):
+        self.handle.bounds(self.x, self.u, radii=self.r, out=self.out)
+
+    def units(self):
+        return self.T
+
+    def roofline(self, pk, ms, launches, kernel):
+        achieved = self.BYTES_PER_TS * self.T / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
+                "peak_src": pk["src"] + " hbm_gbs (STREAM-style copy)", "kernel": kernel,
+                "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
+                "bytes_per_unit": self.BYTES_PER_TS, "units_per_launch": self.T // max(launches, 1)}
+
+    def e2e(self, steps):
+        torch = self.torch
+        hx, hu, hr = (a.cpu().pin_memory() for a in (self.x, self.u, self.r))
+        dx, du, dr = (torch.empty_like(a) for a in (self.x, self.u, self.r))
+        out_h = {k: torch.empty(self.out[k].shape).pin_memory() for k in ("r_lo", "r_hi", "A", "B")}
+
+        def one():
+            for d, hsrc in ((dx, hx), (du, hu), (dr, hr)):
+                d.copy_(hsrc, non_blocking=True)
+            o = self.handle.bounds(dx, du, radii=dr, out=self.out)
+            for k, v in out_h.items():
+                v.copy_(o[k], non_blocking=True)
+        ms = timed_loop(torch, one, steps)
+        return ms, sum(a.numel() * 4 for a in (hx, hu, hr)), sum(v.numel() * 4 for v in out_h.values())
+
+    def oracle_seconds_per_unit(self, budget_s):
+        from oracle import dynamics3d, pbh
+        w = self.w
+        dyn = dynamics3d.Quad3D(14, **w.params)
+        t0 = time.perf_counter()
+        done = 0
+        while time.perf_counter() - t0 < budget_s and done < w.T:
+            t = (done * 97) % w.T
+            a = w.nominal()[t].astype(np.float64)
+            lo, hi = pbh.box_from_set(a, radii=w.radii[t])
+            pbh.pbh(dyn, a, lo, hi)
+            dyn.jacobian(a)
+            done += 1
+        return (time.perf_counter() - t0) / done, done
+
+
 def timed_loop(torch, fn, steps):
     """CUDA-event time per call of fn on the current stream (after one untimed call)."""
     fn()
@@ -559,20 +649,23 @@ def count_launches(torch, fn):
 
 # ------------------------------------------------------------------------------------------------
 def reference_arm(args):
-    """The FP64 oracle as the reference arm, on the host cores: the same step (pbh + crown timesteps
-    over the time of pbh, crown and the adjoint), each step a bounded sample of every form."""
+    """The FP64 oracle as the reference arm, on the host cores: the same step (pbh + crown + pbh_sys
+    timesteps over the time of pbh, crown, the adjoint and pbh_sys), each step a bounded sample of every
+    form."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import torch
     from paper_2607_01203_b300 import inputs
-    from oracle import crown, dynamics, pbh
+    from oracle import crown, dynamics, dynamics3d, pbh
     wq = inputs.quad_chain(n_traj=4, horizon=50)
+    ws = inputs.quad3d(T=4 * 50, n_quads=14, eps=0.05, coupled=True, N=50)
+    dyn3 = dynamics3d.Quad3D(14, **ws.params)
     dyn = dynamics.QuadChain(28, **wq.params, spring_k=wq.spring_k)
     wm = inputs.tanh_mlp(n_traj=2, N=50)
     g = np.random.default_rng(7).normal(size=(2, 168))
-    n_pbh, n_crown, n_bwd = 16, 2, 1
-    T_pbh, T_mlp = 12800, 6400
+    n_pbh, n_crown, n_bwd, n_sys = 16, 2, 1, 8
+    T_pbh, T_mlp, T_sys = 12800, 6400, 12800
     est = []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -592,19 +685,29 @@ def reference_arm(args):
             crown.box_remainder_vjp(wm.Ws, wm.bs, wm.act, wm.x_nom[t], wm.u_nom[t], wm.radii[t], g[0], g[1],
                                     wm.residual)
         t3 = time.perf_counter()
+        for i in range(n_sys):
+            t = (s * n_sys + i) % ws.T
+            a = ws.nominal()[t].astype(np.float64)
+            lo, hi = pbh.box_from_set(a, radii=ws.radii[t])
+            pbh.pbh(dyn3, a, lo, hi)
+            dyn3.jacobian(a)
+        t4 = time.perf_counter()
         if s >= args.warmup:
             # time the oracle would take for one full step of the same workload
-            est.append((t1 - t0) / n_pbh * T_pbh + (t2 - t1) / n_crown * T_mlp + (t3 - t2) / n_bwd * T_mlp)
+            est.append((t1 - t0) / n_pbh * T_pbh + (t2 - t1) / n_crown * T_mlp + (t3 - t2) / n_bwd * T_mlp
+                       + (t4 - t3) / n_sys * T_sys)
     step_s = statistics.mean(est)
-    v = (T_pbh + T_mlp) / step_s
+    v = (T_pbh + T_mlp + T_sys) / step_s
     cores = torch.get_num_threads()
-    sample = (f"per step {n_pbh} PBH timesteps (1 core), {n_crown} CROWN and {n_bwd} adjoint timesteps "
-              f"(torch, {cores} threads) of the bench workloads, scaled to a full step")
+    sample = (f"per step {n_pbh} PBH chain timesteps and {n_sys} coupled 3-D quadrotor timesteps (1 core), "
+              f"{n_crown} CROWN and {n_bwd} adjoint timesteps (torch, {cores} threads) of the bench workloads, "
+              f"scaled to a full step")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "pbh 256x50 quad chain (zonotope) + crown 128x50 tanh MLP + adjoint, "
-                                   "FP64 oracle on a bounded sample per step", "parallelism": "host"},
+            "config": {"workload": "pbh 256x50 quad chain (zonotope) + crown 128x50 tanh MLP + adjoint + "
+                                   "pbh_sys 256x50 coupled 3-D quadrotors, FP64 oracle on a bounded sample per step",
+                       "parallelism": "host"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -616,7 +719,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--forms", default="pbh,crown,backward,proposer,pbh_grad")
+    ap.add_argument("--forms", default="pbh,crown,backward,proposer,pbh_grad,pbh_sys")
     ap.add_argument("--quick", action="store_true", help="small batches (smoke runs, not a bench value)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -648,6 +751,8 @@ def main():
             forms.append(ProposerForm(torch, dev, args.quick))
         elif nm == "pbh_grad":
             forms.append(PbhGradForm(torch, dev, args.quick))
+        elif nm == "pbh_sys":
+            forms.append(PbhSysForm(torch, dev, args.quick))
         else:
             raise SystemExit(f"unknown form {nm}")
     handles = {id(f.handle): f.handle for f in forms if f.handle is not None}
@@ -721,6 +826,8 @@ def main():
             d["us_per_call"] = round(1e3 * form_ms[f.name], 1)
         if f.name == "pbh_grad":
             d["nominal_refinement_table2"] = f.pgd
+        if f.name == "pbh_sys":
+            d["table1_shapes"] = f.table1
         if f.name == "proposer":
             cms = f.certified_ms()
             d.update({"proposal_error_vs_certified": round(f.err, 4), "under_cover_fraction": round(f.under, 4),
@@ -763,7 +870,7 @@ def main():
 
 def cpu_baseline(forms, torch):
     """The oracle as it stands on a bounded sample of each form, scaled to the step's metric."""
-    budget = {"pbh": 6.0, "crown": 6.0, "backward": 8.0}
+    budget = {"pbh": 6.0, "crown": 6.0, "backward": 8.0, "pbh_sys": 4.0}
     step_s, units, parts = 0.0, 0, []
     for f in forms:
         if f.name not in budget:

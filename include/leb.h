@@ -58,7 +58,7 @@ typedef enum {
   LEB_ASYNC_OVERFLOW = 4      /* a reduced-precision operand overflowed; bounds set to [-inf,+inf] */
 } leb_async_flag;
 
-typedef enum { LEB_DYN_QUAD_CHAIN = 0, LEB_DYN_MLP = 1 } leb_dyn_kind;
+typedef enum { LEB_DYN_QUAD_CHAIN = 0, LEB_DYN_MLP = 1, LEB_DYN_SATELLITE = 2, LEB_DYN_QUAD3D = 3 } leb_dyn_kind;
 typedef enum { LEB_ACT_RELU = 0, LEB_ACT_TANH = 1 } leb_act;
 /* arithmetic of the MLP back-substitution: FP32 on CUDA cores, or FP16/BF16 operands on the
    tensor cores with FP32 accumulation and a rigorous rounding inflation */
@@ -74,7 +74,19 @@ typedef enum { LEB_SET_BOX = 0, LEB_SET_ZONO = 1 } leb_set_kind;
  *    doubles; the library encloses them in FP32 intervals.
  *  LEB_DYN_MLP: f(x,u) = [x +] W_L h_{L-1} + b_L, h_i = act(W_i h_{i-1} + b_i), h_0 = [x; u];
  *    widths[0] = n_x + n_u, widths[L] = n_x. W[i] is host FP32 [widths[i+1]][widths[i]], b[i] host
- *    FP32 [widths[i+1]]. residual != 0 adds the identity on x. */
+ *    FP32 [widths[i+1]]. residual != 0 adds the identity on x.
+ *  LEB_DYN_SATELLITE: the rigid satellite of App. A ("Satellite") under forward Euler with step dt:
+ *    qdot = 1/2 zeta(w) q, wdot = I^-1 (v - w x (I w)), I = diag(inertia3). State (q_0..q_3, w_1..w_3),
+ *    input torque (v_1..v_3): n_x = 7, n_u = 3.
+ *  LEB_DYN_QUAD3D: n_quads 3-D quadrotors of App. A ("Coupled 3D Quadrotor") under forward Euler with
+ *    step dt, mass, gravity g and body inertia diag(inertia3); coup_alpha, coup_gamma != 0 add the
+ *    centroid spring-damper -coup_alpha n_quads (p_i - pbar) - coup_gamma (v_i - vbar) to every
+ *    quadrotor's acceleration. State (p_x, p_y, p_z, phi, theta, psi, v_x, v_y, v_z, p, q, r) per
+ *    quadrotor, all states first, then inputs (T, tau_phi, tau_theta, tau_psi) per quadrotor:
+ *    n_x = 12 n_quads, n_u = 4 n_quads, n_quads <= 21. A timestep whose theta box reaches +-1.5707
+ *    (the tan / sec singularity) gets bounds [-inf, +inf] on the rows that use tan / sec (phi, psi).
+ *    leb_bounds needs A and B 16-byte aligned for this kind (LEB_ERR_INVALID_ARG otherwise).
+ *  Both take box sets only (leb_set.kind == LEB_SET_BOX), and no leb_batch with traj_nquads. */
 typedef struct {
   leb_dyn_kind kind;
   int n_quads;
@@ -86,6 +98,8 @@ typedef struct {
   leb_act act;
   int residual;
   leb_prec prec;
+  double inertia3[3];            /* LEB_DYN_SATELLITE / LEB_DYN_QUAD3D: principal moments of inertia */
+  double coup_alpha, coup_gamma; /* LEB_DYN_QUAD3D: centroid coupling gains (0 = independent)        */
 } leb_dynamics_spec;
 
 /* Tube set of every timestep (device pointers, row-major over timesteps).
@@ -239,7 +253,7 @@ leb_status leb_proposer_get_grad(leb_proposer p, int i, float* dW, float* db, vo
  * The scratch (the work-list counter and, for uneven batches, two 8-byte prefix sums per trajectory) is a
  * 64 KiB array inside the library that every GPU loading the library keeps until the process exits.
  * Uneven-dimension batches may have at most leb_bounds_static_max_traj() trajectories; more return
- * LEB_ERR_WORKSPACE. MLP handles return LEB_ERR_UNSUPPORTED. The first call on a device looks up the
+ * LEB_ERR_WORKSPACE. MLP handles return LEB_ERR_UNSUPPORTED; satellite and 3-D quadrotor handles use no scratch. The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress): make that first call before any stream capture. All
  * calls share the array and clear its counter themselves; calls that overlap on the GPU (issued on
  * different streams or from different host threads without ordering) race on it. Nothing is allocated
@@ -256,6 +270,10 @@ int leb_bounds_static_max_traj(void);
  * FP64 host values. */
 leb_status leb_selftest_point_enclosures(const float* x, int n, float* out_sin, float* out_cos, float* out_tanh,
                                          void* stream);
+/* Evaluates the enclosures of tan and sec = 1/cos that the 3-D quadrotor's Hessian entries use, at n
+ * device points x (a degenerate interval each), writing [lo, hi] pairs to out_tan and out_sec ([n, 2]
+ * device arrays). Points outside (-1.5707, 1.5707) give [-inf, +inf]. */
+leb_status leb_selftest_tan_sec(const float* x, int n, float* out_tan, float* out_sec, void* stream);
 
 const char* leb_status_string(leb_status st);
 const char* leb_version(void);

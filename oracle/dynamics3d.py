@@ -106,7 +106,8 @@ class Satellite:
         return self.f_t(torch.tensor(np.asarray(A, np.float64), dtype=DT)).numpy()
 
     def jacobian(self, alpha):
-        return _jac_hess(self.f_t, alpha, self.n_x)[0]
+        a = torch.tensor(np.asarray(alpha, np.float64), dtype=DT)
+        return torch.autograd.functional.jacobian(self.f_t, a).numpy()
 
     def hessian_autodiff(self, alpha):
         return _jac_hess(self.f_t, alpha, self.n_x)[1]

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libleb.so")
 LEB_OK = 0
 STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported", -3: "workspace", -4: "CUDA error", -5: "timeout"}
 ASYNC_NONFINITE, ASYNC_TIMEOUT, ASYNC_OVERFLOW = 1, 2, 4
-DYN_QUAD_CHAIN, DYN_MLP = 0, 1
+DYN_QUAD_CHAIN, DYN_MLP, DYN_SATELLITE, DYN_QUAD3D = 0, 1, 2, 3
 ACT = {"relu": 0, "tanh": 1}
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
 SET_BOX, SET_ZONO = 0, 1
@@ -33,7 +33,8 @@ class DynamicsSpec(C.Structure):
     _fields_ = [("kind", C.c_int), ("n_quads", C.c_int), ("dt", C.c_double), ("mass", C.c_double),
                 ("inertia", C.c_double), ("arm", C.c_double), ("g", C.c_double), ("spring_k", C.c_double),
                 ("n_layers", C.c_int), ("widths", C.POINTER(C.c_int)), ("W", C.POINTER(C.c_void_p)),
-                ("b", C.POINTER(C.c_void_p)), ("act", C.c_int), ("residual", C.c_int), ("prec", C.c_int)]
+                ("b", C.POINTER(C.c_void_p)), ("act", C.c_int), ("residual", C.c_int), ("prec", C.c_int),
+                ("inertia3", C.c_double * 3), ("coup_alpha", C.c_double), ("coup_gamma", C.c_double)]
 
 
 class SetDesc(C.Structure):
@@ -58,7 +59,7 @@ EXPORTS = [
     "leb_proposer_set_norm", "leb_proposer_forward", "leb_proposer_train_step", "leb_proposer_workspace_size",
     "leb_proposer_get_layer", "leb_proposer_set_layer", "leb_proposer_get_grad", "leb_selftest_point_enclosures",
     "leb_bounds_static", "leb_bounds_static_max_traj", "leb_proposer_fit_norm", "leb_proposer_set_periodic", "leb_timing", "leb_timing_read", "leb_status_string", "leb_version",
-    "leb_refine_nominal_pgd", "leb_refine_workspace_size",
+    "leb_refine_nominal_pgd", "leb_refine_workspace_size", "leb_selftest_tan_sec",
 ]
 
 
@@ -103,6 +104,7 @@ def lib():
         L.leb_proposer_set_layer.argtypes = [vp, i32, vp, vp, vp]
         L.leb_proposer_get_grad.argtypes = [vp, i32, vp, vp, vp]
         L.leb_selftest_point_enclosures.argtypes = [vp, i32, vp, vp, vp, vp]
+        L.leb_selftest_tan_sec.argtypes = [vp, i32, vp, vp, vp]
         L.leb_bounds_static.argtypes = [vp, C.POINTER(BatchDesc), i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp, vp, vp,
                                         vp]
         L.leb_bounds_static_max_traj.argtypes = []
@@ -307,6 +309,23 @@ class Handle:
 def quad_chain(n_quads: int, mass: float, inertia: float, arm: float, g: float, dt: float, spring_k: float = 0.0,
                **_) -> Handle:
     spec = DynamicsSpec(DYN_QUAD_CHAIN, int(n_quads), dt, mass, inertia, arm, g, spring_k, 0, None, None, None, 0, 0, 0)
+    return Handle(spec)
+
+
+def satellite(dt: float = 0.05, inertia=(5.0, 2.0, 1.0), **_) -> Handle:
+    """The rigid satellite of App. A (n_x = 7, n_u = 3), forward Euler with step dt."""
+    spec = DynamicsSpec(kind=DYN_SATELLITE, n_quads=1, dt=float(dt))
+    spec.inertia3 = (C.c_double * 3)(*[float(v) for v in inertia])
+    return Handle(spec)
+
+
+def quad3d(n_quads: int = 1, dt: float = 0.05, mass: float = 1.0, g: float = 9.81, inertia=(0.01, 0.01, 0.02),
+           coup_alpha: float = 0.0, coup_gamma: float = 0.0, **_) -> Handle:
+    """n_quads 3-D quadrotors of App. A (n_x = 12 n_quads, n_u = 4 n_quads), optionally coupled by the
+    centroid spring-damper (coup_alpha, coup_gamma)."""
+    spec = DynamicsSpec(kind=DYN_QUAD3D, n_quads=int(n_quads), dt=float(dt), mass=float(mass), g=float(g),
+                        coup_alpha=float(coup_alpha), coup_gamma=float(coup_gamma))
+    spec.inertia3 = (C.c_double * 3)(*[float(v) for v in inertia])
     return Handle(spec)
 
 

@@ -19,6 +19,42 @@ struct QuadConsts {
   int springs;               // k != 0
 };
 
+// FP32 enclosure [lo, hi] and round-to-nearest value f of a real model constant.
+struct SysConst {
+  float lo, hi, f;
+};
+
+// Constants of the satellite and 3-D quadrotor models (all already multiplied by dt).
+struct SysConsts {
+  SysConst dt, half_dt, dt_m;     // dt, dt / 2, dt / m
+  SysConst k[3];                  // bilinear rate coefficients: dt (I_b - I_c) / I_a per rate row
+  SysConst tq[3];                 // dt / I_a (torque inputs)
+  SysConst ca_self, ca_other;     // centroid coupling, position columns: -dt alpha (N - 1), dt alpha
+  SysConst cg_self, cg_other;     // velocity columns: 1 - dt gamma (N - 1) / N, dt gamma / N
+  int coupled;
+};
+
+struct SysArgs {
+  const float* x_nom;
+  const float* u_nom;
+  const float* center;
+  const float* radii;
+  float* r_lo;
+  float* r_hi;
+  float* A;
+  float* B;
+  float* gamma_c;
+  float* gamma_r;
+  float gamma_pad;
+  float* eps;
+  int* flags;
+  long long T;
+  int nq, n_x, n_u;
+  int max_ts;                            // launch-derived: timesteps that 32 consecutive units touch
+  unsigned long long magic_a, magic_b;   // launch-derived: ceil(2^32 / (3 nq)), ceil(2^32 / nq)
+  SysConsts k;
+};
+
 struct PbhPlan {
   int block;          // threads per CTA (zonotope kernel: one producer warp + consumer warps)
   int ctas_per_sm;    // persistent grid = SMs * ctas_per_sm
@@ -119,6 +155,8 @@ struct Ctx {
   PbhPlan pbh_plan{256, 3, 4};
   std::vector<PbhPlan> pbh_candidates;
   int plan_index = -1;
+  // satellite / 3-D quadrotors
+  SysConsts sk{};
   // mlp
   MlpModel mlp;
   int sm_count = 148;
@@ -133,6 +171,12 @@ void timer_end(const Ctx& c, cudaStream_t s);
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_pbh(const Ctx& c, const PbhArgs& a, const PbhPlan& p, cudaStream_t s);
+// Thm. 1 for the satellite and (coupled) 3-D quadrotor models, box sets (pbh_sys.cu)
+leb_status launch_pbh_sys(const Ctx& c, const SysArgs& a, cudaStream_t s);
+// argument checks and launch for leb_bounds / leb_bounds_static (box sets; flags already cleared, T > 0)
+leb_status pbh_sys_bounds(const Ctx& c, const leb_batch* batch, int T, const float* x_nom, const float* u_nom,
+                          const leb_set* set, float* r_lo, float* r_hi, float* A, float* B, const leb_options* opt,
+                          int* flags, cudaStream_t s);
 cudaError_t launch_prefix(const int* traj_offsets, const int* traj_nquads, int n_traj, long long* pre1,
                           long long* pre2, cudaStream_t s);
 cudaError_t launch_zonotope_map(const float* lo, const float* hi, long long count, float pad, float* c, float* r,

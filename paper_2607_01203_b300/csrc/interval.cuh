@@ -86,6 +86,31 @@ __device__ __forceinline__ ivl iv_cos(ivl x) {
   return r;
 }
 
+// Enclosure of tan at a point: CUDA's tanf is documented to within 4 ulp; the slack is 8 ulp of the
+// result (2^-20 relative) plus the smallest normal, checked against FP64 host values by the GPU tests.
+__device__ __forceinline__ ivl point_tan(float x) {
+  const float t = tanf(x);
+  const float e = __fmaf_ru(fabsf(t), 9.5367431640625e-07f, 1.1754944e-38f);
+  return {__fsub_rd(t, e), __fadd_ru(t, e)};
+}
+
+// Range enclosures of tan and sec = 1/cos over [a, b] inside (-pi/2, pi/2), where tan increases and
+// cos > 0; outside that domain (or with a NaN) the whole line.
+constexpr float kTanDomain = 1.5707f;   // a little inside pi/2, so that the FP32 test errs on the safe side
+__device__ __forceinline__ ivl iv_tan(ivl x) {
+  if (!(x.lo > -kTanDomain && x.hi < kTanDomain)) return {-CUDART_INF_F, CUDART_INF_F};
+  return {point_tan(x.lo).lo, point_tan(x.hi).hi};
+}
+__device__ __forceinline__ ivl iv_sec(ivl x) {
+  if (!(x.lo > -kTanDomain && x.hi < kTanDomain)) return {-CUDART_INF_F, CUDART_INF_F};
+  const ivl c = iv_cos(x);
+  if (!(c.lo > 0.f)) return {-CUDART_INF_F, CUDART_INF_F};
+  return {__frcp_rd(c.hi), __frcp_ru(c.lo)};
+}
+
+// Scaling by a constant enclosed in [k.lo, k.hi].
+__device__ __forceinline__ ivl iv_scale(ivl k, ivl a) { return iv_mul(k, a); }
+
 __device__ __forceinline__ bool finite_ivl(ivl a) { return isfinite(a.lo) && isfinite(a.hi); }
 
 }  // namespace leb

@@ -163,6 +163,36 @@ leb_status leb_create(const leb_dynamics_spec* spec, leb_handle* out) {
     enclose(spec->dt * spec->arm / spec->inertia, &k.tq_lo, &k.tq_hi, &k.tq_f);
     k.springs = spec->spring_k != 0.0;
     default_pbh_candidates(*c);
+  } else if (spec->kind == LEB_DYN_SATELLITE || spec->kind == LEB_DYN_QUAD3D) {
+    const double* I = spec->inertia3;
+    const bool quad = spec->kind == LEB_DYN_QUAD3D;
+    if (!finite_pos(spec->dt) || !finite_pos(I[0]) || !finite_pos(I[1]) || !finite_pos(I[2]) ||
+        (quad && (spec->n_quads < 1 || spec->n_quads > 21 || !finite_pos(spec->mass) || !std::isfinite(spec->g) ||
+                  !std::isfinite(spec->coup_alpha) || !std::isfinite(spec->coup_gamma)))) {
+      delete c;
+      return LEB_ERR_INVALID_ARG;
+    }
+    const int N = quad ? spec->n_quads : 1;
+    c->nq = N;
+    c->n_x = quad ? 12 * N : 7;
+    c->n_u = quad ? 4 * N : 3;
+    SysConsts& k = c->sk;
+    auto E = [](double v, SysConst& o) { enclose(v, &o.lo, &o.hi, &o.f); };
+    const double dt = spec->dt;
+    E(dt, k.dt);
+    E(0.5 * dt, k.half_dt);
+    E(quad ? dt / spec->mass : 0.0, k.dt_m);
+    for (int a = 0; a < 3; ++a) {
+      const int b = (a + 1) % 3, cc = (a + 2) % 3;   // cyclic: rate a couples rates b and c
+      E(dt * (I[b] - I[cc]) / I[a], k.k[a]);
+      E(dt / I[a], k.tq[a]);
+    }
+    const double al = quad ? spec->coup_alpha : 0.0, ga = quad ? spec->coup_gamma : 0.0;
+    E(-dt * al * (N - 1), k.ca_self);
+    E(dt * al, k.ca_other);
+    E(1.0 - dt * ga * (N - 1) / N, k.cg_self);
+    E(dt * ga / N, k.cg_other);
+    k.coupled = (al != 0.0 || ga != 0.0) && N > 1;
   } else if (spec->kind == LEB_DYN_MLP) {
     if (spec->n_layers < 2 || spec->n_layers > kMaxLayers || !spec->widths || !spec->W || !spec->b ||
         (spec->act != LEB_ACT_RELU && spec->act != LEB_ACT_TANH) || spec->prec < LEB_PREC_FP32 ||
@@ -227,6 +257,8 @@ leb_status leb_workspace_size(leb_handle h, int T_max, size_t* bytes) {
   if (!h || !bytes || T_max < 0) return LEB_ERR_INVALID_ARG;
   if (h->kind == LEB_DYN_QUAD_CHAIN) {
     *bytes = pbh_ws_bytes(T_max);
+  } else if (h->kind == LEB_DYN_SATELLITE || h->kind == LEB_DYN_QUAD3D) {
+    *bytes = kWsHeader;
   } else {
     MlpWs lay;
     *bytes = kWsHeader + mlp_workspace_floats(*h, T_max, &lay) * sizeof(float);
@@ -296,6 +328,10 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
     timer_end(*h, s);
     if (e != cudaSuccess) return LEB_ERR_CUDA;
     return LEB_OK;
+  }
+  if (h->kind == LEB_DYN_SATELLITE || h->kind == LEB_DYN_QUAD3D) {
+    if (ws_bytes < kWsHeader) return LEB_ERR_WORKSPACE;
+    return pbh_sys_bounds(*h, batch, T, x_nom, u_nom, set, r_lo, r_hi, A, B, opt, dev_flags, s);
   }
   // MLP dynamics
   if (batch && batch->traj_nquads) return LEB_ERR_UNSUPPORTED;
@@ -437,6 +473,10 @@ leb_status leb_plan_string(leb_handle h, char* buf, size_t buf_len) {
     const PbhPlan& p = (h->plan_index >= 0) ? h->pbh_candidates[h->plan_index] : h->pbh_plan;
     os << "kernel=pbh;block=" << p.block << ";ctas_per_sm=" << p.ctas_per_sm << ";stages=" << p.stages
        << ";sms=" << h->sm_count;
+  } else if (h->kind == LEB_DYN_SATELLITE) {
+    os << "kernel=pbh_satellite;timesteps_per_cta=8";
+  } else if (h->kind == LEB_DYN_QUAD3D) {
+    os << "kernel=pbh_quad3d;quads=" << h->nq << ";coupled=" << h->sk.coupled;
   } else {
     os << "kernel=mlp;prec=" << h->mlp.prec << ";layers=" << h->mlp.L;
   }

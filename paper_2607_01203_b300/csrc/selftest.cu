@@ -1,4 +1,5 @@
-// Diagnostic entry point: the point enclosures of sin/cos/tanh used by the bound kernels.
+// Diagnostic entry points: the point enclosures of sin/cos/tanh and the tan/sec enclosures used by the
+// bound kernels.
 #include "internal.h"
 #include "interval.cuh"
 #include "mlp_math.cuh"
@@ -13,6 +14,13 @@ __global__ void point_enclosure_kernel(const float* x, int n, float2* s, float2*
   c[i] = make_float2(b.lo, b.hi);
   th[i] = make_float2(t.lo, t.hi);
 }
+__global__ void tan_sec_kernel(const float* x, int n, float2* t, float2* sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const ivl a = iv_tan(iv(x[i])), b = iv_sec(iv(x[i]));
+  t[i] = make_float2(a.lo, a.hi);
+  sc[i] = make_float2(b.lo, b.hi);
+}
 }  // namespace leb
 
 extern "C" leb_status leb_selftest_point_enclosures(const float* x, int n, float* out_sin, float* out_cos,
@@ -21,5 +29,12 @@ extern "C" leb_status leb_selftest_point_enclosures(const float* x, int n, float
   if (n == 0) return LEB_OK;
   leb::point_enclosure_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
       x, n, (float2*)out_sin, (float2*)out_cos, (float2*)out_tanh);
+  return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
+}
+
+extern "C" leb_status leb_selftest_tan_sec(const float* x, int n, float* out_tan, float* out_sec, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !out_tan || !out_sec))) return LEB_ERR_INVALID_ARG;
+  if (n == 0) return LEB_OK;
+  leb::tan_sec_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(x, n, (float2*)out_tan, (float2*)out_sec);
   return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
 }

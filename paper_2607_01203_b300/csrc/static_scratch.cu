@@ -59,8 +59,16 @@ extern "C" leb_status leb_bounds_static(leb_handle h, const leb_batch* batch, in
                                         float* B, int* dev_flags, void* stream) {
   if (!h || !set || T < 0 || !dev_flags) return LEB_ERR_INVALID_ARG;
   const Ctx& c = *reinterpret_cast<const Ctx*>(h);
-  if (c.kind != LEB_DYN_QUAD_CHAIN) return LEB_ERR_UNSUPPORTED;
+  if (c.kind == LEB_DYN_MLP) return LEB_ERR_UNSUPPORTED;
   if (T > 0 && (!x_nom || !u_nom || !r_lo || !r_hi)) return LEB_ERR_INVALID_ARG;
+  if (c.kind == LEB_DYN_SATELLITE || c.kind == LEB_DYN_QUAD3D) {   // no scratch needed
+    if (set->kind != LEB_SET_BOX && set->kind != LEB_SET_ZONO) return LEB_ERR_INVALID_ARG;
+    if (T > 0 && set->kind == LEB_SET_BOX && !set->radii) return LEB_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(dev_flags, 0, sizeof(int), s) != cudaSuccess) return LEB_ERR_CUDA;
+    if (T == 0) return LEB_OK;
+    return pbh_sys_bounds(c, batch, T, x_nom, u_nom, set, r_lo, r_hi, A, B, nullptr, dev_flags, s);
+  }
   if (set->kind != LEB_SET_BOX && set->kind != LEB_SET_ZONO) return LEB_ERR_INVALID_ARG;
   if (T > 0 && set->kind == LEB_SET_BOX && !set->radii) return LEB_ERR_INVALID_ARG;
   if (T > 0 && set->kind == LEB_SET_ZONO && (!set->G || set->n_gen < 1)) return LEB_ERR_INVALID_ARG;

@@ -18,6 +18,11 @@ Workloads (shapes follow the paper's systems, App. A, at synthetic sizes):
 * ``tanh_mlp``        residual tanh MLP 224->512->512->512->168 dynamics, box sets.
 * ``proposer_data``   state/control/radius triples on quad-chain rollouts for the learned
                       bound proposer.
+* ``satellite``       7-state satellite (App. A "Satellite"), nominal points drawn from the
+                      state / input ranges, local box sets (z, v) + eps E (the width-vs-eps study).
+* ``quad3d``          N 3-D quadrotors (App. A "Coupled 3D Quadrotor"), optionally coupled by the
+                      centroid spring-damper (alpha = 0.75, gamma = 0.25), drawn the same way; the
+                      paper's 168-state system is 14 coupled quadrotors over a horizon of 25.
 """
 from __future__ import annotations
 
@@ -28,6 +33,12 @@ SEED_BASE = 1000
 
 # Planar quadrotor constants of the synthetic workloads (App. A equations).
 QUAD = dict(mass=1.0, inertia=0.01, arm=0.1, g=9.81, dt=0.05)
+
+
+# Satellite and 3-D quadrotor constants (App. A; the 3-D quadrotor's mass and inertia are not printed).
+SATELLITE = dict(dt=0.05, inertia=(5.0, 2.0, 1.0))
+QUAD3D = dict(dt=0.05, mass=1.0, g=9.81, inertia=(0.01, 0.01, 0.02))
+COUPLING = dict(coup_alpha=0.75, coup_gamma=0.25)
 
 
 def _rng(*keys: int) -> np.random.Generator:
@@ -241,3 +252,43 @@ def subset(w: Workload, rows: np.ndarray) -> Workload:
     d.G = None if w.G is None else np.ascontiguousarray(w.G[rows])
     d.traj_offsets = np.arange(len(rows) + 1, dtype=np.int32)
     return d
+
+
+def satellite(seed: int = SEED_BASE + 6, T: int = 1000, eps: float = 0.05, N: int | None = None) -> Workload:
+    """Satellite nominal points (unit quaternion, rates and torques U[-1, 1]) with the local box set of
+    half-width eps in every state and input coordinate. N groups the points into trajectories of
+    that horizon (the bound is per timestep, so the grouping only shapes the batch)."""
+    rng = _rng(seed)
+    q = rng.standard_normal((T, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    X = np.concatenate([q, rng.uniform(-1.0, 1.0, (T, 3))], axis=1)
+    U = rng.uniform(-1.0, 1.0, (T, 3))
+    radii = np.full((T, 10), eps)
+    N = N or T
+    offs = np.arange(0, T + 1, N, dtype=np.int32) if T % N == 0 else np.array([0, T], np.int32)
+    return Workload("satellite", "satellite", 7, 3, X.astype(np.float32), U.astype(np.float32), offs, "box",
+                    radii=radii.astype(np.float32), params=dict(SATELLITE))
+
+
+def quad3d(seed: int = SEED_BASE + 7, T: int = 1000, n_quads: int = 1, eps: float = 0.05, coupled: bool = False,
+           N: int | None = None) -> Workload:
+    """3-D quadrotor nominal points: positions, velocities and body rates U[-1, 1], roll and pitch
+    U[-0.5, 0.5], yaw U[-pi, pi], thrust U[5, 15] (hover at m g = 9.81) and torques U[-0.1, 0.1]; local
+    box set of half-width eps in every coordinate. coupled: the centroid spring-damper gains."""
+    rng = _rng(seed, n_quads)
+    X = np.empty((T, n_quads, 12))
+    X[..., 0:3] = rng.uniform(-1.0, 1.0, (T, n_quads, 3))
+    X[..., 3:5] = rng.uniform(-0.5, 0.5, (T, n_quads, 2))
+    X[..., 5] = rng.uniform(-np.pi, np.pi, (T, n_quads))
+    X[..., 6:12] = rng.uniform(-1.0, 1.0, (T, n_quads, 6))
+    U = np.empty((T, n_quads, 4))
+    U[..., 0] = rng.uniform(5.0, 15.0, (T, n_quads))
+    U[..., 1:4] = rng.uniform(-0.1, 0.1, (T, n_quads, 3))
+    n_x, n_u = 12 * n_quads, 4 * n_quads
+    radii = np.full((T, n_x + n_u), eps)
+    params = dict(QUAD3D, **(COUPLING if coupled else dict(coup_alpha=0.0, coup_gamma=0.0)))
+    N = N or T
+    offs = np.arange(0, T + 1, N, dtype=np.int32) if T % N == 0 else np.array([0, T], np.int32)
+    return Workload("quad3d", "quad3d", n_x, n_u, X.reshape(T, n_x).astype(np.float32),
+                    U.reshape(T, n_u).astype(np.float32), offs, "box", radii=radii.astype(np.float32),
+                    params=params, n_quads=n_quads)
