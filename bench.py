@@ -617,6 +617,44 @@ class PbhSysForm(Form):
         return (time.perf_counter() - t0) / done, done
 
 
+class Table1Form(Form):
+    """PBH at the shapes of Table I on their own (not in the default step; for profiling): the satellite
+    (n_x = 7) and one 3-D quadrotor (n_x = 12), 10^6 nominal points each with box sets of half-width 0.1,
+    A and B written. Bytes per point: satellite 4 (10 + 10 + 2 x 7 + 49 + 21) = 416 B, 3-D quadrotor
+    4 (16 + 16 + 2 x 12 + 144 + 48) = 992 B; the roofline entry is the quadrotor launch's."""
+    name = "table1"
+    BYTES = {"satellite": 416, "quad3d": 992}
+
+    def __init__(self, torch, dev, quick=False):
+        from paper_2607_01203_b300 import binding, inputs
+        self.torch = torch
+        self.T = 10 ** 5 if quick else 10 ** 6
+        self.parts = []
+        for key, w, mk in (("satellite", inputs.satellite(T=self.T, eps=0.1), binding.satellite),
+                           ("quad3d", inputs.quad3d(T=self.T, eps=0.1), binding.quad3d)):
+            h = mk(**w.params)
+            x, u, r = (torch.as_tensor(a).to(dev) for a in (w.x_nom, w.u_nom, w.radii))
+            self.parts.append((key, h, x, u, r, h.bounds(x, u, radii=r)))
+        self.handle = self.parts[1][1]
+        torch.cuda.synchronize()
+        self.desc = f"satellite n_x=7 and 3-D quadrotor n_x=12, {self.T} points each, box sets eps=0.1"
+
+    def run(self):
+        for _, h, x, u, r, o in self.parts:
+            h.bounds(x, u, radii=r, out=o)
+
+    def roofline(self, pk, ms, launches, kernel):
+        achieved = self.BYTES["quad3d"] * self.T / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
+                "peak_src": pk["src"] + " hbm_gbs (STREAM-style copy)", "kernel": kernel,
+                "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
+                "bytes_per_unit": self.BYTES["quad3d"], "units_per_launch": self.T}
+
+    def e2e(self, steps):
+        return 0.0, 0, 0
+
+
 def timed_loop(torch, fn, steps):
     """CUDA-event time per call of fn on the current stream (after one untimed call)."""
     fn()
@@ -753,6 +791,8 @@ def main():
             forms.append(PbhGradForm(torch, dev, args.quick))
         elif nm == "pbh_sys":
             forms.append(PbhSysForm(torch, dev, args.quick))
+        elif nm == "table1":
+            forms.append(Table1Form(torch, dev, args.quick))
         else:
             raise SystemExit(f"unknown form {nm}")
     handles = {id(f.handle): f.handle for f in forms if f.handle is not None}
@@ -855,7 +895,7 @@ def main():
                               if flush is None else "512 MB L2 flush between steps, outside the form timers"),
                        "parallelism": f"replicas x{world}"},
             "roofline": roof[dom.name], "forms": out_forms,
-            "e2e": {"value": units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": units / (e2e_ms * 1e-3) if e2e_ms > 0 else None, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": None if ours is None else ours * args.steps,
             "gpu_launches_detail": {"per_step_ours": ours, "per_step_all_kernels": allk, "kernels": kn},

@@ -50,7 +50,6 @@ struct SysArgs {
   int* flags;
   long long T;
   int nq, n_x, n_u;
-  int max_ts;                            // launch-derived: timesteps that 32 consecutive units touch
   unsigned long long magic_a, magic_b;   // launch-derived: ceil(2^32 / (3 nq)), ceil(2^32 / nq)
   SysConsts k;
 };

@@ -28,7 +28,14 @@
 //   v_z:       (T/m)(-c_th c_phi) at (phi,phi) and (th,th), (T/m) s_th s_phi at (phi,th), -c_th s_phi / m at
 //              (phi,T), -s_th c_phi / m at (th,T)
 //   p, q, r:   (q,r) (J_y - J_z)/J_x, (p,r) (J_z - J_x)/J_y, (p,q) (J_x - J_y)/J_z
-// every entry times dt. The centroid spring-damper coupling is linear: it adds to the Jacobian only.
+//
+// Layout on the GPU: one thread per unit, a unit being one (timestep, quadrotor) pair (one timestep for
+// the satellite), units in timestep-major order, so a unit's own states and inputs are contiguous in
+// x~ and u~. A warp takes 32 consecutive units and runs on its own (no CTA barrier): it stages their
+// boxes in shared memory, each lane computes its unit's trigonometric enclosures once, then the warp
+// walks the row types in lockstep (no divergence); after each row type the lanes leave their unit's
+// own Jacobian block in a shared stage and the warp stores those rows of A_k and B_k with float4 (the
+// rows of 32 units are separate but each row is contiguous and every row's stores complete it).
 #include <cmath>
 
 #include "internal.h"
@@ -37,12 +44,13 @@
 namespace leb {
 namespace {
 
-constexpr int kMaxQuad3 = 21;   // largest chain the staging buffers are sized for
+constexpr int kMaxQuad3 = 21;   // largest chain accepted (the coupling loop reads every quadrotor)
+constexpr int kSysWarps = 4;    // warps per CTA (independent)
 
 __device__ __forceinline__ ivl cv(const SysConst& k) { return iv(k.lo, k.hi); }
 __device__ __forceinline__ float mid(ivl a) { return 0.5f * a.lo + 0.5f * a.hi; }
 
-// Per-timestep view of the box (shared memory): lo, hi and the nominal of every coordinate.
+// A unit's box in shared memory: lo, hi and the nominal of its own coordinates (local indices).
 struct Box {
   const float* lo;
   const float* hi;
@@ -52,76 +60,118 @@ struct Box {
 };
 
 // Accumulates Eq. 15's terms and the Jacobian-rounding term of one output row; the row's own Jacobian
-// block (FP32 values A returned) goes to arow[0..ncol).
+// block (FP32 values A returned) goes to arow (compile-time columns, so it stays in registers).
+// Every Delta_j contains 0 (the box is hulled with the nominal), so the products of the terms take the
+// zero-straddling form of the interval product (identical results, half the multiplies). The rounding
+// term sum_j (J_j - A_j) Delta_j is bounded by its magnitude E = sum_j max|J_j - A_j| max|Delta_j|
+// (rounded up) and added as [-E, E] at the end.
+template <int NC>
 struct Row {
   const Box& b;
-  float* arow;
+  float (&arow)[NC];
   ivl R;
-  __device__ __forceinline__ Row(const Box& bx, float* ar) : b(bx), arow(ar), R(iv(0.f)) {}
+  float E;
+  __device__ __forceinline__ Row(const Box& bx, float (&ar)[NC]) : b(bx), arow(ar), R(iv(0.f)), E(0.f) {}
   // 1/2 [H_kk](X^(k)) Delta_k^2 (the interval of squares)
-  __device__ __forceinline__ void sq(int j, ivl H) { R = iv_add(R, iv_half(iv_mul(H, iv_sqr(b.D(j))))); }
+  __device__ __forceinline__ void sq(int j, ivl H) { R = iv_add(R, iv_half(iv_mul_z(H, iv_sqr_z(b.D(j))))); }
   // [H_kj](X^(j)) Delta_j Delta_k
-  __device__ __forceinline__ void cross(int j, int k, ivl H) { R = iv_add(R, iv_mul(H, iv_mul(b.D(j), b.D(k)))); }
-  // Jacobian entry of coordinate j, enclosed in J: returns A = its nearest-rounded midpoint in column c
-  // and adds (J - A) Delta_j
-  __device__ __forceinline__ void jac(int c, int j, ivl J) {
+  __device__ __forceinline__ void cross(int j, int k, ivl H) { R = iv_add(R, iv_mul_z(H, iv_mul_z(b.D(j), b.D(k)))); }
+  // Jacobian entry of own coordinate j, enclosed in J: A = its nearest-rounded midpoint
+  __device__ __forceinline__ void jac(int j, ivl J) {
     const float A = mid(J);
-    arow[c] = A;
-    R = iv_add(R, iv_mul(iv_sub(J, iv(A)), b.D(j)));
+    arow[j] = A;
+    const ivl d = b.D(j);
+    const float m = fmaxf(__fsub_ru(A, J.lo), __fsub_ru(J.hi, A)), dm = fmaxf(-d.lo, d.hi);
+    E = __fmaf_ru(m, dm, E);
   }
-  // a Jacobian entry stored outside the own block (its FP32 value Af is written by the A pass)
-  __device__ __forceinline__ void jac_ext(int j, ivl J, float Af) { R = iv_add(R, iv_mul(iv_sub(J, iv(Af)), b.D(j))); }
+  __device__ __forceinline__ ivl result() const { return {__fsub_rd(R.lo, E), __fadd_ru(R.hi, E)}; }
 };
 
 // ---- satellite ---------------------------------------------------------------------------------
 // zeta(w) q entry (l, b): index of the rate multiplying q_b (1..3) with its sign; 0 on the diagonal
-__device__ __forceinline__ int zeta_entry(int l, int b) {
-  constexpr int z[4][4] = {{0, -1, -2, -3}, {1, 0, 3, -2}, {2, -3, 0, 1}, {3, 2, -1, 0}};
-  return z[l][b];
-}
+template <int L, int B>
+struct Zeta {
+  static constexpr int z[4][4] = {{0, -1, -2, -3}, {1, 0, 3, -2}, {2, -3, 0, 1}, {3, 2, -1, 0}};
+  static constexpr int e = z[L][B];
+  static constexpr int w = e < 0 ? -e : e;
+};
 
-__device__ __forceinline__ void satellite_row(const SysConsts& K, const Box& b, int l, float* arow, ivl& R) {
-  Row r(b, arow);
-  if (l < 4) {
+template <int L>
+__device__ __forceinline__ ivl satellite_row(const SysConsts& K, const Box& b, float (&arow)[10]) {
+  Row<10> r(b, arow);
+  if constexpr (L < 4) {
     const ivl hp = cv(K.half_dt), hm = iv_neg(hp);
-    for (int q = 0; q < 4; ++q) {
-      const int e = zeta_entry(l, q);
-      if (e != 0) r.cross(q, 3 + (e < 0 ? -e : e), e < 0 ? hm : hp);   // (q_b, w_a), q before w
+    auto sg = [&](int e) { return e < 0 ? hm : hp; };
+    // Hessian (q_b, w_a), q before w
+#define SAT_TERM(B) \
+    if constexpr (Zeta<L, B>::e != 0) r.cross(B, 3 + Zeta<L, B>::w, sg(Zeta<L, B>::e));
+    SAT_TERM(0) SAT_TERM(1) SAT_TERM(2) SAT_TERM(3)
+#undef SAT_TERM
+    // d/dq_b = delta_lb + dt/2 zeta(w~)_lb
+#define SAT_JQ(B)                                                                     \
+    {                                                                                 \
+      ivl J = iv(B == L ? 1.f : 0.f);                                                 \
+      if constexpr (Zeta<L, B>::e != 0)                                               \
+        J = iv_add(J, iv_mul(sg(Zeta<L, B>::e), iv(b.nom[3 + Zeta<L, B>::w])));       \
+      r.jac(B, J);                                                                    \
     }
-    for (int q = 0; q < 4; ++q) {   // d/dq_b = delta_lb + dt/2 zeta(w~)_lb
-      const int e = zeta_entry(l, q);
-      ivl J = iv(q == l ? 1.f : 0.f);
-      if (e != 0) J = iv_add(J, iv_mul(e < 0 ? hm : hp, iv(b.nom[3 + (e < 0 ? -e : e)])));
-      r.jac(q, q, J);
-    }
-    for (int w = 1; w <= 3; ++w) {   // d/dw_a = dt/2 sum_b dzeta_lb/dw_a q~_b
+    SAT_JQ(0) SAT_JQ(1) SAT_JQ(2) SAT_JQ(3)
+#undef SAT_JQ
+    // d/dw_a = dt/2 sum_b dzeta_lb/dw_a q~_b
+    for (int w = 1; w <= 3; ++w) {
       ivl J = iv(0.f);
-      for (int q = 0; q < 4; ++q) {
-        const int e = zeta_entry(l, q);
-        if (e == w || e == -w) J = iv_add(J, iv_mul(e < 0 ? hm : hp, iv(b.nom[q])));
-      }
-      r.jac(3 + w, 3 + w, J);
+#define SAT_JW(B) \
+      if (Zeta<L, B>::e != 0 && Zeta<L, B>::w == w) J = iv_add(J, iv_mul(sg(Zeta<L, B>::e), iv(b.nom[B])));
+      SAT_JW(0) SAT_JW(1) SAT_JW(2) SAT_JW(3)
+#undef SAT_JW
+      if (w == 1) r.jac(4, J);
+      else if (w == 2) r.jac(5, J);
+      else r.jac(6, J);
     }
   } else {
-    const int ax = l - 4, jb = ax == 0 ? 5 : 4, jc = ax == 2 ? 5 : 6;   // the other two rates, jb < jc
+    constexpr int ax = L - 4, jb = ax == 0 ? 5 : 4, jc = ax == 2 ? 5 : 6;   // the other two rates, jb < jc
     const ivl k = cv(K.k[ax]);
     r.cross(jb, jc, k);
-    r.jac(l, l, iv(1.f));
-    r.jac(jb, jb, iv_mul(k, iv(b.nom[jc])));
-    r.jac(jc, jc, iv_mul(k, iv(b.nom[jb])));
-    r.jac(7 + ax, 7 + ax, cv(K.tq[ax]));
+    r.jac(L, iv(1.f));
+    r.jac(jb, iv_mul(k, iv(b.nom[jc])));
+    r.jac(jc, iv_mul(k, iv(b.nom[jb])));
+    r.jac(7 + ax, cv(K.tq[ax]));
   }
-  R = r.R;
+  return r.result();
 }
 
 // ---- 3-D quadrotor -----------------------------------------------------------------------------
+// Local coordinates of a unit: states 0..11, inputs 12..15.
+constexpr int PH = 3, TH = 4, PS = 5, P_ = 9, Q_ = 10, R_ = 11, T_ = 12;
+
+// Trigonometric enclosures of one unit, shared by its rows: over the box of each angle (the prefix
+// sets X^(phi), X^(theta), X^(psi) of the entries that range over it) and at the nominal.
+struct Trig {
+  ivl sP, cP, s0, c0;        // sin, cos of phi: box, nominal
+  ivl sT, cT, st0, ct0;      // theta
+  ivl sS, cS, ss0, cs0;      // psi
+  ivl tanT, secT, tan0, sec0;
+};
+
+__device__ __forceinline__ Trig make_trig(const Box& b) {
+  Trig t;
+  const ivl Ph = b.X(PH), Th = b.X(TH), Ps = b.X(PS);
+  const float ph0 = b.nom[PH], th0 = b.nom[TH], ps0 = b.nom[PS];
+  t.sP = iv_sin(Ph); t.cP = iv_cos(Ph); t.s0 = point_sin(ph0); t.c0 = point_cos(ph0);
+  t.sT = iv_sin(Th); t.cT = iv_cos(Th); t.st0 = point_sin(th0); t.ct0 = point_cos(th0);
+  t.sS = iv_sin(Ps); t.cS = iv_cos(Ps); t.ss0 = point_sin(ps0); t.cs0 = point_cos(ps0);
+  t.tanT = iv_tan(Th); t.secT = iv_sec(Th); t.tan0 = iv_tan(iv(th0)); t.sec0 = iv_sec(iv(th0));
+  return t;
+}
+
 struct G3 {   // g_x or g_y and its partials in (phi, theta, psi)
   ivl g, ph, th, ps, phth, phps, thth, thps;
 };
 
-__device__ __forceinline__ G3 g_parts(int s, ivl sph, ivl cph, ivl sth, ivl cth, ivl sps, ivl cps) {
+template <int S>
+__device__ __forceinline__ G3 g_parts(ivl sph, ivl cph, ivl sth, ivl cth, ivl sps, ivl cps) {
   G3 r;
-  if (s == 6) {   // g_x = c_psi s_th c_phi + s_psi s_phi
+  if constexpr (S == 6) {   // g_x = c_psi s_th c_phi + s_psi s_phi
     r.g = iv_add(iv_mul(iv_mul(cps, sth), cph), iv_mul(sps, sph));
     r.ph = iv_add(iv_neg(iv_mul(iv_mul(cps, sth), sph)), iv_mul(sps, cph));
     r.th = iv_mul(iv_mul(cps, cth), cph);
@@ -130,7 +180,7 @@ __device__ __forceinline__ G3 g_parts(int s, ivl sph, ivl cph, ivl sth, ivl cth,
     r.phps = iv_add(iv_mul(iv_mul(sps, sth), sph), iv_mul(cps, cph));
     r.thth = iv_neg(iv_mul(iv_mul(cps, sth), cph));
     r.thps = iv_neg(iv_mul(iv_mul(sps, cth), cph));
-  } else {        // g_y = s_psi s_th c_phi - c_psi s_phi
+  } else {                  // g_y = s_psi s_th c_phi - c_psi s_phi
     r.g = iv_add(iv_mul(iv_mul(sps, sth), cph), iv_neg(iv_mul(cps, sph)));
     r.ph = iv_add(iv_neg(iv_mul(iv_mul(sps, sth), sph)), iv_neg(iv_mul(cps, cph)));
     r.th = iv_mul(iv_mul(sps, cth), cph);
@@ -143,192 +193,316 @@ __device__ __forceinline__ G3 g_parts(int s, ivl sph, ivl cph, ivl sth, ivl cth,
   return r;
 }
 
-// Row s of quadrotor i. Own-block columns: 0..11 the quadrotor's states, 12..15 its inputs.
-__device__ __forceinline__ void quad3d_row(const SysConsts& K, const Box& b, int nq, int n_x, int i, int s, float* arow, ivl& R) {
-  Row r(b, arow);
-  const int x0 = 12 * i, u0 = n_x + 4 * i;
-  const int PH = x0 + 3, TH = x0 + 4, PS = x0 + 5, P = x0 + 9, Q = x0 + 10, RR = x0 + 11, TT = u0;
+// Row S of the unit (quadrotor i of timestep t).
+// tot: per-timestep sums over all quadrotors of Delta of the coupled columns (p_x, p_y, p_z, v_x, v_y, v_z).
+template <int S>
+__device__ __forceinline__ ivl quad3d_row(const SysArgs& a, const Box& b, const Trig& tr, const float* tot,
+                                          float (&arow)[16]) {
+  const SysConsts& K = a.k;
+  Row<16> r(b, arow);
   const ivl dt = cv(K.dt), mdt = iv_neg(dt);
-  if (s < 3) {
-    r.jac(s, x0 + s, iv(1.f));
-    r.jac(6 + s, x0 + 6 + s, dt);
-  } else if (s <= 5) {
-    const float ph0 = b.nom[PH], th0 = b.nom[TH];
-    const ivl Ph = b.X(PH), Th = b.X(TH);
-    const ivl sP = iv_sin(Ph), cP = iv_cos(Ph), s0 = point_sin(ph0), c0 = point_cos(ph0);
-    const ivl qv = iv(b.nom[Q]), rv = iv(b.nom[RR]);
-    const ivl Aph = iv_add(iv_mul(qv, sP), iv_mul(rv, cP));           // a over X^(phi)
-    const ivl Aphp = iv_add(iv_mul(qv, cP), iv_neg(iv_mul(rv, sP)));  // a_phi over X^(phi)
-    const ivl a0 = iv_add(iv_mul(qv, s0), iv_mul(rv, c0));
-    const ivl ap0 = iv_add(iv_mul(qv, c0), iv_neg(iv_mul(rv, s0)));
-    if (s == 4) {   // theta dot = q cos(phi) - r sin(phi)
+  if constexpr (S < 3) {
+    r.jac(S, iv(1.f));
+    r.jac(6 + S, dt);
+  } else if constexpr (S <= 5) {
+    const ivl qv = iv(b.nom[Q_]), rv = iv(b.nom[R_]);
+    const ivl Aph = iv_add(iv_mul(qv, tr.sP), iv_mul(rv, tr.cP));           // a over X^(phi)
+    const ivl Aphp = iv_add(iv_mul(qv, tr.cP), iv_neg(iv_mul(rv, tr.sP)));  // a_phi over X^(phi)
+    const ivl a0 = iv_add(iv_mul(qv, tr.s0), iv_mul(rv, tr.c0));
+    const ivl ap0 = iv_add(iv_mul(qv, tr.c0), iv_neg(iv_mul(rv, tr.s0)));
+    if constexpr (S == 4) {   // theta dot = q cos(phi) - r sin(phi)
       r.sq(PH, iv_mul(mdt, Aphp));
-      r.cross(PH, Q, iv_mul(mdt, sP));
-      r.cross(PH, RR, iv_mul(mdt, cP));
-      r.jac(3, PH, iv_mul(mdt, a0));
-      r.jac(4, TH, iv(1.f));
-      r.jac(10, Q, iv_mul(dt, c0));
-      r.jac(11, RR, iv_mul(mdt, s0));
-    } else {
-      const ivl tan0 = iv_tan(iv(th0)), sec0 = iv_sec(iv(th0));
-      const ivl tanT = iv_tan(Th), secT = iv_sec(Th);
-      if (s == 3) {   // phi dot = p + a tan(theta)
-        const ivl sec20 = iv_sqr(sec0), secT2 = iv_sqr(secT);
-        r.sq(PH, iv_mul(mdt, iv_mul(Aph, tan0)));
-        r.cross(PH, TH, iv_mul(dt, iv_mul(Aphp, sec20)));
-        r.sq(TH, iv_mul(iv_add(dt, dt), iv_mul(Aph, iv_mul(secT2, tanT))));
-        r.cross(PH, Q, iv_mul(dt, iv_mul(cP, tan0)));
-        r.cross(PH, RR, iv_mul(mdt, iv_mul(sP, tan0)));
-        r.cross(TH, Q, iv_mul(dt, iv_mul(sP, secT2)));
-        r.cross(TH, RR, iv_mul(dt, iv_mul(cP, secT2)));
-        r.jac(3, PH, iv_add(iv(1.f), iv_mul(dt, iv_mul(ap0, tan0))));
-        r.jac(4, TH, iv_mul(dt, iv_mul(a0, sec20)));
-        r.jac(9, P, dt);
-        r.jac(10, Q, iv_mul(dt, iv_mul(s0, tan0)));
-        r.jac(11, RR, iv_mul(dt, iv_mul(c0, tan0)));
-      } else {        // psi dot = a sec(theta)
-        const ivl sec0tan0 = iv_mul(sec0, tan0), secTtanT = iv_mul(secT, tanT);
-        r.sq(PH, iv_mul(mdt, iv_mul(Aph, sec0)));
-        r.cross(PH, TH, iv_mul(dt, iv_mul(Aphp, sec0tan0)));
-        r.sq(TH, iv_mul(dt, iv_mul(Aph, iv_mul(secT, iv_add(iv_sqr(tanT), iv_sqr(secT))))));
-        r.cross(PH, Q, iv_mul(dt, iv_mul(cP, sec0)));
-        r.cross(PH, RR, iv_mul(mdt, iv_mul(sP, sec0)));
-        r.cross(TH, Q, iv_mul(dt, iv_mul(sP, secTtanT)));
-        r.cross(TH, RR, iv_mul(dt, iv_mul(cP, secTtanT)));
-        r.jac(3, PH, iv_mul(dt, iv_mul(ap0, sec0)));
-        r.jac(4, TH, iv_mul(dt, iv_mul(a0, sec0tan0)));
-        r.jac(5, PS, iv(1.f));
-        r.jac(10, Q, iv_mul(dt, iv_mul(s0, sec0)));
-        r.jac(11, RR, iv_mul(dt, iv_mul(c0, sec0)));
-      }
+      r.cross(PH, Q_, iv_mul(mdt, tr.sP));
+      r.cross(PH, R_, iv_mul(mdt, tr.cP));
+      r.jac(PH, iv_mul(mdt, a0));
+      r.jac(TH, iv(1.f));
+      r.jac(Q_, iv_mul(dt, tr.c0));
+      r.jac(R_, iv_mul(mdt, tr.s0));
+    } else if constexpr (S == 3) {   // phi dot = p + a tan(theta)
+      const ivl sec20 = iv_sqr(tr.sec0), secT2 = iv_sqr(tr.secT);
+      r.sq(PH, iv_mul(mdt, iv_mul(Aph, tr.tan0)));
+      r.cross(PH, TH, iv_mul(dt, iv_mul(Aphp, sec20)));
+      r.sq(TH, iv_mul(iv_add(dt, dt), iv_mul(Aph, iv_mul(secT2, tr.tanT))));
+      r.cross(PH, Q_, iv_mul(dt, iv_mul(tr.cP, tr.tan0)));
+      r.cross(PH, R_, iv_mul(mdt, iv_mul(tr.sP, tr.tan0)));
+      r.cross(TH, Q_, iv_mul(dt, iv_mul(tr.sP, secT2)));
+      r.cross(TH, R_, iv_mul(dt, iv_mul(tr.cP, secT2)));
+      r.jac(PH, iv_add(iv(1.f), iv_mul(dt, iv_mul(ap0, tr.tan0))));
+      r.jac(TH, iv_mul(dt, iv_mul(a0, sec20)));
+      r.jac(P_, dt);
+      r.jac(Q_, iv_mul(dt, iv_mul(tr.s0, tr.tan0)));
+      r.jac(R_, iv_mul(dt, iv_mul(tr.c0, tr.tan0)));
+    } else {   // psi dot = a sec(theta)
+      const ivl sec0tan0 = iv_mul(tr.sec0, tr.tan0), secTtanT = iv_mul(tr.secT, tr.tanT);
+      r.sq(PH, iv_mul(mdt, iv_mul(Aph, tr.sec0)));
+      r.cross(PH, TH, iv_mul(dt, iv_mul(Aphp, sec0tan0)));
+      r.sq(TH, iv_mul(dt, iv_mul(Aph, iv_mul(tr.secT, iv_add(iv_sqr(tr.tanT), iv_sqr(tr.secT))))));
+      r.cross(PH, Q_, iv_mul(dt, iv_mul(tr.cP, tr.sec0)));
+      r.cross(PH, R_, iv_mul(mdt, iv_mul(tr.sP, tr.sec0)));
+      r.cross(TH, Q_, iv_mul(dt, iv_mul(tr.sP, secTtanT)));
+      r.cross(TH, R_, iv_mul(dt, iv_mul(tr.cP, secTtanT)));
+      r.jac(PH, iv_mul(dt, iv_mul(ap0, tr.sec0)));
+      r.jac(TH, iv_mul(dt, iv_mul(a0, sec0tan0)));
+      r.jac(PS, iv(1.f));
+      r.jac(Q_, iv_mul(dt, iv_mul(tr.s0, tr.sec0)));
+      r.jac(R_, iv_mul(dt, iv_mul(tr.c0, tr.sec0)));
     }
-  } else if (s <= 8) {   // velocities: (T/m) g + centroid coupling
-    const float ph0 = b.nom[PH], th0 = b.nom[TH], ps0 = b.nom[PS];
-    const ivl dtm = cv(K.dt_m), Tm = iv_mul(dtm, iv(b.nom[TT]));
-    const ivl Ph = b.X(PH), Th = b.X(TH), Ps = b.X(PS);
-    const ivl sP = iv_sin(Ph), cP = iv_cos(Ph), sT = iv_sin(Th), cT = iv_cos(Th);
-    const ivl s0 = point_sin(ph0), c0 = point_cos(ph0), st0 = point_sin(th0), ct0 = point_cos(th0);
-    if (s < 8) {
-      const ivl sS = iv_sin(Ps), cS = iv_cos(Ps), ss0 = point_sin(ps0), cs0 = point_cos(ps0);
-      const G3 gA = g_parts(s, sP, cP, st0, ct0, ss0, cs0);   // over X^(phi)
-      const G3 gB = g_parts(s, sP, cP, sT, cT, ss0, cs0);     // over X^(theta)
-      const G3 gC = g_parts(s, sP, cP, sT, cT, sS, cS);       // over X^(psi)
-      const G3 g0 = g_parts(s, s0, c0, st0, ct0, ss0, cs0);   // at the nominal
-      r.sq(PH, iv_mul(Tm, iv_neg(gA.g)));
-      r.cross(PH, TH, iv_mul(Tm, gA.phth));
-      r.cross(PH, PS, iv_mul(Tm, gA.phps));
-      r.sq(TH, iv_mul(Tm, gB.thth));
-      r.cross(TH, PS, iv_mul(Tm, gB.thps));
-      r.sq(PS, iv_mul(Tm, iv_neg(gC.g)));
-      r.cross(PH, TT, iv_mul(dtm, gA.ph));
-      r.cross(TH, TT, iv_mul(dtm, gB.th));
-      r.cross(PS, TT, iv_mul(dtm, gC.ps));
-      r.jac(3, PH, iv_mul(Tm, g0.ph));
-      r.jac(4, TH, iv_mul(Tm, g0.th));
-      r.jac(5, PS, iv_mul(Tm, g0.ps));
-      r.jac(12, TT, iv_mul(dtm, g0.g));
+  } else if constexpr (S <= 8) {   // velocities: (T/m) g + centroid coupling
+    const ivl dtm = cv(K.dt_m), Tm = iv_mul(dtm, iv(b.nom[T_]));
+    if constexpr (S < 8) {
+      {
+        const G3 g = g_parts<S>(tr.sP, tr.cP, tr.st0, tr.ct0, tr.ss0, tr.cs0);   // over X^(phi)
+        r.sq(PH, iv_mul(Tm, iv_neg(g.g)));
+        r.cross(PH, TH, iv_mul(Tm, g.phth));
+        r.cross(PH, PS, iv_mul(Tm, g.phps));
+        r.cross(PH, T_, iv_mul(dtm, g.ph));
+      }
+      {
+        const G3 g = g_parts<S>(tr.sP, tr.cP, tr.sT, tr.cT, tr.ss0, tr.cs0);     // over X^(theta)
+        r.sq(TH, iv_mul(Tm, g.thth));
+        r.cross(TH, PS, iv_mul(Tm, g.thps));
+        r.cross(TH, T_, iv_mul(dtm, g.th));
+      }
+      {
+        const G3 g = g_parts<S>(tr.sP, tr.cP, tr.sT, tr.cT, tr.sS, tr.cS);       // over X^(psi)
+        r.sq(PS, iv_mul(Tm, iv_neg(g.g)));
+        r.cross(PS, T_, iv_mul(dtm, g.ps));
+      }
+      {
+        const G3 g = g_parts<S>(tr.s0, tr.c0, tr.st0, tr.ct0, tr.ss0, tr.cs0);   // at the nominal
+        r.jac(PH, iv_mul(Tm, g.ph));
+        r.jac(TH, iv_mul(Tm, g.th));
+        r.jac(PS, iv_mul(Tm, g.ps));
+        r.jac(T_, iv_mul(dtm, g.g));
+      }
     } else {   // g_z = cos(theta) cos(phi)
-      r.sq(PH, iv_mul(Tm, iv_neg(iv_mul(ct0, cP))));
-      r.cross(PH, TH, iv_mul(Tm, iv_mul(st0, sP)));
-      r.sq(TH, iv_mul(Tm, iv_neg(iv_mul(cT, cP))));
-      r.cross(PH, TT, iv_mul(dtm, iv_neg(iv_mul(ct0, sP))));
-      r.cross(TH, TT, iv_mul(dtm, iv_neg(iv_mul(sT, cP))));
-      r.jac(3, PH, iv_mul(Tm, iv_neg(iv_mul(ct0, s0))));
-      r.jac(4, TH, iv_mul(Tm, iv_neg(iv_mul(st0, c0))));
-      r.jac(12, TT, iv_mul(dtm, iv_mul(ct0, c0)));
+      r.sq(PH, iv_mul(Tm, iv_neg(iv_mul(tr.ct0, tr.cP))));
+      r.cross(PH, TH, iv_mul(Tm, iv_mul(tr.st0, tr.sP)));
+      r.sq(TH, iv_mul(Tm, iv_neg(iv_mul(tr.cT, tr.cP))));
+      r.cross(PH, T_, iv_mul(dtm, iv_neg(iv_mul(tr.ct0, tr.sP))));
+      r.cross(TH, T_, iv_mul(dtm, iv_neg(iv_mul(tr.sT, tr.cP))));
+      r.jac(PH, iv_mul(Tm, iv_neg(iv_mul(tr.ct0, tr.s0))));
+      r.jac(TH, iv_mul(Tm, iv_neg(iv_mul(tr.st0, tr.c0))));
+      r.jac(T_, iv_mul(dtm, iv_mul(tr.ct0, tr.c0)));
     }
-    const int ax = s - 6;
-    r.jac(ax, x0 + ax, cv(K.ca_self));
-    r.jac(s, x0 + s, cv(K.cg_self));
+    constexpr int ax = S - 6;
+    r.jac(ax, cv(K.ca_self));
+    r.jac(S, cv(K.cg_self));
     if (K.coupled) {
-      for (int j = 0; j < nq; ++j) {
-        if (j == i) continue;
-        r.jac_ext(12 * j + ax, cv(K.ca_other), K.ca_other.f);
-        r.jac_ext(12 * j + s, cv(K.cg_other), K.cg_other.f);
-      }
+      // every other quadrotor's column carries the same real J and the same FP32 A, so
+      // sum_{j != i} (J - A) Delta_j lies in (J - A) (sum_j Delta_j - Delta_i)
+      const ivl op = iv_sub(iv(tot[2 * ax], tot[2 * ax + 1]), b.D(ax));
+      const ivl ov = iv_sub(iv(tot[2 * (3 + ax)], tot[2 * (3 + ax) + 1]), b.D(S));
+      r.R = iv_add(r.R, iv_mul(iv_sub(cv(K.ca_other), iv(K.ca_other.f)), op));
+      r.R = iv_add(r.R, iv_mul(iv_sub(cv(K.cg_other), iv(K.cg_other.f)), ov));
     }
   } else {   // body rates: one bilinear term and the torque input
-    const int ax = s - 9;
+    constexpr int ax = S - 9, jb = ax == 0 ? Q_ : P_, jc = ax == 2 ? Q_ : R_;   // the other two rates
     const ivl k = cv(K.k[ax]);
-    const int jb = ax == 0 ? Q : P, jc = ax == 2 ? Q : RR;   // the other two rates, jb < jc
     r.cross(jb, jc, k);
-    r.jac(s, x0 + s, iv(1.f));
-    r.jac(jb - x0, jb, iv_mul(k, iv(b.nom[jc])));
-    r.jac(jc - x0, jc, iv_mul(k, iv(b.nom[jb])));
-    r.jac(13 + ax, u0 + 1 + ax, cv(K.tq[ax]));
+    r.jac(S, iv(1.f));
+    r.jac(jb, iv_mul(k, iv(b.nom[jc])));
+    r.jac(jc, iv_mul(k, iv(b.nom[jb])));
+    r.jac(13 + ax, cv(K.tq[ax]));
   }
-  R = r.R;
+  return r.result();
 }
 
 // ---- kernel ------------------------------------------------------------------------------------
-// Work unit: one (timestep, quadrotor) pair (one timestep for the satellite), units in timestep-major
-// order. A CTA takes 32 consecutive units; warp s evaluates output row s of the model for all 32 of them
-// (lane = unit), so a warp never diverges over the row type. The units' timesteps are staged in shared
-// memory first (box and nominal), and the outputs of the 32 units -- r_lo, r_hi and the rows of A_k and
-// B_k that belong to them -- are contiguous ranges in HBM, written after the evaluation as coalesced
-// stores (float4 for the 3-D quadrotor, whose row and block widths are multiples of 4).
-constexpr int kUnits = 32;
-
 template <bool kQuad>
 struct SysShape {
-  static constexpr int rows = kQuad ? 12 : 7;     // output rows per unit (= warps per CTA)
-  static constexpr int ncol = kQuad ? 16 : 10;    // own-block Jacobian columns per row (shared stride)
-  static constexpr int threads = 32 * rows;
+  static constexpr int rows = kQuad ? 12 : 7;       // output rows per unit
+  static constexpr int nc = kQuad ? 16 : 10;        // own coordinates per unit (states, inputs)
+  static constexpr int nxu = kQuad ? 12 : 7;        // own states per unit
+  static constexpr int nuu = kQuad ? 4 : 3;         // own inputs per unit
+  static constexpr int bs = nc + 1;                 // box stride (odd: no bank conflicts across lanes)
+  static constexpr int as = kQuad ? 20 : 11;        // stage stride (20: conflict-free float4 per 8 lanes)
+  // per-warp shared floats: row stage, box lo / hi / nominal, r_lo / r_hi of all rows, coupled-column
+  // sums per timestep (quadrotors), bad word per timestep
+  static constexpr int warp_floats = 32 * as + 3 * 32 * bs + 2 * 32 * rows + (kQuad ? 32 * 12 : 0) + 32;
 };
 
 template <bool kQuad>
-__global__ void __launch_bounds__(SysShape<kQuad>::threads) pbh_sys_kernel(SysArgs a) {
+__device__ __forceinline__ ivl eval_row(const SysArgs& a, int s, const Box& b, const Trig& tr, const float* tot,
+                                        float (&arow)[SysShape<kQuad>::nc]) {
+  if constexpr (kQuad) {
+    switch (s) {
+      case 0: return quad3d_row<0>(a, b, tr, tot, arow);
+      case 1: return quad3d_row<1>(a, b, tr, tot, arow);
+      case 2: return quad3d_row<2>(a, b, tr, tot, arow);
+      case 3: return quad3d_row<3>(a, b, tr, tot, arow);
+      case 4: return quad3d_row<4>(a, b, tr, tot, arow);
+      case 5: return quad3d_row<5>(a, b, tr, tot, arow);
+      case 6: return quad3d_row<6>(a, b, tr, tot, arow);
+      case 7: return quad3d_row<7>(a, b, tr, tot, arow);
+      case 8: return quad3d_row<8>(a, b, tr, tot, arow);
+      case 9: return quad3d_row<9>(a, b, tr, tot, arow);
+      case 10: return quad3d_row<10>(a, b, tr, tot, arow);
+      default: return quad3d_row<11>(a, b, tr, tot, arow);
+    }
+  } else {
+    switch (s) {
+      case 0: return satellite_row<0>(a.k, b, arow);
+      case 1: return satellite_row<1>(a.k, b, arow);
+      case 2: return satellite_row<2>(a.k, b, arow);
+      case 3: return satellite_row<3>(a.k, b, arow);
+      case 4: return satellite_row<4>(a.k, b, arow);
+      case 5: return satellite_row<5>(a.k, b, arow);
+      default: return satellite_row<6>(a.k, b, arow);
+    }
+  }
+}
+
+template <bool kQuad>
+__global__ void __launch_bounds__(32 * kSysWarps, kQuad ? 4 : 8) pbh_sys_kernel(SysArgs a) {
   using S = SysShape<kQuad>;
   extern __shared__ __align__(16) float sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* base = sm + warp * S::warp_floats;
+  float* s_stage = base;                          // [32][as]  (first: 16-byte aligned for float4)
+  float* s_lo = s_stage + 32 * S::as;             // [32][bs]
+  float* s_hi = s_lo + 32 * S::bs;
+  float* s_nom = s_hi + 32 * S::bs;
+  float* s_R = s_nom + 32 * S::bs;                // [32 * rows][2]
+  float* s_tot = s_R + 2 * 32 * S::rows;          // [timestep slot][6][2] (quadrotors)
+  int* s_bad = (int*)(s_tot + (kQuad ? 32 * 12 : 0));   // [timestep slot]
   const int n_x = a.n_x, n_u = a.n_u, n = n_x + n_u, nq = kQuad ? a.nq : 1;
-  const int max_ts = a.max_ts;                    // timesteps that 32 consecutive units can touch
-  float* s_A = sm;                                // [32 * rows][ncol]
-  float* s_R = s_A + kUnits * S::rows * S::ncol;  // [32 * rows][2]
-  float* s_lo = s_R + kUnits * S::rows * 2;       // [max_ts][n]
-  float* s_hi = s_lo + max_ts * n;
-  float* s_nom = s_hi + max_ts * n;
-  int* s_bad = (int*)(s_nom + max_ts * n);        // [max_ts]
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long U = a.T * nq;
-  for (long long u0 = (long long)blockIdx.x * kUnits; u0 < U; u0 += (long long)gridDim.x * kUnits) {
-    const int nu = (int)min((long long)kUnits, U - u0);
-    const long long t0 = u0 / nq;
-    const int nts = (int)((u0 + nu - 1) / nq - t0) + 1;
-    if (tid < nts) s_bad[tid] = 0;
-    __syncthreads();
-    // box of the set hulled with the nominal (Thm. 1 needs the nominal inside), staged per timestep
-    for (int e = tid; e < nts * n; e += blockDim.x) {
-      const int p = e / n, j = e - p * n;
-      const long long t = t0 + p;
-      const float nom = j < n_x ? a.x_nom[t * n_x + j] : a.u_nom[t * n_u + (j - n_x)];
-      const float c = a.center ? a.center[t0 * n + e] : nom;
-      const float rad = a.radii[t0 * n + e];
-      s_lo[e] = fminf(__fsub_rd(c, rad), nom);
-      s_hi[e] = fmaxf(__fadd_ru(c, rad), nom);
-      s_nom[e] = nom;
-      if (!(isfinite(nom) && isfinite(c) && isfinite(rad) && rad >= 0.f)) s_bad[p] = 1;
+  const long long stride = (long long)gridDim.x * kSysWarps * 32;
+  for (long long u0 = ((long long)blockIdx.x * kSysWarps + warp) * 32; u0 < U; u0 += stride) {
+    const int nu = (int)min(32LL, U - u0);
+    const long long t_first = u0 / nq;
+    const int i0 = (int)(u0 - t_first * nq);   // quadrotor of the first unit
+    // (i0 + k) / nq for k < 32 without a 64-bit division (magic_b = ceil(2^32 / nq), exact for x < 2^26)
+    auto divq = [&](unsigned x) { return kQuad ? (unsigned)(((unsigned long long)x * a.magic_b) >> 32) : x; };
+    const int nts = (int)((u0 + nu - 1) / nq - t_first) + 1;   // timesteps the units touch (<= 32)
+    s_bad[lane] = 0;
+    __syncwarp();
+    // stage the units' boxes: the set hulled with the nominal (Thm. 1 needs the nominal inside)
+    for (int e = lane; e < nu * S::nc; e += 32) {
+      const int k = e / S::nc, j = e - k * S::nc;
+      const unsigned dq = divq(i0 + k);
+      const long long u = u0 + k, t = t_first + dq;
+      const int i = i0 + k - (int)dq * nq;
+      const int g = j < S::nxu ? S::nxu * i + j : n_x + S::nuu * i + (j - S::nxu);   // column in the timestep
+      const float nom = j < S::nxu ? a.x_nom[u * S::nxu + j] : a.u_nom[u * S::nuu + (j - S::nxu)];
+      const float c = a.center ? a.center[t * n + g] : nom;
+      const float rad = a.radii[t * n + g];
+      s_lo[k * S::bs + j] = fminf(__fsub_rd(c, rad), nom);
+      s_hi[k * S::bs + j] = fmaxf(__fadd_ru(c, rad), nom);
+      s_nom[k * S::bs + j] = nom;
+      if (!(isfinite(nom) && isfinite(c) && isfinite(rad) && rad >= 0.f)) s_bad[t - t_first] = 1;
     }
-    __syncthreads();
-    if (lane < nu) {
-      const long long u = u0 + lane;
-      const int slot = (int)(u / nq - t0), i = (int)(u % nq);
-      const Box b{s_lo + slot * n, s_hi + slot * n, s_nom + slot * n};
-      const int r = lane * S::rows + warp;        // this row among the CTA's 32 * rows
-      float* arow = s_A + r * S::ncol;
+    if constexpr (kQuad) {
+      if (nq > 1) {
+        // a timestep with a bad input is poisoned as a whole: scan every input of the touched timesteps
+        for (int e = lane; e < nts * n; e += 32) {
+          const int p = e / n, j = e - p * n;
+          const long long t = t_first + p;
+          const float nom = j < n_x ? a.x_nom[t * n_x + j] : a.u_nom[t * n_u + (j - n_x)];
+          const float c = a.center ? a.center[t_first * n + e] : nom;
+          const float rad = a.radii[t_first * n + e];
+          if (!(isfinite(nom) && isfinite(c) && isfinite(rad) && rad >= 0.f)) s_bad[p] = 1;
+        }
+        // sums of Delta over all quadrotors of the coupled columns, per touched timestep
+        if (a.k.coupled)
+          for (int e = lane; e < nts * 6; e += 32) {
+            const int p = e / 6, col = e - 6 * p, local = col < 3 ? col : col + 3;
+            const long long t = t_first + p;
+            ivl S = iv(0.f);
+            for (int j = 0; j < nq; ++j) {
+              const int g = 12 * j + local;
+              const float nom = a.x_nom[t * n_x + g];
+              const float c = a.center ? a.center[t * n + g] : nom;
+              const float rad = a.radii[t * n + g];
+              const float lo = fminf(__fsub_rd(c, rad), nom), hi = fmaxf(__fadd_ru(c, rad), nom);
+              S = iv_add(S, iv(__fsub_rd(lo, nom), __fsub_ru(hi, nom)));
+            }
+            s_tot[2 * e] = S.lo;
+            s_tot[2 * e + 1] = S.hi;
+          }
+      }
+    }
+    __syncwarp();
+    const int slot = (int)divq(i0 + lane), i = i0 + lane - slot * nq;
+    const Box b{s_lo + lane * S::bs, s_hi + lane * S::bs, s_nom + lane * S::bs};
+    const float* tot = kQuad ? s_tot + 12 * slot : nullptr;
+    Trig tr{};
+    if constexpr (kQuad) {
+      if (lane < nu) tr = make_trig(b);
+    }
+    const bool bad = lane < nu && s_bad[slot] != 0;
+    if (bad && i == 0) atomicOr(a.flags, LEB_ASYNC_NONFINITE);
+    for (int s = 0; s < S::rows; ++s) {
+      if (lane < nu) {
+        float arow[S::nc];
 #pragma unroll
-      for (int c = 0; c < S::ncol; ++c) arow[c] = 0.f;
-      ivl R;
-      if constexpr (kQuad) quad3d_row(a.k, b, nq, n_x, i, warp, arow, R);
-      else satellite_row(a.k, b, warp, arow, R);
-      if (s_bad[slot] || !finite_ivl(R)) R = iv(-CUDART_INF_F, CUDART_INF_F);
-      s_R[2 * r] = R.lo;
-      s_R[2 * r + 1] = R.hi;
-      if (warp == 0 && i == 0 && s_bad[slot]) atomicOr(a.flags, LEB_ASYNC_NONFINITE);
+        for (int c = 0; c < S::nc; ++c) arow[c] = 0.f;
+        ivl R = eval_row<kQuad>(a, s, b, tr, tot, arow);
+        if (bad || !finite_ivl(R)) R = iv(-CUDART_INF_F, CUDART_INF_F);
+        s_R[2 * (lane * S::rows + s)] = R.lo;
+        s_R[2 * (lane * S::rows + s) + 1] = R.hi;
+        float* st = s_stage + lane * S::as;
+        if constexpr (kQuad) {
+#pragma unroll
+          for (int c = 0; c < 16; c += 4)
+            *reinterpret_cast<float4*>(st + c) = make_float4(arow[c], arow[c + 1], arow[c + 2], arow[c + 3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 10; ++c) st[c] = arow[c];
+        }
+      }
+      __syncwarp();
+      // rows s of A_k and B_k of the 32 units
+      if constexpr (kQuad) {
+        if (a.A) {
+          const unsigned cpr = 3u * nq, total = (unsigned)nu * cpr;
+          for (unsigned q = lane; q < total; q += 32) {
+            const unsigned k = (unsigned)(((unsigned long long)q * a.magic_a) >> 32);   // q / cpr
+            const unsigned c = q - k * cpr, jq = c / 3u, sc = (c - 3u * jq) * 4u;
+            const long long uk = u0 + k;
+            const int ik = i0 + (int)k - (int)divq(i0 + k) * nq;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if ((int)jq == ik) {
+              v = *reinterpret_cast<const float4*>(s_stage + k * S::as + sc);
+            } else if (a.k.coupled && s >= 6 && s <= 8) {
+              // the other quadrotor's position (column s - 6) and velocity (column s) in the same axis
+              const float ca = a.k.ca_other.f, cg = a.k.cg_other.f;
+              auto pick = [&](unsigned col) { return (int)col == s - 6 ? ca : ((int)col == s ? cg : 0.f); };
+              v = make_float4(pick(sc), pick(sc + 1u), pick(sc + 2u), pick(sc + 3u));
+            }
+            reinterpret_cast<float4*>(a.A + (uk * 12 + s) * n_x)[c] = v;
+          }
+        }
+        if (a.B) {
+          const unsigned total = (unsigned)nu * (unsigned)nq;
+          for (unsigned q = lane; q < total; q += 32) {
+            const unsigned k = (unsigned)(((unsigned long long)q * a.magic_b) >> 32);   // q / nq
+            const unsigned c = q - k * (unsigned)nq;
+            const long long uk = u0 + k;
+            const int ik = i0 + (int)k - (int)divq(i0 + k) * nq;
+            const float4 v = (int)c == ik ? *reinterpret_cast<const float4*>(s_stage + k * S::as + 12)
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+            reinterpret_cast<float4*>(a.B + (uk * 12 + s) * n_u)[c] = v;
+          }
+        }
+      } else {
+        if (a.A)
+          for (int q = lane; q < nu * 7; q += 32) {
+            const int k = q / 7, m = q - 7 * k;
+            a.A[((u0 + k) * 7 + s) * 7 + m] = s_stage[k * S::as + m];
+          }
+        if (a.B)
+          for (int q = lane; q < nu * 3; q += 32) {
+            const int k = q / 3, m = q - 3 * k;
+            a.B[((u0 + k) * 7 + s) * 3 + m] = s_stage[k * S::as + 7 + m];
+          }
+      }
+      __syncwarp();
     }
-    __syncthreads();
-    // r_lo, r_hi (and the zonotope map): the rows of units u0 .. u0 + nu - 1 are one contiguous range
+    // r_lo, r_hi (and the zonotope map) of the 32 units: one contiguous range
     const long long o0 = u0 * S::rows;
-    for (int r = tid; r < nu * S::rows; r += blockDim.x) {
+    for (int r = lane; r < nu * S::rows; r += 32) {
       const float lo = s_R[2 * r], hi = s_R[2 * r + 1];
       a.r_lo[o0 + r] = lo;
       a.r_hi[o0 + r] = hi;
@@ -339,57 +513,7 @@ __global__ void __launch_bounds__(SysShape<kQuad>::threads) pbh_sys_kernel(SysAr
       }
       if (a.eps) a.eps[o0 + r] = 0.f;
     }
-    if constexpr (kQuad) {
-      // A rows: 3 nq float4 chunks per row; chunk (row R, c) covers columns 4c .. 4c + 3 of block c / 3
-      if (a.A) {
-        const unsigned cpr = 3u * nq, total = (unsigned)(nu * S::rows) * cpr;
-        float4* dst = reinterpret_cast<float4*>(a.A + o0 * n_x);
-        for (unsigned q = tid; q < total; q += blockDim.x) {
-          const unsigned R = (unsigned)(((unsigned long long)q * a.magic_a) >> 32);   // q / cpr
-          const unsigned c = q - R * cpr, jq = c / 3u, sc = (c - 3u * jq) * 4u;
-          const unsigned un = R / 12u, s = R - 12u * un;
-          const int i = (int)((u0 + un) % nq);
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if ((int)jq == i) {
-            v = *reinterpret_cast<const float4*>(s_A + R * S::ncol + sc);
-          } else if (a.k.coupled && s >= 6u && s <= 8u) {
-            // the other quadrotor's position (column s - 6) and velocity (column s) in the same axis
-            const float ca = a.k.ca_other.f, cg = a.k.cg_other.f;
-            auto pick = [&](unsigned col) { return col == s - 6u ? ca : (col == s ? cg : 0.f); };
-            v = make_float4(pick(sc), pick(sc + 1u), pick(sc + 2u), pick(sc + 3u));
-          }
-          dst[q] = v;
-        }
-      }
-      // B rows: nq float4 chunks per row, the unit's own inputs in chunk i
-      if (a.B) {
-        const unsigned total = (unsigned)(nu * S::rows) * (unsigned)nq;
-        float4* dst = reinterpret_cast<float4*>(a.B + o0 * n_u);
-        for (unsigned q = tid; q < total; q += blockDim.x) {
-          const unsigned R = (unsigned)(((unsigned long long)q * a.magic_b) >> 32);   // q / nq
-          const unsigned c = q - R * (unsigned)nq, un = R / 12u;
-          const int i = (int)((u0 + un) % nq);
-          dst[q] = (int)c == i ? *reinterpret_cast<const float4*>(s_A + R * S::ncol + 12)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-      }
-    } else {
-      if (a.A) {
-        float* dst = a.A + o0 * 7;
-        for (int e = tid; e < nu * 49; e += blockDim.x) {
-          const int R = e / 7, m = e - 7 * R;
-          dst[e] = s_A[R * S::ncol + m];
-        }
-      }
-      if (a.B) {
-        float* dst = a.B + o0 * 3;
-        for (int e = tid; e < nu * 21; e += blockDim.x) {
-          const int R = e / 3, m = e - 3 * R;
-          dst[e] = s_A[R * S::ncol + 7 + m];
-        }
-      }
-    }
-    __syncthreads();   // shared buffers are reused by the next 32 units
+    __syncwarp();   // the shared buffers are reused by the warp's next 32 units
   }
 }
 
@@ -400,20 +524,30 @@ leb_status launch_pbh_sys(const Ctx& c, const SysArgs& args, cudaStream_t s) {
   const bool quad = c.kind == LEB_DYN_QUAD3D;
   if (quad && args.nq > kMaxQuad3) return LEB_ERR_UNSUPPORTED;
   SysArgs a = args;
-  const int nq = quad ? a.nq : 1, n = a.n_x + a.n_u;
-  a.max_ts = (kUnits - 1) / nq + 2;                                   // timesteps 32 consecutive units span
+  const int nq = quad ? a.nq : 1;
   a.magic_a = (0x100000000ULL + 3ULL * nq - 1) / (3ULL * nq);         // ceil(2^32 / (3 nq))
   a.magic_b = (0x100000000ULL + nq - 1) / (unsigned long long)nq;    // ceil(2^32 / nq)
-  const int rows = quad ? SysShape<true>::rows : SysShape<false>::rows;
-  const int ncol = quad ? SysShape<true>::ncol : SysShape<false>::ncol;
-  const size_t smem = (size_t)kUnits * rows * (ncol + 2) * sizeof(float) + (size_t)a.max_ts * 3 * n * sizeof(float) +
-                      (size_t)a.max_ts * sizeof(int);
-  const long long groups = (a.T * nq + kUnits - 1) / kUnits;
-  const long long cap = (quad ? 4LL : 8LL) * c.sm_count;
+  const size_t smem = (size_t)kSysWarps * (quad ? SysShape<true>::warp_floats : SysShape<false>::warp_floats) *
+                      sizeof(float);
+  if (quad && cudaFuncSetAttribute(pbh_sys_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                  cudaSuccess)
+    return LEB_ERR_CUDA;
+  // persistent grid: exactly the CTAs that fit at once, so the warps' uniform iterations leave no tail wave
+  static int resident[2] = {0, 0};
+  int& nb = resident[quad ? 1 : 0];
+  if (nb == 0) {
+    const cudaError_t e = quad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pbh_sys_kernel<true>,
+                                                                                 32 * kSysWarps, smem)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pbh_sys_kernel<false>,
+                                                                                 32 * kSysWarps, smem);
+    if (e != cudaSuccess || nb < 1) nb = 1;
+  }
+  const long long groups = (a.T * nq + 32 * kSysWarps - 1) / (32 * kSysWarps);
+  const long long cap = (long long)nb * c.sm_count;
   const int grid = (int)(groups < cap ? groups : cap);
   timer_begin(c, s, quad ? "pbh_quad3d" : "pbh_satellite");
-  if (quad) pbh_sys_kernel<true><<<grid, SysShape<true>::threads, smem, s>>>(a);
-  else pbh_sys_kernel<false><<<grid, SysShape<false>::threads, smem, s>>>(a);
+  if (quad) pbh_sys_kernel<true><<<grid, 32 * kSysWarps, smem, s>>>(a);
+  else pbh_sys_kernel<false><<<grid, 32 * kSysWarps, smem, s>>>(a);
   timer_end(c, s);
   return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
 }
