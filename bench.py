@@ -56,6 +56,9 @@ DRAM_BYTES_PER_TS_LAUNCH = {
     "pbh": 311_519_744 / 800,                  # pbh_zono_tma_kernel
     "crown": 44_803_072 / (3 * 400),           # crown_tc_kernel, mean over its 3 launches
     "backward": 86_559_744 / (5 * 400),        # 2 tight crown_tc_kernel + 3 adjoint_tc_kernel launches, mean
+    # pbh_sys_kernel<true>, captured at the bench's own size (12800 timesteps of the 168-state coupled
+    # system, profiles/pbh_sys_kernel_coupled_quad3d14_T12800.md)
+    "pbh_sys": (39_297_792 + 1_901_738_000) / 12800,
 }
 
 
@@ -581,7 +584,8 @@ class PbhSysForm(Form):
     def roofline(self, pk, ms, launches, kernel):
         achieved = self.BYTES_PER_TS * self.T / (ms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
+                "frac": round(achieved / pk["hbm_gbs"], 4),
+                "traffic": dram_traffic("pbh_sys", self.T // max(launches, 1)),
                 "peak_src": pk["src"] + " hbm_gbs (STREAM-style copy)", "kernel": kernel,
                 "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
                 "bytes_per_unit": self.BYTES_PER_TS, "units_per_launch": self.T // max(launches, 1)}
