@@ -15,6 +15,11 @@ written from the paper's definitions:
                        activation-pattern enumeration with linear programs for ReLU networks.
 * ``oracle.sampling``  sampled true remainders for soundness checks.
 * ``oracle.proposer``  the learned bound proposer's MLP forward/backward/Adam step.
+* ``oracle.dynamics3d`` the satellite and (coupled) 3-D quadrotor models of App. A with their
+                       hand-derived Hessian entries.
+* ``oracle.pbh_grad``  the gradient of the PBH bound (differentiable LEBs, Sec. III-D).
+* ``oracle.tube``      the step after the LEB: Ebar_j = [E(z_j) R_j] (Eq. 18b) and the tube centre and
+                       width h^mu, h^sigma (Eqs. 20-21) from packed system responses.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import this
 package. The product path (``paper_2607_01203_b300``) never imports it, and this package imports

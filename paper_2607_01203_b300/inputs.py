@@ -20,6 +20,9 @@ Workloads (shapes follow the paper's systems, App. A, at synthetic sizes):
                       bound proposer.
 * ``satellite``       7-state satellite (App. A "Satellite"), nominal points drawn from the
                       state / input ranges, local box sets (z, v) + eps E (the width-vs-eps study).
+* ``tube``            system responses Phi_{k,j} of a stable LTV closed loop (packed lower-triangular
+                      blocks) with Gamma-map centres / radii and a diagonal disturbance scaling, the
+                      inputs of the tube centre and width (Sec. IV-A).
 * ``quad3d``          N 3-D quadrotors (App. A "Coupled 3D Quadrotor"), optionally coupled by the
                       centroid spring-damper (alpha = 0.75, gamma = 0.25), drawn the same way; the
                       paper's 168-state system is 14 coupled quadrotors over a horizon of 25.
@@ -292,3 +295,60 @@ def quad3d(seed: int = SEED_BASE + 7, T: int = 1000, n_quads: int = 1, eps: floa
     return Workload("quad3d", "quad3d", n_x, n_u, X.reshape(T, n_x).astype(np.float32),
                     U.reshape(T, n_u).astype(np.float32), offs, "box", radii=radii.astype(np.float32),
                     params=params, n_quads=n_quads)
+
+
+@dataclasses.dataclass
+class TubeWorkload:
+    """Inputs of the tube centre / width step. Phi: [n_traj, N (N + 1) / 2, n_x + n_u, n_x] packed
+    (block k (k - 1) / 2 + j holds [Phi^x_{k,j}; Phi^u_{k,j}]); c, r: [n_traj * N, n_x] Gamma-map
+    centres and radii; e: [n_x] diagonal of the disturbance scaling E. A, B, K: the closed loop the
+    responses come from ([n_traj, N + 1, ...]; Phi^x_{k+1,j} = (A_k + B_k K_k) Phi^x_{k,j},
+    Phi^u_{k,j} = K_k Phi^x_{k,j}, Phi^x_{j+1,j} = I)."""
+    n_traj: int
+    N: int
+    n_x: int
+    n_u: int
+    Phi: np.ndarray
+    c: np.ndarray
+    r: np.ndarray
+    e: np.ndarray
+    A: np.ndarray
+    B: np.ndarray
+    K: np.ndarray
+    Phi64: np.ndarray | None = None     # the responses before their rounding to FP32 (keep_model only)
+
+
+def tube(seed: int = SEED_BASE + 8, n_traj: int = 2, N: int = 25, n_x: int = 12, n_u: int = 4,
+         keep_model: bool = True) -> TubeWorkload:
+    """Responses of a random stable LTV closed loop: A_k = 0.95 I + 0.1 N(0, 1/n_x), B_k = 0.1 N(0, 1/n_x),
+    K_k = 0.3 N(0, 1/n_x); Gamma-map centres N(0, 1e-3^2), radii U[1e-4, 1e-2]; E = 5e-3 diag(U[0, 1])
+    (the paper's E scales a subset of the states by 5e-3 or 5e-2, App. A). Per-trajectory streams."""
+    P = N * (N + 1) // 2
+    n = n_x + n_u
+    Phi = np.empty((n_traj, P, n, n_x), np.float32)
+    Phi64 = np.empty((n_traj, P, n, n_x)) if keep_model else None
+    A = np.empty((n_traj, N + 1, n_x, n_x)) if keep_model else None
+    Bm = np.empty((n_traj, N + 1, n_x, n_u)) if keep_model else None
+    K = np.empty((n_traj, N + 1, n_u, n_x)) if keep_model else None
+    for b in range(n_traj):
+        rng = _rng(seed, b)
+        Ab = 0.95 * np.eye(n_x) + 0.1 * rng.standard_normal((N + 1, n_x, n_x)) / np.sqrt(n_x)
+        Bb = 0.1 * rng.standard_normal((N + 1, n_x, n_u)) / np.sqrt(n_x)
+        Kb = 0.3 * rng.standard_normal((N + 1, n_u, n_x)) / np.sqrt(n_x)
+        for j in range(N):
+            X = np.eye(n_x)
+            for k in range(j + 1, N + 1):
+                p = k * (k - 1) // 2 + j
+                Phi[b, p, :n_x] = X
+                Phi[b, p, n_x:] = Kb[k] @ X
+                if keep_model:
+                    Phi64[b, p, :n_x] = X
+                    Phi64[b, p, n_x:] = Kb[k] @ X
+                X = (Ab[k] + Bb[k] @ Kb[k]) @ X
+        if keep_model:
+            A[b], Bm[b], K[b] = Ab, Bb, Kb
+    rng = _rng(seed, 10 ** 6)
+    c = (1e-3 * rng.standard_normal((n_traj * N, n_x))).astype(np.float32)
+    r = rng.uniform(1e-4, 1e-2, (n_traj * N, n_x)).astype(np.float32)
+    e = (5e-3 * rng.uniform(0.0, 1.0, n_x)).astype(np.float32)
+    return TubeWorkload(n_traj, N, n_x, n_u, Phi, c, r, e, A, Bm, K, Phi64)
