@@ -1,6 +1,6 @@
 """Benchmark of the certified LEB hot path on B300 (one JSON line on rank 0).
 
-A step is one pass of the whole hot path over one batch of seeded synthetic input, six forms in turn:
+A step is one pass of the whole hot path over one batch of seeded synthetic input, seven forms in turn:
   * plain form (pbh): path-based Hessian bounds (Thm. 1) for the 28-quadrotor spring chain
     (n_x = 168, n_u = 56), 256 trajectories x N = 50 (T = 12800), zonotope tube sets with 2 n_x = 336
     generators, A_k and B_k written;
@@ -16,9 +16,11 @@ A step is one pass of the whole hot path over one batch of seeded synthetic inpu
     against random sampling) measured once at start-up and reported beside it;
   * pbh_sys: PBH for the paper's own 168-state system, 14 3-D quadrotors with the centroid
     spring-damper (256 x 50 timesteps, box sets, A_k and B_k written), with the runtime at the Table I
-    shapes (satellite, one 3-D quadrotor) measured once at start-up and reported beside it.
+    shapes (satellite, one 3-D quadrotor) measured once at start-up and reported beside it;
+  * tube: the step after the LEB, tube centre and width (Eqs. 18b, 20-21) of the 168-state shape over
+    16 trajectories of horizon 25.
 ``value`` = certified timestep-bounds per second of the whole step (pbh + crown + pbh_sys timesteps, all
-at n_x = 168, over the time of all six forms), summed over ranks.
+at n_x = 168, over the time of all seven forms), summed over ranks.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--forms pbh,crown,...]
 For N > 1 it runs under torchrun, one independent replica per GPU (every timestep's bound is independent,
@@ -385,6 +387,7 @@ class ProposerForm(Form):
 
     Algorithmic FLOPs per sample: 2 (392 x 256 + 256 x 256 + 256 x 336) = 503,808."""
     name = "proposer"
+    kernel_label = "proposer forward (prop_gemm_kernel x3 + elementwise)"
 
     def __init__(self, torch, dev, quick=False):
         from paper_2607_01203_b300 import inputs
@@ -621,6 +624,72 @@ class PbhSysForm(Form):
         return (time.perf_counter() - t0) / done, done
 
 
+class TubeForm(Form):
+    """The step after the LEB (Sec. IV-A, Eqs. 18b, 20-21): tube centre and width of the 168-state shape
+    (n_x = 168, n_u = 56) over 16 trajectories of horizon 25 (the paper's coupled-quadrotor horizon),
+    packed responses of a stable LTV loop, Gamma-map centres and radii, diagonal E.
+
+    Bytes per launch: the packed responses read once (16 x 325 x 224 x 168 x 4 = 782.6 MB), c, r
+    (2 x 16 x 25 x 168 x 4), e, and mu, sigma written (2 x 16 x 26 x 224 x 4): 783.9 MB."""
+    name = "tube"
+    kernel_label = "tube_kernel (one launch, timed by CUDA events around the form)"
+
+    def __init__(self, torch, dev, quick=False):
+        from paper_2607_01203_b300 import binding, inputs
+        self.torch, self.binding = torch, binding
+        self.w = inputs.tube(n_traj=2 if quick else 16, N=25, n_x=168, n_u=56, keep_model=False)
+        w = self.w
+        self.T = w.n_traj
+        self.Phi, self.e, self.c, self.r = (torch.as_tensor(a).to(dev) for a in (w.Phi, w.e, w.c, w.r))
+        self.bytes = 4 * (self.Phi.numel() + self.c.numel() + self.r.numel() + self.e.numel()
+                          + 2 * w.n_traj * (w.N + 1) * (w.n_x + w.n_u))
+        self.out = {}
+        self.run()
+        torch.cuda.synchronize()
+        self.desc = f"tube centre/width n_x=168 n_u=56, {w.n_traj} traj x N=25, packed responses {self.bytes / 1e6:.0f} MB"
+
+    def run(self):
+        w = self.w
+        self.binding.tube(self.Phi, self.e, self.c, self.r, w.n_traj, w.N, w.n_x, w.n_u, out=self.out)
+
+    def roofline(self, pk, ms, launches, kernel):
+        achieved = self.bytes / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
+                "peak_src": pk["src"] + " hbm_gbs (STREAM-style copy)", "kernel": kernel,
+                "kernel_ms": round(ms, 4), "launches_per_step": 1, "bytes_per_unit": self.bytes // self.T,
+                "units_per_launch": self.T}
+
+    def e2e(self, steps):
+        torch = self.torch
+        hs = [a.cpu().pin_memory() for a in (self.Phi, self.e, self.c, self.r)]
+        ds = [torch.empty_like(a) for a in (self.Phi, self.e, self.c, self.r)]
+        outs = [torch.empty(self.out[k].shape).pin_memory() for k in ("mu", "sigma")]
+        w = self.w
+
+        def one():
+            for d, h in zip(ds, hs):
+                d.copy_(h, non_blocking=True)
+            mu, sigma, _ = self.binding.tube(ds[0], ds[1], ds[2], ds[3], w.n_traj, w.N, w.n_x, w.n_u, out=self.out)
+            outs[0].copy_(mu, non_blocking=True)
+            outs[1].copy_(sigma, non_blocking=True)
+        ms = timed_loop(torch, one, steps)
+        return ms, sum(h.numel() * 4 for h in hs), sum(o.numel() * 4 for o in outs)
+
+    def oracle_seconds_per_unit(self, budget_s):
+        """The FP64 oracle on whole trajectories of this batch: seconds per trajectory."""
+        from oracle import tube as otube
+        w = self.w
+        t0 = time.perf_counter()
+        done = 0
+        while (time.perf_counter() - t0 < budget_s or done == 0) and done < w.n_traj:
+            b = done
+            sl = slice(b * w.N, (b + 1) * w.N)
+            otube.tube(w.Phi[b], w.N, w.c[sl], w.r[sl], w.e.astype(np.float64))
+            done += 1
+        return (time.perf_counter() - t0) / done, done
+
+
 class Table1Form(Form):
     """PBH at the shapes of Table I on their own (not in the default step; for profiling): the satellite
     (n_x = 7) and one 3-D quadrotor (n_x = 12), 10^6 nominal points each with box sets of half-width 0.1,
@@ -703,6 +772,8 @@ def reference_arm(args):
     wq = inputs.quad_chain(n_traj=4, horizon=50)
     ws = inputs.quad3d(T=4 * 50, n_quads=14, eps=0.05, coupled=True, N=50)
     dyn3 = dynamics3d.Quad3D(14, **ws.params)
+    wt = inputs.tube(n_traj=2, N=25, n_x=168, n_u=56, keep_model=False)
+    from oracle import tube as otube
     dyn = dynamics.QuadChain(28, **wq.params, spring_k=wq.spring_k)
     wm = inputs.tanh_mlp(n_traj=2, N=50)
     g = np.random.default_rng(7).normal(size=(2, 168))
@@ -734,21 +805,24 @@ def reference_arm(args):
             pbh.pbh(dyn3, a, lo, hi)
             dyn3.jacobian(a)
         t4 = time.perf_counter()
+        b = s % wt.n_traj
+        otube.tube(wt.Phi[b], wt.N, wt.c[b * wt.N:(b + 1) * wt.N], wt.r[b * wt.N:(b + 1) * wt.N], wt.e.astype(np.float64))
+        t5 = time.perf_counter()
         if s >= args.warmup:
             # time the oracle would take for one full step of the same workload
             est.append((t1 - t0) / n_pbh * T_pbh + (t2 - t1) / n_crown * T_mlp + (t3 - t2) / n_bwd * T_mlp
-                       + (t4 - t3) / n_sys * T_sys)
+                       + (t4 - t3) / n_sys * T_sys + (t5 - t4) * 16)
     step_s = statistics.mean(est)
     v = (T_pbh + T_mlp + T_sys) / step_s
     cores = torch.get_num_threads()
     sample = (f"per step {n_pbh} PBH chain timesteps and {n_sys} coupled 3-D quadrotor timesteps (1 core), "
-              f"{n_crown} CROWN and {n_bwd} adjoint timesteps (torch, {cores} threads) of the bench workloads, "
-              f"scaled to a full step")
+              f"{n_crown} CROWN and {n_bwd} adjoint timesteps (torch, {cores} threads) and 1 of the 16 tube "
+              f"trajectories (NumPy) of the bench workloads, scaled to a full step")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "pbh 256x50 quad chain (zonotope) + crown 128x50 tanh MLP + adjoint + "
-                                   "pbh_sys 256x50 coupled 3-D quadrotors, FP64 oracle on a bounded sample per step",
+                                   "pbh_sys 256x50 coupled 3-D quadrotors + tube 16x25, FP64 oracle on a bounded sample per step",
                        "parallelism": "host"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -761,7 +835,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--forms", default="pbh,crown,backward,proposer,pbh_grad,pbh_sys")
+    ap.add_argument("--forms", default="pbh,crown,backward,proposer,pbh_grad,pbh_sys,tube")
     ap.add_argument("--quick", action="store_true", help="small batches (smoke runs, not a bench value)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -795,6 +869,8 @@ def main():
             forms.append(PbhGradForm(torch, dev, args.quick))
         elif nm == "pbh_sys":
             forms.append(PbhSysForm(torch, dev, args.quick))
+        elif nm == "tube":
+            forms.append(TubeForm(torch, dev, args.quick))
         elif nm == "table1":
             forms.append(Table1Form(torch, dev, args.quick))
         else:
@@ -855,7 +931,7 @@ def main():
             ms, n, name = f.handle.timing_read(f.which)
             kt[f.name] = (ms / args.steps, n // args.steps, name)
         else:
-            kt[f.name] = (form_ms[f.name], 1, "proposer forward (prop_gemm_kernel x3 + elementwise)")
+            kt[f.name] = (form_ms[f.name], 1, f.kernel_label)
     units = sum(f.units() for f in forms) * world
     value = units / (ms_max * 1e-3)
     out_forms = {}
@@ -872,6 +948,8 @@ def main():
             d["nominal_refinement_table2"] = f.pgd
         if f.name == "pbh_sys":
             d["table1_shapes"] = f.table1
+        if f.name == "tube":
+            d["tube_timesteps_per_s"] = round(f.w.n_traj * f.w.N / (form_ms["tube"] * 1e-3), 1)
         if f.name == "proposer":
             cms = f.certified_ms()
             d.update({"proposal_error_vs_certified": round(f.err, 4), "under_cover_fraction": round(f.under, 4),
@@ -914,7 +992,7 @@ def main():
 
 def cpu_baseline(forms, torch):
     """The oracle as it stands on a bounded sample of each form, scaled to the step's metric."""
-    budget = {"pbh": 6.0, "crown": 6.0, "backward": 8.0, "pbh_sys": 4.0}
+    budget = {"pbh": 6.0, "crown": 6.0, "backward": 8.0, "pbh_sys": 4.0, "tube": 2.0}
     step_s, units, parts = 0.0, 0, []
     for f in forms:
         if f.name not in budget:

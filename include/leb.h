@@ -263,6 +263,23 @@ leb_status leb_bounds_static(leb_handle h, const leb_batch* batch, int T, const 
                              void* stream);
 int leb_bounds_static_max_traj(void);
 
+/* ---- the step after the LEB: tube centre and width (Sec. IV-A, Eqs. 18b, 20-21) --------------------- */
+/* For n_traj trajectories of horizon N (n_x states, n_u inputs) the zonotope of timestep j's disturbance
+ * and linearization error is c_j + Ebar_j E_{2 n_x} with Ebar_j = [E(z_j)  diag(r_j)] (Eq. 18b; c_j, r_j
+ * the Gamma map of the LEB, leb_options gamma_c / gamma_r), and the tube of timestep k is
+ *   h^mu_k    = sum_{j<k} Phi_{k,j} c_j,   h^sigma_k = sum_{j<k} || Phi_{k,j} Ebar_j ||_{1,r}   (Eqs. 20-21).
+ *  Phi: device [n_traj, N (N + 1) / 2, n_x + n_u, n_x], packed: block k (k - 1) / 2 + j (1 <= k <= N,
+ *    0 <= j < k) holds [Phi^x_{k,j}; Phi^u_{k,j}] row-major (the input rows of k = N are used as given).
+ *  e: device diagonal of E(z_j): [n_x] shared (e_per_step = 0) or [n_traj * N, n_x] (e_per_step != 0).
+ *  c, r: device [n_traj * N, n_x] (timestep j of trajectory b at row b N + j).
+ *  mu, sigma: device [n_traj, N + 1, n_x + n_u] written (k = 0: zeros). sigma is rounded up and includes
+ *    the enclosure error of mu, so [mu - sigma, mu + sigma] contains the exact tube box of the FP32 inputs.
+ *    A row whose result is not finite gets mu = 0, sigma = +inf and raises LEB_ASYNC_NONFINITE.
+ * Diagonal E only (the paper's systems). Needs 8 N n_x <= 200 KiB of shared memory, else
+ * LEB_ERR_UNSUPPORTED. Asynchronous on the stream, allocates nothing; *dev_flags is cleared first. */
+leb_status leb_tube(int n_traj, int N, int n_x, int n_u, const float* Phi, const float* e, int e_per_step,
+                    const float* c, const float* r, float* mu, float* sigma, int* dev_flags, void* stream);
+
 /* ---- diagnostics -------------------------------------------------------------------------------- */
 /* Evaluates the library's point enclosures of sin, cos and tanh (the CUDA function value widened by
  * the slack that covers its documented error) at n device inputs x, writing [lo, hi] pairs to the

@@ -14,7 +14,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libleb.so")
 
-LEB_OK = 0
+LEB_OK, LEB_ERR_INVALID_ARG, LEB_ERR_UNSUPPORTED, LEB_ERR_WORKSPACE, LEB_ERR_CUDA = 0, -1, -2, -3, -4
 STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported", -3: "workspace", -4: "CUDA error", -5: "timeout"}
 ASYNC_NONFINITE, ASYNC_TIMEOUT, ASYNC_OVERFLOW = 1, 2, 4
 DYN_QUAD_CHAIN, DYN_MLP, DYN_SATELLITE, DYN_QUAD3D = 0, 1, 2, 3
@@ -59,7 +59,7 @@ EXPORTS = [
     "leb_proposer_set_norm", "leb_proposer_forward", "leb_proposer_train_step", "leb_proposer_workspace_size",
     "leb_proposer_get_layer", "leb_proposer_set_layer", "leb_proposer_get_grad", "leb_selftest_point_enclosures",
     "leb_bounds_static", "leb_bounds_static_max_traj", "leb_proposer_fit_norm", "leb_proposer_set_periodic", "leb_timing", "leb_timing_read", "leb_status_string", "leb_version",
-    "leb_refine_nominal_pgd", "leb_refine_workspace_size", "leb_selftest_tan_sec",
+    "leb_refine_nominal_pgd", "leb_refine_workspace_size", "leb_selftest_tan_sec", "leb_tube",
 ]
 
 
@@ -105,6 +105,7 @@ def lib():
         L.leb_proposer_get_grad.argtypes = [vp, i32, vp, vp, vp]
         L.leb_selftest_point_enclosures.argtypes = [vp, i32, vp, vp, vp, vp]
         L.leb_selftest_tan_sec.argtypes = [vp, i32, vp, vp, vp]
+        L.leb_tube.argtypes = [i32, i32, i32, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp]
         L.leb_bounds_static.argtypes = [vp, C.POINTER(BatchDesc), i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp, vp, vp,
                                         vp]
         L.leb_bounds_static_max_traj.argtypes = []
@@ -339,6 +340,22 @@ def mlp(Ws, bs, act: str, residual: bool = True, prec: str = "fp32") -> Handle:
     bp = (C.c_void_p * len(bn))(*[b.ctypes.data for b in bn])
     spec = DynamicsSpec(DYN_MLP, 0, 0, 0, 0, 0, 0, 0, len(Wn), warr, Wp, bp, ACT[act], int(bool(residual)), PREC[prec])
     return Handle(spec, keep=(Wn, bn, warr, Wp, bp))
+
+
+def tube(Phi, e, c, r, n_traj: int, N: int, n_x: int, n_u: int, out=None):
+    """Tube centre and width after the LEB (leb_tube, Eqs. 18b, 20-21). Phi: [n_traj, N (N + 1) / 2,
+    n_x + n_u, n_x] packed responses; e: [n_x] or [n_traj N, n_x] diagonal of E; c, r: [n_traj N, n_x]
+    Gamma-map centres and radii. Returns (mu, sigma, flags), device tensors [n_traj, N + 1, n_x + n_u]."""
+    dev = Phi.device
+    o = out if out is not None else {}
+    if "mu" not in o:
+        o["mu"] = torch.empty(n_traj, N + 1, n_x + n_u, device=dev)
+        o["sigma"] = torch.empty(n_traj, N + 1, n_x + n_u, device=dev)
+        o["flags"] = torch.zeros(1, device=dev, dtype=torch.int32)
+    per_step = int(e.dim() == 2)
+    check(lib().leb_tube(int(n_traj), int(N), int(n_x), int(n_u), _ptr(Phi), _ptr(e), per_step, _ptr(c), _ptr(r),
+                         _ptr(o["mu"]), _ptr(o["sigma"]), _ptr(o["flags"]), _stream()), "leb_tube")
+    return o["mu"], o["sigma"], o["flags"]
 
 
 def zonotope_map(r_lo, r_hi, pad: float = 0.0):
