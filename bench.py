@@ -61,6 +61,9 @@ DRAM_BYTES_PER_TS_LAUNCH = {
     # pbh_sys_kernel<true>, captured at the bench's own size (12800 timesteps of the 168-state coupled
     # system, profiles/pbh_sys_kernel_coupled_quad3d14_T12800.md)
     "pbh_sys": (39_297_792 + 1_901_738_000) / 12800,
+    # tube_kernel, captured at the bench's own size (16 trajectories: one unit = one trajectory,
+    # profiles/tube_kernel_168x25_16traj.md)
+    "tube": (783_316_480 + 6_126_592) / 16,
 }
 
 
@@ -655,7 +658,7 @@ class TubeForm(Form):
     def roofline(self, pk, ms, launches, kernel):
         achieved = self.bytes / (ms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
+                "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": dram_traffic("tube", self.T),
                 "peak_src": pk["src"] + " hbm_gbs (STREAM-style copy)", "kernel": kernel,
                 "kernel_ms": round(ms, 4), "launches_per_step": 1, "bytes_per_unit": self.bytes // self.T,
                 "units_per_launch": self.T}
