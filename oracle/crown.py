@@ -185,8 +185,21 @@ def _back_substitute(Ws, bs, relaxations, layer: int, upper: bool, c, r):
     return Lam, bias, value
 
 
-def crown(Ws, bs, act: str, lo: torch.Tensor, hi: torch.Tensor):
-    """Thm. 2 over the box [lo, hi]: returns (W_lo, b_lo, W_hi, b_hi, hidden bounds [(l_i, u_i)])."""
+def ibp_layer(W, b, act: str, l_prev, u_prev):
+    """Interval bound propagation through one hidden layer: the activation is monotone, so the previous
+    layer's outputs lie in [act(l), act(u)], and the affine map's range over that box is its centre
+    image plus |W| times its radius."""
+    hl, hh = act_fn(act, l_prev), act_fn(act, u_prev)
+    hc, hr = 0.5 * (hl + hh), 0.5 * (hh - hl)
+    return W @ hc - W.abs() @ hr + b, W @ hc + W.abs() @ hr + b
+
+
+def crown(Ws, bs, act: str, lo: torch.Tensor, hi: torch.Tensor, intermediate: str = "crown"):
+    """Thm. 2 over the box [lo, hi]: returns (W_lo, b_lo, W_hi, b_hi, hidden bounds [(l_i, u_i)]).
+
+    ``intermediate`` selects how the pre-activation bounds of hidden layers 2.. are obtained: "crown"
+    (full back-substitution, the default) or "ibp" (interval bound propagation from the previous layer's
+    bounds, the cheaper and looser variant); the output layer is always back-substituted."""
     c = 0.5 * (lo + hi)
     r = 0.5 * (hi - lo)
     L = len(Ws)
@@ -197,8 +210,11 @@ def crown(Ws, bs, act: str, lo: torch.Tensor, hi: torch.Tensor):
     bounds.append((l1, u1))
     relaxations.append(relax(act, l1, u1))
     for layer in range(1, L - 1):
-        _, _, li = _back_substitute(Ws, bs, relaxations, layer, False, c, r)
-        _, _, ui = _back_substitute(Ws, bs, relaxations, layer, True, c, r)
+        if intermediate == "ibp":
+            li, ui = ibp_layer(Ws[layer], bs[layer], act, *bounds[-1])
+        else:
+            _, _, li = _back_substitute(Ws, bs, relaxations, layer, False, c, r)
+            _, _, ui = _back_substitute(Ws, bs, relaxations, layer, True, c, r)
         bounds.append((li, ui))
         relaxations.append(relax(act, li, ui))
     W_lo, b_lo, _ = _back_substitute(Ws, bs, relaxations, L - 1, False, c, r)
@@ -207,12 +223,12 @@ def crown(Ws, bs, act: str, lo: torch.Tensor, hi: torch.Tensor):
 
 
 def remainder_bounds(Ws, bs, act: str, nominal: torch.Tensor, lo: torch.Tensor, hi: torch.Tensor,
-                     residual: bool = True):
+                     residual: bool = True, intermediate: str = "crown"):
     """Thm. 3 for the dynamics x+ = [x +] MLP([x; u]). Returns (r_lo, r_hi, J_full, crown_parts).
 
     J_full is [A B] of the full dynamics; with ``residual`` both the CROWN slopes and J carry the same
     identity block, which therefore cancels in W - J."""
-    W_lo, b_lo, W_hi, b_hi, bounds = crown(Ws, bs, act, lo, hi)
+    W_lo, b_lo, W_hi, b_hi, bounds = crown(Ws, bs, act, lo, hi, intermediate)
     J = jacobian(Ws, bs, act, nominal)
     f_nom, _ = forward(Ws, bs, act, nominal)
     n_x = J.shape[0]
@@ -237,14 +253,14 @@ def to_t(x) -> torch.Tensor:
     return torch.as_tensor(x, dtype=F64)
 
 
-def box_remainder(Ws, bs, act, x_nom, u_nom, radii, residual=True):
+def box_remainder(Ws, bs, act, x_nom, u_nom, radii, residual=True, intermediate="crown"):
     """One timestep with a box set centred at the nominal: Thm. 3 bounds and [A B]. FP64 numpy out."""
     Ws_t = [to_t(W) for W in Ws]
     bs_t = [to_t(b) for b in bs]
     a = torch.cat([to_t(x_nom), to_t(u_nom)])
     rho = to_t(radii)
     with torch.no_grad():
-        r_lo, r_hi, J, _ = remainder_bounds(Ws_t, bs_t, act, a, a - rho, a + rho, residual)
+        r_lo, r_hi, J, _ = remainder_bounds(Ws_t, bs_t, act, a, a - rho, a + rho, residual, intermediate)
     return r_lo.numpy(), r_hi.numpy(), J.numpy()
 
 

@@ -248,3 +248,60 @@ def test_proposer_bf16_rounding_matches_torch():
     assert abs(l1 - l0) < 5e-2 * abs(l0)
     for a, b in zip(g0, g1):
         assert np.max(np.abs(a - b)) < 5e-2 * np.abs(a).max()
+
+
+def test_ibp_intermediate_single_hidden_layer_equals_crown():
+    """With one hidden layer there is no intermediate layer to bound, so the IBP variant is CROWN itself."""
+    Ws, bs = _net((5, 24, 3), 30)
+    for act in ("relu", "tanh"):
+        a = np.random.default_rng(31).normal(size=5)
+        r = np.full(5, 0.2)
+        c1 = crown.box_remainder(Ws, bs, act, a[:3], a[3:], r, residual=True)
+        c2 = crown.box_remainder(Ws, bs, act, a[:3], a[3:], r, residual=True, intermediate="ibp")
+        assert np.array_equal(c1[0], c2[0]) and np.array_equal(c1[1], c2[1])
+
+
+def test_ibp_layer_is_exact_for_monotone_nets():
+    """Positive diagonal first layer, non-negative second layer, monotone activation: every layer-2
+    pre-activation is increasing in every input, so its range over a box is [z(lo), z(hi)], which IBP
+    must reproduce."""
+    rng = np.random.default_rng(32)
+    W1 = np.diag(rng.uniform(0.5, 2.0, 4))
+    b1 = rng.normal(size=4) * 0.1
+    W2 = rng.uniform(0.0, 1.0, (5, 4))
+    b2 = rng.normal(size=5) * 0.1
+    t = lambda x: torch.tensor(x)
+    for act in ("relu", "tanh"):
+        lo, hi = rng.normal(size=4) - 0.5, None
+        hi = lo + rng.uniform(0.1, 1.0, 4)
+        l1, u1 = W1 @ lo + b1, W1 @ hi + b1
+        l2, u2 = crown.ibp_layer(t(W2), t(b2), act, t(l1), t(u1))
+        f = (lambda z: np.maximum(z, 0)) if act == "relu" else np.tanh
+        assert np.allclose(l2.numpy(), W2 @ f(l1) + b2, rtol=1e-14, atol=1e-15)
+        assert np.allclose(u2.numpy(), W2 @ f(u1) + b2, rtol=1e-14, atol=1e-15)
+
+
+@pytest.mark.parametrize("act", ["relu", "tanh"])
+def test_ibp_intermediate_bounds_and_remainder_are_sound(act):
+    """Sampled pre-activations of every hidden layer lie in the IBP bounds, and the resulting Thm. 3
+    bound contains the sampled true remainder; ReLU: it contains the exact range by enumeration."""
+    rng = np.random.default_rng(33)
+    Ws, bs = _net((6, 16, 16, 16, 4), 34)
+    Wt = [torch.tensor(W) for W in Ws]
+    bt = [torch.tensor(b) for b in bs]
+    a = rng.normal(size=6)
+    lo, hi = a - 0.25, a + 0.25
+    _, _, _, _, bounds = crown.crown(Wt, bt, act, torch.tensor(lo), torch.tensor(hi), intermediate="ibp")
+    P = sampling.box_points(lo, hi, 20000, rng)
+    h = torch.tensor(P)
+    for i, (l, u) in enumerate(bounds):
+        z = h @ Wt[i].T + bt[i]
+        assert torch.all(z >= l - 1e-12) and torch.all(z <= u + 1e-12)
+        h = crown.act_fn(act, z)
+    r_lo, r_hi, J, _ = crown.remainder_bounds(Wt, bt, act, torch.tensor(a), torch.tensor(lo), torch.tensor(hi),
+                                              residual=False, intermediate="ibp")
+    R = sampling.remainders(sampling.mlp_f_batch(Ws, bs, act, residual=False), a, J.numpy(), P)
+    assert np.all(R.min(0) >= r_lo.numpy() - 1e-12) and np.all(R.max(0) <= r_hi.numpy() + 1e-12)
+    if act == "relu":
+        el, eh, _ = exact.relu_exact_range(Ws, bs, a, lo, hi, residual=False)
+        assert np.all(r_lo.numpy() <= el + 1e-12) and np.all(r_hi.numpy() >= eh - 1e-12)
