@@ -271,7 +271,22 @@ class CrownForm(Form):
         self.r = torch.as_tensor(w.radii).to(dev)
         self.out = self.handle.bounds(self.x, self.u, radii=self.r)
         torch.cuda.synchronize()
+        self.ibp = self._ibp_variant(torch, binding)
         self.desc = f"residual tanh MLP 224-512-512-512-168, {self.T // 50} traj x N=50, box sets, FP16 TC"
+
+    def _ibp_variant(self, torch, binding):
+        """Once at start-up (untimed in the step): the IBP-intermediate variant on the same batch, its
+        time per call and its width relative to full CROWN."""
+        w = self.w
+        h = binding.mlp(w.Ws, w.bs, w.act, w.residual, "fp16", intermediate="ibp")
+        o = h.bounds(self.x, self.u, radii=self.r)
+        torch.cuda.synchronize()
+        ms = timed_loop(torch, lambda: h.bounds(self.x, self.u, radii=self.r, out=o), 3)
+        ms_crown = timed_loop(torch, self.run, 3)
+        wi = float((o["r_hi"] - o["r_lo"]).mean())
+        wc = float((self.out["r_hi"] - self.out["r_lo"]).mean())
+        return {"ms_per_call": round(ms, 3), "crown_ms_per_call": round(ms_crown, 3),
+                "mean_width": wi, "crown_mean_width": wc, "width_ratio": round(wi / wc, 3)}
 
     def run(self):
         self.handle.bounds(self.x, self.u, radii=self.r, out=self.out)
@@ -951,6 +966,8 @@ def main():
             d["nominal_refinement_table2"] = f.pgd
         if f.name == "pbh_sys":
             d["table1_shapes"] = f.table1
+        if f.name == "crown":
+            d["ibp_intermediate_variant"] = f.ibp
         if f.name == "tube":
             d["tube_timesteps_per_s"] = round(f.w.n_traj * f.w.N / (form_ms["tube"] * 1e-3), 1)
         if f.name == "proposer":

@@ -64,6 +64,9 @@ typedef enum { LEB_ACT_RELU = 0, LEB_ACT_TANH = 1 } leb_act;
    tensor cores with FP32 accumulation and a rigorous rounding inflation */
 typedef enum { LEB_PREC_FP32 = 0, LEB_PREC_FP16 = 1, LEB_PREC_BF16 = 2 } leb_prec;
 typedef enum { LEB_SET_BOX = 0, LEB_SET_ZONO = 1 } leb_set_kind;
+/* bounds of the MLP's hidden layers 2..: CROWN back-substitution (Thm. 2 for every layer) or interval
+   bound propagation (the cheaper, looser variant); the output layer is always back-substituted */
+typedef enum { LEB_INTERMEDIATE_CROWN = 0, LEB_INTERMEDIATE_IBP = 1 } leb_intermediate;
 
 /* Dynamics specification (read during leb_create only; weights are copied into the handle).
  *  LEB_DYN_QUAD_CHAIN: n_quads planar quadrotors of App. A ("Planar Quadrotor") integrated by forward
@@ -100,6 +103,7 @@ typedef struct {
   leb_prec prec;
   double inertia3[3];            /* LEB_DYN_SATELLITE / LEB_DYN_QUAD3D: principal moments of inertia */
   double coup_alpha, coup_gamma; /* LEB_DYN_QUAD3D: centroid coupling gains (0 = independent)        */
+  leb_intermediate intermediate; /* LEB_DYN_MLP: hidden-layer bounds (leb_bounds_backward needs CROWN) */
 } leb_dynamics_spec;
 
 /* Tube set of every timestep (device pointers, row-major over timesteps).

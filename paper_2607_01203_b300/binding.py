@@ -34,7 +34,8 @@ class DynamicsSpec(C.Structure):
                 ("inertia", C.c_double), ("arm", C.c_double), ("g", C.c_double), ("spring_k", C.c_double),
                 ("n_layers", C.c_int), ("widths", C.POINTER(C.c_int)), ("W", C.POINTER(C.c_void_p)),
                 ("b", C.POINTER(C.c_void_p)), ("act", C.c_int), ("residual", C.c_int), ("prec", C.c_int),
-                ("inertia3", C.c_double * 3), ("coup_alpha", C.c_double), ("coup_gamma", C.c_double)]
+                ("inertia3", C.c_double * 3), ("coup_alpha", C.c_double), ("coup_gamma", C.c_double),
+                ("intermediate", C.c_int)]
 
 
 class SetDesc(C.Structure):
@@ -330,7 +331,10 @@ def quad3d(n_quads: int = 1, dt: float = 0.05, mass: float = 1.0, g: float = 9.8
     return Handle(spec)
 
 
-def mlp(Ws, bs, act: str, residual: bool = True, prec: str = "fp32") -> Handle:
+INTERMEDIATE = {"crown": 0, "ibp": 1}
+
+
+def mlp(Ws, bs, act: str, residual: bool = True, prec: str = "fp32", intermediate: str = "crown") -> Handle:
     import numpy as np
     Wn = [np.ascontiguousarray(np.asarray(W, np.float32)) for W in Ws]
     bn = [np.ascontiguousarray(np.asarray(b, np.float32)) for b in bs]
@@ -339,6 +343,7 @@ def mlp(Ws, bs, act: str, residual: bool = True, prec: str = "fp32") -> Handle:
     Wp = (C.c_void_p * len(Wn))(*[W.ctypes.data for W in Wn])
     bp = (C.c_void_p * len(bn))(*[b.ctypes.data for b in bn])
     spec = DynamicsSpec(DYN_MLP, 0, 0, 0, 0, 0, 0, 0, len(Wn), warr, Wp, bp, ACT[act], int(bool(residual)), PREC[prec])
+    spec.intermediate = INTERMEDIATE[intermediate]
     return Handle(spec, keep=(Wn, bn, warr, Wp, bp))
 
 

@@ -98,6 +98,7 @@ struct MlpModel {
   int act = 0;
   int residual = 0;
   int prec = 0;
+  int ibp = 0;                    // hidden-layer bounds by interval bound propagation instead of CROWN
   // device copies
   float* W[kMaxLayers] = {};      // [out, in] FP32
   float* WT[kMaxLayers] = {};     // [in, out] FP32 (transposed, for K-major operand tiles)

@@ -212,9 +212,14 @@ leb_status leb_create(const leb_dynamics_spec* spec, leb_handle* out) {
     c->n_u = m.widths[0] - c->n_x;
     if (spec->residual && c->n_u < 0) { delete c; return LEB_ERR_INVALID_ARG; }
     if (c->n_u < 0) { delete c; return LEB_ERR_INVALID_ARG; }
+    if (spec->intermediate != LEB_INTERMEDIATE_CROWN && spec->intermediate != LEB_INTERMEDIATE_IBP) {
+      delete c;
+      return LEB_ERR_INVALID_ARG;
+    }
     m.act = spec->act;
     m.residual = spec->residual;
     m.prec = spec->prec;
+    m.ibp = spec->intermediate == LEB_INTERMEDIATE_IBP;
     // device copies of the weights
     for (int i = 0; i < m.L; ++i) {
       const size_t nw = (size_t)m.widths[i + 1] * m.widths[i], nb = m.widths[i + 1];
@@ -355,7 +360,7 @@ leb_status leb_bounds_backward(leb_handle h, int T, const float* x_nom, const fl
     if (cudaMemsetAsync(dev_flags, 0, sizeof(int), s) != cudaSuccess) return LEB_ERR_CUDA;
     return pbh_bounds_backward(*h, T, x_nom, u_nom, set->radii, g_rlo, g_rhi, g_x, g_u, g_radii, dev_flags, s);
   }
-  if (h->kind != LEB_DYN_MLP) return LEB_ERR_UNSUPPORTED;
+  if (h->kind != LEB_DYN_MLP || h->mlp.ibp) return LEB_ERR_UNSUPPORTED;   // the adjoint differentiates CROWN
   MlpWs lay;
   const size_t need = kWsHeader + mlp_workspace_floats(*h, T, &lay) * sizeof(float);
   if (ws_bytes < need) return LEB_ERR_WORKSPACE;
@@ -478,7 +483,8 @@ leb_status leb_plan_string(leb_handle h, char* buf, size_t buf_len) {
   } else if (h->kind == LEB_DYN_QUAD3D) {
     os << "kernel=pbh_quad3d;quads=" << h->nq << ";coupled=" << h->sk.coupled;
   } else {
-    os << "kernel=mlp;prec=" << h->mlp.prec << ";layers=" << h->mlp.L;
+    os << "kernel=mlp;prec=" << h->mlp.prec << ";layers=" << h->mlp.L << ";intermediate="
+       << (h->mlp.ibp ? "ibp" : "crown");
   }
   if (!h->plan_note.empty()) os << ";" << h->plan_note;
   std::string s = os.str();

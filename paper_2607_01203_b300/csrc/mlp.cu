@@ -375,6 +375,93 @@ struct TcWeights {
   float c1, v1scale, usub, gam;
 };
 
+// Interval bound propagation through hidden layer i (the IBP-intermediate variant of CROWN): the
+// previous layer's pre-activations lie in [l, u] (ld_in, over the set), the monotone activation maps them
+// into [act(l), act(u)] (enclosed), and the range of z = W h + b over that box is, per output c,
+//   lo = b + sum_k min(W_ck h_lo_k, W_ck h_hi_k),   hi = b + sum_k max(...),
+// i.e. the endpoint chosen by the sign of W_ck, every product and partial sum rounded outward (a rounded
+// down FMA accumulates a lower bound of the exact sum). A CTA computes a 64 (timesteps) x 64 (neurons)
+// tile, 4 x 4 per thread, over K chunks staged in shared memory.
+// It also states how far the FP32 bounds can lie from the exact IBP bounds (bslack: the accumulated
+// rounding of K + 1 terms, gam = gamma_{K+1}, times sum_k |W_ck| max(|h_lo_k|, |h_hi_k|) + |b_c|).
+__global__ void __launch_bounds__(256) mlp_ibp_kernel(int T, int K, int N, int act, const float* W, const float* b,
+                                                     const float* l_in, const float* u_in, int ld_in, float* lo,
+                                                     float* hi, float* bslack, float gam, int ld_out) {
+  __shared__ __align__(16) float s_hl[kKC][kNomBT + 4];
+  __shared__ __align__(16) float s_hh[kKC][kNomBT + 4];
+  __shared__ __align__(16) float s_w[kKC][kNomBN + 4];
+  const int t0 = blockIdx.x * kNomBT, c0 = blockIdx.y * kNomBN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // thread owns t = t0 + 4ty.., c = c0 + 4tx..
+  float alo[4][4], ahi[4][4], amag[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = c0 + 4 * tx + j;
+    const float bc = c < N ? b[c] : 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      alo[i][j] = ahi[i][j] = bc;
+      amag[i][j] = fabsf(bc);
+    }
+  }
+  for (int k0 = 0; k0 < K; k0 += kKC) {
+    for (int e = threadIdx.x; e < kKC * kNomBT; e += 256) {
+      const int tt = e / kKC, kk = e - tt * kKC;
+      const int t = t0 + tt, k = k0 + kk;
+      float hl = 0.f, hh = 0.f;
+      if (t < T && k < K) {
+        const long long o = (long long)t * ld_in + k;
+        const float l = l_in[o], u = u_in[o];
+        if (act == kActTanh) {
+          hl = point_tanh(l).lo;
+          hh = point_tanh(u).hi;
+        } else {
+          hl = fmaxf(l, 0.f);
+          hh = fmaxf(u, 0.f);
+        }
+      }
+      s_hl[kk][tt] = hl;
+      s_hh[kk][tt] = hh;
+    }
+    for (int e = threadIdx.x; e < kKC * kNomBN; e += 256) {
+      const int cc = e / kKC, kk = e - cc * kKC;
+      const int c = c0 + cc, k = k0 + kk;
+      s_w[kk][cc] = (c < N && k < K) ? W[(long long)c * K + k] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kKC; ++kk) {
+      const float4 w4 = *reinterpret_cast<const float4*>(&s_w[kk][4 * tx]);
+      const float4 l4 = *reinterpret_cast<const float4*>(&s_hl[kk][4 * ty]);
+      const float4 h4 = *reinterpret_cast<const float4*>(&s_hh[kk][4 * ty]);
+      const float wv[4] = {w4.x, w4.y, w4.z, w4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w}, hv[4] = {h4.x, h4.y, h4.z, h4.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bool pos = wv[j] >= 0.f;
+          alo[i][j] = __fmaf_rd(wv[j], pos ? lv[i] : hv[i], alo[i][j]);
+          ahi[i][j] = __fmaf_ru(wv[j], pos ? hv[i] : lv[i], ahi[i][j]);
+          amag[i][j] = __fmaf_ru(fabsf(wv[j]), fmaxf(fabsf(lv[i]), fabsf(hv[i])), amag[i][j]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int t = t0 + 4 * ty + i;
+    if (t >= T) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + 4 * tx + j;
+      if (c < N) {
+        lo[(long long)t * ld_out + c] = alo[i][j];
+        hi[(long long)t * ld_out + c] = ahi[i][j];
+        bslack[(long long)t * ld_out + c] = __fmul_ru(gam, amag[i][j]);
+      }
+    }
+  }
+}
+
 __global__ void mlp_relax_kernel(int T, int width, int ld, int off, int act, const float* lo, const float* hi,
                                  const float* zhat, const float* zrad, const float* bslack, float* sL, float* tL,
                                  float* sU, float* tU, float* D, float* abar, float* loss, const float* v1,
@@ -769,10 +856,19 @@ leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_
     }
     mlp_nominal_kernel<<<grid, 256, 0, s>>>(na);
     if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
-    // bounds of hidden layer i by back-substitution, then its relaxation
-    leb_status st = run_chain(c, T, i, L, ws, nullptr, nullptr, nullptr, nullptr, nullptr, s, bad, opt, flags, simt,
-                              tight);
-    if (st != LEB_OK) return st;
+    if (m.ibp) {
+      // bounds of hidden layer i by interval bound propagation from layer i-1's bounds
+      mlp_ibp_kernel<<<grid, 256, 0, s>>>(T, na.K, na.N, m.act, m.W[i], m.b[i], ws + L.lo + L.hoff[i - 1],
+                                          ws + L.hi + L.hoff[i - 1], L.H, ws + L.lo + L.hoff[i],
+                                          ws + L.hi + L.hoff[i], ws + L.bslack + L.hoff[i],
+                                          gamma_n(na.K + 1), L.H);
+      if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
+    } else {
+      // bounds of hidden layer i by back-substitution
+      leb_status st = run_chain(c, T, i, L, ws, nullptr, nullptr, nullptr, nullptr, nullptr, s, bad, opt, flags,
+                                simt, tight);
+      if (st != LEB_OK) return st;
+    }
     const int blocks = (int)std::min<long long>(((long long)T * na.N + 255) / 256, 148LL * 32);
     mlp_relax_kernel<<<blocks, 256, 0, s>>>(T, na.N, L.H, L.hoff[i], m.act, ws + L.lo, ws + L.hi, ws + L.zhat,
                                             ws + L.zrad, ws + L.bslack, ws + L.sL, ws + L.tL, ws + L.sU, ws + L.tU,
