@@ -118,3 +118,30 @@ def pbh_workload_row(dyn, nominal, radii=None, G=None, center=None):
     lo, hi = box_from_set(nominal, radii=radii, G=G, center=center)
     R_lo, R_hi = pbh(dyn, nominal, lo, hi)
     return R_lo, R_hi, dyn.jacobian(nominal), lo, hi
+
+
+def split_pieces(nominal: np.ndarray, lo: np.ndarray, hi: np.ndarray, dims):
+    """Input-domain partitioning (Sec. III-D): the box cut at the nominal along each coordinate of
+    ``dims`` into its lower part [lo_j, a_j] and upper part [a_j, hi_j]; 2^len(dims) pieces, each still
+    containing the nominal (Thm. 1). Yields (lo_p, hi_p) in the order of the bits of p (bit i = upper part
+    of dims[i])."""
+    a = np.asarray(nominal, np.float64)
+    for p in range(1 << len(dims)):
+        lp, hp = np.array(lo, np.float64), np.array(hi, np.float64)
+        for i, j in enumerate(dims):
+            if (p >> i) & 1:
+                lp[j] = a[j]
+            else:
+                hp[j] = a[j]
+        yield lp, hp
+
+
+def pbh_partitioned(dyn, nominal, lo, hi, dims):
+    """Thm. 1 on every piece of the partition, and the componentwise hull of the pieces' bounds: a bound
+    of the remainder over the whole box (every point lies in some piece)."""
+    R_lo, R_hi = None, None
+    for lp, hp in split_pieces(nominal, lo, hi, dims):
+        l, h = pbh(dyn, nominal, lp, hp)
+        R_lo = l if R_lo is None else np.minimum(R_lo, l)
+        R_hi = h if R_hi is None else np.maximum(R_hi, h)
+    return R_lo, R_hi

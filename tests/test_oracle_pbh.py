@@ -185,3 +185,39 @@ def test_nominal_outside_set_is_hulled():
 def test_gamma_map():
     c, rad = pbh.gamma_map(np.array([-1.0, 0.0]), np.array([3.0, 0.0]), pad=1e-6)
     assert c.tolist() == [1.0, 0.0] and rad.tolist() == [2.0 + 1e-6, 1e-6]
+
+
+def test_partitioned_pbh_is_inside_plain_and_contains_the_exact_range():
+    """Input-domain partitioning at the nominal: every piece's Thm. 1 bound is an interval extension over
+    a subset of the box, so the hull of the pieces lies inside the plain bound (inclusion monotonicity),
+    and it still contains the exact range (1-D analysis of the planar quadrotor)."""
+    from oracle import exact
+    w = inputs.planar_quad()
+    dyn = dynamics.QuadChain(1, **w.params)
+    gain = []
+    for t in range(w.T):
+        a = w.nominal()[t].astype(np.float64)
+        lo, hi = pbh.box_from_set(a, radii=w.radii[t])
+        P = pbh.pbh(dyn, a, lo, hi)
+        S = pbh.pbh_partitioned(dyn, a, lo, hi, dims=[2, 6, 7])
+        assert np.all(S[0] >= P[0] - 1e-15) and np.all(S[1] <= P[1] + 1e-15)
+        el, eh = exact.quad_exact_range(dyn, a, lo, hi)
+        assert np.all(S[0] <= el + 1e-12) and np.all(S[1] >= eh - 1e-12)
+        gain.append((S[1] - S[0]).sum() / (P[1] - P[0]).sum())
+    # the pieces keep the nominal, so every |Delta_j| keeps its range: the gain is small (0.998 here)
+    assert np.mean(gain) <= 1.0
+
+
+def test_partition_pieces_cover_the_box():
+    rng = np.random.default_rng(80)
+    a = rng.normal(size=5)
+    lo, hi = a - rng.uniform(0.1, 1.0, 5), a + rng.uniform(0.1, 1.0, 5)
+    pieces = list(pbh.split_pieces(a, lo, hi, [0, 3]))
+    assert len(pieces) == 4
+    for lp, hp in pieces:   # every piece contains the nominal and lies in the box
+        assert np.all(lp <= a) and np.all(a <= hp) and np.all(lp >= lo) and np.all(hp <= hi)
+    X = lo + rng.uniform(0, 1, (1000, 5)) * (hi - lo)
+    inside = np.zeros(len(X), bool)
+    for lp, hp in pieces:
+        inside |= np.all((X >= lp) & (X <= hp), axis=1)
+    assert inside.all()
