@@ -171,6 +171,19 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
 leb_status leb_bounds_backward(leb_handle h, int T, const float* x_nom, const float* u_nom, const leb_set* set,
                                const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_radii,
                                void* workspace, size_t ws_bytes, int* dev_flags, void* stream);
+/* The same adjoint from the forward pass's saved state: the workspace must hold the state of the last
+ * leb_bounds call on this handle with the same T, x_nom, u_nom and set (box, centred at the nominal,
+ * no leb_batch), with no other call on that workspace in between. FP32 MLP handles skip the recompute
+ * of the hidden-layer bounds (the forward computed exactly the bounds the adjoint differentiates);
+ * reduced-precision MLP handles return LEB_ERR_UNSUPPORTED (their forward bounds carry the rounding
+ * inflation, 40-80 % of the width, whose lines would move the gradient by 1-8 %; leb_bounds_backward
+ * recomputes the bounds without it); other kinds keep no state and behave as leb_bounds_backward. The
+ * library cannot check the contract: a workspace that does not hold that state gives a wrong gradient
+ * (no fault). */
+leb_status leb_bounds_backward_saved(leb_handle h, int T, const float* x_nom, const float* u_nom,
+                                     const leb_set* set, const float* g_rlo, const float* g_rhi, float* g_x,
+                                     float* g_u, float* g_radii, void* workspace, size_t ws_bytes, int* dev_flags,
+                                     void* stream);
 
 /* ---- nominal refinement by projected gradient descent (Sec. IV, Table II) ------------------------ */
 /* Minimises, per timestep, the summed width sum_l (r_hi - r_lo) of the Thm. 1 bound over nominal points in

@@ -60,7 +60,7 @@ EXPORTS = [
     "leb_proposer_set_norm", "leb_proposer_forward", "leb_proposer_train_step", "leb_proposer_workspace_size",
     "leb_proposer_get_layer", "leb_proposer_set_layer", "leb_proposer_get_grad", "leb_selftest_point_enclosures",
     "leb_bounds_static", "leb_bounds_static_max_traj", "leb_proposer_fit_norm", "leb_proposer_set_periodic", "leb_timing", "leb_timing_read", "leb_status_string", "leb_version",
-    "leb_refine_nominal_pgd", "leb_refine_workspace_size", "leb_selftest_tan_sec", "leb_tube",
+    "leb_refine_nominal_pgd", "leb_refine_workspace_size", "leb_selftest_tan_sec", "leb_tube", "leb_bounds_backward_saved",
 ]
 
 
@@ -86,6 +86,7 @@ def lib():
         L.leb_bounds.argtypes = [vp, C.POINTER(BatchDesc), i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp, vp,
                                  C.POINTER(Options), vp, sz, vp, vp]
         L.leb_bounds_backward.argtypes = [vp, i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp, vp, vp, vp, sz, vp, vp]
+        L.leb_bounds_backward_saved.argtypes = L.leb_bounds_backward.argtypes
         L.leb_zonotope_map.argtypes = [vp, vp, C.c_longlong, C.c_float, vp, vp, vp]
         L.leb_autotune.argtypes = [vp, i32, i32, i32, C.c_char_p, vp, sz, vp]
         L.leb_plan_string.argtypes = [vp, C.c_char_p, sz]
@@ -272,7 +273,9 @@ class Handle:
                 o["B"] = o["B"].view(T, self.n_x, self.n_u)
         return o
 
-    def bounds_backward(self, x_nom, u_nom, radii, g_rlo, g_rhi):
+    def bounds_backward(self, x_nom, u_nom, radii, g_rlo, g_rhi, saved: bool = False):
+        """dL/d(x~, u~, radii) (leb_bounds_backward). saved: reuse the state the last ``bounds`` call of
+        this handle left in its workspace (same inputs, box set; leb_bounds_backward_saved)."""
         dev = x_nom.device
         T = int(x_nom.shape[0])
         f32 = dict(device=dev, dtype=torch.float32)
@@ -282,9 +285,9 @@ class Handle:
         flags = torch.zeros(1, device=dev, dtype=torch.int32)
         sd = self.set_desc(radii=radii)
         ws = self.workspace(T, dev)
-        check(lib().leb_bounds_backward(self.h, T, _ptr(x_nom), _ptr(u_nom), C.byref(sd), _ptr(g_rlo.contiguous()),
-                                        _ptr(g_rhi.contiguous()), _ptr(g_x), _ptr(g_u), _ptr(g_r), _ptr(ws),
-                                        ws.numel(), _ptr(flags), _stream()), "leb_bounds_backward")
+        fn = lib().leb_bounds_backward_saved if saved else lib().leb_bounds_backward
+        check(fn(self.h, T, _ptr(x_nom), _ptr(u_nom), C.byref(sd), _ptr(g_rlo.contiguous()), _ptr(g_rhi.contiguous()),
+                 _ptr(g_x), _ptr(g_u), _ptr(g_r), _ptr(ws), ws.numel(), _ptr(flags), _stream()), "leb_bounds_backward")
         return g_x, g_u, g_r, flags
 
     def refine_nominal_pgd(self, x0, u0, radii, eps: float, lr: float, steps: int):

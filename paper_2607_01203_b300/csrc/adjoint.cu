@@ -445,7 +445,7 @@ static leb_status launch_chain_bwd(const Ctx& c, int T, int target, const MlpWs&
 
 leb_status mlp_bounds_backward(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set,
                                const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_rad, void* ws_base,
-                               int* flags, cudaStream_t s) {
+                               int* flags, cudaStream_t s, bool saved) {
   const MlpModel& m = c.mlp;
   // reduced-precision handles with a tensor-core adjoint: chains on the tensor cores, and the hidden
   // bounds recomputed by the tensor-core chains without their rounding inflation, i.e. the algorithm's
@@ -454,9 +454,14 @@ leb_status mlp_bounds_backward(Ctx& c, int T, const float* x_nom, const float* u
   const bool tc = m.adj != nullptr;
   int stot = 0;
   if (!tc && bwd_chain_smem(c, m.L - 1, &stot) > 227 * 1024) return LEB_ERR_UNSUPPORTED;
-  // 1. forward recompute (every hidden layer's bounds and lines)
-  leb_status st = mlp_forward_hidden(c, T, x_nom, u_nom, set, ws_base, flags, s, !tc, nullptr, tc);
-  if (st != LEB_OK) return st;
+  // 1. forward recompute (every hidden layer's bounds and lines), unless the workspace still holds the
+  //    state of the forward call on the same inputs (saved): then its lines are those of the bounds it
+  //    returned, inflation included
+  leb_status st = LEB_OK;
+  if (!saved) {
+    st = mlp_forward_hidden(c, T, x_nom, u_nom, set, ws_base, flags, s, !tc, nullptr, tc);
+    if (st != LEB_OK) return st;
+  }
   MlpWs L;
   mlp_workspace_floats(c, T, &L);
   float* ws = (float*)((char*)ws_base + 256);

@@ -185,9 +185,10 @@ cudaError_t launch_zonotope_map(const float* lo, const float* hi, long long coun
 size_t mlp_workspace_floats(const Ctx& c, int T, MlpWs* layout);
 leb_status mlp_bounds(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set, float* r_lo,
                       float* r_hi, float* A, float* B, const leb_options* opt, void* ws, int* flags, cudaStream_t s);
+// saved: the workspace holds the state of the forward call on the same inputs (skip its recompute)
 leb_status mlp_bounds_backward(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set,
                                const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_rad,
-                               void* ws, int* flags, cudaStream_t s);
+                               void* ws, int* flags, cudaStream_t s, bool saved = false);
 leb_status mlp_prepare(Ctx& c);
 void mlp_release(Ctx& c);
 size_t simt_chain_smem(int maxw);

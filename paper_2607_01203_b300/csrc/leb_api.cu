@@ -346,9 +346,9 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
   return mlp_bounds(*h, T, x_nom, u_nom, set, r_lo, r_hi, A, B, opt, workspace, dev_flags, s);
 }
 
-leb_status leb_bounds_backward(leb_handle h, int T, const float* x_nom, const float* u_nom, const leb_set* set,
-                               const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_radii,
-                               void* workspace, size_t ws_bytes, int* dev_flags, void* stream) {
+static leb_status bounds_backward(leb_handle h, int T, const float* x_nom, const float* u_nom, const leb_set* set,
+                                  const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_radii,
+                                  void* workspace, size_t ws_bytes, int* dev_flags, void* stream, bool saved) {
   if (!h || !set || T < 0 || !dev_flags) return LEB_ERR_INVALID_ARG;
   h->timer.phase = 1;
   if (set->kind != LEB_SET_BOX || set->center) return LEB_ERR_UNSUPPORTED;
@@ -361,13 +361,29 @@ leb_status leb_bounds_backward(leb_handle h, int T, const float* x_nom, const fl
     return pbh_bounds_backward(*h, T, x_nom, u_nom, set->radii, g_rlo, g_rhi, g_x, g_u, g_radii, dev_flags, s);
   }
   if (h->kind != LEB_DYN_MLP || h->mlp.ibp) return LEB_ERR_UNSUPPORTED;   // the adjoint differentiates CROWN
+  if (saved && h->mlp.prec != LEB_PREC_FP32) return LEB_ERR_UNSUPPORTED;  // forward bounds carry inflation
   MlpWs lay;
   const size_t need = kWsHeader + mlp_workspace_floats(*h, T, &lay) * sizeof(float);
   if (ws_bytes < need) return LEB_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(dev_flags, 0, sizeof(int), s) != cudaSuccess) return LEB_ERR_CUDA;
   if (T == 0) return LEB_OK;
-  return mlp_bounds_backward(*h, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, workspace, dev_flags, s);
+  return mlp_bounds_backward(*h, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, workspace, dev_flags, s,
+                             saved);
+}
+
+leb_status leb_bounds_backward(leb_handle h, int T, const float* x_nom, const float* u_nom, const leb_set* set,
+                               const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_radii,
+                               void* workspace, size_t ws_bytes, int* dev_flags, void* stream) {
+  return bounds_backward(h, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, workspace, ws_bytes, dev_flags,
+                         stream, false);
+}
+
+leb_status leb_bounds_backward_saved(leb_handle h, int T, const float* x_nom, const float* u_nom, const leb_set* set,
+                                     const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_radii,
+                                     void* workspace, size_t ws_bytes, int* dev_flags, void* stream) {
+  return bounds_backward(h, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, workspace, ws_bytes, dev_flags,
+                         stream, true);
 }
 
 // ---- nominal refinement (projected gradient descent on the PBH width) ----------------------------

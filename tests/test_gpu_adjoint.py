@@ -114,3 +114,32 @@ def test_tensor_core_adjoint_matches_cuda_core_adjoint():
     err = np.abs(got - ref) / (scale + np.abs(ref))
     print(f"tensor-core vs CUDA-core adjoint: worst {err.max():.2e}, mean {err.mean():.2e}")
     assert err.max() <= 1e-2 and err.mean() <= 1e-3
+
+
+def test_adjoint_from_saved_forward_state():
+    """leb_bounds_backward_saved right after leb_bounds on the same inputs (FP32 handle): the forward left
+    exactly the bounds the adjoint differentiates, so the gradient equals the recomputing adjoint (up to
+    the order of its atomic sums) and matches the FP64 oracle; reduced-precision handles refuse."""
+    w = inputs.tanh_mlp(n_traj=2, N=50)
+    rows = [0, 7, 33, 60, 99]
+    h = binding.mlp(w.Ws, w.bs, w.act, w.residual, "fp32")
+    rng = np.random.default_rng(6)
+    g_lo = rng.normal(size=(len(rows), w.n_x)).astype(np.float32)
+    g_hi = rng.normal(size=(len(rows), w.n_x)).astype(np.float32)
+    x, u, r = _t(w.x_nom[rows]), _t(w.u_nom[rows]), _t(w.radii[rows])
+    recompute = torch.cat(h.bounds_backward(x, u, r, _t(g_lo), _t(g_hi))[:3], 1).cpu().numpy()
+    h.bounds(x, u, radii=r)
+    gx, gu, gr, fl = h.bounds_backward(x, u, r, _t(g_lo), _t(g_hi), saved=True)
+    torch.cuda.synchronize()
+    assert int(fl.item()) == 0
+    got = torch.cat([gx, gu, gr], 1).cpu().numpy()
+    for i, t in enumerate(rows):
+        ref = np.concatenate(crown.box_remainder_vjp(w.Ws, w.bs, w.act, w.x_nom[t], w.u_nom[t], w.radii[t], g_lo[i],
+                                                     g_hi[i], w.residual))
+        assert np.all(np.abs(got[i] - ref) <= 5e-3 * (np.abs(ref).max() + np.abs(ref))), t
+    d = np.abs(got - recompute) / (np.abs(recompute).max(axis=1, keepdims=True) + np.abs(recompute))
+    assert d.max() <= 1e-5
+    h16 = binding.mlp(w.Ws, w.bs, w.act, w.residual, "fp16")
+    h16.bounds(x, u, radii=r)
+    with pytest.raises(binding.LebError):
+        h16.bounds_backward(x, u, r, _t(g_lo), _t(g_hi), saved=True)
