@@ -154,11 +154,13 @@ def relax(act: str, l: torch.Tensor, u: torch.Tensor):
 # ------------------------------------------------------------------------------------------------
 # CROWN back-substitution (Thm. 2)
 # ------------------------------------------------------------------------------------------------
-def _back_substitute(Ws, bs, relaxations, layer: int, upper: bool, c, r):
-    """Affine bound of the pre-activation of ``layer`` (0-based index into Ws) over the box (c, r).
+def _back_substitute(Ws, bs, relaxations, layer: int, upper: bool, c, r, G=None):
+    """Affine bound of the pre-activation of ``layer`` (0-based index into Ws) over the box (c, r), or
+    over the zonotope c + G xi, |xi|_inf <= 1, when G is given.
 
     Returns (Lambda, bias, value): Lambda alpha + bias bounds the layer from below (or above), and
-    value is its minimum (or maximum) over the box."""
+    value is its minimum (or maximum) over the set: Lambda c -+ |Lambda| r over the box,
+    Lambda c -+ ||Lambda G||_{1,r} over the zonotope."""
     Lam = Ws[layer].clone()
     bias = bs[layer].clone()
     for k in range(layer - 1, -1, -1):
@@ -178,10 +180,8 @@ def _back_substitute(Ws, bs, relaxations, layer: int, upper: bool, c, r):
         LamS = Lam * s_sel
         bias = bias + LamS @ bs[k]
         Lam = LamS @ Ws[k]
-    if upper:
-        value = Lam @ c + Lam.abs() @ r + bias
-    else:
-        value = Lam @ c - Lam.abs() @ r + bias
+    spread = Lam.abs() @ r if G is None else (Lam @ G).abs().sum(dim=-1)
+    value = Lam @ c + spread + bias if upper else Lam @ c - spread + bias
     return Lam, bias, value
 
 
@@ -276,3 +276,59 @@ def box_remainder_vjp(Ws, bs, act, x_nom, u_nom, radii, g_lo, g_hi, residual=Tru
     L = (to_t(g_lo) * r_lo).sum() + (to_t(g_hi) * r_hi).sum()
     gx, gu, gr = torch.autograd.grad(L, [x, u, rho])
     return gx.numpy(), gu.numpy(), gr.numpy()
+
+
+def zono_hull_nominal(nominal: torch.Tensor, c: torch.Tensor, G: torch.Tensor):
+    """A zonotope that contains both c + G E and the nominal point: the segment from c to the nominal
+    appended as one more generator, (c + a) / 2 + [G, (a - c) / 2] E (the set itself when c = a)."""
+    half = 0.5 * (nominal - c)
+    return c + half, torch.cat([G, half[:, None]], dim=1)
+
+
+def crown_zono(Ws, bs, act: str, c: torch.Tensor, G: torch.Tensor):
+    """Thm. 2 over the zonotope c + G E: the same back-substitution and relaxations as ``crown``, every
+    bound concretised over the zonotope instead of its interval hull."""
+    L = len(Ws)
+    bounds = []
+    relaxations = []
+    spread = (Ws[0] @ G).abs().sum(dim=1)
+    l1 = Ws[0] @ c - spread + bs[0]
+    u1 = Ws[0] @ c + spread + bs[0]
+    bounds.append((l1, u1))
+    relaxations.append(relax(act, l1, u1))
+    for layer in range(1, L - 1):
+        _, _, li = _back_substitute(Ws, bs, relaxations, layer, False, c, None, G)
+        _, _, ui = _back_substitute(Ws, bs, relaxations, layer, True, c, None, G)
+        bounds.append((li, ui))
+        relaxations.append(relax(act, li, ui))
+    W_lo, b_lo, _ = _back_substitute(Ws, bs, relaxations, L - 1, False, c, None, G)
+    W_hi, b_hi, _ = _back_substitute(Ws, bs, relaxations, L - 1, True, c, None, G)
+    return W_lo, b_lo, W_hi, b_hi, bounds
+
+
+def zono_remainder(Ws, bs, act, x_nom, u_nom, G, center=None, residual=True):
+    """Thm. 3 over a zonotope tube set (Eq. 18a) concretised exactly: the set hulled with the nominal
+    (``zono_hull_nominal``), CROWN over it, and r = min / max over the zonotope of the affine remainder
+    bounds, M c -+ ||M G||_{1,r} + const. FP64 numpy out: (r_lo, r_hi, [A B])."""
+    Ws_t = [to_t(W) for W in Ws]
+    bs_t = [to_t(b) for b in bs]
+    a = torch.cat([to_t(x_nom), to_t(u_nom)])
+    c0 = a if center is None else to_t(center)
+    with torch.no_grad():
+        c, Gh = zono_hull_nominal(a, c0, to_t(G))
+        W_lo, b_lo, W_hi, b_hi, _ = crown_zono(Ws_t, bs_t, act, c, Gh)
+        J = jacobian(Ws_t, bs_t, act, a)
+        f_nom, _ = forward(Ws_t, bs_t, act, a)
+        n_x = J.shape[0]
+        if residual:
+            eye = torch.zeros_like(J)
+            eye[:, :n_x] = torch.eye(n_x, dtype=J.dtype)
+            J = J + eye
+            W_lo = W_lo + eye
+            W_hi = W_hi + eye
+            f_nom = f_nom + a[:n_x]
+        const = J @ a - f_nom
+        M_lo, M_hi = W_lo - J, W_hi - J
+        r_lo = M_lo @ c - (M_lo @ Gh).abs().sum(dim=1) + const + b_lo
+        r_hi = M_hi @ c + (M_hi @ Gh).abs().sum(dim=1) + const + b_hi
+    return r_lo.numpy(), r_hi.numpy(), J.numpy()

@@ -305,3 +305,38 @@ def test_ibp_intermediate_bounds_and_remainder_are_sound(act):
     if act == "relu":
         el, eh, _ = exact.relu_exact_range(Ws, bs, a, lo, hi, residual=False)
         assert np.all(r_lo.numpy() <= el + 1e-12) and np.all(r_hi.numpy() >= eh - 1e-12)
+
+
+def test_zonotope_crown_with_diagonal_generators_is_the_box_version():
+    """G = diag(r) makes the zonotope the box c +- r: every concretisation ||Lambda G||_{1,r} = |Lambda| r,
+    so the zonotope version reproduces the box version."""
+    w = inputs.tanh_mlp(seed=4300, n_traj=1, N=3, widths=(12, 24, 24, 6))
+    for t in range(w.T):
+        G = np.diag(w.radii[t].astype(np.float64))
+        zl, zh, zJ = crown.zono_remainder(w.Ws, w.bs, w.act, w.x_nom[t], w.u_nom[t], G)
+        bl, bh, bJ = crown.box_remainder(w.Ws, w.bs, w.act, w.x_nom[t], w.u_nom[t], w.radii[t])
+        assert np.allclose(zl, bl, rtol=1e-12, atol=1e-15) and np.allclose(zh, bh, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("act", ["relu", "tanh"])
+def test_zonotope_crown_sound_on_sampled_zonotope_points(act):
+    """Thm. 3 over a skewed zonotope (more generators than dimensions, centre off the nominal): every
+    sampled point's true remainder lies in the bound, vertices of the generator cube included; and the
+    hull construction contains the nominal."""
+    rng = np.random.default_rng(35)
+    Ws, bs = _net((6, 16, 16, 4), 36)
+    n_x = 4
+    a = rng.normal(size=6)
+    G = rng.normal(size=(6, 9)) * 0.05
+    c = a + rng.normal(size=6) * 0.02
+    ch, Gh = crown.zono_hull_nominal(torch.tensor(a), torch.tensor(c), torch.tensor(G))
+    xi = np.linalg.lstsq(Gh.numpy(), a - ch.numpy(), rcond=None)[0]
+    assert np.allclose(Gh.numpy() @ xi + ch.numpy(), a)
+    rl, rh, J = crown.zono_remainder(Ws, bs, act, a[:n_x], a[n_x:], G, center=c, residual=False)
+    Xi = np.concatenate([rng.uniform(-1, 1, (20000, 9)), rng.choice([-1.0, 1.0], (5000, 9))])
+    P = c + Xi @ G.T
+    R = sampling.remainders(sampling.mlp_f_batch(Ws, bs, act, residual=False), a, J, P)
+    assert np.all(R.min(0) >= rl - 1e-12) and np.all(R.max(0) <= rh + 1e-12)
+    # the exact concretisation is never looser than the box hull's at the first layer
+    W1 = torch.tensor(Ws[0])
+    assert torch.all((W1 @ torch.tensor(G)).abs().sum(1) <= W1.abs() @ torch.tensor(np.abs(G).sum(1)) + 1e-15)
