@@ -63,7 +63,9 @@ typedef enum { LEB_ACT_RELU = 0, LEB_ACT_TANH = 1 } leb_act;
 /* arithmetic of the MLP back-substitution: FP32 on CUDA cores, or FP16/BF16 operands on the
    tensor cores with FP32 accumulation and a rigorous rounding inflation */
 typedef enum { LEB_PREC_FP32 = 0, LEB_PREC_FP16 = 1, LEB_PREC_BF16 = 2 } leb_prec;
-typedef enum { LEB_SET_BOX = 0, LEB_SET_ZONO = 1 } leb_set_kind;
+/* LEB_SET_ZONO_EXACT: a zonotope whose CROWN bounds (every layer and Thm. 3) are concretised over the
+   zonotope itself, Lambda c -+ ||Lambda G||_{1,r}, instead of its interval hull (FP32 MLP handles only) */
+typedef enum { LEB_SET_BOX = 0, LEB_SET_ZONO = 1, LEB_SET_ZONO_EXACT = 2 } leb_set_kind;
 /* bounds of the MLP's hidden layers 2..: CROWN back-substitution (Thm. 2 for every layer) or interval
    bound propagation (the cheaper, looser variant); the output layer is always back-substituted */
 typedef enum { LEB_INTERMEDIATE_CROWN = 0, LEB_INTERMEDIATE_IBP = 1 } leb_intermediate;
@@ -111,7 +113,8 @@ typedef struct {
  *  LEB_SET_BOX:  radii [T, n], non-negative half-widths.
  *  LEB_SET_ZONO: G [T, n, n_gen] generators; the set is center + G xi, |xi|_inf <= 1.
  * The set is replaced by its interval hull and hulled with the nominal point (Thm. 1 needs the
- * nominal inside the set; a tube with a centre offset may not contain it). */
+ * nominal inside the set; a tube with a centre offset may not contain it). LEB_SET_ZONO_EXACT keeps the
+ * zonotope (G, n_gen as for LEB_SET_ZONO) and adds the segment to the nominal as one more generator. */
 typedef struct {
   leb_set_kind kind;
   const float* center;

@@ -20,7 +20,7 @@ ASYNC_NONFINITE, ASYNC_TIMEOUT, ASYNC_OVERFLOW = 1, 2, 4
 DYN_QUAD_CHAIN, DYN_MLP, DYN_SATELLITE, DYN_QUAD3D = 0, 1, 2, 3
 ACT = {"relu": 0, "tanh": 1}
 PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
-SET_BOX, SET_ZONO = 0, 1
+SET_BOX, SET_ZONO, SET_ZONO_EXACT = 0, 1, 2
 
 
 class LebError(RuntimeError):
@@ -207,9 +207,9 @@ class Handle:
 
     # -- descriptors ------------------------------------------------------------------------------
     @staticmethod
-    def set_desc(radii=None, G=None, center=None):
+    def set_desc(radii=None, G=None, center=None, zono_exact=False):
         if G is not None:
-            return SetDesc(SET_ZONO, _ptr(center), None, _ptr(G), int(G.shape[-1]))
+            return SetDesc(SET_ZONO_EXACT if zono_exact else SET_ZONO, _ptr(center), None, _ptr(G), int(G.shape[-1]))
         return SetDesc(SET_BOX, _ptr(center), _ptr(radii), None, 0)
 
     @staticmethod
@@ -219,7 +219,7 @@ class Handle:
         return BatchDesc(int(traj_offsets.numel() - 1), _ptr(traj_offsets), _ptr(traj_nquads))
 
     def bounds(self, x_nom, u_nom, radii=None, G=None, center=None, traj_offsets=None, traj_nquads=None,
-               want_AB=True, gamma_pad=None, want_eps=False, out=None, n_gen_per_quad=None):
+               want_AB=True, gamma_pad=None, want_eps=False, out=None, n_gen_per_quad=None, zono_exact=False):
         """Certified bounds for T timesteps (device tensors in, device tensors out).
 
         Returns a dict with r_lo, r_hi [T, n_x] (packed for uneven batches), A, B (or None), the
@@ -255,7 +255,7 @@ class Handle:
         if n_gen_per_quad is not None and G is not None:
             sd = SetDesc(SET_ZONO, _ptr(center), None, _ptr(G), int(n_gen_per_quad))
         else:
-            sd = self.set_desc(radii, G, center)
+            sd = self.set_desc(radii, G, center, zono_exact)
         bd = self.batch_desc(traj_offsets, traj_nquads)
         ws = self.workspace(max(T, 1), dev, extra=0 if bd is None else bd.n_traj)
         check(lib().leb_bounds(self.h, None if bd is None else C.byref(bd), T, _ptr(x_nom), _ptr(u_nom), C.byref(sd),

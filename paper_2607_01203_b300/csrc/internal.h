@@ -192,9 +192,10 @@ leb_status mlp_bounds_backward(Ctx& c, int T, const float* x_nom, const float* u
 leb_status mlp_prepare(Ctx& c);
 void mlp_release(Ctx& c);
 size_t simt_chain_smem(int maxw);
+// zset: the caller's set; LEB_SET_ZONO_EXACT (CUDA-core chains) concretises over the zonotope itself
 leb_status run_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, float* r_lo, float* r_hi, float* A,
                      float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags,
-                     bool simt, bool tight = false);
+                     bool simt, bool tight = false, const leb_set* zset = nullptr);
 // prep, enclosed nominal pass, bounds and relaxation of every hidden layer (chains on CUDA cores if simt).
 // tight: tensor-core chains without the rounding inflation (not sound; the adjoint's recompute of the
 // algorithm's bounds).

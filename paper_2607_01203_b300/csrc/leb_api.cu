@@ -277,9 +277,12 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
   if (!h || !set || T < 0 || !dev_flags) return LEB_ERR_INVALID_ARG;
   h->timer.phase = 0;
   if (T > 0 && (!x_nom || !u_nom || !r_lo || !r_hi)) return LEB_ERR_INVALID_ARG;
-  if (set->kind != LEB_SET_BOX && set->kind != LEB_SET_ZONO) return LEB_ERR_INVALID_ARG;
+  if (set->kind != LEB_SET_BOX && set->kind != LEB_SET_ZONO && set->kind != LEB_SET_ZONO_EXACT)
+    return LEB_ERR_INVALID_ARG;
   if (T > 0 && set->kind == LEB_SET_BOX && !set->radii) return LEB_ERR_INVALID_ARG;
-  if (T > 0 && set->kind == LEB_SET_ZONO && (!set->G || set->n_gen < 1)) return LEB_ERR_INVALID_ARG;
+  if (T > 0 && set->kind != LEB_SET_BOX && (!set->G || set->n_gen < 1)) return LEB_ERR_INVALID_ARG;
+  if (set->kind == LEB_SET_ZONO_EXACT && (h->kind != LEB_DYN_MLP || h->mlp.prec != LEB_PREC_FP32))
+    return LEB_ERR_UNSUPPORTED;
   if (opt && ((opt->gamma_c == nullptr) != (opt->gamma_r == nullptr))) return LEB_ERR_INVALID_ARG;
   if (opt && !(opt->gamma_pad >= 0.f)) return LEB_ERR_INVALID_ARG;
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return LEB_ERR_WORKSPACE;

@@ -131,7 +131,7 @@ __global__ void mlp_prep_kernel(int T, int n_x, int n_u, const float* x_nom, con
   if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (set.kind == LEB_SET_ZONO) {
+  if (set.kind == LEB_SET_ZONO || set.kind == LEB_SET_ZONO_EXACT) {   // the hull (exact sets refine it later)
     const int p = set.n_gen;
     for (int r = warp; r < n; r += nw) {
       const float* row = set.G + ((long long)t * n + r) * p;
@@ -512,6 +512,11 @@ struct ChainArgs {
   float* bslack;                 // stated slack of the intermediate bounds (non-negative floats, max-combined)
   float *r_lo, *r_hi, *A, *B, *eps, *gamma_c, *gamma_r;
   float gamma_pad;
+  // exact concretisation over a zonotope set (zG != nullptr): generators [T, n, zp], centres [T, n] or
+  // nullptr (centred at the nominal), nominal [T, n]; zgam = gamma_n for a sum of n products
+  const float *zG, *zc, *anom;
+  int zp;
+  float zgam;
 };
 
 __device__ __forceinline__ float warp_sum_dir(float v, int dir) {  // dir: -1 round down, +1 round up
@@ -521,6 +526,44 @@ __device__ __forceinline__ float warp_sum_dir(float v, int dir) {  // dir: -1 ro
     v = dir < 0 ? __fadd_rd(v, w) : __fadd_ru(v, w);
   }
   return v;
+}
+
+// Range of sum_m M_m Delta_m over the zonotope set hulled with the nominal, for a warp's row with
+// coefficients M_m = Mof(m) (intervals; points for the chain rows of hidden layers). With cd = (c - a) / 2
+// the hull is (c + a) / 2 + [G, -cd] E, so Delta = alpha - a = cd (1 - xi_p) + G xi: its range is
+// (sum_m M_m cd_m) [0, 2] -+ sum_g |sum_m M_m G_mg|. Each |sum_m M_m G_mg| is bounded by
+// |fl(sum_m mid_m G_mg)| + gamma_n sum_m |mid_m| |G_mg| + sum_m rad_m |G_mg| (rounded up). Warp-wide result.
+template <typename MF>
+__device__ __forceinline__ ivl zono_range(const ChainArgs& a, long long t, int n, MF Mof, int lane) {
+  const long long tn = t * n;
+  ivl v = iv(0.f);
+  if (a.zc) {
+    for (int m = lane; m < n; m += 32) {
+      const float c = a.zc[tn + m], nom = a.anom[tn + m];
+      const ivl cd = iv(__fmul_rd(__fsub_rd(c, nom), 0.5f), __fmul_ru(__fsub_ru(c, nom), 0.5f));
+      v = iv_add(v, iv_mul(Mof(m), cd));
+    }
+  }
+  v.lo = warp_sum_dir(v.lo, -1);
+  v.hi = warp_sum_dir(v.hi, 1);
+  const ivl v2 = iv(fminf(0.f, 2.f * v.lo), fmaxf(0.f, 2.f * v.hi));   // times [0, 2] (exact doubling)
+  float S = 0.f;
+  const float* G = a.zG + tn * a.zp;
+  for (int g = lane; g < a.zp; g += 32) {
+    float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    for (int m = 0; m < n; ++m) {
+      const ivl M = Mof(m);
+      const float mid = 0.5f * M.lo + 0.5f * M.hi;
+      const float rad = fmaxf(__fsub_ru(M.hi, mid), __fsub_ru(mid, M.lo));
+      const float gv = G[(long long)m * a.zp + g], ga = fabsf(gv);
+      s1 = fmaf(mid, gv, s1);
+      s2 = __fmaf_ru(fabsf(mid), ga, s2);
+      s3 = __fmaf_ru(rad, ga, s3);
+    }
+    S = __fadd_ru(S, __fadd_ru(__fadd_ru(fabsf(s1), __fmul_ru(a.zgam, s2)), s3));
+  }
+  S = warp_sum_dir(S, 1);
+  return iv(__fsub_rd(v2.lo, S), __fadd_ru(v2.hi, S));
 }
 
 template <int CG>
@@ -662,20 +705,26 @@ __global__ void __launch_bounds__(256, 1) mlp_chain_simt_kernel(ChainArgs a) {
       if (role == 2) continue;
       const int l = (row0 + r) / 3;
       const float* Jr = C + (r - role + 2) * maxw;
-      float acc = 0.f;
-      for (int mcol = lane; mcol < n; mcol += 32) {
-        const float lam = C[r * maxw + mcol], jv = Jr[mcol];
-        ivl M;
+      const float* Cr = C + r * maxw;
+      auto Mof = [&](int mcol) {
+        const float lam = Cr[mcol], jv = Jr[mcol];
         if (a.m.residual && mcol == l) {
           const float aret = 1.f + jv;  // the value written to A
-          M = iv(__fadd_rd(__fsub_rd(lam, aret), 1.f), __fadd_ru(__fsub_ru(lam, aret), 1.f));
-        } else {
-          M = iv(__fsub_rd(lam, jv), __fsub_ru(lam, jv));
+          return iv(__fadd_rd(__fsub_rd(lam, aret), 1.f), __fadd_ru(__fsub_ru(lam, aret), 1.f));
         }
-        const ivl term = iv_mul(M, iv(a.dlo[tn + mcol], a.dhi[tn + mcol]));
-        acc = role == 0 ? __fadd_rd(acc, term.lo) : __fadd_ru(acc, term.hi);
+        return iv(__fsub_rd(lam, jv), __fsub_ru(lam, jv));
+      };
+      float acc = 0.f;
+      if (a.zG) {
+        const ivl zr = zono_range(a, t, n, Mof, lane);
+        acc = role == 0 ? zr.lo : zr.hi;
+      } else {
+        for (int mcol = lane; mcol < n; mcol += 32) {
+          const ivl term = iv_mul(Mof(mcol), iv(a.dlo[tn + mcol], a.dhi[tn + mcol]));
+          acc = role == 0 ? __fadd_rd(acc, term.lo) : __fadd_ru(acc, term.hi);
+        }
+        acc = warp_sum_dir(acc, role == 0 ? -1 : 1);
       }
-      acc = warp_sum_dir(acc, role == 0 ? -1 : 1);
       // partner row (the other direction of the same l) gives the stated slack as well
       if (lane == 0) {
         float val;
@@ -705,11 +754,17 @@ __global__ void __launch_bounds__(256, 1) mlp_chain_simt_kernel(ChainArgs a) {
       const int role = (row0 + r) % 2;
       const int c = (row0 + r) / 2;
       float acc = 0.f;
-      for (int mcol = lane; mcol < n; mcol += 32) {
-        const ivl term = iv_mul(iv(C[r * maxw + mcol]), iv(a.dlo[tn + mcol], a.dhi[tn + mcol]));
-        acc = role == 0 ? __fadd_rd(acc, term.lo) : __fadd_ru(acc, term.hi);
+      if (a.zG) {
+        const float* Cr = C + r * maxw;
+        const ivl zr = zono_range(a, t, n, [&](int mcol) { return iv(Cr[mcol]); }, lane);
+        acc = role == 0 ? zr.lo : zr.hi;
+      } else {
+        for (int mcol = lane; mcol < n; mcol += 32) {
+          const ivl term = iv_mul(iv(C[r * maxw + mcol]), iv(a.dlo[tn + mcol], a.dhi[tn + mcol]));
+          acc = role == 0 ? __fadd_rd(acc, term.lo) : __fadd_ru(acc, term.hi);
+        }
+        acc = warp_sum_dir(acc, role == 0 ? -1 : 1);
       }
-      acc = warp_sum_dir(acc, role == 0 ? -1 : 1);
       if (lane == 0) {
         const long long o = tH + a.hoff[a.target] + c;
         const float zh = a.zhat[o], e = a.zrad[o];
@@ -847,6 +902,12 @@ leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_
     if (i == 0) {
       mlp_nominal_kernel<<<grid, 256, 0, s>>>(na);
       if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
+      if (set->kind == LEB_SET_ZONO_EXACT) {
+        // layer-0 bounds over the zonotope itself (the nominal pass gave them over its interval hull)
+        leb_status st = run_chain(c, T, 0, L, ws, nullptr, nullptr, nullptr, nullptr, nullptr, s, bad, opt, flags,
+                                  true, false, set);
+        if (st != LEB_OK) return st;
+      }
       const int blocks = (int)std::min<long long>(((long long)T * na.N + 255) / 256, 148LL * 32);
       mlp_relax_kernel<<<blocks, 256, 0, s>>>(T, na.N, L.H, L.hoff[0], m.act, ws + L.lo, ws + L.hi, ws + L.zhat,
                                               ws + L.zrad, nullptr, ws + L.sL, ws + L.tL, ws + L.sU, ws + L.tU,
@@ -866,7 +927,7 @@ leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_
     } else {
       // bounds of hidden layer i by back-substitution
       leb_status st = run_chain(c, T, i, L, ws, nullptr, nullptr, nullptr, nullptr, nullptr, s, bad, opt, flags,
-                                simt, tight);
+                                simt, tight, set);
       if (st != LEB_OK) return st;
     }
     const int blocks = (int)std::min<long long>(((long long)T * na.N + 255) / 256, 148LL * 32);
@@ -889,12 +950,12 @@ leb_status mlp_bounds(Ctx& c, int T, const float* x_nom, const float* u_nom, con
   float* ws = (float*)((char*)ws_base + 256);
   // output rows: lower, upper and Jacobian chains -> r_lo, r_hi, A, B
   return run_chain(c, T, c.mlp.L - 1, L, ws, r_lo, r_hi, A, B, opt ? opt->eps : nullptr, s, (int*)(ws + L.bad), opt,
-                   flags, simt);
+                   flags, simt, false, set);
 }
 
 leb_status run_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, float* r_lo, float* r_hi, float* A,
                      float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags,
-                     bool simt, bool tight) {
+                     bool simt, bool tight, const leb_set* zset) {
   const MlpModel& m = c.mlp;
   if (!simt) return tc_chain(c, T, target, L, ws, r_lo, r_hi, A, B, eps, s, bad, opt, flags, tight);
   ChainArgs a{};
@@ -933,6 +994,13 @@ leb_status run_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws,
   a.gamma_c = opt ? opt->gamma_c : nullptr;
   a.gamma_r = opt ? opt->gamma_r : nullptr;
   a.gamma_pad = opt ? opt->gamma_pad : 0.f;
+  if (zset && zset->kind == LEB_SET_ZONO_EXACT) {
+    a.zG = zset->G;
+    a.zp = zset->n_gen;
+    a.zc = zset->center;
+    a.anom = ws + L.anom;
+    a.zgam = gamma_n(m.widths[0]);
+  }
   return launch_simt_chain(c, a, s);
 }
 
