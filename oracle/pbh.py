@@ -43,16 +43,33 @@ def prefix_box(lo: np.ndarray, hi: np.ndarray, nominal: np.ndarray, j: int):
     return plo, phi
 
 
-def pbh(dyn, nominal: np.ndarray, lo: np.ndarray, hi: np.ndarray):
-    """Thm. 1 enclosure [R_lo, R_hi] of the linearization error of every output row."""
+def ordered_prefix_box(lo, hi, nominal, rank, j: int):
+    """X^(j) for the path order with ranks ``rank`` (rank[c] = position of coordinate c on the path):
+    the coordinates at or before j range over [lo, hi], the later ones sit at the nominal."""
+    inpre = np.asarray(rank) <= rank[j]
+    a = np.asarray(nominal, np.float64)
+    return np.where(inpre, lo, a), np.where(inpre, hi, a)
+
+
+def pbh(dyn, nominal: np.ndarray, lo: np.ndarray, hi: np.ndarray, order=None):
+    """Thm. 1 enclosure [R_lo, R_hi] of the linearization error of every output row. ``order``: the path
+    order as a permutation of the coordinates (default the natural one); each entry (j, k) is evaluated
+    over the prefix set of whichever of j, k comes first on the path."""
     a = np.asarray(nominal, np.float64)
     D = [(lo[i] - a[i], hi[i] - a[i]) for i in range(dyn.n)]
     R_lo = np.zeros(dyn.n_x)
     R_hi = np.zeros(dyn.n_x)
+    rank = None
+    if order is not None:
+        rank = np.empty(dyn.n, int)
+        rank[np.asarray(order)] = np.arange(dyn.n)
     for row in range(dyn.n_x):
         R = (0.0, 0.0)
         for j, k, fn in dyn.hessian_terms(row):
-            plo, phi = prefix_box(lo, hi, a, min(j, k))
+            if rank is None:
+                plo, phi = prefix_box(lo, hi, a, min(j, k))
+            else:
+                plo, phi = ordered_prefix_box(lo, hi, a, rank, j if rank[j] <= rank[k] else k)
             Hv = fn(plo, phi)
             if j == k:
                 term = iv_scale(0.5, iv_mul(Hv, iv_sqr(D[k])))

@@ -221,3 +221,32 @@ def test_partition_pieces_cover_the_box():
     for lp, hp in pieces:
         inside |= np.all((X >= lp) & (X <= hp), axis=1)
     assert inside.all()
+
+
+def test_path_orderings():
+    """Thm. 1 holds for any path order (the proof only needs a coordinate-wise path): every order's bound
+    contains the exact range of the planar quadrotor; the identity permutation is the default; for the
+    satellite (constant Hessian) every order gives the same, exact, bound."""
+    from oracle import dynamics3d, exact
+    rng = np.random.default_rng(81)
+    w = inputs.planar_quad()
+    dyn = dynamics.QuadChain(1, **w.params)
+    orders = [list(range(8)), [6, 7, 0, 1, 2, 3, 4, 5], list(range(8))[::-1]] + \
+        [list(rng.permutation(8)) for _ in range(3)]
+    for t in range(0, w.T, 4):
+        a = w.nominal()[t].astype(np.float64)
+        lo, hi = pbh.box_from_set(a, radii=w.radii[t])
+        el, eh = exact.quad_exact_range(dyn, a, lo, hi)
+        base = pbh.pbh(dyn, a, lo, hi)
+        for od in orders:
+            l, h = pbh.pbh(dyn, a, lo, hi, order=od)
+            assert np.all(l <= el + 1e-12) and np.all(h >= eh - 1e-12)
+        l0, h0 = pbh.pbh(dyn, a, lo, hi, order=list(range(8)))
+        assert np.array_equal(l0, base[0]) and np.array_equal(h0, base[1])
+    sat = dynamics3d.Satellite()
+    a = np.concatenate([rng.normal(size=4) / 2, rng.uniform(-1, 1, 6)])
+    lo, hi = a - 0.1, a + 0.1
+    b = pbh.pbh(sat, a, lo, hi)
+    for _ in range(4):
+        l, h = pbh.pbh(sat, a, lo, hi, order=list(rng.permutation(10)))
+        assert np.allclose(l, b[0], rtol=1e-13, atol=1e-16) and np.allclose(h, b[1], rtol=1e-13, atol=1e-16)
