@@ -748,6 +748,20 @@ class Table1Form(Form):
         return 0.0, 0, 0
 
 
+def slowest_rank_ms(torch, dist, step_ms, device):
+    """The step time of the whole job: the maximum over the ranks (every rank runs an independent
+    replica; the slowest one sets the job's time). One rank: the value itself."""
+    t = torch.tensor([float(step_ms)], device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, ms_max):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / (ms_max * 1e-3)
+
+
 def timed_loop(torch, fn, steps):
     """CUDA-event time per call of fn on the current stream (after one untimed call)."""
     fn()
@@ -938,10 +952,7 @@ def main():
                for i, f in enumerate(forms)}
     step_ms = sum(form_ms.values())
     wall_ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([step_ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = slowest_rank_ms(torch, dist, step_ms, dev)
     for h in handles.values():
         h.timing(False)
     # main-kernel times per step, from the event pairs recorded around their launches in the timed region
@@ -953,7 +964,7 @@ def main():
         else:
             kt[f.name] = (form_ms[f.name], 1, f.kernel_label)
     units = sum(f.units() for f in forms) * world
-    value = units / (ms_max * 1e-3)
+    value = job_value(sum(f.units() for f in forms), world, ms_max)
     out_forms = {}
     roof = {}
     for f in forms:
