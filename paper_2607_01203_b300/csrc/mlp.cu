@@ -207,6 +207,10 @@ __device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y
 __device__ __forceinline__ float2 abs2(float2 v) { return make_float2(fabsf(v.x), fabsf(v.y)); }
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 
+// FIRST: the first hidden layer (its bounds over the displacement box come out of this pass too);
+// V2: the reduced-precision operand term v2 = |W - W~| abar is wanted (tensor-core handles). Both are
+// template parameters so that the unused accumulators take no registers.
+template <bool FIRST, bool V2>
 __global__ void __launch_bounds__(256) mlp_nominal_kernel(NomArgs a) {
   __shared__ __align__(16) float s_in[kKC][kNomBT + 4];
   __shared__ __align__(16) float s_q[kKC][kNomBT + 4];
@@ -240,7 +244,7 @@ __global__ void __launch_bounds__(256) mlp_nominal_kernel(NomArgs a) {
         x = a.in[o];
         const float rad = a.in_rad ? a.in_rad[o] : 0.f;
         q = __fmaf_ru(a.gam, fabsf(x), rad);
-        if (a.first) {
+        if (FIRST) {
           dl = a.dlo[o];
           dh = a.dhi[o];
           ab = fmaxf(fabsf(dl), fabsf(dh));
@@ -292,9 +296,9 @@ __global__ void __launch_bounds__(256) mlp_nominal_kernel(NomArgs a) {
           cmp[i][j] = __fadd2_rn(cmp[i][j], __fadd2_rn(pe, se));
           err[i][j] = __ffma2_ru(wa2[j], dup2(q[i]), err[i][j]);
           vv[i][j] = __ffma2_ru(wa2[j], dup2(ab[i]), vv[i][j]);
-          vw[i][j] = __ffma2_ru(we2[j], dup2(ab[i]), vw[i][j]);
+          if (V2) vw[i][j] = __ffma2_ru(we2[j], dup2(ab[i]), vw[i][j]);
         }
-      if (a.first) {
+      if (FIRST) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const float2 dl = dup2(s_dl[kk][4 * ty + i]), dh = dup2(s_dh[kk][4 * ty + i]);
@@ -338,8 +342,8 @@ __global__ void __launch_bounds__(256) mlp_nominal_kernel(NomArgs a) {
       a.zhat[o] = zh;
       a.zrad[o] = e;
       a.v1[o] = v1;
-      if (a.v2) a.v2[o] = v2;
-      if (a.first) {
+      if (V2) a.v2[o] = v2;
+      if (FIRST) {
         a.lo[o] = __fadd_rd(__fsub_rd(zh, e), bl);
         a.hi[o] = __fadd_ru(__fadd_ru(zh, e), bh);
       }
@@ -834,6 +838,17 @@ leb_status launch_simt_chain(const Ctx& c, const ChainArgs& a, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
 }
 
+static void launch_nominal(const NomArgs& na, dim3 grid, cudaStream_t s) {
+  const bool v2 = na.v2 != nullptr;
+  if (na.first) {
+    if (v2) mlp_nominal_kernel<true, true><<<grid, 256, 0, s>>>(na);
+    else mlp_nominal_kernel<true, false><<<grid, 256, 0, s>>>(na);
+  } else {
+    if (v2) mlp_nominal_kernel<false, true><<<grid, 256, 0, s>>>(na);
+    else mlp_nominal_kernel<false, false><<<grid, 256, 0, s>>>(na);
+  }
+}
+
 leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set,
                               void* ws_base, int* flags, cudaStream_t s, bool simt, const leb_options* opt, bool tight) {
   const MlpModel& m = c.mlp;
@@ -900,7 +915,7 @@ leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_
     }
     dim3 grid((T + kNomBT - 1) / kNomBT, (na.N + kNomBN - 1) / kNomBN);
     if (i == 0) {
-      mlp_nominal_kernel<<<grid, 256, 0, s>>>(na);
+      launch_nominal(na, grid, s);
       if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
       if (set->kind == LEB_SET_ZONO_EXACT) {
         // layer-0 bounds over the zonotope itself (the nominal pass gave them over its interval hull)
@@ -915,7 +930,7 @@ leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_
       if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
       continue;
     }
-    mlp_nominal_kernel<<<grid, 256, 0, s>>>(na);
+    launch_nominal(na, grid, s);
     if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
     if (m.ibp) {
       // bounds of hidden layer i by interval bound propagation from layer i-1's bounds
