@@ -407,7 +407,7 @@ class ProposerForm(Form):
 
     Algorithmic FLOPs per sample: 2 (392 x 256 + 256 x 256 + 256 x 336) = 503,808."""
     name = "proposer"
-    kernel_label = "proposer forward (prop_gemm_kernel x3 + elementwise)"
+    kernel_label = "proposer forward (prop_tc_gemm_kernel x3, tcgen05 BF16, + standardisation)"
 
     def __init__(self, torch, dev, quick=False):
         from paper_2607_01203_b300 import inputs
@@ -458,10 +458,11 @@ class ProposerForm(Form):
     def roofline(self, pk, ms, launches, kernel):
         flop = PROPOSER_FLOP * self.T
         achieved = flop / (ms * 1e-3) / 1e12
-        peak = fp32_simt_peak_tflops(pk)
-        return {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+        peak = pk["bf16_tflops"]
+        return {"bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_src": "FP32 FMA peak derived: 148 SM x 128 lanes x 2 FLOP x max SM clock",
+                "peak_src": pk["src"] + " bf16_tflops (6.4 GFLOP per call: launch latency, not the tensor pipe, "
+                            "sets the time)",
                 "kernel": kernel, "kernel_ms": round(ms, 4), "launches_per_step": launches,
                 "flop_per_unit": PROPOSER_FLOP, "units_per_step": self.T}
 

@@ -819,6 +819,8 @@ leb_status tc_prepare(Ctx& c) {
   return LEB_OK;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return encode_fn(); }
+
 const void* tc_weight_t(const Ctx& c, int k) {
   const TcState* st = tc_state(c);
   return st ? st->WT[k] : nullptr;

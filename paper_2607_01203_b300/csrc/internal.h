@@ -1,5 +1,7 @@
 // Internal declarations shared by the library's translation units (not part of the C ABI).
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cstdint>
@@ -201,6 +203,8 @@ leb_status run_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws,
 // algorithm's bounds).
 leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set, void* ws,
                               int* flags, cudaStream_t s, bool simt, const leb_options* opt, bool tight = false);
+// the driver's cuTensorMapEncodeTiled (nullptr if unavailable)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 // tensor-core back-substitution (reduced-precision operands, FP32 accumulation in TMEM)
 leb_status tc_prepare(Ctx& c);
 void tc_release(Ctx& c);

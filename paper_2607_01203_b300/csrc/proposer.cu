@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "tc_ptx.cuh"
 
 struct leb_proposer_s {
   int n_in = 0, H = 0, n_out = 0;
@@ -26,11 +27,147 @@ struct leb_proposer_s {
   float* norm = nullptr;  // in_mean [n_in], in_std [n_in], out_mean [n_out], out_std [n_out]
   int* periodic = nullptr;  // [n_in] 1: the input is an angle, wrapped to [-pi, pi) before standardising
   int step = 0;
+  // inference on the tensor cores: BF16 copies of the weights (refreshed by every forward call) and their
+  // tensor maps; tc = false when the shapes do not fit the tcgen05 GEMM (then the CUDA-core GEMMs run)
+  bool tc = false;
+  int w_version = 0, wb_version = -1;   // bumped by every weight change; the BF16 copies' version
+  __nv_bfloat16* Wb[3] = {};
+  CUtensorMap wmap[3];
+  int nchunk[3] = {};
 };
 
 namespace leb {
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// ---------------------------------------------------------------------------------------------------
+// Inference GEMM on the tensor cores: C[M, N] = A[M, K] W[N, K]^T + bias (ReLU), A and W in BF16
+// (K-major, 128-byte swizzled tiles by TMA, zero fill past K and M), FP32 accumulation in TMEM.
+// One CTA = 128 rows of A and all N <= 512 columns (TMEM columns), issued as nchunk MMAs of N / nchunk
+// columns (a multiple of 16, at most 256). Warp 0 lane 0 loads, warp 1 lane 0 issues the MMAs, all four
+// warps read TMEM (thread = row) for the epilogue, which writes BF16 (the next layer's operand) or FP32
+// (the output, optionally taken back out of its standardisation: y std + mean).
+// Every wait is bounded; a wait that runs out leaves the tile's outputs NaN.
+// ---------------------------------------------------------------------------------------------------
+constexpr int kPtStages = 2;
+constexpr int kPtATile = 128 * 64 * 2;     // 16 KB
+constexpr int kPtBTile = 512 * 64 * 2;     // 64 KB (N <= 512)
+constexpr int kPtSmem = 1024 + kPtStages * (kPtATile + kPtBTile) + 64;
+
+__global__ void __launch_bounds__(128, 1) prop_tc_gemm_kernel(const __grid_constant__ CUtensorMap amap,
+                                                              const __grid_constant__ CUtensorMap wmap, int M, int N,
+                                                              int K, int nchunk, const float* bias, int relu,
+                                                              __nv_bfloat16* outb, float* outf, int ldo,
+                                                              const float* omean, const float* ostd) {
+  extern __shared__ uint8_t sraw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sraw) + 1023) & ~uintptr_t(1023));
+  uint8_t* At = base;                                        // [stages][16 KB]
+  uint8_t* Bt = base + kPtStages * kPtATile;                 // [stages][64 KB]
+  uint64_t* full = reinterpret_cast<uint64_t*>(Bt + kPtStages * kPtBTile);
+  uint64_t* empty = full + kPtStages;
+  uint64_t* acc = empty + kPtStages;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * 128, nK = (K + 63) / 64, nb = N / nchunk;
+  const uint32_t tcols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : (N <= 256 ? 256 : 512)));
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kPtStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc, 1);
+    mbar_fence_init();
+    s_fail = 0;
+  }
+  if (warp == 1) tmem_alloc(&tmem_slot, tcols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t abytes = kPtATile, bbytes = (uint32_t)N * 128u;
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&amap);
+    tma_prefetch_desc(&wmap);
+    for (int kb = 0; kb < nK; ++kb) {
+      const int s = kb % kPtStages;
+      if (kb >= kPtStages && !mbar_wait(&empty[s], ((kb / kPtStages) - 1) & 1u)) { s_fail = 1; break; }
+      mbar_arrive_expect_tx(&full[s], abytes + bbytes);
+      tma_load_2d(At + s * kPtATile, &amap, kb * 64, m0, &full[s]);
+      for (int c = 0; c < nchunk; ++c) tma_load_2d(Bt + s * kPtBTile + c * nb * 128, &wmap, kb * 64, c * nb, &full[s]);
+    }
+    // every posted copy lands before the block can exit
+    for (int kb = nK > kPtStages ? nK - kPtStages : 0; kb < nK; ++kb) mbar_wait(&full[kb % kPtStages], (kb / kPtStages) & 1u);
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = idesc_f16(128, nb, 1);
+    bool ok = true;
+    for (int kb = 0; kb < nK && ok; ++kb) {
+      const int s = kb % kPtStages;
+      if (!mbar_wait(&full[s], (kb / kPtStages) & 1u)) { ok = false; s_fail = 1; break; }
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(At + s * kPtATile), b0 = smem_u32(Bt + s * kPtBTile);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        for (int c = 0; c < nchunk; ++c)
+          tc_mma_f16(tmem + (uint32_t)(c * nb), sw128_desc(a0 + kk * 32), sw128_desc(b0 + c * nb * 128 + kk * 32),
+                     idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+      tc_commit(&empty[s]);
+    }
+    tc_commit(acc);
+  }
+  __syncwarp();
+  // ---- epilogue: thread = row m0 + 32 warp + lane, TMEM lane of the same index ---------------------
+  const bool ok = mbar_wait(acc, 0u) && !*(volatile int*)&s_fail;
+  tc_fence_after();
+  const int row = m0 + warp * 32 + lane;
+  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+  for (int c0 = 0; c0 < N; c0 += 16) {
+    float v[16];
+    tmem_ld16(tl + (uint32_t)c0, v);   // every thread of the warp takes part (sync.aligned)
+    if (row >= M) continue;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      float x = ok ? v[e] + bias[c0 + e] : __int_as_float(0x7fc00000);
+      x = relu ? fmaxf(x, 0.f) : x;
+      v[e] = omean ? fmaf(x, ostd[c0 + e], omean[c0 + e]) : x;   // back to the bounds' units
+    }
+    if (outb) {
+      uint32_t w[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+        w[e] = *reinterpret_cast<const uint32_t*>(&h);
+      }
+      uint4* dst = reinterpret_cast<uint4*>(outb + (long long)row * ldo + c0);
+      dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+      dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    } else {
+      float4* dst = reinterpret_cast<float4*>(outf + (long long)row * ldo + c0);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, tcols);
+}
+
+// The three weight matrices to their BF16 copies in one launch.
+__global__ void prop_weights_bf16_kernel(const float* W0, long long n0, const float* W1, long long n1, const float* W2,
+                                         long long n2, __nv_bfloat16* B0, __nv_bfloat16* B1, __nv_bfloat16* B2) {
+  const long long total = n0 + n1 + n2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    if (i < n0) B0[i] = __float2bfloat16_rn(W0[i]);
+    else if (i < n0 + n1) B1[i - n0] = __float2bfloat16_rn(W1[i - n0]);
+    else B2[i - n0 - n1] = __float2bfloat16_rn(W2[i - n0 - n1]);
+  }
+}
+
+__global__ void prop_to_bf16_kernel(long long total, const float* x, __nv_bfloat16* y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
 
 // C[M, N] = op(A) op(B) (+ bias[N]) (ReLU) or (* (Mask > 0)); operands rounded to BF16, FP32 accumulate.
 // op(A)[m, k] = tA ? A[k * lda + m] : A[m * lda + k];  op(B)[k, n] = tB ? B[n * ldb + k] : B[k * ldb + n].
@@ -113,6 +250,16 @@ __global__ void prop_destandardize_kernel(long long total, int n, const float* y
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(e % n);
     Y[e] = fmaf(y[e], stdv[j], mean[j]);
+  }
+}
+
+// Standardised inputs straight into the BF16 operand of the first layer.
+__global__ void prop_standardize_bf16_kernel(long long total, int n, const float* X, const int* periodic,
+                                             const float* mean, const float* stdv, __nv_bfloat16* Xb) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e % n);
+    const float x = periodic[j] ? wrap_pi(X[e]) : X[e];
+    Xb[e] = __float2bfloat16_rn((x - mean[j]) / stdv[j]);
   }
 }
 
@@ -224,6 +371,88 @@ size_t ws_floats(const leb_proposer_s* p, int B) {
 
 using namespace leb;
 
+// Chunks of an N-column product for the tcgen05 GEMM: the fewest with N / c a multiple of 16, at most 256.
+static int mma_chunks(int N) {
+  for (int c = 1; c <= N / 16; ++c)
+    if (N % c == 0 && (N / c) % 16 == 0 && N / c <= 256) return c;
+  return 0;
+}
+
+// BF16 weight copies and their tensor maps for tensor-core inference; false only on an allocation
+// failure (shapes the GEMM does not take leave p->tc false).
+static bool setup_tc(leb_proposer p) {
+  const int ins[3] = {p->n_in, p->H, p->H}, outs[3] = {p->H, p->H, p->n_out};
+  auto enc = tensor_map_encoder();
+  if (!enc || p->n_in % 8 != 0 || p->H % 8 != 0 || p->H > 512 || p->n_out > 512) return true;
+  for (int i = 0; i < 3; ++i) {
+    p->nchunk[i] = mma_chunks(outs[i]);
+    if (p->nchunk[i] == 0) return true;
+  }
+  for (int i = 0; i < 3; ++i) {
+    if (cudaMalloc(&p->Wb[i], (size_t)ins[i] * outs[i] * 2) != cudaSuccess) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)ins[i], (cuuint64_t)outs[i]};
+    cuuint64_t strides[1] = {(cuuint64_t)ins[i] * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)(outs[i] / p->nchunk[i])};
+    cuuint32_t estr[2] = {1, 1};
+    if (enc(&p->wmap[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p->Wb[i], dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return true;
+  }
+  if (cudaFuncSetAttribute(prop_tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPtSmem) != cudaSuccess)
+    return true;
+  p->tc = true;
+  return true;
+}
+
+// Activations [rows, cols] BF16 as the A operand of the tcgen05 GEMM (box 64 x 128, zero fill).
+static bool act_map(CUtensorMap* m, const __nv_bfloat16* x, int rows, int cols) {
+  auto enc = tensor_map_encoder();
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {64, 128};
+  cuuint32_t estr[2] = {1, 1};
+  return enc && enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(x), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Inference forward on the tensor cores, written to Y in the bounds' units; false: not taken.
+static bool forward_tc(leb_proposer p, int B, const float* X, float* ws, float* Y, cudaStream_t s, leb_status* st) {
+  const int n_in = p->n_in, H = p->H, n_out = p->n_out;
+  const size_t o1 = 0, o2 = (o1 + ((size_t)B * n_in + 1) / 2 + 3) & ~size_t(3);
+  const size_t o3 = (o2 + ((size_t)B * H + 1) / 2 + 3) & ~size_t(3);
+  const size_t end = o3 + ((size_t)B * H + 1) / 2;
+  // TMA needs 16-byte aligned operands, the epilogue stores Y rows as float4
+  if (!p->tc || end > ws_floats(p, B) || ((reinterpret_cast<uintptr_t>(ws) | reinterpret_cast<uintptr_t>(Y)) & 15u))
+    return false;
+  __nv_bfloat16* Xb = reinterpret_cast<__nv_bfloat16*>(ws + o1);
+  __nv_bfloat16* H1 = reinterpret_cast<__nv_bfloat16*>(ws + o2);
+  __nv_bfloat16* H2 = reinterpret_cast<__nv_bfloat16*>(ws + o3);
+  CUtensorMap m0, m1, m2;
+  if (!act_map(&m0, Xb, B, n_in) || !act_map(&m1, H1, B, H) || !act_map(&m2, H2, B, H)) return false;
+  *st = LEB_ERR_CUDA;
+  if (p->wb_version != p->w_version) {   // the weights changed since their last BF16 copy
+    const long long n0 = (long long)n_in * H, n1 = (long long)H * H, n2 = (long long)H * n_out;
+    prop_weights_bf16_kernel<<<blocks_for(n0 + n1 + n2), 256, 0, s>>>(p->W[0], n0, p->W[1], n1, p->W[2], n2, p->Wb[0],
+                                                                        p->Wb[1], p->Wb[2]);
+    p->wb_version = p->w_version;
+  }
+  prop_standardize_bf16_kernel<<<blocks_for((long long)B * n_in), 256, 0, s>>>((long long)B * n_in, n_in, X,
+                                                                                 p->periodic, p->norm, p->norm + n_in,
+                                                                                 Xb);
+  const int grid = (B + 127) / 128;
+  const float* omean = p->norm + 2 * n_in;
+  prop_tc_gemm_kernel<<<grid, 128, kPtSmem, s>>>(m0, p->wmap[0], B, H, n_in, p->nchunk[0], p->b[0], 1, H1, nullptr, H,
+                                                 nullptr, nullptr);
+  prop_tc_gemm_kernel<<<grid, 128, kPtSmem, s>>>(m1, p->wmap[1], B, H, H, p->nchunk[1], p->b[1], 1, H2, nullptr, H,
+                                                 nullptr, nullptr);
+  prop_tc_gemm_kernel<<<grid, 128, kPtSmem, s>>>(m2, p->wmap[2], B, n_out, H, p->nchunk[2], p->b[2], 0, nullptr, Y,
+                                                 n_out, omean, omean + n_out);
+  *st = cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
+  return true;
+}
+
 extern "C" {
 
 leb_status leb_proposer_create(int n_in, int n_hidden, int n_out, unsigned long long seed, leb_proposer* out) {
@@ -259,6 +488,7 @@ leb_status leb_proposer_create(int n_in, int n_hidden, int n_out, unsigned long 
     for (int j = 0; j < n_out; ++j) h[2 * n_in + n_out + j] = 1.f;
     ok = cudaMemcpy(p->norm, h.data(), h.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
   }
+  if (ok) ok = setup_tc(p);
   if (!ok || cudaDeviceSynchronize() != cudaSuccess) {
     leb_proposer_destroy(p);
     return LEB_ERR_CUDA;
@@ -271,6 +501,7 @@ leb_status leb_proposer_destroy(leb_proposer p) {
   if (!p) return LEB_ERR_INVALID_ARG;
   for (int i = 0; i < 3; ++i)
     for (float* q : {p->W[i], p->gW[i], p->mW[i], p->vW[i], p->b[i], p->gb[i], p->mb[i], p->vb[i]}) cudaFree(q);
+  for (int i = 0; i < 3; ++i) cudaFree(p->Wb[i]);
   cudaFree(p->norm);
   cudaFree(p->periodic);
   delete p;
@@ -336,7 +567,9 @@ leb_status leb_proposer_forward(leb_proposer p, int B, const float* X, float* Y,
   if (B == 0) return LEB_OK;
   cudaStream_t s = (cudaStream_t)stream;
   float* ws = (float*)workspace;
-  leb_status st = forward_impl(p, B, X, ws, s);
+  leb_status st = LEB_OK;
+  if (forward_tc(p, B, X, ws, Y, s, &st)) return st;   // Y written by the last GEMM's epilogue
+  st = forward_impl(p, B, X, ws, s);
   if (st != LEB_OK) return st;
   const float* y = ws + (size_t)B * (p->n_in + 2 * p->H);
   const long long tot = (long long)B * p->n_out;
@@ -380,6 +613,7 @@ leb_status leb_proposer_train_step(leb_proposer p, int B, const float* X, const 
   if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
   // Adam
   p->step += 1;
+  p->w_version += 1;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - std::pow(b1, (float)p->step), c2 = 1.f - std::pow(b2, (float)p->step);
   const int ins[3] = {n_in, H, H}, outs[3] = {H, H, n_out};
@@ -414,6 +648,7 @@ leb_status leb_proposer_set_layer(leb_proposer p, int i, const float* W, const f
   int in, out;
   if (layer_dims(p, i, &in, &out) != LEB_OK || !W || !b) return LEB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  p->w_version += 1;   // the BF16 inference copies are stale
   return (cudaMemcpyAsync(p->W[i], W, (size_t)in * out * 4, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
           cudaMemcpyAsync(p->b[i], b, (size_t)out * 4, cudaMemcpyDeviceToDevice, s) == cudaSuccess)
              ? LEB_OK

@@ -46,6 +46,29 @@ def test_gradients_and_adam_step_vs_oracle():
         assert np.allclose(W1.cpu().numpy(), pW, rtol=1e-5, atol=1e-7)
 
 
+@pytest.mark.parametrize("B", [300, 12800])
+def test_tensor_core_inference_vs_oracle(B):
+    """Inference of the 392-256-256-336 proposer on the tensor cores (tcgen05, BF16 operands, FP32
+    accumulation in TMEM), against the oracle's forward at the same operand precision: FP32 against FP64
+    accumulation over at most 392 terms and the rare hidden activation that rounds to the other BF16
+    neighbour give |y_gpu - y_oracle| <= 1e-3 max|y_oracle|. B = 300 leaves a partial 128-row tile;
+    12800 is the bench's batch (sampled rows)."""
+    rng = np.random.default_rng(21)
+    p = Proposer(392, 256, 336, seed=5)
+    Ws = [p.layer(i)[0].cpu().numpy().astype(np.float64) for i in range(3)]
+    bs = [rng.normal(size=w.shape[0]) * 0.1 for w in Ws]
+    for i in range(3):
+        p.set_layer(i, torch.as_tensor(Ws[i], dtype=torch.float32).cuda(), torch.as_tensor(bs[i], dtype=torch.float32).cuda())
+    X = rng.normal(size=(B, 392)).astype(np.float32)
+    Y = p.forward(torch.as_tensor(X).cuda())
+    torch.cuda.synchronize()
+    Y = Y.cpu().numpy().astype(np.float64)
+    rows = np.arange(B) if B <= 1000 else np.sort(rng.choice(B, 700, replace=False))
+    ref, _ = oprop.forward((Ws, bs), X[rows], bf16_ops=True)
+    assert np.all(np.isfinite(Y))
+    assert np.max(np.abs(Y[rows] - ref)) <= 1e-3 * np.abs(ref).max(), np.max(np.abs(Y[rows] - ref))
+
+
 CURVED = [6 * i + s for i in range(28) for s in (3, 4)]   # v_x, v_y rows (the only curved rows)
 
 
