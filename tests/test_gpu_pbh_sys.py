@@ -296,3 +296,19 @@ def test_width_vs_eps_report():
             lines.append(f"{name:10s} {eps:4.2f}  " + "  ".join(f"{v:9.3e}" for v in acc))
             assert acc[0] <= acc[1] <= acc[2] * (1 + 1e-4) and acc[2] <= acc[3] * (1 + 1e-12)
     print("\n" + "\n".join(lines))
+
+
+def test_graph_capture_matches_direct_call():
+    """leb_graph_capture of the satellite and the 168-state coupled system: replays give the direct call's
+    bits (the launch is allocation-free and capturable for these kinds too)."""
+    for w in (inputs.satellite(T=333, eps=0.1), inputs.quad3d(T=3 * 25, n_quads=14, eps=0.05, coupled=True, N=25)):
+        h, _ = _pair(w)
+        ref = run_gpu(h, w)
+        x, u, r = _t(w.x_nom), _t(w.u_nom), _t(w.radii)
+        gr = binding.Graph(h, x, u, radii=r)
+        for _ in range(3):
+            out = gr.launch()
+        torch.cuda.synchronize()
+        assert int(out["flags"].item()) == 0
+        for k in ("r_lo", "r_hi", "A", "B"):
+            assert np.array_equal(out[k].cpu().numpy(), ref[k]), k
