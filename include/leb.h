@@ -264,6 +264,14 @@ leb_status leb_proposer_get_layer(leb_proposer p, int i, float* W, float* b, voi
 leb_status leb_proposer_set_layer(leb_proposer p, int i, const float* W, const float* b, void* stream);
 /* Raw gradients of the last train step (for checks): dW [out, in], db [out]. */
 leb_status leb_proposer_get_grad(leb_proposer p, int i, float* dW, float* db, void* stream);
+/* Checkpoint / resume of the whole training state (FP32 master weights and biases, Adam moments and
+ * step count, standardisation statistics, angle mask) through a host buffer of leb_proposer_state_size
+ * bytes (a small header of the dimensions first). save copies out and waits for the copies (it
+ * synchronizes the stream); load refuses a buffer of other dimensions (LEB_ERR_INVALID_ARG) and makes a
+ * proposer continue exactly as the saved one would have. */
+leb_status leb_proposer_state_size(leb_proposer p, size_t* bytes);
+leb_status leb_proposer_save_state(leb_proposer p, void* host_buf, size_t bytes, void* stream);
+leb_status leb_proposer_load_state(leb_proposer p, const void* host_buf, size_t bytes, void* stream);
 
 /* ---- allocation-free bounds (quad chains) --------------------------------------------------------- */
 /* The same bounds as leb_bounds for LEB_DYN_QUAD_CHAIN handles, without a workspace argument: for callers

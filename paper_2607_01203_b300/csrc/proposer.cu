@@ -6,6 +6,7 @@
 // accumulation, bias/ReLU epilogues, mean-squared-error gradient, column sums for the bias gradients,
 // and a fused Adam update of the FP32 master weights.
 #include <cmath>
+#include <cstring>
 #include <cuda_bf16.h>
 #include <new>
 #include <vector>
@@ -663,6 +664,76 @@ leb_status leb_proposer_get_grad(leb_proposer p, int i, float* dW, float* db, vo
           cudaMemcpyAsync(db, p->gb[i], (size_t)out * 4, cudaMemcpyDeviceToDevice, s) == cudaSuccess)
              ? LEB_OK
              : LEB_ERR_CUDA;
+}
+
+// ---- checkpoint / resume ----------------------------------------------------------------------
+namespace {
+struct StateHeader {
+  uint32_t magic;   // 'LEBP'
+  int32_t n_in, H, n_out, step;
+  int32_t pad[3];
+};
+constexpr uint32_t kStateMagic = 0x5042454Cu;
+
+// The device arrays of the state in a fixed order, with their sizes in bytes.
+std::vector<std::pair<void*, size_t>> state_arrays(leb_proposer p) {
+  std::vector<std::pair<void*, size_t>> v;
+  const int ins[3] = {p->n_in, p->H, p->H}, outs[3] = {p->H, p->H, p->n_out};
+  for (int i = 0; i < 3; ++i) {
+    const size_t nw = (size_t)ins[i] * outs[i] * 4, nb = (size_t)outs[i] * 4;
+    v.push_back({p->W[i], nw});
+    v.push_back({p->b[i], nb});
+    v.push_back({p->mW[i], nw});
+    v.push_back({p->vW[i], nw});
+    v.push_back({p->mb[i], nb});
+    v.push_back({p->vb[i], nb});
+  }
+  v.push_back({p->norm, (size_t)2 * (p->n_in + p->n_out) * 4});
+  v.push_back({p->periodic, (size_t)p->n_in * sizeof(int)});
+  return v;
+}
+}  // namespace
+
+leb_status leb_proposer_state_size(leb_proposer p, size_t* bytes) {
+  if (!p || !bytes) return LEB_ERR_INVALID_ARG;
+  size_t n = sizeof(StateHeader);
+  for (const auto& a : state_arrays(p)) n += a.second;
+  *bytes = n;
+  return LEB_OK;
+}
+
+leb_status leb_proposer_save_state(leb_proposer p, void* host_buf, size_t bytes, void* stream) {
+  size_t need = 0;
+  if (leb_proposer_state_size(p, &need) != LEB_OK || !host_buf || bytes < need) return LEB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  StateHeader h{kStateMagic, p->n_in, p->H, p->n_out, p->step, {0, 0, 0}};
+  std::memcpy(host_buf, &h, sizeof h);
+  char* dst = static_cast<char*>(host_buf) + sizeof h;
+  for (const auto& a : state_arrays(p)) {
+    if (cudaMemcpyAsync(dst, a.first, a.second, cudaMemcpyDeviceToHost, s) != cudaSuccess) return LEB_ERR_CUDA;
+    dst += a.second;
+  }
+  return cudaStreamSynchronize(s) == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
+}
+
+leb_status leb_proposer_load_state(leb_proposer p, const void* host_buf, size_t bytes, void* stream) {
+  size_t need = 0;
+  if (leb_proposer_state_size(p, &need) != LEB_OK || !host_buf || bytes < need) return LEB_ERR_INVALID_ARG;
+  StateHeader h;
+  std::memcpy(&h, host_buf, sizeof h);
+  if (h.magic != kStateMagic || h.n_in != p->n_in || h.H != p->H || h.n_out != p->n_out || h.step < 0)
+    return LEB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const char* src = static_cast<const char*>(host_buf) + sizeof h;
+  for (const auto& a : state_arrays(p)) {
+    if (cudaMemcpyAsync(a.first, src, a.second, cudaMemcpyHostToDevice, s) != cudaSuccess) return LEB_ERR_CUDA;
+    src += a.second;
+  }
+  // the host buffer may be released once the call returns: wait for the copies out of it
+  if (cudaStreamSynchronize(s) != cudaSuccess) return LEB_ERR_CUDA;
+  p->step = h.step;
+  p->w_version += 1;   // the BF16 inference copies are stale
+  return LEB_OK;
 }
 
 }  // extern "C"

@@ -81,6 +81,29 @@ class Proposer:
         check(lib().leb_proposer_get_grad(self.h, i, _ptr(W), _ptr(b), _stream()), "leb_proposer_get_grad")
         return W, b
 
+    def state_bytes(self) -> bytes:
+        """The whole training state (weights, Adam moments and step, standardisation, angle mask)."""
+        n = C.c_size_t()
+        check(lib().leb_proposer_state_size(self.h, C.byref(n)), "leb_proposer_state_size")
+        buf = (C.c_char * n.value)()
+        check(lib().leb_proposer_save_state(self.h, buf, n.value, _stream()), "leb_proposer_save_state")
+        return bytes(buf)
+
+    def load_state_bytes(self, data: bytes):
+        buf = (C.c_char * len(data)).from_buffer_copy(data)
+        check(lib().leb_proposer_load_state(self.h, buf, len(data), _stream()), "leb_proposer_load_state")
+
+    def save(self, path: str):
+        """Checkpoint to a .pt file (torch.save of the dimensions and the raw state)."""
+        torch.save({"dims": torch.tensor([self.n_in, self.n_hidden, self.n_out]),
+                    "state": torch.frombuffer(bytearray(self.state_bytes()), dtype=torch.uint8)}, path)
+
+    def load(self, path: str):
+        ck = torch.load(path, weights_only=True)
+        if tuple(ck["dims"].tolist()) != (self.n_in, self.n_hidden, self.n_out):
+            raise ValueError(f"checkpoint dimensions {ck['dims'].tolist()} differ from this proposer's")
+        self.load_state_bytes(ck["state"].numpy().tobytes())
+
     def fit(self, X, Y, epochs: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0):
         """Mini-batch training loop (batch order from torch.randperm; every step runs in the kernels)."""
         g = torch.Generator(device="cpu").manual_seed(seed)

@@ -129,3 +129,34 @@ def test_trains_on_certified_bounds_and_gains_over_random_choice():
     print(f"gain test: excess certified width over the best of 64 — screened {gap_s:.4f}, random {gap_r:.4f}")
     assert best_screened.mean() < best_random.mean()
     assert gap_s < 0.85 * gap_r, (gap_s, gap_r)
+
+
+def test_checkpoint_resume_continues_exactly(tmp_path):
+    """Save after some steps, keep training; a fresh proposer loaded from the checkpoint and trained on the
+    same batches ends with the same bits (weights, Adam state and step count all restored); a checkpoint
+    of other dimensions is refused."""
+    rng = np.random.default_rng(22)
+    n_in, H, n_out, B = 24, 32, 16, 64
+    X = [torch.as_tensor(rng.normal(size=(B, n_in)).astype(np.float32)).cuda() for _ in range(6)]
+    Y = [torch.as_tensor(rng.normal(size=(B, n_out)).astype(np.float32)).cuda() for _ in range(6)]
+    a = Proposer(n_in, H, n_out, seed=9)
+    a.fit_norm(X[0], Y[0])
+    for k in range(3):
+        a.train_step(X[k], Y[k], 1e-3)
+    path = str(tmp_path / "proposer.pt")
+    a.save(path)
+    for k in range(3, 6):
+        a.train_step(X[k], Y[k], 1e-3)
+    b = Proposer(n_in, H, n_out, seed=123)   # other initial weights: everything must come from the file
+    b.load(path)
+    for k in range(3, 6):
+        b.train_step(X[k], Y[k], 1e-3)
+    torch.cuda.synchronize()
+    for i in range(3):
+        (Wa, ba), (Wb, bb) = a.layer(i), b.layer(i)
+        assert torch.equal(Wa, Wb) and torch.equal(ba, bb)
+    assert torch.equal(a.forward(X[0]), b.forward(X[0]))
+    with pytest.raises(ValueError):
+        Proposer(n_in, H + 8, n_out).load(path)
+    with pytest.raises(binding.LebError):
+        Proposer(n_in, H + 8, n_out).load_state_bytes(a.state_bytes())
