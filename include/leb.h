@@ -319,6 +319,11 @@ leb_status leb_selftest_point_enclosures(const float* x, int n, float* out_sin, 
  * device points x (a degenerate interval each), writing [lo, hi] pairs to out_tan and out_sec ([n, 2]
  * device arrays). Points outside (-1.5707, 1.5707) give [-inf, +inf]. */
 leb_status leb_selftest_tan_sec(const float* x, int n, float* out_tan, float* out_sec, void* stream);
+/* Runs the kernels' bounded mbarrier wait, with limit_ns (at most 4 s), on a barrier that nothing
+ * arrives at: the wait gives up, the kernel ORs LEB_ASYNC_TIMEOUT into *dev_flags (cleared first),
+ * writes the nanoseconds it waited to *dev_waited_ns and returns; the context stays usable. */
+leb_status leb_selftest_wait_timeout(int* dev_flags, unsigned long long limit_ns, unsigned long long* dev_waited_ns,
+                                     void* stream);
 
 const char* leb_status_string(leb_status st);
 const char* leb_version(void);

@@ -3,6 +3,7 @@
 #include "internal.h"
 #include "interval.cuh"
 #include "mlp_math.cuh"
+#include "sync.cuh"
 
 namespace leb {
 __global__ void point_enclosure_kernel(const float* x, int n, float2* s, float2* c, float2* th) {
@@ -21,7 +22,28 @@ __global__ void tan_sec_kernel(const float* x, int n, float2* t, float2* sc) {
   t[i] = make_float2(a.lo, a.hi);
   sc[i] = make_float2(b.lo, b.hi);
 }
+// A wait that nothing ends: an mbarrier expecting one arrival that never comes, waited on with the
+// kernels' bounded wait and the given limit. It must give up, report LEB_ASYNC_TIMEOUT and return.
+__global__ void wait_timeout_kernel(int* flags, unsigned long long limit_ns, unsigned long long* waited_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  mbar_fence_init();
+  const unsigned long long t0 = global_ns();
+  const bool ok = mbar_wait_for(&bar, 0u, limit_ns);
+  *waited_ns = global_ns() - t0;
+  if (!ok) atomicOr(flags, LEB_ASYNC_TIMEOUT);
+}
 }  // namespace leb
+
+extern "C" leb_status leb_selftest_wait_timeout(int* dev_flags, unsigned long long limit_ns,
+                                                unsigned long long* dev_waited_ns, void* stream) {
+  if (!dev_flags || !dev_waited_ns || limit_ns > 4000000000ull) return LEB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(dev_flags, 0, sizeof(int), s) != cudaSuccess) return LEB_ERR_CUDA;
+  leb::wait_timeout_kernel<<<1, 32, 0, s>>>(dev_flags, limit_ns, dev_waited_ns);
+  return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
+}
 
 extern "C" leb_status leb_selftest_point_enclosures(const float* x, int n, float* out_sin, float* out_cos,
                                                      float* out_tanh, void* stream) {
