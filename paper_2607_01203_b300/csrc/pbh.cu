@@ -180,6 +180,53 @@ __device__ __forceinline__ void write_AB(const PbhArgs& a, const Item& it, const
   }
 }
 
+// The same A_k and B_k in two phases, for writers that are few: phase 1 stores zeros over both matrices
+// (16-byte stores), phase 2 the nonzeros (at most 6 per row of A, 2 per row of B), one (row, slot) per
+// thread. The caller orders phase 1 before phase 2 with a barrier among the writing threads; the zero
+// stores keep their lines in L2, so the nonzero stores merge there.
+__device__ __forceinline__ void zero_fill(float* p, long long count, int tid, int nthr) {
+  if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+    float4* p4 = reinterpret_cast<float4*>(p);
+    const long long n4 = count >> 2;
+    for (long long i = tid; i < n4; i += nthr) p4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long long i = (n4 << 2) + tid; i < count; i += nthr) p[i] = 0.f;
+  } else {
+    for (long long i = tid; i < count; i += nthr) p[i] = 0.f;
+  }
+}
+
+__device__ __forceinline__ void write_AB_zero(const PbhArgs& a, const Item& it, int tid, int nthr) {
+  const long long nx = 6LL * it.nq, nu = 2LL * it.nq;
+  if (a.A) zero_fill(a.A + it.a_off, nx * nx, tid, nthr);
+  if (a.B) zero_fill(a.B + it.b_off, nx * nu, tid, nthr);
+}
+
+__device__ __forceinline__ void nz_slot(const RowNz& r, int k, int& c, float& v) {
+  c = k == 0 ? r.c0 : k == 1 ? r.c1 : k == 2 ? r.c2 : k == 3 ? r.c3 : k == 4 ? r.c4 : r.c5;
+  v = k == 0 ? r.v0 : k == 1 ? r.v1 : k == 2 ? r.v2 : k == 3 ? r.v3 : k == 4 ? r.v4 : r.v5;
+}
+
+__device__ __forceinline__ void write_AB_nz(const PbhArgs& a, const Item& it, const QuadA* qa, int tid, int nthr) {
+  const QuadConsts& K = a.k;
+  const int nq = it.nq, nx = 6 * nq, nu = 2 * nq;
+  if (a.A)
+    for (int e = tid; e < 6 * nx; e += nthr) {
+      const int l = e / 6;
+      int c;
+      float v;
+      nz_slot(a_row(l, nq, qa[l / 6], K), e - 6 * l, c, v);
+      if (c >= 0) a.A[it.a_off + (long long)l * nx + c] = v;
+    }
+  if (a.B)
+    for (int e = tid; e < 2 * nx; e += nthr) {
+      const int l = e >> 1;
+      int c;
+      float v;
+      nz_slot(b_row(l, qa[l / 6], K), e & 1, c, v);
+      if (c >= 0) a.B[it.b_off + (long long)l * nu + c] = v;
+    }
+}
+
 __device__ __forceinline__ void emit_row(const PbhArgs& a, const Item& it, int l, ivl R, bool bad) {
   if (bad || !finite_ivl(R)) R = iv(-CUDART_INF_F, CUDART_INF_F);
   const long long o = it.x_off + l;
@@ -354,8 +401,17 @@ struct StageMeta {
 
 __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, int stage_bytes_cap) {
   extern __shared__ __align__(128) unsigned char sraw[];
+  // Warp roles: warp 0 streams the generators (one thread), warp 1 writes A_k and B_k when they are
+  // wanted (the writer), the others reduce the set rows and evaluate Eq. 15 (the consumers). The writer
+  // takes a finished timestep's per-quadrotor values from its shared-memory slot while the consumers go
+  // on with the next timesteps, so the A/B stores overlap the generator stream instead of pausing it.
+  __shared__ Item s_item[2];                  // timestep handed to the writer, per slot (nq < 0: end)
+  __shared__ __align__(8) uint64_t wbar[4];   // [0..1] slot filled (consumers -> writer), [2..3] slot written
+  __shared__ int s_wok;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int ncons = nwarps - 1, ncthr = ncons * 32;
+  const bool writer = (a.A != nullptr || a.B != nullptr) && nwarps >= 3;
+  const int c_warp0 = writer ? 2 : 1;         // first consumer warp
+  const int ncons = nwarps - c_warp0, ncthr = ncons * 32;
   const int n_max = 8 * a.nq;
   unsigned char* stages = sraw;  // S * stage_bytes_cap, 128-byte aligned
   float* s_lo = reinterpret_cast<float*>(sraw + (size_t)S * stage_bytes_cap);  // [2][n_max]
@@ -371,11 +427,29 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], ncons);
     }
+    for (int b = 0; b < 4; ++b) mbar_init(&wbar[b], 1);
     mbar_fence_init();
   }
   __syncthreads();
 
-  if (warp == 0) {
+  if (warp == 1 && writer) {
+    // ---- writer: A_k, B_k rows of each finished timestep, slots in turn ----------------------------
+    uint32_t par = 0;
+    for (int slot = 0;; slot ^= 1) {
+      if (!mbar_wait(&wbar[slot], (par >> slot) & 1u)) {
+        if (lane == 0) atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
+        break;
+      }
+      par ^= 1u << slot;
+      const Item it = s_item[slot];
+      if (it.nq < 0) break;
+      write_AB_zero(a, it, lane, 32);
+      __syncwarp();
+      write_AB_nz(a, it, s_qa + slot * a.nq, lane, 32);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&wbar[2 + slot]);
+    }
+  } else if (warp == 0) {
     if (lane == 0) {
       // ---- producer --------------------------------------------------------------------------
       uint32_t k = 0;
@@ -418,9 +492,18 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
     __syncwarp();
   } else {
     // ---- consumers ---------------------------------------------------------------------------
-    const int cw = warp - 1, ctid = threadIdx.x - 32;
+    const int cw = warp - c_warp0, ctid = threadIdx.x - 32 * c_warp0;
     uint32_t k = 0;
     int slot = 0;
+    uint32_t used = 0, wpar = 0;   // writer slots handed over, and their completion parities
+    // thread 0: wait until the writer is done with a slot (if it was handed over); true if free
+    auto slot_free = [&](int sl) -> bool {
+      if (!((used >> sl) & 1u)) return true;
+      const bool r = mbar_wait(&wbar[2 + sl], (wpar >> sl) & 1u);
+      wpar ^= 1u << sl;
+      used &= ~(1u << sl);
+      return r;
+    };
     Item it{};
     bool ok = true;  // this thread saw only finite rows
     for (;;) {
@@ -431,13 +514,31 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
         break;
       }
       const StageMeta m = meta[s];
-      if (m.t < 0) break;
+      if (m.t < 0) {
+        // tell the writer there is nothing more (after it is done with the slot's last timestep)
+        if (writer && ctid == 0) {
+          const bool fr = slot_free(slot);
+          s_item[slot].nq = -1;
+          mbar_arrive(&wbar[slot]);
+          if (!fr) atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
+        }
+        break;
+      }
       if (m.chunk == 0) it = make_item(a, m.t);  // the item changes only at a timestep's first chunk
       const float* xn = a.x_nom + it.x_off;
       const float* un = a.u_nom + it.u_off;
       float* lo = s_lo + slot * n_max;
       float* hi = s_hi + slot * n_max;
       QuadA* qa = s_qa + slot * a.nq;
+      if (m.chunk == 0 && writer) {
+        // the slot's per-quadrotor values are rewritten below: the writer must be done with them
+        if (ctid == 0) s_wok = slot_free(slot) ? 1 : 0;
+        bar_sync(2, ncthr);
+        if (!s_wok) {
+          if (ctid == 0) atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
+          break;
+        }
+      }
       if (m.chunk == 0) compute_qa(xn, un, it.nq, a.k, qa, ctid, ncthr);
       const int p = it.n_gen;
       const int rows_per = m.rows_per;
@@ -453,7 +554,18 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
         const bool bad = bar_sync_or(1, ncthr, !ok);
         ok = true;
         pbh_rows(a, it, xn, un, lo, hi, qa, bad, ctid, ncthr);
-        write_AB(a, it, qa, cw, ncons, lane);
+        if (writer) {
+          // every consumer's qa values are in place (the barrier above): hand the timestep over
+          if (ctid == 0) {
+            s_item[slot] = it;
+            mbar_arrive(&wbar[slot]);
+            used |= 1u << slot;
+          }
+        } else {
+          write_AB_zero(a, it, ctid, ncthr);
+          bar_sync(2, ncthr);
+          write_AB_nz(a, it, qa, ctid, ncthr);
+        }
         if (bad && ctid == 0) atomicOr(a.flags, LEB_ASYNC_NONFINITE);
         slot ^= 1;
       }
@@ -508,7 +620,10 @@ cudaError_t launch_pbh(const Ctx& c, const PbhArgs& a, const PbhPlan& p, cudaStr
     const size_t smem = pbh_tma_smem(a, p.stages);
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(pbh_zono_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      // the opt-in limit covers the kernel's static shared memory too
+      cudaFuncAttributes fa{};
+      const size_t stat = cudaFuncGetAttributes(&fa, pbh_zono_tma_kernel) == cudaSuccess ? fa.sharedSizeBytes : 1024;
+      cudaFuncSetAttribute(pbh_zono_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(227 * 1024 - stat));
       attr = true;
     }
     pbh_zono_tma_kernel<<<grid, p.block, smem, s>>>(a, p.stages, kPbhStageCap);

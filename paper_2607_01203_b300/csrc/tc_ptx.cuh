@@ -132,6 +132,17 @@ __device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, float v[16]) {
       : "memory");
 }
 
+// 8 columns without the wait, written straight into float registers.
+__device__ __forceinline__ void tmem_ld8_async(uint32_t taddr, float v[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_regs_fence8(float v[8]) {
+  asm volatile("" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]));
+}
+
 // Ties 16 registers filled by a *_nowait TMEM load to a point after tmem_wait_ld(): reads of v placed after
 // this call cannot be moved above it (the empty volatile statement redefines them and is not reordered
 // with the wait).
