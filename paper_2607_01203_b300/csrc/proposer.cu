@@ -50,30 +50,37 @@ __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__floa
 // (the output, optionally taken back out of its standardisation: y std + mean).
 // Every wait is bounded; a wait that runs out leaves the tile's outputs NaN.
 // ---------------------------------------------------------------------------------------------------
-constexpr int kPtStages = 2;
+constexpr int kPtMaxStages = 8;
 constexpr int kPtATile = 128 * 64 * 2;     // 16 KB
-constexpr int kPtBTile = 512 * 64 * 2;     // 64 KB (N <= 512)
-constexpr int kPtSmem = 1024 + kPtStages * (kPtATile + kPtBTile) + 64;
+constexpr int kPtSmem = 227 * 1024 - 64;   // the ring takes as many stages of (16 KB + N x 128 B) as fit
+
+// Stages of the K ring for N output columns: as many as fit the shared memory, at most kPtMaxStages.
+static inline int pt_stages(int N) {
+  const int per = kPtATile + N * 128;
+  const int st = (kPtSmem - 1024 - 2 * kPtMaxStages * 8 - 8) / per;
+  return st < kPtMaxStages ? st : kPtMaxStages;
+}
 
 __global__ void __launch_bounds__(128, 1) prop_tc_gemm_kernel(const __grid_constant__ CUtensorMap amap,
                                                               const __grid_constant__ CUtensorMap wmap, int M, int N,
                                                               int K, int nchunk, const float* bias, int relu,
                                                               __nv_bfloat16* outb, float* outf, int ldo,
-                                                              const float* omean, const float* ostd) {
+                                                              const float* omean, const float* ostd, int stages) {
   extern __shared__ uint8_t sraw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sraw) + 1023) & ~uintptr_t(1023));
+  const int btile = N * 128;                              // N rows x 64 K x 2 bytes (a multiple of 1 KB)
   uint8_t* At = base;                                        // [stages][16 KB]
-  uint8_t* Bt = base + kPtStages * kPtATile;                 // [stages][64 KB]
-  uint64_t* full = reinterpret_cast<uint64_t*>(Bt + kPtStages * kPtBTile);
-  uint64_t* empty = full + kPtStages;
-  uint64_t* acc = empty + kPtStages;
+  uint8_t* Bt = base + stages * kPtATile;                 // [stages][N x 128 B]
+  uint64_t* full = reinterpret_cast<uint64_t*>(Bt + stages * btile);
+  uint64_t* empty = full + stages;
+  uint64_t* acc = empty + stages;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * 128, nK = (K + 63) / 64, nb = N / nchunk;
   const uint32_t tcols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : (N <= 256 ? 256 : 512)));
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kPtStages; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -91,22 +98,22 @@ __global__ void __launch_bounds__(128, 1) prop_tc_gemm_kernel(const __grid_const
     tma_prefetch_desc(&amap);
     tma_prefetch_desc(&wmap);
     for (int kb = 0; kb < nK; ++kb) {
-      const int s = kb % kPtStages;
-      if (kb >= kPtStages && !mbar_wait(&empty[s], ((kb / kPtStages) - 1) & 1u)) { s_fail = 1; break; }
+      const int s = kb % stages;
+      if (kb >= stages && !mbar_wait(&empty[s], ((kb / stages) - 1) & 1u)) { s_fail = 1; break; }
       mbar_arrive_expect_tx(&full[s], abytes + bbytes);
       tma_load_2d(At + s * kPtATile, &amap, kb * 64, m0, &full[s]);
-      for (int c = 0; c < nchunk; ++c) tma_load_2d(Bt + s * kPtBTile + c * nb * 128, &wmap, kb * 64, c * nb, &full[s]);
+      for (int c = 0; c < nchunk; ++c) tma_load_2d(Bt + s * btile + c * nb * 128, &wmap, kb * 64, c * nb, &full[s]);
     }
     // every posted copy lands before the block can exit
-    for (int kb = nK > kPtStages ? nK - kPtStages : 0; kb < nK; ++kb) mbar_wait(&full[kb % kPtStages], (kb / kPtStages) & 1u);
+    for (int kb = nK > stages ? nK - stages : 0; kb < nK; ++kb) mbar_wait(&full[kb % stages], (kb / stages) & 1u);
   } else if (warp == 1 && lane == 0) {
     const uint32_t idesc = idesc_f16(128, nb, 1);
     bool ok = true;
     for (int kb = 0; kb < nK && ok; ++kb) {
-      const int s = kb % kPtStages;
-      if (!mbar_wait(&full[s], (kb / kPtStages) & 1u)) { ok = false; s_fail = 1; break; }
+      const int s = kb % stages;
+      if (!mbar_wait(&full[s], (kb / stages) & 1u)) { ok = false; s_fail = 1; break; }
       tc_fence_after();
-      const uint32_t a0 = smem_u32(At + s * kPtATile), b0 = smem_u32(Bt + s * kPtBTile);
+      const uint32_t a0 = smem_u32(At + s * kPtATile), b0 = smem_u32(Bt + s * btile);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
         for (int c = 0; c < nchunk; ++c)
@@ -255,12 +262,20 @@ __global__ void prop_destandardize_kernel(long long total, int n, const float* y
 }
 
 // Standardised inputs straight into the BF16 operand of the first layer.
-__global__ void prop_standardize_bf16_kernel(long long total, int n, const float* X, const int* periodic,
-                                             const float* mean, const float* stdv, __nv_bfloat16* Xb) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(e % n);
-    const float x = periodic[j] ? wrap_pi(X[e]) : X[e];
-    Xb[e] = __float2bfloat16_rn((x - mean[j]) / stdv[j]);
+__global__ void prop_standardize_bf16_kernel(int B, int n, const float* X, const int* periodic, const float* mean,
+                                             const float* stdv, __nv_bfloat16* Xb) {
+  // a warp per row, column pairs per lane (n even)
+  const int warps = (int)(blockDim.x >> 5), lane = threadIdx.x & 31;
+  for (int row = blockIdx.x * warps + (threadIdx.x >> 5); row < B; row += gridDim.x * warps) {
+    const float2* xr = reinterpret_cast<const float2*>(X + (long long)row * n);
+    __nv_bfloat162* yr = reinterpret_cast<__nv_bfloat162*>(Xb + (long long)row * n);
+    for (int c = lane; c < (n >> 1); c += 32) {
+      const int j = 2 * c;
+      float2 x = xr[c];
+      if (periodic[j]) x.x = wrap_pi(x.x);
+      if (periodic[j + 1]) x.y = wrap_pi(x.y);
+      yr[c] = __floats2bfloat162_rn((x.x - mean[j]) / stdv[j], (x.y - mean[j + 1]) / stdv[j + 1]);
+    }
   }
 }
 
@@ -425,7 +440,8 @@ static bool forward_tc(leb_proposer p, int B, const float* X, float* ws, float* 
   const size_t o3 = (o2 + ((size_t)B * H + 1) / 2 + 3) & ~size_t(3);
   const size_t end = o3 + ((size_t)B * H + 1) / 2;
   // TMA needs 16-byte aligned operands, the epilogue stores Y rows as float4
-  if (!p->tc || end > ws_floats(p, B) || ((reinterpret_cast<uintptr_t>(ws) | reinterpret_cast<uintptr_t>(Y)) & 15u))
+  if (!p->tc || end > ws_floats(p, B) || ((reinterpret_cast<uintptr_t>(ws) | reinterpret_cast<uintptr_t>(Y)) & 15u) ||
+      (reinterpret_cast<uintptr_t>(X) & 7u))
     return false;
   __nv_bfloat16* Xb = reinterpret_cast<__nv_bfloat16*>(ws + o1);
   __nv_bfloat16* H1 = reinterpret_cast<__nv_bfloat16*>(ws + o2);
@@ -439,17 +455,16 @@ static bool forward_tc(leb_proposer p, int B, const float* X, float* ws, float* 
                                                                         p->Wb[1], p->Wb[2]);
     p->wb_version = p->w_version;
   }
-  prop_standardize_bf16_kernel<<<blocks_for((long long)B * n_in), 256, 0, s>>>((long long)B * n_in, n_in, X,
-                                                                                 p->periodic, p->norm, p->norm + n_in,
-                                                                                 Xb);
+  const int sblocks = (int)std::min<long long>(((long long)B + 7) / 8, 148LL * 16);
+  prop_standardize_bf16_kernel<<<sblocks, 256, 0, s>>>(B, n_in, X, p->periodic, p->norm, p->norm + n_in, Xb);
   const int grid = (B + 127) / 128;
   const float* omean = p->norm + 2 * n_in;
   prop_tc_gemm_kernel<<<grid, 128, kPtSmem, s>>>(m0, p->wmap[0], B, H, n_in, p->nchunk[0], p->b[0], 1, H1, nullptr, H,
-                                                 nullptr, nullptr);
+                                                 nullptr, nullptr, pt_stages(H));
   prop_tc_gemm_kernel<<<grid, 128, kPtSmem, s>>>(m1, p->wmap[1], B, H, H, p->nchunk[1], p->b[1], 1, H2, nullptr, H,
-                                                 nullptr, nullptr);
+                                                 nullptr, nullptr, pt_stages(H));
   prop_tc_gemm_kernel<<<grid, 128, kPtSmem, s>>>(m2, p->wmap[2], B, n_out, H, p->nchunk[2], p->b[2], 0, nullptr, Y,
-                                                 n_out, omean, omean + n_out);
+                                                 n_out, omean, omean + n_out, pt_stages(n_out));
   *st = cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
   return true;
 }
