@@ -280,36 +280,58 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       constexpr int GS = 8 * NR;                 // rows per group: whole groups of NR, whole 8-column loads
       const int Kt = a.widths[target];
       // ---- prologue: B = (W_target rows o s_{target-1}) (difference form for output rows) ----------
+      // Both neurons of the thread go through the rows together, and the W_target entries of the next
+      // 8-row chunk (the row groups it touches, at most 4) are loaded while a chunk is written.
       {
         const int Kp = (Kt + 63) & ~63;
+        const int nu = nrn0 + 256 < Kp ? 2 : (nrn0 < Kp ? 1 : 0);   // neurons of this thread in the layer
+        if (nu > 0) {
+          bool live[2];
+          float sl[2], su[2], dd[2];
+          const float* wcol[2];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int j = nrn0 + 256 * u;
-          if (j < Kp) {
-            const bool live = j < Kt;
-            const long long o = (long long)t * a.H + a.hoff[target - 1] + (live ? j : 0);
-            const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f, dd = live ? a.D[o] : 0.f;
-            const float* wcol = a.W_target + (live ? j : 0);
-            float wv = 0.f;   // the W_target entry of the current row group, carried across chunks
-#pragma unroll 1
-            for (int rb = 0; rb < 128; rb += 8) {
-              const int off = rb % NR;
-              const uint32_t lm = NR == 3 ? (0x49u << ((3 - off) % 3)) & 0xFFu : (off == 0 ? 0x55u : 0xAAu);
-              const uint32_t jm = NR == 3 ? (0x49u << ((5 - off) % 3)) & 0xFFu : 0u;
-              float v[8];
+          for (int u = 0; u < 2; ++u) {
+            const int j = nrn0 + 256 * u;
+            live[u] = u < nu && j < Kt;
+            const long long o = (long long)t * a.H + a.hoff[target - 1] + (live[u] ? j : 0);
+            sl[u] = live[u] ? a.sL[o] : 0.f;
+            su[u] = live[u] ? a.sU[o] : 0.f;
+            dd[u] = live[u] ? a.D[o] : 0.f;
+            wcol[u] = a.W_target + (live[u] ? j : 0);
+          }
+          // W_target entries of the row groups rb / NR .. rb / NR + 3 (0 for a group past the valid rows)
+          auto wload = [&](int rb, float2 (&w)[4]) {
 #pragma unroll
-              for (int e = 0; e < 8; ++e) {
-                const bool isL = (lm >> e) & 1u, isJ = (jm >> e) & 1u;
-                if (isL) {
-                  const int r = rb + e;
-                  wv = (live && r + NR - 1 < nrows) ? __ldg(wcol + (long long)((row0 + r) / NR) * Kt) : 0.f;
-                }
-                const float lam = wv, jd = NR == 3 ? lam * dd : 0.f;
-                const bool useL = isL == !signbit(lam);
-                v[e] = isJ ? jd : fmaf(lam, useL ? sl : su, -jd);
-              }
-              put8(rb, j, v);
+            for (int i = 0; i < 4; ++i) {
+              const int g = rb / NR + i;
+              const bool grp = NR * g + NR - 1 < nrows;
+              const long long wo = (long long)(row0 / NR + g) * Kt;
+              w[i].x = (live[0] && grp) ? __ldg(wcol[0] + wo) : 0.f;
+              w[i].y = (live[1] && grp) ? __ldg(wcol[1] + wo) : 0.f;
             }
+          };
+          float2 wn[4];
+          wload(0, wn);
+#pragma unroll 1
+          for (int rb = 0; rb < 128; rb += 8) {
+            const float2 wc[4] = {wn[0], wn[1], wn[2], wn[3]};
+            if (rb + 8 < 128) wload(rb + 8, wn);
+            const int off = rb % NR;
+            const uint32_t lm = NR == 3 ? (0x49u << ((3 - off) % 3)) & 0xFFu : (off == 0 ? 0x55u : 0xAAu);
+            const uint32_t jm = NR == 3 ? (0x49u << ((5 - off) % 3)) & 0xFFu : 0u;
+            float v0[8], v1[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const bool isL = (lm >> e) & 1u, isJ = (jm >> e) & 1u;
+              const int gi = (off + e) / NR;   // group of row rb + e, relative to rb / NR
+              const float2 lam = gi == 0 ? wc[0] : (gi == 1 ? wc[1] : (gi == 2 ? wc[2] : wc[3]));
+              const float jd0 = NR == 3 ? lam.x * dd[0] : 0.f, jd1 = NR == 3 ? lam.y * dd[1] : 0.f;
+              const bool useL0 = isL == !signbit(lam.x), useL1 = isL == !signbit(lam.y);
+              v0[e] = isJ ? jd0 : fmaf(lam.x, useL0 ? sl[0] : su[0], -jd0);
+              v1[e] = isJ ? jd1 : fmaf(lam.y, useL1 ? sl[1] : su[1], -jd1);
+            }
+            put8(rb, nrn0, v0);
+            if (nu > 1) put8(rb, nrn0 + 256, v1);
           }
         }
         operand_ready();
