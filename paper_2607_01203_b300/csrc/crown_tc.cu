@@ -613,6 +613,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
         }
         return true;
       };
+      // the displacement-box columns of this warp's chunks are pulled into L1 first, so that only the
+      // first chunk waits for them
+      {
+        const int c = lane >> 2;
+        const int j = c0 + 32 * cq + 64 * c + ((lane & 1) ? 31 : 0);
+        if (j < c0 + nc) prefetch_l1(((lane & 2) ? dhi : dlo) + j);
+      }
       // 32-column chunks j0 = c0 + 32 cq + 64 c
       for (int j0 = c0 + 32 * cq; j0 < c0 + nc; j0 += 64) {
         float L0[32];

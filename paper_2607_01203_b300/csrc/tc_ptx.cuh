@@ -153,6 +153,9 @@ __device__ __forceinline__ void tmem_regs_fence16(float v[16]) {
                  "+f"(v[15]));
 }
 
+// Pulls the line holding p into L1 (no register result, no wait).
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 // 4-byte asynchronous copy global -> shared (cp.async, L1-cached); completed by cp_async_wait_all().
 __device__ __forceinline__ void cp_async4(void* dst_smem, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
