@@ -722,7 +722,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
           break;
         }
       }
-      // final stage: concretise over the box
+      // final stage: concretise over the box. The values the finalisation reads from global memory (the
+      // nominal's enclosure for hidden targets, the timestep's bad-input word) go to L1 meanwhile.
+      if (!OUT && ri.bound) {
+        const long long o = (long long)t * a.H + a.hoff[target] + ri.idx;
+        prefetch_l1(a.zhat + o);
+        prefetch_l1(a.zrad + o);
+      }
+      if (lane == 0) prefetch_l1(a.bad + t);
       float2 sum = z2;
       const int N0 = a.widths[0], split0 = stage_split(0);
       for (int h = 0; h < (N0 > split0 ? 2 : 1) && ok; ++h, ++jc)
