@@ -271,6 +271,26 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       *reinterpret_cast<uint4*>(Bop + b_off8(r0, j)) = q;
     };
 
+    // Pulls the thread's two neurons' entries of hidden layer hl's vectors (sL, sU, D and, with taus,
+    // tL, tU) of timestep t into L1; issued before a wait for the tensor cores, whose work hides it.
+    auto pf_vec = [&](int t, int hl, bool taus) {
+      const int width = a.widths[hl + 1];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int j = nrn0 + 256 * u;
+        if (j < width) {
+          const long long o = (long long)t * a.H + a.hoff[hl] + j;
+          prefetch_l1(a.sL + o);
+          prefetch_l1(a.sU + o);
+          prefetch_l1(a.D + o);
+          if (taus) {
+            prefetch_l1(a.tL + o);
+            prefetch_l1(a.tU + o);
+          }
+        }
+      }
+    };
+
     // Rows of a tile come in groups of NR (output: lower, upper, Jacobian; hidden: lower, upper) and a
     // tile starts on a group, so the role of row r0 + e with r0 a multiple of 8 NR is e mod NR: a
     // compile-time constant in the unrolled loops. Rows past the tile's valid rows carry zero cotangents
@@ -338,6 +358,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       }
       // ---- forward stages k = target-1 .. 1 --------------------------------------------------------
       for (int k = target - 1; k >= 1; --k) {
+        pf_vec(t, k - 1, false);
         if (!wait_acc()) return false;
         const int N = a.widths[k];             // neurons of hidden layer k-1 (rows of this product)
         const int Np = (N + 63) & ~63;
@@ -407,6 +428,9 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       }
       // ---- G_{-1} from lambda_{-1} (neurons = inputs m < n) --------------------------------------------
       {
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          if (nrn0 + 256 * u < n) prefetch_l1(a.radii + (long long)t * n + nrn0 + 256 * u);
         if (!wait_acc()) return false;
         const int np = (n + 63) & ~63;
 #pragma unroll
@@ -455,6 +479,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       // ---- backward stages k = 0 .. target-1 -------------------------------------------------------
       // The thread's two neurons go side by side through packed FP32x2 arithmetic.
       for (int k = 0; k < target; ++k) {
+        pf_vec(t, k, true);
         if (!wait_acc()) return false;
         const int N = a.widths[k + 1];            // neurons of hidden layer k
         const bool last = k == target - 1;
