@@ -169,6 +169,16 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------------
+class E2EParts:
+    """One pass of a form through the public API from pinned host buffers, in three parts that a caller
+    can put on three streams: the host-to-device copies of its inputs, the library call(s), and the
+    device-to-host copies of its results (byte counts of both directions per pass)."""
+
+    def __init__(self, h2d, compute, d2h, h2d_bytes, d2h_bytes):
+        self.h2d, self.compute, self.d2h = h2d, compute, d2h
+        self.h2d_bytes, self.d2h_bytes = h2d_bytes, d2h_bytes
+
+
 class Form:
     """One form of the hot path: set-up (untimed), run (one pass), its timed main kernel and extras."""
     name = ""
@@ -177,6 +187,21 @@ class Form:
 
     def units(self):
         return 0
+
+    def e2e_parts(self):
+        return None
+
+    def e2e(self, steps):
+        """The form alone end to end, copies and call in order on the current stream: ms per pass."""
+        p = self.e2e_parts()
+        if p is None:
+            return 0.0, 0, 0
+
+        def one():
+            p.h2d()
+            p.compute()
+            p.d2h()
+        return timed_loop(self.torch, one, steps), p.h2d_bytes, p.d2h_bytes
 
 
 class PbhForm(Form):
@@ -214,8 +239,8 @@ class PbhForm(Form):
                 "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
                 "bytes_per_unit": PBH_BYTES_PER_TS, "units_per_launch": self.T // max(launches, 1)}
 
-    def e2e(self, steps):
-        """The same work through the C ABI from pinned host buffers, copies inside the timed region."""
+    def e2e_parts(self):
+        """The same work through the C ABI from pinned host buffers."""
         torch = self.torch
         hx = torch.as_tensor(self.w.x_nom).pin_memory()
         hu = torch.as_tensor(self.w.u_nom).pin_memory()
@@ -223,17 +248,19 @@ class PbhForm(Form):
         out_h = {k: torch.empty(self.out[k].shape).pin_memory() for k in ("r_lo", "r_hi", "A", "B")}
         dx, du, dG = torch.empty_like(self.x), torch.empty_like(self.u), torch.empty_like(self.G)
 
-        def one():
+        def h2d():
             dx.copy_(hx, non_blocking=True)
             du.copy_(hu, non_blocking=True)
             dG.copy_(hG, non_blocking=True)
-            o = self.handle.bounds(dx, du, G=dG, out=self.out)
+
+        def compute():
+            self.handle.bounds(dx, du, G=dG, out=self.out)
+
+        def d2h():
             for k, v in out_h.items():
-                v.copy_(o[k], non_blocking=True)
-        ms = timed_loop(torch, one, steps)
-        h2d = (hx.numel() + hu.numel() + hG.numel()) * 4
-        d2h = sum(v.numel() * 4 for v in out_h.values())
-        return ms, h2d, d2h
+                v.copy_(self.out[k], non_blocking=True)
+        return E2EParts(h2d, compute, d2h, (hx.numel() + hu.numel() + hG.numel()) * 4,
+                        sum(v.numel() * 4 for v in out_h.values()))
 
     def oracle_seconds_per_unit(self, budget_s):
         """The FP64 oracle as it stands on a sample of this batch's timesteps: seconds per timestep."""
@@ -304,21 +331,25 @@ class CrownForm(Form):
                 "kernel": kernel, "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
                 "flop_per_unit": crown_flop_per_ts(), "units_per_step": self.T}
 
-    def e2e(self, steps):
+    def e2e_parts(self):
         torch = self.torch
         hx, hu, hr = (torch.as_tensor(a).pin_memory() for a in (self.w.x_nom, self.w.u_nom, self.w.radii))
         out_h = {k: torch.empty(self.out[k].shape).pin_memory() for k in ("r_lo", "r_hi", "A", "B")}
         dx, du, dr = torch.empty_like(self.x), torch.empty_like(self.u), torch.empty_like(self.r)
 
-        def one():
+        def h2d():
             dx.copy_(hx, non_blocking=True)
             du.copy_(hu, non_blocking=True)
             dr.copy_(hr, non_blocking=True)
-            o = self.handle.bounds(dx, du, radii=dr, out=self.out)
+
+        def compute():
+            self.handle.bounds(dx, du, radii=dr, out=self.out)
+
+        def d2h():
             for k, v in out_h.items():
-                v.copy_(o[k], non_blocking=True)
-        ms = timed_loop(torch, one, steps)
-        return ms, (hx.numel() + hu.numel() + hr.numel()) * 4, sum(v.numel() * 4 for v in out_h.values())
+                v.copy_(self.out[k], non_blocking=True)
+        return E2EParts(h2d, compute, d2h, (hx.numel() + hu.numel() + hr.numel()) * 4,
+                        sum(v.numel() * 4 for v in out_h.values()))
 
     def oracle_seconds_per_unit(self, budget_s):
         from oracle import crown
@@ -369,7 +400,7 @@ class BackwardForm(Form):
                 "kernel": kernel, "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
                 "flop_per_unit": adjoint_flop_per_ts(), "units_per_step": self.T}
 
-    def e2e(self, steps):
+    def e2e_parts(self):
         torch = self.torch
         c = self.c
         hs = [torch.as_tensor(a).pin_memory() for a in (c.w.x_nom, c.w.u_nom, c.w.radii)]
@@ -378,15 +409,20 @@ class BackwardForm(Form):
         dg = [torch.empty_like(self.glo), torch.empty_like(self.ghi)]
         outs = [torch.empty(self.T, 168).pin_memory(), torch.empty(self.T, 56).pin_memory(),
                 torch.empty(self.T, 224).pin_memory()]
+        res = {}
 
-        def one():
+        def h2d():
             for d, h in zip(ds + dg, hs + hg):
                 d.copy_(h, non_blocking=True)
-            gx, gu, gr, _ = self.handle.bounds_backward(ds[0], ds[1], ds[2], dg[0], dg[1])
-            for o, g in zip(outs, (gx, gu, gr)):
+
+        def compute():
+            res["g"] = self.handle.bounds_backward(ds[0], ds[1], ds[2], dg[0], dg[1])[:3]
+
+        def d2h():
+            for o, g in zip(outs, res["g"]):
+                g.record_stream(torch.cuda.current_stream())
                 o.copy_(g, non_blocking=True)
-        ms = timed_loop(torch, one, steps)
-        return ms, sum(h.numel() * 4 for h in hs + hg), sum(o.numel() * 4 for o in outs)
+        return E2EParts(h2d, compute, d2h, sum(h.numel() * 4 for h in hs + hg), sum(o.numel() * 4 for o in outs))
 
     def oracle_seconds_per_unit(self, budget_s):
         from oracle import crown
@@ -466,17 +502,23 @@ class ProposerForm(Form):
                 "kernel": kernel, "kernel_ms": round(ms, 4), "launches_per_step": launches,
                 "flop_per_unit": PROPOSER_FLOP, "units_per_step": self.T}
 
-    def e2e(self, steps):
+    def e2e_parts(self):
         torch = self.torch
         hX = self.X.cpu().pin_memory()
         hY = torch.empty(self.T, 336).pin_memory()
         dX = torch.empty_like(self.X)
+        res = {}
 
-        def one():
+        def h2d():
             dX.copy_(hX, non_blocking=True)
-            hY.copy_(self.p.forward(dX), non_blocking=True)
-        ms = timed_loop(torch, one, steps)
-        return ms, hX.numel() * 4, hY.numel() * 4
+
+        def compute():
+            res["Y"] = self.p.forward(dX)
+
+        def d2h():
+            res["Y"].record_stream(torch.cuda.current_stream())
+            hY.copy_(res["Y"], non_blocking=True)
+        return E2EParts(h2d, compute, d2h, hX.numel() * 4, hY.numel() * 4)
 
 
 class PbhGradForm(Form):
@@ -540,21 +582,27 @@ class PbhGradForm(Form):
                 "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
                 "bytes_per_unit": self.BYTES_PER_TS, "units_per_launch": self.T // max(launches, 1)}
 
-    def e2e(self, steps):
+    def e2e_parts(self):
         torch = self.torch
         hx, hu, hr = (a.cpu().pin_memory() for a in (self.x, self.u, self.r))
         hgl, hgh = self.glo.cpu().pin_memory(), self.ghi.cpu().pin_memory()
         dx, du, dr, dgl, dgh = (torch.empty_like(a) for a in (self.x, self.u, self.r, self.glo, self.ghi))
         outs = [torch.empty(self.T, k).pin_memory() for k in (168, 56, 224)]
+        res = {}
 
-        def one():
+        def h2d():
             for d, hsrc in ((dx, hx), (du, hu), (dr, hr), (dgl, hgl), (dgh, hgh)):
                 d.copy_(hsrc, non_blocking=True)
-            g = self.handle.bounds_backward(dx, du, dr, dgl, dgh)
-            for o, gg in zip(outs, g[:3]):
+
+        def compute():
+            res["g"] = self.handle.bounds_backward(dx, du, dr, dgl, dgh)[:3]
+
+        def d2h():
+            for o, gg in zip(outs, res["g"]):
+                gg.record_stream(torch.cuda.current_stream())
                 o.copy_(gg, non_blocking=True)
-        ms = timed_loop(torch, one, steps)
-        return ms, sum(a.numel() * 4 for a in (hx, hu, hr, hgl, hgh)), sum(o.numel() * 4 for o in outs)
+        return E2EParts(h2d, compute, d2h, sum(a.numel() * 4 for a in (hx, hu, hr, hgl, hgh)),
+                        sum(o.numel() * 4 for o in outs))
 
 
 class PbhSysForm(Form):
@@ -614,20 +662,24 @@ class PbhSysForm(Form):
                 "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
                 "bytes_per_unit": self.BYTES_PER_TS, "units_per_launch": self.T // max(launches, 1)}
 
-    def e2e(self, steps):
+    def e2e_parts(self):
         torch = self.torch
         hx, hu, hr = (a.cpu().pin_memory() for a in (self.x, self.u, self.r))
         dx, du, dr = (torch.empty_like(a) for a in (self.x, self.u, self.r))
         out_h = {k: torch.empty(self.out[k].shape).pin_memory() for k in ("r_lo", "r_hi", "A", "B")}
 
-        def one():
+        def h2d():
             for d, hsrc in ((dx, hx), (du, hu), (dr, hr)):
                 d.copy_(hsrc, non_blocking=True)
-            o = self.handle.bounds(dx, du, radii=dr, out=self.out)
+
+        def compute():
+            self.handle.bounds(dx, du, radii=dr, out=self.out)
+
+        def d2h():
             for k, v in out_h.items():
-                v.copy_(o[k], non_blocking=True)
-        ms = timed_loop(torch, one, steps)
-        return ms, sum(a.numel() * 4 for a in (hx, hu, hr)), sum(v.numel() * 4 for v in out_h.values())
+                v.copy_(self.out[k], non_blocking=True)
+        return E2EParts(h2d, compute, d2h, sum(a.numel() * 4 for a in (hx, hu, hr)),
+                        sum(v.numel() * 4 for v in out_h.values()))
 
     def oracle_seconds_per_unit(self, budget_s):
         from oracle import dynamics3d, pbh
@@ -681,21 +733,24 @@ class TubeForm(Form):
                 "kernel_ms": round(ms, 4), "launches_per_step": 1, "bytes_per_unit": self.bytes // self.T,
                 "units_per_launch": self.T}
 
-    def e2e(self, steps):
+    def e2e_parts(self):
         torch = self.torch
         hs = [a.cpu().pin_memory() for a in (self.Phi, self.e, self.c, self.r)]
         ds = [torch.empty_like(a) for a in (self.Phi, self.e, self.c, self.r)]
         outs = [torch.empty(self.out[k].shape).pin_memory() for k in ("mu", "sigma")]
         w = self.w
 
-        def one():
+        def h2d():
             for d, h in zip(ds, hs):
                 d.copy_(h, non_blocking=True)
-            mu, sigma, _ = self.binding.tube(ds[0], ds[1], ds[2], ds[3], w.n_traj, w.N, w.n_x, w.n_u, out=self.out)
-            outs[0].copy_(mu, non_blocking=True)
-            outs[1].copy_(sigma, non_blocking=True)
-        ms = timed_loop(torch, one, steps)
-        return ms, sum(h.numel() * 4 for h in hs), sum(o.numel() * 4 for o in outs)
+
+        def compute():
+            self.binding.tube(ds[0], ds[1], ds[2], ds[3], w.n_traj, w.N, w.n_x, w.n_u, out=self.out)
+
+        def d2h():
+            outs[0].copy_(self.out["mu"], non_blocking=True)
+            outs[1].copy_(self.out["sigma"], non_blocking=True)
+        return E2EParts(h2d, compute, d2h, sum(h.numel() * 4 for h in hs), sum(o.numel() * 4 for o in outs))
 
     def oracle_seconds_per_unit(self, budget_s):
         """The FP64 oracle on whole trajectories of this batch: seconds per trajectory."""
@@ -745,8 +800,6 @@ class Table1Form(Form):
                 "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
                 "bytes_per_unit": self.BYTES["quad3d"], "units_per_launch": self.T}
 
-    def e2e(self, steps):
-        return 0.0, 0, 0
 
 
 def slowest_rank_ms(torch, dist, step_ms, device):
@@ -773,6 +826,68 @@ def timed_loop(torch, fn, steps):
     for _ in range(steps):
         fn()
     e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+# Order of the forms in the pipelined end-to-end step: the 3-D quadrotor PBH (large results, tiny
+# inputs and call) first, so that its results are copied out while the adjoint (most of the step's
+# device time, few bytes) runs and the PBH generators are copied in.
+E2E_ORDER = ("pbh_sys", "backward", "pbh", "crown", "tube", "pbh_grad", "proposer")
+
+
+def e2e_pipelined(torch, forms, steps):
+    """The whole step end to end through the public API, as a serving loop runs it: every form's inputs
+    copied in from pinned host memory, its library call(s), and its results copied back, every step, on
+    three streams (host-to-device copies, calls, device-to-host copies) ordered by events, so that the
+    copies of one form overlap the calls of another and the two copy directions overlap each other.
+    Buffers are reused from step to step: a form's copy-in waits until its previous call has read the
+    inputs, and its call waits until its previous results have been copied out. CUDA-event time per
+    step over `steps` steps (after one untimed step), fill and drain included."""
+    parts = {f.name: f.e2e_parts() for f in forms}
+    names = [n for n in E2E_ORDER if parts.get(n) is not None]
+    names += [f.name for f in forms if f.name not in names and parts[f.name] is not None]
+    if not names:
+        return 0.0
+    seq = [parts[n] for n in names]
+    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    prev_c, prev_o = [None] * len(seq), [None] * len(seq)
+
+    def one_step():
+        for i, p in enumerate(seq):
+            with torch.cuda.stream(s_in):
+                if prev_c[i] is not None:
+                    s_in.wait_event(prev_c[i])
+                p.h2d()
+                ev_in = torch.cuda.Event()
+                ev_in.record(s_in)
+            with torch.cuda.stream(s_cmp):
+                s_cmp.wait_event(ev_in)
+                if prev_o[i] is not None:
+                    s_cmp.wait_event(prev_o[i])
+                p.compute()
+                prev_c[i] = torch.cuda.Event()
+                prev_c[i].record(s_cmp)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(prev_c[i])
+                p.d2h()
+                prev_o[i] = torch.cuda.Event()
+                prev_o[i].record(s_out)
+
+    main = torch.cuda.current_stream()
+    for s in (s_in, s_cmp, s_out):
+        s.wait_stream(main)
+    one_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(main)
+    for s in (s_in, s_cmp, s_out):
+        s.wait_event(e0)
+    for _ in range(steps):
+        one_step()
+    for s in (s_in, s_cmp, s_out):
+        main.wait_stream(s)
+    e1.record(main)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / steps
 
@@ -994,6 +1109,8 @@ def main():
     # dominant kernel: the largest share of the step
     dom = max(forms, key=lambda f: kt[f.name][0])
     # end to end through the public API from pinned host memory
+    # (each form alone, copies and call in order on one stream: per-form context; the step's e2e value is
+    # the pipelined serving loop over all forms)
     e2e_ms, h2d, d2h = 0.0, 0, 0
     for f in forms:
         m, a, b = f.e2e(1 if f.name == "backward" else max(2, min(5, args.steps)))
@@ -1001,6 +1118,7 @@ def main():
         h2d += a
         d2h += b
         out_forms[f.name]["e2e_ms"] = round(m, 4)
+    pipe_ms = e2e_pipelined(torch, forms, max(3, args.steps))
     ours, allk, kn = count_launches(torch, step)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -1011,8 +1129,12 @@ def main():
                               if flush is None else "512 MB L2 flush between steps, outside the form timers"),
                        "parallelism": f"replicas x{world}"},
             "roofline": roof[dom.name], "forms": out_forms,
-            "e2e": {"value": units / (e2e_ms * 1e-3) if e2e_ms > 0 else None, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+            "e2e": {"value": units / (pipe_ms * 1e-3) if pipe_ms > 0 else None, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": round(pipe_ms, 3),
+                    "how": "every form's inputs copied in from pinned host memory, its library calls and its "
+                           "results copied out, every step, on three streams (copy-in, calls, copy-out) so "
+                           "that copies overlap calls; each form alone, in order on one stream: "
+                           f"{round(e2e_ms, 3)} ms per step"},
             "gpu_launches": None if ours is None else ours * args.steps,
             "gpu_launches_detail": {"per_step_ours": ours, "per_step_all_kernels": allk, "kernels": kn},
             "wall_ms_per_step": round(wall_ms, 3), "clocks": clocks}
