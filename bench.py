@@ -223,7 +223,26 @@ class PbhForm(Form):
         self.G = torch.as_tensor(w.G).to(dev)
         self.out = self.handle.bounds(self.x, self.u, G=self.G)
         torch.cuda.synchronize()
+        self.ragged = self._ragged(torch, dev, binding, inputs, quick)
         self.desc = f"28-quadrotor spring chain n_x=168 n_u=56, {self.T // 50} traj x N=50, zonotope 224x336"
+
+    @staticmethod
+    def _ragged(torch, dev, binding, inputs, quick):
+        """Once at start-up (untimed in the step): the chain batch with ragged horizons U{20..60} (256
+        trajectories, zonotope sets) as one persistent launch with the autotuned plan, captured in a CUDA
+        graph and relaunched: ms per launch and timestep-bounds/s."""
+        w = inputs.quad_chain(n_traj=16 if quick else 256, horizon=(20, 60))
+        h = binding.quad_chain(28, **w.params, spring_k=w.spring_k)
+        x, u, G = (torch.as_tensor(a).to(dev) for a in (w.x_nom, w.u_nom, w.G))
+        offs = torch.as_tensor(w.traj_offsets).to(dev)
+        h.autotune(w.T, binding.SET_ZONO, int(G.shape[-1]))
+        g = binding.Graph(h, x, u, G=G, traj_offsets=offs)
+        ms = timed_loop(torch, g.launch, 10)
+        res = {"trajectories": int(offs.numel() - 1), "timesteps": w.T, "plan": h.plan(), "ms_per_launch": round(ms, 4),
+               "timestep_bounds_per_s": round(w.T / (ms * 1e-3), 1),
+               "hbm_frac": round(PBH_BYTES_PER_TS * w.T / (ms * 1e-3) / 1e9 / peaks()["hbm_gbs"], 4)}
+        del g, G
+        return res
 
     def run(self):
         self.handle.bounds(self.x, self.u, G=self.G, out=self.out)
@@ -1097,6 +1116,8 @@ def main():
             d["table1_shapes"] = f.table1
         if f.name == "crown":
             d["ibp_intermediate_variant"] = f.ibp
+        if f.name == "pbh":
+            d["ragged_horizons_graph"] = f.ragged
         if f.name == "tube":
             d["tube_timesteps_per_s"] = round(f.w.n_traj * f.w.N / (form_ms["tube"] * 1e-3), 1)
         if f.name == "proposer":
