@@ -1,6 +1,6 @@
 // Learned LEB proposer: a ReLU MLP n_in -> H -> H -> n_out that maps (x~_k, u~_k, state radii) to
 // standardised (r_lo, r_hi). It only proposes bounds; the certified kernels stay the final answer and
-// the judge of its error. (An addition to the paper's method.)
+// the measure of its error. (An addition to the paper's method.)
 //
 // Training and inference run in this file's kernels: GEMMs with operands rounded to BF16 and FP32
 // accumulation, bias/ReLU epilogues, mean-squared-error gradient, column sums for the bias gradients,

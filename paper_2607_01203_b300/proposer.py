@@ -1,7 +1,7 @@
 """Learned LEB proposer (binding of the leb_proposer_* entry points; argument marshalling only).
 
 A ReLU MLP n_in -> n_hidden -> n_hidden -> n_out trained by the library's own kernels on certified
-bounds. It proposes bounds; the certified kernel remains the final answer and the judge of its error.
+bounds. It proposes bounds; the certified kernel remains the final answer and the measure of its error.
 """
 from __future__ import annotations
 
