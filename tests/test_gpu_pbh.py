@@ -286,3 +286,29 @@ def test_gamma_map_outputs():
     assert np.allclose(c, oc, rtol=1e-6, atol=1e-12) and np.allclose(r, orad, rtol=1e-5, atol=1e-12)
     c2, r2 = binding.zonotope_map(_t(lo), _t(hi), 1e-6)
     assert np.array_equal(c2.cpu().numpy(), c) and np.array_equal(r2.cpu().numpy(), r)
+
+
+def test_zonotope_kernel_with_only_A_or_only_B():
+    """The zonotope kernel's A/B writer with one of the two matrices requested: the same bounds, and the
+    requested matrix identical to the one a call with both writes."""
+    import ctypes as C
+    w = inputs.quad_chain(n_traj=3, horizon=(2, 5), n_quads=28)
+    h = binding.quad_chain(28, **w.params, spring_k=w.spring_k)
+    x, u, G = _t(w.x_nom), _t(w.u_nom), _t(w.G)
+    full = h.bounds(x, u, G=G)
+    torch.cuda.synchronize()
+    sd = h.set_desc(G=G)
+    for keep in ("A", "B"):
+        lo, hi = torch.empty_like(full["r_lo"]), torch.empty_like(full["r_hi"])
+        mat = torch.full_like(full[keep], float("nan"))
+        flags = torch.zeros(1, device=DEV, dtype=torch.int32)
+        ws = h.workspace(w.T)
+        ptr = binding._ptr
+        st = binding.lib().leb_bounds(h.h, None, w.T, ptr(x), ptr(u), C.byref(sd), ptr(lo), ptr(hi),
+                                      ptr(mat) if keep == "A" else None, ptr(mat) if keep == "B" else None, None,
+                                      ptr(ws), ws.numel(), ptr(flags), binding._stream())
+        binding.check(st, "leb_bounds")
+        torch.cuda.synchronize()
+        assert int(flags.item()) == 0
+        assert torch.equal(lo, full["r_lo"]) and torch.equal(hi, full["r_hi"])
+        assert torch.equal(mat, full[keep]), keep
