@@ -52,16 +52,21 @@ __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__floa
 // ---------------------------------------------------------------------------------------------------
 constexpr int kPtMaxStages = 8;
 constexpr int kPtATile = 128 * 64 * 2;     // 16 KB
-constexpr int kPtSmem = 227 * 1024 - 64;   // the ring takes as many stages of (16 KB + N x 128 B) as fit
+constexpr int kPtSmem = 227 * 1024 - 64;   // the largest launch: as many ring stages of (16 KB + N x 128 B) as fit
 
-// Stages of the K ring for N output columns: as many as fit the shared memory, at most kPtMaxStages.
+// Stages of the K ring for N output columns. Up to 256 columns, two stages, so that two CTAs share an SM
+// (their TMEM, 2 x 256 columns, fits too) and one CTA's epilogue overlaps the other's MMAs; wider
+// layers take as many stages as fit one CTA per SM.
 static inline int pt_stages(int N) {
+  if (N <= 256) return 2;
   const int per = kPtATile + N * 128;
   const int st = (kPtSmem - 1024 - 2 * kPtMaxStages * 8 - 8) / per;
   return st < kPtMaxStages ? st : kPtMaxStages;
 }
+// Dynamic shared memory of a launch: alignment slack, the ring, its barriers and the accumulator barrier.
+static inline int pt_smem(int N, int stages) { return 1024 + stages * (kPtATile + N * 128) + (2 * stages + 1) * 8; }
 
-__global__ void __launch_bounds__(128, 1) prop_tc_gemm_kernel(const __grid_constant__ CUtensorMap amap,
+__global__ void __launch_bounds__(128, 2) prop_tc_gemm_kernel(const __grid_constant__ CUtensorMap amap,
                                                               const __grid_constant__ CUtensorMap wmap, int M, int N,
                                                               int K, int nchunk, const float* bias, int relu,
                                                               __nv_bfloat16* outb, float* outf, int ldo,
@@ -459,12 +464,13 @@ static bool forward_tc(leb_proposer p, int B, const float* X, float* ws, float* 
   prop_standardize_bf16_kernel<<<sblocks, 256, 0, s>>>(B, n_in, X, p->periodic, p->norm, p->norm + n_in, Xb);
   const int grid = (B + 127) / 128;
   const float* omean = p->norm + 2 * n_in;
-  prop_tc_gemm_kernel<<<grid, 128, kPtSmem, s>>>(m0, p->wmap[0], B, H, n_in, p->nchunk[0], p->b[0], 1, H1, nullptr, H,
-                                                 nullptr, nullptr, pt_stages(H));
-  prop_tc_gemm_kernel<<<grid, 128, kPtSmem, s>>>(m1, p->wmap[1], B, H, H, p->nchunk[1], p->b[1], 1, H2, nullptr, H,
-                                                 nullptr, nullptr, pt_stages(H));
-  prop_tc_gemm_kernel<<<grid, 128, kPtSmem, s>>>(m2, p->wmap[2], B, n_out, H, p->nchunk[2], p->b[2], 0, nullptr, Y,
-                                                 n_out, omean, omean + n_out, pt_stages(n_out));
+  const int sh = pt_stages(H), so = pt_stages(n_out);
+  prop_tc_gemm_kernel<<<grid, 128, pt_smem(H, sh), s>>>(m0, p->wmap[0], B, H, n_in, p->nchunk[0], p->b[0], 1, H1,
+                                                        nullptr, H, nullptr, nullptr, sh);
+  prop_tc_gemm_kernel<<<grid, 128, pt_smem(H, sh), s>>>(m1, p->wmap[1], B, H, H, p->nchunk[1], p->b[1], 1, H2,
+                                                        nullptr, H, nullptr, nullptr, sh);
+  prop_tc_gemm_kernel<<<grid, 128, pt_smem(n_out, so), s>>>(m2, p->wmap[2], B, n_out, H, p->nchunk[2], p->b[2], 0,
+                                                            nullptr, Y, n_out, omean, omean + n_out, so);
   *st = cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
   return true;
 }
