@@ -34,7 +34,7 @@ struct leb_proposer_s {
   int w_version = 0, wb_version = -1;   // bumped by every weight change; the BF16 copies' version
   __nv_bfloat16* Wb[3] = {};
   CUtensorMap wmap[3];
-  int nchunk[3] = {};
+  int parts[3] = {};                    // column parts of each layer (one CTA each per 128-row tile)
 };
 
 namespace leb {
@@ -44,8 +44,9 @@ __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__floa
 // ---------------------------------------------------------------------------------------------------
 // Inference GEMM on the tensor cores: C[M, N] = A[M, K] W[N, K]^T + bias (ReLU), A and W in BF16
 // (K-major, 128-byte swizzled tiles by TMA, zero fill past K and M), FP32 accumulation in TMEM.
-// One CTA = 128 rows of A and all N <= 512 columns (TMEM columns), issued as nchunk MMAs of N / nchunk
-// columns (a multiple of 16, at most 256). Warp 0 lane 0 loads, warp 1 lane 0 issues the MMAs, all four
+// One CTA = 128 rows of A and the N columns [n0, n0 + N) of part n0 = blockIdx.y N of the layer's output
+// (TMEM columns), issued as nchunk MMAs of N / nchunk columns (a multiple of 16, at most 256). The layers
+// are split into parts of at most 128 columns, so that a tile's epilogue is spread over several CTAs. Warp 0 lane 0 loads, warp 1 lane 0 issues the MMAs, all four
 // warps read TMEM (thread = row) for the epilogue, which writes BF16 (the next layer's operand) or FP32
 // (the output, optionally taken back out of its standardisation: y std + mean).
 // Every wait is bounded; a wait that runs out leaves the tile's outputs NaN.
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(128, 2) prop_tc_gemm_kernel(const __grid_const
   __shared__ int s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * 128, nK = (K + 63) / 64, nb = N / nchunk;
+  const int n0 = blockIdx.y * N;   // this CTA's columns [n0, n0 + N) of the layer's output
   const uint32_t tcols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : (N <= 256 ? 256 : 512)));
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
@@ -107,7 +109,8 @@ __global__ void __launch_bounds__(128, 2) prop_tc_gemm_kernel(const __grid_const
       if (kb >= stages && !mbar_wait(&empty[s], ((kb / stages) - 1) & 1u)) { s_fail = 1; break; }
       mbar_arrive_expect_tx(&full[s], abytes + bbytes);
       tma_load_2d(At + s * kPtATile, &amap, kb * 64, m0, &full[s]);
-      for (int c = 0; c < nchunk; ++c) tma_load_2d(Bt + s * btile + c * nb * 128, &wmap, kb * 64, c * nb, &full[s]);
+      for (int c = 0; c < nchunk; ++c)
+        tma_load_2d(Bt + s * btile + c * nb * 128, &wmap, kb * 64, n0 + c * nb, &full[s]);
     }
     // every posted copy lands before the block can exit
     for (int kb = nK > stages ? nK - stages : 0; kb < nK; ++kb) mbar_wait(&full[kb % stages], (kb / stages) & 1u);
@@ -140,9 +143,9 @@ __global__ void __launch_bounds__(128, 2) prop_tc_gemm_kernel(const __grid_const
     if (row >= M) continue;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
-      float x = ok ? v[e] + bias[c0 + e] : __int_as_float(0x7fc00000);
+      float x = ok ? v[e] + bias[n0 + c0 + e] : __int_as_float(0x7fc00000);
       x = relu ? fmaxf(x, 0.f) : x;
-      v[e] = omean ? fmaf(x, ostd[c0 + e], omean[c0 + e]) : x;   // back to the bounds' units
+      v[e] = omean ? fmaf(x, ostd[n0 + c0 + e], omean[n0 + c0 + e]) : x;   // back to the bounds' units
     }
     if (outb) {
       uint32_t w[8];
@@ -151,11 +154,11 @@ __global__ void __launch_bounds__(128, 2) prop_tc_gemm_kernel(const __grid_const
         const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
         w[e] = *reinterpret_cast<const uint32_t*>(&h);
       }
-      uint4* dst = reinterpret_cast<uint4*>(outb + (long long)row * ldo + c0);
+      uint4* dst = reinterpret_cast<uint4*>(outb + (long long)row * ldo + n0 + c0);
       dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
       dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
     } else {
-      float4* dst = reinterpret_cast<float4*>(outf + (long long)row * ldo + c0);
+      float4* dst = reinterpret_cast<float4*>(outf + (long long)row * ldo + n0 + c0);
 #pragma unroll
       for (int e = 0; e < 4; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
     }
@@ -393,9 +396,12 @@ size_t ws_floats(const leb_proposer_s* p, int B) {
 using namespace leb;
 
 // Chunks of an N-column product for the tcgen05 GEMM: the fewest with N / c a multiple of 16, at most 256.
-static int mma_chunks(int N) {
-  for (int c = 1; c <= N / 16; ++c)
-    if (N % c == 0 && (N / c) % 16 == 0 && N / c <= 256) return c;
+// Column parts of a layer of N outputs: the fewest parts of at most 128 columns (a multiple of 16) each,
+// else of at most 256; 0 if N has no such split. Each part is one CTA's single MMA chunk.
+static int mma_parts(int N) {
+  for (int lim : {128, 256})
+    for (int c = 1; c <= N / 16; ++c)
+      if (N % c == 0 && (N / c) % 16 == 0 && N / c <= lim) return c;
   return 0;
 }
 
@@ -406,14 +412,14 @@ static bool setup_tc(leb_proposer p) {
   auto enc = tensor_map_encoder();
   if (!enc || p->n_in % 8 != 0 || p->H % 8 != 0 || p->H > 512 || p->n_out > 512) return true;
   for (int i = 0; i < 3; ++i) {
-    p->nchunk[i] = mma_chunks(outs[i]);
-    if (p->nchunk[i] == 0) return true;
+    p->parts[i] = mma_parts(outs[i]);
+    if (p->parts[i] == 0) return true;
   }
   for (int i = 0; i < 3; ++i) {
     if (cudaMalloc(&p->Wb[i], (size_t)ins[i] * outs[i] * 2) != cudaSuccess) return false;
     cuuint64_t dims[2] = {(cuuint64_t)ins[i], (cuuint64_t)outs[i]};
     cuuint64_t strides[1] = {(cuuint64_t)ins[i] * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)(outs[i] / p->nchunk[i])};
+    cuuint32_t box[2] = {64, (cuuint32_t)(outs[i] / p->parts[i])};
     cuuint32_t estr[2] = {1, 1};
     if (enc(&p->wmap[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p->Wb[i], dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -462,15 +468,18 @@ static bool forward_tc(leb_proposer p, int B, const float* X, float* ws, float* 
   }
   const int sblocks = (int)std::min<long long>(((long long)B + 7) / 8, 148LL * 16);
   prop_standardize_bf16_kernel<<<sblocks, 256, 0, s>>>(B, n_in, X, p->periodic, p->norm, p->norm + n_in, Xb);
-  const int grid = (B + 127) / 128;
+  const int tiles = (B + 127) / 128;
   const float* omean = p->norm + 2 * n_in;
-  const int sh = pt_stages(H), so = pt_stages(n_out);
-  prop_tc_gemm_kernel<<<grid, 128, pt_smem(H, sh), s>>>(m0, p->wmap[0], B, H, n_in, p->nchunk[0], p->b[0], 1, H1,
-                                                        nullptr, H, nullptr, nullptr, sh);
-  prop_tc_gemm_kernel<<<grid, 128, pt_smem(H, sh), s>>>(m1, p->wmap[1], B, H, H, p->nchunk[1], p->b[1], 1, H2,
-                                                        nullptr, H, nullptr, nullptr, sh);
-  prop_tc_gemm_kernel<<<grid, 128, pt_smem(n_out, so), s>>>(m2, p->wmap[2], B, n_out, H, p->nchunk[2], p->b[2], 0,
-                                                            nullptr, Y, n_out, omean, omean + n_out, so);
+  // layer i: a CTA per (128-row tile, column part of N / parts columns)
+  auto layer = [&](int i, const CUtensorMap& am, int N, int K, int relu, __nv_bfloat16* ob, float* of,
+                   const float* mn, const float* sd) {
+    const int np = N / p->parts[i], ns = pt_stages(np);
+    prop_tc_gemm_kernel<<<dim3(tiles, p->parts[i]), 128, pt_smem(np, ns), s>>>(am, p->wmap[i], B, np, K, 1, p->b[i],
+                                                                                relu, ob, of, N, mn, sd, ns);
+  };
+  layer(0, m0, H, n_in, 1, H1, nullptr, nullptr, nullptr);
+  layer(1, m1, H, H, 1, H2, nullptr, nullptr, nullptr);
+  layer(2, m2, n_out, H, 0, nullptr, Y, omean, omean + n_out);
   *st = cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
   return true;
 }
