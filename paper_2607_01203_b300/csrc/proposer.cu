@@ -269,20 +269,24 @@ __global__ void prop_destandardize_kernel(long long total, int n, const float* y
   }
 }
 
-// Standardised inputs straight into the BF16 operand of the first layer.
+// Standardised inputs straight into the BF16 operand of the first layer: a thread per column pair (n
+// even) keeps that pair's angle flags, means and deviations in registers and walks kStdRows rows, whose
+// loads are independent; a row's pairs are consecutive threads (coalesced).
+constexpr int kStdRows = 16;
 __global__ void prop_standardize_bf16_kernel(int B, int n, const float* X, const int* periodic, const float* mean,
                                              const float* stdv, __nv_bfloat16* Xb) {
-  // a warp per row, column pairs per lane (n even)
-  const int warps = (int)(blockDim.x >> 5), lane = threadIdx.x & 31;
-  for (int row = blockIdx.x * warps + (threadIdx.x >> 5); row < B; row += gridDim.x * warps) {
-    const float2* xr = reinterpret_cast<const float2*>(X + (long long)row * n);
-    __nv_bfloat162* yr = reinterpret_cast<__nv_bfloat162*>(Xb + (long long)row * n);
-    for (int c = lane; c < (n >> 1); c += 32) {
-      const int j = 2 * c;
-      float2 x = xr[c];
-      if (periodic[j]) x.x = wrap_pi(x.x);
-      if (periodic[j + 1]) x.y = wrap_pi(x.y);
-      yr[c] = __floats2bfloat162_rn((x.x - mean[j]) / stdv[j], (x.y - mean[j + 1]) / stdv[j + 1]);
+  const int r0 = blockIdx.x * kStdRows, r1 = min(B, r0 + kStdRows);
+  for (int c = threadIdx.x; c < (n >> 1); c += blockDim.x) {
+    const int j = 2 * c;
+    const bool w0 = periodic[j] != 0, w1 = periodic[j + 1] != 0;
+    const float m0 = mean[j], m1 = mean[j + 1], s0 = stdv[j], s1 = stdv[j + 1];
+#pragma unroll 4
+    for (int row = r0; row < r1; ++row) {
+      float2 x = reinterpret_cast<const float2*>(X + (long long)row * n)[c];
+      if (w0) x.x = wrap_pi(x.x);
+      if (w1) x.y = wrap_pi(x.y);
+      reinterpret_cast<__nv_bfloat162*>(Xb + (long long)row * n)[c] =
+          __floats2bfloat162_rn((x.x - m0) / s0, (x.y - m1) / s1);
     }
   }
 }
@@ -466,8 +470,9 @@ static bool forward_tc(leb_proposer p, int B, const float* X, float* ws, float* 
                                                                         p->Wb[1], p->Wb[2]);
     p->wb_version = p->w_version;
   }
-  const int sblocks = (int)std::min<long long>(((long long)B + 7) / 8, 148LL * 16);
-  prop_standardize_bf16_kernel<<<sblocks, 256, 0, s>>>(B, n_in, X, p->periodic, p->norm, p->norm + n_in, Xb);
+  const int sthreads = std::min(1024, ((n_in / 2) + 31) / 32 * 32);
+  prop_standardize_bf16_kernel<<<(B + kStdRows - 1) / kStdRows, sthreads, 0, s>>>(B, n_in, X, p->periodic, p->norm,
+                                                                                 p->norm + n_in, Xb);
   const int tiles = (B + 127) / 128;
   const float* omean = p->norm + 2 * n_in;
   // layer i: a CTA per (128-row tile, column part of N / parts columns)
