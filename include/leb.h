@@ -217,6 +217,16 @@ leb_status leb_autotune(leb_handle h, int T, leb_set_kind set_kind, int n_gen, c
                         void* workspace, size_t ws_bytes, void* stream);
 /* Current plan as text ("key=value;..."), for logs and tests. */
 leb_status leb_plan_string(leb_handle h, char* buf, size_t buf_len);
+/* Path order of the path-based Hessian bound (Thm. 1, Sec. III-B): the path from the nominal runs
+ * coordinate by coordinate, in any order, and each Hessian entry (j, k) is bounded over the prefix set of
+ * whichever of j, k comes first. order 0: the natural order [x; u] (the default); 1: the inputs first,
+ * then the states (for the planar quadrotor chain the (phi, u) entries then take phi at its nominal and the
+ * (phi, phi) entry the inputs over their box). Planar quadrotor chain handles only (other kinds:
+ * LEB_ERR_UNSUPPORTED); applies to the later leb_bounds, leb_bounds_static and graph captures of the
+ * handle. leb_bounds_backward and leb_refine_nominal_pgd differentiate the natural order and return
+ * LEB_ERR_UNSUPPORTED while order 1 is set. Invalid order or NULL handle: LEB_ERR_INVALID_ARG. */
+leb_status leb_set_path_order(leb_handle h, int order);
+
 /* Force a plan by its index in the candidate list (-1 = back to the default / autotuned plan). */
 leb_status leb_plan_select(leb_handle h, int index);
 leb_status leb_plan_count(leb_handle h, int* count);

@@ -260,24 +260,30 @@ __device__ __forceinline__ void pbh_rows(const PbhArgs& a, const Item& it, const
       const int jp = 6 * i + 2, j1 = nx + 2 * i, j2 = j1 + 1;
       const float phi0 = xn[jp];
       const float u1 = un[2 * i], u2 = un[2 * i + 1];
-      const ivl S = iv(__fadd_rd(u1, u2), __fadd_ru(u1, u2));  // S~ (inputs fixed on X^(phi))
+      // S~ at the nominal, and S on the prefix set of phi: S~ in the natural order (the inputs come after
+      // phi), the inputs' box when they come first
+      const ivl S0 = iv(__fadd_rd(u1, u2), __fadd_ru(u1, u2));
+      const ivl S = K.inputs_first ? iv(__fadd_rd(s_lo[j1], s_lo[j2]), __fadd_ru(s_hi[j1], s_hi[j2])) : S0;
       const ivl Phi = iv(s_lo[jp], s_hi[jp]);
       const ivl Dp = D(jp), D1 = D(j1), D2 = D(j2);
       const ivl Dp2 = iv_sqr(Dp), Dp1 = iv_mul(Dp, D1), Dpu2 = iv_mul(Dp, D2);
       const ivl sinP = iv_sin(Phi), cosP = iv_cos(Phi);
       const ivl sin0 = point_sin(phi0), cos0 = point_cos(phi0);
-      const ivl cS = iv_mul(cI, S);
+      const ivl cS = iv_mul(cI, S), cS0 = iv_mul(cI, S0);
       const QuadA q = qa[i];
       const int deg = K.springs ? (i > 0) + (i + 1 < nq) : 0;
       for (int row = 0; row < 2; ++row) {
         // v_x: 1/2 [(dt/m) S sin](X^(phi)) Dphi^2 - [(dt/m) cos](X^(phi)) Dphi (Du1 + Du2 termwise)
         // v_y: -1/2 [(dt/m) S cos](X^(phi)) Dphi^2 - [(dt/m) sin](X^(phi)) Dphi (Du1, Du2 termwise)
         const ivl Hpp = row == 0 ? iv_mul(cS, sinP) : iv_neg(iv_mul(cS, cosP));
-        const ivl Hup = iv_neg(iv_mul(cI, row == 0 ? cosP : sinP));
+        // the (phi, u) entries over the prefix set of the coordinate that comes first: phi's (phi over its
+        // box) in the natural order, the input's (phi at its nominal) with the inputs first
+        const ivl Hup = K.inputs_first ? iv_neg(iv_mul(cI, row == 0 ? cos0 : sin0))
+                                       : iv_neg(iv_mul(cI, row == 0 ? cosP : sinP));
         ivl R = iv_half(iv_mul(Hpp, Dp2));
         R = iv_add(R, iv_mul(Hup, Dp1));
         R = iv_add(R, iv_mul(Hup, Dpu2));
-        const ivl Jphi = iv_neg(iv_mul(cS, row == 0 ? cos0 : sin0));
+        const ivl Jphi = iv_neg(iv_mul(cS0, row == 0 ? cos0 : sin0));   // the Jacobian at the nominal
         const ivl Ju = row == 0 ? iv_neg(iv_mul(cI, sin0)) : iv_mul(cI, cos0);
         R = iv_add(R, corr(Jphi, row == 0 ? q.aphi_x : q.aphi_y, Dp));
         R = iv_add(R, corr(Ju, row == 0 ? q.au_x : q.au_y, D1));
