@@ -226,6 +226,15 @@ leb_status leb_plan_string(leb_handle h, char* buf, size_t buf_len);
  * handle. leb_bounds_backward and leb_refine_nominal_pgd differentiate the natural order and return
  * LEB_ERR_UNSUPPORTED while order 1 is set. Invalid order or NULL handle: LEB_ERR_INVALID_ARG. */
 leb_status leb_set_path_order(leb_handle h, int order);
+/* Input-domain partitioning (Sec. III-D names it as a use of the parallel evaluation): with
+ * split_attitude = 1 every quadrotor's attitude box is cut at the nominal into [lo, phi~] and [phi~, hi],
+ * Thm. 1 is evaluated on each piece (each still contains the nominal) and each row's bound is the hull of
+ * the pieces' bounds — a bound over the whole set, never wider than the plain one. 0 (the default): no
+ * cut. Planar quadrotor chain handles only (other kinds: LEB_ERR_UNSUPPORTED); applies to later
+ * leb_bounds, leb_bounds_static and graph captures. leb_bounds_backward and leb_refine_nominal_pgd
+ * differentiate the plain bound and return LEB_ERR_UNSUPPORTED while the cut is on. Invalid argument
+ * or NULL handle: LEB_ERR_INVALID_ARG. */
+leb_status leb_set_partition(leb_handle h, int split_attitude);
 
 /* Force a plan by its index in the candidate list (-1 = back to the default / autotuned plan). */
 leb_status leb_plan_select(leb_handle h, int index);

@@ -55,7 +55,7 @@ _lib = None
 
 EXPORTS = [
     "leb_create", "leb_destroy", "leb_dims", "leb_workspace_size", "leb_bounds", "leb_bounds_backward",
-    "leb_zonotope_map", "leb_autotune", "leb_plan_string", "leb_plan_select", "leb_plan_count", "leb_set_path_order",
+    "leb_zonotope_map", "leb_autotune", "leb_plan_string", "leb_plan_select", "leb_plan_count", "leb_set_path_order", "leb_set_partition",
     "leb_graph_capture", "leb_graph_launch", "leb_graph_destroy", "leb_proposer_create", "leb_proposer_destroy",
     "leb_proposer_set_norm", "leb_proposer_forward", "leb_proposer_train_step", "leb_proposer_workspace_size",
     "leb_proposer_get_layer", "leb_proposer_set_layer", "leb_proposer_get_grad", "leb_selftest_point_enclosures",
@@ -93,6 +93,7 @@ def lib():
         L.leb_plan_string.argtypes = [vp, C.c_char_p, sz]
         L.leb_plan_select.argtypes = [vp, i32]
         L.leb_set_path_order.argtypes = [vp, i32]
+        L.leb_set_partition.argtypes = [vp, i32]
         L.leb_plan_count.argtypes = [vp, C.POINTER(i32)]
         L.leb_graph_capture.argtypes = [vp, C.POINTER(BatchDesc), i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp, vp,
                                         C.POINTER(Options), vp, sz, vp, C.POINTER(vp)]
@@ -208,6 +209,10 @@ class Handle:
     def set_path_order(self, inputs_first: bool):
         """Path order of Thm. 1 (leb_set_path_order): the natural [x; u] or the inputs first."""
         check(lib().leb_set_path_order(self.h, int(bool(inputs_first))), "leb_set_path_order")
+
+    def set_partition(self, split_attitude: bool):
+        """Input-domain partitioning (leb_set_partition): each attitude box cut at the nominal, hull."""
+        check(lib().leb_set_partition(self.h, int(bool(split_attitude))), "leb_set_partition")
 
     def autotune(self, T: int, set_kind: int, n_gen: int = 0, cache_path: str | None = None):
         ws = self.workspace(T)

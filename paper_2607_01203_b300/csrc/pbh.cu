@@ -243,6 +243,7 @@ __device__ __forceinline__ void emit_row(const PbhArgs& a, const Item& it, int l
 // Eq. 15 for every output row of one timestep, plus (J - A) Delta. Items 0..nq-1: the two curved rows
 // (v_x, v_y) of quadrotor i, which share their trigonometric enclosures; items nq..5nq-1: the four
 // linear rows of each quadrotor (only the Jacobian-rounding term).
+template <bool kSplit>
 __device__ __forceinline__ void pbh_rows(const PbhArgs& a, const Item& it, const float* xn, const float* un,
                                          const float* s_lo, const float* s_hi, const QuadA* qa, bool bad, int tid,
                                          int nthr) {
@@ -264,37 +265,56 @@ __device__ __forceinline__ void pbh_rows(const PbhArgs& a, const Item& it, const
       // phi), the inputs' box when they come first
       const ivl S0 = iv(__fadd_rd(u1, u2), __fadd_ru(u1, u2));
       const ivl S = K.inputs_first ? iv(__fadd_rd(s_lo[j1], s_lo[j2]), __fadd_ru(s_hi[j1], s_hi[j2])) : S0;
-      const ivl Phi = iv(s_lo[jp], s_hi[jp]);
-      const ivl Dp = D(jp), D1 = D(j1), D2 = D(j2);
-      const ivl Dp2 = iv_sqr(Dp), Dp1 = iv_mul(Dp, D1), Dpu2 = iv_mul(Dp, D2);
-      const ivl sinP = iv_sin(Phi), cosP = iv_cos(Phi);
+      const ivl D1 = D(j1), D2 = D(j2);
       const ivl sin0 = point_sin(phi0), cos0 = point_cos(phi0);
       const ivl cS = iv_mul(cI, S), cS0 = iv_mul(cI, S0);
       const QuadA q = qa[i];
       const int deg = K.springs ? (i > 0) + (i + 1 < nq) : 0;
-      for (int row = 0; row < 2; ++row) {
-        // v_x: 1/2 [(dt/m) S sin](X^(phi)) Dphi^2 - [(dt/m) cos](X^(phi)) Dphi (Du1 + Du2 termwise)
-        // v_y: -1/2 [(dt/m) S cos](X^(phi)) Dphi^2 - [(dt/m) sin](X^(phi)) Dphi (Du1, Du2 termwise)
-        const ivl Hpp = row == 0 ? iv_mul(cS, sinP) : iv_neg(iv_mul(cS, cosP));
-        // the (phi, u) entries over the prefix set of the coordinate that comes first: phi's (phi over its
-        // box) in the natural order, the input's (phi at its nominal) with the inputs first
-        const ivl Hup = K.inputs_first ? iv_neg(iv_mul(cI, row == 0 ? cos0 : sin0))
-                                       : iv_neg(iv_mul(cI, row == 0 ? cosP : sinP));
-        ivl R = iv_half(iv_mul(Hpp, Dp2));
-        R = iv_add(R, iv_mul(Hup, Dp1));
-        R = iv_add(R, iv_mul(Hup, Dpu2));
-        const ivl Jphi = iv_neg(iv_mul(cS0, row == 0 ? cos0 : sin0));   // the Jacobian at the nominal
-        const ivl Ju = row == 0 ? iv_neg(iv_mul(cI, sin0)) : iv_mul(cI, cos0);
-        R = iv_add(R, corr(Jphi, row == 0 ? q.aphi_x : q.aphi_y, Dp));
-        R = iv_add(R, corr(Ju, row == 0 ? q.au_x : q.au_y, D1));
-        R = iv_add(R, corr(Ju, row == 0 ? q.au_x : q.au_y, D2));
-        if (deg) {
-          const ivl ks = iv(K.ks_lo, K.ks_hi);
-          const ivl self = iv_mul(iv(-(float)deg), ks);
-          R = iv_add(R, corr(self, -(float)deg * K.ks_f, D(6 * i + row)));
-          if (i > 0) R = iv_add(R, corr(ks, K.ks_f, D(6 * (i - 1) + row)));
-          if (i + 1 < nq) R = iv_add(R, corr(ks, K.ks_f, D(6 * (i + 1) + row)));
+      // Eq. 15 for both curved rows over an attitude box [plo, phi_] (containing the nominal)
+      auto curved = [&](float plo, float phi_, ivl& Rx, ivl& Ry) {
+        const ivl Phi = iv(plo, phi_);
+        const ivl Dp = iv(__fsub_rd(plo, phi0), __fsub_ru(phi_, phi0));
+        const ivl Dp2 = iv_sqr(Dp), Dp1 = iv_mul(Dp, D1), Dpu2 = iv_mul(Dp, D2);
+        const ivl sinP = iv_sin(Phi), cosP = iv_cos(Phi);
+#pragma unroll
+        for (int row = 0; row < 2; ++row) {
+          // v_x: 1/2 [(dt/m) S sin](X^(phi)) Dphi^2 - [(dt/m) cos](X^(phi)) Dphi (Du1 + Du2 termwise)
+          // v_y: -1/2 [(dt/m) S cos](X^(phi)) Dphi^2 - [(dt/m) sin](X^(phi)) Dphi (Du1, Du2 termwise)
+          const ivl Hpp = row == 0 ? iv_mul(cS, sinP) : iv_neg(iv_mul(cS, cosP));
+          // the (phi, u) entries over the prefix set of the coordinate that comes first: phi's (phi over
+          // its box) in the natural order, the input's (phi at its nominal) with the inputs first
+          const ivl Hup = K.inputs_first ? iv_neg(iv_mul(cI, row == 0 ? cos0 : sin0))
+                                         : iv_neg(iv_mul(cI, row == 0 ? cosP : sinP));
+          ivl R = iv_half(iv_mul(Hpp, Dp2));
+          R = iv_add(R, iv_mul(Hup, Dp1));
+          R = iv_add(R, iv_mul(Hup, Dpu2));
+          const ivl Jphi = iv_neg(iv_mul(cS0, row == 0 ? cos0 : sin0));   // the Jacobian at the nominal
+          const ivl Ju = row == 0 ? iv_neg(iv_mul(cI, sin0)) : iv_mul(cI, cos0);
+          R = iv_add(R, corr(Jphi, row == 0 ? q.aphi_x : q.aphi_y, Dp));
+          R = iv_add(R, corr(Ju, row == 0 ? q.au_x : q.au_y, D1));
+          R = iv_add(R, corr(Ju, row == 0 ? q.au_x : q.au_y, D2));
+          if (deg) {
+            const ivl ks = iv(K.ks_lo, K.ks_hi);
+            const ivl self = iv_mul(iv(-(float)deg), ks);
+            R = iv_add(R, corr(self, -(float)deg * K.ks_f, D(6 * i + row)));
+            if (i > 0) R = iv_add(R, corr(ks, K.ks_f, D(6 * (i - 1) + row)));
+            if (i + 1 < nq) R = iv_add(R, corr(ks, K.ks_f, D(6 * (i + 1) + row)));
+          }
+          if (row == 0) Rx = R; else Ry = R;
         }
+      };
+      // the attitude's box as one piece, or (input-domain partitioning) as its two pieces [lo, phi~] and
+      // [phi~, hi], each still containing the nominal; each row's bound is the hull over the pieces
+      ivl Rr[2];
+      curved(s_lo[jp], kSplit ? phi0 : s_hi[jp], Rr[0], Rr[1]);
+      if constexpr (kSplit) {
+        ivl Rx, Ry;
+        curved(phi0, s_hi[jp], Rx, Ry);
+        Rr[0] = iv(fminf(Rr[0].lo, Rx.lo), fmaxf(Rr[0].hi, Rx.hi));
+        Rr[1] = iv(fminf(Rr[1].lo, Ry.lo), fmaxf(Rr[1].hi, Ry.hi));
+      }
+      for (int row = 0; row < 2; ++row) {
+        const ivl R = Rr[row];
         emit_row(a, it, 6 * i + 3 + row, R, bad);
       }
     } else {
@@ -353,7 +373,7 @@ __device__ __forceinline__ bool hull_row(const PbhArgs& a, const Item& it, const
 // Kernel 1 (box sets, and zonotopes that cannot be bulk-copied): all warps reduce the set, then all
 // warps evaluate the rows and store A_k, B_k.
 // ---------------------------------------------------------------------------------------------------
-template <bool kZono>
+template <bool kZono, bool kSplit>
 __global__ void __launch_bounds__(256, 4) pbh_chain_kernel(PbhArgs a) {
   extern __shared__ float smem[];
   __shared__ int s_t;
@@ -389,7 +409,7 @@ __global__ void __launch_bounds__(256, 4) pbh_chain_kernel(PbhArgs a) {
     }
     compute_qa(xn, un, it.nq, a.k, s_qa, threadIdx.x, blockDim.x);
     const bool bad = __syncthreads_or(!ok) != 0;
-    pbh_rows(a, it, xn, un, s_lo, s_hi, s_qa, bad, threadIdx.x, blockDim.x);
+    pbh_rows<kSplit>(a, it, xn, un, s_lo, s_hi, s_qa, bad, threadIdx.x, blockDim.x);
     write_AB(a, it, s_qa, warp, nwarps, lane);
     if (bad && threadIdx.x == 0) atomicOr(a.flags, LEB_ASYNC_NONFINITE);
     __syncthreads();  // shared buffers are reused by the next timestep
@@ -405,6 +425,7 @@ struct StageMeta {
   int t, chunk, last, rows, rows_per, pad0, pad1, pad2;
 };
 
+template <bool kSplit>
 __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, int stage_bytes_cap) {
   extern __shared__ __align__(128) unsigned char sraw[];
   // Warp roles: warp 0 streams the generators (one thread), warp 1 writes A_k and B_k when they are
@@ -559,7 +580,7 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
       if (m.last) {
         const bool bad = bar_sync_or(1, ncthr, !ok);
         ok = true;
-        pbh_rows(a, it, xn, un, lo, hi, qa, bad, ctid, ncthr);
+        pbh_rows<kSplit>(a, it, xn, un, lo, hi, qa, bad, ctid, ncthr);
         if (writer) {
           // every consumer's qa values are in place (the barrier above): hand the timestep over
           if (ctid == 0) {
@@ -627,21 +648,28 @@ cudaError_t launch_pbh(const Ctx& c, const PbhArgs& a, const PbhPlan& p, cudaStr
     static bool attr = false;
     if (!attr) {
       // the opt-in limit covers the kernel's static shared memory too
-      cudaFuncAttributes fa{};
-      const size_t stat = cudaFuncGetAttributes(&fa, pbh_zono_tma_kernel) == cudaSuccess ? fa.sharedSizeBytes : 1024;
-      cudaFuncSetAttribute(pbh_zono_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(227 * 1024 - stat));
+      for (const void* f : {(const void*)pbh_zono_tma_kernel<false>, (const void*)pbh_zono_tma_kernel<true>}) {
+        cudaFuncAttributes fa{};
+        const size_t stat = cudaFuncGetAttributes(&fa, f) == cudaSuccess ? fa.sharedSizeBytes : 1024;
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(227 * 1024 - stat));
+      }
       attr = true;
     }
-    pbh_zono_tma_kernel<<<grid, p.block, smem, s>>>(a, p.stages, kPbhStageCap);
+    if (a.k.split_phi) pbh_zono_tma_kernel<true><<<grid, p.block, smem, s>>>(a, p.stages, kPbhStageCap);
+    else pbh_zono_tma_kernel<false><<<grid, p.block, smem, s>>>(a, p.stages, kPbhStageCap);
     return cudaGetLastError();
   }
   const int n_max = 8 * a.nq;
   const size_t smem = (size_t)(2 * n_max) * sizeof(float) + (size_t)a.nq * sizeof(QuadA);
   const int block = p.block > 256 ? 256 : p.block;
-  if (a.zono)
-    pbh_chain_kernel<true><<<c.sm_count * 4, block, smem, s>>>(a);
-  else
-    pbh_chain_kernel<false><<<c.sm_count * 4, block, smem, s>>>(a);
+  const int g = c.sm_count * 4;
+  if (a.zono) {
+    if (a.k.split_phi) pbh_chain_kernel<true, true><<<g, block, smem, s>>>(a);
+    else pbh_chain_kernel<true, false><<<g, block, smem, s>>>(a);
+  } else {
+    if (a.k.split_phi) pbh_chain_kernel<false, true><<<g, block, smem, s>>>(a);
+    else pbh_chain_kernel<false, false><<<g, block, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

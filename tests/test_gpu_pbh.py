@@ -355,3 +355,36 @@ def test_inputs_first_path_order_parity():
         scale = np.abs(ol) + np.abs(oh) + 1e-300
         assert np.all(gc["r_lo"][t] <= ol + 1e-12 * scale) and np.all(gc["r_hi"][t] >= oh - 1e-12 * scale)
         assert np.all((gc["r_hi"][t] - gc["r_lo"][t]) <= (oh - ol) * (1 + 1e-5) + eps)
+
+
+def test_attitude_partition_parity():
+    """Input-domain partitioning (leb_set_partition): every quadrotor's attitude box cut at the nominal,
+    Thm. 1 on each piece, the hull; against the oracle's partitioned bound on every timestep of the planar
+    quadrotor and of two coupled quadrotors, inside the plain GPU bound."""
+    cases = []
+    w = inputs.planar_quad()
+    cases.append((w, dynamics.QuadChain(1, **w.params), dict(radii=w.radii), [2]))
+    w2 = inputs.quad_chain(n_traj=2, horizon=4, n_quads=2)
+    cases.append((w2, dynamics.QuadChain(2, **w2.params, spring_k=w2.spring_k), dict(G=w2.G, batch=True), [2, 8]))
+    for wk, dyn, kw, dims in cases:
+        h = binding.quad_chain(wk.n_quads, **wk.params, spring_k=wk.spring_k)
+        h.set_partition(True)
+        g = run_gpu(wk, handle=h, **kw)
+        gp = run_gpu(wk, **kw)
+        assert g["flags"][0] == 0
+        assert np.all(g["r_lo"] >= gp["r_lo"]) and np.all(g["r_hi"] <= gp["r_hi"])
+        assert np.array_equal(g["A"], gp["A"]) and np.array_equal(g["B"], gp["B"])
+        for t in range(wk.T):
+            a = wk.nominal()[t].astype(np.float64)
+            if "G" in kw:
+                lo, hi = pbh.box_from_set(a, G=wk.G[t])
+            else:
+                lo, hi = pbh.box_from_set(a, radii=wk.radii[t])
+            ol, oh = pbh.pbh_partitioned(dyn, a, lo, hi, dims)
+            eps = tolerance(dyn, a, lo, hi, dyn.jacobian(a))
+            scale = np.abs(ol) + np.abs(oh) + 1e-300
+            assert np.all(g["r_lo"][t] <= ol + 1e-12 * scale) and np.all(g["r_hi"][t] >= oh - 1e-12 * scale)
+            assert np.all((g["r_hi"][t] - g["r_lo"][t]) <= (oh - ol) * (1 + 1e-5) + eps)
+    with pytest.raises(binding.LebError):
+        h.bounds_backward(_t(w2.x_nom), _t(w2.u_nom), _t(np.full((w2.T, 16), 0.05, np.float32)),
+                          _t(np.ones((w2.T, 12))), _t(np.ones((w2.T, 12))))
