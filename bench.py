@@ -55,7 +55,7 @@ PROPOSER_FLOP = 2 * (392 * 256 + 256 * 256 + 256 * 336)                         
 # tanh-MLP timesteps); traffic grows in proportion to the timesteps a launch processes, so a launch of T
 # timesteps moves T times this. Summary and command: profiles/dram_traffic_bench_kernels_quick.md.
 DRAM_BYTES_PER_TS_LAUNCH = {
-    "pbh": 312_952_320 / 800,                  # pbh_zono_tma_kernel
+    "pbh": 312_957_184 / 800,                  # pbh_zono_tma_kernel<false> (no attitude cut)
     "crown": 44_853_504 / (3 * 400),           # crown_tc_kernel, mean over its 3 launches
     "backward": 90_078_976 / (5 * 400),        # 2 tight crown_tc_kernel + 3 adjoint_tc_kernel launches, mean
     # pbh_sys_kernel<true>, captured at the bench's own size (12800 timesteps of the 168-state coupled
