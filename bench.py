@@ -567,7 +567,7 @@ class ProposerForm(Form):
 
 
 class PbhGradForm(Form):
-    """Adjoint of the PBH bound (differentiable LEBs, Sec. III-D) of the 28-quadrotor chain, 256 x 50
+    """Adjoint of the PBH bound (differentiable LEBs, Sec. IV-D) of the 28-quadrotor chain, 256 x 50
     timesteps with box sets (state radii U[0.01, 0.1], control radii 0.05), random cotangents. Beside it,
     once at start-up (untimed), the nominal refinement of Table II: projected gradient descent on the PBH
     width within eps = 0.05 of 1280 nominal points against random sampling with as many bound evaluations.
@@ -743,7 +743,7 @@ class PbhSysForm(Form):
 
 
 class TubeForm(Form):
-    """The step after the LEB (Sec. IV-A, Eqs. 18b, 20-21): tube centre and width of the 168-state shape
+    """The step after the LEB (Sec. V-A, Eqs. 18b, 20-21): tube centre and width of the 168-state shape
     (n_x = 168, n_u = 56) over 16 trajectories of horizon 25 (the paper's coupled-quadrotor horizon),
     packed responses of a stable LTV loop, Gamma-map centres and radii, diagonal E.
 

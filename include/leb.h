@@ -136,7 +136,7 @@ typedef struct {
 } leb_batch;
 
 /* Optional outputs and overrides (NULL = none). All pointers device, [T, n_x] (packed like r_lo).
- *  gamma_c, gamma_r: the zonotope map of Sec. III-C: c = (r_lo + r_hi)/2, R = diag((r_hi - r_lo)/2) +
+ *  gamma_c, gamma_r: the zonotope map of Sec. IV-C: c = (r_lo + r_hi)/2, R = diag((r_hi - r_lo)/2) +
  *    gamma_pad (diagonal returned as a vector; rounded upward so that c +- R contains [r_lo, r_hi]).
  *  eps: per-bound stated a-priori slack of the reduced-precision MLP path (rounding inflation plus a
  *    bound on the deviation caused by rounded operands); zero for exact-arithmetic paths. */
@@ -165,7 +165,7 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
                       const leb_set* set, float* r_lo, float* r_hi, float* A, float* B,
                       const leb_options* opt, void* workspace, size_t ws_bytes, int* dev_flags, void* stream);
 
-/* ---- adjoint of the bounds (differentiable LEBs, Sec. III-D) ------------------------------------ */
+/* ---- adjoint of the bounds (differentiable LEBs, Sec. IV-D) ------------------------------------ */
 /* Box sets centred at the nominal only (set->center NULL), uniform batches. Given g_rlo = dL/dr_lo and
  * g_rhi = dL/dr_hi [T, n_x], writes g_x [T, n_x], g_u [T, n_u], g_radii [T, n] = dL/d(x~, u~, radii) of
  * the piecewise-smooth bound with every case fixed at the evaluation point: the relaxation case of each
@@ -188,7 +188,7 @@ leb_status leb_bounds_backward_saved(leb_handle h, int T, const float* x_nom, co
                                      float* g_u, float* g_radii, void* workspace, size_t ws_bytes, int* dev_flags,
                                      void* stream);
 
-/* ---- nominal refinement by projected gradient descent (Sec. IV, Table II) ------------------------ */
+/* ---- nominal refinement by projected gradient descent (Sec. VI-A, Table II) ------------------------ */
 /* Minimises, per timestep, the summed width sum_l (r_hi - r_lo) of the Thm. 1 bound over nominal points in
  * the box |x - x0| <= eps, |u - u0| <= eps (componentwise), for box sets of the given radii centred at the
  * nominal. Each of `steps` steps moves every coordinate by lr against the sign of its gradient
@@ -203,7 +203,7 @@ leb_status leb_refine_nominal_pgd(leb_handle h, int T, const float* x0, const fl
                                   float* w_best, void* workspace, size_t ws_bytes, int* dev_flags, void* stream);
 leb_status leb_refine_workspace_size(leb_handle h, int T_max, size_t* bytes);
 
-/* ---- zonotope map of Sec. III-C as a standalone call -------------------------------------------- */
+/* ---- zonotope map of Sec. IV-C as a standalone call -------------------------------------------- */
 /* c = (lo+hi)/2, r = (hi-lo)/2 + pad over count elements (device), r rounded up, c to nearest. */
 leb_status leb_zonotope_map(const float* r_lo, const float* r_hi, long long count, float pad, float* c,
                             float* r, void* stream);
@@ -217,7 +217,7 @@ leb_status leb_autotune(leb_handle h, int T, leb_set_kind set_kind, int n_gen, c
                         void* workspace, size_t ws_bytes, void* stream);
 /* Current plan as text ("key=value;..."), for logs and tests. */
 leb_status leb_plan_string(leb_handle h, char* buf, size_t buf_len);
-/* Path order of the path-based Hessian bound (Thm. 1, Sec. III-B): the path from the nominal runs
+/* Path order of the path-based Hessian bound (Thm. 1, Sec. IV-A): the path from the nominal runs
  * coordinate by coordinate, in any order, and each Hessian entry (j, k) is bounded over the prefix set of
  * whichever of j, k comes first. order 0: the natural order [x; u] (the default); 1: the inputs first,
  * then the states (for the planar quadrotor chain the (phi, u) entries then take phi at its nominal and the
@@ -226,7 +226,7 @@ leb_status leb_plan_string(leb_handle h, char* buf, size_t buf_len);
  * handle. leb_bounds_backward and leb_refine_nominal_pgd differentiate the natural order and return
  * LEB_ERR_UNSUPPORTED while order 1 is set. Invalid order or NULL handle: LEB_ERR_INVALID_ARG. */
 leb_status leb_set_path_order(leb_handle h, int order);
-/* Input-domain partitioning (Sec. III-D names it as a use of the parallel evaluation): with
+/* Input-domain partitioning (Sec. IV-D names it as a use of the parallel evaluation): with
  * split_attitude = 1 every quadrotor's attitude box is cut at the nominal into [lo, phi~] and [phi~, hi],
  * Thm. 1 is evaluated on each piece (each still contains the nominal) and each row's bound is the hull of
  * the pieces' bounds — a bound over the whole set, never wider than the plain one. 0 (the default): no
@@ -301,7 +301,9 @@ leb_status leb_proposer_load_state(leb_proposer p, const void* host_buf, size_t 
  * 64 KiB array inside the library that every GPU loading the library keeps until the process exits.
  * Uneven-dimension batches may have at most leb_bounds_static_max_traj() trajectories; more return
  * LEB_ERR_WORKSPACE. MLP handles return LEB_ERR_UNSUPPORTED; satellite and 3-D quadrotor handles use no scratch. The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress): make that first call before any stream capture. All
+ * array's device address (cudaGetSymbolAddress): make that first call before any stream capture. The
+ * address is kept for the life of the process: after a cudaDeviceReset the module is loaded again and the
+ * kept address is stale, so do not call this entry point again after resetting a device. All
  * calls share the array and clear its counter themselves; calls that overlap on the GPU (issued on
  * different streams or from different host threads without ordering) race on it. Nothing is allocated
  * or freed. Other arguments and outputs as leb_bounds (no leb_options). */
@@ -310,7 +312,7 @@ leb_status leb_bounds_static(leb_handle h, const leb_batch* batch, int T, const 
                              void* stream);
 int leb_bounds_static_max_traj(void);
 
-/* ---- the step after the LEB: tube centre and width (Sec. IV-A, Eqs. 18b, 20-21) --------------------- */
+/* ---- the step after the LEB: tube centre and width (Sec. V-A, Eqs. 18b, 20-21) --------------------- */
 /* For n_traj trajectories of horizon N (n_x states, n_u inputs) the zonotope of timestep j's disturbance
  * and linearization error is c_j + Ebar_j E_{2 n_x} with Ebar_j = [E(z_j)  diag(r_j)] (Eq. 18b; c_j, r_j
  * the Gamma map of the LEB, leb_options gamma_c / gamma_r), and the tube of timestep k is
@@ -343,6 +345,13 @@ leb_status leb_selftest_tan_sec(const float* x, int n, float* out_tan, float* ou
  * writes the nanoseconds it waited to *dev_waited_ns and returns; the context stays usable. */
 leb_status leb_selftest_wait_timeout(int* dev_flags, unsigned long long limit_ns, unsigned long long* dev_waited_ns,
                                      void* stream);
+/* Sets the limit of every wait of the quad-chain zonotope PBH kernel (its producer, consumer and writer
+ * warps; not the final wait for the copies already posted, which keeps the library's 2 s) for the
+ * handle's later calls; 0 restores the library's 2 s. With a short limit the waits run out while the
+ * pipeline still runs: the kernel must then record LEB_ASYNC_TIMEOUT and return (the bounds of that call
+ * are not valid), and the handle's next call with the default limit must work normally. A test of the
+ * kernel's failure path; QUAD_CHAIN handles only (others: LEB_ERR_UNSUPPORTED). */
+leb_status leb_selftest_set_wait_limit(leb_handle h, unsigned long long limit_ns);
 
 const char* leb_status_string(leb_status st);
 const char* leb_version(void);

@@ -7,7 +7,7 @@ written from the paper's definitions:
                        their Jacobians (Eq. 8) and hand-derived Hessian entries.
 * ``oracle.pbh``       set -> box hull (Eq. 18a, Eq. 21 row-l1 norm), the path-based Hessian bound
                        (Thm. 1, Eq. 15), the expanded and classic interval-Hessian bounds (Eqs. 12-13),
-                       and the zonotope map Gamma (Sec. III-C).
+                       and the zonotope map Gamma (Sec. IV-C).
 * ``oracle.crown``     MLP forward pass, Jacobian, activation relaxations, CROWN back-substitution
                        (Thm. 2) and the Jacobian-corrected remainder bound (Thm. 3), in torch FP64 on CPU
                        so that its gradient is available for the adjoint checks.
@@ -17,7 +17,7 @@ written from the paper's definitions:
 * ``oracle.proposer``  the learned bound proposer's MLP forward/backward/Adam step.
 * ``oracle.dynamics3d`` the satellite and (coupled) 3-D quadrotor models of App. A with their
                        hand-derived Hessian entries.
-* ``oracle.pbh_grad``  the gradient of the PBH bound (differentiable LEBs, Sec. III-D).
+* ``oracle.pbh_grad``  the gradient of the PBH bound (differentiable LEBs, Sec. IV-D).
 * ``oracle.tube``      the step after the LEB: Ebar_j = [E(z_j) R_j] (Eq. 18b) and the tube centre and
                        width h^mu, h^sigma (Eqs. 20-21) from packed system responses.
 

@@ -1,18 +1,18 @@
 """Path-based Hessian bound (Thm. 1) and its baselines, plain FP64.
 
-Steps, in the paper's order (Sec. III-A):
+Steps, in the paper's order (Sec. IV-A):
 
 1. Tube set -> box X (Eq. 18a box ``c + diag(sigma) E``, or a zonotope ``c + G E`` reduced to its interval
-   hull ``c +- ||G||_{1,r}`` with the row-wise l1 norm of Sec. II and Eq. 21), hulled with the nominal
+   hull ``c +- ||G||_{1,r}`` with the row-wise l1 norm of Sec. III and Eq. 21), hulled with the nominal
    point so that ``alpha~ in X`` as Thm. 1 requires.
 2. Displacement set Delta = X (-) alpha~ (Eq. 12).
 3. For each output row l and each structurally nonzero Hessian entry (j <= k):
    evaluate [H_{l,kj}] over the prefix set X^(j) (coordinates 0..j range over X, the rest are fixed at
-   the nominal; Sec. III-A, "coordinate-wise path"), multiply by Delta_j * Delta_k (j < k) or by
+   the nominal; Sec. IV-A, "coordinate-wise path"), multiply by Delta_j * Delta_k (j < k) or by
    1/2 Delta_k^2 (j = k, the interval of squares), and sum the terms one by one (Eq. 15).
 
 ``ih_expand`` (Eq. 13) evaluates every entry over the full X; ``ih_classic`` (Eq. 12) forms the interval
-quadratic form 1/2 Delta^T ([H](X) Delta). ``gamma_map`` is the zonotope map of Sec. III-C.
+quadratic form 1/2 Delta^T ([H](X) Delta). ``gamma_map`` is the zonotope map of Sec. IV-C.
 """
 from __future__ import annotations
 
@@ -124,7 +124,7 @@ def ih_classic(dyn, nominal, lo, hi):
 
 
 def gamma_map(r_lo: np.ndarray, r_hi: np.ndarray, pad: float = 0.0):
-    """Zonotope of an interval bound (Sec. III-C): c = (lo+hi)/2, R = diag((hi-lo)/2) (+ diagonal padding)."""
+    """Zonotope of an interval bound (Sec. IV-C): c = (lo+hi)/2, R = diag((hi-lo)/2) (+ diagonal padding)."""
     c = 0.5 * (np.asarray(r_lo, np.float64) + np.asarray(r_hi, np.float64))
     rad = 0.5 * (np.asarray(r_hi, np.float64) - np.asarray(r_lo, np.float64)) + pad
     return c, rad
@@ -138,7 +138,7 @@ def pbh_workload_row(dyn, nominal, radii=None, G=None, center=None):
 
 
 def split_pieces(nominal: np.ndarray, lo: np.ndarray, hi: np.ndarray, dims):
-    """Input-domain partitioning (Sec. III-D): the box cut at the nominal along each coordinate of
+    """Input-domain partitioning (Sec. IV-D): the box cut at the nominal along each coordinate of
     ``dims`` into its lower part [lo_j, a_j] and upper part [a_j, hi_j]; 2^len(dims) pieces, each still
     containing the nominal (Thm. 1). Yields (lo_p, hi_p) in the order of the bits of p (bit i = upper part
     of dims[i])."""

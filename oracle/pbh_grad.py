@@ -1,9 +1,9 @@
-"""Gradient of the path-based Hessian bound (Thm. 1) for differentiable LEBs (Sec. III-D), plain FP64.
+"""Gradient of the path-based Hessian bound (Thm. 1) for differentiable LEBs (Sec. IV-D), plain FP64.
 
 Test infrastructure (the oracle), not part of the product path.
 
-The paper calls for LEBs that are differentiable in the nominal point (Sec. III-D) and optimises nominal
-points by projected gradient descent on the PBH bound's width (Sec. IV, Table II). The bound is a
+The paper calls for LEBs that are differentiable in the nominal point (Sec. IV-D) and optimises nominal
+points by projected gradient descent on the PBH bound's width (Sec. VI-A, Table II). The bound is a
 piecewise-smooth function of the nominal point and the tube radii: interval endpoints are minima and
 maxima of endpoint values, and the range of sin / cos over an interval is either an endpoint value or an
 interior extremum (+-1). Its gradient here is that of the same algorithm with every such selection

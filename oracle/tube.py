@@ -1,9 +1,9 @@
-"""Tube centre and width from the linearization-error bounds (Sec. IV-A), plain FP64.
+"""Tube centre and width from the linearization-error bounds (Sec. V-A), plain FP64.
 
 Test infrastructure (the oracle), not part of the product path.
 
-The LEB of timestep j enters the SLS problem through the zonotope map Gamma (Sec. III-C): its centre
-c_j and diagonal radius R_j = diag(r_j) (Eq. 22 with the padding of Sec. IV-B). The zonotope of the
+The LEB of timestep j enters the SLS problem through the zonotope map Gamma (Sec. IV-C): its centre
+c_j and diagonal radius R_j = diag(r_j) (Eq. 22 with the padding of Sec. V-A). The zonotope of the
 exogenous disturbance and the linearization error is c_j + Ebar_j E_{2 n_x} with the generator matrix
 Ebar_j = [E(z_j)  R_j] (Eq. 18b). Given the system responses Phi_{k,j} = [Phi^x_{k,j}; Phi^u_{k,j}]
 ((n_x + n_u) x n_x, j < k), the tube centre and width of timestep k are (Eqs. 20-21)

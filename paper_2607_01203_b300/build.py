@@ -1,7 +1,8 @@
 """Builds the in-tree shared library ``libleb.so`` (the C ABI of include/leb.h) for sm_103a with nvcc.
 
 Usage: ``python -m paper_2607_01203_b300.build [--verbose]``. The library is rebuilt when any source under
-``csrc/`` or the public header is newer than it.
+``csrc/`` or the public header is newer than it. Every ``.cu`` file compiles to its own object (in parallel,
+under ``_build/`` next to this file), then one link step writes the library.
 """
 from __future__ import annotations
 
@@ -9,11 +10,14 @@ import glob
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libleb.so")
+OBJ = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 
 
 def sources():
@@ -36,16 +40,34 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if not force and not needs_build():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-I", os.path.join(ROOT, "include"), "-o", LIB + ".tmp", *sources()]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    os.makedirs(OBJ, exist_ok=True)
+    inc = ["-I", os.path.join(ROOT, "include")]
+
+    def compile_one(src):
+        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+        cmd = [nvcc, *ARCH, *FLAGS, *inc, "-c", "-o", obj, src]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        return obj, r
+
+    with ThreadPoolExecutor(max_workers=max(1, min(len(sources()), os.cpu_count() or 1))) as ex:
+        results = list(ex.map(compile_one, sources()))
+    failed = False
+    objs = []
+    for obj, r in results:
+        objs.append(obj)
+        if r.returncode != 0:
+            failed = True
+            sys.stderr.write(r.stdout + r.stderr)
+        elif verbose:
+            sys.stderr.write(r.stderr)
+    if failed:
+        raise RuntimeError("nvcc failed building libleb.so")
+    r = subprocess.run([nvcc, *ARCH, "-shared", "-o", LIB + ".tmp", *objs], capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)
-        raise RuntimeError("nvcc failed building libleb.so")
-    if verbose:
-        sys.stderr.write(r.stderr)
+        raise RuntimeError("nvcc failed linking libleb.so")
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

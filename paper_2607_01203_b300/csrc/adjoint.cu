@@ -1,4 +1,4 @@
-// Adjoint of the CROWN remainder bound (differentiable LEBs, Sec. III-D): dL/d(x~, u~, radii) for
+// Adjoint of the CROWN remainder bound (differentiable LEBs, Sec. IV-D): dL/d(x~, u~, radii) for
 // L = sum g_lo r_lo + g_hi r_hi, box sets centred at the nominal. FP32 on CUDA cores.
 //
 // The bound is a piecewise-smooth function of the nominal and the radii; its gradient is taken with the

@@ -1,4 +1,4 @@
-// Adjoint of the CROWN remainder bound (differentiable LEBs, Sec. III-D) on the tensor cores: the chain
+// Adjoint of the CROWN remainder bound (differentiable LEBs, Sec. IV-D) on the tensor cores: the chain
 // part of the reverse pass for reduced-precision (FP16 / BF16) handles.
 //
 // For one back-substitution target (the output rows, or the lower/upper rows of hidden layer `target`)
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
     auto epi_sync = [&]() -> bool {
       __syncwarp();
       if (lane == 0) mbar_arrive(ebar);
-      const bool res = mbar_wait(ebar, nbar & 1u);
+      const bool res = mbar_wait_warp(ebar, nbar & 1u);
       ++nbar;
       return res;
     };
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       if (lane == 0) mbar_arrive(a_full);
     };
     auto wait_acc = [&]() -> bool {
-      if (!mbar_wait(acc_full, nacc & 1u)) return false;
+      if (!mbar_wait_warp(acc_full, nacc & 1u)) return false;
       ++nacc;
       tc_fence_after();
       return true;

@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     auto epi_sync = [&]() -> bool {
       __syncwarp();
       if (lane == 0) mbar_arrive(ebar);
-      const bool res = mbar_wait(ebar, nbar & 1u);
+      const bool res = mbar_wait_warp(ebar, nbar & 1u);
       ++nbar;
       return res;
     };
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     };
     auto wait_free = [&](int b) -> bool {
       if ((apend >> b) & 1u) {
-        if (!mbar_wait(&a_free[b], (apar >> b) & 1u)) return false;
+        if (!mbar_wait_warp(&a_free[b], (apar >> b) & 1u)) return false;
         apar ^= 1u << b;
         apend &= ~(1u << b);
       }
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       if (lane == 0) mbar_arrive(&a_ready[b]);
     };
     auto wait_acc = [&](uint32_t hb) -> bool {
-      if (!mbar_wait(&acc_full[hb], (cpar >> hb) & 1u)) return false;
+      if (!mbar_wait_warp(&acc_full[hb], (cpar >> hb) & 1u)) return false;
       cpar ^= 1u << hb;
       tc_fence_after();
       return true;
@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(&xbar[cq]);
-          if (!mbar_wait(&xbar[cq], xph & 1u)) return false;
+          if (!mbar_wait_warp(&xbar[cq], xph & 1u)) return false;
           ++xph;
         }
 #pragma unroll

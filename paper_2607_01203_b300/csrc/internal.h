@@ -90,6 +90,7 @@ struct PbhArgs {
   const long long* pre1;    // [n_traj] sum_{b'<b} H_b' nq_b'
   const long long* pre2;    // [n_traj] sum_{b'<b} H_b' nq_b'^2
   int* counter;             // work-list counter
+  unsigned long long wait_ns;   // limit of the zonotope kernel's waits (the library's 2 s; shorter in a self-test)
   QuadConsts k;
 };
 
@@ -165,6 +166,7 @@ struct Ctx {
   MlpModel mlp;
   int sm_count = 148;
   int device = 0;
+  unsigned long long wait_ns = 2000000000ull;   // limit of the PBH zonotope kernel's waits (self-test: shorter)
   std::string plan_note;
   mutable KernelTimer timer;
 };

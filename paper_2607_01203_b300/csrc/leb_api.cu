@@ -286,6 +286,15 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
   if (opt && ((opt->gamma_c == nullptr) != (opt->gamma_r == nullptr))) return LEB_ERR_INVALID_ARG;
   if (opt && !(opt->gamma_pad >= 0.f)) return LEB_ERR_INVALID_ARG;
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return LEB_ERR_WORKSPACE;
+  // argument errors of each model are returned before anything is queued on the stream
+  if (h->kind == LEB_DYN_QUAD_CHAIN && T > 0) {
+    if (batch && (batch->n_traj < 1 || !batch->traj_offsets)) return LEB_ERR_INVALID_ARG;
+    if (ws_bytes < pbh_ws_bytes(batch && batch->traj_nquads ? batch->n_traj : 0)) return LEB_ERR_WORKSPACE;
+  }
+  if (h->kind == LEB_DYN_SATELLITE || h->kind == LEB_DYN_QUAD3D) {
+    if (ws_bytes < kWsHeader) return LEB_ERR_WORKSPACE;
+    if (T > 0 && (set->kind != LEB_SET_BOX || (batch && batch->traj_nquads))) return LEB_ERR_UNSUPPORTED;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(dev_flags, 0, sizeof(int), s) != cudaSuccess) return LEB_ERR_CUDA;
   if (T == 0) return LEB_OK;

@@ -17,6 +17,8 @@
 // Curved entries (all with prefix set X^(phi): phi ranges over X, the inputs sit at the nominal):
 //   v_x row: H_{phi phi} = (dt/m) S sin phi, H_{u_r phi} = -(dt/m) cos phi
 //   v_y row: H_{phi phi} = -(dt/m) S cos phi, H_{u_r phi} = -(dt/m) sin phi
+#include <mutex>
+
 #include "internal.h"
 #include "interval.cuh"
 #include "sync.cuh"
@@ -434,7 +436,8 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
   // on with the next timesteps, so the A/B stores overlap the generator stream instead of pausing it.
   __shared__ Item s_item[2];                  // timestep handed to the writer, per slot (nq < 0: end)
   __shared__ __align__(8) uint64_t wbar[4];   // [0..1] slot filled (consumers -> writer), [2..3] slot written
-  __shared__ int s_wok;
+  __shared__ __align__(8) GroupBar cbar;      // the consumer warps' barrier (bounded wait)
+  const unsigned long long lim = a.wait_ns;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const bool writer = (a.A != nullptr || a.B != nullptr) && nwarps >= 3;
   const int c_warp0 = writer ? 2 : 1;         // first consumer warp
@@ -455,6 +458,7 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
       mbar_init(&empty[s], ncons);
     }
     for (int b = 0; b < 4; ++b) mbar_init(&wbar[b], 1);
+    group_bar_init(&cbar, (uint32_t)ncons);
     mbar_fence_init();
   }
   __syncthreads();
@@ -463,7 +467,7 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
     // ---- writer: A_k, B_k rows of each finished timestep, slots in turn ----------------------------
     uint32_t par = 0;
     for (int slot = 0;; slot ^= 1) {
-      if (!mbar_wait(&wbar[slot], (par >> slot) & 1u)) {
+      if (!mbar_wait_warp_for(&wbar[slot], (par >> slot) & 1u, lim)) {
         if (lane == 0) atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
         break;
       }
@@ -495,7 +499,7 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
         for (int c = 0; c < nch; ++c, ++k) {
           const int s = (int)(k % (uint32_t)S);
           const uint32_t ph = (k / (uint32_t)S) & 1u;
-          if (k >= (uint32_t)S && !mbar_wait(&empty[s], ph ^ 1u)) { ok = false; break; }
+          if (k >= (uint32_t)S && !mbar_wait_for(&empty[s], ph ^ 1u, lim)) { ok = false; break; }
           if (done) {
             meta[s] = StageMeta{-1, 0, 1, 0, 1, 0, 0, 0};
             mbar_arrive(&full[s]);
@@ -509,24 +513,25 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
           }
         }
       }
-      if (!ok) {
-        atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
-        // drain: every posted copy must land before the block exits
-        for (uint32_t j = (k > (uint32_t)S ? k - (uint32_t)S : 0u); j < k; ++j)
-          mbar_wait(&full[j % (uint32_t)S], (j / (uint32_t)S) & 1u);
-      }
+      if (!ok) atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
+      // drain: every posted copy must land before the block exits, also when the consumers gave up
+      // early (the library's full limit here, whatever the kernel's wait limit: a valid copy always lands)
+      for (uint32_t j = (k > (uint32_t)S ? k - (uint32_t)S : 0u); j < k; ++j)
+        mbar_wait(&full[j % (uint32_t)S], (j / (uint32_t)S) & 1u);
     }
     __syncwarp();
   } else {
     // ---- consumers ---------------------------------------------------------------------------
+    // A warp whose own wait runs out leaves the loop; the consumers' barriers are mbarrier waits bounded
+    // like every other, so the warps that stay give up at their next barrier instead of hanging there.
     const int cw = warp - c_warp0, ctid = threadIdx.x - 32 * c_warp0;
-    uint32_t k = 0;
+    uint32_t k = 0, gph = 0;
     int slot = 0;
     uint32_t used = 0, wpar = 0;   // writer slots handed over, and their completion parities
     // thread 0: wait until the writer is done with a slot (if it was handed over); true if free
     auto slot_free = [&](int sl) -> bool {
       if (!((used >> sl) & 1u)) return true;
-      const bool r = mbar_wait(&wbar[2 + sl], (wpar >> sl) & 1u);
+      const bool r = mbar_wait_for(&wbar[2 + sl], (wpar >> sl) & 1u, lim);
       wpar ^= 1u << sl;
       used &= ~(1u << sl);
       return r;
@@ -536,7 +541,7 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
     for (;;) {
       const int s = (int)(k % (uint32_t)S);
       const uint32_t ph = (k / (uint32_t)S) & 1u;
-      if (!mbar_wait(&full[s], ph)) {
+      if (!mbar_wait_warp_for(&full[s], ph, lim)) {
         if (ctid == 0) atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
         break;
       }
@@ -559,9 +564,10 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
       QuadA* qa = s_qa + slot * a.nq;
       if (m.chunk == 0 && writer) {
         // the slot's per-quadrotor values are rewritten below: the writer must be done with them
-        if (ctid == 0) s_wok = slot_free(slot) ? 1 : 0;
-        bar_sync(2, ncthr);
-        if (!s_wok) {
+        const bool busy = ctid == 0 && !slot_free(slot);
+        bool gok;
+        const bool any_busy = group_sync_or(&cbar, gph, busy, &gok, lim);
+        if (any_busy || !gok) {
           if (ctid == 0) atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
           break;
         }
@@ -578,7 +584,12 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
       if (lane == 0) mbar_arrive(&empty[s]);
       ++k;
       if (m.last) {
-        const bool bad = bar_sync_or(1, ncthr, !ok);
+        bool gok;
+        const bool bad = group_sync_or(&cbar, gph, !ok, &gok, lim);
+        if (!gok) {
+          if (ctid == 0) atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
+          break;
+        }
         ok = true;
         pbh_rows<kSplit>(a, it, xn, un, lo, hi, qa, bad, ctid, ncthr);
         if (writer) {
@@ -590,7 +601,12 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
           }
         } else {
           write_AB_zero(a, it, ctid, ncthr);
-          bar_sync(2, ncthr);
+          bool gok;
+          group_sync_or(&cbar, gph, false, &gok, lim);
+          if (!gok) {
+            if (ctid == 0) atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
+            break;
+          }
           write_AB_nz(a, it, qa, ctid, ncthr);
         }
         if (bad && ctid == 0) atomicOr(a.flags, LEB_ASYNC_NONFINITE);
@@ -641,20 +657,38 @@ size_t pbh_tma_smem(const PbhArgs& a, int S) {
   return b + 2 * (size_t)S * 8;
 }
 
-cudaError_t launch_pbh(const Ctx& c, const PbhArgs& a, const PbhPlan& p, cudaStream_t s) {
+// The zonotope kernel's dynamic shared-memory opt-in, set once per device (the attribute is per device,
+// and the first calls of several host threads may race).
+static cudaError_t pbh_tma_attr() {
+  constexpr int kMaxDev = 64;
+  static std::once_flag once[kMaxDev];
+  static cudaError_t err[kMaxDev];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  std::call_once(once[dev], [dev]() {
+    cudaError_t r = cudaSuccess;
+    // the opt-in limit covers the kernel's static shared memory too
+    for (const void* f : {(const void*)pbh_zono_tma_kernel<false>, (const void*)pbh_zono_tma_kernel<true>}) {
+      cudaFuncAttributes fa{};
+      const size_t stat = cudaFuncGetAttributes(&fa, f) == cudaSuccess ? fa.sharedSizeBytes : 1024;
+      const cudaError_t e2 = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(227 * 1024 - stat));
+      if (e2 != cudaSuccess) r = e2;
+    }
+    err[dev] = r;
+  });
+  return err[dev];
+}
+
+cudaError_t launch_pbh(const Ctx& c, const PbhArgs& args, const PbhPlan& p, cudaStream_t s) {
   const int grid = c.sm_count * p.ctas_per_sm;
+  PbhArgs a = args;
+  a.wait_ns = c.wait_ns;
   if (pbh_tma_ok(a)) {
     const size_t smem = pbh_tma_smem(a, p.stages);
-    static bool attr = false;
-    if (!attr) {
-      // the opt-in limit covers the kernel's static shared memory too
-      for (const void* f : {(const void*)pbh_zono_tma_kernel<false>, (const void*)pbh_zono_tma_kernel<true>}) {
-        cudaFuncAttributes fa{};
-        const size_t stat = cudaFuncGetAttributes(&fa, f) == cudaSuccess ? fa.sharedSizeBytes : 1024;
-        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(227 * 1024 - stat));
-      }
-      attr = true;
-    }
+    const cudaError_t e = pbh_tma_attr();
+    if (e != cudaSuccess) return e;
     if (a.k.split_phi) pbh_zono_tma_kernel<true><<<grid, p.block, smem, s>>>(a, p.stages, kPbhStageCap);
     else pbh_zono_tma_kernel<false><<<grid, p.block, smem, s>>>(a, p.stages, kPbhStageCap);
     return cudaGetLastError();

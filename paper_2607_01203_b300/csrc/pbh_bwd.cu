@@ -1,5 +1,5 @@
 // Adjoint of the path-based Hessian bound (Thm. 1) for the quadrotor chain, and projected gradient descent
-// on the nominal points with it (differentiable LEBs, Sec. III-D; the nominal optimisation of Sec. IV,
+// on the nominal points with it (differentiable LEBs, Sec. IV-D; the nominal optimisation of Sec. VI-A,
 // Table II).
 //
 // For a box set of radii rho centred at the nominal (hulled with it), Delta = [-rho, rho] and the only

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(128, 2) prop_tc_gemm_kernel(const __grid_const
   }
   __syncwarp();
   // ---- epilogue: thread = row m0 + 32 warp + lane, TMEM lane of the same index ---------------------
-  const bool ok = mbar_wait(acc, 0u) && !*(volatile int*)&s_fail;
+  const bool ok = mbar_wait_warp(acc, 0u) && !*(volatile int*)&s_fail;
   tc_fence_after();
   const int row = m0 + warp * 32 + lane;
   const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);

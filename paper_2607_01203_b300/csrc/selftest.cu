@@ -60,3 +60,11 @@ extern "C" leb_status leb_selftest_tan_sec(const float* x, int n, float* out_tan
   leb::tan_sec_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(x, n, (float2*)out_tan, (float2*)out_sec);
   return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
 }
+
+extern "C" leb_status leb_selftest_set_wait_limit(leb_handle h, unsigned long long limit_ns) {
+  if (!h || limit_ns > 4000000000ull) return LEB_ERR_INVALID_ARG;
+  leb::Ctx& c = *reinterpret_cast<leb::Ctx*>(h);
+  if (c.kind != LEB_DYN_QUAD_CHAIN) return LEB_ERR_UNSUPPORTED;
+  c.wait_ns = limit_ns ? limit_ns : 2000000000ull;
+  return LEB_OK;
+}

@@ -8,7 +8,8 @@
 //
 // That array lives in every GPU that loads the library until the process exits. In host code its name
 // is only a host-side stand-in, so the device address is looked up once per device with
-// cudaGetSymbolAddress (with that device current) on the first call on that device and cached. All
+// cudaGetSymbolAddress (with that device current) on the first call on that device and cached (a device
+// reset reloads the module and makes the cached address stale: no call after a reset). All
 // calls share the array: the counter is cleared at the start of every call, and calls whose work overlaps
 // on the GPU (different streams, or different host threads on one device) race on it and must not be
 // issued concurrently.
@@ -64,6 +65,8 @@ extern "C" leb_status leb_bounds_static(leb_handle h, const leb_batch* batch, in
   if (c.kind == LEB_DYN_SATELLITE || c.kind == LEB_DYN_QUAD3D) {   // no scratch needed
     if (set->kind != LEB_SET_BOX && set->kind != LEB_SET_ZONO) return LEB_ERR_INVALID_ARG;
     if (T > 0 && set->kind == LEB_SET_BOX && !set->radii) return LEB_ERR_INVALID_ARG;
+    // what these models do not support is refused before anything is queued on the stream
+    if (set->kind != LEB_SET_BOX || (batch && batch->traj_nquads)) return LEB_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(dev_flags, 0, sizeof(int), s) != cudaSuccess) return LEB_ERR_CUDA;
     if (T == 0) return LEB_OK;

@@ -58,6 +58,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return mbar_wait_for(bar, parity, kWaitLimitNs);
 }
 
+// A wait that all 32 lanes of a warp make together (each lane waits, so each has its own acquire of the
+// phase): the result is the same in every lane. Without the vote, lanes whose waits end on either side of
+// the limit would take different branches, and a later warp-wide shuffle or __syncwarp would wait for
+// lanes that have left.
+__device__ __forceinline__ bool mbar_wait_warp_for(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
+  return __all_sync(0xffffffffu, mbar_wait_for(bar, parity, limit_ns));
+}
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_warp_for(bar, parity, kWaitLimitNs);
+}
+
 // Bulk (non-tensor) async copy global -> shared, completion counted in bytes on an mbarrier.
 // Source, destination and size must be multiples of 16 bytes.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -83,6 +94,40 @@ __device__ __forceinline__ bool bar_sync_or(int id, int count, bool pred) {
 
 __device__ __forceinline__ void bar_sync(int id, int count) {
   asm volatile("barrier.cta.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Barrier among the warps of a group (one arrival per warp, the mbarrier initialised with the group's
+// warp count) whose wait is bounded, unlike a named barrier: if a warp of the group has left after a
+// wait of its own ran out, the others give up after the limit too instead of waiting forever. It also
+// ORs a per-thread predicate over the group. The OR words rotate over three phases: the word of phase
+// p + 2 is cleared after phase p completes, when no warp can still read it (its readers all arrived
+// at phase p) and none can write it yet (its writers must first pass phase p + 1).
+struct GroupBar {
+  uint64_t bar;
+  int orw[3];
+};
+
+__device__ __forceinline__ void group_bar_init(GroupBar* g, uint32_t warps) {
+  mbar_init(&g->bar, warps);
+  g->orw[0] = g->orw[1] = g->orw[2] = 0;
+}
+
+// Every lane of every warp of the group calls this with the same phase counter (advanced here).
+// Returns the OR of pred over the group; *ok = false if the wait ran out (the result is then unusable).
+__device__ __forceinline__ bool group_sync_or(GroupBar* g, uint32_t& phase, bool pred, bool* ok,
+                                              unsigned long long limit_ns) {
+  const bool any = __any_sync(0xffffffffu, pred);
+  const int slot = (int)(phase % 3u);
+  if ((threadIdx.x & 31) == 0) {
+    if (any) atomicOr(&g->orw[slot], 1);
+    mbar_arrive(&g->bar);
+  }
+  *ok = mbar_wait_warp_for(&g->bar, phase & 1u, limit_ns);
+  const bool res = *(volatile int*)&g->orw[slot] != 0;
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) g->orw[(slot + 2) % 3] = 0;
+  ++phase;
+  return res;
 }
 
 }  // namespace leb

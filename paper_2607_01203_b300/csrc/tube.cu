@@ -1,11 +1,11 @@
-// The step after the LEB (Sec. IV-A): the zonotope generator matrix Ebar_j = [E(z_j) R_j] (Eq. 18b) of
+// The step after the LEB (Sec. V-A): the zonotope generator matrix Ebar_j = [E(z_j) R_j] (Eq. 18b) of
 // every timestep and the tube centre and width of Eqs. 20-21,
 //
 //     h^mu_k[l]    = sum_{j<k} sum_i Phi_{k,j}[l,i] c_j[i],
 //     h^sigma_k[l] = sum_{j<k} || (Phi_{k,j} Ebar_j)[l,:] ||_1 = sum_{j<k} sum_i |Phi_{k,j}[l,i]| (|e_j[i]| + r_j[i]),
 //
 // the second form because E(z_j) = diag(e_j) and R_j = diag(r_j) are diagonal (the Gamma map of
-// Sec. III-C and the paper's constant disturbance scaling), so the row-wise l1 norm of the product splits
+// Sec. IV-C and the paper's constant disturbance scaling), so the row-wise l1 norm of the product splits
 // column by column. Both are read-once streams of the packed responses Phi: HBM-bound.
 //
 // Soundness: h^sigma is summed with every product and sum rounded up (all terms are non-negative);

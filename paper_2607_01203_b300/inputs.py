@@ -22,7 +22,7 @@ Workloads (shapes follow the paper's systems, App. A, at synthetic sizes):
                       state / input ranges, local box sets (z, v) + eps E (the width-vs-eps study).
 * ``tube``            system responses Phi_{k,j} of a stable LTV closed loop (packed lower-triangular
                       blocks) with Gamma-map centres / radii and a diagonal disturbance scaling, the
-                      inputs of the tube centre and width (Sec. IV-A).
+                      inputs of the tube centre and width (Sec. V-A).
 * ``quad3d``          N 3-D quadrotors (App. A "Coupled 3D Quadrotor"), optionally coupled by the
                       centroid spring-damper (alpha = 0.75, gamma = 0.25), drawn the same way; the
                       paper's 168-state system is 14 coupled quadrotors over a horizon of 25.

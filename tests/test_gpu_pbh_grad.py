@@ -1,5 +1,5 @@
-"""GPU parity of the adjoint of the PBH bound (Thm. 1; differentiable LEBs, Sec. III-D) and of the nominal
-refinement by projected gradient descent (Sec. IV, Table II), through the C ABI.
+"""GPU parity of the adjoint of the PBH bound (Thm. 1; differentiable LEBs, Sec. IV-D) and of the nominal
+refinement by projected gradient descent (Sec. VI-A, Table II), through the C ABI.
 
 Tolerance of the gradient: the kernel differentiates the same algorithm as the FP64 oracle, with the
 same interval selections, in FP32 (round to nearest, sincosf accurate to a few ulps at the rollouts'

@@ -233,7 +233,7 @@ def dataclass_with(w, **kw):
 
 
 def test_options_static_entry_and_gamma():
-    """The zonotope map outputs of Sec. III-C, and leb_bounds_static giving the same bits as leb_bounds."""
+    """The zonotope map outputs of Sec. IV-C, and leb_bounds_static giving the same bits as leb_bounds."""
     w = inputs.quad3d(T=100, n_quads=3, eps=0.1, coupled=True)
     h, _ = _pair(w)
     g = run_gpu(h, w, gamma_pad=1e-3, want_eps=True)

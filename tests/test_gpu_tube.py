@@ -1,4 +1,4 @@
-"""GPU parity of the tube centre and width after the LEB (Sec. IV-A, Eqs. 18b, 20-21) against the FP64
+"""GPU parity of the tube centre and width after the LEB (Sec. V-A, Eqs. 18b, 20-21) against the FP64
 oracle, through the C ABI.
 
 Tolerance (from the kernel's FP32 arithmetic): sigma is a sum of m = k n_x non-negative products per

@@ -1,4 +1,4 @@
-"""Pins of the FP64 gradient oracle of the PBH bound (Thm. 1, differentiable LEBs of Sec. III-D), CPU only."""
+"""Pins of the FP64 gradient oracle of the PBH bound (Thm. 1, differentiable LEBs of Sec. IV-D), CPU only."""
 import math
 
 import numpy as np

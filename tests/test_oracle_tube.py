@@ -1,4 +1,4 @@
-"""Pins of the oracle's tube centre and width (Sec. IV-A, Eqs. 18b, 20-21), CPU only."""
+"""Pins of the oracle's tube centre and width (Sec. V-A, Eqs. 18b, 20-21), CPU only."""
 import itertools
 
 import numpy as np
