@@ -562,16 +562,7 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
       float* lo = s_lo + slot * n_max;
       float* hi = s_hi + slot * n_max;
       QuadA* qa = s_qa + slot * a.nq;
-      if (m.chunk == 0 && writer) {
-        // the slot's per-quadrotor values are rewritten below: the writer must be done with them
-        const bool busy = ctid == 0 && !slot_free(slot);
-        bool gok;
-        const bool any_busy = group_sync_or(&cbar, gph, busy, &gok, lim);
-        if (any_busy || !gok) {
-          if (ctid == 0) atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
-          break;
-        }
-      }
+      // (the writer released this slot before the previous timestep's barrier)
       if (m.chunk == 0) compute_qa(xn, un, it.nq, a.k, qa, ctid, ncthr);
       const int p = it.n_gen;
       const int rows_per = m.rows_per;
@@ -584,12 +575,16 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
       if (lane == 0) mbar_arrive(&empty[s]);
       ++k;
       if (m.last) {
+        // One barrier per timestep: every row of the box is in place, the non-finite check is ORed, and
+        // the slot of the next timestep (rewritten right after it) has been released by the writer.
+        const bool busy = writer && ctid == 0 && !slot_free(slot ^ 1);
         bool gok;
-        const bool bad = group_sync_or(&cbar, gph, !ok, &gok, lim);
-        if (!gok) {
+        const uint32_t orb = group_sync_or(&cbar, gph, (ok ? 0u : 1u) | (busy ? 2u : 0u), &gok, lim);
+        if (!gok || (orb & 2u)) {
           if (ctid == 0) atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
           break;
         }
+        const bool bad = (orb & 1u) != 0;
         ok = true;
         pbh_rows<kSplit>(a, it, xn, un, lo, hi, qa, bad, ctid, ncthr);
         if (writer) {
@@ -599,10 +594,9 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
             mbar_arrive(&wbar[slot]);
             used |= 1u << slot;
           }
-        } else {
+        } else if (a.A || a.B) {
           write_AB_zero(a, it, ctid, ncthr);
-          bool gok;
-          group_sync_or(&cbar, gph, false, &gok, lim);
+          group_sync_or(&cbar, gph, 0u, &gok, lim);
           if (!gok) {
             if (ctid == 0) atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
             break;

@@ -113,18 +113,18 @@ __device__ __forceinline__ void group_bar_init(GroupBar* g, uint32_t warps) {
 }
 
 // Every lane of every warp of the group calls this with the same phase counter (advanced here).
-// Returns the OR of pred over the group; *ok = false if the wait ran out (the result is then unusable).
-__device__ __forceinline__ bool group_sync_or(GroupBar* g, uint32_t& phase, bool pred, bool* ok,
-                                              unsigned long long limit_ns) {
-  const bool any = __any_sync(0xffffffffu, pred);
+// Returns the OR of every thread's bits over the group; *ok = false if the wait ran out (the result is
+// then unusable).
+__device__ __forceinline__ uint32_t group_sync_or(GroupBar* g, uint32_t& phase, uint32_t bits, bool* ok,
+                                                  unsigned long long limit_ns) {
+  const uint32_t wor = __reduce_or_sync(0xffffffffu, bits);
   const int slot = (int)(phase % 3u);
   if ((threadIdx.x & 31) == 0) {
-    if (any) atomicOr(&g->orw[slot], 1);
+    if (wor) atomicOr(&g->orw[slot], (int)wor);
     mbar_arrive(&g->bar);
   }
   *ok = mbar_wait_warp_for(&g->bar, phase & 1u, limit_ns);
-  const bool res = *(volatile int*)&g->orw[slot] != 0;
-  __syncwarp();
+  const uint32_t res = (uint32_t)*(volatile int*)&g->orw[slot];
   if ((threadIdx.x & 31) == 0) g->orw[(slot + 2) % 3] = 0;
   ++phase;
   return res;

@@ -224,6 +224,33 @@ def tanh_mlp(seed: int = SEED_BASE + 4, n_traj: int = 128, N: int = 50, widths=(
     return Workload("tanh_mlp", "mlp", n_x, n_u, X, U, offs, "box", radii=radii, Ws=Ws, bs=bs, act="tanh")
 
 
+def tanh_mlp_cancelling(seed: int = SEED_BASE + 9, N: int = 8, widths=(64, 512, 512, 32), scale: float = 2.0,
+                        radius: float = 1e-5) -> Workload:
+    """An adversarial residual tanh MLP for the reduced-precision rounding terms: weights four times the
+    workloads' scale (scale * N(0, 1/fan_in)) and cancelling pairs of hidden neurons (neuron j + w/2 of each
+    hidden layer copies neuron j's incoming weights up to a 1 % perturbation; the next layer takes it with
+    the opposite sign, up to 1 %), so that the Jacobian is small next to the sum of the magnitudes of its
+    terms, which is what the operand rounding scales with. Nominal points N(0, 0.5^2) per coordinate, drawn
+    independently per timestep; box radius ``radius`` everywhere."""
+    rng = _rng(seed)
+    Ws, bs = _mlp_weights(rng, widths, scale)
+    for i in range(len(widths) - 2):
+        h = widths[i + 1] // 2
+        W = Ws[i].astype(np.float64)
+        W[h:2 * h] = W[:h] * (1.0 + 0.01 * rng.standard_normal(W[:h].shape))
+        Ws[i] = W.astype(np.float32)
+        Wn = Ws[i + 1].astype(np.float64)
+        Wn[:, h:2 * h] = -Wn[:, :h] * (1.0 + 0.01 * rng.standard_normal(Wn[:, :h].shape))
+        Ws[i + 1] = Wn.astype(np.float32)
+    n_x = widths[-1]
+    n_u = widths[0] - n_x
+    X = (0.5 * rng.standard_normal((N, n_x))).astype(np.float32)
+    U = (0.5 * rng.standard_normal((N, n_u))).astype(np.float32)
+    radii = np.full((N, widths[0]), radius, np.float32)
+    return Workload("tanh_mlp_cancelling", "mlp", n_x, n_u, X, U, np.array([0, N], np.int32), "box", radii=radii,
+                    Ws=Ws, bs=bs, act="tanh")
+
+
 def proposer_data(seed: int = SEED_BASE + 5, n_rollouts: int = 2000, N: int = 50, n_quads: int = 28,
                   spring_k: float = 0.5, state_radius=(0.01, 0.1), control_radius: float = 0.05) -> Workload:
     """Quad-chain rollouts with box sets: state radii U[0.01, 0.1], control radii fixed."""
