@@ -502,7 +502,21 @@ class ProposerForm(Form):
         lo_p, hi_p, lo_c, hi_c = P[:, curved], P[:, curved + 168], Yv[:, curved], Yv[:, curved + 168]
         wmean = (hi_c - lo_c).mean()
         self.err = ((lo_p - lo_c).abs().mean() + (hi_p - hi_c).abs().mean()).item() / 2 / wmean.item()
-        self.under = ((lo_p > lo_c) | (hi_p < hi_c)).float().mean().item()
+        # calibration (leb_proposer_calibrate, q = 0.985 per side) on the first half of the held-out 10 %,
+        # under-coverage measured on the second half, before and after
+        n_cal = n_tr + (X.shape[0] - n_tr) // 2
+
+        def cover(P_):
+            lp, hp = P_[:, curved], P_[:, curved + 168]
+            lc, hc = Y[n_cal:][:, curved], Y[n_cal:][:, curved + 168]
+            return ((lp > lc) | (hp < hc)).float().mean().item(), ((hp - lp).mean() / (hc - lc).mean()).item()
+
+        self.under_raw, self.width_raw = cover(self.p.forward(X[n_cal:]))
+        self.p.calibrate(X[n_tr:n_cal], Y[n_tr:n_cal], n_lower=168, q=0.985)
+        self.under, self.width_cal = cover(self.p.forward(X[n_cal:]))
+        self.train4096 = self._train_batch(torch, X[:n_tr], Y[:n_tr], 4096)
+        # the same step where the GEMMs rather than the ~20 launches set the time
+        self.train_large = self._train_batch(torch, X[:n_tr], Y[:n_tr], 32768 if not quick else 8192)
         # inference batch: 12800 fresh inputs
         t = inputs.proposer_data(seed=1777, n_rollouts=256)
         self.T = t.T
@@ -515,6 +529,24 @@ class ProposerForm(Form):
         torch.cuda.synchronize()
         self.large = self._large_batch(torch, dev, 10 ** 5 if quick else 10 ** 6)
         self.desc = "proposer 392-256-256-336 inference, 12800 quad-chain box inputs"
+
+    def _train_batch(self, torch, X, Y, B):
+        """Once at start-up (untimed in the step): training steps at batch B on a copy of the trained
+        proposer's state (the served proposer is left as it is), ms per step and its rate against the BF16
+        peak. FLOPs per sample: forward 2 (392 x 256 + 256 x 256 + 256 x 336), the weight gradients as many,
+        the input gradients of layers 2 and 1, 2 (336 x 256 + 256 x 256)."""
+        from paper_2607_01203_b300.proposer import Proposer
+        q = Proposer(seed=2)
+        q.load_state_bytes(self.p.state_bytes())
+        xb, yb = X[:B].contiguous(), Y[:B].contiguous()
+        q.train_step(xb, yb, 1e-4)
+        ms = timed_loop(torch, lambda: q.train_step(xb, yb, 1e-4), 20)
+        flop = (2 * PROPOSER_FLOP + 2 * (336 * 256 + 256 * 256)) * B
+        tf = flop / (ms * 1e-3) / 1e12
+        return {"batch": B, "ms_per_step": round(ms, 4), "samples_per_s": round(B / (ms * 1e-3), 1),
+                "tflops": round(tf, 2), "frac_of_bf16_peak": round(tf / peaks()["bf16_tflops"], 4),
+                "gemms": "tcgen05 (prop_tc_gemm_kernel: 3 forward, 3 weight gradients split over the batch, "
+                         "2 input gradients)"}
 
     def _large_batch(self, torch, dev, B):
         """Once at start-up (untimed in the step): inference on B inputs (the 12800 of the step repeated),
@@ -1150,8 +1182,14 @@ def main():
             d["tube_timesteps_per_s"] = round(f.w.n_traj * f.w.N / (form_ms["tube"] * 1e-3), 1)
         if f.name == "proposer":
             cms = f.certified_ms()
-            d.update({"proposal_error_vs_certified": round(f.err, 4), "under_cover_fraction": round(f.under, 4),
+            d.update({"proposal_error_vs_certified": round(f.err, 4),
+                      "under_cover_fraction": round(f.under, 4),
+                      "under_cover_fraction_uncalibrated": round(f.under_raw, 4),
+                      "proposed_over_certified_width": {"uncalibrated": round(f.width_raw, 4),
+                                                        "calibrated": round(f.width_cal, 4)},
                       "train_step_ms_batch256": round(f.train_ms_per_step, 4),
+                      "train_batch4096": f.train4096,
+                      "train_large_batch": f.train_large,
                       "certified_pbh_box_ms_same_inputs": round(cms, 4),
                       "speedup_vs_certified": round(cms / form_ms["proposer"], 3),
                       "large_batch": f.large})

@@ -274,7 +274,11 @@ leb_status leb_proposer_forward(leb_proposer p, int B, const float* X, float* Y,
                                 size_t ws_bytes, void* stream);
 /* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the mean-squared error between the network
  * output and the targets Ytgt [B, n_out] (given in original units; standardised inside with out_mean,
- * out_std); loss (device float, may be NULL) receives the mean squared error in standardised units. */
+ * out_std); loss (device float, may be NULL) receives the mean squared error in standardised units.
+ * The GEMMs of the step run on the tensor cores (tcgen05, BF16 operands, FP32 accumulation; the weight
+ * gradients split over the batch in parts summed in a fixed order, so a step is deterministic) when every
+ * layer width fits them (n_in, n_hidden multiples of 8, n_hidden and n_out at most 512 and split into
+ * column parts of a multiple of 16) and B is a multiple of 8; otherwise on CUDA cores, same arithmetic. */
 leb_status leb_proposer_train_step(leb_proposer p, int B, const float* X, const float* Ytgt, float lr,
                                    float* loss, void* workspace, size_t ws_bytes, void* stream);
 leb_status leb_proposer_workspace_size(leb_proposer p, int B_max, size_t* bytes);
@@ -288,6 +292,21 @@ leb_status leb_proposer_get_grad(leb_proposer p, int i, float* dW, float* db, vo
  * bytes (a small header of the dimensions first). save copies out and waits for the copies (it
  * synchronizes the stream); load refuses a buffer of other dimensions (LEB_ERR_INVALID_ARG) and makes a
  * proposer continue exactly as the saved one would have. */
+/* Calibration of the proposals against certified bounds (not in the paper; a split-conformal margin per
+ * output). X [B, n_in] held-out inputs, Y [B, n_out] their certified bounds (device), the first n_lower
+ * outputs lower bounds and the rest upper bounds. For each output the residual by which the proposal is
+ * narrower than the certified bound (lower: proposal - certified; upper: certified - proposal) is taken
+ * over the B samples, and the output's margin set to its k-th smallest value, k = ceil(q (B + 1)) (at
+ * least 0). From then on leb_proposer_forward returns lower outputs minus their margin and upper outputs
+ * plus theirs, so that on data from the same distribution a fraction of about 1 - q of each output's
+ * proposals is narrower than the certified bound. The proposals are still not certified: the certified
+ * kernels stay the final answer. 1 <= B <= 16384, 0 < q < 1, workspace as leb_proposer_workspace_size(B).
+ * Training steps are not affected; the margins are part of the saved state. */
+leb_status leb_proposer_calibrate(leb_proposer p, int B, const float* X, const float* Y, int n_lower, float q,
+                                  void* workspace, size_t ws_bytes, void* stream);
+/* The signed per-output offsets (device [n_out]: -margin for lower outputs, +margin for upper) and whether
+ * they are applied (*calibrated, host). */
+leb_status leb_proposer_get_offset(leb_proposer p, float* offset, int* calibrated, void* stream);
 leb_status leb_proposer_state_size(leb_proposer p, size_t* bytes);
 leb_status leb_proposer_save_state(leb_proposer p, void* host_buf, size_t bytes, void* stream);
 leb_status leb_proposer_load_state(leb_proposer p, const void* host_buf, size_t bytes, void* stream);

@@ -62,7 +62,7 @@ EXPORTS = [
     "leb_bounds_static", "leb_bounds_static_max_traj", "leb_proposer_fit_norm", "leb_proposer_set_periodic", "leb_timing", "leb_timing_read", "leb_status_string", "leb_version",
     "leb_refine_nominal_pgd", "leb_refine_workspace_size", "leb_selftest_tan_sec", "leb_tube", "leb_bounds_backward_saved",
     "leb_proposer_state_size", "leb_proposer_save_state", "leb_proposer_load_state", "leb_selftest_wait_timeout",
-    "leb_selftest_set_wait_limit",
+    "leb_selftest_set_wait_limit", "leb_proposer_calibrate", "leb_proposer_get_offset",
 ]
 
 
@@ -114,6 +114,8 @@ def lib():
         L.leb_tube.argtypes = [i32, i32, i32, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp]
         L.leb_selftest_wait_timeout.argtypes = [vp, C.c_ulonglong, vp, vp]
         L.leb_selftest_set_wait_limit.argtypes = [vp, C.c_ulonglong]
+        L.leb_proposer_calibrate.argtypes = [vp, i32, vp, vp, i32, C.c_float, vp, sz, vp]
+        L.leb_proposer_get_offset.argtypes = [vp, vp, C.POINTER(i32), vp]
         L.leb_proposer_state_size.argtypes = [vp, C.POINTER(sz)]
         L.leb_proposer_save_state.argtypes = [vp, vp, sz, vp]
         L.leb_proposer_load_state.argtypes = [vp, vp, sz, vp]

@@ -12,6 +12,8 @@
 #include <vector>
 #include <algorithm>
 
+#include <math_constants.h>
+
 #include "internal.h"
 #include "tc_ptx.cuh"
 
@@ -35,6 +37,17 @@ struct leb_proposer_s {
   __nv_bfloat16* Wb[3] = {};
   CUtensorMap wmap[3];
   int parts[3] = {};                    // column parts of each layer (one CTA each per 128-row tile)
+  // training on the tensor cores: transposed BF16 copies W_i^T [in, out] of layers 1 and 2 (the B operand
+  // of the input gradients d_{i-1} = (d_i W_i) o (h_{i-1} > 0)), refreshed with the copies above
+  __nv_bfloat16* WbT[3] = {};
+  CUtensorMap wTmap[3];
+  // calibration: per-output additive offset of the proposals (leb_proposer_calibrate)
+  float* offset = nullptr;
+  bool calibrated = false;
+  // the training step's operand maps, kept while the workspace and the batch stay the same
+  const void* tr_ws = nullptr;
+  int tr_B = 0;
+  CUtensorMap tr_maps[11];
 };
 
 namespace leb {
@@ -67,11 +80,34 @@ static inline int pt_stages(int N) {
 // Dynamic shared memory of a launch: alignment slack, the ring, its barriers and the accumulator barrier.
 static inline int pt_smem(int N, int stages) { return 1024 + stages * (kPtATile + N * 128) + (2 * stages + 1) * 8; }
 
+// What the epilogue does with a tile (every pointer optional). Column n is global (n0 + local column),
+// row m global. In order: x = acc + bias[n]; ReLU; x = 0 where mask[m, n] <= 0 (the ReLU derivative of a
+// stored BF16 activation); x = x std[n] + mean[n] (back to the bounds' units); x += offset[n]. Then
+// stores: BF16 outb[m, n] (row stride ldo, rows 16-byte aligned), BF16 outbT[n, m] (stride ldT), FP32
+// outf[m, n] (stride ldf, + blockIdx.z zstride: one slice per K part), FP32 outfT[n, m] (stride ldfT).
+struct PtEpi {
+  const float* bias;
+  int relu;
+  const __nv_bfloat16* mask;
+  int ldm;
+  const float* omean;
+  const float* ostd;
+  const float* offset;
+  __nv_bfloat16* outb;
+  int ldo;
+  __nv_bfloat16* outbT;
+  int ldT;
+  float* outf;
+  int ldf;
+  long long zstride;
+  float* outfT;
+  int ldfT;
+};
+
+// kpb: K blocks (of 64) per K part; blockIdx.z takes blocks [z kpb, min(nK, (z + 1) kpb)).
 __global__ void __launch_bounds__(128, 2) prop_tc_gemm_kernel(const __grid_constant__ CUtensorMap amap,
                                                               const __grid_constant__ CUtensorMap wmap, int M, int N,
-                                                              int K, int nchunk, const float* bias, int relu,
-                                                              __nv_bfloat16* outb, float* outf, int ldo,
-                                                              const float* omean, const float* ostd, int stages) {
+                                                              int K, int nchunk, int stages, int kpb, const PtEpi e) {
   extern __shared__ uint8_t sraw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sraw) + 1023) & ~uintptr_t(1023));
   const int btile = N * 128;                              // N rows x 64 K x 2 bytes (a multiple of 1 KB)
@@ -83,7 +119,9 @@ __global__ void __launch_bounds__(128, 2) prop_tc_gemm_kernel(const __grid_const
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * 128, nK = (K + 63) / 64, nb = N / nchunk;
+  const int m0 = blockIdx.x * 128, nb = N / nchunk;
+  const int nKall = (K + 63) / 64;
+  const int kb0 = blockIdx.z * kpb, kb1 = min(nKall, kb0 + kpb), nK = kb1 - kb0;   // nK >= 1 by the launch
   const int n0 = blockIdx.y * N;   // this CTA's columns [n0, n0 + N) of the layer's output
   const uint32_t tcols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : (N <= 256 ? 256 : 512)));
   if (threadIdx.x == 0) {
@@ -108,9 +146,9 @@ __global__ void __launch_bounds__(128, 2) prop_tc_gemm_kernel(const __grid_const
       const int s = kb % stages;
       if (kb >= stages && !mbar_wait(&empty[s], ((kb / stages) - 1) & 1u)) { s_fail = 1; break; }
       mbar_arrive_expect_tx(&full[s], abytes + bbytes);
-      tma_load_2d(At + s * kPtATile, &amap, kb * 64, m0, &full[s]);
+      tma_load_2d(At + s * kPtATile, &amap, (kb0 + kb) * 64, m0, &full[s]);
       for (int c = 0; c < nchunk; ++c)
-        tma_load_2d(Bt + s * btile + c * nb * 128, &wmap, kb * 64, n0 + c * nb, &full[s]);
+        tma_load_2d(Bt + s * btile + c * nb * 128, &wmap, (kb0 + kb) * 64, n0 + c * nb, &full[s]);
     }
     // every posted copy lands before the block can exit
     for (int kb = nK > stages ? nK - stages : 0; kb < nK; ++kb) mbar_wait(&full[kb % stages], (kb / stages) & 1u);
@@ -141,32 +179,221 @@ __global__ void __launch_bounds__(128, 2) prop_tc_gemm_kernel(const __grid_const
     float v[16];
     tmem_ld16(tl + (uint32_t)c0, v);   // every thread of the warp takes part (sync.aligned)
     if (row >= M) continue;
+    const int nc = n0 + c0;            // global column of v[0]
+    float mk[16];
+    if (e.mask) {
+      const uint4* src = reinterpret_cast<const uint4*>(e.mask + (long long)row * e.ldm + nc);
+      const uint4 q0 = src[0], q1 = src[1];
+      const uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      float x = ok ? v[e] + bias[n0 + c0 + e] : __int_as_float(0x7fc00000);
-      x = relu ? fmaxf(x, 0.f) : x;
-      v[e] = omean ? fmaf(x, ostd[n0 + c0 + e], omean[n0 + c0 + e]) : x;   // back to the bounds' units
+      for (int j = 0; j < 8; ++j) {
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[j]));
+        mk[2 * j] = f.x;
+        mk[2 * j + 1] = f.y;
+      }
     }
-    if (outb) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      float x = ok ? v[j] + (e.bias ? e.bias[nc + j] : 0.f) : __int_as_float(0x7fc00000);
+      if (e.relu) x = fmaxf(x, 0.f);
+      if (e.mask) x = mk[j] > 0.f ? x : 0.f;
+      if (e.omean) x = fmaf(x, e.ostd[nc + j], e.omean[nc + j]);   // back to the bounds' units
+      if (e.offset) x += e.offset[nc + j];
+      v[j] = x;
+    }
+    if (e.outb) {
       uint32_t w[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-        w[e] = *reinterpret_cast<const uint32_t*>(&h);
+      for (int j = 0; j < 8; ++j) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        w[j] = *reinterpret_cast<const uint32_t*>(&h);
       }
-      uint4* dst = reinterpret_cast<uint4*>(outb + (long long)row * ldo + n0 + c0);
+      uint4* dst = reinterpret_cast<uint4*>(e.outb + (long long)row * e.ldo + nc);
       dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
       dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
-    } else {
-      float4* dst = reinterpret_cast<float4*>(outf + (long long)row * ldo + n0 + c0);
+    }
+    if (e.outbT) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+      for (int j = 0; j < 16; ++j) e.outbT[(long long)(nc + j) * e.ldT + row] = __float2bfloat16_rn(v[j]);
+    }
+    if (e.outf) {
+      float4* dst = reinterpret_cast<float4*>(e.outf + blockIdx.z * e.zstride + (long long)row * e.ldf + nc);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    }
+    if (e.outfT) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) e.outfT[(long long)(nc + j) * e.ldfT + row] = v[j];
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem, tcols);
+}
+
+// W [out, in] FP32 -> WT [in, out] BF16 (the transposed copies of the training path).
+__global__ void prop_transpose_bf16_kernel(const float* W, int out, int in, __nv_bfloat16* WT) {
+  const long long total = (long long)out * in;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / out, r = e - c * out;   // WT[c][r] = W[r][c]
+    WT[e] = __float2bfloat16_rn(W[r * in + c]);
+  }
+}
+
+// Column sums of G [M, N] (the bias gradients), first pass: block (x, y) sums columns 32 x .. 32 x + 31 over
+// the rows of slab y (kColSlab rows; each warp a strided set of them, lane = column, coalesced) into
+// part[y][n], the 8 warps' partial sums added in a fixed order. prop_reduce_parts_kernel then sums the
+// slabs in order (deterministic).
+constexpr int kColSlab = 64;
+__global__ void __launch_bounds__(256) prop_colsum_tiled_kernel(int M, int N, const float* G, float* part) {
+  __shared__ float acc8[8][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n = blockIdx.x * 32 + lane;
+  const int r0 = blockIdx.y * kColSlab, r1 = min(M, r0 + kColSlab);
+  float acc = 0.f;
+  if (n < N)
+    for (int m = r0 + warp; m < r1; m += 8) acc += G[(long long)m * N + n];
+  acc8[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && n < N) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += acc8[w][lane];
+    part[(long long)blockIdx.y * N + n] = t;
+  }
+}
+
+// BF16 transpose in [R, C] -> out [C, R] through 32 x 32 shared-memory tiles (coalesced on both sides).
+__global__ void __launch_bounds__(256) prop_transpose_act_kernel(int R, int C, const __nv_bfloat16* in,
+                                                                 __nv_bfloat16* out) {
+  __shared__ __nv_bfloat16 t[32][34];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int i = ty; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + tx;
+    if (r < R && c < C) t[i][tx] = in[(long long)r * C + c];
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int c = c0 + i, r = r0 + tx;
+    if (r < R && c < C) out[(long long)c * R + r] = t[tx][i];
+  }
+}
+
+// Sum of the K-part slices of a product, in slice order (deterministic): out[m, n] = sum_z P[z][m, n]
+// (transposed: out[n, m]).
+__global__ void prop_reduce_parts_kernel(int nz, int M, int N, const float* P, long long zstride, float* out,
+                                         int transpose) {
+  const long long total = (long long)M * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int z = 0; z < nz; ++z) acc += P[z * zstride + e];
+    if (transpose) {
+      const long long m = e / N, n = e - m * N;
+      out[n * M + m] = acc;
+    } else {
+      out[e] = acc;
+    }
+  }
+}
+
+// dy = 2 (y - t) / (B n) as in prop_mse_kernel, also rounded to BF16; the loss summed per block first
+// (one atomic per block). B n < 2^31.
+__global__ void __launch_bounds__(256) prop_mse_bf16_kernel(int B, int n, const float* y, const float* Y,
+                                                            const float* mean, const float* stdv, float* dy,
+                                                            __nv_bfloat16* dyb, float* loss) {
+  __shared__ float red[8];
+  float part = 0.f;
+  const int total = B * n;
+  const float scale = 2.f / (float)total;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int j = e % n;
+    const float tgt = (Y[e] - mean[j]) / stdv[j];
+    const float d = y[e] - tgt;
+    const float g = scale * d;
+    dy[e] = g;
+    dyb[e] = __float2bfloat16_rn(g);
+    part = fmaf(d, d, part);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0 && loss) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    atomicAdd(loss, t / (float)total);
+  }
+}
+
+// Adam on several parameter arrays in one launch (segment i: n[i] entries of p, g, m, v).
+struct AdamSegs {
+  float* p[6];
+  const float* g[6];
+  float* m[6];
+  float* v[6];
+  long long start[7];
+};
+__global__ void prop_adam_multi_kernel(AdamSegs a, int nseg, float lr, float b1, float b2, float eps, float c1,
+                                       float c2) {
+  const long long total = a.start[nseg];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    int i = 0;
+    while (i + 1 < nseg && e >= a.start[i + 1]) ++i;
+    const long long k = e - a.start[i];
+    const float gg = a.g[i][k];
+    const float mm = b1 * a.m[i][k] + (1.f - b1) * gg;
+    const float vv = b2 * a.v[i][k] + (1.f - b2) * gg * gg;
+    a.m[i][k] = mm;
+    a.v[i][k] = vv;
+    a.p[i][k] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+  }
+}
+
+constexpr int kCalMax = 16384;   // calibration samples per call (sorted in shared memory)
+
+// Calibration margin of one output per CTA: the residuals by which the proposals are narrower than the
+// certified bounds (lower outputs j < n_lower: proposal - certified; upper: certified - proposal) are
+// sorted in shared memory (bitonic, padded with +inf to a power of two); the margin is the k-th smallest,
+// k = ceil(q (B + 1)) - 1 clamped to [0, B - 1] (the split-conformal quantile), floored at 0; the signed
+// offset (-margin for lower outputs, +margin for upper) is written.
+__global__ void prop_calibrate_kernel(int B, int n, int n_lower, float q, const float* P, const float* Y, float* offset) {
+  extern __shared__ float sv[];
+  const int j = blockIdx.x;
+  int L = 1;
+  while (L < B) L <<= 1;
+  for (int b = threadIdx.x; b < L; b += blockDim.x) {
+    float r = CUDART_INF_F;
+    if (b < B) {
+      const float pv = P[(long long)b * n + j], cv = Y[(long long)b * n + j];
+      r = j < n_lower ? pv - cv : cv - pv;
+      if (r != r) r = CUDART_INF_F;   // a NaN proposal counts as uncovered
+    }
+    sv[b] = r;
+  }
+  __syncthreads();
+  for (int k = 2; k <= L; k <<= 1)
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const int ixj = i ^ jj;
+        if (ixj > i) {
+          const bool up = (i & k) == 0;
+          const float a = sv[i], c = sv[ixj];
+          if ((a > c) == up) {
+            sv[i] = c;
+            sv[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  if (threadIdx.x == 0) {
+    int k = (int)ceilf(q * (float)(B + 1)) - 1;
+    k = k < 0 ? 0 : (k > B - 1 ? B - 1 : k);
+    const float m = fmaxf(sv[k], 0.f);
+    offset[j] = j < n_lower ? -m : m;
+  }
 }
 
 // The three weight matrices to their BF16 copies in one launch.
@@ -262,10 +489,10 @@ __global__ void prop_standardize_kernel(long long total, int n, const float* X, 
 }
 
 __global__ void prop_destandardize_kernel(long long total, int n, const float* y, const float* mean, const float* stdv,
-                                          float* Y) {
+                                          const float* offset, float* Y) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(e % n);
-    Y[e] = fmaf(y[e], stdv[j], mean[j]);
+    Y[e] = fmaf(y[e], stdv[j], mean[j]) + (offset ? offset[j] : 0.f);
   }
 }
 
@@ -273,8 +500,10 @@ __global__ void prop_destandardize_kernel(long long total, int n, const float* y
 // even) keeps that pair's angle flags, means and deviations in registers and walks kStdRows rows, whose
 // loads are independent; a row's pairs are consecutive threads (coalesced).
 constexpr int kStdRows = 16;
+// XbT (optional): the same values transposed, [n, B] (the training path's operand of the first layer's
+// weight gradient).
 __global__ void prop_standardize_bf16_kernel(int B, int n, const float* X, const int* periodic, const float* mean,
-                                             const float* stdv, __nv_bfloat16* Xb) {
+                                             const float* stdv, __nv_bfloat16* Xb, __nv_bfloat16* XbT) {
   const int r0 = blockIdx.x * kStdRows, r1 = min(B, r0 + kStdRows);
   for (int c = threadIdx.x; c < (n >> 1); c += blockDim.x) {
     const int j = 2 * c;
@@ -285,8 +514,12 @@ __global__ void prop_standardize_bf16_kernel(int B, int n, const float* X, const
       float2 x = reinterpret_cast<const float2*>(X + (long long)row * n)[c];
       if (w0) x.x = wrap_pi(x.x);
       if (w1) x.y = wrap_pi(x.y);
-      reinterpret_cast<__nv_bfloat162*>(Xb + (long long)row * n)[c] =
-          __floats2bfloat162_rn((x.x - m0) / s0, (x.y - m1) / s1);
+      const __nv_bfloat162 v = __floats2bfloat162_rn((x.x - m0) / s0, (x.y - m1) / s1);
+      reinterpret_cast<__nv_bfloat162*>(Xb + (long long)row * n)[c] = v;
+      if (XbT) {
+        XbT[(long long)j * B + row] = v.x;
+        XbT[(long long)(j + 1) * B + row] = v.y;
+      }
     }
   }
 }
@@ -389,10 +622,63 @@ cudaError_t gemm(cudaStream_t s, int M, int N, int K, const float* A, int lda, i
   return cudaGetLastError();
 }
 
-// workspace (floats): Xs [B, n_in], h0 [B, H], h1 [B, H], y [B, n_out], dy [B, n_out], d1 [B, H], d0 [B, H]
-size_t ws_floats(const leb_proposer_s* p, int B) {
-  return (size_t)B * (p->n_in + 4 * p->H + 2 * p->n_out) + 64;
+// Layout of the tensor-core training step's workspace (byte offsets, 16-byte aligned): the standardised
+// inputs and the activations in BF16, row-major and transposed (the transposed copies are the K-major
+// operands of the weight gradients, whose K is the batch), the FP32 outputs and input gradients (for the
+// loss and the bias gradients), and the K-part slices of the weight gradients.
+struct TrainLayout {
+  size_t Xb, XbT, h0b, h0T, h1b, h1T, y, dy, dyb, dyT, d1, d1b, d1T, d0, d0T, part, total;
+  int kpb[3], nz[3];   // weight gradient of layer i: K blocks per part, parts
+};
+
+static TrainLayout train_layout(const leb_proposer_s* p, int B) {
+  TrainLayout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 255) & ~size_t(255); return r; };
+  const size_t b = (size_t)B, n_in = p->n_in, H = p->H, n_out = p->n_out;
+  L.Xb = take(2 * b * n_in);
+  L.XbT = take(2 * b * n_in);
+  L.h0b = take(2 * b * H);
+  L.h0T = take(2 * b * H);
+  L.h1b = take(2 * b * H);
+  L.h1T = take(2 * b * H);
+  L.y = take(4 * b * n_out);
+  L.dy = take(4 * b * n_out);
+  L.dyb = take(2 * b * n_out);
+  L.dyT = take(2 * b * n_out);
+  L.d1 = take(4 * b * H);
+  L.d1b = take(2 * b * H);
+  L.d1T = take(2 * b * H);
+  L.d0 = take(4 * b * H);
+  L.d0T = take(2 * b * H);
+  // weight gradient of layer i as C[M_i, H] (layer 0 transposed: dW0^T [n_in, H]), K = B split in parts so
+  // that the grid fills the SMs
+  const int Ms[3] = {p->n_in, p->H, p->n_out};
+  const int parts = p->parts[0] > 0 ? p->parts[0] : 1;
+  const int kblocks = (B + 63) / 64;
+  size_t part = 0;
+  for (int i = 0; i < 3; ++i) {
+    const int mt = (Ms[i] + 127) / 128;
+    const int target = std::max(1, 148 / (mt * parts));
+    L.kpb[i] = (kblocks + target - 1) / target;
+    L.nz[i] = (kblocks + L.kpb[i] - 1) / L.kpb[i];
+    part = std::max(part, (size_t)L.nz[i] * Ms[i] * H * 4);
+  }
+  part = std::max(part, (size_t)((B + kColSlab - 1) / kColSlab) * std::max(H, n_out) * 4);   // column-sum slabs
+  L.part = take(part);
+  L.total = o;
+  return L;
 }
+
+// workspace (floats): the CUDA-core path's Xs [B, n_in], h0 [B, H], h1 [B, H], y [B, n_out], dy [B, n_out],
+// d1 [B, H], d0 [B, H], or the tensor-core training layout, whichever is larger; then [B, n_out] for the
+// proposals of a calibration call
+size_t ws_base_floats(const leb_proposer_s* p, int B) {
+  const size_t core = (size_t)B * (p->n_in + 4 * p->H + 2 * p->n_out) + 64;
+  const size_t tc = train_layout(p, B).total / 4 + 64;
+  return (std::max(core, tc) + 63) & ~size_t(63);
+}
+size_t ws_floats(const leb_proposer_s* p, int B) { return ws_base_floats(p, B) + (size_t)B * p->n_out; }
 
 }  // namespace
 }  // namespace leb
@@ -430,22 +716,48 @@ static bool setup_tc(leb_proposer p) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return true;
   }
+  // transposed copies of layers 1 and 2 for the training path's input gradients: W_i^T [in_i, out_i] as
+  // the B operand (N = in_i = H rows, K = out_i)
+  for (int i = 1; i < 3; ++i) {
+    if (cudaMalloc(&p->WbT[i], (size_t)ins[i] * outs[i] * 2) != cudaSuccess) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)outs[i], (cuuint64_t)ins[i]};
+    cuuint64_t strides[1] = {(cuuint64_t)outs[i] * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)(ins[i] / p->parts[0])};
+    cuuint32_t estr[2] = {1, 1};
+    if (enc(&p->wTmap[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p->WbT[i], dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return true;
+  }
   if (cudaFuncSetAttribute(prop_tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPtSmem) != cudaSuccess)
     return true;
   p->tc = true;
   return true;
 }
 
-// Activations [rows, cols] BF16 as the A operand of the tcgen05 GEMM (box 64 x 128, zero fill).
-static bool act_map(CUtensorMap* m, const __nv_bfloat16* x, int rows, int cols) {
+// A BF16 matrix [rows, cols] (cols = K, contiguous) as an operand of the tcgen05 GEMM: box 64 x box_rows
+// (128 for the A operand; a column part's width for the B operand), zero fill past the edges.
+static bool act_map(CUtensorMap* m, const __nv_bfloat16* x, int rows, int cols, int box_rows = 128) {
   auto enc = tensor_map_encoder();
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  cuuint32_t box[2] = {64, 128};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   return enc && enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(x), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Refresh the BF16 weight copies (and the transposed ones) after the weights changed.
+static void refresh_bf16(leb_proposer p, cudaStream_t s) {
+  if (p->wb_version == p->w_version) return;
+  const int n_in = p->n_in, H = p->H, n_out = p->n_out;
+  const long long n0 = (long long)n_in * H, n1 = (long long)H * H, n2 = (long long)H * n_out;
+  prop_weights_bf16_kernel<<<blocks_for(n0 + n1 + n2), 256, 0, s>>>(p->W[0], n0, p->W[1], n1, p->W[2], n2, p->Wb[0],
+                                                                      p->Wb[1], p->Wb[2]);
+  prop_transpose_bf16_kernel<<<blocks_for(n1), 256, 0, s>>>(p->W[1], H, H, p->WbT[1]);
+  prop_transpose_bf16_kernel<<<blocks_for(n2), 256, 0, s>>>(p->W[2], n_out, H, p->WbT[2]);
+  p->wb_version = p->w_version;
 }
 
 // Inference forward on the tensor cores, written to Y in the bounds' units; false: not taken.
@@ -464,29 +776,186 @@ static bool forward_tc(leb_proposer p, int B, const float* X, float* ws, float* 
   CUtensorMap m0, m1, m2;
   if (!act_map(&m0, Xb, B, n_in) || !act_map(&m1, H1, B, H) || !act_map(&m2, H2, B, H)) return false;
   *st = LEB_ERR_CUDA;
-  if (p->wb_version != p->w_version) {   // the weights changed since their last BF16 copy
-    const long long n0 = (long long)n_in * H, n1 = (long long)H * H, n2 = (long long)H * n_out;
-    prop_weights_bf16_kernel<<<blocks_for(n0 + n1 + n2), 256, 0, s>>>(p->W[0], n0, p->W[1], n1, p->W[2], n2, p->Wb[0],
-                                                                        p->Wb[1], p->Wb[2]);
-    p->wb_version = p->w_version;
-  }
+  refresh_bf16(p, s);   // after a weight change
   const int sthreads = std::min(1024, ((n_in / 2) + 31) / 32 * 32);
   prop_standardize_bf16_kernel<<<(B + kStdRows - 1) / kStdRows, sthreads, 0, s>>>(B, n_in, X, p->periodic, p->norm,
-                                                                                 p->norm + n_in, Xb);
+                                                                                 p->norm + n_in, Xb, nullptr);
   const int tiles = (B + 127) / 128;
   const float* omean = p->norm + 2 * n_in;
   // layer i: a CTA per (128-row tile, column part of N / parts columns)
   auto layer = [&](int i, const CUtensorMap& am, int N, int K, int relu, __nv_bfloat16* ob, float* of,
-                   const float* mn, const float* sd) {
+                   const float* mn, const float* sd, const float* off) {
+    PtEpi e{};
+    e.bias = p->b[i];
+    e.relu = relu;
+    e.omean = mn;
+    e.ostd = sd;
+    e.offset = off;
+    e.outb = ob;
+    e.ldo = N;
+    e.outf = of;
+    e.ldf = N;
     const int np = N / p->parts[i], ns = pt_stages(np);
-    prop_tc_gemm_kernel<<<dim3(tiles, p->parts[i]), 128, pt_smem(np, ns), s>>>(am, p->wmap[i], B, np, K, 1, p->b[i],
-                                                                                relu, ob, of, N, mn, sd, ns);
+    prop_tc_gemm_kernel<<<dim3(tiles, p->parts[i]), 128, pt_smem(np, ns), s>>>(am, p->wmap[i], B, np, K, 1, ns,
+                                                                                (K + 63) / 64, e);
   };
-  layer(0, m0, H, n_in, 1, H1, nullptr, nullptr, nullptr);
-  layer(1, m1, H, H, 1, H2, nullptr, nullptr, nullptr);
-  layer(2, m2, n_out, H, 0, nullptr, Y, omean, omean + n_out);
+  layer(0, m0, H, n_in, 1, H1, nullptr, nullptr, nullptr, nullptr);
+  layer(1, m1, H, H, 1, H2, nullptr, nullptr, nullptr, nullptr);
+  layer(2, m2, n_out, H, 0, nullptr, Y, omean, omean + n_out, p->calibrated ? p->offset : nullptr);
   *st = cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
   return true;
+}
+
+// One training step on the tensor cores (the GEMMs of prop_tc_gemm_kernel; elementwise work in the small
+// kernels above), the same arithmetic as the CUDA-core step: BF16 operands, FP32 accumulation.
+//   forward: h0 = relu(Xs W0^T + b0), h1 = relu(h0 W1^T + b1), y = h1 W2^T + b2 (standardised units)
+//   dy = 2 (y - t) / (B n_out);  dW2 = dy^T h1, d1 = (dy W2) o (h1 > 0);  dW1 = d1^T h0,
+//   d0 = (d1 W1) o (h0 > 0);  dW0 = d0^T Xs (computed as dW0^T = Xs^T d0: 392 columns do not split into
+//   parts of a multiple of 16);  db_i = column sums;  then Adam on the FP32 master weights.
+// The weight gradients contract over the batch: their operands are the transposed BF16 copies the
+// producing kernels write, and K is split in parts whose FP32 slices are summed in order afterwards
+// (deterministic). Taken when the shapes fit the tcgen05 GEMM and B is a multiple of 8 (TMA strides);
+// false: not taken (the CUDA-core step runs).
+static bool train_tc(leb_proposer p, int B, const float* X, const float* Yt, float* loss, void* wsv, cudaStream_t s,
+                     leb_status* st) {
+  if (!p->tc || B % 8 != 0 || (reinterpret_cast<uintptr_t>(wsv) & 255u) || (reinterpret_cast<uintptr_t>(X) & 7u))
+    return false;
+  const int n_in = p->n_in, H = p->H, n_out = p->n_out;
+  const TrainLayout L = train_layout(p, B);
+  char* ws = static_cast<char*>(wsv);
+  auto bf = [&](size_t o) { return reinterpret_cast<__nv_bfloat16*>(ws + o); };
+  auto fp = [&](size_t o) { return reinterpret_cast<float*>(ws + o); };
+  CUtensorMap* tm = p->tr_maps;
+  CUtensorMap &mXb = tm[0], &mXbT = tm[1], &mh0b = tm[2], &mh0T = tm[3], &mh1b = tm[4], &mh1T = tm[5], &mdyb = tm[6],
+              &mdyT = tm[7], &md1b = tm[8], &md1T = tm[9], &md0T = tm[10];
+  if (p->tr_ws != wsv || p->tr_B != B) {
+    const int np = H / p->parts[0];   // column part of an H-wide product
+    p->tr_ws = nullptr;
+    const bool ok = act_map(&mXb, bf(L.Xb), B, n_in) && act_map(&mh0b, bf(L.h0b), B, H) &&
+                    act_map(&mh1b, bf(L.h1b), B, H) && act_map(&mdyb, bf(L.dyb), B, n_out) &&
+                    act_map(&md1b, bf(L.d1b), B, H) && act_map(&mdyT, bf(L.dyT), n_out, B) &&
+                    act_map(&md1T, bf(L.d1T), H, B) && act_map(&mXbT, bf(L.XbT), n_in, B) &&
+                    act_map(&mh1T, bf(L.h1T), H, B, np) && act_map(&mh0T, bf(L.h0T), H, B, np) &&
+                    act_map(&md0T, bf(L.d0T), H, B, np);
+    if (!ok) return false;
+    p->tr_ws = wsv;
+    p->tr_B = B;
+  }
+  *st = LEB_ERR_CUDA;
+  refresh_bf16(p, s);
+  const int sthreads = std::min(1024, ((n_in / 2) + 31) / 32 * 32);
+  prop_standardize_bf16_kernel<<<(B + kStdRows - 1) / kStdRows, sthreads, 0, s>>>(B, n_in, X, p->periodic, p->norm,
+                                                                                 p->norm + n_in, bf(L.Xb), nullptr);
+  auto transpose = [&](const __nv_bfloat16* in, int R, int C, __nv_bfloat16* out) {
+    prop_transpose_act_kernel<<<dim3((C + 31) / 32, (R + 31) / 32), 256, 0, s>>>(R, C, in, out);
+  };
+  auto colsum = [&](int M, int N, const float* G, float* out) {   // slabs into the part slices, then in order
+    const int slabs = (M + kColSlab - 1) / kColSlab;
+    prop_colsum_tiled_kernel<<<dim3((N + 31) / 32, slabs), 256, 0, s>>>(M, N, G, fp(L.part));
+    prop_reduce_parts_kernel<<<blocks_for(N), 256, 0, s>>>(slabs, 1, N, fp(L.part), N, out, 0);
+  };
+  transpose(bf(L.Xb), B, n_in, bf(L.XbT));
+  const int tiles = (B + 127) / 128;
+  // C[M, N] on a grid of (128-row tiles, column parts, K parts)
+  auto gemm_tc = [&](const CUtensorMap& am, const CUtensorMap& bm, int M, int N, int parts, int K, int kpb, int nz,
+                     const PtEpi& e) {
+    const int n = N / parts, ns = pt_stages(n);
+    prop_tc_gemm_kernel<<<dim3((M + 127) / 128, parts, nz), 128, pt_smem(n, ns), s>>>(am, bm, M, n, K, 1, ns, kpb, e);
+  };
+  const int kall = (H + 63) / 64;
+  {   // forward
+    PtEpi e{};
+    e.bias = p->b[0];
+    e.relu = 1;
+    e.outb = bf(L.h0b);
+    e.ldo = H;
+    e.outbT = bf(L.h0T);
+    e.ldT = B;
+    gemm_tc(mXb, p->wmap[0], B, H, p->parts[0], n_in, (n_in + 63) / 64, 1, e);
+    e.bias = p->b[1];
+    e.outb = bf(L.h1b);
+    e.outbT = bf(L.h1T);
+    gemm_tc(mh0b, p->wmap[1], B, H, p->parts[1], H, kall, 1, e);
+    PtEpi f{};
+    f.bias = p->b[2];
+    f.outf = fp(L.y);
+    f.ldf = n_out;
+    gemm_tc(mh1b, p->wmap[2], B, n_out, p->parts[2], H, kall, 1, f);
+  }
+  if (loss && cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) return true;
+  const long long tot = (long long)B * n_out;
+  prop_mse_bf16_kernel<<<blocks_for(tot), 256, 0, s>>>(B, n_out, fp(L.y), Yt, p->norm + 2 * n_in,
+                                                        p->norm + 2 * n_in + n_out, fp(L.dy), bf(L.dyb), loss);
+  transpose(bf(L.dyb), B, n_out, bf(L.dyT));
+  colsum(B, n_out, fp(L.dy), p->gb[2]);
+  // weight gradient C[M, H] (K = B in nz parts) into the slices, then summed in order
+  auto wgrad = [&](int i, const CUtensorMap& am, const CUtensorMap& bm, int M, int transpose) {
+    PtEpi e{};
+    e.outf = fp(L.part);
+    e.ldf = H;
+    e.zstride = (long long)M * H;
+    gemm_tc(am, bm, M, H, p->parts[0], B, L.kpb[i], L.nz[i], e);
+    prop_reduce_parts_kernel<<<blocks_for((long long)M * H), 256, 0, s>>>(L.nz[i], M, H, fp(L.part), (long long)M * H,
+                                                                           p->gW[i], transpose);
+  };
+  wgrad(2, mdyT, mh1T, n_out, 0);
+  {   // d1 = (dy W2) o (h1 > 0)
+    PtEpi e{};
+    e.mask = bf(L.h1b);
+    e.ldm = H;
+    e.outf = fp(L.d1);
+    e.ldf = H;
+    e.outb = bf(L.d1b);
+    e.ldo = H;
+    e.outbT = bf(L.d1T);
+    e.ldT = B;
+    gemm_tc(mdyb, p->wTmap[2], B, H, p->parts[0], n_out, (n_out + 63) / 64, 1, e);
+  }
+  colsum(B, H, fp(L.d1), p->gb[1]);
+  wgrad(1, md1T, mh0T, H, 0);
+  {   // d0 = (d1 W1) o (h0 > 0)
+    PtEpi e{};
+    e.mask = bf(L.h0b);
+    e.ldm = H;
+    e.outf = fp(L.d0);
+    e.ldf = H;
+    e.outbT = bf(L.d0T);
+    e.ldT = B;
+    gemm_tc(md1b, p->wTmap[1], B, H, p->parts[0], H, kall, 1, e);
+  }
+  colsum(B, H, fp(L.d0), p->gb[0]);
+  wgrad(0, mXbT, md0T, n_in, 1);   // dW0^T [n_in, H] -> gW[0] [H, n_in]
+  *st = cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
+  return true;
+}
+
+// Adam on every weight and bias from the gradients of the step just computed (one launch; the same
+// per-element arithmetic as prop_adam_kernel).
+static leb_status adam_all(leb_proposer p, float lr, cudaStream_t s) {
+  p->step += 1;
+  p->w_version += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)p->step), c2 = 1.f - std::pow(b2, (float)p->step);
+  const int ins[3] = {p->n_in, p->H, p->H}, outs[3] = {p->H, p->H, p->n_out};
+  AdamSegs a{};
+  long long o = 0;
+  for (int i = 0; i < 3; ++i) {
+    a.p[2 * i] = p->W[i];
+    a.g[2 * i] = p->gW[i];
+    a.m[2 * i] = p->mW[i];
+    a.v[2 * i] = p->vW[i];
+    a.start[2 * i] = o;
+    o += (long long)ins[i] * outs[i];
+    a.p[2 * i + 1] = p->b[i];
+    a.g[2 * i + 1] = p->gb[i];
+    a.m[2 * i + 1] = p->mb[i];
+    a.v[2 * i + 1] = p->vb[i];
+    a.start[2 * i + 1] = o;
+    o += outs[i];
+  }
+  a.start[6] = o;
+  prop_adam_multi_kernel<<<blocks_for(o), 256, 0, s>>>(a, 6, lr, b1, b2, 1e-8f, c1, c2);
+  return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
 }
 
 extern "C" {
@@ -515,6 +984,10 @@ leb_status leb_proposer_create(int n_in, int n_hidden, int n_out, unsigned long 
     ok = ok && cudaGetLastError() == cudaSuccess;
   }
   ok = ok && cudaMalloc(&p->norm, (size_t)2 * (n_in + n_out) * 4) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->offset, (size_t)n_out * 4) == cudaSuccess &&
+       cudaMemset(p->offset, 0, (size_t)n_out * 4) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(prop_calibrate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kCalMax * (int)sizeof(float)) == cudaSuccess;
   ok = ok && cudaMalloc(&p->periodic, (size_t)n_in * sizeof(int)) == cudaSuccess &&
        cudaMemset(p->periodic, 0, (size_t)n_in * sizeof(int)) == cudaSuccess;
   if (ok) {
@@ -537,7 +1010,11 @@ leb_status leb_proposer_destroy(leb_proposer p) {
   if (!p) return LEB_ERR_INVALID_ARG;
   for (int i = 0; i < 3; ++i)
     for (float* q : {p->W[i], p->gW[i], p->mW[i], p->vW[i], p->b[i], p->gb[i], p->mb[i], p->vb[i]}) cudaFree(q);
-  for (int i = 0; i < 3; ++i) cudaFree(p->Wb[i]);
+  for (int i = 0; i < 3; ++i) {
+    cudaFree(p->Wb[i]);
+    cudaFree(p->WbT[i]);
+  }
+  cudaFree(p->offset);
   cudaFree(p->norm);
   cudaFree(p->periodic);
   delete p;
@@ -610,7 +1087,8 @@ leb_status leb_proposer_forward(leb_proposer p, int B, const float* X, float* Y,
   const float* y = ws + (size_t)B * (p->n_in + 2 * p->H);
   const long long tot = (long long)B * p->n_out;
   prop_destandardize_kernel<<<blocks_for(tot), 256, 0, s>>>(tot, p->n_out, y, p->norm + 2 * p->n_in,
-                                                             p->norm + 2 * p->n_in + p->n_out, Y);
+                                                             p->norm + 2 * p->n_in + p->n_out,
+                                                             p->calibrated ? p->offset : nullptr, Y);
   return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
 }
 
@@ -620,9 +1098,14 @@ leb_status leb_proposer_train_step(leb_proposer p, int B, const float* X, const 
   if (!workspace || ws_bytes < ws_floats(p, B) * sizeof(float)) return LEB_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   float* ws = (float*)workspace;
-  leb_status st = forward_impl(p, B, X, ws, s);
-  if (st != LEB_OK) return st;
   const int n_in = p->n_in, H = p->H, n_out = p->n_out;
+  leb_status st = LEB_OK;
+  if (train_tc(p, B, X, Ytgt, loss, workspace, s, &st)) {
+    if (st != LEB_OK) return st;
+    return adam_all(p, lr, s);
+  }
+  st = forward_impl(p, B, X, ws, s);
+  if (st != LEB_OK) return st;
   float* Xs = ws;
   float* h0 = Xs + (size_t)B * n_in;
   float* h1 = h0 + (size_t)B * H;
@@ -647,19 +1130,7 @@ leb_status leb_proposer_train_step(leb_proposer p, int B, const float* X, const 
   if (gemm(s, H, n_in, B, d0, H, 1, Xs, n_in, 0, p->gW[0], n_in, nullptr, nullptr, 0) != cudaSuccess) return LEB_ERR_CUDA;
   prop_colsum_kernel<<<(H + 255) / 256, 256, 0, s>>>(B, H, d0, p->gb[0]);
   if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
-  // Adam
-  p->step += 1;
-  p->w_version += 1;
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float c1 = 1.f - std::pow(b1, (float)p->step), c2 = 1.f - std::pow(b2, (float)p->step);
-  const int ins[3] = {n_in, H, H}, outs[3] = {H, H, n_out};
-  for (int i = 0; i < 3; ++i) {
-    const long long nw = (long long)ins[i] * outs[i];
-    prop_adam_kernel<<<blocks_for(nw), 256, 0, s>>>(nw, p->W[i], p->gW[i], p->mW[i], p->vW[i], lr, b1, b2, 1e-8f, c1, c2);
-    prop_adam_kernel<<<blocks_for(outs[i]), 256, 0, s>>>(outs[i], p->b[i], p->gb[i], p->mb[i], p->vb[i], lr, b1, b2,
-                                                          1e-8f, c1, c2);
-  }
-  return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
+  return adam_all(p, lr, s);
 }
 
 static leb_status layer_dims(leb_proposer p, int i, int* in, int* out) {
@@ -725,6 +1196,7 @@ std::vector<std::pair<void*, size_t>> state_arrays(leb_proposer p) {
   }
   v.push_back({p->norm, (size_t)2 * (p->n_in + p->n_out) * 4});
   v.push_back({p->periodic, (size_t)p->n_in * sizeof(int)});
+  v.push_back({p->offset, (size_t)p->n_out * 4});
   return v;
 }
 }  // namespace
@@ -741,7 +1213,7 @@ leb_status leb_proposer_save_state(leb_proposer p, void* host_buf, size_t bytes,
   size_t need = 0;
   if (leb_proposer_state_size(p, &need) != LEB_OK || !host_buf || bytes < need) return LEB_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  StateHeader h{kStateMagic, p->n_in, p->H, p->n_out, p->step, {0, 0, 0}};
+  StateHeader h{kStateMagic, p->n_in, p->H, p->n_out, p->step, {p->calibrated ? 1 : 0, 0, 0}};
   std::memcpy(host_buf, &h, sizeof h);
   char* dst = static_cast<char*>(host_buf) + sizeof h;
   for (const auto& a : state_arrays(p)) {
@@ -767,8 +1239,36 @@ leb_status leb_proposer_load_state(leb_proposer p, const void* host_buf, size_t 
   // the host buffer may be released once the call returns: wait for the copies out of it
   if (cudaStreamSynchronize(s) != cudaSuccess) return LEB_ERR_CUDA;
   p->step = h.step;
+  p->calibrated = h.pad[0] != 0;
   p->w_version += 1;   // the BF16 inference copies are stale
   return LEB_OK;
+}
+
+leb_status leb_proposer_calibrate(leb_proposer p, int B, const float* X, const float* Y, int n_lower, float q,
+                                  void* workspace, size_t ws_bytes, void* stream) {
+  if (!p || B < 1 || B > kCalMax || !X || !Y || n_lower < 0 || n_lower > p->n_out || !(q > 0.f && q < 1.f))
+    return LEB_ERR_INVALID_ARG;
+  if (!workspace || ws_bytes < ws_floats(p, B) * sizeof(float)) return LEB_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* P = static_cast<float*>(workspace) + ws_base_floats(p, B);
+  p->calibrated = false;   // the residuals are those of the uncalibrated proposals
+  const leb_status st = leb_proposer_forward(p, B, X, P, workspace, ws_bytes, stream);
+  if (st != LEB_OK) return st;
+  int L = 1;
+  while (L < B) L <<= 1;
+  prop_calibrate_kernel<<<p->n_out, 1024, (size_t)L * sizeof(float), s>>>(B, p->n_out, n_lower, q, P, Y, p->offset);
+  if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
+  p->calibrated = true;
+  return LEB_OK;
+}
+
+leb_status leb_proposer_get_offset(leb_proposer p, float* offset, int* calibrated, void* stream) {
+  if (!p || !offset || !calibrated) return LEB_ERR_INVALID_ARG;
+  *calibrated = p->calibrated ? 1 : 0;
+  return cudaMemcpyAsync(offset, p->offset, (size_t)p->n_out * 4, cudaMemcpyDeviceToDevice, (cudaStream_t)stream) ==
+                 cudaSuccess
+             ? LEB_OK
+             : LEB_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -61,6 +61,21 @@ class Proposer:
                                             _ptr(ws), ws.numel(), _stream()), "leb_proposer_train_step")
         return self._loss
 
+    def calibrate(self, X, Y, n_lower: int, q: float):
+        """Per-output margins from held-out inputs X and their certified bounds Y (leb_proposer_calibrate):
+        the first n_lower outputs are lower bounds, the rest upper bounds; q the quantile of each output's
+        residual taken as its margin. Later forward calls include the margins."""
+        ws = self._workspace(X.shape[0])
+        check(lib().leb_proposer_calibrate(self.h, X.shape[0], _ptr(X), _ptr(Y), int(n_lower), C.c_float(q),
+                                           _ptr(ws), ws.numel(), _stream()), "leb_proposer_calibrate")
+
+    def offset(self):
+        """(signed per-output offsets [n_out] on the device, whether they are applied)."""
+        o = torch.empty(self.n_out, device="cuda")
+        cal = C.c_int()
+        check(lib().leb_proposer_get_offset(self.h, _ptr(o), C.byref(cal), _stream()), "leb_proposer_get_offset")
+        return o, bool(cal.value)
+
     def layer(self, i: int):
         ins = [self.n_in, self.n_hidden, self.n_hidden][i]
         outs = [self.n_hidden, self.n_hidden, self.n_out][i]

@@ -46,6 +46,45 @@ def test_gradients_and_adam_step_vs_oracle():
         assert np.allclose(W1.cpu().numpy(), pW, rtol=1e-5, atol=1e-7)
 
 
+@pytest.mark.parametrize("n_in,H,n_out,B", [(64, 128, 48, 200), (392, 256, 336, 1000)])
+def test_tensor_core_training_step_vs_oracle(n_in, H, n_out, B):
+    """A training step whose GEMMs run on the tensor cores (B a multiple of 8, widths that split into
+    tcgen05 column parts; 200 and 1000 rows leave partial 128-row tiles and a partial last K block of the
+    weight gradients, whose K is the batch and which are split into K parts): loss, every gradient and the
+    Adam step against the FP64 oracle at the same operand precision, with the tolerance of the CUDA-core
+    step (FP32 against FP64 accumulation, here over up to 1000 terms)."""
+    rng = np.random.default_rng(23)
+    p = Proposer(n_in, H, n_out, seed=4)
+    Ws = [p.layer(i)[0].cpu().numpy().astype(np.float64) for i in range(3)]
+    bs = [rng.normal(size=w.shape[0]) * 0.1 for w in Ws]
+    for i in range(3):
+        p.set_layer(i, torch.as_tensor(Ws[i], dtype=torch.float32).cuda(), torch.as_tensor(bs[i], dtype=torch.float32).cuda())
+    X = rng.normal(size=(B, n_in)).astype(np.float32)
+    Y = rng.normal(size=(B, n_out)).astype(np.float32)
+    lr = 1e-3
+    p.train_step(torch.as_tensor(X).cuda(), torch.as_tensor(Y).cuda(), lr)
+    torch.cuda.synchronize()
+    loss, gWs, gbs = oprop.loss_and_grads((Ws, bs), X, Y, bf16_ops=True)
+    assert p._loss.item() == pytest.approx(loss, rel=1e-4)
+    for i in range(3):
+        gW, gb = p.grad(i)
+        gW, gb = gW.cpu().numpy(), gb.cpu().numpy()
+        assert np.max(np.abs(gW - gWs[i])) <= 1e-3 * np.abs(gWs[i]).max(), (i, np.max(np.abs(gW - gWs[i])))
+        assert np.max(np.abs(gb - gbs[i])) <= 1e-3 * np.abs(gbs[i]).max(), i
+        W1, _ = p.layer(i)
+        pW, _, _ = oprop.adam_step(Ws[i], gW.astype(np.float64), 0 * Ws[i], 0 * Ws[i], 1, lr)
+        assert np.allclose(W1.cpu().numpy(), pW, rtol=1e-5, atol=1e-7)
+    # a second step runs on the updated weights (their BF16 copies, plain and transposed, refreshed)
+    Ws2, bs2 = zip(*[(W.cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64))
+                     for W, b in (p.layer(i) for i in range(3))])
+    p.train_step(torch.as_tensor(X).cuda(), torch.as_tensor(Y).cuda(), lr)
+    torch.cuda.synchronize()
+    _, gWs2, _ = oprop.loss_and_grads((list(Ws2), list(bs2)), X, Y, bf16_ops=True)
+    for i in range(3):
+        gW = p.grad(i)[0].cpu().numpy()
+        assert np.max(np.abs(gW - gWs2[i])) <= 1e-3 * np.abs(gWs2[i]).max(), ("second step", i)
+
+
 @pytest.mark.parametrize("B", [300, 12800])
 def test_tensor_core_inference_vs_oracle(B):
     """Inference of the 392-256-256-336 proposer on the tensor cores (tcgen05, BF16 operands, FP32
@@ -100,6 +139,25 @@ def test_trains_on_certified_bounds_and_gains_over_random_choice():
     after = val_err()
     print(f"proposer validation error / mean width: {before:.3f} -> {after:.3f}")
     assert after < 0.25 * before and after < 0.25, (before, after)
+
+    # calibration: margins from the first half of the held-out 10 % (q = 0.985 per side, so that at most
+    # about 3 % of the (timestep, row) pairs have either side too narrow), measured on the second half
+    n_cal = n_tr + (X.shape[0] - n_tr) // 2
+    Xt, Yt = X[n_cal:], Y[n_cal:]
+
+    def under(P):
+        lo_p, hi_p = P[:, :168][:, curved], P[:, 168:][:, curved]
+        lo_c, hi_c = Yt[:, :168][:, curved], Yt[:, 168:][:, curved]
+        return ((lo_p > lo_c) | (hi_p < hi_c)).float().mean().item(), ((hi_p - lo_p).mean() / (hi_c - lo_c).mean()).item()
+
+    raw_under, raw_w = under(p.forward(Xt))
+    p.calibrate(X[n_tr:n_cal], Y[n_tr:n_cal], n_lower=168, q=0.985)
+    cal_under, cal_w = under(p.forward(Xt))
+    off, on = p.offset()
+    assert on and torch.all(off[:168] <= 0) and torch.all(off[168:] >= 0)
+    print(f"held-out under-coverage {raw_under:.3f} -> {cal_under:.3f} (proposed / certified width "
+          f"{raw_w:.3f} -> {cal_w:.3f})")
+    assert cal_under <= 0.05, cal_under
 
     # gain test on fresh timesteps
     t_ = lambda a: torch.as_tensor(a).cuda()
