@@ -162,3 +162,64 @@ def pbh_partitioned(dyn, nominal, lo, hi, dims):
         R_lo = l if R_lo is None else np.minimum(R_lo, l)
         R_hi = h if R_hi is None else np.maximum(R_hi, h)
     return R_lo, R_hi
+
+
+def recentred_cuts(lo_j: float, hi_j: float, K: int):
+    """The K equal pieces of [lo_j, hi_j] and their midpoints, with the interior cut points and the
+    midpoints as the library forms them in FP32 from FP32 ends (round to nearest: w = hi - lo,
+    p_k = lo + w (k / K), beta_k = p_k / 2 + p_{k+1} / 2): they are part of the partition's definition, so
+    both sides use the same points. The outer cuts are the box ends themselves (so the pieces cover the
+    box whatever its ends are), and each midpoint is kept inside its piece. Returns FP64 arrays (cuts
+    [K + 1], mids [K])."""
+    f = np.float32
+    lo32, hi32 = f(lo_j), f(hi_j)
+    w = f(hi32 - lo32)
+    c32 = [lo32]
+    for k in range(1, K):
+        p = f(lo32 + f(w * f(f(k) / f(K))))
+        c32.append(min(max(p, lo32), hi32))
+    c32.append(hi32)
+    cuts = np.array([float(lo_j)] + [float(c) for c in c32[1:K]] + [float(hi_j)], np.float64)
+    mids = np.array([f(f(f(0.5) * c32[k]) + f(f(0.5) * c32[k + 1])) for k in range(K)], np.float64)
+    mids = np.minimum(np.maximum(mids, cuts[:-1]), cuts[1:])
+    return cuts, mids
+
+
+def pbh_recentred(dyn, nominal, lo, hi, dims, K: int, A=None):
+    """Input-domain partitioning with re-centred pieces (Sec. IV-D names partitioning; Thm. 1 needs the
+    expansion point inside the set, so a piece away from the nominal is expanded around a point beta of its
+    own). For alpha in a piece P with beta in P, and A the returned linearization (default the Jacobian at
+    the nominal),
+        r(alpha; alpha~) = f(alpha) - f(alpha~) - A (alpha - alpha~)
+                         = [f(alpha) - f(beta) - J(beta)(alpha - beta)]     Thm. 1 around beta over P
+                         + [f(beta) - f(alpha~) - A (beta - alpha~)]       a point value
+                         + (J(beta) - A)(alpha - beta)                      an interval product over P.
+    Each coordinate d of ``dims`` is cut alone into K equal pieces (``recentred_cuts``; the other
+    coordinates keep their whole range, beta = the nominal with beta_d = the piece's midpoint); the hull
+    over the pieces bounds the remainder over the box, and the bounds of the several coordinates are
+    intersected (each is valid). FP64 numpy (R_lo, R_hi)."""
+    a = np.asarray(nominal, np.float64)
+    A = dyn.jacobian(a) if A is None else np.asarray(A, np.float64)
+    f0 = dyn.f(a)
+    R_lo = np.full(dyn.n_x, -np.inf)
+    R_hi = np.full(dyn.n_x, np.inf)
+    for d in dims:
+        cuts, mids = recentred_cuts(lo[d], hi[d], K)
+        H_lo = np.full(dyn.n_x, np.inf)
+        H_hi = np.full(dyn.n_x, -np.inf)
+        for k in range(K):
+            lp, hp = np.array(lo, np.float64), np.array(hi, np.float64)
+            lp[d], hp[d] = cuts[k], cuts[k + 1]
+            beta = a.copy()
+            beta[d] = mids[k]
+            l, h = pbh(dyn, beta, lp, hp)
+            point = dyn.f(beta) - f0 - A @ (beta - a)
+            M = dyn.jacobian(beta) - A
+            Dl, Dh = lp - beta, hp - beta
+            cl = np.minimum(M * Dl, M * Dh).sum(axis=1)
+            ch = np.maximum(M * Dl, M * Dh).sum(axis=1)
+            H_lo = np.minimum(H_lo, l + point + cl)
+            H_hi = np.maximum(H_hi, h + point + ch)
+        R_lo = np.maximum(R_lo, H_lo)
+        R_hi = np.minimum(R_hi, H_hi)
+    return R_lo, R_hi

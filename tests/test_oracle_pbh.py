@@ -250,3 +250,48 @@ def test_path_orderings():
     for _ in range(4):
         l, h = pbh.pbh(sat, a, lo, hi, order=list(rng.permutation(10)))
         assert np.allclose(l, b[0], rtol=1e-13, atol=1e-16) and np.allclose(h, b[1], rtol=1e-13, atol=1e-16)
+
+
+def test_recentred_partition_contains_exact_range_and_converges():
+    """Re-centred input-domain partitioning of the attitude: K = 1 on a box centred at the nominal is the
+    plain bound (beta = nominal); for K = 2, 4, 16 every bound contains the exact range (1-D analysis of the
+    planar quadrotor, w.r.t. the same A); the width decreases with K and the excess over the exact range
+    shrinks at least fourfold from K = 1 to K = 16 (it vanishes as the pieces shrink)."""
+    from oracle import exact
+    w = inputs.planar_quad()
+    dyn = dynamics.QuadChain(1, **w.params)
+    ex1, ex16 = [], []
+    for t in range(w.T):
+        a = w.nominal()[t].astype(np.float64)
+        lo, hi = pbh.box_from_set(a, radii=w.radii[t])
+        P = pbh.pbh(dyn, a, lo, hi)
+        R1 = pbh.pbh_recentred(dyn, a, lo, hi, [2], 1)   # beta = the FP32 midpoint: the nominal up to an ulp
+        tol = 1e-6 * (P[1] - P[0]).max()
+        assert np.allclose(R1[0], P[0], rtol=0, atol=tol) and np.allclose(R1[1], P[1], rtol=0, atol=tol)
+        el, eh = exact.quad_exact_range(dyn, a, lo, hi)
+        widths = []
+        for K in (2, 4, 16):
+            l, h = pbh.pbh_recentred(dyn, a, lo, hi, [2], K)
+            assert np.all(l <= el + 1e-12) and np.all(h >= eh - 1e-12), (t, K)
+            widths.append((h - l).sum())
+            if K == 16:
+                ex16.append((h - l).sum() - (eh - el).sum())
+        assert widths[0] >= widths[1] >= widths[2]
+        ex1.append((P[1] - P[0]).sum() - (eh - el).sum())
+    assert np.sum(ex16) <= 0.25 * np.sum(ex1), (np.sum(ex16), np.sum(ex1))
+
+
+def test_recentred_partition_sampled_on_the_chain():
+    """Two coupled quadrotors with zonotope hulls, every attitude cut into 8 re-centred pieces: the bound
+    (each row from its own quadrotor's attitude pieces) contains sampled remainders."""
+    from oracle import sampling
+    w = inputs.quad_chain(n_traj=1, horizon=3, n_quads=2)
+    dyn = dynamics.QuadChain(2, **w.params, spring_k=w.spring_k)
+    rng = np.random.default_rng(81)
+    for t in range(w.T):
+        a = w.nominal()[t].astype(np.float64)
+        lo, hi = pbh.box_from_set(a, G=w.G[t])
+        l, h = pbh.pbh_recentred(dyn, a, lo, hi, [dyn.ix(0, 2), dyn.ix(1, 2)], 8)
+        P = sampling.box_points(lo, hi, 20000, rng)
+        R = sampling.remainders(lambda X: np.array([dyn.f(x) for x in X]), a, dyn.jacobian(a), P)
+        assert np.all(R >= l - 1e-12) and np.all(R <= h + 1e-12)
