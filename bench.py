@@ -226,6 +226,8 @@ class PbhForm(Form):
         self.ragged = self._ragged(torch, dev, binding, inputs, quick)
         self.order = self._variant(torch, binding, lambda h: h.set_path_order(True))
         self.partition = self._variant(torch, binding, lambda h: h.set_partition(True))
+        self.recentred = {f"{k}_pieces": self._variant(torch, binding, lambda h, k=k: h.set_partition_recentred(k))
+                          for k in (4, 16)}
         self.desc = f"28-quadrotor spring chain n_x=168 n_u=56, {self.T // 50} traj x N=50, zonotope 224x336"
 
     def _variant(self, torch, binding, setup):
@@ -1178,6 +1180,7 @@ def main():
             d["ragged_horizons_graph"] = f.ragged
             d["inputs_first_path_order"] = f.order
             d["attitude_partition"] = f.partition
+            d["recentred_partition"] = f.recentred
         if f.name == "tube":
             d["tube_timesteps_per_s"] = round(f.w.n_traj * f.w.N / (form_ms["tube"] * 1e-3), 1)
         if f.name == "proposer":

@@ -235,6 +235,20 @@ leb_status leb_set_path_order(leb_handle h, int order);
  * differentiate the plain bound and return LEB_ERR_UNSUPPORTED while the cut is on. Invalid argument
  * or NULL handle: LEB_ERR_INVALID_ARG. */
 leb_status leb_set_partition(leb_handle h, int split_attitude);
+/* Input-domain partitioning with re-centred pieces (Sec. IV-D; Thm. 1 needs the expansion point inside the
+ * set, so each piece is expanded around a point of its own): every quadrotor's attitude box [lo, hi] is cut
+ * into `pieces` equal pieces, cut points p_k = lo + (hi - lo)(k / pieces) and midpoints beta_k =
+ * p_k / 2 + p_{k+1} / 2 formed in FP32 round to nearest (p_0 = lo, p_pieces = hi), and for alpha in piece k
+ *   r(alpha; alpha~) = [Thm. 1 around beta_k over the piece] + [f(beta_k) - f(alpha~) - A (beta_k - alpha~)]
+ *                      + (J(beta_k) - A)(alpha - beta_k),
+ * all in outward-rounded FP32 with the returned A; each curved row's bound is the hull over its
+ * quadrotor's pieces, intersected with the plain bound (never wider than it). The bound tends to the exact
+ * remainder range as the pieces shrink. pieces 2..32
+ * turns it on (and leb_set_partition's cut off), 0 or 1 off. Planar quadrotor chain handles only (others:
+ * LEB_ERR_UNSUPPORTED); applies to later leb_bounds, leb_bounds_static and graph captures;
+ * leb_bounds_backward and leb_refine_nominal_pgd return LEB_ERR_UNSUPPORTED while it is on. pieces outside
+ * 0..32 or NULL handle: LEB_ERR_INVALID_ARG. */
+leb_status leb_set_partition_recentred(leb_handle h, int pieces);
 
 /* Force a plan by its index in the candidate list (-1 = back to the default / autotuned plan). */
 leb_status leb_plan_select(leb_handle h, int index);

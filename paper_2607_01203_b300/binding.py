@@ -63,6 +63,7 @@ EXPORTS = [
     "leb_refine_nominal_pgd", "leb_refine_workspace_size", "leb_selftest_tan_sec", "leb_tube", "leb_bounds_backward_saved",
     "leb_proposer_state_size", "leb_proposer_save_state", "leb_proposer_load_state", "leb_selftest_wait_timeout",
     "leb_selftest_set_wait_limit", "leb_proposer_calibrate", "leb_proposer_get_offset",
+    "leb_set_partition_recentred",
 ]
 
 
@@ -95,6 +96,7 @@ def lib():
         L.leb_plan_select.argtypes = [vp, i32]
         L.leb_set_path_order.argtypes = [vp, i32]
         L.leb_set_partition.argtypes = [vp, i32]
+        L.leb_set_partition_recentred.argtypes = [vp, i32]
         L.leb_plan_count.argtypes = [vp, C.POINTER(i32)]
         L.leb_graph_capture.argtypes = [vp, C.POINTER(BatchDesc), i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp, vp,
                                         C.POINTER(Options), vp, sz, vp, C.POINTER(vp)]
@@ -217,6 +219,11 @@ class Handle:
     def set_partition(self, split_attitude: bool):
         """Input-domain partitioning (leb_set_partition): each attitude box cut at the nominal, hull."""
         check(lib().leb_set_partition(self.h, int(bool(split_attitude))), "leb_set_partition")
+
+    def set_partition_recentred(self, pieces: int):
+        """Re-centred input-domain partitioning (leb_set_partition_recentred): every attitude box in
+        `pieces` equal pieces, each expanded around its midpoint; 0 or 1 switches it off."""
+        check(lib().leb_set_partition_recentred(self.h, int(pieces)), "leb_set_partition_recentred")
 
     def autotune(self, T: int, set_kind: int, n_gen: int = 0, cache_path: str | None = None):
         ws = self.workspace(T)

@@ -21,6 +21,7 @@ struct QuadConsts {
   int springs;               // k != 0
   int inputs_first;          // path order of Thm. 1: 0 the natural [x; u], 1 the inputs, then the states
   int split_phi;             // input-domain partitioning: each attitude box cut at the nominal, bounds hulled
+  int pieces;                // re-centred partitioning: each attitude box in this many pieces (>= 2: on)
 };
 
 // FP32 enclosure [lo, hi] and round-to-nearest value f of a real model constant.

@@ -369,7 +369,7 @@ static leb_status bounds_backward(leb_handle h, int T, const float* x_nom, const
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return LEB_ERR_WORKSPACE;
   if (h->kind == LEB_DYN_QUAD_CHAIN) {
     // the adjoint differentiates the plain bound in the natural order
-    if (h->qk.inputs_first || h->qk.split_phi) return LEB_ERR_UNSUPPORTED;
+    if (h->qk.inputs_first || h->qk.split_phi || h->qk.pieces) return LEB_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(dev_flags, 0, sizeof(int), s) != cudaSuccess) return LEB_ERR_CUDA;
     return pbh_bounds_backward(*h, T, x_nom, u_nom, set->radii, g_rlo, g_rhi, g_x, g_u, g_radii, dev_flags, s);
@@ -438,7 +438,7 @@ leb_status leb_refine_nominal_pgd(leb_handle h, int T, const float* x0, const fl
                                   float eps, float lr, int steps, float* x_opt, float* u_opt, float* w_init,
                                   float* w_best, void* workspace, size_t ws_bytes, int* dev_flags, void* stream) {
   if (!h || T < 0 || steps < 0 || !dev_flags) return LEB_ERR_INVALID_ARG;
-  if (h->kind != LEB_DYN_QUAD_CHAIN || h->qk.inputs_first || h->qk.split_phi) return LEB_ERR_UNSUPPORTED;
+  if (h->kind != LEB_DYN_QUAD_CHAIN || h->qk.inputs_first || h->qk.split_phi || h->qk.pieces) return LEB_ERR_UNSUPPORTED;
   if (!(eps >= 0.f) || !(lr >= 0.f) || !std::isfinite(eps) || !std::isfinite(lr)) return LEB_ERR_INVALID_ARG;
   if (T > 0 && (!x0 || !u0 || !radii || !x_opt || !u_opt)) return LEB_ERR_INVALID_ARG;
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return LEB_ERR_WORKSPACE;
@@ -503,6 +503,15 @@ leb_status leb_set_partition(leb_handle h, int split_attitude) {
   if (!h || (split_attitude != 0 && split_attitude != 1)) return LEB_ERR_INVALID_ARG;
   if (h->kind != LEB_DYN_QUAD_CHAIN) return LEB_ERR_UNSUPPORTED;
   h->qk.split_phi = split_attitude;
+  if (split_attitude) h->qk.pieces = 0;
+  return LEB_OK;
+}
+
+leb_status leb_set_partition_recentred(leb_handle h, int pieces) {
+  if (!h || pieces < 0 || pieces > 32) return LEB_ERR_INVALID_ARG;
+  if (h->kind != LEB_DYN_QUAD_CHAIN) return LEB_ERR_UNSUPPORTED;
+  h->qk.pieces = pieces >= 2 ? pieces : 0;
+  if (pieces >= 2) h->qk.split_phi = 0;
   return LEB_OK;
 }
 

@@ -245,7 +245,15 @@ __device__ __forceinline__ void emit_row(const PbhArgs& a, const Item& it, int l
 // Eq. 15 for every output row of one timestep, plus (J - A) Delta. Items 0..nq-1: the two curved rows
 // (v_x, v_y) of quadrotor i, which share their trigonometric enclosures; items nq..5nq-1: the four
 // linear rows of each quadrotor (only the Jacobian-rounding term).
-template <bool kSplit>
+// kMode: 0 the plain bound; 1 input-domain partitioning with every attitude box cut at the nominal (both
+// pieces contain it); 2 re-centred partitioning: the attitude box cut into K.pieces equal pieces, each
+// expanded around its own midpoint beta,
+//   r(alpha; alpha~) = [Eq. 15 around beta over the piece] + [f(beta) - f(alpha~) - A (beta - alpha~)]
+//                      + (J(beta) - A)(alpha - beta),
+// with cut points p_k = lo + (hi - lo)(k / K) and midpoints beta_k = p_k / 2 + p_{k+1} / 2 in FP32 round to
+// nearest (p_0 = lo, p_K = hi). In modes 1 and 2 a row's bound is the hull over the pieces; in mode 2 it is
+// also intersected with the plain bound (both are valid), so that it is never wider than the plain one.
+template <int kMode>
 __device__ __forceinline__ void pbh_rows(const PbhArgs& a, const Item& it, const float* xn, const float* un,
                                          const float* s_lo, const float* s_hi, const QuadA* qa, bool bad, int tid,
                                          int nthr) {
@@ -272,10 +280,12 @@ __device__ __forceinline__ void pbh_rows(const PbhArgs& a, const Item& it, const
       const ivl cS = iv_mul(cI, S), cS0 = iv_mul(cI, S0);
       const QuadA q = qa[i];
       const int deg = K.springs ? (i > 0) + (i + 1 < nq) : 0;
-      // Eq. 15 for both curved rows over an attitude box [plo, phi_] (containing the nominal)
-      auto curved = [&](float plo, float phi_, ivl& Rx, ivl& Ry) {
+      // Eq. 15 for both curved rows around the attitude beta (sin/cos enclosures sB, cB; every other
+      // coordinate at its nominal) over the attitude piece [plo, phi_] containing beta, plus
+      // (J(beta) - A)(alpha - beta) with the Jacobian at that point
+      auto curved = [&](float plo, float phi_, float beta, ivl sB, ivl cB, ivl& Rx, ivl& Ry) {
         const ivl Phi = iv(plo, phi_);
-        const ivl Dp = iv(__fsub_rd(plo, phi0), __fsub_ru(phi_, phi0));
+        const ivl Dp = iv(__fsub_rd(plo, beta), __fsub_ru(phi_, beta));
         const ivl Dp2 = iv_sqr(Dp), Dp1 = iv_mul(Dp, D1), Dpu2 = iv_mul(Dp, D2);
         const ivl sinP = iv_sin(Phi), cosP = iv_cos(Phi);
 #pragma unroll
@@ -284,14 +294,14 @@ __device__ __forceinline__ void pbh_rows(const PbhArgs& a, const Item& it, const
           // v_y: -1/2 [(dt/m) S cos](X^(phi)) Dphi^2 - [(dt/m) sin](X^(phi)) Dphi (Du1, Du2 termwise)
           const ivl Hpp = row == 0 ? iv_mul(cS, sinP) : iv_neg(iv_mul(cS, cosP));
           // the (phi, u) entries over the prefix set of the coordinate that comes first: phi's (phi over
-          // its box) in the natural order, the input's (phi at its nominal) with the inputs first
-          const ivl Hup = K.inputs_first ? iv_neg(iv_mul(cI, row == 0 ? cos0 : sin0))
+          // its box) in the natural order, the input's (phi at the expansion point) with the inputs first
+          const ivl Hup = K.inputs_first ? iv_neg(iv_mul(cI, row == 0 ? cB : sB))
                                          : iv_neg(iv_mul(cI, row == 0 ? cosP : sinP));
           ivl R = iv_half(iv_mul(Hpp, Dp2));
           R = iv_add(R, iv_mul(Hup, Dp1));
           R = iv_add(R, iv_mul(Hup, Dpu2));
-          const ivl Jphi = iv_neg(iv_mul(cS0, row == 0 ? cos0 : sin0));   // the Jacobian at the nominal
-          const ivl Ju = row == 0 ? iv_neg(iv_mul(cI, sin0)) : iv_mul(cI, cos0);
+          const ivl Jphi = iv_neg(iv_mul(cS0, row == 0 ? cB : sB));   // the Jacobian at the expansion point
+          const ivl Ju = row == 0 ? iv_neg(iv_mul(cI, sB)) : iv_mul(cI, cB);
           R = iv_add(R, corr(Jphi, row == 0 ? q.aphi_x : q.aphi_y, Dp));
           R = iv_add(R, corr(Ju, row == 0 ? q.au_x : q.au_y, D1));
           R = iv_add(R, corr(Ju, row == 0 ? q.au_x : q.au_y, D2));
@@ -305,15 +315,43 @@ __device__ __forceinline__ void pbh_rows(const PbhArgs& a, const Item& it, const
           if (row == 0) Rx = R; else Ry = R;
         }
       };
-      // the attitude's box as one piece, or (input-domain partitioning) as its two pieces [lo, phi~] and
-      // [phi~, hi], each still containing the nominal; each row's bound is the hull over the pieces
+      auto hull = [](ivl& H, ivl R) { H = iv(fminf(H.lo, R.lo), fmaxf(H.hi, R.hi)); };
       ivl Rr[2];
-      curved(s_lo[jp], kSplit ? phi0 : s_hi[jp], Rr[0], Rr[1]);
-      if constexpr (kSplit) {
-        ivl Rx, Ry;
-        curved(phi0, s_hi[jp], Rx, Ry);
-        Rr[0] = iv(fminf(Rr[0].lo, Rx.lo), fmaxf(Rr[0].hi, Rx.hi));
-        Rr[1] = iv(fminf(Rr[1].lo, Ry.lo), fmaxf(Rr[1].hi, Ry.hi));
+      if constexpr (kMode == 2) {
+        const float lo = s_lo[jp], hi = s_hi[jp];
+        const float w = __fsub_rn(hi, lo);
+        const int P = K.pieces;
+        float pa = lo;
+        Rr[0] = Rr[1] = iv(CUDART_INF_F, -CUDART_INF_F);
+        for (int k = 0; k < P; ++k) {
+          float pb = k + 1 == P ? hi : __fadd_rn(lo, __fmul_rn(w, (float)(k + 1) / (float)P));
+          pb = fminf(fmaxf(pb, pa), hi);
+          const float beta = fminf(fmaxf(__fadd_rn(__fmul_rn(0.5f, pa), __fmul_rn(0.5f, pb)), pa), pb);
+          const ivl sB = point_sin(beta), cB = point_cos(beta);
+          ivl Rx, Ry;
+          curved(pa, pb, beta, sB, cB, Rx, Ry);
+          // f(beta) - f(alpha~) - A (beta - alpha~): only the attitude moved
+          const ivl db = iv(__fsub_rd(beta, phi0), __fsub_ru(beta, phi0));
+          const ivl px = iv_sub(iv_neg(iv_mul(cS0, iv_sub(sB, sin0))), iv_mul(iv(q.aphi_x), db));
+          const ivl py = iv_sub(iv_mul(cS0, iv_sub(cB, cos0)), iv_mul(iv(q.aphi_y), db));
+          hull(Rr[0], iv_add(Rx, px));
+          hull(Rr[1], iv_add(Ry, py));
+          pa = pb;
+        }
+        ivl Px, Py;
+        curved(lo, hi, phi0, sin0, cos0, Px, Py);
+        Rr[0] = iv(fmaxf(Rr[0].lo, Px.lo), fminf(Rr[0].hi, Px.hi));
+        Rr[1] = iv(fmaxf(Rr[1].lo, Py.lo), fminf(Rr[1].hi, Py.hi));
+      } else {
+        // the attitude's box as one piece, or (kMode 1) as its two pieces [lo, phi~] and [phi~, hi], each
+        // still containing the nominal
+        curved(s_lo[jp], kMode == 1 ? phi0 : s_hi[jp], phi0, sin0, cos0, Rr[0], Rr[1]);
+        if constexpr (kMode == 1) {
+          ivl Rx, Ry;
+          curved(phi0, s_hi[jp], phi0, sin0, cos0, Rx, Ry);
+          hull(Rr[0], Rx);
+          hull(Rr[1], Ry);
+        }
       }
       for (int row = 0; row < 2; ++row) {
         const ivl R = Rr[row];
@@ -375,7 +413,7 @@ __device__ __forceinline__ bool hull_row(const PbhArgs& a, const Item& it, const
 // Kernel 1 (box sets, and zonotopes that cannot be bulk-copied): all warps reduce the set, then all
 // warps evaluate the rows and store A_k, B_k.
 // ---------------------------------------------------------------------------------------------------
-template <bool kZono, bool kSplit>
+template <bool kZono, int kMode>
 __global__ void __launch_bounds__(256, 4) pbh_chain_kernel(PbhArgs a) {
   extern __shared__ float smem[];
   __shared__ int s_t;
@@ -411,7 +449,7 @@ __global__ void __launch_bounds__(256, 4) pbh_chain_kernel(PbhArgs a) {
     }
     compute_qa(xn, un, it.nq, a.k, s_qa, threadIdx.x, blockDim.x);
     const bool bad = __syncthreads_or(!ok) != 0;
-    pbh_rows<kSplit>(a, it, xn, un, s_lo, s_hi, s_qa, bad, threadIdx.x, blockDim.x);
+    pbh_rows<kMode>(a, it, xn, un, s_lo, s_hi, s_qa, bad, threadIdx.x, blockDim.x);
     write_AB(a, it, s_qa, warp, nwarps, lane);
     if (bad && threadIdx.x == 0) atomicOr(a.flags, LEB_ASYNC_NONFINITE);
     __syncthreads();  // shared buffers are reused by the next timestep
@@ -427,7 +465,7 @@ struct StageMeta {
   int t, chunk, last, rows, rows_per, pad0, pad1, pad2;
 };
 
-template <bool kSplit>
+template <int kMode>
 __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, int stage_bytes_cap) {
   extern __shared__ __align__(128) unsigned char sraw[];
   // Warp roles: warp 0 streams the generators (one thread), warp 1 writes A_k and B_k when they are
@@ -586,7 +624,7 @@ __global__ void __launch_bounds__(256, 3) pbh_zono_tma_kernel(PbhArgs a, int S, 
         }
         const bool bad = (orb & 1u) != 0;
         ok = true;
-        pbh_rows<kSplit>(a, it, xn, un, lo, hi, qa, bad, ctid, ncthr);
+        pbh_rows<kMode>(a, it, xn, un, lo, hi, qa, bad, ctid, ncthr);
         if (writer) {
           // every consumer's qa values are in place (the barrier above): hand the timestep over
           if (ctid == 0) {
@@ -664,7 +702,8 @@ static cudaError_t pbh_tma_attr() {
   std::call_once(once[dev], [dev]() {
     cudaError_t r = cudaSuccess;
     // the opt-in limit covers the kernel's static shared memory too
-    for (const void* f : {(const void*)pbh_zono_tma_kernel<false>, (const void*)pbh_zono_tma_kernel<true>}) {
+    for (const void* f : {(const void*)pbh_zono_tma_kernel<0>, (const void*)pbh_zono_tma_kernel<1>,
+                          (const void*)pbh_zono_tma_kernel<2>}) {
       cudaFuncAttributes fa{};
       const size_t stat = cudaFuncGetAttributes(&fa, f) == cudaSuccess ? fa.sharedSizeBytes : 1024;
       const cudaError_t e2 = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(227 * 1024 - stat));
@@ -679,12 +718,14 @@ cudaError_t launch_pbh(const Ctx& c, const PbhArgs& args, const PbhPlan& p, cuda
   const int grid = c.sm_count * p.ctas_per_sm;
   PbhArgs a = args;
   a.wait_ns = c.wait_ns;
+  const int mode = a.k.pieces >= 2 ? 2 : (a.k.split_phi ? 1 : 0);
   if (pbh_tma_ok(a)) {
     const size_t smem = pbh_tma_smem(a, p.stages);
     const cudaError_t e = pbh_tma_attr();
     if (e != cudaSuccess) return e;
-    if (a.k.split_phi) pbh_zono_tma_kernel<true><<<grid, p.block, smem, s>>>(a, p.stages, kPbhStageCap);
-    else pbh_zono_tma_kernel<false><<<grid, p.block, smem, s>>>(a, p.stages, kPbhStageCap);
+    if (mode == 2) pbh_zono_tma_kernel<2><<<grid, p.block, smem, s>>>(a, p.stages, kPbhStageCap);
+    else if (mode == 1) pbh_zono_tma_kernel<1><<<grid, p.block, smem, s>>>(a, p.stages, kPbhStageCap);
+    else pbh_zono_tma_kernel<0><<<grid, p.block, smem, s>>>(a, p.stages, kPbhStageCap);
     return cudaGetLastError();
   }
   const int n_max = 8 * a.nq;
@@ -692,11 +733,13 @@ cudaError_t launch_pbh(const Ctx& c, const PbhArgs& args, const PbhPlan& p, cuda
   const int block = p.block > 256 ? 256 : p.block;
   const int g = c.sm_count * 4;
   if (a.zono) {
-    if (a.k.split_phi) pbh_chain_kernel<true, true><<<g, block, smem, s>>>(a);
-    else pbh_chain_kernel<true, false><<<g, block, smem, s>>>(a);
+    if (mode == 2) pbh_chain_kernel<true, 2><<<g, block, smem, s>>>(a);
+    else if (mode == 1) pbh_chain_kernel<true, 1><<<g, block, smem, s>>>(a);
+    else pbh_chain_kernel<true, 0><<<g, block, smem, s>>>(a);
   } else {
-    if (a.k.split_phi) pbh_chain_kernel<false, true><<<g, block, smem, s>>>(a);
-    else pbh_chain_kernel<false, false><<<g, block, smem, s>>>(a);
+    if (mode == 2) pbh_chain_kernel<false, 2><<<g, block, smem, s>>>(a);
+    else if (mode == 1) pbh_chain_kernel<false, 1><<<g, block, smem, s>>>(a);
+    else pbh_chain_kernel<false, 0><<<g, block, smem, s>>>(a);
   }
   return cudaGetLastError();
 }

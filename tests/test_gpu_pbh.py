@@ -388,3 +388,86 @@ def test_attitude_partition_parity():
     with pytest.raises(binding.LebError):
         h.bounds_backward(_t(w2.x_nom), _t(w2.u_nom), _t(np.full((w2.T, 16), 0.05, np.float32)),
                           _t(np.ones((w2.T, 12))), _t(np.ones((w2.T, 12))))
+
+
+def recentred_tolerance(dyn, a, lo, hi, J):
+    """The plain bound's FP32 tolerance plus, per curved row, the enclosure slack of the re-centred terms:
+    the point remainder at beta (a difference of two sin or cos enclosures, each within 2^-22 of the value,
+    times (dt/m) S, plus the rounding of A (beta - alpha~)) and the Jacobian at beta (its sin/cos
+    enclosures times the piece's displacements)."""
+    eps = tolerance(dyn, a, lo, hi, J)
+    D = np.maximum(np.abs(lo - a), np.abs(hi - a))
+    c = dyn.dt / dyn.m
+    for i in range(dyn.nq):
+        jp, j1, j2 = dyn.ix(i, 2), dyn.n_x + 2 * i, dyn.n_x + 2 * i + 1
+        Smax = abs(a[j1]) + abs(a[j2]) + D[j1] + D[j2]
+        slack = c * Smax * 8 * 2.0 ** -22 + 4 * 2.0 ** -22 * c * (Smax * D[jp] + D[j1] + D[j2])
+        slack += 2.0 ** -22 * (np.abs(J[dyn.ix(i, 3)]).max() + np.abs(J[dyn.ix(i, 4)]).max()) * D[jp]
+        eps[dyn.ix(i, 3)] += slack
+        eps[dyn.ix(i, 4)] += slack
+    return eps
+
+
+@pytest.mark.parametrize("pieces", [4, 16])
+def test_recentred_partition_parity(pieces):
+    """Re-centred input-domain partitioning (leb_set_partition_recentred): each attitude box in equal
+    pieces expanded around their midpoints, against the oracle's pbh_recentred with the same pieces and
+    the returned A, on every timestep of the planar quadrotor (box sets) and of a ragged batch of two
+    coupled quadrotors (zonotope hulls); A and B are those of the plain call. The planar quadrotor's
+    bounds also contain its exact remainder range and are narrower than the plain ones."""
+    from oracle import exact
+    cases = []
+    w = inputs.planar_quad()
+    cases.append((w, dynamics.QuadChain(1, **w.params), dict(radii=w.radii)))
+    w2 = inputs.quad_chain(n_traj=2, horizon=4, n_quads=2)
+    cases.append((w2, dynamics.QuadChain(2, **w2.params, spring_k=w2.spring_k), dict(G=w2.G, batch=True)))
+    for wk, dyn, kw in cases:
+        h = binding.quad_chain(wk.n_quads, **wk.params, spring_k=wk.spring_k)
+        h.set_partition_recentred(pieces)
+        g = run_gpu(wk, handle=h, **kw)
+        gp = run_gpu(wk, **kw)
+        assert g["flags"][0] == 0
+        assert np.array_equal(g["A"], gp["A"]) and np.array_equal(g["B"], gp["B"])
+        dims = [dyn.ix(i, 2) for i in range(dyn.nq)]
+        for t in range(wk.T):
+            a = wk.nominal()[t].astype(np.float64)
+            lo, hi = pbh.box_from_set(a, G=wk.G[t]) if "G" in kw else pbh.box_from_set(a, radii=wk.radii[t])
+            AB = np.concatenate([g["A"][t], g["B"][t]], axis=1).astype(np.float64)
+            ol, oh = pbh.pbh_recentred(dyn, a, lo, hi, dims, pieces, A=AB)
+            eps = recentred_tolerance(dyn, a, lo, hi, dyn.jacobian(a))
+            scale = np.abs(ol) + np.abs(oh) + 1e-300
+            assert np.all(g["r_lo"][t] <= ol + 1e-12 * scale), (t, np.max(g["r_lo"][t] - ol))
+            assert np.all(g["r_hi"][t] >= oh - 1e-12 * scale), (t, np.max(oh - g["r_hi"][t]))
+            assert np.all((g["r_hi"][t] - g["r_lo"][t]) <= (oh - ol) * (1 + 1e-5) + eps)
+            if dyn.nq == 1:
+                el, eh = exact.quad_exact_range(dyn, a, lo, hi)
+                # w.r.t. the FP32 A: the exact range moves by at most (J - A) Delta
+                d = np.abs(dyn.jacobian(a) - AB) @ np.maximum(np.abs(lo - a), np.abs(hi - a))
+                assert np.all(g["r_lo"][t] <= el + d + 1e-12) and np.all(g["r_hi"][t] >= eh - d - 1e-12)
+        ratio = (g["r_hi"] - g["r_lo"]).sum() / (gp["r_hi"] - gp["r_lo"]).sum()
+        print(f"re-centred partition, {pieces} pieces, {dyn.nq} quadrotor(s): width / plain = {ratio:.4f}")
+        if dyn.nq == 1:
+            assert ratio < 1.0
+
+
+def test_recentred_partition_full_size_sampled():
+    """The benchmark's 256 x 50 chain of 28 quadrotors (zonotope 224 x 336) with 8 re-centred pieces per
+    attitude, in the benchmark's launch configuration (the persistent TMA kernel); sampled timesteps
+    against the oracle one by one."""
+    w = inputs.quad_chain(n_traj=256, horizon=50)
+    dyn = dynamics.QuadChain(28, **w.params, spring_k=w.spring_k)
+    h = binding.quad_chain(28, **w.params, spring_k=w.spring_k)
+    h.set_partition_recentred(8)
+    g = run_gpu(w, G=w.G, handle=h)
+    assert g["flags"][0] == 0
+    dims = [dyn.ix(i, 2) for i in range(28)]
+    rng = np.random.default_rng(4)
+    for t in sorted(rng.choice(w.T, 12, replace=False).tolist()) + [w.T - 1]:
+        a = w.nominal()[t].astype(np.float64)
+        lo, hi = pbh.box_from_set(a, G=w.G[t])
+        AB = np.concatenate([g["A"][t], g["B"][t]], axis=1).astype(np.float64)
+        ol, oh = pbh.pbh_recentred(dyn, a, lo, hi, dims, 8, A=AB)
+        eps = recentred_tolerance(dyn, a, lo, hi, dyn.jacobian(a))
+        scale = np.abs(ol) + np.abs(oh) + 1e-300
+        assert np.all(g["r_lo"][t] <= ol + 1e-12 * scale) and np.all(g["r_hi"][t] >= oh - 1e-12 * scale), t
+        assert np.all((g["r_hi"][t] - g["r_lo"][t]) <= (oh - ol) * (1 + 1e-5) + eps), t
