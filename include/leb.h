@@ -226,6 +226,17 @@ leb_status leb_plan_string(leb_handle h, char* buf, size_t buf_len);
  * handle. leb_bounds_backward and leb_refine_nominal_pgd differentiate the natural order and return
  * LEB_ERR_UNSUPPORTED while order 1 is set. Invalid order or NULL handle: LEB_ERR_INVALID_ARG. */
 leb_status leb_set_path_order(leb_handle h, int order);
+/* A general path order (Thm. 1 holds for any coordinate-wise path; Sec. IV-A): order[p] is the local
+ * coordinate at position p of the path, applied to every quadrotor of the handle, and each Hessian entry
+ * (j, k) is bounded over the prefix set of whichever of j, k comes first (every variable it depends on
+ * over its box if it is on the path at or before that coordinate, else at its nominal). Local coordinates:
+ * LEB_DYN_QUAD3D, n = 16: p_x, p_y, p_z, phi, theta, psi, v_x, v_y, v_z, p, q, r, then T, tau_phi,
+ * tau_theta, tau_psi; LEB_DYN_QUAD_CHAIN, n = 8: p_x, p_y, phi, v_x, v_y, omega, u1, u2 (for the chain only
+ * whether each input comes before phi changes the bound). order = NULL: the natural order. Not a
+ * permutation of 0..n-1: LEB_ERR_INVALID_ARG; other kinds: LEB_ERR_UNSUPPORTED (the satellite's Hessian
+ * is constant: every order gives its exact range). Applies to later leb_bounds, leb_bounds_static and
+ * graph captures; the chain's backward and nominal refinement refuse a non-natural order. */
+leb_status leb_set_path_order_perm(leb_handle h, const int* order, int n);
 /* Input-domain partitioning (Sec. IV-D names it as a use of the parallel evaluation): with
  * split_attitude = 1 every quadrotor's attitude box is cut at the nominal into [lo, phi~] and [phi~, hi],
  * Thm. 1 is evaluated on each piece (each still contains the nominal) and each row's bound is the hull of

@@ -63,7 +63,7 @@ EXPORTS = [
     "leb_refine_nominal_pgd", "leb_refine_workspace_size", "leb_selftest_tan_sec", "leb_tube", "leb_bounds_backward_saved",
     "leb_proposer_state_size", "leb_proposer_save_state", "leb_proposer_load_state", "leb_selftest_wait_timeout",
     "leb_selftest_set_wait_limit", "leb_proposer_calibrate", "leb_proposer_get_offset",
-    "leb_set_partition_recentred",
+    "leb_set_partition_recentred", "leb_set_path_order_perm",
 ]
 
 
@@ -97,6 +97,7 @@ def lib():
         L.leb_set_path_order.argtypes = [vp, i32]
         L.leb_set_partition.argtypes = [vp, i32]
         L.leb_set_partition_recentred.argtypes = [vp, i32]
+        L.leb_set_path_order_perm.argtypes = [vp, C.POINTER(i32), i32]
         L.leb_plan_count.argtypes = [vp, C.POINTER(i32)]
         L.leb_graph_capture.argtypes = [vp, C.POINTER(BatchDesc), i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp, vp,
                                         C.POINTER(Options), vp, sz, vp, C.POINTER(vp)]
@@ -215,6 +216,13 @@ class Handle:
     def set_path_order(self, inputs_first: bool):
         """Path order of Thm. 1 (leb_set_path_order): the natural [x; u] or the inputs first."""
         check(lib().leb_set_path_order(self.h, int(bool(inputs_first))), "leb_set_path_order")
+
+    def set_path_order_perm(self, order):
+        """A general path order of each quadrotor's local coordinates (leb_set_path_order_perm); None: the
+        natural order."""
+        arr = None if order is None else (C.c_int * len(order))(*[int(v) for v in order])
+        check(lib().leb_set_path_order_perm(self.h, arr, 0 if order is None else len(order)),
+              "leb_set_path_order_perm")
 
     def set_partition(self, split_attitude: bool):
         """Input-domain partitioning (leb_set_partition): each attitude box cut at the nominal, hull."""

@@ -19,7 +19,9 @@ struct QuadConsts {
   float ks_lo, ks_hi, ks_f;  // dt * k / m
   float tq_lo, tq_hi, tq_f;  // dt * arm / I
   int springs;               // k != 0
-  int inputs_first;          // path order of Thm. 1: 0 the natural [x; u], 1 the inputs, then the states
+  int inputs_first;          // path order of Thm. 1: bit r set = input u_{r+1} comes before the attitude on the
+                             // path (0: the natural [x; u]; 3: the inputs first); nothing else of the order
+                             // changes the chain's bound
   int split_phi;             // input-domain partitioning: each attitude box cut at the nominal, bounds hulled
   int pieces;                // re-centred partitioning: each attitude box in this many pieces (>= 2: on)
 };
@@ -37,6 +39,8 @@ struct SysConsts {
   SysConst ca_self, ca_other;     // centroid coupling, position columns: -dt alpha (N - 1), dt alpha
   SysConst cg_self, cg_other;     // velocity columns: 1 - dt gamma (N - 1) / N, dt gamma / N
   int coupled;
+  int custom_order;               // 3-D quadrotor: path order from rank (else the natural order)
+  int rank[16];                   // position on the path of each local coordinate (states 0..11, inputs 12..15)
 };
 
 struct SysArgs {

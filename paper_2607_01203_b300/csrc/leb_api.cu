@@ -495,7 +495,35 @@ leb_status leb_plan_count(leb_handle h, int* count) {
 leb_status leb_set_path_order(leb_handle h, int order) {
   if (!h || (order != 0 && order != 1)) return LEB_ERR_INVALID_ARG;
   if (h->kind != LEB_DYN_QUAD_CHAIN) return LEB_ERR_UNSUPPORTED;
-  h->qk.inputs_first = order;
+  h->qk.inputs_first = order ? 3 : 0;
+  return LEB_OK;
+}
+
+leb_status leb_set_path_order_perm(leb_handle h, const int* order, int n) {
+  if (!h) return LEB_ERR_INVALID_ARG;
+  if (h->kind != LEB_DYN_QUAD_CHAIN && h->kind != LEB_DYN_QUAD3D) return LEB_ERR_UNSUPPORTED;
+  const int nc = h->kind == LEB_DYN_QUAD3D ? 16 : 8;
+  int rank[16];
+  if (order) {
+    if (n != nc) return LEB_ERR_INVALID_ARG;
+    for (int c = 0; c < nc; ++c) rank[c] = -1;
+    for (int p = 0; p < nc; ++p) {
+      if (order[p] < 0 || order[p] >= nc || rank[order[p]] >= 0) return LEB_ERR_INVALID_ARG;   // not a permutation
+      rank[order[p]] = p;
+    }
+  } else {
+    for (int c = 0; c < nc; ++c) rank[c] = c;
+  }
+  if (h->kind == LEB_DYN_QUAD_CHAIN) {   // local coordinates p_x, p_y, phi, v_x, v_y, omega, u1, u2
+    h->qk.inputs_first = (rank[6] < rank[2] ? 1 : 0) | (rank[7] < rank[2] ? 2 : 0);
+  } else {
+    bool natural = true;
+    for (int c = 0; c < 16; ++c) {
+      h->sk.rank[c] = rank[c];
+      natural = natural && rank[c] == c;
+    }
+    h->sk.custom_order = natural ? 0 : 1;
+  }
   return LEB_OK;
 }
 

@@ -274,7 +274,9 @@ __device__ __forceinline__ void pbh_rows(const PbhArgs& a, const Item& it, const
       // S~ at the nominal, and S on the prefix set of phi: S~ in the natural order (the inputs come after
       // phi), the inputs' box when they come first
       const ivl S0 = iv(__fadd_rd(u1, u2), __fadd_ru(u1, u2));
-      const ivl S = K.inputs_first ? iv(__fadd_rd(s_lo[j1], s_lo[j2]), __fadd_ru(s_hi[j1], s_hi[j2])) : S0;
+      // (each input over its box if it comes before phi on the path, else at its nominal)
+      const bool f1 = (K.inputs_first & 1) != 0, f2 = (K.inputs_first & 2) != 0;
+      const ivl S = iv(__fadd_rd(f1 ? s_lo[j1] : u1, f2 ? s_lo[j2] : u2), __fadd_ru(f1 ? s_hi[j1] : u1, f2 ? s_hi[j2] : u2));
       const ivl D1 = D(j1), D2 = D(j2);
       const ivl sin0 = point_sin(phi0), cos0 = point_cos(phi0);
       const ivl cS = iv_mul(cI, S), cS0 = iv_mul(cI, S0);
@@ -293,13 +295,12 @@ __device__ __forceinline__ void pbh_rows(const PbhArgs& a, const Item& it, const
           // v_x: 1/2 [(dt/m) S sin](X^(phi)) Dphi^2 - [(dt/m) cos](X^(phi)) Dphi (Du1 + Du2 termwise)
           // v_y: -1/2 [(dt/m) S cos](X^(phi)) Dphi^2 - [(dt/m) sin](X^(phi)) Dphi (Du1, Du2 termwise)
           const ivl Hpp = row == 0 ? iv_mul(cS, sinP) : iv_neg(iv_mul(cS, cosP));
-          // the (phi, u) entries over the prefix set of the coordinate that comes first: phi's (phi over
-          // its box) in the natural order, the input's (phi at the expansion point) with the inputs first
-          const ivl Hup = K.inputs_first ? iv_neg(iv_mul(cI, row == 0 ? cB : sB))
-                                         : iv_neg(iv_mul(cI, row == 0 ? cosP : sinP));
+          // the (phi, u_r) entries over the prefix set of the coordinate that comes first: phi's (phi over
+          // its box) when phi comes first, the input's (phi at the expansion point) when the input does
+          const ivl HupB = iv_neg(iv_mul(cI, row == 0 ? cosP : sinP)), HupN = iv_neg(iv_mul(cI, row == 0 ? cB : sB));
           ivl R = iv_half(iv_mul(Hpp, Dp2));
-          R = iv_add(R, iv_mul(Hup, Dp1));
-          R = iv_add(R, iv_mul(Hup, Dpu2));
+          R = iv_add(R, iv_mul(f1 ? HupN : HupB, Dp1));
+          R = iv_add(R, iv_mul(f2 ? HupN : HupB, Dpu2));
           const ivl Jphi = iv_neg(iv_mul(cS0, row == 0 ? cB : sB));   // the Jacobian at the expansion point
           const ivl Ju = row == 0 ? iv_neg(iv_mul(cI, sB)) : iv_mul(cI, cB);
           R = iv_add(R, corr(Jphi, row == 0 ? q.aphi_x : q.aphi_y, Dp));

@@ -193,54 +193,138 @@ __device__ __forceinline__ G3 g_parts(ivl sph, ivl cph, ivl sth, ivl cth, ivl sp
   return r;
 }
 
+// Path order (Thm. 1's path runs coordinate by coordinate in any order): each Hessian entry (j, k) is
+// bounded over the prefix set of whichever of j, k comes first, i.e. every variable the entry depends on
+// ranges over its box when it is on the path at or before that coordinate and sits at its nominal
+// otherwise. kOrd = false: the natural order (local index = rank, folded at compile time); true: the
+// handle's rank table (a permutation of the 16 local coordinates, the same for every quadrotor).
+template <bool kOrd>
+__device__ __forceinline__ int rnk(const SysArgs& a, int c) {
+  if constexpr (kOrd) return a.k.rank[c];
+  else return c;
+}
+template <bool kOrd>
+__device__ __forceinline__ int first_of(const SysArgs& a, int j, int k) {
+  return rnk<kOrd>(a, j) <= rnk<kOrd>(a, k) ? j : k;
+}
+
+// Enclosures of the variables the 3-D quadrotor's Hessian entries depend on, over the prefix set of
+// coordinate f.
+struct Pre {
+  ivl sph, cph, sth, cth, tth, secth, sps, cps, q, r, T;
+};
+template <bool kOrd>
+__device__ __forceinline__ Pre prefix(const SysArgs& a, const Box& b, const Trig& tr, int f) {
+  const int rf = rnk<kOrd>(a, f);
+  const bool bp = rnk<kOrd>(a, PH) <= rf, bt = rnk<kOrd>(a, TH) <= rf, bs = rnk<kOrd>(a, PS) <= rf;
+  const bool bq = rnk<kOrd>(a, Q_) <= rf, br = rnk<kOrd>(a, R_) <= rf, bT = rnk<kOrd>(a, T_) <= rf;
+  Pre p;
+  p.sph = bp ? tr.sP : tr.s0;
+  p.cph = bp ? tr.cP : tr.c0;
+  p.sth = bt ? tr.sT : tr.st0;
+  p.cth = bt ? tr.cT : tr.ct0;
+  p.tth = bt ? tr.tanT : tr.tan0;
+  p.secth = bt ? tr.secT : tr.sec0;
+  p.sps = bs ? tr.sS : tr.ss0;
+  p.cps = bs ? tr.cS : tr.cs0;
+  p.q = bq ? b.X(Q_) : iv(b.nom[Q_]);
+  p.r = br ? b.X(R_) : iv(b.nom[R_]);
+  p.T = bT ? b.X(T_) : iv(b.nom[T_]);
+  return p;
+}
+
 // Row S of the unit (quadrotor i of timestep t).
 // tot: per-timestep sums over all quadrotors of Delta of the coupled columns (p_x, p_y, p_z, v_x, v_y, v_z).
-template <int S>
+template <int S, bool kOrd>
 __device__ __forceinline__ ivl quad3d_row(const SysArgs& a, const Box& b, const Trig& tr, const float* tot,
                                           float (&arow)[16]) {
   const SysConsts& K = a.k;
   Row<16> r(b, arow);
   const ivl dt = cv(K.dt), mdt = iv_neg(dt);
+  auto pre = [&](int f) { return prefix<kOrd>(a, b, tr, f); };
+  auto first = [&](int j, int k) { return first_of<kOrd>(a, j, k); };
   if constexpr (S < 3) {
     r.jac(S, iv(1.f));
     r.jac(6 + S, dt);
   } else if constexpr (S <= 5) {
+    auto A_ = [](const Pre& p) { return iv_add(iv_mul(p.q, p.sph), iv_mul(p.r, p.cph)); };          // a
+    auto Ap_ = [](const Pre& p) { return iv_add(iv_mul(p.q, p.cph), iv_neg(iv_mul(p.r, p.sph))); };  // a_phi
     const ivl qv = iv(b.nom[Q_]), rv = iv(b.nom[R_]);
-    const ivl Aph = iv_add(iv_mul(qv, tr.sP), iv_mul(rv, tr.cP));           // a over X^(phi)
-    const ivl Aphp = iv_add(iv_mul(qv, tr.cP), iv_neg(iv_mul(rv, tr.sP)));  // a_phi over X^(phi)
     const ivl a0 = iv_add(iv_mul(qv, tr.s0), iv_mul(rv, tr.c0));
     const ivl ap0 = iv_add(iv_mul(qv, tr.c0), iv_neg(iv_mul(rv, tr.s0)));
     if constexpr (S == 4) {   // theta dot = q cos(phi) - r sin(phi)
-      r.sq(PH, iv_mul(mdt, Aphp));
-      r.cross(PH, Q_, iv_mul(mdt, tr.sP));
-      r.cross(PH, R_, iv_mul(mdt, tr.cP));
+      r.sq(PH, iv_mul(mdt, Ap_(pre(PH))));
+      r.cross(PH, Q_, iv_mul(mdt, pre(first(PH, Q_)).sph));
+      r.cross(PH, R_, iv_mul(mdt, pre(first(PH, R_)).cph));
       r.jac(PH, iv_mul(mdt, a0));
       r.jac(TH, iv(1.f));
       r.jac(Q_, iv_mul(dt, tr.c0));
       r.jac(R_, iv_mul(mdt, tr.s0));
     } else if constexpr (S == 3) {   // phi dot = p + a tan(theta)
-      const ivl sec20 = iv_sqr(tr.sec0), secT2 = iv_sqr(tr.secT);
-      r.sq(PH, iv_mul(mdt, iv_mul(Aph, tr.tan0)));
-      r.cross(PH, TH, iv_mul(dt, iv_mul(Aphp, sec20)));
-      r.sq(TH, iv_mul(iv_add(dt, dt), iv_mul(Aph, iv_mul(secT2, tr.tanT))));
-      r.cross(PH, Q_, iv_mul(dt, iv_mul(tr.cP, tr.tan0)));
-      r.cross(PH, R_, iv_mul(mdt, iv_mul(tr.sP, tr.tan0)));
-      r.cross(TH, Q_, iv_mul(dt, iv_mul(tr.sP, secT2)));
-      r.cross(TH, R_, iv_mul(dt, iv_mul(tr.cP, secT2)));
+      {
+        const Pre p = pre(PH);
+        r.sq(PH, iv_mul(mdt, iv_mul(A_(p), p.tth)));
+      }
+      {
+        const Pre p = pre(first(PH, TH));
+        r.cross(PH, TH, iv_mul(dt, iv_mul(Ap_(p), iv_sqr(p.secth))));
+      }
+      {
+        const Pre p = pre(TH);
+        r.sq(TH, iv_mul(iv_add(dt, dt), iv_mul(A_(p), iv_mul(iv_sqr(p.secth), p.tth))));
+      }
+      {
+        const Pre p = pre(first(PH, Q_));
+        r.cross(PH, Q_, iv_mul(dt, iv_mul(p.cph, p.tth)));
+      }
+      {
+        const Pre p = pre(first(PH, R_));
+        r.cross(PH, R_, iv_mul(mdt, iv_mul(p.sph, p.tth)));
+      }
+      {
+        const Pre p = pre(first(TH, Q_));
+        r.cross(TH, Q_, iv_mul(dt, iv_mul(p.sph, iv_sqr(p.secth))));
+      }
+      {
+        const Pre p = pre(first(TH, R_));
+        r.cross(TH, R_, iv_mul(dt, iv_mul(p.cph, iv_sqr(p.secth))));
+      }
+      const ivl sec20 = iv_sqr(tr.sec0);
       r.jac(PH, iv_add(iv(1.f), iv_mul(dt, iv_mul(ap0, tr.tan0))));
       r.jac(TH, iv_mul(dt, iv_mul(a0, sec20)));
       r.jac(P_, dt);
       r.jac(Q_, iv_mul(dt, iv_mul(tr.s0, tr.tan0)));
       r.jac(R_, iv_mul(dt, iv_mul(tr.c0, tr.tan0)));
     } else {   // psi dot = a sec(theta)
-      const ivl sec0tan0 = iv_mul(tr.sec0, tr.tan0), secTtanT = iv_mul(tr.secT, tr.tanT);
-      r.sq(PH, iv_mul(mdt, iv_mul(Aph, tr.sec0)));
-      r.cross(PH, TH, iv_mul(dt, iv_mul(Aphp, sec0tan0)));
-      r.sq(TH, iv_mul(dt, iv_mul(Aph, iv_mul(tr.secT, iv_add(iv_sqr(tr.tanT), iv_sqr(tr.secT))))));
-      r.cross(PH, Q_, iv_mul(dt, iv_mul(tr.cP, tr.sec0)));
-      r.cross(PH, R_, iv_mul(mdt, iv_mul(tr.sP, tr.sec0)));
-      r.cross(TH, Q_, iv_mul(dt, iv_mul(tr.sP, secTtanT)));
-      r.cross(TH, R_, iv_mul(dt, iv_mul(tr.cP, secTtanT)));
+      {
+        const Pre p = pre(PH);
+        r.sq(PH, iv_mul(mdt, iv_mul(A_(p), p.secth)));
+      }
+      {
+        const Pre p = pre(first(PH, TH));
+        r.cross(PH, TH, iv_mul(dt, iv_mul(Ap_(p), iv_mul(p.secth, p.tth))));
+      }
+      {
+        const Pre p = pre(TH);
+        r.sq(TH, iv_mul(dt, iv_mul(A_(p), iv_mul(p.secth, iv_add(iv_sqr(p.tth), iv_sqr(p.secth))))));
+      }
+      {
+        const Pre p = pre(first(PH, Q_));
+        r.cross(PH, Q_, iv_mul(dt, iv_mul(p.cph, p.secth)));
+      }
+      {
+        const Pre p = pre(first(PH, R_));
+        r.cross(PH, R_, iv_mul(mdt, iv_mul(p.sph, p.secth)));
+      }
+      {
+        const Pre p = pre(first(TH, Q_));
+        r.cross(TH, Q_, iv_mul(dt, iv_mul(p.sph, iv_mul(p.secth, p.tth))));
+      }
+      {
+        const Pre p = pre(first(TH, R_));
+        r.cross(TH, R_, iv_mul(dt, iv_mul(p.cph, iv_mul(p.secth, p.tth))));
+      }
+      const ivl sec0tan0 = iv_mul(tr.sec0, tr.tan0);
       r.jac(PH, iv_mul(dt, iv_mul(ap0, tr.sec0)));
       r.jac(TH, iv_mul(dt, iv_mul(a0, sec0tan0)));
       r.jac(PS, iv(1.f));
@@ -248,41 +332,65 @@ __device__ __forceinline__ ivl quad3d_row(const SysArgs& a, const Box& b, const 
       r.jac(R_, iv_mul(dt, iv_mul(tr.c0, tr.sec0)));
     }
   } else if constexpr (S <= 8) {   // velocities: (T/m) g + centroid coupling
-    const ivl dtm = cv(K.dt_m), Tm = iv_mul(dtm, iv(b.nom[T_]));
+    const ivl dtm = cv(K.dt_m);
+    auto Tm = [&](const Pre& p) { return iv_mul(dtm, p.T); };
     if constexpr (S < 8) {
+      // g and its partials over the prefix set of each coordinate that can come first in an entry
+      const Pre pP = pre(PH), pT = pre(TH), pS = pre(PS), pU = pre(T_);
+      auto gp = [](const Pre& p) { return g_parts<S>(p.sph, p.cph, p.sth, p.cth, p.sps, p.cps); };
+      const G3 gP = gp(pP), gT = gp(pT), gS = gp(pS), gU = gp(pU);
+      auto G = [&](int f) -> const G3& { return f == PH ? gP : (f == TH ? gT : (f == PS ? gS : gU)); };
+      auto TmF = [&](int f) { return Tm(f == PH ? pP : (f == TH ? pT : (f == PS ? pS : pU))); };
+      r.sq(PH, iv_mul(Tm(pP), iv_neg(gP.g)));
       {
-        const G3 g = g_parts<S>(tr.sP, tr.cP, tr.st0, tr.ct0, tr.ss0, tr.cs0);   // over X^(phi)
-        r.sq(PH, iv_mul(Tm, iv_neg(g.g)));
-        r.cross(PH, TH, iv_mul(Tm, g.phth));
-        r.cross(PH, PS, iv_mul(Tm, g.phps));
-        r.cross(PH, T_, iv_mul(dtm, g.ph));
+        const int f = first(PH, TH);
+        r.cross(PH, TH, iv_mul(TmF(f), G(f).phth));
       }
       {
-        const G3 g = g_parts<S>(tr.sP, tr.cP, tr.sT, tr.cT, tr.ss0, tr.cs0);     // over X^(theta)
-        r.sq(TH, iv_mul(Tm, g.thth));
-        r.cross(TH, PS, iv_mul(Tm, g.thps));
-        r.cross(TH, T_, iv_mul(dtm, g.th));
+        const int f = first(PH, PS);
+        r.cross(PH, PS, iv_mul(TmF(f), G(f).phps));
       }
+      r.cross(PH, T_, iv_mul(dtm, G(first(PH, T_)).ph));
+      r.sq(TH, iv_mul(Tm(pT), gT.thth));
       {
-        const G3 g = g_parts<S>(tr.sP, tr.cP, tr.sT, tr.cT, tr.sS, tr.cS);       // over X^(psi)
-        r.sq(PS, iv_mul(Tm, iv_neg(g.g)));
-        r.cross(PS, T_, iv_mul(dtm, g.ps));
+        const int f = first(TH, PS);
+        r.cross(TH, PS, iv_mul(TmF(f), G(f).thps));
       }
+      r.cross(TH, T_, iv_mul(dtm, G(first(TH, T_)).th));
+      r.sq(PS, iv_mul(Tm(pS), iv_neg(gS.g)));
+      r.cross(PS, T_, iv_mul(dtm, G(first(PS, T_)).ps));
       {
         const G3 g = g_parts<S>(tr.s0, tr.c0, tr.st0, tr.ct0, tr.ss0, tr.cs0);   // at the nominal
-        r.jac(PH, iv_mul(Tm, g.ph));
-        r.jac(TH, iv_mul(Tm, g.th));
-        r.jac(PS, iv_mul(Tm, g.ps));
+        const ivl Tm0 = iv_mul(dtm, iv(b.nom[T_]));
+        r.jac(PH, iv_mul(Tm0, g.ph));
+        r.jac(TH, iv_mul(Tm0, g.th));
+        r.jac(PS, iv_mul(Tm0, g.ps));
         r.jac(T_, iv_mul(dtm, g.g));
       }
     } else {   // g_z = cos(theta) cos(phi)
-      r.sq(PH, iv_mul(Tm, iv_neg(iv_mul(tr.ct0, tr.cP))));
-      r.cross(PH, TH, iv_mul(Tm, iv_mul(tr.st0, tr.sP)));
-      r.sq(TH, iv_mul(Tm, iv_neg(iv_mul(tr.cT, tr.cP))));
-      r.cross(PH, T_, iv_mul(dtm, iv_neg(iv_mul(tr.ct0, tr.sP))));
-      r.cross(TH, T_, iv_mul(dtm, iv_neg(iv_mul(tr.sT, tr.cP))));
-      r.jac(PH, iv_mul(Tm, iv_neg(iv_mul(tr.ct0, tr.s0))));
-      r.jac(TH, iv_mul(Tm, iv_neg(iv_mul(tr.st0, tr.c0))));
+      {
+        const Pre p = pre(PH);
+        r.sq(PH, iv_mul(Tm(p), iv_neg(iv_mul(p.cth, p.cph))));
+      }
+      {
+        const Pre p = pre(first(PH, TH));
+        r.cross(PH, TH, iv_mul(Tm(p), iv_mul(p.sth, p.sph)));
+      }
+      {
+        const Pre p = pre(TH);
+        r.sq(TH, iv_mul(Tm(p), iv_neg(iv_mul(p.cth, p.cph))));
+      }
+      {
+        const Pre p = pre(first(PH, T_));
+        r.cross(PH, T_, iv_mul(dtm, iv_neg(iv_mul(p.cth, p.sph))));
+      }
+      {
+        const Pre p = pre(first(TH, T_));
+        r.cross(TH, T_, iv_mul(dtm, iv_neg(iv_mul(p.sth, p.cph))));
+      }
+      const ivl Tm0 = iv_mul(dtm, iv(b.nom[T_]));
+      r.jac(PH, iv_mul(Tm0, iv_neg(iv_mul(tr.ct0, tr.s0))));
+      r.jac(TH, iv_mul(Tm0, iv_neg(iv_mul(tr.st0, tr.c0))));
       r.jac(T_, iv_mul(dtm, iv_mul(tr.ct0, tr.c0)));
     }
     constexpr int ax = S - 6;
@@ -322,23 +430,23 @@ struct SysShape {
   static constexpr int warp_floats = 32 * as + 3 * 32 * bs + 2 * 32 * rows + (kQuad ? 32 * 12 : 0) + 32;
 };
 
-template <bool kQuad>
+template <bool kQuad, bool kOrd>
 __device__ __forceinline__ ivl eval_row(const SysArgs& a, int s, const Box& b, const Trig& tr, const float* tot,
                                         float (&arow)[SysShape<kQuad>::nc]) {
   if constexpr (kQuad) {
     switch (s) {
-      case 0: return quad3d_row<0>(a, b, tr, tot, arow);
-      case 1: return quad3d_row<1>(a, b, tr, tot, arow);
-      case 2: return quad3d_row<2>(a, b, tr, tot, arow);
-      case 3: return quad3d_row<3>(a, b, tr, tot, arow);
-      case 4: return quad3d_row<4>(a, b, tr, tot, arow);
-      case 5: return quad3d_row<5>(a, b, tr, tot, arow);
-      case 6: return quad3d_row<6>(a, b, tr, tot, arow);
-      case 7: return quad3d_row<7>(a, b, tr, tot, arow);
-      case 8: return quad3d_row<8>(a, b, tr, tot, arow);
-      case 9: return quad3d_row<9>(a, b, tr, tot, arow);
-      case 10: return quad3d_row<10>(a, b, tr, tot, arow);
-      default: return quad3d_row<11>(a, b, tr, tot, arow);
+      case 0: return quad3d_row<0, kOrd>(a, b, tr, tot, arow);
+      case 1: return quad3d_row<1, kOrd>(a, b, tr, tot, arow);
+      case 2: return quad3d_row<2, kOrd>(a, b, tr, tot, arow);
+      case 3: return quad3d_row<3, kOrd>(a, b, tr, tot, arow);
+      case 4: return quad3d_row<4, kOrd>(a, b, tr, tot, arow);
+      case 5: return quad3d_row<5, kOrd>(a, b, tr, tot, arow);
+      case 6: return quad3d_row<6, kOrd>(a, b, tr, tot, arow);
+      case 7: return quad3d_row<7, kOrd>(a, b, tr, tot, arow);
+      case 8: return quad3d_row<8, kOrd>(a, b, tr, tot, arow);
+      case 9: return quad3d_row<9, kOrd>(a, b, tr, tot, arow);
+      case 10: return quad3d_row<10, kOrd>(a, b, tr, tot, arow);
+      default: return quad3d_row<11, kOrd>(a, b, tr, tot, arow);
     }
   } else {
     switch (s) {
@@ -353,7 +461,7 @@ __device__ __forceinline__ ivl eval_row(const SysArgs& a, int s, const Box& b, c
   }
 }
 
-template <bool kQuad>
+template <bool kQuad, bool kOrd>
 __global__ void __launch_bounds__(32 * kSysWarps, kQuad ? 4 : 8) pbh_sys_kernel(SysArgs a) {
   using S = SysShape<kQuad>;
   extern __shared__ __align__(16) float sm[];
@@ -438,7 +546,7 @@ __global__ void __launch_bounds__(32 * kSysWarps, kQuad ? 4 : 8) pbh_sys_kernel(
         float arow[S::nc];
 #pragma unroll
         for (int c = 0; c < S::nc; ++c) arow[c] = 0.f;
-        ivl R = eval_row<kQuad>(a, s, b, tr, tot, arow);
+        ivl R = eval_row<kQuad, kOrd>(a, s, b, tr, tot, arow);
         if (bad || !finite_ivl(R)) R = iv(-CUDART_INF_F, CUDART_INF_F);
         s_R[2 * (lane * S::rows + s)] = R.lo;
         s_R[2 * (lane * S::rows + s) + 1] = R.hi;
@@ -529,25 +637,28 @@ leb_status launch_pbh_sys(const Ctx& c, const SysArgs& args, cudaStream_t s) {
   a.magic_b = (0x100000000ULL + nq - 1) / (unsigned long long)nq;    // ceil(2^32 / nq)
   const size_t smem = (size_t)kSysWarps * (quad ? SysShape<true>::warp_floats : SysShape<false>::warp_floats) *
                       sizeof(float);
-  if (quad && cudaFuncSetAttribute(pbh_sys_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                  cudaSuccess)
+  const bool ord = quad && a.k.custom_order;
+  if (quad && (cudaFuncSetAttribute(pbh_sys_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem) != cudaSuccess ||
+               cudaFuncSetAttribute(pbh_sys_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem) != cudaSuccess))
     return LEB_ERR_CUDA;
   // persistent grid: exactly the CTAs that fit at once, so the warps' uniform iterations leave no tail wave
-  static int resident[2] = {0, 0};
-  int& nb = resident[quad ? 1 : 0];
-  if (nb == 0) {
-    const cudaError_t e = quad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pbh_sys_kernel<true>,
-                                                                                 32 * kSysWarps, smem)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pbh_sys_kernel<false>,
-                                                                                 32 * kSysWarps, smem);
-    if (e != cudaSuccess || nb < 1) nb = 1;
-  }
+  int nb = 0;
+  const cudaError_t e = !quad ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pbh_sys_kernel<false, false>,
+                                                                              32 * kSysWarps, smem)
+                        : ord ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pbh_sys_kernel<true, true>,
+                                                                              32 * kSysWarps, smem)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pbh_sys_kernel<true, false>,
+                                                                              32 * kSysWarps, smem);
+  if (e != cudaSuccess || nb < 1) nb = 1;
   const long long groups = (a.T * nq + 32 * kSysWarps - 1) / (32 * kSysWarps);
   const long long cap = (long long)nb * c.sm_count;
   const int grid = (int)(groups < cap ? groups : cap);
   timer_begin(c, s, quad ? "pbh_quad3d" : "pbh_satellite");
-  if (quad) pbh_sys_kernel<true><<<grid, 32 * kSysWarps, smem, s>>>(a);
-  else pbh_sys_kernel<false><<<grid, 32 * kSysWarps, smem, s>>>(a);
+  if (!quad) pbh_sys_kernel<false, false><<<grid, 32 * kSysWarps, smem, s>>>(a);
+  else if (ord) pbh_sys_kernel<true, true><<<grid, 32 * kSysWarps, smem, s>>>(a);
+  else pbh_sys_kernel<true, false><<<grid, 32 * kSysWarps, smem, s>>>(a);
   timer_end(c, s);
   return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
 }

@@ -312,3 +312,95 @@ def test_graph_capture_matches_direct_call():
         assert int(out["flags"].item()) == 0
         for k in ("r_lo", "r_hi", "A", "B"):
             assert np.array_equal(out[k].cpu().numpy(), ref[k]), k
+
+
+def _global_order(dyn, local):
+    """The path order over all coordinates of a (coupled) 3-D quadrotor system given each quadrotor's
+    local order (states 0..11, inputs 12..15): quadrotor by quadrotor, each in its local order (only the
+    relative order of a quadrotor's own coordinates matters to its rows)."""
+    g = []
+    for i in range(dyn.nq):
+        for c in local:
+            g.append(12 * i + c if c < 12 else 12 * dyn.nq + 4 * i + (c - 12))
+    return g
+
+
+def _angle_orders():
+    """The 12 orders of the path-order study: the three angles in any order, the thrust first or last, the
+    other coordinates in their natural places."""
+    import itertools
+    out = []
+    for perm in itertools.permutations((3, 4, 5)):
+        nat = [0, 1, 2] + list(perm) + [6, 7, 8, 9, 10, 11, 12, 13, 14, 15]
+        out.append(nat)
+        out.append([12] + [c for c in nat if c != 12])
+    return out
+
+
+def test_general_path_order_parity():
+    """leb_set_path_order_perm on the 3-D quadrotor: for the 12 orders of the study (angle orders, thrust
+    first or last) and random permutations of all 16 coordinates, the GPU bounds against the oracle's Thm. 1
+    with the same order (each entry over the prefix set of its first coordinate), on single and three
+    coupled quadrotors; A and B do not depend on the order. The best of the 12 is reported against the
+    natural order on the E1 points."""
+    rng = np.random.default_rng(61)
+    orders = _angle_orders() + [list(rng.permutation(16)) for _ in range(4)]
+    assert len({tuple(o) for o in orders[:12]}) == 12
+    for nq, coupled in ((1, False), (3, True)):
+        w = inputs.quad3d(T=24, n_quads=nq, eps=0.1, coupled=coupled)
+        h, dyn = _pair(w)
+        plain = run_gpu(h, w)
+        widths = []
+        for od in orders:
+            h.set_path_order_perm(od)
+            g = run_gpu(h, w)
+            assert g["flags"][0] == 0
+            assert np.array_equal(g["A"], plain["A"]) and np.array_equal(g["B"], plain["B"])
+            go = _global_order(dyn, od)
+            for t in range(w.T):
+                a = w.nominal()[t].astype(np.float64)
+                lo, hi = pbh.box_from_set(a, radii=w.radii[t], center=None)
+                ol, oh = pbh.pbh(dyn, a, lo, hi, order=go)
+                eps = tolerance(dyn, a, lo, hi, dyn.jacobian(a))
+                scale = np.abs(ol) + np.abs(oh) + 1e-300
+                gl, gh = g["r_lo"][t].astype(np.float64), g["r_hi"][t].astype(np.float64)
+                assert np.all(gl <= ol + 1e-12 * scale) and np.all(gh >= oh - 1e-12 * scale), (od, t)
+                assert np.all((gh - gl) <= (oh - ol) * (1 + 1e-5) + eps), (od, t)
+            widths.append(float((g["r_hi"] - g["r_lo"]).mean()))
+        h.set_path_order_perm(None)
+        g = run_gpu(h, w)
+        assert np.array_equal(g["r_lo"], plain["r_lo"]) and np.array_equal(g["r_hi"], plain["r_hi"])
+        nat = float((plain["r_hi"] - plain["r_lo"]).mean())
+        best = int(np.argmin(widths[:12]))
+        print(f"{nq} quadrotor(s): best of the 12 orders {orders[best]} width / natural = {widths[best] / nat:.4f}")
+    with pytest.raises(binding.LebError):
+        h.set_path_order_perm([0] * 16)
+    with pytest.raises(binding.LebError):
+        h.set_path_order_perm(list(range(15)))
+
+
+def test_chain_general_path_order_parity():
+    """The quad chain with one input before the attitude and the other after it (a local order that
+    leb_set_path_order cannot express), against the oracle's Thm. 1 with that order, every timestep of a
+    two-quadrotor zonotope batch."""
+    from oracle import dynamics
+    import test_gpu_pbh as tp
+    w = inputs.quad_chain(n_traj=2, horizon=4, n_quads=2)
+    dyn = dynamics.QuadChain(2, **w.params, spring_k=w.spring_k)
+    h = binding.quad_chain(2, **w.params, spring_k=w.spring_k)
+    local = [0, 1, 7, 3, 2, 4, 5, 6]        # u2 before phi, u1 after
+    h.set_path_order_perm(local)
+    g = tp.run_gpu(w, G=w.G, handle=h, batch=True)
+    assert g["flags"][0] == 0
+    go = []
+    for i in range(2):
+        for c in local:
+            go.append(6 * i + c if c < 6 else 12 + 2 * i + (c - 6))
+    for t in range(w.T):
+        a = w.nominal()[t].astype(np.float64)
+        lo, hi = pbh.box_from_set(a, G=w.G[t])
+        ol, oh = pbh.pbh(dyn, a, lo, hi, order=go)
+        eps = tp.tolerance(dyn, a, lo, hi, dyn.jacobian(a))
+        scale = np.abs(ol) + np.abs(oh) + 1e-300
+        assert np.all(g["r_lo"][t] <= ol + 1e-12 * scale) and np.all(g["r_hi"][t] >= oh - 1e-12 * scale), t
+        assert np.all((g["r_hi"][t] - g["r_lo"][t]) <= (oh - ol) * (1 + 1e-5) + eps), t
