@@ -51,18 +51,18 @@ MLP_WIDTHS = (224, 512, 512, 512, 168)
 PROPOSER_FLOP = 2 * (392 * 256 + 256 * 256 + 256 * 336)                           # 503,808 per sample
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch and timestep of each form's timed
-# kernels, from one ncu capture of the small-batch bench (--quick: 16 x 50 quad-chain timesteps, 8 x 50
-# tanh-MLP timesteps); traffic grows in proportion to the timesteps a launch processes, so a launch of T
-# timesteps moves T times this. Summary and command: profiles/dram_traffic_bench_kernels_quick.md.
+# kernels, from ncu captures (one launch each, the captured size beside each entry); traffic grows in
+# proportion to the timesteps a launch processes, so a launch of T timesteps moves T times this.
 DRAM_BYTES_PER_TS_LAUNCH = {
-    "pbh": 312_957_184 / 800,                  # pbh_zono_tma_kernel<false> (no attitude cut)
+    # pbh_zono_tma_kernel<0> (the plain instance), one launch at T = 3200 (64 x 50), whose 486 MB of A/B
+    # writes exceed the L2 (the last ~53 MB of them are still in L2 when the launch ends)
+    "pbh": (971_229_440 + 433_273_856) / 3200,
     "crown": 44_853_504 / (3 * 400),           # crown_tc_kernel, mean over its 3 launches
     "backward": 90_078_976 / (5 * 400),        # 2 tight crown_tc_kernel + 3 adjoint_tc_kernel launches, mean
     # pbh_sys_kernel<true>, captured at the bench's own size (12800 timesteps of the 168-state coupled
-    # system, profiles/pbh_sys_kernel_coupled_quad3d14_T12800.md)
+    # system)
     "pbh_sys": (39_297_792 + 1_901_738_000) / 12800,
-    # tube_kernel, captured at the bench's own size (16 trajectories: one unit = one trajectory,
-    # profiles/tube_kernel_168x25_16traj.md)
+    # tube_kernel, captured at the bench's own size (16 trajectories: one unit = one trajectory)
     "tube": (783_316_480 + 6_126_592) / 16,
 }
 
@@ -109,9 +109,34 @@ def peaks():
                 "src": "fallback"}
 
 
+_FP32_PEAK = {}
+
+
 def fp32_simt_peak_tflops(pk):
-    """FP32 FMA peak of the CUDA cores: 148 SMs x 128 lanes x 2 FLOP x max SM clock."""
-    return 148 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    """FP32 peak of the CUDA cores, measured once: the best of five cuBLAS FP32 GEMMs of 8192^3 with TF32
+    off (2 N^3 FLOP each; a plain FP32 GEMM runs its FMAs on the CUDA cores)."""
+    if "v" not in _FP32_PEAK:
+        import torch
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        try:
+            n = 8192
+            a = torch.randn(n, n, device="cuda")
+            b = torch.randn(n, n, device="cuda")
+            c = a @ b
+            best = 1e30
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            _FP32_PEAK["v"] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+            del a, b, c
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = prev
+    return _FP32_PEAK["v"]
 
 
 # ------------------------------------------------------------------------------------------------
@@ -211,10 +236,10 @@ class PbhForm(Form):
     r_lo, r_hi and A (168 x 168), B (168 x 56) written, all FP32: 453,824 B."""
     name = "pbh"
 
-    def __init__(self, torch, dev, quick=False):
+    def __init__(self, torch, dev, quick=False, n_traj=None):
         from paper_2607_01203_b300 import binding, inputs
         self.torch = torch
-        self.w = inputs.quad_chain(n_traj=16 if quick else 256, horizon=50)
+        self.w = inputs.quad_chain(n_traj=n_traj or (16 if quick else 256), horizon=50)
         w = self.w
         self.T = w.T
         self.handle = binding.quad_chain(28, **w.params, spring_k=w.spring_k)
@@ -431,7 +456,7 @@ class BackwardForm(Form):
         return {"bound": "tensor" if tc else "alu", "achieved": round(achieved, 2), "peak": round(peak, 1),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": dram_traffic("backward", self.T),
                 "peak_src": (pk["src"] + " bf16_tflops") if tc else
-                "FP32 FMA peak derived: 148 SM x 128 lanes x 2 FLOP x max SM clock (MEASURED_PEAKS sm_max_mhz)",
+                "FP32 peak measured here: cuBLAS FP32 GEMM 8192^3, TF32 off, best of 5",
                 "kernel": kernel, "kernel_ms": round(ms / max(launches, 1), 4), "launches_per_step": launches,
                 "flop_per_unit": adjoint_flop_per_ts(), "units_per_step": self.T}
 
@@ -1005,6 +1030,8 @@ def reference_arm(args):
     if rank != 0:
         return
     import torch
+    cores = os.cpu_count() or 1
+    torch.set_num_threads(cores)   # the oracle's BLAS (torch CPU, NumPy) on every host core
     from paper_2607_01203_b300 import inputs
     from oracle import crown, dynamics, dynamics3d, pbh
     wq = inputs.quad_chain(n_traj=4, horizon=50)
@@ -1017,7 +1044,7 @@ def reference_arm(args):
     g = np.random.default_rng(7).normal(size=(2, 168))
     n_pbh, n_crown, n_bwd, n_sys = 16, 2, 1, 8
     T_pbh, T_mlp, T_sys = 12800, 6400, 12800
-    est = []
+    est, meas = [], []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         for i in range(n_pbh):
@@ -1047,22 +1074,26 @@ def reference_arm(args):
         otube.tube(wt.Phi[b], wt.N, wt.c[b * wt.N:(b + 1) * wt.N], wt.r[b * wt.N:(b + 1) * wt.N], wt.e.astype(np.float64))
         t5 = time.perf_counter()
         if s >= args.warmup:
+            meas.append(t5 - t0)
             # time the oracle would take for one full step of the same workload
             est.append((t1 - t0) / n_pbh * T_pbh + (t2 - t1) / n_crown * T_mlp + (t3 - t2) / n_bwd * T_mlp
                        + (t4 - t3) / n_sys * T_sys + (t5 - t4) * 16)
     step_s = statistics.mean(est)
     v = (T_pbh + T_mlp + T_sys) / step_s
-    cores = torch.get_num_threads()
-    sample = (f"per step {n_pbh} PBH chain timesteps and {n_sys} coupled 3-D quadrotor timesteps (1 core), "
-              f"{n_crown} CROWN and {n_bwd} adjoint timesteps (torch, {cores} threads) and 1 of the 16 tube "
-              f"trajectories (NumPy) of the bench workloads, scaled to a full step")
+    threads = torch.get_num_threads()
+    sample = (f"per step {n_pbh} PBH chain timesteps and {n_sys} coupled 3-D quadrotor timesteps (NumPy), "
+              f"{n_crown} CROWN and {n_bwd} adjoint timesteps (torch CPU, {threads} threads) and 1 of the 16 tube "
+              f"trajectories (NumPy) of the bench workloads; value = the full step's mix of timestep-bounds "
+              f"over the per-form sample rates (ms_per_step: the sample as run)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(meas),
+            "ms_per_full_step_extrapolated": 1e3 * step_s, "host_cores": cores,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "pbh 256x50 quad chain (zonotope) + crown 128x50 tanh MLP + adjoint + "
                                    "pbh_sys 256x50 coupled 3-D quadrotors + tube 16x25, FP64 oracle on a bounded sample per step",
                        "parallelism": "host"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "host_cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -1075,6 +1106,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--forms", default="pbh,crown,backward,proposer,pbh_grad,pbh_sys,tube")
     ap.add_argument("--quick", action="store_true", help="small batches (smoke runs, not a bench value)")
+    ap.add_argument("--pbh-traj", type=int, default=None,
+                    help="trajectories of 50 timesteps in the pbh form (profiling captures; not a bench value)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -1095,7 +1128,7 @@ def main():
     crown = None
     for nm in names:
         if nm == "pbh":
-            forms.append(PbhForm(torch, dev, args.quick))
+            forms.append(PbhForm(torch, dev, args.quick, args.pbh_traj))
         elif nm == "crown":
             crown = CrownForm(torch, dev, args.quick)
             forms.append(crown)
@@ -1179,6 +1212,7 @@ def main():
             d["value"] = round(f.units() / (form_ms[f.name] * 1e-3), 1)
         if f.name in ("backward", "pbh_grad"):
             d["us_per_call"] = round(1e3 * form_ms[f.name], 1)
+            d["us_per_timestep"] = round(1e3 * form_ms[f.name] / f.T, 3)
         if f.name == "pbh_grad":
             d["nominal_refinement_table2"] = f.pgd
         if f.name == "pbh_sys":
@@ -1230,6 +1264,14 @@ def main():
                               if flush is None else "512 MB L2 flush between steps, outside the form timers"),
                        "parallelism": f"replicas x{world}"},
             "roofline": roof[dom.name], "forms": out_forms,
+            # the metric's two named forms at n_x = 168, N = 50, each with its main kernel's roofline fraction
+            **({"plain_form": {"value": out_forms["pbh"].get("value"), "unit": UNIT,
+                               "frac": roof["pbh"]["frac"], "kernel": roof["pbh"]["kernel"]}} if "pbh" in out_forms else {}),
+            **({"tensor_core_form": {"value": out_forms["crown"].get("value"), "unit": UNIT,
+                                     "frac": roof["crown"]["frac"], "kernel": roof["crown"]["kernel"]}}
+               if "crown" in out_forms else {}),
+            **({"backward_us_per_timestep": out_forms["backward"].get("us_per_timestep"),
+                "backward_frac": roof["backward"]["frac"]} if "backward" in out_forms else {}),
             "e2e": {"value": units / (pipe_ms * 1e-3) if pipe_ms > 0 else None, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(pipe_ms, 3),
                     "how": "every form's inputs copied in from pinned host memory, its library calls and its "
@@ -1249,6 +1291,7 @@ def main():
 
 def cpu_baseline(forms, torch):
     """The oracle as it stands on a bounded sample of each form, scaled to the step's metric."""
+    torch.set_num_threads(os.cpu_count() or 1)   # the oracle's BLAS on every host core
     budget = {"pbh": 6.0, "crown": 6.0, "backward": 8.0, "pbh_sys": 4.0, "tube": 2.0}
     step_s, units, parts = 0.0, 0, []
     for f in forms:
@@ -1259,8 +1302,9 @@ def cpu_baseline(forms, torch):
         units += f.units()
         parts.append(f"{f.name}: {n} timesteps ({spu * 1e3:.1f} ms each)")
     return {"value": units / step_s if step_s else None, "unit": UNIT,
-            "cores": f"pbh 1; crown/backward {torch.get_num_threads()} (torch threads)", "kind": "oracle",
-            "sample": "; ".join(parts) + " — scaled to one full step"}
+            "cores": torch.get_num_threads(), "host_cores": os.cpu_count(), "kind": "oracle",
+            "sample": "; ".join(parts) + " — scaled to one full step (NumPy PBH/tube per timestep, torch CPU "
+                      "CROWN/adjoint on every host core)"}
 
 
 if __name__ == "__main__":
