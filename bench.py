@@ -357,10 +357,38 @@ class CrownForm(Form):
         self.x = torch.as_tensor(w.x_nom).to(dev)
         self.u = torch.as_tensor(w.u_nom).to(dev)
         self.r = torch.as_tensor(w.radii).to(dev)
-        self.out = self.handle.bounds(self.x, self.u, radii=self.r)
+        self.handle.autotune(self.T, binding.SET_BOX)   # the chain kernels' job width (bit-identical plans)
+        self.plan = self.handle.plan()
+        self.out = self.handle.bounds(self.x, self.u, radii=self.r, want_eps=True)
         torch.cuda.synchronize()
         self.ibp = self._ibp_variant(torch, binding)
+        self.formats = self._formats(torch, binding)
         self.desc = f"residual tanh MLP 224-512-512-512-168, {self.T // 50} traj x N=50, box sets, FP16 TC"
+
+    def _formats(self, torch, binding):
+        """Once at start-up (untimed in the step): the same batch with BF16 operands and on the FP32 CUDA-core
+        chains; per format the time per call, the summed width against the FP32 path's, and the share of the
+        width that is the stated rounding slack (eps / 2 per side against the width)."""
+        res = {}
+        w32 = None
+        outs = {"fp16": self.out}
+        for fmt in ("bf16", "fp32"):
+            h = binding.mlp(self.w.Ws, self.w.bs, self.w.act, self.w.residual, fmt)
+            if fmt == "bf16":
+                h.autotune(self.T, binding.SET_BOX)
+            o = h.bounds(self.x, self.u, radii=self.r, want_eps=True)
+            torch.cuda.synchronize()
+            ms = timed_loop(torch, lambda: h.bounds(self.x, self.u, radii=self.r, out=o), 1 if fmt == "fp32" else 5)
+            outs[fmt] = {k: v for k, v in o.items()}
+            res[fmt] = {"ms_per_call": round(ms, 3)}
+            del h
+        w32 = (outs["fp32"]["r_hi"] - outs["fp32"]["r_lo"]).double().sum()
+        for fmt, o in outs.items():
+            wsum = (o["r_hi"] - o["r_lo"]).double().sum()
+            d = res.setdefault(fmt, {})
+            d["width_vs_fp32_path"] = round(float(wsum / w32), 4)
+            d["stated_slack_share_of_width"] = round(float((o["eps"].double()).sum() / wsum), 4)
+        return res
 
     def _ibp_variant(self, torch, binding):
         """Once at start-up (untimed in the step): the IBP-intermediate variant on the same batch, its
@@ -1220,6 +1248,8 @@ def main():
             d["path_order_best_of_12"] = f.order
         if f.name == "crown":
             d["ibp_intermediate_variant"] = f.ibp
+            d["formats"] = f.formats
+            d["plan"] = f.plan
         if f.name == "pbh":
             d["ragged_horizons_graph"] = f.ragged
             d["inputs_first_path_order"] = f.order

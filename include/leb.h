@@ -212,7 +212,12 @@ leb_status leb_zonotope_map(const float* r_lo, const float* r_hi, long long coun
 /* Times the candidate launch configurations of this handle on synthetic data of T timesteps and the
  * given set kind / generator count, keeps the fastest in the handle, and (if cache_path is not NULL)
  * reads/writes a text cache keyed by GPU name and problem signature. Synchronizes the device: do not
- * call during stream capture. Buffers: workspace as for leb_bounds. */
+ * call during stream capture. Buffers: workspace as for leb_bounds. Candidates: for quad chains the
+ * PBH kernel's block size, CTAs per SM and ring stages; for MLP handles on the tensor cores (FP16/BF16)
+ * the chain kernels' job width, 256 or 128 columns (how the final stage, and hidden stages of at most 256
+ * columns, are issued as MMA jobs; a wider hidden stage always takes two jobs; box sets are timed whatever
+ * set_kind says); every candidate gives the same bits. Other handles: nothing to tune
+ * (LEB_OK). */
 leb_status leb_autotune(leb_handle h, int T, leb_set_kind set_kind, int n_gen, const char* cache_path,
                         void* workspace, size_t ws_bytes, void* stream);
 /* Current plan as text ("key=value;..."), for logs and tests. */

@@ -49,8 +49,7 @@ namespace leb {
 constexpr int kTcEpiWarps = 8;                  // 2 per TMEM lane quarter, 32 columns of every 64-column block each
 constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
 constexpr int kTcNSB = 2;                       // B ring stages
-constexpr int kTcBRows = 256;                   // N rows of one B tile (the MMA's N)
-constexpr int kTcBStage = kTcBRows * 128;       // 256 rows x 64 K x 2 bytes
+constexpr int kTcBStage = 256 * 128;            // B tile of at most 256 rows (one job) x 64 K x 2 bytes
 constexpr int kTcARegion = 128 * 512 * 2;       // 128 rows x 512 K x 2 bytes (8 blocks of 16 KB)
 constexpr int kTcVecBuf = 512 * 24 + 512 * 4;   // per-neuron line slots {s, tau'} x {lower, upper, Jacobian}, w
 constexpr int kTcStat = 128 * 2 * 3 * 4;        // [row][column group][3]
@@ -63,7 +62,8 @@ static_assert(kTcSmem <= 227 * 1024, "tensor-core chain shared memory");
 
 struct TcArgs {
   CUtensorMap tmap[kMaxLayers];  // W_k^T in FP16/BF16: [widths[k] rows, widths[k+1] cols], box {64, brows[k]}
-  int brows[kMaxLayers];         // rows of a B tile of W_k^T: min(128, widths[k])
+  int brows[kMaxLayers];         // rows of a B tile of W_k^T: min(jw, widths[k])
+  int jw;                        // job width (the plan's choice, a multiple of 64, at most 256: one TMEM half)
   int L;
   int widths[kMaxLayers + 1];
   int residual;
@@ -220,11 +220,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  // Jobs of stage k (the product with W_k, N = widths[k] columns): one job if N <= 256, else two, split
-  // at a multiple of 64 so that every job of a hidden stage covers whole operand blocks.
-  auto stage_split = [&](int k) -> int {
+  // Jobs of stage k (the product with W_k, N = widths[k] columns); jobs alternate TMEM halves.
+  // A hidden stage (k >= 1) writes the next operand over blocks the stage's last job still reads, so a
+  // job's epilogue can finish only after that last job: with two TMEM halves a hidden stage has at most
+  // two jobs (one if N <= jw, else two split at a multiple of 64 covering whole operand blocks). The final
+  // stage (k = 0) writes no operand: jobs of jw columns, [h jw, min(N, (h + 1) jw)).
+  const int jw = a.jw;
+  auto njobs = [&](int k) -> int {
     const int N = a.widths[k];
-    return N > 256 ? 64 * ((N + 127) / 128) : N;
+    return k == 0 ? (N + jw - 1) / jw : (N > jw ? 2 : 1);
+  };
+  auto job_c0 = [&](int k, int h) -> int {
+    const int N = a.widths[k];
+    return k == 0 ? h * jw : (h ? 64 * ((N + 127) / 128) : 0);
+  };
+  auto job_nc = [&](int k, int h) -> int {
+    const int N = a.widths[k];
+    if (k == 0) return min(jw, N - h * jw);
+    if (N <= jw) return N;
+    const int split = 64 * ((N + 127) / 128);
+    return h ? N - split : split;
   };
 
   if (warp == 0) {
@@ -235,18 +250,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       bool ok = true;
       for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
         for (int k = target - 1; k >= 0 && ok; --k) {
-          const int N = a.widths[k], nK = a.widths[k + 1] / 64, split = stage_split(k);
-          for (int h = 0; h < (N > split ? 2 : 1) && ok; ++h) {
-            const int c0 = h ? split : 0, nc = h ? N - split : split;
-            const int nbt = (nc + kTcBRows - 1) / kTcBRows;
-            for (int kc = 0; kc < nK && ok; ++kc)
-              for (int bt = 0; bt < nbt; ++bt, ++kb) {
-                const int s = (int)(kb % kTcNSB);
-                if (kb >= (uint32_t)kTcNSB && !mbar_wait(&b_empty[s], ((kb / kTcNSB) - 1) & 1u)) { ok = false; break; }
-                if (*(volatile int*)&s_abort) { ok = false; break; }
-                mbar_arrive_expect_tx(&b_full[s], (uint32_t)a.brows[k] * 128u);
-                tma_load_2d(Bsm + (size_t)s * kTcBStage, &a.tmap[k], kc * 64, c0 + bt * kTcBRows, &b_full[s]);
-              }
+          const int nK = a.widths[k + 1] / 64, nh = njobs(k);
+          for (int h = 0; h < nh && ok; ++h) {
+            const int c0 = job_c0(k, h);
+            for (int kc = 0; kc < nK && ok; ++kc, ++kb) {
+              const int s = (int)(kb % kTcNSB);
+              if (kb >= (uint32_t)kTcNSB && !mbar_wait(&b_empty[s], ((kb / kTcNSB) - 1) & 1u)) { ok = false; break; }
+              if (*(volatile int*)&s_abort) { ok = false; break; }
+              mbar_arrive_expect_tx(&b_full[s], (uint32_t)a.brows[k] * 128u);
+              tma_load_2d(Bsm + (size_t)s * kTcBStage, &a.tmap[k], kc * 64, c0, &b_full[s]);
+            }
           }
         }
       }
@@ -267,11 +280,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       bool ok = true;
       for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
         for (int k = target - 1; k >= 0 && ok; --k) {
-          const int N = a.widths[k], nK = a.widths[k + 1] / 64, split = stage_split(k);
-          const int nh = N > split ? 2 : 1;
+          const int nK = a.widths[k + 1] / 64, nh = njobs(k);
           for (int h = 0; h < nh && ok; ++h, ++jc) {
-            const int nc = h ? N - split : split;
-            const int nbt = (nc + kTcBRows - 1) / kTcBRows;
+            const int nc = job_nc(k, h);
             const uint32_t hb = jc & 1u;
             if ((used >> hb) & 1u) {
               if (!mbar_wait(&acc_free[hb], (fpar >> hb) & 1u)) { ok = false; break; }
@@ -285,20 +296,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
                 rpar ^= 1u << kc;
                 tc_fence_after();
               }
-              for (int bt = 0; bt < nbt; ++bt, ++kb) {
+              {
                 const int s = (int)(kb % kTcNSB);
                 if (!mbar_wait(&b_full[s], (kb / kTcNSB) & 1u)) { ok = false; break; }
                 tc_fence_after();
-                const int nn = min(kTcBRows, nc - bt * kTcBRows);
-                const uint32_t idesc = idesc_f16(128, nn, FMT);
+                const uint32_t idesc = idesc_f16(128, nc, FMT);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
                   const uint64_t ad = sw128_desc(a_base + kc * 16384 + kk * 32);
                   const uint64_t bd = sw128_desc(b_base + s * kTcBStage + kk * 32);
-                  tc_mma_f16(tmem + hb * 256u + (uint32_t)(bt * kTcBRows), ad, bd, idesc,
-                             (kc > 0 || kk > 0) ? 1u : 0u);
+                  tc_mma_f16(tmem + hb * 256u, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
                 }
                 tc_commit(&b_empty[s]);
+                ++kb;
               }
               if (h == nh - 1) tc_commit(&a_free[kc]);
             }
@@ -703,9 +713,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
         prefetch_next(t, k - 1, next);
         apend |= (1u << (a.widths[k + 1] / 64)) - 1u;   // stage k's reads of the operand it consumes
         if (ri.bound) ucon = __fadd_ru(ucon, ucon_of(t, k - 1));
-        const int N = a.widths[k], split = stage_split(k);
-        for (int h = 0; h < (N > split ? 2 : 1) && ok; ++h, ++jc)
-          ok = stage_job(ri, jc & 1u, h ? split : 0, h ? N - split : split, vcur, beta, infl);
+        const int nh = njobs(k);
+        for (int h = 0; h < nh && ok; ++h, ++jc)
+          ok = stage_job(ri, jc & 1u, job_c0(k, h), job_nc(k, h), vcur, beta, infl);
       }
       if (!ok) break;
       // the next item's prologue, built while the tensor cores run this item's final stage
@@ -731,9 +741,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       }
       if (lane == 0) prefetch_l1(a.bad + t);
       float2 sum = z2;
-      const int N0 = a.widths[0], split0 = stage_split(0);
-      for (int h = 0; h < (N0 > split0 ? 2 : 1) && ok; ++h, ++jc)
-        ok = conc_job(t, ri, jc & 1u, h ? split0 : 0, h ? N0 - split0 : split0, sum);
+      const int nh0 = njobs(0);
+      for (int h = 0; h < nh0 && ok; ++h, ++jc)
+        ok = conc_job(t, ri, jc & 1u, job_c0(0, h), job_nc(0, h), sum);
       if (!ok) break;
       if (!finalize(t, tile, ri, sum, beta, infl, ucon)) { ok = false; break; }
       beta[0] = beta_n[0];
@@ -788,9 +798,12 @@ __global__ void transpose_round_kernel(const float* W, int rows, int cols, uint1
 
 }  // namespace
 
+// Job widths of the tensor-core chain plans (leb_autotune / leb_plan_select choose among them).
+constexpr int kTcJobWidths[kTcPlans] = {256, 128};
+
 struct TcState {
   uint16_t* WT[kMaxLayers] = {};
-  CUtensorMap maps[kMaxLayers];
+  CUtensorMap maps[kTcPlans][kMaxLayers];   // per plan: B tiles of min(job width, widths[k]) rows
 };
 
 static TcState* tc_state(const Ctx& c) { return reinterpret_cast<TcState*>(c.mlp.tc); }
@@ -816,12 +829,15 @@ leb_status tc_prepare(Ctx& c) {
     if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)N};
     cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)(N < kTcBRows ? N : kTcBRows)};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(&st->maps[k], fmt == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                     st->WT[k], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return LEB_ERR_UNSUPPORTED;
+    for (int p = 0; p < kTcPlans; ++p) {
+      const int jw = k == 0 ? kTcJobWidths[p] : 256;   // hidden stages: jobs of up to 256 columns
+      cuuint32_t box[2] = {64, (cuuint32_t)(N < jw ? N : jw)};
+      cuuint32_t estr[2] = {1, 1};
+      CUresult r = enc(&st->maps[p][k], fmt == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                       2, st->WT[k], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return LEB_ERR_UNSUPPORTED;
+    }
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return LEB_ERR_CUDA;
   const void* kernels[] = {(const void*)crown_tc_kernel<false, false, 0>, (const void*)crown_tc_kernel<true, false, 0>,
@@ -864,9 +880,12 @@ leb_status tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, 
   if (!st) return LEB_ERR_UNSUPPORTED;
   TcArgs a;
   memset(&a, 0, sizeof(a));
+  const int plan = (c.plan_index >= 0 && c.plan_index < kTcPlans) ? c.plan_index : m.tc_plan;
+  a.jw = kTcJobWidths[plan];
   for (int k = 0; k + 1 < m.L; ++k) {
-    a.tmap[k] = st->maps[k];
-    a.brows[k] = m.widths[k] < kTcBRows ? m.widths[k] : kTcBRows;
+    a.tmap[k] = st->maps[plan][k];
+    const int box = k == 0 ? a.jw : 256;
+    a.brows[k] = m.widths[k] < box ? m.widths[k] : box;
   }
   a.L = m.L;
   for (int i = 0; i <= m.L; ++i) a.widths[i] = m.widths[i];

@@ -101,6 +101,7 @@ struct PbhArgs {
 
 // ---- MLP ---------------------------------------------------------------------------------------
 constexpr int kMaxLayers = 8;
+constexpr int kTcPlans = 2;       // tensor-core chain plans: job widths 256, 128 columns
 
 struct MlpModel {
   int L = 0;                      // affine layers
@@ -117,6 +118,7 @@ struct MlpModel {
   float* Werr[kMaxLayers] = {};   // [out, in] |W - W~| (W~ = reduced-precision value), FP32 rounded up
   float* Wabs_h[kMaxLayers] = {}; // [out, in] |W~| FP32
   void* tc = nullptr;             // tensor-core state (rounded transposed weights, TMA descriptors)
+  int tc_plan = 0;                // tensor-core chain plan in use (job width; leb_autotune)
   void* adj = nullptr;            // tensor-core adjoint state (rounded weights, TMA descriptors)
 };
 

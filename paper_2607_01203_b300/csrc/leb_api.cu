@@ -488,7 +488,8 @@ leb_status leb_zonotope_map(const float* r_lo, const float* r_hi, long long coun
 // ---- plans ---------------------------------------------------------------------------------------
 leb_status leb_plan_count(leb_handle h, int* count) {
   if (!h || !count) return LEB_ERR_INVALID_ARG;
-  *count = h->kind == LEB_DYN_QUAD_CHAIN ? (int)h->pbh_candidates.size() : 1;
+  *count = h->kind == LEB_DYN_QUAD_CHAIN ? (int)h->pbh_candidates.size()
+           : (h->kind == LEB_DYN_MLP && h->mlp.tc) ? kTcPlans : 1;
   return LEB_OK;
 }
 
@@ -548,7 +549,7 @@ leb_status leb_plan_select(leb_handle h, int index) {
   int n = 0;
   leb_plan_count(h, &n);
   if (index < -1 || index >= n) return LEB_ERR_INVALID_ARG;
-  h->plan_index = h->kind == LEB_DYN_QUAD_CHAIN ? index : -1;
+  h->plan_index = (h->kind == LEB_DYN_QUAD_CHAIN || (h->kind == LEB_DYN_MLP && h->mlp.tc)) ? index : -1;
   return LEB_OK;
 }
 
@@ -566,6 +567,10 @@ leb_status leb_plan_string(leb_handle h, char* buf, size_t buf_len) {
   } else {
     os << "kernel=mlp;prec=" << h->mlp.prec << ";layers=" << h->mlp.L << ";intermediate="
        << (h->mlp.ibp ? "ibp" : "crown");
+    if (h->mlp.tc) {
+      static const int jws[kTcPlans] = {256, 128};
+      os << ";tc_job_cols=" << jws[h->plan_index >= 0 ? h->plan_index : h->mlp.tc_plan];
+    }
   }
   if (!h->plan_note.empty()) os << ";" << h->plan_note;
   std::string s = os.str();
@@ -573,10 +578,97 @@ leb_status leb_plan_string(leb_handle h, char* buf, size_t buf_len) {
   return LEB_OK;
 }
 
+// Tensor-core MLP handles: time leb_bounds (box sets, radii 0.01, the nominal at 0.1) under every chain plan
+// (job width), keep the fastest; the plans give the same bits (only how a stage's columns are grouped into
+// MMA jobs differs, not any sum).
+static leb_status mlp_autotune(leb_handle h, int T, const char* cache_path, void* workspace, size_t ws_bytes,
+                               void* stream) {
+  MlpWs lay;
+  if (!workspace || ws_bytes < kWsHeader + mlp_workspace_floats(*h, T, &lay) * sizeof(float)) return LEB_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) return LEB_ERR_CUDA;
+  std::ostringstream sig;
+  sig << prop.name << "|mlp|prec=" << h->mlp.prec << "|ibp=" << h->mlp.ibp << "|widths=";
+  for (int i = 0; i <= h->mlp.L; ++i) sig << h->mlp.widths[i] << ",";
+  sig << "|T=" << T;
+  const std::string key = sig.str();
+  if (cache_path) {
+    std::ifstream in(cache_path);
+    std::string line;
+    while (std::getline(in, line)) {
+      const size_t bar = line.rfind('|');
+      if (bar == std::string::npos || line.substr(0, bar) != key) continue;
+      int idx = -1;
+      if (std::sscanf(line.c_str() + bar + 1, "%d", &idx) == 1 && idx >= 0 && idx < kTcPlans) {
+        h->mlp.tc_plan = idx;
+        h->plan_index = -1;
+        h->plan_note = "autotune=cache";
+        return LEB_OK;
+      }
+    }
+  }
+  const int nx = h->n_x, nu = h->n_u, n = nx + nu;
+  float *x = nullptr, *u = nullptr, *R = nullptr, *lo = nullptr, *hi = nullptr, *A = nullptr, *B = nullptr;
+  int* flags = nullptr;
+  bool ok = cudaMalloc(&x, (size_t)T * nx * 4) == cudaSuccess && cudaMalloc(&u, (size_t)T * nu * 4) == cudaSuccess &&
+            cudaMalloc(&R, (size_t)T * n * 4) == cudaSuccess && cudaMalloc(&lo, (size_t)T * nx * 4) == cudaSuccess &&
+            cudaMalloc(&hi, (size_t)T * nx * 4) == cudaSuccess && cudaMalloc(&A, (size_t)T * nx * nx * 4) == cudaSuccess &&
+            cudaMalloc(&B, (size_t)T * nx * nu * 4) == cudaSuccess && cudaMalloc(&flags, 4) == cudaSuccess;
+  leb_status st = ok ? LEB_OK : LEB_ERR_CUDA;
+  if (ok) {
+    std::vector<float> hx((size_t)T * nx, 0.1f), hu((size_t)T * nu, 0.1f), hr((size_t)T * n, 0.01f);
+    ok = cudaMemcpy(x, hx.data(), hx.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(u, hu.data(), hu.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(R, hr.data(), hr.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) st = LEB_ERR_CUDA;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ok) ok = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  int best = -1;
+  float best_ms = 1e30f;
+  std::ostringstream all;
+  leb_set set{LEB_SET_BOX, nullptr, R, nullptr, 0};
+  for (int i = 0; ok && i < kTcPlans; ++i) {
+    h->plan_index = i;
+    float ms_min = 1e30f;
+    for (int rep = 0; rep < 4 && ok; ++rep) {
+      cudaEventRecord(e0, s);
+      st = leb_bounds(h, nullptr, T, x, u, &set, lo, hi, A, B, nullptr, workspace, ws_bytes, flags, s);
+      cudaEventRecord(e1, s);
+      if (st != LEB_OK || cudaEventSynchronize(e1) != cudaSuccess) { ok = false; break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0 && ms < ms_min) ms_min = ms;
+    }
+    all << (i ? "," : "") << ms_min;
+    if (ok && ms_min < best_ms) { best_ms = ms_min; best = i; }
+  }
+  h->plan_index = -1;
+  if (best >= 0) {
+    h->mlp.tc_plan = best;
+    std::ostringstream note;
+    note << "autotune=measured;ms=" << best_ms << ";ms_per_plan=" << all.str();
+    h->plan_note = note.str();
+    if (cache_path) {
+      std::ofstream outf(cache_path, std::ios::app);
+      outf << key << "|" << best << "\n";
+    }
+    st = LEB_OK;
+  } else if (st == LEB_OK) {
+    st = LEB_ERR_CUDA;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(x); cudaFree(u); cudaFree(R); cudaFree(lo); cudaFree(hi); cudaFree(A); cudaFree(B); cudaFree(flags);
+  return st;
+}
+
 leb_status leb_autotune(leb_handle h, int T, leb_set_kind set_kind, int n_gen, const char* cache_path,
                         void* workspace, size_t ws_bytes, void* stream) {
   if (!h || T < 1 || (set_kind == LEB_SET_ZONO && n_gen < 1)) return LEB_ERR_INVALID_ARG;
-  if (h->kind != LEB_DYN_QUAD_CHAIN) return LEB_OK;  // MLP plans are fixed by the layer shapes
+  if (h->kind == LEB_DYN_MLP && h->mlp.tc) return mlp_autotune(h, T, cache_path, workspace, ws_bytes, stream);
+  if (h->kind != LEB_DYN_QUAD_CHAIN) return LEB_OK;  // the other kernels' launch shapes follow the problem
   if (!workspace || ws_bytes < pbh_ws_bytes(0)) return LEB_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   cudaDeviceProp prop;

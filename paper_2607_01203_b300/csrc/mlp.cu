@@ -495,9 +495,22 @@ __global__ void mlp_relax_kernel(int T, int width, int ld, int off, int act, con
     if (tw.winf) {
       const float v1s = __fmul_ru(v1[o], tw.v1scale);
       tw.winf[o] = __fmaf_ru(tw.c1, v1s, __fmul_ru(1.0000001f, v2[o]));
-      atomicAdd(tw.ucon + t * tw.ldu + layer, __fmul_ru(tw.usub * (1.f + tw.gam), v1s));
     }
   }
+}
+
+// The per-layer constant ucon = u_sub (1 + gamma_K) sum_j v1'_j of every timestep (tensor-core handles):
+// a warp per timestep, lane-strided sums then a fixed shuffle tree, all rounded up (an upper bound of the
+// exact sum, and the same bits on every run).
+__global__ void tc_ucon_kernel(int T, int width, int ld, int off, const float* v1, TcWeights tw, int layer) {
+  const int t = blockIdx.x;
+  if (t >= T) return;
+  const int lane = threadIdx.x;
+  float s = 0.f;
+  for (int j = lane; j < width; j += 32) s = __fadd_ru(s, __fmul_ru(v1[(long long)t * ld + off + j], tw.v1scale));
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) s = __fadd_ru(s, __shfl_xor_sync(0xffffffffu, s, d));
+  if (lane == 0) tw.ucon[(long long)t * tw.ldu + layer] = __fmul_ru(__fmul_ru(tw.usub, __fadd_ru(1.f, tw.gam)), s);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -927,6 +940,7 @@ leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_
       mlp_relax_kernel<<<blocks, 256, 0, s>>>(T, na.N, L.H, L.hoff[0], m.act, ws + L.lo, ws + L.hi, ws + L.zhat,
                                               ws + L.zrad, nullptr, ws + L.sL, ws + L.tL, ws + L.sU, ws + L.tU,
                                               ws + L.D, ws + L.abar, ws + L.loss, ws + L.v1, ws + L.v2, tcw(0), 0);
+      if (tc) tc_ucon_kernel<<<T, 32, 0, s>>>(T, na.N, L.H, L.hoff[0], ws + L.v1, tcw(0), 0);
       if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
       continue;
     }
@@ -949,6 +963,7 @@ leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_
     mlp_relax_kernel<<<blocks, 256, 0, s>>>(T, na.N, L.H, L.hoff[i], m.act, ws + L.lo, ws + L.hi, ws + L.zhat,
                                             ws + L.zrad, ws + L.bslack, ws + L.sL, ws + L.tL, ws + L.sU, ws + L.tU,
                                             ws + L.D, ws + L.abar, ws + L.loss, ws + L.v1, ws + L.v2, tcw(i), i);
+    if (tc) tc_ucon_kernel<<<T, 32, 0, s>>>(T, na.N, L.H, L.hoff[i], ws + L.v1, tcw(i), i);
     if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
   }
   return LEB_OK;

@@ -142,3 +142,46 @@ def test_adversarial_net_needs_the_inflation():
         deflated_violations[fmt] = n_defl
     print("sampled violations of the bounds without their inflation:", deflated_violations)
     assert deflated_violations["bf16"] > 0
+
+
+@pytest.mark.parametrize("fmt", ["fp16", "bf16"])
+def test_tc_plans_bit_identical_and_autotune(fmt):
+    """The tensor-core chain plans (job widths 256 and 128: how the final stage's and narrow hidden stages'
+    columns are grouped into MMA jobs) give the same bits, forward (bounds, A, B, stated slack) and adjoint,
+    on the benchmark's net (final stage 224 columns: a partial second job) and on a net of uneven widths
+    (hidden stages of 192 and 128 columns); leb_autotune times them and keeps one, with the same bits. (The
+    adjoint's atomic sums are compared up to their order.)"""
+    nets = [inputs.tanh_mlp(n_traj=4, N=50), inputs.tanh_mlp(seed=4104, n_traj=1, N=6, widths=(96, 192, 128, 40))]
+    for w in nets:
+        h = binding.mlp(w.Ws, w.bs, w.act, w.residual, fmt)
+        assert h.plan_count() == 2
+        x, u, r = _t(w.x_nom), _t(w.u_nom), _t(w.radii)
+        rng = np.random.default_rng(31)
+        glo, ghi = _t(rng.normal(size=(w.T, w.n_x))), _t(rng.normal(size=(w.T, w.n_x)))
+        ref = None
+        for p in range(2):
+            h.select_plan(p)
+            assert f"tc_job_cols={(256, 128)[p]}" in h.plan()
+            o = h.bounds(x, u, radii=r, want_eps=True)
+            gx, gu, gr, fl = h.bounds_backward(x, u, r, glo, ghi)
+            torch.cuda.synchronize()
+            assert int(o["flags"].item()) == 0 and int(fl.item()) == 0
+            got = [o["r_lo"].clone(), o["r_hi"].clone(), o["A"].clone(), o["B"].clone(), o["eps"].clone(),
+                   torch.cat([gx, gu, gr], 1)]
+            if ref is None:
+                ref = got
+            else:
+                for a_, b_ in zip(ref[:5], got[:5]):
+                    assert torch.equal(a_, b_), p
+                # the adjoint sums its per-neuron terms with atomic adds, whose order varies from run to run
+                # (also within one plan): equal up to that reordering
+                g0, g1 = ref[5].double(), got[5].double()
+                scale = g0.abs().max(dim=1, keepdim=True).values + g0.abs()
+                assert torch.all((g0 - g1).abs() <= 1e-5 * scale), p
+        h.select_plan(-1)
+        h.autotune(w.T, binding.SET_BOX)
+        assert "autotune=measured" in h.plan()
+        o = h.bounds(x, u, radii=r, want_eps=True)
+        torch.cuda.synchronize()
+        assert torch.equal(o["r_lo"], ref[0]) and torch.equal(o["r_hi"], ref[1])
+        print(fmt, w.Ws[0].shape, h.plan())
