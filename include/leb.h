@@ -166,14 +166,16 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
                       const leb_options* opt, void* workspace, size_t ws_bytes, int* dev_flags, void* stream);
 
 /* ---- adjoint of the bounds (differentiable LEBs, Sec. IV-D) ------------------------------------ */
-/* Box sets centred at the nominal only (set->center NULL), uniform batches. Given g_rlo = dL/dr_lo and
- * g_rhi = dL/dr_hi [T, n_x], writes g_x [T, n_x], g_u [T, n_u], g_radii [T, n] = dL/d(x~, u~, radii) of
- * the piecewise-smooth bound with every case fixed at the evaluation point: the relaxation case of each
- * neuron (MLP handles, Thms. 2-3) or the selected endpoint of each interval (quad-chain handles, Thm. 1).
- * All device pointers. */
-leb_status leb_bounds_backward(leb_handle h, int T, const float* x_nom, const float* u_nom, const leb_set* set,
-                               const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_radii,
-                               void* workspace, size_t ws_bytes, int* dev_flags, void* stream);
+/* Box sets centred at the nominal only (set->center NULL; other sets: LEB_ERR_UNSUPPORTED). batch: NULL or
+ * trajectories of any horizons (traj_offsets; each timestep's bound is independent, so the gradient is
+ * that of the timesteps in a row); chains of uneven length (traj_nquads) return LEB_ERR_UNSUPPORTED.
+ * Given g_rlo = dL/dr_lo and g_rhi = dL/dr_hi [T, n_x], writes g_x [T, n_x], g_u [T, n_u],
+ * g_radii [T, n] = dL/d(x~, u~, radii) of the piecewise-smooth bound with every case fixed at the
+ * evaluation point: the relaxation case of each neuron (MLP handles, Thms. 2-3) or the selected endpoint
+ * of each interval (quad-chain handles, Thm. 1). All device pointers. */
+leb_status leb_bounds_backward(leb_handle h, const leb_batch* batch, int T, const float* x_nom, const float* u_nom,
+                               const leb_set* set, const float* g_rlo, const float* g_rhi, float* g_x, float* g_u,
+                               float* g_radii, void* workspace, size_t ws_bytes, int* dev_flags, void* stream);
 /* The same adjoint from the forward pass's saved state: the workspace must hold the state of the last
  * leb_bounds call on this handle with the same T, x_nom, u_nom and set (box, centred at the nominal,
  * no leb_batch), with no other call on that workspace in between. FP32 MLP handles skip the recompute
@@ -183,10 +185,10 @@ leb_status leb_bounds_backward(leb_handle h, int T, const float* x_nom, const fl
  * recomputes the bounds without it); other kinds keep no state and behave as leb_bounds_backward. The
  * library cannot check the contract: a workspace that does not hold that state gives a wrong gradient
  * (no fault). */
-leb_status leb_bounds_backward_saved(leb_handle h, int T, const float* x_nom, const float* u_nom,
-                                     const leb_set* set, const float* g_rlo, const float* g_rhi, float* g_x,
-                                     float* g_u, float* g_radii, void* workspace, size_t ws_bytes, int* dev_flags,
-                                     void* stream);
+leb_status leb_bounds_backward_saved(leb_handle h, const leb_batch* batch, int T, const float* x_nom,
+                                     const float* u_nom, const leb_set* set, const float* g_rlo, const float* g_rhi,
+                                     float* g_x, float* g_u, float* g_radii, void* workspace, size_t ws_bytes,
+                                     int* dev_flags, void* stream);
 
 /* ---- nominal refinement by projected gradient descent (Sec. VI-A, Table II) ------------------------ */
 /* Minimises, per timestep, the summed width sum_l (r_hi - r_lo) of the Thm. 1 bound over nominal points in

@@ -88,7 +88,8 @@ def lib():
         L.leb_workspace_size.argtypes = [vp, i32, C.POINTER(sz)]
         L.leb_bounds.argtypes = [vp, C.POINTER(BatchDesc), i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp, vp,
                                  C.POINTER(Options), vp, sz, vp, vp]
-        L.leb_bounds_backward.argtypes = [vp, i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp, vp, vp, vp, sz, vp, vp]
+        L.leb_bounds_backward.argtypes = [vp, C.POINTER(BatchDesc), i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp, vp,
+                                          vp, vp, sz, vp, vp]
         L.leb_bounds_backward_saved.argtypes = L.leb_bounds_backward.argtypes
         L.leb_zonotope_map.argtypes = [vp, vp, C.c_longlong, C.c_float, vp, vp, vp]
         L.leb_autotune.argtypes = [vp, i32, i32, i32, C.c_char_p, vp, sz, vp]
@@ -307,9 +308,10 @@ class Handle:
                 o["B"] = o["B"].view(T, self.n_x, self.n_u)
         return o
 
-    def bounds_backward(self, x_nom, u_nom, radii, g_rlo, g_rhi, saved: bool = False):
+    def bounds_backward(self, x_nom, u_nom, radii, g_rlo, g_rhi, saved: bool = False, traj_offsets=None):
         """dL/d(x~, u~, radii) (leb_bounds_backward). saved: reuse the state the last ``bounds`` call of
-        this handle left in its workspace (same inputs, box set; leb_bounds_backward_saved)."""
+        this handle left in its workspace (same inputs, box set; leb_bounds_backward_saved). traj_offsets:
+        the batch's trajectories (optional; the gradient does not depend on them)."""
         dev = x_nom.device
         T = int(x_nom.shape[0])
         f32 = dict(device=dev, dtype=torch.float32)
@@ -320,7 +322,9 @@ class Handle:
         sd = self.set_desc(radii=radii)
         ws = self.workspace(T, dev)
         fn = lib().leb_bounds_backward_saved if saved else lib().leb_bounds_backward
-        check(fn(self.h, T, _ptr(x_nom), _ptr(u_nom), C.byref(sd), _ptr(g_rlo.contiguous()), _ptr(g_rhi.contiguous()),
+        bd = self.batch_desc(traj_offsets)
+        check(fn(self.h, None if bd is None else C.byref(bd), T, _ptr(x_nom), _ptr(u_nom), C.byref(sd),
+                 _ptr(g_rlo.contiguous()), _ptr(g_rhi.contiguous()),
                  _ptr(g_x), _ptr(g_u), _ptr(g_r), _ptr(ws), ws.numel(), _ptr(flags), _stream()), "leb_bounds_backward")
         return g_x, g_u, g_r, flags
 

@@ -358,11 +358,16 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
   return mlp_bounds(*h, T, x_nom, u_nom, set, r_lo, r_hi, A, B, opt, workspace, dev_flags, s);
 }
 
-static leb_status bounds_backward(leb_handle h, int T, const float* x_nom, const float* u_nom, const leb_set* set,
-                                  const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_radii,
-                                  void* workspace, size_t ws_bytes, int* dev_flags, void* stream, bool saved) {
+static leb_status bounds_backward(leb_handle h, const leb_batch* batch, int T, const float* x_nom,
+                                  const float* u_nom, const leb_set* set, const float* g_rlo, const float* g_rhi,
+                                  float* g_x, float* g_u, float* g_radii, void* workspace, size_t ws_bytes,
+                                  int* dev_flags, void* stream, bool saved) {
   if (!h || !set || T < 0 || !dev_flags) return LEB_ERR_INVALID_ARG;
   h->timer.phase = 1;
+  // every timestep's bound is independent of the others: a batch of trajectories of any horizons is the
+  // same problem as its timesteps in a row; chains of uneven length are not supported by the adjoint
+  if (batch && (batch->n_traj < 1 || !batch->traj_offsets)) return LEB_ERR_INVALID_ARG;
+  if (batch && batch->traj_nquads) return LEB_ERR_UNSUPPORTED;
   if (set->kind != LEB_SET_BOX || set->center) return LEB_ERR_UNSUPPORTED;
   if (T > 0 && (!x_nom || !u_nom || !set->radii || !g_rlo || !g_rhi || !g_x || !g_u || !g_radii))
     return LEB_ERR_INVALID_ARG;
@@ -386,18 +391,19 @@ static leb_status bounds_backward(leb_handle h, int T, const float* x_nom, const
                              saved);
 }
 
-leb_status leb_bounds_backward(leb_handle h, int T, const float* x_nom, const float* u_nom, const leb_set* set,
-                               const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_radii,
-                               void* workspace, size_t ws_bytes, int* dev_flags, void* stream) {
-  return bounds_backward(h, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, workspace, ws_bytes, dev_flags,
-                         stream, false);
+leb_status leb_bounds_backward(leb_handle h, const leb_batch* batch, int T, const float* x_nom, const float* u_nom,
+                               const leb_set* set, const float* g_rlo, const float* g_rhi, float* g_x, float* g_u,
+                               float* g_radii, void* workspace, size_t ws_bytes, int* dev_flags, void* stream) {
+  return bounds_backward(h, batch, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, workspace, ws_bytes,
+                         dev_flags, stream, false);
 }
 
-leb_status leb_bounds_backward_saved(leb_handle h, int T, const float* x_nom, const float* u_nom, const leb_set* set,
-                                     const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_radii,
-                                     void* workspace, size_t ws_bytes, int* dev_flags, void* stream) {
-  return bounds_backward(h, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, workspace, ws_bytes, dev_flags,
-                         stream, true);
+leb_status leb_bounds_backward_saved(leb_handle h, const leb_batch* batch, int T, const float* x_nom,
+                                     const float* u_nom, const leb_set* set, const float* g_rlo, const float* g_rhi,
+                                     float* g_x, float* g_u, float* g_radii, void* workspace, size_t ws_bytes,
+                                     int* dev_flags, void* stream) {
+  return bounds_backward(h, batch, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, workspace, ws_bytes,
+                         dev_flags, stream, true);
 }
 
 // ---- nominal refinement (projected gradient descent on the PBH width) ----------------------------

@@ -1,16 +1,17 @@
 """GPU adjoint of the CROWN bound against the oracle's gradient (itself pinned by central finite
 differences in FP64, tests/test_oracle_crown.py), through the C ABI and the autograd.Function.
 
-Tolerance: the kernels differentiate the same algorithm in FP32 (relaxation cases fixed at the evaluation
-point). The relaxation points themselves are the FP32 bounds, which sit about 1e-3 (relative to the
-interval widths; the forward's stated slack) away from the FP64 ones, and the slopes' derivatives move
-with them, so the gradient agrees to that order relative to the gradient's scale:
-    |g_gpu - g_oracle| <= rel max|g_oracle| + rel |g_oracle|,   rel = 5e-3
-per timestep, the max taken over the whole gradient (x~, u~ and radii together: the shifts move every
-component by amounts set by that scale, and the x~, u~ parts are often 10-400 times smaller than the
-radii part, so a per-part max would hold them to a far tighter relative bar than the argument gives). The tensor-core adjoint rounds its GEMM operands to the
-handle's format (unit roundoff u = 2^-11 FP16, 2^-8 BF16), which moves every chain product by about u
-relative; it is held to rel = 5e-3 + 2u.
+Tolerance, per timestep, relative to the gradient's scale (the max over x~, u~ and radii together: the
+x~, u~ parts are often 10-400 times smaller than the radii part, and every part moves by amounts set by
+that scale):
+    |g_gpu - g_oracle| <= rel max|g_oracle| + rel |g_oracle|.
+The kernels differentiate the same algorithm with every relaxation case fixed at the evaluation point;
+what differs is where the relaxation points sit. On the CUDA-core (FP32) path they are the FP32 bounds,
+within the path's stated slack of the FP64 ones (0.4 % of the widths on the benchmark net, measured by
+the benchmark's formats row), and the worst gradient error measured on B300 over these tests is 2.3e-4:
+rel = 1e-3. The tensor-core adjoint also rounds its GEMM operands to the handle's format (unit roundoff
+u = 2^-11 FP16, 2^-8 BF16), which moves the recomputed bounds and every chain product by a few u
+relative; measured worst 1.1e-3 (2.3 u) for FP16 and 7.5e-3 (1.9 u) for BF16: rel = 1e-3 + 4 u.
 """
 import numpy as np
 import pytest
@@ -27,7 +28,7 @@ def _t(x):
     return torch.as_tensor(np.ascontiguousarray(x)).cuda().float()
 
 
-def check(w, rows, seed=0, prec="fp32", rel=5e-3, report=False):
+def check(w, rows, seed=0, prec="fp32", rel=1e-3, report=False):
     h = binding.mlp(w.Ws, w.bs, w.act, w.residual, prec)
     rng = np.random.default_rng(seed)
     g_lo = rng.normal(size=(len(rows), w.n_x)).astype(np.float32)
@@ -75,7 +76,7 @@ U_OP = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8}
 def test_tensor_core_adjoint_small_nets(prec, act):
     w = inputs.tanh_mlp(seed=4102, n_traj=1, N=3, widths=(64, 128, 128, 32)) if act == "tanh" else \
         inputs.relu_mlp(seed=4103, N=3, widths=(64, 128, 128, 32))
-    check(w, [0, 1, 2], prec=prec, rel=5e-3 + 2 * U_OP[prec])
+    check(w, [0, 1, 2], prec=prec, rel=1e-3 + 4 * U_OP[prec])
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
@@ -83,14 +84,14 @@ def test_tensor_core_adjoint_workload_many_tiles_per_cta(prec):
     """100 timesteps of the full network: 400 output tiles and 800 tiles per hidden target, more than
     one per SM, so every CTA carries several tiles through the scratch and the barriers."""
     w = inputs.tanh_mlp(n_traj=2, N=50)
-    check(w, [0, 7, 33, 60, 99], prec=prec, rel=5e-3 + 2 * U_OP[prec])
+    check(w, [0, 7, 33, 60, 99], prec=prec, rel=1e-3 + 4 * U_OP[prec])
 
 
 def test_tensor_core_adjoint_uneven_widths():
     """Widths that leave partial M-tiles, a partial K-block of the inputs and a partial output tile (96
     inputs, 192 and 128 hidden, 40 outputs: 120 of the tile's 126 rows)."""
     w = inputs.tanh_mlp(seed=4104, n_traj=1, N=3, widths=(96, 192, 128, 40))
-    check(w, [0, 1, 2], prec="fp16", rel=5e-3 + 2 * U_OP["fp16"])
+    check(w, [0, 1, 2], prec="fp16", rel=1e-3 + 4 * U_OP["fp16"])
 
 
 def test_tensor_core_adjoint_matches_cuda_core_adjoint():
@@ -136,10 +137,39 @@ def test_adjoint_from_saved_forward_state():
     for i, t in enumerate(rows):
         ref = np.concatenate(crown.box_remainder_vjp(w.Ws, w.bs, w.act, w.x_nom[t], w.u_nom[t], w.radii[t], g_lo[i],
                                                      g_hi[i], w.residual))
-        assert np.all(np.abs(got[i] - ref) <= 5e-3 * (np.abs(ref).max() + np.abs(ref))), t
+        assert np.all(np.abs(got[i] - ref) <= 1e-3 * (np.abs(ref).max() + np.abs(ref))), t
     d = np.abs(got - recompute) / (np.abs(recompute).max(axis=1, keepdims=True) + np.abs(recompute))
     assert d.max() <= 1e-5
     h16 = binding.mlp(w.Ws, w.bs, w.act, w.residual, "fp16")
     h16.bounds(x, u, radii=r)
     with pytest.raises(binding.LebError):
         h16.bounds_backward(x, u, r, _t(g_lo), _t(g_hi), saved=True)
+
+
+def test_adjoint_takes_a_batch_of_ragged_trajectories():
+    """leb_bounds_backward with a leb_batch of trajectories of uneven horizon gives the gradient of the
+    same timesteps in a row (every timestep's bound is independent); a batch of uneven chain lengths is
+    refused, and so is a malformed one."""
+    w = inputs.tanh_mlp(seed=4105, n_traj=1, N=9, widths=(64, 128, 128, 32))
+    h = binding.mlp(w.Ws, w.bs, w.act, w.residual, "fp16")
+    rng = np.random.default_rng(8)
+    g_lo, g_hi = _t(rng.normal(size=(w.T, w.n_x))), _t(rng.normal(size=(w.T, w.n_x)))
+    x, u, r = _t(w.x_nom), _t(w.u_nom), _t(w.radii)
+    plain = torch.cat(h.bounds_backward(x, u, r, g_lo, g_hi)[:3], 1)
+    offs = torch.tensor([0, 2, 7, 9], dtype=torch.int32, device="cuda")
+    gx, gu, gr, fl = h.bounds_backward(x, u, r, g_lo, g_hi, traj_offsets=offs)
+    torch.cuda.synchronize()
+    assert int(fl.item()) == 0
+    got = torch.cat([gx, gu, gr], 1)
+    scale = plain.abs().max(dim=1, keepdim=True).values + plain.abs()
+    assert torch.all((got - plain).abs() <= 1e-5 * scale)   # the adjoint's atomic sums, up to their order
+    lib = binding.lib()
+    bd = binding.BatchDesc(3, offs.data_ptr(), offs.data_ptr())
+    sd = h.set_desc(radii=r)
+    ws = h.workspace(w.T)
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    args = (w.T, x.data_ptr(), u.data_ptr(), binding.C.byref(sd), g_lo.data_ptr(), g_hi.data_ptr(), gx.data_ptr(),
+            gu.data_ptr(), gr.data_ptr(), ws.data_ptr(), ws.numel(), flags.data_ptr(), None)
+    assert lib.leb_bounds_backward(h.h, binding.C.byref(bd), *args) == binding.LEB_ERR_UNSUPPORTED
+    bad = binding.BatchDesc(0, offs.data_ptr(), None)
+    assert lib.leb_bounds_backward(h.h, binding.C.byref(bad), *args) == binding.LEB_ERR_INVALID_ARG
