@@ -363,6 +363,7 @@ class CrownForm(Form):
         torch.cuda.synchronize()
         self.ibp = self._ibp_variant(torch, binding)
         self.formats = self._formats(torch, binding)
+        self.zono = self._zono_exact(torch, binding, dev)
         self.desc = f"residual tanh MLP 224-512-512-512-168, {self.T // 50} traj x N=50, box sets, FP16 TC"
 
     def _formats(self, torch, binding):
@@ -388,6 +389,39 @@ class CrownForm(Form):
             d = res.setdefault(fmt, {})
             d["width_vs_fp32_path"] = round(float(wsum / w32), 4)
             d["stated_slack_share_of_width"] = round(float((o["eps"].double()).sum() / wsum), 4)
+        return res
+
+    def _zono_exact(self, torch, binding, dev, n_gen=64, n_fp32=100):
+        """Once at start-up (untimed in the step): the same batch over zonotope tube sets (64 generators of
+        N(0, (0.0375 rho)^2) entries per input, centre off the nominal by U[-0.2, 0.2] rho; rho the box
+        radii) concretised exactly on the FP16 tensor-core chains (LEB_SET_ZONO_EXACT), against their
+        interval hull on the same chains, and the exact concretisation of the FP32 CUDA-core chains on the
+        first 100 timesteps: time per call and summed widths."""
+        w = self.w
+        rng = np.random.default_rng(4800)
+        G = torch.as_tensor((rng.normal(size=(w.T, w.n, n_gen)) * (0.3 / 8.0) * w.radii[:, :, None])
+                            .astype(np.float32)).to(dev)
+        c = torch.as_tensor((w.nominal() + 0.2 * w.radii * rng.uniform(-1, 1, size=(w.T, w.n)))
+                            .astype(np.float32)).to(dev)
+        h = self.handle
+        oz = h.bounds(self.x, self.u, G=G, center=c, zono_exact=True)
+        ms_z = timed_loop(torch, lambda: h.bounds(self.x, self.u, G=G, center=c, zono_exact=True, out=oz), 3)
+        oh = h.bounds(self.x, self.u, G=G, center=c)
+        ms_h = timed_loop(torch, lambda: h.bounds(self.x, self.u, G=G, center=c, out=oh), 3)
+        k = min(n_fp32, w.T)
+        h32 = binding.mlp(w.Ws, w.bs, w.act, w.residual, "fp32")
+        sl = slice(0, k)
+        o32 = h32.bounds(self.x[sl], self.u[sl], G=G[sl].contiguous(), center=c[sl].contiguous(), zono_exact=True)
+        ms_32 = timed_loop(torch, lambda: h32.bounds(self.x[sl], self.u[sl], G=G[sl].contiguous(),
+                                                     center=c[sl].contiguous(), zono_exact=True, out=o32), 1)
+        torch.cuda.synchronize()
+        flags = int(oz["flags"].item())
+        wsum = lambda o, s=slice(None): float((o["r_hi"][s] - o["r_lo"][s]).double().sum())
+        res = {"n_gen": n_gen, "tc_fp16_exact_ms_per_call": round(ms_z, 3), "tc_fp16_hull_ms_per_call": round(ms_h, 3),
+               "exact_over_hull_width": round(wsum(oz) / wsum(oh), 4),
+               "fp32_exact_ms_per_timestep": round(ms_32 / k, 4),
+               "tc_fp16_over_fp32_exact_width_first_100": round(wsum(oz, sl) / wsum(o32), 4), "flags": flags}
+        del h32, o32, oz, oh, G, c
         return res
 
     def _ibp_variant(self, torch, binding):
@@ -1249,6 +1283,7 @@ def main():
         if f.name == "crown":
             d["ibp_intermediate_variant"] = f.ibp
             d["formats"] = f.formats
+            d["zonotope_exact"] = f.zono
             d["plan"] = f.plan
         if f.name == "pbh":
             d["ragged_horizons_graph"] = f.ragged

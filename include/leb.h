@@ -64,7 +64,9 @@ typedef enum { LEB_ACT_RELU = 0, LEB_ACT_TANH = 1 } leb_act;
    tensor cores with FP32 accumulation and a rigorous rounding inflation */
 typedef enum { LEB_PREC_FP32 = 0, LEB_PREC_FP16 = 1, LEB_PREC_BF16 = 2 } leb_prec;
 /* LEB_SET_ZONO_EXACT: a zonotope whose CROWN bounds (every layer and Thm. 3) are concretised over the
-   zonotope itself, Lambda c -+ ||Lambda G||_{1,r}, instead of its interval hull (FP32 MLP handles only) */
+   zonotope itself, Lambda c -+ ||Lambda G||_{1,r}, instead of its interval hull (MLP handles; FP16/BF16
+   handles take it on the tensor cores as one more GEMM with the generators, n_gen <= 510, and need the
+   workspace leb_workspace_size_set gives) */
 typedef enum { LEB_SET_BOX = 0, LEB_SET_ZONO = 1, LEB_SET_ZONO_EXACT = 2 } leb_set_kind;
 /* bounds of the MLP's hidden layers 2..: CROWN back-substitution (Thm. 2 for every layer) or interval
    bound propagation (the cheaper, looser variant); the output layer is always back-substituted */
@@ -154,6 +156,11 @@ leb_status leb_destroy(leb_handle h);
 leb_status leb_dims(leb_handle h, int* n_x, int* n_u);
 /* Bytes of device workspace leb_bounds and leb_bounds_backward need for up to T_max timesteps. */
 leb_status leb_workspace_size(leb_handle h, int T_max, size_t* bytes);
+/* The same for a set of the given kind: LEB_SET_ZONO_EXACT on a tensor-core MLP handle also holds the
+ * transposed generator blocks of every timestep (2 bytes x round_up(n_gen + 2, 16) x n per timestep);
+ * every other combination returns leb_workspace_size. LEB_ERR_INVALID_ARG for an unknown kind or
+ * n_gen < 0. */
+leb_status leb_workspace_size_set(leb_handle h, int T_max, leb_set_kind set_kind, int n_gen, size_t* bytes);
 
 /* ---- forward bounds (Thm. 1 / Thm. 2-3) -------------------------------------------------------- */
 /* x_nom [T, n_x], u_nom [T, n_u]: nominal points (device). r_lo, r_hi [T, n_x] (device, written).

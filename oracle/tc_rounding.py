@@ -201,3 +201,106 @@ def emulate_jacobian(Ws, bs, act: str, nominal, fmt: str):
             op = (Lam.to(torch.float32) * crown.act_deriv(act, zs[k]).to(torch.float32)).to(F64)
             Lam = emulate_stage(op, Ws_t[k], fmt)
     return Lam.numpy()
+
+
+# ------------------------------------------------------------------------------------------------
+# Zonotope sets concretised exactly (Sec. IV-C sets, Eq. 18a) with a reduced-precision last product
+# ------------------------------------------------------------------------------------------------
+# Over the zonotope Z = cd (1 - xi_0) + G xi (the tube set hulled with the nominal, Delta = alpha - a,
+# cd = (c - a) / 2, |xi|_inf <= 1) the minimum of M Delta is V = v_0 - sum_{g >= 1} |v_g| with
+# v = M [cd | G | -cd]. A kernel that forms v with M and the block rounded to the format (cd first
+# rounded to FP32 from fl(c - a) / 2) and FP32 sums of K products errs on V by at most, per row,
+#   sum_i |M_i| (cz h_i + wadd) + zc1 sum_i h_i + zc2
+# with h_i = 2 |cd_i| + sum_g |G_ig| (the hull's half-width) and
+#   cz = (gamma_K (1 + u) + u)(1 + u) + u + 2^-23,  wadd = (Pp + 2) u_sub (2 + gamma_K),
+#   zc1 = u_sub (1 + u)(1 + gamma_K),                 zc2 = 2 n (Pp + 2) u_sub^2,
+# Pp = n_gen + 2 rounded up to 16 (the product's columns) and K = n rounded up to 64. Derivation: with
+# M~ = fl(M), B~ = fl(B), |M~ - M| <= u |M| + u_sub, |B~ - B| <= u |B| + u_sub entrywise, the error of
+# every column is |M~ B~ - M B| + gamma_K |M~| |B~| <= (|M~ - M| |B~| + |M| |B~ - B|) + gamma_K |M~||B~|;
+# summed over the columns with sum_g |B_ig| <= h_i (1 + 2^-24) + 2^-149 (cd's FP32 rounding, which also
+# moves V itself by at most |M| (2^-24 h + 2^-149)) this gives the terms above.
+
+
+def zono_stage_constants(n: int, n_gen: int, fmt: str):
+    """(cz, wadd, zc1, zc2, Pp) of the zonotope stage for n inputs and n_gen generators."""
+    u, u_sub = FORMATS[fmt]
+    K = 64 * ((n + 63) // 64)
+    g = gamma(K)
+    Pp = 16 * ((n_gen + 2 + 15) // 16)
+    cz = (g * (1 + u) + u) * (1 + u) + u + 2.0 ** -23
+    wadd = (Pp + 2) * u_sub * (2 + g)
+    zc1 = u_sub * (1 + u) * (1 + g)
+    zc2 = 2.0 * n * (Pp + 2) * u_sub ** 2
+    return cz, wadd, zc1, zc2, Pp
+
+
+def zono_stage_allowance(M: torch.Tensor, h: torch.Tensor, n_gen: int, fmt: str) -> torch.Tensor:
+    """Per-row bound on |computed V - exact V| (M: [R, n] FP64 rows, h: [n] hull half-widths)."""
+    cz, wadd, zc1, zc2, _ = zono_stage_constants(M.shape[1], n_gen, fmt)
+    return M.abs() @ (cz * h + wadd) + zc1 * float(h.sum()) + zc2
+
+
+def zono_min(M: torch.Tensor, cd: torch.Tensor, G: torch.Tensor) -> torch.Tensor:
+    """Exact min over Z of M Delta, FP64: M cd - |M cd| - sum_g |M G_g|."""
+    v0 = M @ cd
+    return v0 - v0.abs() - (M @ G).abs().sum(dim=1)
+
+
+def emulate_zono_stage(M: torch.Tensor, c: torch.Tensor, a: torch.Tensor, G: torch.Tensor, fmt: str):
+    """V computed the way a reduced-precision kernel computes it: cd = fl32(c - a) / 2, the block
+    [cd | G | -cd] and M rounded to the format, the products summed in FP32 (torch's FP32 matmul)."""
+    cd = ((c.to(torch.float32) - a.to(torch.float32)) * 0.5).to(F64)
+    block = torch.cat([cd[:, None], G, -cd[:, None]], dim=1)
+    v = (round_to(M, fmt).to(torch.float32) @ round_to(block, fmt).to(torch.float32)).to(F64)
+    return v[:, 0] - v[:, 1:].abs().sum(dim=1)
+
+
+def zono_remainder_envelope(Ws, bs, act: str, x_nom, u_nom, G, center, fmt: str, k: float,
+                            residual: bool = True):
+    """Thm. 3 over the zonotope tube set concretised exactly (``crown.zono_remainder``) with the
+    reduced-precision inflation applied k times: every hidden layer's bounds (the first one included,
+    which now also comes out of a rounded product) widened by k times their chain inflation plus the
+    zonotope stage's allowance, and the output bounds moved by k times theirs. Returns FP64 numpy
+    (r_lo, r_hi, infl_lo, infl_hi), infl_* the output rows' total inflation (one times)."""
+    Ws_t = [crown.to_t(W) for W in Ws]
+    bs_t = [crown.to_t(b) for b in bs]
+    a = torch.cat([crown.to_t(x_nom), crown.to_t(u_nom)])
+    G0 = crown.to_t(G)
+    c0 = a if center is None else crown.to_t(center)
+    n_gen = G0.shape[1]
+    with torch.no_grad():
+        c, Gh = crown.zono_hull_nominal(a, c0, G0)
+        h = Gh.abs().sum(dim=1) + (c - a).abs()                 # the hull's half-width around a
+        allow = lambda M: zono_stage_allowance(M, h, n_gen, fmt)
+        _, z_nom = crown.forward(Ws_t, bs_t, act, a)
+        L = len(Ws_t)
+        weights = [stage_weights(Ws_t[0], h, fmt)]
+        spread = (Ws_t[0] @ Gh).abs().sum(dim=1)
+        a0 = allow(Ws_t[0])
+        l1 = Ws_t[0] @ c - spread + bs_t[0] - k * a0
+        u1 = Ws_t[0] @ c + spread + bs_t[0] + k * a0
+        bounds = [(l1, u1)]
+        relaxations = [crown.relax(act, l1, u1)]
+        for layer in range(1, L - 1):
+            weights.append(stage_weights(Ws_t[layer], _abar(act, *bounds[-1], z_nom[layer - 1]), fmt))
+            Ll, _, li = crown._back_substitute(Ws_t, bs_t, relaxations, layer, False, c, None, Gh)
+            Lu, _, ui = crown._back_substitute(Ws_t, bs_t, relaxations, layer, True, c, None, Gh)
+            _, il = _chain(Ws_t, relaxations, layer, False, weights)
+            _, iu = _chain(Ws_t, relaxations, layer, True, weights)
+            li, ui = li - k * (il + allow(Ll)), ui + k * (iu + allow(Lu))
+            bounds.append((li, ui))
+            relaxations.append(crown.relax(act, li, ui))
+        weights.append(None)
+        W_lo, b_lo, _ = crown._back_substitute(Ws_t, bs_t, relaxations, L - 1, False, c, None, Gh)
+        W_hi, b_hi, _ = crown._back_substitute(Ws_t, bs_t, relaxations, L - 1, True, c, None, Gh)
+        _, il = _chain(Ws_t, relaxations, L - 1, False, weights)
+        _, iu = _chain(Ws_t, relaxations, L - 1, True, weights)
+        J = crown.jacobian(Ws_t, bs_t, act, a)
+        f_nom, _ = crown.forward(Ws_t, bs_t, act, a)
+        const = J @ a - f_nom           # the residual identity cancels in W - J
+        M_lo, M_hi = W_lo - J, W_hi - J
+        il = il + allow(M_lo)
+        iu = iu + allow(M_hi)
+        r_lo = M_lo @ c - (M_lo @ Gh).abs().sum(dim=1) + const + b_lo - k * il
+        r_hi = M_hi @ c + (M_hi @ Gh).abs().sum(dim=1) + const + b_hi + k * iu
+    return r_lo.numpy(), r_hi.numpy(), il.numpy(), iu.numpy()

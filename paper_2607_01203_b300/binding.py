@@ -54,7 +54,8 @@ class Options(C.Structure):
 _lib = None
 
 EXPORTS = [
-    "leb_create", "leb_destroy", "leb_dims", "leb_workspace_size", "leb_bounds", "leb_bounds_backward",
+    "leb_create", "leb_destroy", "leb_dims", "leb_workspace_size", "leb_workspace_size_set", "leb_bounds",
+    "leb_bounds_backward",
     "leb_zonotope_map", "leb_autotune", "leb_plan_string", "leb_plan_select", "leb_plan_count", "leb_set_path_order", "leb_set_partition",
     "leb_graph_capture", "leb_graph_launch", "leb_graph_destroy", "leb_proposer_create", "leb_proposer_destroy",
     "leb_proposer_set_norm", "leb_proposer_forward", "leb_proposer_train_step", "leb_proposer_workspace_size",
@@ -86,6 +87,7 @@ def lib():
         L.leb_destroy.argtypes = [vp]
         L.leb_dims.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         L.leb_workspace_size.argtypes = [vp, i32, C.POINTER(sz)]
+        L.leb_workspace_size_set.argtypes = [vp, i32, i32, i32, C.POINTER(sz)]
         L.leb_bounds.argtypes = [vp, C.POINTER(BatchDesc), i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp, vp,
                                  C.POINTER(Options), vp, sz, vp, vp]
         L.leb_bounds_backward.argtypes = [vp, C.POINTER(BatchDesc), i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp, vp,
@@ -179,13 +181,14 @@ class Handle:
         except Exception:
             pass
 
-    def workspace_bytes(self, T: int) -> int:
+    def workspace_bytes(self, T: int, set_kind: int = SET_BOX, n_gen: int = 0) -> int:
         b = C.c_size_t()
-        check(lib().leb_workspace_size(self.h, int(T), C.byref(b)), "leb_workspace_size")
+        check(lib().leb_workspace_size_set(self.h, int(T), int(set_kind), int(n_gen), C.byref(b)),
+              "leb_workspace_size_set")
         return b.value
 
-    def workspace(self, T: int, device="cuda", extra: int = 0):
-        need = max(self.workspace_bytes(max(int(T), 1) + extra), 256)
+    def workspace(self, T: int, device="cuda", extra: int = 0, set_kind: int = SET_BOX, n_gen: int = 0):
+        need = max(self.workspace_bytes(max(int(T), 1) + extra, set_kind, n_gen), 256)
         if self._ws is None or self._ws.numel() < need or self._ws.device != torch.device(device):
             self._ws = torch.empty(need, dtype=torch.uint8, device=device)
         return self._ws
@@ -292,7 +295,7 @@ class Handle:
         else:
             sd = self.set_desc(radii, G, center, zono_exact)
         bd = self.batch_desc(traj_offsets, traj_nquads)
-        ws = self.workspace(max(T, 1), dev, extra=0 if bd is None else bd.n_traj)
+        ws = self.workspace(max(T, 1), dev, extra=0 if bd is None else bd.n_traj, set_kind=sd.kind, n_gen=sd.n_gen)
         check(lib().leb_bounds(self.h, None if bd is None else C.byref(bd), T, _ptr(x_nom), _ptr(u_nom), C.byref(sd),
                                _ptr(o["r_lo"]), _ptr(o["r_hi"]), _ptr(o["A"]), _ptr(o["B"]),
                                None if opt is None else C.byref(opt), _ptr(ws), ws.numel(), _ptr(o["flags"]),

@@ -24,6 +24,18 @@
 // per TMEM lane quarter, each on one 32-column half of every 64-column block, the next block's TMEM
 // load in flight while a block is processed; the per-neuron vectors of the next pass arrive by cp.async).
 //
+// Zonotope sets (ZONO instances, LEB_SET_ZONO_EXACT): every bound is concretised over the zonotope
+// Delta = cd (1 - xi_p) + G xi (the set widened by the segment to the nominal, cd = (c - alpha~) / 2)
+// instead of its interval hull: after the last weight stage the epilogue writes the row M over the inputs
+// (Lambda_{-1}; for output rows Lambda - J with the returned J, as an interval) as one more operand, and
+// a last MMA stage multiplies it by the timestep's generator block [cd | G | -cd]; its epilogue takes the
+// centre column minus the l1 norm of the generator columns (min over xi). The extra product's rounding
+// (operand and generators rounded to the format, FP32 sums) moves that value by at most
+// sum_i |M_i| wz_i + zcon, wz_i = cz h_i + Pp u_sub (2 + gamma_n), cz = (gamma_n (1 + u) + u)(1 + u) + u
+// + 2^-23, h_i the hull half-width (which bounds sum_g |generator entries| of input i; the 2^-23 covers the
+// FP32 rounding of cd), and the interval width of M_i adds rad_i h_i; all of it is subtracted (rounded
+// down) with the rest of the bound. The hidden layer-1 bounds (target 0) take the same last stage with
+// the operand W_0's rows.
 // Rigour of the reduced-precision GEMM (per stage, per row): with A~ the rounded operand, W~ the rounded
 // weights and the FP32 accumulation error bounded by gamma_K |A~| |W~| (u = 2^-23, i.e. without assuming
 // round-to-nearest accumulation), the computed Lambda' differs from the exact (Lambda o s) W_k by at most
@@ -79,6 +91,13 @@ struct TcArgs {
   float gamma_pad;
   int tight;                     // 1: no rounding inflation (the adjoint's recompute; not a sound bound)
   int* flags;
+  // zonotope sets concretised exactly (ZONO instances): per timestep the generator block
+  // [cd | G | -cd | 0] transposed, [T * Pp rows, widths[0] cols] in the operand format (gmap, box {64,
+  // zbrows}); zcols = n_gen + 2 of the Pp columns are used; wz [T, n] the per-input weight of the extra
+  // product's rounding, zcon [T] its subnormal constant (see the zonotope stage below)
+  CUtensorMap gmap;
+  int Pp, zcols, zbrows;
+  const float *wz, *zcon;
 };
 
 // Store 32 operand values (row r, columns j0..j0+31, packed pairs) into the 128-byte-swizzled K-major tile
@@ -167,7 +186,7 @@ __device__ __forceinline__ void tmem_wait32(float v[32]) {
   tmem_regs_fence16(v + 16);
 }
 
-template <bool OUT, bool EPS, int FMT>
+template <bool OUT, bool EPS, int FMT, bool ZONO>
 __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_constant__ TcArgs a) {
   extern __shared__ uint8_t sraw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sraw) + 1023) & ~uintptr_t(1023));
@@ -224,17 +243,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
   // A hidden stage (k >= 1) writes the next operand over blocks the stage's last job still reads, so a
   // job's epilogue can finish only after that last job: with two TMEM halves a hidden stage has at most
   // two jobs (one if N <= jw, else two split at a multiple of 64 covering whole operand blocks). The final
-  // stage (k = 0) writes no operand: jobs of jw columns, [h jw, min(N, (h + 1) jw)).
+  // stage (k = 0) writes no operand: jobs of jw columns, [h jw, min(N, (h + 1) jw)). ZONO instances run
+  // with jw = 256, so that their stage 0, which writes the zonotope stage's operand, has at most two jobs
+  // too, and add the zonotope stage (k = -1): N = Pp generator columns in jobs of 256, K = nzb blocks.
   const int jw = a.jw;
+  const int nzb = (a.widths[0] + 63) / 64;
+  constexpr int klast = ZONO ? -1 : 0;
+  auto stage_nK = [&](int k) -> int { return k < 0 ? nzb : a.widths[k + 1] / 64; };
   auto njobs = [&](int k) -> int {
+    if (k < 0) return (a.Pp + 255) / 256;
     const int N = a.widths[k];
     return k == 0 ? (N + jw - 1) / jw : (N > jw ? 2 : 1);
   };
   auto job_c0 = [&](int k, int h) -> int {
+    if (k < 0) return 256 * h;
     const int N = a.widths[k];
     return k == 0 ? h * jw : (h ? 64 * ((N + 127) / 128) : 0);
   };
   auto job_nc = [&](int k, int h) -> int {
+    if (k < 0) return min(256, a.Pp - 256 * h);
     const int N = a.widths[k];
     if (k == 0) return min(jw, N - h * jw);
     if (N <= jw) return N;
@@ -246,19 +273,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
       for (int k = 0; k < target; ++k) tma_prefetch_desc(&a.tmap[k]);
+      if (ZONO) tma_prefetch_desc(&a.gmap);
       uint32_t kb = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
-        for (int k = target - 1; k >= 0 && ok; --k) {
-          const int nK = a.widths[k + 1] / 64, nh = njobs(k);
+        const int t = item / a.tiles_per_t;
+        for (int k = target - 1; k >= klast && ok; --k) {
+          const int nK = stage_nK(k), nh = njobs(k);
+          // B tiles: W_k^T rows, or the timestep's generator block (rows t Pp + column)
+          const CUtensorMap* map = k < 0 ? &a.gmap : &a.tmap[k];
+          const uint32_t rows = k < 0 ? (uint32_t)a.zbrows : (uint32_t)a.brows[k];
           for (int h = 0; h < nh && ok; ++h) {
-            const int c0 = job_c0(k, h);
+            const int c0 = job_c0(k, h) + (k < 0 ? t * a.Pp : 0);
             for (int kc = 0; kc < nK && ok; ++kc, ++kb) {
               const int s = (int)(kb % kTcNSB);
               if (kb >= (uint32_t)kTcNSB && !mbar_wait(&b_empty[s], ((kb / kTcNSB) - 1) & 1u)) { ok = false; break; }
               if (*(volatile int*)&s_abort) { ok = false; break; }
-              mbar_arrive_expect_tx(&b_full[s], (uint32_t)a.brows[k] * 128u);
-              tma_load_2d(Bsm + (size_t)s * kTcBStage, &a.tmap[k], kc * 64, c0, &b_full[s]);
+              mbar_arrive_expect_tx(&b_full[s], rows * 128u);
+              tma_load_2d(Bsm + (size_t)s * kTcBStage, map, kc * 64, c0, &b_full[s]);
             }
           }
         }
@@ -279,8 +311,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       uint32_t kb = 0, jc = 0, rpar = 0, fpar = 0, used = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
-        for (int k = target - 1; k >= 0 && ok; --k) {
-          const int nK = a.widths[k + 1] / 64, nh = njobs(k);
+        for (int k = target - 1; k >= klast && ok; --k) {
+          const int nK = stage_nK(k), nh = njobs(k);
           for (int h = 0; h < nh && ok; ++h, ++jc) {
             const int nc = job_nc(k, h);
             const uint32_t hb = jc & 1u;
@@ -525,72 +557,112 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       return true;
     };
 
+    // Output rows (OUT): the row's coefficient on input m is M_m = Lambda_m - J_m (lower rows) or
+    // Lambda_m + J_m (upper rows, carried negated), with J the tile's Jacobian row of the same state.
+    struct XRow {
+      int src;        // lane holding the Jacobian row's values
+      bool importer;  // the Jacobian row sits in the next lane quarter: read it from the exchange buffer
+      bool exporter;  // Jacobian row whose bound rows sit in the previous lane quarter
+      int dcol;       // diagonal column of the state (residual nets: A = I + J there), else -1
+    };
+    auto xrow = [&](const RowInfo& ri) -> XRow {
+      XRow x;
+      const int role = ri.isJ ? 2 : (ri.neg ? 1 : 0);
+      x.src = lane + 2 - role;
+      x.importer = OUT && ri.bound && x.src >= 32;
+      x.exporter = OUT && ri.isJ && lane < 2;
+      x.dcol = (OUT && a.residual && ri.bound) ? ri.idx : -1;
+      return x;
+    };
+    // A and B rows start on 16-byte boundaries when n_x and n_u are multiples of 4 (A, B, the workspace
+    // and every device buffer the binding allocates are 16-byte aligned)
+    const bool vec_ab = (n_x % 4 == 0) && ((n - n_x) % 4 == 0) &&
+                        ((reinterpret_cast<uintptr_t>(a.A) | reinterpret_cast<uintptr_t>(a.B)) & 15u) == 0;
+    // Jacobian rows of a 32-column chunk of the last product -> A (residual: + I) and B; the Jacobian
+    // rows of the lower/upper rows 30, 31 and 63 of a 126-row tile (next lane quarter) go through the
+    // exchange buffer xb (the others are read by shuffle)
+    auto jx_chunk = [&](int t, const RowInfo& ri, const XRow& xr, const float lam[32], int j0,
+                        const float*& xb) -> bool {
+      xb = xch;
+      if (!OUT) return true;
+      float* xw = xch + ((cq * 2 + (int)(xph & 1u)) * 2) * 32;
+      xb = xw;
+      if (xr.exporter)
+#pragma unroll
+        for (int e = 0; e < 32; e += 4)
+          *reinterpret_cast<float4*>(xw + (q - 1) * 32 + e) = make_float4(lam[e], lam[e + 1], lam[e + 2], lam[e + 3]);
+      if (ri.isJ && ri.valid) {
+        const int l = ri.idx;
+        float* Ar = a.A ? a.A + ((long long)t * n_x + l) * n_x : nullptr;
+        float* Br = a.B ? a.B + ((long long)t * n_x + l) * (n - n_x) : nullptr;
+        if (vec_ab) {
+#pragma unroll
+          for (int e = 0; e < 32; e += 4) {
+            const int m = j0 + e;
+            float4 v = make_float4(lam[e], lam[e + 1], lam[e + 2], lam[e + 3]);
+            if (m < n_x) {
+              if (a.residual && (unsigned)(l - m) < 4u) {
+                const int d = l - m;
+                v.x += d == 0 ? 1.f : 0.f;
+                v.y += d == 1 ? 1.f : 0.f;
+                v.z += d == 2 ? 1.f : 0.f;
+                v.w += d == 3 ? 1.f : 0.f;
+              }
+              if (Ar) *reinterpret_cast<float4*>(Ar + m) = v;
+            } else if (Br) {
+              *reinterpret_cast<float4*>(Br + (m - n_x)) = v;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const int m = j0 + e;
+            if (m < n_x) {
+              if (Ar) Ar[m] = (a.residual && m == l) ? 1.f + lam[e] : lam[e];
+            } else if (Br) {
+              Br[m - n_x] = lam[e];
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&xbar[cq]);
+      if (!mbar_wait_warp(&xbar[cq], xph & 1u)) return false;
+      ++xph;
+      return true;
+    };
+    // the interval [mlo, mhi] of M on column j0 + e (hidden targets: the point lam)
+    auto m_ivl = [&](const RowInfo& ri, const XRow& xr, const float lam[32], const float* xb, int e, int j0,
+                     float& mlo, float& mhi) {
+      mlo = lam[e];
+      mhi = lam[e];
+      if (OUT) {
+        float jv = __shfl_sync(0xffffffffu, lam[e], xr.src & 31);
+        if (xr.importer) jv = xb[q * 32 + e];
+        float jl = jv, jh = jv;
+        if (j0 + e == xr.dcol) {
+          // the returned A has 1 + J on the diagonal: J_eff = fl(1 + J) - 1, enclosed
+          const float aret = 1.f + jv;
+          jl = __fsub_rd(aret, 1.f);
+          jh = __fsub_ru(aret, 1.f);
+        }
+        // lower rows: M = lam - J; upper rows (lam = -Lambda^U): M = lam + J
+        const float pl = ri.neg ? jl : -jh, ph = ri.neg ? jh : -jl;
+        mlo = __fadd_rd(lam[e], pl);
+        mhi = __fadd_ru(lam[e], ph);
+      }
+    };
+
     // one job of the final stage: concretise columns [c0, c0 + nc) over the displacement box
     auto conc_job = [&](int t, const RowInfo& ri, uint32_t hb, int c0, int nc, float2& sum) -> bool {
       if (!wait_acc(hb)) return false;
       const uint32_t tb = t_lane + hb * 256u;
       const float* dlo = a.dlo + (long long)t * n;
       const float* dhi = a.dhi + (long long)t * n;
-      // Jacobian rows: the lower/upper rows of a state whose Jacobian row sits in the next lane quarter
-      // (rows 30, 31 and 63 of a 126-row tile) read it from the exchange buffer, the others by shuffle
-      const int role = ri.isJ ? 2 : (ri.neg ? 1 : 0);
-      const int src = lane + 2 - role;
-      const bool importer = OUT && ri.bound && src >= 32;
-      const bool exporter = OUT && ri.isJ && lane < 2;
-      const int dcol = (OUT && a.residual && ri.bound) ? ri.idx : -1;   // diagonal column of the state
-      // A and B rows start on 16-byte boundaries when n_x and n_u are multiples of 4 (A, B, the workspace
-      // and every device buffer the binding allocates are 16-byte aligned)
-      const bool vec_ab = (n_x % 4 == 0) && ((n - n_x) % 4 == 0) &&
-                          ((reinterpret_cast<uintptr_t>(a.A) | reinterpret_cast<uintptr_t>(a.B)) & 15u) == 0;
+      const XRow xr = xrow(ri);
       auto chunk = [&](const float lam[32], int j0) -> bool {
-        const float* xb = xch;
-        if (OUT) {
-          float* xw = xch + ((cq * 2 + (int)(xph & 1u)) * 2) * 32;
-          xb = xw;
-          if (exporter)
-#pragma unroll
-            for (int e = 0; e < 32; e += 4)
-              *reinterpret_cast<float4*>(xw + (q - 1) * 32 + e) = make_float4(lam[e], lam[e + 1], lam[e + 2], lam[e + 3]);
-          if (ri.isJ && ri.valid) {
-            // this Jacobian row chunk -> A (residual: + I) and B, four columns per store where the rows allow
-            const int l = ri.idx;
-            float* Ar = a.A ? a.A + ((long long)t * n_x + l) * n_x : nullptr;
-            float* Br = a.B ? a.B + ((long long)t * n_x + l) * (n - n_x) : nullptr;
-            if (vec_ab) {
-#pragma unroll
-              for (int e = 0; e < 32; e += 4) {
-                const int m = j0 + e;
-                float4 v = make_float4(lam[e], lam[e + 1], lam[e + 2], lam[e + 3]);
-                if (m < n_x) {
-                  if (a.residual && (unsigned)(l - m) < 4u) {
-                    const int d = l - m;
-                    v.x += d == 0 ? 1.f : 0.f;
-                    v.y += d == 1 ? 1.f : 0.f;
-                    v.z += d == 2 ? 1.f : 0.f;
-                    v.w += d == 3 ? 1.f : 0.f;
-                  }
-                  if (Ar) *reinterpret_cast<float4*>(Ar + m) = v;
-                } else if (Br) {
-                  *reinterpret_cast<float4*>(Br + (m - n_x)) = v;
-                }
-              }
-            } else {
-#pragma unroll
-              for (int e = 0; e < 32; ++e) {
-                const int m = j0 + e;
-                if (m < n_x) {
-                  if (Ar) Ar[m] = (a.residual && m == l) ? 1.f + lam[e] : lam[e];
-                } else if (Br) {
-                  Br[m - n_x] = lam[e];
-                }
-              }
-            }
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&xbar[cq]);
-          if (!mbar_wait_warp(&xbar[cq], xph & 1u)) return false;
-          ++xph;
-        }
+        const float* xb;
+        if (!jx_chunk(t, ri, xr, lam, j0, xb)) return false;
 #pragma unroll
         for (int e4 = 0; e4 < 32; e4 += 4) {
           const float4 dl4 = __ldg(reinterpret_cast<const float4*>(dlo + j0 + e4));
@@ -599,22 +671,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int e = e4 + u;
-            float mlo = lam[e], mhi = lam[e];
-            if (OUT) {
-              float jv = __shfl_sync(0xffffffffu, lam[e], src & 31);
-              if (importer) jv = xb[q * 32 + e];
-              float jl = jv, jh = jv;
-              if (j0 + e == dcol) {
-                // the returned A has 1 + J on the diagonal: J_eff = fl(1 + J) - 1, enclosed
-                const float aret = 1.f + jv;
-                jl = __fsub_rd(aret, 1.f);
-                jh = __fsub_ru(aret, 1.f);
-              }
-              // lower rows: M = lam - J; upper rows (lam = -Lambda^U): M = lam + J
-              const float pl = ri.neg ? jl : -jh, ph = ri.neg ? jh : -jl;
-              mlo = __fadd_rd(lam[e], pl);
-              mhi = __fadd_ru(lam[e], ph);
-            }
+            float mlo, mhi;
+            m_ivl(ri, xr, lam, xb, e, j0, mlo, mhi);
             // [mlo, mhi] x [dlo, dhi] with dlo <= 0 <= dhi: min = min(mlo dhi, mhi dlo)
             const float term = fminf(__fmul_rd(mlo, dh[u]), __fmul_rd(mhi, dl[u]));
             if (u & 1) sum.y = __fadd_rd(sum.y, term);
@@ -636,6 +694,112 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
         tmem_ld32_async(tb + (uint32_t)(j0 - c0), L0);
         tmem_wait32(L0);
         if (!chunk(L0, j0)) return false;
+      }
+      release_acc(hb);
+      return true;
+    };
+
+    // ZONO: 32 columns j0.. of the zonotope stage's operand, the midpoint of M (bound rows; zero for the
+    // other rows and for columns past the inputs), packed; zacc.x += sum |mid_i| wz_i and zacc.y +=
+    // sum rad_i h_i (both rounded up; h_i = max(-dlo_i, dhi_i) bounds |Delta_i| over the set)
+    auto zop32 = [&](int t, const RowInfo& ri, const float mlo[32], const float mhi[32], int j0,
+                     uint32_t packed[16], float2& zacc) {
+      if (!ri.bound || j0 >= n) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) packed[e] = 0u;
+        return;
+      }
+      const float* wz = a.wz + (long long)t * n + j0;
+      const float* dlo = a.dlo + (long long)t * n + j0;
+      const float* dhi = a.dhi + (long long)t * n + j0;
+#pragma unroll
+      for (int e4 = 0; e4 < 32; e4 += 4) {
+        const float4 w4 = __ldg(reinterpret_cast<const float4*>(wz + e4));
+        const float4 dl4 = __ldg(reinterpret_cast<const float4*>(dlo + e4));
+        const float4 dh4 = __ldg(reinterpret_cast<const float4*>(dhi + e4));
+        const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+        const float hv[4] = {fmaxf(-dl4.x, dh4.x), fmaxf(-dl4.y, dh4.y), fmaxf(-dl4.z, dh4.z), fmaxf(-dl4.w, dh4.w)};
+        float mid[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = e4 + u;
+          mid[u] = OUT ? 0.5f * mlo[e] + 0.5f * mhi[e] : mlo[e];
+          zacc.x = __fmaf_ru(fabsf(mid[u]), wv[u], zacc.x);
+          if (OUT) {
+            const float rad = fmaxf(__fsub_ru(mhi[e], mid[u]), __fsub_ru(mid[u], mlo[e]));
+            zacc.y = __fmaf_ru(rad, hv[u], zacc.y);
+          }
+        }
+        packed[e4 >> 1] = pack2<FMT>(mid[0], mid[1]);
+        packed[(e4 >> 1) + 1] = pack2<FMT>(mid[2], mid[3]);
+      }
+    };
+    // ZONO: one job of stage 0 (columns [c0, c0 + nc) of the row over the inputs in TMEM half hb) ->
+    // operand blocks of the zonotope stage; blocks past the inputs are written as zeros
+    auto zprep_job = [&](int t, const RowInfo& ri, uint32_t hb, int c0, int nc, float2& zacc) -> bool {
+      if (!wait_acc(hb)) return false;
+      const uint32_t tb = t_lane + hb * 256u;
+      const XRow xr = xrow(ri);
+      const int cend = c0 + ((nc + 63) & ~63);
+      for (int j0 = c0 + 32 * cq; j0 < cend; j0 += 64) {
+        uint32_t packed[16];
+        if (j0 < n) {
+          float L0[32], mlo[32], mhi[32];
+          tmem_ld32_async(tb + (uint32_t)(j0 - c0), L0);
+          tmem_wait32(L0);
+          const float* xb;
+          if (!jx_chunk(t, ri, xr, L0, j0, xb)) return false;
+#pragma unroll
+          for (int e = 0; e < 32; ++e) m_ivl(ri, xr, L0, xb, e, j0, mlo[e], mhi[e]);
+          zop32(t, ri, mlo, mhi, j0, packed, zacc);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) packed[e] = 0u;
+        }
+        if (!put32(j0, j0 >> 6, packed)) return false;
+      }
+      release_acc(hb);
+      return true;
+    };
+    // ZONO, target 0 (the first hidden layer's bounds): the zonotope stage's operand is W_0's row
+    // (negated for upper rows)
+    auto zprologue = [&](int t, const RowInfo& ri, float2& zacc) -> bool {
+      const float sg = ri.neg ? -1.f : 1.f;
+      for (int j0 = 32 * cq; j0 < 64 * nzb; j0 += 64) {
+        uint32_t packed[16];
+        float m[32];
+        if (ri.valid && j0 < n) {
+          const float* src = a.W_target + (long long)ri.idx * n + j0;
+#pragma unroll
+          for (int e = 0; e < 32; e += 4) {
+            const float4 w4 = __ldg(reinterpret_cast<const float4*>(src + e));
+            m[e] = sg * w4.x; m[e + 1] = sg * w4.y; m[e + 2] = sg * w4.z; m[e + 3] = sg * w4.w;
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 32; ++e) m[e] = 0.f;
+        }
+        zop32(t, ri, m, m, j0, packed, zacc);
+        if (!put32(j0, j0 >> 6, packed)) return false;
+      }
+      return true;
+    };
+    // ZONO: one job of the zonotope stage: columns [c0, c0 + nc) of M [cd | G | -cd]; the lower bound over
+    // the set is the centre column minus the l1 norm of the generator columns (columns >= zcols: padding)
+    auto conc_zono = [&](uint32_t hb, int c0, int nc, float2& sum) -> bool {
+      if (!wait_acc(hb)) return false;
+      const uint32_t tb = t_lane + hb * 256u;
+      for (int j0 = c0 + 32 * cq; j0 < c0 + nc; j0 += 64) {
+        float v[32];
+        tmem_ld32_async(tb + (uint32_t)(j0 - c0), v);
+        tmem_wait32(v);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          const int g = j0 + e;
+          const float term = g == 0 ? v[e] : (g < a.zcols ? -fabsf(v[e]) : 0.f);
+          if (e & 1) sum.y = __fadd_rd(sum.y, term);
+          else sum.x = __fadd_rd(sum.x, term);
+        }
       }
       release_acc(hb);
       return true;
@@ -693,14 +857,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     int item = blockIdx.x;
     float2 beta[2] = {z2, z2}, infl[2] = {z2, z2};
     float ucon = 0.f;
+    float2 zacc = z2;      // ZONO: the zonotope stage's rounding and interval allowances of the item
     if (item < n_items) {
       // first item's prologue
       const int t0 = item / a.tiles_per_t;
-      prefetch(t0, target - 1);
-      const int v0 = vb;
-      ok = install();
-      prefetch_next(t0, target - 1, item + gridDim.x);
-      if (ok) ok = prologue(t0, row_info(a, item - t0 * a.tiles_per_t, r), v0, beta, infl, ucon);
+      const RowInfo ri0 = row_info(a, item - t0 * a.tiles_per_t, r);
+      if (ZONO && target == 0) {
+        ok = zprologue(t0, ri0, zacc);
+      } else {
+        prefetch(t0, target - 1);
+        const int v0 = vb;
+        ok = install();
+        prefetch_next(t0, target - 1, item + gridDim.x);
+        if (ok) ok = prologue(t0, ri0, v0, beta, infl, ucon);
+      }
     }
     for (; item < n_items && ok; item += gridDim.x) {
       const int t = item / a.tiles_per_t, tile = item - t * a.tiles_per_t;
@@ -718,18 +888,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
           ok = stage_job(ri, jc & 1u, job_c0(k, h), job_nc(k, h), vcur, beta, infl);
       }
       if (!ok) break;
+      if (ZONO && target >= 1) {
+        // stage 0's jobs write the zonotope stage's operand over the blocks stage 0 reads
+        apend |= (1u << (a.widths[1] / 64)) - 1u;
+        const int nh0 = njobs(0);
+        for (int h = 0; h < nh0 && ok; ++h, ++jc) ok = zprep_job(t, ri, jc & 1u, job_c0(0, h), job_nc(0, h), zacc);
+        if (!ok) break;
+      }
       // the next item's prologue, built while the tensor cores run this item's final stage
-      apend |= (1u << (a.widths[1] / 64)) - 1u;
+      apend |= ZONO ? (1u << nzb) - 1u : (1u << (a.widths[1] / 64)) - 1u;
       float2 beta_n[2] = {z2, z2}, infl_n[2] = {z2, z2};
       float ucon_n = 0.f;
+      float2 zacc_n = z2;
       if (next < n_items) {
         const int tn = next / a.tiles_per_t;
-        const int vcur = vb;
-        if (!install()) { ok = false; break; }
-        prefetch_next(tn, target - 1, next + gridDim.x);
-        if (!prologue(tn, row_info(a, next - tn * a.tiles_per_t, r), vcur, beta_n, infl_n, ucon_n)) {
-          ok = false;
-          break;
+        const RowInfo rin = row_info(a, next - tn * a.tiles_per_t, r);
+        if (ZONO && target == 0) {
+          if (!zprologue(tn, rin, zacc_n)) { ok = false; break; }
+        } else {
+          const int vcur = vb;
+          if (!install()) { ok = false; break; }
+          prefetch_next(tn, target - 1, next + gridDim.x);
+          if (!prologue(tn, rin, vcur, beta_n, infl_n, ucon_n)) {
+            ok = false;
+            break;
+          }
         }
       }
       // final stage: concretise over the box. The values the finalisation reads from global memory (the
@@ -741,16 +924,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       }
       if (lane == 0) prefetch_l1(a.bad + t);
       float2 sum = z2;
-      const int nh0 = njobs(0);
-      for (int h = 0; h < nh0 && ok; ++h, ++jc)
-        ok = conc_job(t, ri, jc & 1u, job_c0(0, h), job_nc(0, h), sum);
-      if (!ok) break;
+      if (ZONO) {
+        const int nhz = njobs(-1);
+        for (int h = 0; h < nhz && ok; ++h, ++jc) ok = conc_zono(jc & 1u, job_c0(-1, h), job_nc(-1, h), sum);
+        if (!ok) break;
+        if (ri.bound) {
+          // the zonotope stage's allowances: rounding (also stated as slack) and M's interval width
+          sum.x = __fsub_rd(sum.x, __fadd_ru(zacc.x, zacc.y));
+          if (EPS) infl[0].x = __fadd_ru(infl[0].x, zacc.x);
+          ucon = __fadd_ru(ucon, a.zcon[t]);
+        }
+      } else {
+        const int nh0 = njobs(0);
+        for (int h = 0; h < nh0 && ok; ++h, ++jc)
+          ok = conc_job(t, ri, jc & 1u, job_c0(0, h), job_nc(0, h), sum);
+        if (!ok) break;
+      }
       if (!finalize(t, tile, ri, sum, beta, infl, ucon)) { ok = false; break; }
       beta[0] = beta_n[0];
       beta[1] = beta_n[1];
       infl[0] = infl_n[0];
       infl[1] = infl_n[1];
       ucon = ucon_n;
+      zacc = zacc_n;
       if (*(volatile int*)&s_abort) ok = false;
     }
     cp_async_wait_all();
@@ -794,6 +990,61 @@ __global__ void transpose_round_kernel(const float* W, int rows, int cols, uint1
     const long long c = e / rows, r = e - c * rows;  // WT[c][r] = W[r][c]
     WT[e] = to_op(W[r * cols + c], fmt);
   }
+}
+
+// Zonotope stage inputs of timestep t = blockIdx.x: the transposed generator block GhT[t Pp + g][i] in the
+// operand format (g = 0: cd_i, 1 <= g <= p: G_ig, g = p + 1: -cd_i, further columns 0), with cd =
+// fl(c - alpha~) / 2 (0 without a centre); the per-input weight wz_i = cz h_i + wadd (rounded up) and
+// the constant zcon = zc1 sum_i h_i + zc2 (rounded up, summed in a fixed order), h_i = max(-dlo_i, dhi_i).
+__global__ void zono_tc_prep_kernel(int n, int p, int Pp, const float* __restrict__ G, const float* __restrict__ ctr,
+                                    const float* __restrict__ anom, const float* __restrict__ dlo,
+                                    const float* __restrict__ dhi, int fmt, float cz, float wadd, float zc1,
+                                    float zc2, uint16_t* __restrict__ GhT, float* __restrict__ wz,
+                                    float* __restrict__ zcon) {
+  __shared__ float tile[32][33];
+  __shared__ float red[256];
+  const int t = blockIdx.x;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  const long long tn = (long long)t * n;
+  const float* Gt = G + tn * p;
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    for (int g0 = 0; g0 < Pp; g0 += 32) {
+      // read rows i0.. (inputs), columns g0 + tx (generator block columns): consecutive g per warp
+      for (int di = ty; di < 32; di += 8) {
+        const int i = i0 + di, g = g0 + tx;
+        float v = 0.f;
+        if (i < n) {
+          if (g >= 1 && g <= p) {
+            v = Gt[(long long)i * p + (g - 1)];
+          } else if (ctr && (g == 0 || g == p + 1)) {
+            const float cd = 0.5f * (ctr[tn + i] - anom[tn + i]);
+            v = g == 0 ? cd : -cd;
+          }
+        }
+        tile[di][tx] = v;
+      }
+      __syncthreads();
+      // write rows g0 + dg (generator columns), columns i0 + tx: consecutive i per warp
+      for (int dg = ty; dg < 32; dg += 8) {
+        const int g = g0 + dg, i = i0 + tx;
+        if (g < Pp && i < n) GhT[((long long)t * Pp + g) * n + i] = to_op(tile[tx][dg], fmt);
+      }
+      __syncthreads();
+    }
+  }
+  float hs = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float h = fmaxf(-dlo[tn + i], dhi[tn + i]);
+    wz[tn + i] = __fmaf_ru(cz, h, wadd);
+    hs = __fadd_ru(hs, h);
+  }
+  red[threadIdx.x] = hs;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] = __fadd_ru(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) zcon[t] = __fadd_ru(__fmul_ru(zc1, red[0]), zc2);
 }
 
 }  // namespace
@@ -840,9 +1091,13 @@ leb_status tc_prepare(Ctx& c) {
     }
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return LEB_ERR_CUDA;
-  const void* kernels[] = {(const void*)crown_tc_kernel<false, false, 0>, (const void*)crown_tc_kernel<true, false, 0>,
-                           (const void*)crown_tc_kernel<true, true, 0>,   (const void*)crown_tc_kernel<false, false, 1>,
-                           (const void*)crown_tc_kernel<true, false, 1>,  (const void*)crown_tc_kernel<true, true, 1>};
+  const void* kernels[] = {
+      (const void*)crown_tc_kernel<false, false, 0, false>, (const void*)crown_tc_kernel<true, false, 0, false>,
+      (const void*)crown_tc_kernel<true, true, 0, false>,   (const void*)crown_tc_kernel<false, false, 1, false>,
+      (const void*)crown_tc_kernel<true, false, 1, false>,  (const void*)crown_tc_kernel<true, true, 1, false>,
+      (const void*)crown_tc_kernel<false, false, 0, true>,  (const void*)crown_tc_kernel<true, false, 0, true>,
+      (const void*)crown_tc_kernel<true, true, 0, true>,    (const void*)crown_tc_kernel<false, false, 1, true>,
+      (const void*)crown_tc_kernel<true, false, 1, true>,   (const void*)crown_tc_kernel<true, true, 1, true>};
   for (const void* k : kernels)
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) != cudaSuccess)
       return LEB_ERR_CUDA;
@@ -873,14 +1128,51 @@ float gamma_tc(int K) {
   return std::nextafterf((float)g * 1.0000002f, INFINITY);
 }
 
+// unit roundoff of the operand format and half its smallest subnormal spacing
+static void op_units(const MlpModel& m, double* u, double* usub) {
+  const bool bf = m.prec == LEB_PREC_BF16;
+  *u = std::ldexp(1.0, bf ? -8 : -11);
+  *usub = std::ldexp(1.0, bf ? -134 : -25);
+}
+
+static float up(double v) {   // the float nearest above v (v >= 0)
+  float f = (float)v;
+  if ((double)f < v) f = std::nextafterf(f, INFINITY);
+  return f;
+}
+
+leb_status tc_zono_prep(const Ctx& c, int T, const leb_set* set, const MlpWs& L, float* ws, cudaStream_t s) {
+  const MlpModel& m = c.mlp;
+  if (L.zPp <= 0 || set->n_gen + 2 != L.zcols) return LEB_ERR_INVALID_ARG;
+  const int n = m.widths[0], Pp = L.zPp;
+  double u, usub;
+  op_units(m, &u, &usub);
+  const double g = gamma_tc(64 * ((n + 63) / 64));
+  // rounding of the zonotope stage's product (operand and generators rounded to the format, FP32 sums)
+  // and of cd: |M| wz per input, zcon per row (the kernel's comment derives them)
+  const double cz = ((g * (1 + u) + u) * (1 + u) + u + std::ldexp(1.0, -23)) * (1 + std::ldexp(1.0, -20));
+  const double wadd = (Pp + 2) * usub * (2 + g) * (1 + std::ldexp(1.0, -20));
+  const double zc1 = usub * (1 + u) * (1 + g) * (1 + std::ldexp(1.0, -20));
+  const double zc2 = 2.0 * n * (Pp + 2) * usub * usub;
+  zono_tc_prep_kernel<<<T, 256, 0, s>>>(n, set->n_gen, Pp, set->G, set->center, ws + L.anom, ws + L.dlo, ws + L.dhi,
+                                        m.prec == LEB_PREC_BF16 ? 1 : 0, up(cz), up(wadd), up(zc1), up(zc2),
+                                        reinterpret_cast<uint16_t*>(ws + L.zg), ws + L.zw, ws + L.zcon);
+  return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
+}
+
 leb_status tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, float* r_lo, float* r_hi, float* A,
-                    float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags, bool tight) {
+                    float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags, bool tight,
+                    const leb_set* zset) {
   const MlpModel& m = c.mlp;
   TcState* st = tc_state(c);
   if (!st) return LEB_ERR_UNSUPPORTED;
+  const bool zono = zset && zset->kind == LEB_SET_ZONO_EXACT;
+  if (zono && (L.zPp <= 0 || tight)) return LEB_ERR_INVALID_ARG;
+  if (!zono && target == 0) return LEB_ERR_INVALID_ARG;   // the first layer's box bounds come from the nominal pass
   TcArgs a;
   memset(&a, 0, sizeof(a));
-  const int plan = (c.plan_index >= 0 && c.plan_index < kTcPlans) ? c.plan_index : m.tc_plan;
+  // zonotope chains take the 256-column jobs (their stage 0 writes an operand: at most two jobs)
+  const int plan = zono ? 0 : (c.plan_index >= 0 && c.plan_index < kTcPlans) ? c.plan_index : m.tc_plan;
   a.jw = kTcJobWidths[plan];
   for (int k = 0; k + 1 < m.L; ++k) {
     a.tmap[k] = st->maps[plan][k];
@@ -925,19 +1217,42 @@ leb_status tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, 
   a.gamma_pad = opt ? opt->gamma_pad : 0.f;
   a.flags = flags;
   a.tight = tight ? 1 : 0;
+  if (zono) {
+    const int n = m.widths[0];
+    a.Pp = L.zPp;
+    a.zcols = L.zcols;
+    a.zbrows = a.Pp < 256 ? a.Pp : 256;
+    a.wz = ws + L.zw;
+    a.zcon = ws + L.zcon;
+    auto enc = encode_fn();
+    if (!enc) return LEB_ERR_UNSUPPORTED;
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)T * (cuuint64_t)a.Pp};
+    cuuint64_t strides[1] = {(cuuint64_t)n * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)a.zbrows};
+    cuuint32_t estr[2] = {1, 1};
+    if (enc(&a.gmap, a.fmt == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ws + L.zg, dims,
+            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return LEB_ERR_UNSUPPORTED;
+  }
   const int items = T * a.tiles_per_t;
   const int grid = items < c.sm_count ? items : c.sm_count;
   if (grid == 0) return LEB_OK;
   timer_begin(c, s, "crown_tc_kernel");
+#define LEB_TC_LAUNCH(F, Z)                                                                   \
+  do {                                                                                         \
+    if (!output) crown_tc_kernel<false, false, F, Z><<<grid, kTcThreads, kTcSmem, s>>>(a);     \
+    else if (eps) crown_tc_kernel<true, true, F, Z><<<grid, kTcThreads, kTcSmem, s>>>(a);      \
+    else crown_tc_kernel<true, false, F, Z><<<grid, kTcThreads, kTcSmem, s>>>(a);              \
+  } while (0)
   if (a.fmt == 0) {
-    if (!output) crown_tc_kernel<false, false, 0><<<grid, kTcThreads, kTcSmem, s>>>(a);
-    else if (eps) crown_tc_kernel<true, true, 0><<<grid, kTcThreads, kTcSmem, s>>>(a);
-    else crown_tc_kernel<true, false, 0><<<grid, kTcThreads, kTcSmem, s>>>(a);
+    if (zono) LEB_TC_LAUNCH(0, true);
+    else LEB_TC_LAUNCH(0, false);
   } else {
-    if (!output) crown_tc_kernel<false, false, 1><<<grid, kTcThreads, kTcSmem, s>>>(a);
-    else if (eps) crown_tc_kernel<true, true, 1><<<grid, kTcThreads, kTcSmem, s>>>(a);
-    else crown_tc_kernel<true, false, 1><<<grid, kTcThreads, kTcSmem, s>>>(a);
+    if (zono) LEB_TC_LAUNCH(1, true);
+    else LEB_TC_LAUNCH(1, false);
   }
+#undef LEB_TC_LAUNCH
   timer_end(c, s);
   return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
 }

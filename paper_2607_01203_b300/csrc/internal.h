@@ -142,6 +142,11 @@ struct MlpWs {
   size_t adj;               // tensor-core adjoint: per-CTA lambda store (0 floats for FP32 handles)
   size_t anom, dlo, dhi;    // [T, n] nominal alpha~ and displacement box Delta = X - alpha~
   size_t bad;               // [T] int: non-finite inputs
+  // tensor-core chains over a zonotope set (LEB_SET_ZONO_EXACT; zPp = 0 otherwise): the transposed
+  // generator blocks [T, zPp, n] in the operand format, the per-input rounding weights [T, n] and the
+  // per-timestep constants [T] of the zonotope stage; zcols = n_gen + 2 of the zPp columns are used
+  size_t zg, zw, zcon;
+  int zPp, zcols;
   size_t total;             // floats
   int H;                    // total hidden neurons
   int hoff[kMaxLayers];     // offset of hidden layer i (0-based) inside H
@@ -195,7 +200,8 @@ cudaError_t launch_prefix(const int* traj_offsets, const int* traj_nquads, int n
 cudaError_t launch_zonotope_map(const float* lo, const float* hi, long long count, float pad, float* c, float* r,
                                 cudaStream_t s);
 
-size_t mlp_workspace_floats(const Ctx& c, int T, MlpWs* layout);
+// n_gen: generators of a LEB_SET_ZONO_EXACT set (tensor-core handles need room for the zonotope stage), else 0
+size_t mlp_workspace_floats(const Ctx& c, int T, MlpWs* layout, int n_gen = 0);
 leb_status mlp_bounds(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set, float* r_lo,
                       float* r_hi, float* A, float* B, const leb_options* opt, void* ws, int* flags, cudaStream_t s);
 // saved: the workspace holds the state of the forward call on the same inputs (skip its recompute)
@@ -220,9 +226,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 leb_status tc_prepare(Ctx& c);
 void tc_release(Ctx& c);
 float gamma_tc(int K);  // accumulation bound of K exact products in FP32 (unit roundoff 2^-23)
+// zset: a LEB_SET_ZONO_EXACT set concretises every bound over the zonotope (tc_zono_prep first; target 0
+// gives the first hidden layer's bounds); otherwise target >= 1 and the box of the workspace
 leb_status tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, float* r_lo, float* r_hi, float* A,
                     float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags,
-                    bool tight = false);
+                    bool tight = false, const leb_set* zset = nullptr);
+// the zonotope stage's inputs of every timestep (after the prep kernel wrote the nominal and the box)
+leb_status tc_zono_prep(const Ctx& c, int T, const leb_set* set, const MlpWs& L, float* ws, cudaStream_t s);
+constexpr int kTcMaxZonoCols = 512;   // n_gen + 2 columns of the zonotope stage, rounded up to 16
 const void* tc_weight_t(const Ctx& c, int k);   // W_k^T in the operand format, [widths[k], widths[k+1]]
 // adjoint of the PBH bound of the quadrotor chain (box sets centred at the nominal); g_lo == nullptr:
 // cotangents -1 on r_lo and +1 on r_hi (the gradient of the summed width)

@@ -258,6 +258,17 @@ leb_status leb_dims(leb_handle h, int* n_x, int* n_u) {
   return LEB_OK;
 }
 
+leb_status leb_workspace_size_set(leb_handle h, int T_max, leb_set_kind set_kind, int n_gen, size_t* bytes) {
+  if (!h || !bytes || T_max < 0 || n_gen < 0) return LEB_ERR_INVALID_ARG;
+  if (set_kind != LEB_SET_BOX && set_kind != LEB_SET_ZONO && set_kind != LEB_SET_ZONO_EXACT) return LEB_ERR_INVALID_ARG;
+  if (set_kind == LEB_SET_ZONO_EXACT && h->kind == LEB_DYN_MLP) {
+    MlpWs lay;
+    *bytes = kWsHeader + mlp_workspace_floats(*h, T_max, &lay, n_gen) * sizeof(float);
+    return LEB_OK;
+  }
+  return leb_workspace_size(h, T_max, bytes);
+}
+
 leb_status leb_workspace_size(leb_handle h, int T_max, size_t* bytes) {
   if (!h || !bytes || T_max < 0) return LEB_ERR_INVALID_ARG;
   if (h->kind == LEB_DYN_QUAD_CHAIN) {
@@ -281,8 +292,11 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
     return LEB_ERR_INVALID_ARG;
   if (T > 0 && set->kind == LEB_SET_BOX && !set->radii) return LEB_ERR_INVALID_ARG;
   if (T > 0 && set->kind != LEB_SET_BOX && (!set->G || set->n_gen < 1)) return LEB_ERR_INVALID_ARG;
-  if (set->kind == LEB_SET_ZONO_EXACT && (h->kind != LEB_DYN_MLP || h->mlp.prec != LEB_PREC_FP32))
-    return LEB_ERR_UNSUPPORTED;
+  if (set->kind == LEB_SET_ZONO_EXACT) {
+    // CROWN over the zonotope itself: MLP handles; tensor-core chains take up to kTcMaxZonoCols - 2 generators
+    if (h->kind != LEB_DYN_MLP) return LEB_ERR_UNSUPPORTED;
+    if (h->mlp.prec != LEB_PREC_FP32 && (!h->mlp.tc || set->n_gen + 2 > kTcMaxZonoCols)) return LEB_ERR_UNSUPPORTED;
+  }
   if (opt && ((opt->gamma_c == nullptr) != (opt->gamma_r == nullptr))) return LEB_ERR_INVALID_ARG;
   if (opt && !(opt->gamma_pad >= 0.f)) return LEB_ERR_INVALID_ARG;
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return LEB_ERR_WORKSPACE;
@@ -353,7 +367,8 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
   // MLP dynamics
   if (batch && batch->traj_nquads) return LEB_ERR_UNSUPPORTED;
   MlpWs lay;
-  const size_t need = kWsHeader + mlp_workspace_floats(*h, T, &lay) * sizeof(float);
+  const size_t need =
+      kWsHeader + mlp_workspace_floats(*h, T, &lay, set->kind == LEB_SET_ZONO_EXACT ? set->n_gen : 0) * sizeof(float);
   if (ws_bytes < need) return LEB_ERR_WORKSPACE;
   return mlp_bounds(*h, T, x_nom, u_nom, set, r_lo, r_hi, A, B, opt, workspace, dev_flags, s);
 }

@@ -30,7 +30,7 @@ namespace leb {
 // ---------------------------------------------------------------------------------------------------
 // workspace layout
 // ---------------------------------------------------------------------------------------------------
-size_t mlp_workspace_floats(const Ctx& c, int T, MlpWs* w) {
+size_t mlp_workspace_floats(const Ctx& c, int T, MlpWs* w, int n_gen) {
   const MlpModel& m = c.mlp;
   int H = 0;
   for (int i = 0; i + 1 < m.L; ++i) {
@@ -76,6 +76,16 @@ size_t mlp_workspace_floats(const Ctx& c, int T, MlpWs* w) {
   w->winf = take(TH);
   w->ucon = take((size_t)T * (m.L > 1 ? m.L - 1 : 1));
   w->bad = take(T);
+  w->zPp = 0;
+  w->zcols = 0;
+  w->zg = w->zw = w->zcon = o;
+  if (n_gen > 0 && m.prec != LEB_PREC_FP32) {
+    w->zcols = n_gen + 2;
+    w->zPp = (w->zcols + 15) & ~15;
+    w->zg = take(((size_t)T * w->zPp * m.widths[0] + 1) / 2);   // 2-byte operands
+    w->zw = take(Tn);
+    w->zcon = take(T);
+  }
   w->total = o;
   return o;
 }
@@ -866,9 +876,10 @@ leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_
                               void* ws_base, int* flags, cudaStream_t s, bool simt, const leb_options* opt, bool tight) {
   const MlpModel& m = c.mlp;
   MlpWs L;
-  mlp_workspace_floats(c, T, &L);
-  float* ws = (float*)((char*)ws_base + 256);
   const bool tc = !simt && m.prec != LEB_PREC_FP32;
+  const bool zexact = set->kind == LEB_SET_ZONO_EXACT;
+  mlp_workspace_floats(c, T, &L, zexact && tc ? set->n_gen : 0);
+  float* ws = (float*)((char*)ws_base + 256);
   auto tcw = [&](int layer) {
     TcWeights w{};
     if (!tc) return w;
@@ -890,6 +901,10 @@ leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_
     return LEB_ERR_CUDA;
   mlp_prep_kernel<<<T, 256, 0, s>>>(T, n_x, n_u, x_nom, u_nom, *set, ws + L.anom, ws + L.dlo, ws + L.dhi, bad, flags);
   if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
+  if (zexact && tc) {
+    leb_status st = tc_zono_prep(c, T, set, L, ws, s);
+    if (st != LEB_OK) return st;
+  }
 
   // nominal pass of every hidden layer; layer-0 bounds come out of the first pass
   for (int i = 0; i + 1 < m.L; ++i) {
@@ -933,7 +948,7 @@ leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_
       if (set->kind == LEB_SET_ZONO_EXACT) {
         // layer-0 bounds over the zonotope itself (the nominal pass gave them over its interval hull)
         leb_status st = run_chain(c, T, 0, L, ws, nullptr, nullptr, nullptr, nullptr, nullptr, s, bad, opt, flags,
-                                  true, false, set);
+                                  !tc, false, set);
         if (st != LEB_OK) return st;
       }
       const int blocks = (int)std::min<long long>(((long long)T * na.N + 255) / 256, 148LL * 32);
@@ -976,7 +991,7 @@ leb_status mlp_bounds(Ctx& c, int T, const float* x_nom, const float* u_nom, con
   leb_status st = mlp_forward_hidden(c, T, x_nom, u_nom, set, ws_base, flags, s, simt, opt);
   if (st != LEB_OK) return st;
   MlpWs L;
-  mlp_workspace_floats(c, T, &L);
+  mlp_workspace_floats(c, T, &L, set->kind == LEB_SET_ZONO_EXACT && !simt ? set->n_gen : 0);
   float* ws = (float*)((char*)ws_base + 256);
   // output rows: lower, upper and Jacobian chains -> r_lo, r_hi, A, B
   return run_chain(c, T, c.mlp.L - 1, L, ws, r_lo, r_hi, A, B, opt ? opt->eps : nullptr, s, (int*)(ws + L.bad), opt,
@@ -987,7 +1002,7 @@ leb_status run_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws,
                      float* B, float* eps, cudaStream_t s, const int* bad, const leb_options* opt, int* flags,
                      bool simt, bool tight, const leb_set* zset) {
   const MlpModel& m = c.mlp;
-  if (!simt) return tc_chain(c, T, target, L, ws, r_lo, r_hi, A, B, eps, s, bad, opt, flags, tight);
+  if (!simt) return tc_chain(c, T, target, L, ws, r_lo, r_hi, A, B, eps, s, bad, opt, flags, tight, zset);
   ChainArgs a{};
   a.m = view(m);
   a.T = T;
