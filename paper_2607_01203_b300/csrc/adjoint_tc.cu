@@ -97,7 +97,9 @@ __device__ __forceinline__ uint32_t b_off8(int r0, int j) {
 
 __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid_constant__ AdjTcArgs a) {
   extern __shared__ uint8_t sraw[];
-  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sraw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte aligned base, as an offset from the shared array (so that every derived pointer keeps the
+  // shared address space and its accesses compile to shared-memory instructions)
+  uint8_t* base = sraw + ((1024u - (smem_u32(sraw) & 1023u)) & 1023u);
   uint8_t* Bop = base;                                   // per-row operand
   uint8_t* ring = base + kAdjBRegion;                    // weight tiles
   float* gws = reinterpret_cast<float*>(ring + kAdjStages * kAdjATile);   // [2][128] row cotangents

@@ -189,7 +189,9 @@ __device__ __forceinline__ void tmem_wait32(float v[32]) {
 template <bool OUT, bool EPS, int FMT, bool ZONO>
 __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_constant__ TcArgs a) {
   extern __shared__ uint8_t sraw[];
-  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sraw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte aligned base, as an offset from the shared array (so that every derived pointer keeps the
+  // shared address space and its accesses compile to shared-memory instructions)
+  uint8_t* base = sraw + ((1024u - (smem_u32(sraw) & 1023u)) & 1023u);
   uint8_t* Asm = base;                                     // A operand
   uint8_t* Bsm = base + kTcARegion;                        // B ring
   uint8_t* Vsm = Bsm + kTcNSB * kTcBStage;                 // 2 x per-neuron vectors

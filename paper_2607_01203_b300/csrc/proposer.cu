@@ -109,7 +109,9 @@ __global__ void __launch_bounds__(128, 2) prop_tc_gemm_kernel(const __grid_const
                                                               const __grid_constant__ CUtensorMap wmap, int M, int N,
                                                               int K, int nchunk, int stages, int kpb, const PtEpi e) {
   extern __shared__ uint8_t sraw[];
-  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sraw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte aligned base, as an offset from the shared array (so that every derived pointer keeps the
+  // shared address space and its accesses compile to shared-memory instructions)
+  uint8_t* base = sraw + ((1024u - (smem_u32(sraw) & 1023u)) & 1023u);
   const int btile = N * 128;                              // N rows x 64 K x 2 bytes (a multiple of 1 KB)
   uint8_t* At = base;                                        // [stages][16 KB]
   uint8_t* Bt = base + stages * kPtATile;                 // [stages][N x 128 B]
