@@ -563,26 +563,32 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
               const bool isJ = (jm >> e) & 1u, isL = (lm >> e) & 1u;
-              const float2 x = make_float2(ga0[e], ga1[e]), l = make_float2(l0[e], l1[e]);
-              const float2 gg = make_float2(g[e], g[e]);
-              const float2 p1 = __fmul2_rn(x, l), p2 = __fmul2_rn(gg, l);
+              // scalar arithmetic: the two neurons' values sit in separate arrays, so packed FP32x2
+              // operations would first have to move them into register pairs
+              const float x0 = ga0[e], x1 = ga1[e], la = l0[e], lb = l1[e];
+              const float p10 = x0 * la, p11 = x1 * lb, p20 = g[e] * la, p21 = g[e] * lb;
               // lower line chosen (sg) / upper line chosen (ng); both 0 on Jacobian rows. The choice is
               // the sign bit of the stored lambda, as in the forward recompute.
-              const bool u0 = isL == !signbit(l.x), u1 = isL == !signbit(l.y);
-              const float2 sg = make_float2(!isJ && u0 ? 1.f : 0.f, !isJ && u1 ? 1.f : 0.f);
-              const float2 ng = make_float2(!isJ && !u0 ? 1.f : 0.f, !isJ && !u1 ? 1.f : 0.f);
-              SL = __ffma2_rn(sg, p1, SL);
-              SU = __ffma2_rn(ng, p1, SU);
-              TL = __ffma2_rn(sg, p2, TL);
-              TU = __ffma2_rn(ng, p2, TU);
+              const bool u0 = isL == !signbit(la), u1 = isL == !signbit(lb);
+              const float sg0 = !isJ && u0 ? 1.f : 0.f, sg1 = !isJ && u1 ? 1.f : 0.f;
+              const float ng0 = !isJ && !u0 ? 1.f : 0.f, ng1 = !isJ && !u1 ? 1.f : 0.f;
+              SL.x = fmaf(sg0, p10, SL.x);
+              SL.y = fmaf(sg1, p11, SL.y);
+              SU.x = fmaf(ng0, p10, SU.x);
+              SU.y = fmaf(ng1, p11, SU.y);
+              TL.x = fmaf(sg0, p20, TL.x);
+              TL.y = fmaf(sg1, p21, TL.y);
+              TU.x = fmaf(ng0, p20, TU.x);
+              TU.y = fmaf(ng1, p21, TU.y);
               float2 G;
               if (isJ) {
-                GD = __fadd2_rn(GD, p1);
-                G = __fmul2_rn(x, dd2);
+                GD.x += p10;
+                GD.y += p11;
+                G = make_float2(x0 * dd2.x, x1 * dd2.y);
               } else {
-                const float2 sv = make_float2(u0 ? sl[0] : su[0], u1 ? sl[1] : su[1]);
-                const float2 tv = make_float2(u0 ? tlv[0] : tu[0], u1 ? tlv[1] : tu[1]);
-                G = __ffma2_rn(x, sv, __fmul2_rn(gg, tv));
+                const float sv0 = u0 ? sl[0] : su[0], sv1 = u1 ? sl[1] : su[1];
+                const float tv0 = u0 ? tlv[0] : tu[0], tv1 = u1 ? tlv[1] : tu[1];
+                G = make_float2(fmaf(x0, sv0, g[e] * tv0), fmaf(x1, sv1, g[e] * tv1));
               }
               G0[e] = G.x;
               G1[e] = G.y;

@@ -84,6 +84,7 @@ struct TcArgs {
   int H;
   int hoff[kMaxLayers];
   const float* W_target;
+  const float* WT_target;        // W_target transposed, FP32 [widths[target], widths[target + 1]]
   const float *zhat, *zrad, *sL, *tL, *sU, *tU, *D, *winf, *ucon, *dlo, *dhi;
   const int* bad;
   float *lo, *hi;
@@ -144,13 +145,17 @@ __device__ __forceinline__ void row_pass16(const float lam[16], int j0, const fl
       k1 &= smask;
     }
     const float2 v0 = base[3 * e + k0], v1 = base[3 * (e + 1) + k1];
-    const float2 av = __fmul2_rn(l, make_float2(v0.x, v1.x));
-    beta = __ffma2_rd(l, make_float2(v0.y, v1.y), beta);
+    // scalar arithmetic: the two elements' line values come from separate loads, so packed FP32x2
+    // operations would first have to move them into register pairs
+    const float a0 = l.x * v0.x, a1 = l.y * v1.x;
+    beta.x = __fmaf_rd(l.x, v0.y, beta.x);
+    beta.y = __fmaf_rd(l.y, v1.y, beta.y);
     if (EPS) {
       const float2 w = *reinterpret_cast<const float2*>(sw + j0 + e);
-      infl = __ffma2_ru(make_float2(fabsf(av.x), fabsf(av.y)), w, infl);
+      infl.x = __fmaf_ru(fabsf(a0), w.x, infl.x);
+      infl.y = __fmaf_ru(fabsf(a1), w.y, infl.y);
     }
-    packed[e >> 1] = pack2<FMT>(av.x, av.y);
+    packed[e >> 1] = pack2<FMT>(a0, a1);
   }
 }
 
@@ -492,19 +497,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     auto prologue = [&](int t, const RowInfo& ri, int vcur, float2 (&beta)[2], float2 (&infl)[2],
                         float& ucon) -> bool {
       const int K = a.widths[target], nb = K / 64;
-      const float* Wrow = a.W_target + (long long)ri.idx * K + 32 * cq;
-      const float2 sg = ri.neg ? make_float2(-1.f, -1.f) : make_float2(1.f, 1.f);
+      const int R = a.widths[target + 1];
+      const float sg = ri.neg ? -1.f : 1.f;
       // 16-column halves h = 2 bb + hh of this warp's 32 columns of block bb; the next half's weights are
-      // loaded while a half is processed
+      // loaded while a half is processed. The weights come from the transposed copy: for one column the
+      // lanes of a warp read consecutive rows, so every load instruction touches one or two cache lines.
+      const float* Wcol = a.WT_target + (long long)(32 * cq) * R + ri.idx;
       auto ldw = [&](float v[16], int h) {
         if (ri.valid) {
-          const float* src = Wrow + 64 * (h >> 1) + 16 * (h & 1);
+          const float* src = Wcol + (long long)(64 * (h >> 1) + 16 * (h & 1)) * R;
 #pragma unroll
-          for (int e = 0; e < 16; e += 4) {
-            const float4 w4 = __ldg(reinterpret_cast<const float4*>(src + e));
-            const float2 x = __fmul2_rn(make_float2(w4.x, w4.y), sg), y = __fmul2_rn(make_float2(w4.z, w4.w), sg);
-            v[e] = x.x; v[e + 1] = x.y; v[e + 2] = y.x; v[e + 3] = y.y;
-          }
+          for (int e = 0; e < 16; ++e) v[e] = sg * __ldg(src + (long long)e * R);
         } else {
 #pragma unroll
           for (int e = 0; e < 16; ++e) v[e] = 0.f;
@@ -771,12 +774,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
         uint32_t packed[16];
         float m[32];
         if (ri.valid && j0 < n) {
-          const float* src = a.W_target + (long long)ri.idx * n + j0;
+          // the transposed copy: for one column the lanes of a warp read consecutive rows
+          const int R = a.widths[1];
+          const float* src = a.WT_target + (long long)j0 * R + ri.idx;
 #pragma unroll
-          for (int e = 0; e < 32; e += 4) {
-            const float4 w4 = __ldg(reinterpret_cast<const float4*>(src + e));
-            m[e] = sg * w4.x; m[e + 1] = sg * w4.y; m[e + 2] = sg * w4.z; m[e + 3] = sg * w4.w;
-          }
+          for (int e = 0; e < 32; ++e) m[e] = sg * __ldg(src + (long long)e * R);
         } else {
 #pragma unroll
           for (int e = 0; e < 32; ++e) m[e] = 0.f;
@@ -985,6 +987,15 @@ __device__ __forceinline__ uint16_t to_op(float a, int fmt) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(a));
 }
 
+__global__ void transpose_f32_kernel(const float* W, int rows, int cols, float* WT) {
+  // W [rows, cols] -> WT [cols, rows]
+  const long long total = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / rows, r = e - c * rows;
+    WT[e] = W[r * cols + c];
+  }
+}
+
 __global__ void transpose_round_kernel(const float* W, int rows, int cols, uint16_t* WT, int fmt) {
   // W [rows, cols] -> WT [cols, rows] in the operand format
   const long long total = (long long)rows * cols;
@@ -1056,6 +1067,7 @@ constexpr int kTcJobWidths[kTcPlans] = {256, 128};
 
 struct TcState {
   uint16_t* WT[kMaxLayers] = {};
+  float* WT32[kMaxLayers] = {};             // W_k transposed in FP32 (the prologues' coalesced weight reads)
   CUtensorMap maps[kTcPlans][kMaxLayers];   // per plan: B tiles of min(job width, widths[k]) rows
 };
 
@@ -1092,6 +1104,12 @@ leb_status tc_prepare(Ctx& c) {
       if (r != CUDA_SUCCESS) return LEB_ERR_UNSUPPORTED;
     }
   }
+  for (int k = 0; k < m.L; ++k) {
+    const int R = m.widths[k + 1], K = m.widths[k];   // W_k [R, K] -> [K, R]
+    if (cudaMalloc(&st->WT32[k], (size_t)R * K * 4) != cudaSuccess) return LEB_ERR_CUDA;
+    transpose_f32_kernel<<<256, 256>>>(m.W[k], R, K, st->WT32[k]);
+    if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) return LEB_ERR_CUDA;
   const void* kernels[] = {
       (const void*)crown_tc_kernel<false, false, 0, false>, (const void*)crown_tc_kernel<true, false, 0, false>,
@@ -1117,7 +1135,10 @@ void tc_release(Ctx& c) {
   adj_tc_release(c);
   TcState* st = tc_state(c);
   if (!st) return;
-  for (int k = 0; k < kMaxLayers; ++k) cudaFree(st->WT[k]);
+  for (int k = 0; k < kMaxLayers; ++k) {
+    cudaFree(st->WT[k]);
+    cudaFree(st->WT32[k]);
+  }
   delete st;
   c.mlp.tc = nullptr;
 }
@@ -1195,6 +1216,7 @@ leb_status tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, 
   a.H = L.H;
   for (int i = 0; i + 1 < m.L; ++i) a.hoff[i] = L.hoff[i];
   a.W_target = m.W[target];
+  a.WT_target = st->WT32[target];
   a.zhat = ws + L.zhat;
   a.zrad = ws + L.zrad;
   a.sL = ws + L.sL;
