@@ -20,9 +20,10 @@
 // prologue (its first operand) is built before the current timestep's final concretisation, so the
 // tensor cores start the next tile while the epilogue concretises.
 // Warp roles: warp 0 streams W_k^T tiles (128 rows x 64 K) with TMA through a ring of kTcNSB stages,
-// warp 1 allocates TMEM and one of its threads issues the MMAs, warps 2..9 run the epilogue (two warps
-// per TMEM lane quarter, each on one 32-column half of every 64-column block, the next block's TMEM
-// load in flight while a block is processed; the per-neuron vectors of the next pass arrive by cp.async).
+// warp 1 allocates TMEM and one of its threads issues the MMAs (warps 2, 3 complete their warpgroup and
+// idle), warps 4..15 run the epilogue: three warps per TMEM lane quarter, each on every third 32-column
+// chunk, the next 16 columns' TMEM load in flight while 16 are processed; the per-neuron vectors of the
+// next pass arrive by cp.async. Warpgroup 0 hands most of its registers to the epilogue (setmaxnreg).
 //
 // Zonotope sets (ZONO instances, LEB_SET_ZONO_EXACT): every bound is concretised over the zonotope
 // Delta = cd (1 - xi_p) + G xi (the set widened by the segment to the nominal, cd = (c - alpha~) / 2)
@@ -58,16 +59,24 @@
 
 namespace leb {
 
-constexpr int kTcEpiWarps = 8;                  // 2 per TMEM lane quarter, 32 columns of every 64-column block each
-constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
+constexpr int kTcColGroups = 3;                 // epilogue warps per TMEM lane quarter (column groups)
+constexpr int kTcEpiWarps = 4 * kTcColGroups;   // warps 4 .. 15
+constexpr int kTcCtlWarps = 4;                  // warpgroup 0: TMA warp, MMA warp, two idle warps
+constexpr int kTcThreads = 32 * (kTcCtlWarps + kTcEpiWarps);
+// Register split (setmaxnreg): warpgroup 0 keeps 40 registers a thread, the three epilogue warpgroups take
+// 152. The increases draw on what the block was launched with, so the compiled kernel must have at least
+// kTcRegsLaunchMin registers a thread (checked before any launch).
+constexpr int kTcRegsCtl = 40, kTcRegsEpi = 152;
+constexpr int kTcRegsLaunchMin = (128 * kTcRegsCtl + 32 * kTcEpiWarps * kTcRegsEpi + kTcThreads - 1) / kTcThreads;
+constexpr int kTcBlockWriters = 8;              // arrivals per operand block: 4 lane quarters x 2 halves
 constexpr int kTcNSB = 2;                       // B ring stages
 constexpr int kTcBStage = 256 * 128;            // B tile of at most 256 rows (one job) x 64 K x 2 bytes
 constexpr int kTcARegion = 128 * 512 * 2;       // 128 rows x 512 K x 2 bytes (8 blocks of 16 KB)
 constexpr int kTcVecBuf = 512 * 24 + 512 * 4;   // per-neuron line slots {s, tau'} x {lower, upper, Jacobian}, w
-constexpr int kTcStat = 128 * 2 * 3 * 4;        // [row][column group][3]
+constexpr int kTcStat = 128 * (kTcColGroups - 1) * 3 * 4;   // [row][column group 1..][3]
 constexpr int kTcVals = 2 * 128 * 4;            // [128] final values, [128] stated slack
-constexpr int kTcXch = 2 * 2 * 2 * 32 * 4;      // [column group][buffer][slot][32] Jacobian values
-constexpr int kTcNBar = 2 * kTcNSB + 8 + 8 + 2 + 2 + 1 + 1 + 2;
+constexpr int kTcXch = kTcColGroups * 2 * 2 * 32 * 4;   // [column group][buffer][slot][32] Jacobian values
+constexpr int kTcNBar = 2 * kTcNSB + 8 + 8 + 2 + 2 + 1 + 1 + kTcColGroups;
 constexpr int kTcSmem = 1024 + kTcARegion + kTcNSB * kTcBStage + 2 * kTcVecBuf + kTcStat + kTcVals + kTcXch +
                         kTcNBar * 8;
 static_assert(kTcSmem <= 227 * 1024, "tensor-core chain shared memory");
@@ -200,11 +209,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
   uint8_t* Asm = base;                                     // A operand
   uint8_t* Bsm = base + kTcARegion;                        // B ring
   uint8_t* Vsm = Bsm + kTcNSB * kTcBStage;                 // 2 x per-neuron vectors
-  float* stat = reinterpret_cast<float*>(Vsm + 2 * kTcVecBuf);   // [128][2][3]
-  float* vals = stat + 128 * 6;                            // [128]
+  float* stat = reinterpret_cast<float*>(Vsm + 2 * kTcVecBuf);   // [128][kTcColGroups - 1][3]
+  float* vals = stat + 128 * (kTcColGroups - 1) * 3;       // [128]
   float* slk = vals + 128;                                 // [128]
-  float* xch = slk + 128;                                  // [2][2][2][32]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(xch + 2 * 2 * 2 * 32);
+  float* xch = slk + 128;                                  // [kTcColGroups][2][2][32]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(xch + kTcColGroups * 2 * 2 * 32);
   uint64_t* b_full = bars;                 // [kTcNSB]  B tile landed
   uint64_t* b_empty = bars + kTcNSB;       // [kTcNSB]  B tile consumed
   uint64_t* a_ready = bars + 2 * kTcNSB;   // [8]  operand block written by the epilogue
@@ -213,7 +222,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
   uint64_t* acc_free = acc_full + 2;       // [2]  TMEM half read by the epilogue
   uint64_t* drain = acc_free + 2;
   uint64_t* ebar = drain + 1;              // epilogue-warps barrier
-  uint64_t* xbar = ebar + 1;               // [2]  per column group (Jacobian exchange)
+  uint64_t* xbar = ebar + 1;               // [kTcColGroups]  per column group (Jacobian exchange)
   __shared__ uint32_t tmem_slot;
   __shared__ int s_abort;
 
@@ -227,7 +236,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       mbar_init(&b_empty[s], 1);
     }
     for (int b = 0; b < 8; ++b) {
-      mbar_init(&a_ready[b], kTcEpiWarps);
+      mbar_init(&a_ready[b], kTcBlockWriters);
       mbar_init(&a_free[b], 1);
     }
     for (int h = 0; h < 2; ++h) {
@@ -236,7 +245,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     }
     mbar_init(drain, 1);
     mbar_init(ebar, kTcEpiWarps);
-    for (int c = 0; c < 2; ++c) mbar_init(&xbar[c], 4);
+    for (int c = 0; c < kTcColGroups; ++c) mbar_init(&xbar[c], 4);
     mbar_fence_init();
     s_abort = 0;
   }
@@ -276,6 +285,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     return h ? N - split : split;
   };
 
+  if (warp < kTcCtlWarps) regs_dec<kTcRegsCtl>();   // warpgroup 0: its four warps together
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
@@ -363,15 +373,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       mbar_wait(drain, 0);
     }
     __syncwarp();
-  } else {
+  } else if (warp >= kTcCtlWarps) {
+    regs_inc<kTcRegsEpi>();   // the three epilogue warpgroups
     // ---------------------------------------------------------------- epilogue warps
-    const int ew = warp - 2;
+    const int ew = warp - kTcCtlWarps;
     const int q = warp & 3;                 // TMEM lane quarter of this warp
-    const int cq = ew >> 2;                 // 32-column half of every 64-column block
+    const int cq = ew >> 2;                 // column group: the 32-column chunks c with c mod kTcColGroups == cq
     const int r = q * 32 + lane;            // tile row = TMEM lane
     const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16);
-    const int etid = threadIdx.x - 64;
+    const int etid = threadIdx.x - 32 * kTcCtlWarps;
     constexpr int kEThreads = kTcEpiWarps * 32;
+    // this warp's first 32-column chunk at or after chunk c_lo (chunk c = columns 32 c .. 32 c + 31)
+    auto first_chunk = [&](int c_lo) -> int {
+      return c_lo + ((cq - c_lo % kTcColGroups) % kTcColGroups + kTcColGroups) % kTcColGroups;
+    };
     const int n = a.widths[0];
     const int n_x = a.widths[a.L];
     const bool tight = a.tight != 0;
@@ -485,7 +500,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       vptr(vcur, sl, sw);
       row_pass16<OUT, EPS, FMT>(lam, j0, sl, sw, ri.isJ ? 0u : 1u, ri.isJ ? 2u : 0u, packed, beta, infl);
     };
-    // this warp's 32 columns of operand block b -> shared memory, then the block is announced
+    // this warp's 32 columns j0.. of operand block b -> shared memory, then its half of the block is
+    // announced
     auto put32 = [&](int j0, int b, const uint32_t packed[16]) -> bool {
       if (!wait_free(b)) return false;
       store_a32(Asm, r, j0, packed);
@@ -496,16 +512,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     // prologue of an item: operand = W_target rows (negated for upper rows) o slopes of layer target-1
     auto prologue = [&](int t, const RowInfo& ri, int vcur, float2 (&beta)[2], float2 (&infl)[2],
                         float& ucon) -> bool {
-      const int K = a.widths[target], nb = K / 64;
+      const int K = a.widths[target];
       const int R = a.widths[target + 1];
       const float sg = ri.neg ? -1.f : 1.f;
-      // 16-column halves h = 2 bb + hh of this warp's 32 columns of block bb; the next half's weights are
-      // loaded while a half is processed. The weights come from the transposed copy: for one column the
-      // lanes of a warp read consecutive rows, so every load instruction touches one or two cache lines.
-      const float* Wcol = a.WT_target + (long long)(32 * cq) * R + ri.idx;
-      auto ldw = [&](float v[16], int h) {
+      // 16-column halves of this warp's chunks; the next half's weights are loaded while a half is
+      // processed. The weights come from the transposed copy: for one column the lanes of a warp read
+      // consecutive rows, so every load instruction touches one or two cache lines.
+      const float* Wcol = a.WT_target + ri.idx;
+      auto ldw = [&](float v[16], int col) {
         if (ri.valid) {
-          const float* src = Wcol + (long long)(64 * (h >> 1) + 16 * (h & 1)) * R;
+          const float* src = Wcol + (long long)col * R;
 #pragma unroll
           for (int e = 0; e < 16; ++e) v[e] = sg * __ldg(src + (long long)e * R);
         } else {
@@ -515,45 +531,51 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       };
       float A0[16], A1[16];
       uint32_t packed[16];
-      ldw(A0, 0);
-      for (int bb = 0; bb < nb; ++bb) {
-        const int j0 = 64 * bb + 32 * cq;
-        ldw(A1, 2 * bb + 1);
+      int c = first_chunk(0);
+      if (32 * c < K) ldw(A0, 32 * c);
+      for (; 32 * c < K; c += kTcColGroups) {
+        const int j0 = 32 * c;
+        ldw(A1, j0 + 16);
         pass16(A0, j0, vcur, ri, packed, beta[0], infl[0]);
-        if (bb + 1 < nb) ldw(A0, 2 * bb + 2);
+        if (32 * (c + kTcColGroups) < K) ldw(A0, 32 * (c + kTcColGroups));
         pass16(A1, j0 + 16, vcur, ri, packed + 8, beta[1], infl[1]);
-        if (!put32(j0, bb, packed)) return false;
+        if (!put32(j0, j0 >> 6, packed)) return false;
       }
       if (ri.bound) ucon = __fadd_ru(ucon, ucon_of(t, target - 1));
       return true;
     };
 
-    // one job of a hidden stage k >= 1: TMEM half hb holds columns [c0, c0 + nc) of Lambda'; write them as
-    // operand blocks of stage k - 1 (vectors of hidden layer k - 1 in buffer vcur). The next block's TMEM
-    // load is in flight while a block is processed.
+    // one job of a hidden stage k >= 1: TMEM half hb holds columns [c0, c0 + nc) of Lambda'; write this
+    // warp's chunks of them as operand blocks of stage k - 1 (vectors of hidden layer k - 1 in buffer
+    // vcur). The next 16 columns' TMEM load is in flight while 16 are processed.
     auto stage_job = [&](const RowInfo& ri, uint32_t hb, int c0, int nc, int vcur, float2 (&beta)[2],
                          float2 (&infl)[2]) -> bool {
       if (!wait_acc(hb)) return false;
-      const uint32_t tb = t_lane + hb * 256u + (uint32_t)(32 * cq);
-      const int nb = nc / 64, b0 = c0 >> 6;
+      const uint32_t tb = t_lane + hb * 256u;
+      const int cend = c0 + nc;
       float A0[16], A1[16];
       uint32_t packed[16];
-      tmem_ld16_async(tb, A0);
-      tmem_wait_ld();
-      tmem_regs_fence16(A0);
-      for (int bb = 0; bb < nb; ++bb) {
-        const int j0 = c0 + 64 * bb + 32 * cq;
-        tmem_ld16_async(tb + (uint32_t)(64 * bb + 16), A1);
+      int c = first_chunk(c0 >> 5);
+      if (32 * c < cend) {
+        tmem_ld16_async(tb + (uint32_t)(32 * c - c0), A0);
+        tmem_wait_ld();
+        tmem_regs_fence16(A0);
+      }
+      for (; 32 * c < cend; c += kTcColGroups) {
+        const int j0 = 32 * c;
+        const uint32_t col = (uint32_t)(j0 - c0);
+        const bool more = 32 * (c + kTcColGroups) < cend;
+        tmem_ld16_async(tb + col + 16u, A1);
         pass16(A0, j0, vcur, ri, packed, beta[0], infl[0]);
         tmem_wait_ld();
         tmem_regs_fence16(A1);
-        if (bb + 1 < nb) tmem_ld16_async(tb + (uint32_t)(64 * (bb + 1)), A0);
+        if (more) tmem_ld16_async(tb + col + (uint32_t)(32 * kTcColGroups), A0);
         pass16(A1, j0 + 16, vcur, ri, packed + 8, beta[1], infl[1]);
-        if (!put32(j0, b0 + bb, packed)) {
+        if (!put32(j0, j0 >> 6, packed)) {
           tmem_wait_ld();
           return false;
         }
-        if (bb + 1 < nb) {
+        if (more) {
           tmem_wait_ld();
           tmem_regs_fence16(A0);
         }
@@ -687,14 +709,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
         return true;
       };
       // the displacement-box columns of this warp's chunks are pulled into L1 first, so that only the
-      // first chunk waits for them
+      // first chunk waits for them (lanes 4 k .. 4 k + 3: both ends of the k-th chunk in dlo and dhi)
+      const int cf = first_chunk(c0 >> 5);
       {
-        const int c = lane >> 2;
-        const int j = c0 + 32 * cq + 64 * c + ((lane & 1) ? 31 : 0);
+        const int j = 32 * (cf + kTcColGroups * (lane >> 2)) + ((lane & 1) ? 31 : 0);
         if (j < c0 + nc) prefetch_l1(((lane & 2) ? dhi : dlo) + j);
       }
-      // 32-column chunks j0 = c0 + 32 cq + 64 c
-      for (int j0 = c0 + 32 * cq; j0 < c0 + nc; j0 += 64) {
+      for (int j0 = 32 * cf; j0 < c0 + nc; j0 += 32 * kTcColGroups) {
         float L0[32];
         tmem_ld32_async(tb + (uint32_t)(j0 - c0), L0);
         tmem_wait32(L0);
@@ -746,7 +767,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
       const uint32_t tb = t_lane + hb * 256u;
       const XRow xr = xrow(ri);
       const int cend = c0 + ((nc + 63) & ~63);
-      for (int j0 = c0 + 32 * cq; j0 < cend; j0 += 64) {
+      for (int j0 = 32 * first_chunk(c0 >> 5); j0 < cend; j0 += 32 * kTcColGroups) {
         uint32_t packed[16];
         if (j0 < n) {
           float L0[32], mlo[32], mhi[32];
@@ -770,7 +791,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     // (negated for upper rows)
     auto zprologue = [&](int t, const RowInfo& ri, float2& zacc) -> bool {
       const float sg = ri.neg ? -1.f : 1.f;
-      for (int j0 = 32 * cq; j0 < 64 * nzb; j0 += 64) {
+      for (int j0 = 32 * first_chunk(0); j0 < 64 * nzb; j0 += 32 * kTcColGroups) {
         uint32_t packed[16];
         float m[32];
         if (ri.valid && j0 < n) {
@@ -793,7 +814,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     auto conc_zono = [&](uint32_t hb, int c0, int nc, float2& sum) -> bool {
       if (!wait_acc(hb)) return false;
       const uint32_t tb = t_lane + hb * 256u;
-      for (int j0 = c0 + 32 * cq; j0 < c0 + nc; j0 += 64) {
+      for (int j0 = 32 * first_chunk(c0 >> 5); j0 < c0 + nc; j0 += 32 * kTcColGroups) {
         float v[32];
         tmem_ld32_async(tb + (uint32_t)(j0 - c0), v);
         tmem_wait32(v);
@@ -812,14 +833,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
     // combine the column groups of every row and write the bounds of an item
     auto finalize = [&](int t, int tile, const RowInfo& ri, float2 sum, const float2 (&beta)[2],
                         const float2 (&infl)[2], float ucon) -> bool {
-      float* st = stat + (r * 2 + cq) * 3;
-      st[0] = __fadd_rd(sum.x, sum.y);
-      st[1] = __fadd_rd(__fadd_rd(beta[0].x, beta[0].y), __fadd_rd(beta[1].x, beta[1].y));
-      st[2] = EPS ? __fadd_ru(__fadd_ru(infl[0].x, infl[0].y), __fadd_ru(infl[1].x, infl[1].y)) : 0.f;
+      // column groups 1.. leave their partial sums in stat; group 0 adds them to its own
+      const float own_tot = __fadd_rd(sum.x, sum.y);
+      const float own_beta = __fadd_rd(__fadd_rd(beta[0].x, beta[0].y), __fadd_rd(beta[1].x, beta[1].y));
+      const float own_infl = EPS ? __fadd_ru(__fadd_ru(infl[0].x, infl[0].y), __fadd_ru(infl[1].x, infl[1].y)) : 0.f;
+      if (cq > 0) {
+        float* st = stat + (r * (kTcColGroups - 1) + cq - 1) * 3;
+        st[0] = own_tot;
+        st[1] = own_beta;
+        st[2] = own_infl;
+      }
       if (!epi_sync()) return false;
       if (cq == 0 && ri.bound) {
-        const float* s0 = stat + r * 6;
-        const float tot = __fadd_rd(s0[0], s0[3]), bsum = __fadd_rd(s0[1], s0[4]), isum = __fadd_ru(s0[2], s0[5]);
+        const float* s1 = stat + r * (kTcColGroups - 1) * 3;
+        float tot = own_tot, bsum = own_beta, isum = own_infl;
+#pragma unroll
+        for (int g = 0; g < kTcColGroups - 1; ++g) {
+          tot = __fadd_rd(tot, s1[3 * g]);
+          bsum = __fadd_rd(bsum, s1[3 * g + 1]);
+          isum = __fadd_ru(isum, s1[3 * g + 2]);
+        }
         // lower bound of this row's (possibly negated) chain value; the inflation is inside beta
         const float val = __fsub_rd(__fadd_rd(tot, bsum), ucon);
         const bool nonfinite = !isfinite(val);
@@ -1118,9 +1151,14 @@ leb_status tc_prepare(Ctx& c) {
       (const void*)crown_tc_kernel<false, false, 0, true>,  (const void*)crown_tc_kernel<true, false, 0, true>,
       (const void*)crown_tc_kernel<true, true, 0, true>,    (const void*)crown_tc_kernel<false, false, 1, true>,
       (const void*)crown_tc_kernel<true, false, 1, true>,   (const void*)crown_tc_kernel<true, true, 1, true>};
-  for (const void* k : kernels)
+  for (const void* k : kernels) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) != cudaSuccess)
       return LEB_ERR_CUDA;
+    // the register split needs the launch budget it draws on: never launch a kernel compiled below it
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return LEB_ERR_CUDA;
+    if (fa.numRegs < kTcRegsLaunchMin) return LEB_ERR_UNSUPPORTED;
+  }
   return LEB_OK;
 }
 

@@ -153,6 +153,14 @@ __device__ __forceinline__ void tmem_regs_fence16(float v[16]) {
                  "+f"(v[15]));
 }
 
+// Per-warpgroup register budgets (setmaxnreg): every thread of a warpgroup executes the same call. The
+// increases draw on the registers the block was launched with, so a kernel's split must add up to at
+// most its launch budget (threads x registers of the compiled kernel).
+template <int N>
+__device__ __forceinline__ void regs_dec() { asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N)); }
+template <int N>
+__device__ __forceinline__ void regs_inc() { asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N)); }
+
 // Pulls the line holding p into L1 (no register result, no wait).
 __device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
