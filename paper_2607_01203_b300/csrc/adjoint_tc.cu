@@ -19,8 +19,9 @@
 // so the weights are the streamed A operand (128 neurons x 64 K tiles by TMA, a ring of kAdjStages) and
 // the per-row operand is the resident B operand (128 rows x K, K-major, 128-byte swizzle). TMEM holds
 // D[neuron][row]: lane = neuron inside an M-tile of 128, column = 128 * M-tile + row. Every epilogue
-// thread owns two neurons (M-tiles m and m + 2 of one TMEM lane), so every sum over chain rows is a
-// register sum, and the role of a row (lower, upper, Jacobian) is the same across a warp.
+// thread owns one neuron (16 epilogue warps: 4 M-tiles x 4 TMEM lane quarters, four per SM
+// sub-partition, with most of warpgroup 0's registers handed to them by setmaxnreg), so every sum over
+// chain rows is a register sum, and the role of a row (lower, upper, Jacobian) is the same across a warp.
 //
 // Output rows are carried in difference form: the lower and upper rows hold delta = lambda - lambda^J
 // (their operand lambda o s_sel - lambda^J o sigma'(z~) is formed in FP32 from the row and the Jacobian
@@ -42,8 +43,15 @@
 
 namespace leb {
 
-constexpr int kAdjEpiWarps = 8;                     // 2 M-tile pairs x 4 TMEM lane quarters
-constexpr int kAdjThreads = 32 * (2 + kAdjEpiWarps);
+constexpr int kAdjNU = 1;                           // neurons per epilogue thread (M-tiles m, m + 4 / kAdjNU)
+constexpr int kAdjEpiWarps = 16 / kAdjNU;           // M-tiles per thread set x 4 TMEM lane quarters
+constexpr int kAdjCtlWarps = 4;                     // warpgroup 0: TMA warp, MMA warp, two idle warps
+constexpr int kAdjThreads = 32 * (kAdjCtlWarps + kAdjEpiWarps);
+// Register split (setmaxnreg): warpgroup 0 keeps 32 registers a thread, the epilogue warpgroups take 112.
+// The increases draw on what the block was launched with, so the compiled kernel must have at least
+// kAdjRegsLaunchMin registers a thread (checked before any launch).
+constexpr int kAdjRegsCtl = 32, kAdjRegsEpi = 112;
+constexpr int kAdjRegsLaunchMin = (128 * kAdjRegsCtl + 32 * kAdjEpiWarps * kAdjRegsEpi + kAdjThreads - 1) / kAdjThreads;
 constexpr int kAdjStages = 6;                       // weight-tile ring
 constexpr int kAdjATile = 128 * 64 * 2;             // 128 neurons x 64 K x 2 bytes
 constexpr int kAdjBRegion = 128 * 512 * 2;          // 128 rows x K <= 512 x 2 bytes
@@ -152,6 +160,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
     }
   };
 
+  if (warp < kAdjCtlWarps) regs_dec<kAdjRegsCtl>();   // warpgroup 0: its four warps together
   if (warp == 0) {
     // ------------------------------------------------------------------ TMA producer (weight tiles)
     if (lane == 0) {
@@ -229,15 +238,17 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       mbar_wait(drain, 0);
     }
     __syncwarp();
-  } else {
+  } else if (warp >= kAdjCtlWarps) {
+    regs_inc<kAdjRegsEpi>();   // the epilogue warpgroups
     // ------------------------------------------------------------------ epilogue warps
-    // Each thread owns two neurons, nrn[0] in M-tile mt and nrn[1] = nrn[0] + 256 in M-tile mt + 2 (same
-    // TMEM lane), and works on both side by side.
+    // Each thread owns kAdjNU neurons: nrn[0] in M-tile mt and, with two, nrn[1] = nrn[0] + 256 in M-tile
+    // mt + 2 (same TMEM lane), worked on side by side. The code below is written for up to two; with one,
+    // every second-neuron branch is dead.
     const int q = warp & 3;                    // TMEM lane quarter
-    const int mt = (warp - 2) >> 2;            // 0 or 1
+    const int mt = (warp - kAdjCtlWarps) >> 2;   // M-tile of the thread's first neuron
     const int nrn0 = mt * 128 + q * 32 + lane;
     const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * 128);   // + 256 for nrn[1]
-    const int etid = threadIdx.x - 64;
+    const int etid = threadIdx.x - 32 * kAdjCtlWarps;
     __half* scr = a.scratch + (size_t)blockIdx.x * a.stot * 128;
     const int n = a.widths[0];
     const bool output = target == a.L - 1;
@@ -273,12 +284,12 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       *reinterpret_cast<uint4*>(Bop + b_off8(r0, j)) = q;
     };
 
-    // Pulls the thread's two neurons' entries of hidden layer hl's vectors (sL, sU, D and, with taus,
+    // Pulls the thread's neurons' entries of hidden layer hl's vectors (sL, sU, D and, with taus,
     // tL, tU) of timestep t into L1; issued before a wait for the tensor cores, whose work hides it.
     auto pf_vec = [&](int t, int hl, bool taus) {
       const int width = a.widths[hl + 1];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < kAdjNU; ++u) {
         const int j = nrn0 + 256 * u;
         if (j < width) {
           const long long o = (long long)t * a.H + a.hoff[hl] + j;
@@ -306,13 +317,13 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       // 8-row chunk (the row groups it touches, at most 4) are loaded while a chunk is written.
       {
         const int Kp = (Kt + 63) & ~63;
-        const int nu = nrn0 + 256 < Kp ? 2 : (nrn0 < Kp ? 1 : 0);   // neurons of this thread in the layer
+        const int nu = (kAdjNU == 2 && nrn0 + 256 < Kp) ? 2 : (nrn0 < Kp ? 1 : 0);   // neurons of this thread in the layer
         if (nu > 0) {
           bool live[2];
           float sl[2], su[2], dd[2];
           const float* wcol[2];
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
+          for (int u = 0; u < kAdjNU; ++u) {
             const int j = nrn0 + 256 * u;
             live[u] = u < nu && j < Kt;
             const long long o = (long long)t * a.H + a.hoff[target - 1] + (live[u] ? j : 0);
@@ -365,7 +376,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
         const int N = a.widths[k];             // neurons of hidden layer k-1 (rows of this product)
         const int Np = (N + 63) & ~63;
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kAdjNU; ++u) {
           const int j = nrn0 + 256 * u;
           if (j >= Np) continue;
           const bool live = j < N;
@@ -431,12 +442,12 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       // ---- G_{-1} from lambda_{-1} (neurons = inputs m < n) --------------------------------------------
       {
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
+        for (int u = 0; u < kAdjNU; ++u)
           if (nrn0 + 256 * u < n) prefetch_l1(a.radii + (long long)t * n + nrn0 + 256 * u);
         if (!wait_acc()) return false;
         const int np = (n + 63) & ~63;
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < kAdjNU; ++u) {
           const int j = nrn0 + 256 * u;
           if (j >= np) continue;
           const bool live = j < n;
@@ -479,14 +490,14 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
         operand_ready();
       }
       // ---- backward stages k = 0 .. target-1 -------------------------------------------------------
-      // The thread's two neurons go side by side through packed FP32x2 arithmetic.
+      // The thread's neurons go side by side.
       for (int k = 0; k < target; ++k) {
         pf_vec(t, k, true);
         if (!wait_acc()) return false;
         const int N = a.widths[k + 1];            // neurons of hidden layer k
         const bool last = k == target - 1;
         const int Np = (N + 63) & ~63;
-        const int nu = nrn0 + 256 < Np ? 2 : (nrn0 < Np ? 1 : 0);   // neurons of this thread in the layer
+        const int nu = (kAdjNU == 2 && nrn0 + 256 < Np) ? 2 : (nrn0 < Np ? 1 : 0);   // neurons of this thread in the layer
         if (nu > 0) {
           bool live[2];
           long long o[2];
@@ -494,7 +505,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
           const __half* lrow[2];
           const float* wcol[2];
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
+          for (int u = 0; u < kAdjNU; ++u) {
             const int j = nrn0 + 256 * u;
             live[u] = u < nu && j < N;
             o[u] = (long long)t * a.H + a.hoff[k] + (live[u] ? j : 0);
@@ -605,7 +616,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
           const float gsl[2] = {SL.x, SL.y}, gsu[2] = {SU.x, SU.y}, gtl[2] = {TL.x, TL.y}, gtu[2] = {TU.x, TU.y};
           const float gd[2] = {GD.x, GD.y};
 #pragma unroll
-          for (int u = 0; u < 2; ++u)
+          for (int u = 0; u < kAdjNU; ++u)
             if (live[u]) {
               if (gsl[u] != 0.f) atomicAdd(a.gsL + o[u], gsl[u] * gscale);
               if (gsu[u] != 0.f) atomicAdd(a.gsU + o[u], gsu[u] * gscale);
@@ -727,6 +738,10 @@ leb_status adj_tc_prepare(Ctx& c) {
   if (cudaDeviceSynchronize() != cudaSuccess) return LEB_ERR_CUDA;
   if (cudaFuncSetAttribute(adjoint_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdjSmem) != cudaSuccess)
     return LEB_ERR_CUDA;
+  // the register split needs the launch budget it draws on: never launch a kernel compiled below it
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, adjoint_tc_kernel) != cudaSuccess) return LEB_ERR_CUDA;
+  if (fa.numRegs < kAdjRegsLaunchMin) return LEB_ERR_UNSUPPORTED;
   return LEB_OK;
 }
 
