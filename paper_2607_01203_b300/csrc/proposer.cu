@@ -104,7 +104,10 @@ struct PtEpi {
   int ldfT;
 };
 
-// kpb: K blocks (of 64) per K part; blockIdx.z takes blocks [z kpb, min(nK, (z + 1) kpb)).
+// kpb: K blocks (of 64) per K part; blockIdx.z takes blocks [z kpb, min(nK, (z + 1) kpb)). kTrain: the
+// training instance (masks, transposed and K-part outputs); the inference instance keeps only the bias,
+// ReLU, the output's standardisation and offsets and the row-major outputs.
+template <bool kTrain>
 __global__ void __launch_bounds__(128, 2) prop_tc_gemm_kernel(const __grid_constant__ CUtensorMap amap,
                                                               const __grid_constant__ CUtensorMap wmap, int M, int N,
                                                               int K, int nchunk, int stages, int kpb, const PtEpi e) {
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(128, 2) prop_tc_gemm_kernel(const __grid_const
     if (row >= M) continue;
     const int nc = n0 + c0;            // global column of v[0]
     float mk[16];
-    if (e.mask) {
+    if (kTrain && e.mask) {
       const uint4* src = reinterpret_cast<const uint4*>(e.mask + (long long)row * e.ldm + nc);
       const uint4 q0 = src[0], q1 = src[1];
       const uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(128, 2) prop_tc_gemm_kernel(const __grid_const
     for (int j = 0; j < 16; ++j) {
       float x = ok ? v[j] + (e.bias ? e.bias[nc + j] : 0.f) : __int_as_float(0x7fc00000);
       if (e.relu) x = fmaxf(x, 0.f);
-      if (e.mask) x = mk[j] > 0.f ? x : 0.f;
+      if (kTrain && e.mask) x = mk[j] > 0.f ? x : 0.f;
       if (e.omean) x = fmaf(x, e.ostd[nc + j], e.omean[nc + j]);   // back to the bounds' units
       if (e.offset) x += e.offset[nc + j];
       v[j] = x;
@@ -214,16 +217,16 @@ __global__ void __launch_bounds__(128, 2) prop_tc_gemm_kernel(const __grid_const
       dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
       dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
     }
-    if (e.outbT) {
+    if (kTrain && e.outbT) {
 #pragma unroll
       for (int j = 0; j < 16; ++j) e.outbT[(long long)(nc + j) * e.ldT + row] = __float2bfloat16_rn(v[j]);
     }
     if (e.outf) {
-      float4* dst = reinterpret_cast<float4*>(e.outf + blockIdx.z * e.zstride + (long long)row * e.ldf + nc);
+      float4* dst = reinterpret_cast<float4*>(e.outf + (kTrain ? blockIdx.z * e.zstride : 0) + (long long)row * e.ldf + nc);
 #pragma unroll
       for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
     }
-    if (e.outfT) {
+    if (kTrain && e.outfT) {
 #pragma unroll
       for (int j = 0; j < 16; ++j) e.outfT[(long long)(nc + j) * e.ldfT + row] = v[j];
     }
@@ -731,7 +734,9 @@ static bool setup_tc(leb_proposer p) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return true;
   }
-  if (cudaFuncSetAttribute(prop_tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPtSmem) != cudaSuccess)
+  if (cudaFuncSetAttribute(prop_tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPtSmem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(prop_tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPtSmem) != cudaSuccess)
     return true;
   p->tc = true;
   return true;
@@ -798,7 +803,7 @@ static bool forward_tc(leb_proposer p, int B, const float* X, float* ws, float* 
     e.outf = of;
     e.ldf = N;
     const int np = N / p->parts[i], ns = pt_stages(np);
-    prop_tc_gemm_kernel<<<dim3(tiles, p->parts[i]), 128, pt_smem(np, ns), s>>>(am, p->wmap[i], B, np, K, 1, ns,
+    prop_tc_gemm_kernel<false><<<dim3(tiles, p->parts[i]), 128, pt_smem(np, ns), s>>>(am, p->wmap[i], B, np, K, 1, ns,
                                                                                 (K + 63) / 64, e);
   };
   layer(0, m0, H, n_in, 1, H1, nullptr, nullptr, nullptr, nullptr);
@@ -862,7 +867,8 @@ static bool train_tc(leb_proposer p, int B, const float* X, const float* Yt, flo
   auto gemm_tc = [&](const CUtensorMap& am, const CUtensorMap& bm, int M, int N, int parts, int K, int kpb, int nz,
                      const PtEpi& e) {
     const int n = N / parts, ns = pt_stages(n);
-    prop_tc_gemm_kernel<<<dim3((M + 127) / 128, parts, nz), 128, pt_smem(n, ns), s>>>(am, bm, M, n, K, 1, ns, kpb, e);
+    prop_tc_gemm_kernel<true><<<dim3((M + 127) / 128, parts, nz), 128, pt_smem(n, ns), s>>>(am, bm, M, n, K, 1, ns, kpb,
+                                                                                             e);
   };
   const int kall = (H + 63) / 64;
   {   // forward
