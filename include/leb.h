@@ -173,7 +173,8 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
                       const leb_options* opt, void* workspace, size_t ws_bytes, int* dev_flags, void* stream);
 
 /* ---- adjoint of the bounds (differentiable LEBs, Sec. IV-D) ------------------------------------ */
-/* Box sets centred at the nominal only (set->center NULL; other sets: LEB_ERR_UNSUPPORTED). batch: NULL or
+/* Box sets centred at the nominal (set->center NULL; a box with a centre: leb_bounds_backward_box; other
+ * sets: LEB_ERR_UNSUPPORTED, a centre without a centre gradient: LEB_ERR_INVALID_ARG). batch: NULL or
  * trajectories of any horizons (traj_offsets; each timestep's bound is independent, so the gradient is
  * that of the timesteps in a row); chains of uneven length (traj_nquads) return LEB_ERR_UNSUPPORTED.
  * Given g_rlo = dL/dr_lo and g_rhi = dL/dr_hi [T, n_x], writes g_x [T, n_x], g_u [T, n_u],
@@ -183,6 +184,17 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
 leb_status leb_bounds_backward(leb_handle h, const leb_batch* batch, int T, const float* x_nom, const float* u_nom,
                                const leb_set* set, const float* g_rlo, const float* g_rhi, float* g_x, float* g_u,
                                float* g_radii, void* workspace, size_t ws_bytes, int* dev_flags, void* stream);
+/* The adjoint for box sets with or without a centre (Sec. IV-D; the tube of Sec. V-A is centred off the
+ * nominal). With set->center [T, n] the set is the box center +- radii hulled with the nominal, i.e. the
+ * displacement box dlo = min(center - radii, alpha~) - alpha~, dhi = max(center + radii, alpha~) - alpha~,
+ * and g_center [T, n] (device, written; required) receives dL/d center; where the nominal lies outside
+ * the box on a side, that side's end is the nominal and moves with neither centre nor radius. With
+ * set->center NULL it is leb_bounds_backward (g_center may be NULL). MLP handles (Thms. 2-3); quad-chain
+ * handles take centred sets only (a centre: LEB_ERR_UNSUPPORTED). Otherwise as leb_bounds_backward. */
+leb_status leb_bounds_backward_box(leb_handle h, const leb_batch* batch, int T, const float* x_nom,
+                                   const float* u_nom, const leb_set* set, const float* g_rlo, const float* g_rhi,
+                                   float* g_x, float* g_u, float* g_radii, float* g_center, void* workspace,
+                                   size_t ws_bytes, int* dev_flags, void* stream);
 /* The same adjoint from the forward pass's saved state: the workspace must hold the state of the last
  * leb_bounds call on this handle with the same T, x_nom, u_nom and set (box, centred at the nominal,
  * no leb_batch), with no other call on that workspace in between. FP32 MLP handles skip the recompute

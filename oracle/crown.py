@@ -253,29 +253,45 @@ def to_t(x) -> torch.Tensor:
     return torch.as_tensor(x, dtype=F64)
 
 
-def box_remainder(Ws, bs, act, x_nom, u_nom, radii, residual=True, intermediate="crown"):
-    """One timestep with a box set centred at the nominal: Thm. 3 bounds and [A B]. FP64 numpy out."""
+def _box_hull(a, rho, center):
+    """The box center +- rho hulled with the nominal a (the set of Thm. 3 must contain it; Sec. V-A's tube
+    is centred off the nominal): [min(c - rho, a), max(c + rho, a)]; the box a +- rho without a centre."""
+    if center is None:
+        return a - rho, a + rho
+    return torch.minimum(center - rho, a), torch.maximum(center + rho, a)
+
+
+def box_remainder(Ws, bs, act, x_nom, u_nom, radii, residual=True, intermediate="crown", center=None):
+    """One timestep with a box set (centred at the nominal, or at ``center`` and hulled with the nominal):
+    Thm. 3 bounds and [A B]. FP64 numpy out."""
     Ws_t = [to_t(W) for W in Ws]
     bs_t = [to_t(b) for b in bs]
     a = torch.cat([to_t(x_nom), to_t(u_nom)])
     rho = to_t(radii)
     with torch.no_grad():
-        r_lo, r_hi, J, _ = remainder_bounds(Ws_t, bs_t, act, a, a - rho, a + rho, residual, intermediate)
+        lo, hi = _box_hull(a, rho, None if center is None else to_t(center))
+        r_lo, r_hi, J, _ = remainder_bounds(Ws_t, bs_t, act, a, lo, hi, residual, intermediate)
     return r_lo.numpy(), r_hi.numpy(), J.numpy()
 
 
-def box_remainder_vjp(Ws, bs, act, x_nom, u_nom, radii, g_lo, g_hi, residual=True):
-    """Gradient of sum(g_lo * r_lo + g_hi * r_hi) w.r.t. (x~, u~, radii) for a box set at the nominal."""
+def box_remainder_vjp(Ws, bs, act, x_nom, u_nom, radii, g_lo, g_hi, residual=True, center=None):
+    """Gradient of sum(g_lo * r_lo + g_hi * r_hi) w.r.t. (x~, u~, radii) for a box set at the nominal, and
+    also w.r.t. the centre for a box set at ``center`` (then a 4-tuple)."""
     Ws_t = [to_t(W) for W in Ws]
     bs_t = [to_t(b) for b in bs]
     x = to_t(x_nom).requires_grad_(True)
     u = to_t(u_nom).requires_grad_(True)
     rho = to_t(radii).requires_grad_(True)
+    c = None if center is None else to_t(center).requires_grad_(True)
     a = torch.cat([x, u])
-    r_lo, r_hi, _, _ = remainder_bounds(Ws_t, bs_t, act, a, a - rho, a + rho, residual)
+    lo, hi = _box_hull(a, rho, c)
+    r_lo, r_hi, _, _ = remainder_bounds(Ws_t, bs_t, act, a, lo, hi, residual)
     L = (to_t(g_lo) * r_lo).sum() + (to_t(g_hi) * r_hi).sum()
-    gx, gu, gr = torch.autograd.grad(L, [x, u, rho])
-    return gx.numpy(), gu.numpy(), gr.numpy()
+    if c is None:
+        gx, gu, gr = torch.autograd.grad(L, [x, u, rho])
+        return gx.numpy(), gu.numpy(), gr.numpy()
+    gx, gu, gr, gc = torch.autograd.grad(L, [x, u, rho, c])
+    return gx.numpy(), gu.numpy(), gr.numpy(), gc.numpy()
 
 
 def zono_hull_nominal(nominal: torch.Tensor, c: torch.Tensor, G: torch.Tensor):

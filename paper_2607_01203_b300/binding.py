@@ -64,7 +64,7 @@ EXPORTS = [
     "leb_refine_nominal_pgd", "leb_refine_workspace_size", "leb_selftest_tan_sec", "leb_tube", "leb_bounds_backward_saved",
     "leb_proposer_state_size", "leb_proposer_save_state", "leb_proposer_load_state", "leb_selftest_wait_timeout",
     "leb_selftest_set_wait_limit", "leb_proposer_calibrate", "leb_proposer_get_offset",
-    "leb_set_partition_recentred", "leb_set_path_order_perm",
+    "leb_set_partition_recentred", "leb_set_path_order_perm", "leb_bounds_backward_box",
 ]
 
 
@@ -93,6 +93,8 @@ def lib():
         L.leb_bounds_backward.argtypes = [vp, C.POINTER(BatchDesc), i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp, vp,
                                           vp, vp, sz, vp, vp]
         L.leb_bounds_backward_saved.argtypes = L.leb_bounds_backward.argtypes
+        L.leb_bounds_backward_box.argtypes = [vp, C.POINTER(BatchDesc), i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp,
+                                              vp, vp, vp, vp, sz, vp, vp]
         L.leb_zonotope_map.argtypes = [vp, vp, C.c_longlong, C.c_float, vp, vp, vp]
         L.leb_autotune.argtypes = [vp, i32, i32, i32, C.c_char_p, vp, sz, vp]
         L.leb_plan_string.argtypes = [vp, C.c_char_p, sz]
@@ -311,10 +313,12 @@ class Handle:
                 o["B"] = o["B"].view(T, self.n_x, self.n_u)
         return o
 
-    def bounds_backward(self, x_nom, u_nom, radii, g_rlo, g_rhi, saved: bool = False, traj_offsets=None):
+    def bounds_backward(self, x_nom, u_nom, radii, g_rlo, g_rhi, saved: bool = False, traj_offsets=None,
+                        center=None):
         """dL/d(x~, u~, radii) (leb_bounds_backward). saved: reuse the state the last ``bounds`` call of
         this handle left in its workspace (same inputs, box set; leb_bounds_backward_saved). traj_offsets:
-        the batch's trajectories (optional; the gradient does not depend on them)."""
+        the batch's trajectories (optional; the gradient does not depend on them). center: the box's centre
+        [T, n] (leb_bounds_backward_box); then dL/d center comes back too, before the flags."""
         dev = x_nom.device
         T = int(x_nom.shape[0])
         f32 = dict(device=dev, dtype=torch.float32)
@@ -322,10 +326,17 @@ class Handle:
         g_u = torch.empty(T, self.n_u, **f32)
         g_r = torch.empty(T, self.n_x + self.n_u, **f32)
         flags = torch.zeros(1, device=dev, dtype=torch.int32)
-        sd = self.set_desc(radii=radii)
+        sd = self.set_desc(radii=radii, center=center)
         ws = self.workspace(T, dev)
-        fn = lib().leb_bounds_backward_saved if saved else lib().leb_bounds_backward
         bd = self.batch_desc(traj_offsets)
+        if center is not None:
+            g_c = torch.empty(T, self.n_x + self.n_u, **f32)
+            check(lib().leb_bounds_backward_box(self.h, None if bd is None else C.byref(bd), T, _ptr(x_nom), _ptr(u_nom),
+                                                C.byref(sd), _ptr(g_rlo.contiguous()), _ptr(g_rhi.contiguous()),
+                                                _ptr(g_x), _ptr(g_u), _ptr(g_r), _ptr(g_c), _ptr(ws), ws.numel(),
+                                                _ptr(flags), _stream()), "leb_bounds_backward_box")
+            return g_x, g_u, g_r, g_c, flags
+        fn = lib().leb_bounds_backward_saved if saved else lib().leb_bounds_backward
         check(fn(self.h, None if bd is None else C.byref(bd), T, _ptr(x_nom), _ptr(u_nom), C.byref(sd),
                  _ptr(g_rlo.contiguous()), _ptr(g_rhi.contiguous()),
                  _ptr(g_x), _ptr(g_u), _ptr(g_r), _ptr(ws), ws.numel(), _ptr(flags), _stream()), "leb_bounds_backward")

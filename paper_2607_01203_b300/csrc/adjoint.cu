@@ -1,18 +1,21 @@
-// Adjoint of the CROWN remainder bound (differentiable LEBs, Sec. IV-D): dL/d(x~, u~, radii) for
-// L = sum g_lo r_lo + g_hi r_hi, box sets centred at the nominal. FP32 on CUDA cores.
+// Adjoint of the CROWN remainder bound (differentiable LEBs, Sec. IV-D): dL/d(x~, u~, radii[, centre]) for
+// L = sum g_lo r_lo + g_hi r_hi, box sets (centred at the nominal or hulled with it). FP32 on CUDA cores.
 //
 // The bound is a piecewise-smooth function of the nominal and the radii; its gradient is taken with the
 // relaxation cases fixed at the evaluation point (as automatic differentiation of the same algorithm
 // would). Reverse mode, top-down:
 //   1. forward recompute (nominal pass, every hidden layer's bounds and relaxation lines);
 //   2. output chains backward: for each output row the chain lambda_{T-1} = W_T row, a_k = lambda_k o s_k,
-//      lambda_{k-1} = a_k W_k is recomputed in shared memory, then G_{-1} = dr/dlambda_{-1} (from
-//      -|M| rho with M = lambda_{-1} - J), Ga_k = G_{k-1} W_k^T, G_k = Ga_k o s_k + g tau_k, and per neuron
+//      lambda_{k-1} = a_k W_k is recomputed in shared memory, then G_{-1} = dr/dlambda_{-1} (the end of the
+//      displacement box [dlo, dhi] each sign of M = lambda_{-1} - J takes), Ga_k = G_{k-1} W_k^T,
+//      G_k = Ga_k o s_k + g tau_k, and per neuron
 //      d/ds_sel += Ga_k lambda_k, d/dtau_sel += g lambda_k, d/dD += Ga_k lambda^J_k (Jacobian rows);
 //   3. for each hidden layer i = L-2 .. 0: derivatives of its lines w.r.t. (l_i, u_i, z~_i) (slope rules,
 //      envelope theorem for the offsets, implicit differentiation of the tangent points), then the same
-//      chain backward for the chains that produced l_i, u_i (layer 0: the interval product -|W_0| rho);
-//   4. the nominal pass backward: dz~_{i-1} += (W_i^T dz~_i) o sigma'(z~_{i-1}), d alpha~ = W_0^T dz~_0.
+//      chain backward for the chains that produced l_i, u_i (layer 0: the interval product of W_0 and the
+//      box); every chain's concretisation also gives the gradients of the box's ends dlo, dhi;
+//   4. the nominal pass backward: dz~_{i-1} += (W_i^T dz~_i) o sigma'(z~_{i-1}), d alpha~ = W_0^T dz~_0,
+//      and the box's ends back to the radii (and the centre and the nominal, for a box off the nominal).
 #include <algorithm>
 #include <cmath>
 
@@ -39,10 +42,10 @@ struct ChainBwdArgs {
   int soff[kMaxLayers + 1];  // offset of lambda_k (k = target-1 .. -1) in the per-row store, index k + 1
   int stot;
   const float *sL, *tL, *sU, *tU, *D;
-  const float* radii;        // [T, n]
+  const float *dlo, *dhi;    // [T, n] the displacement box Delta = X - alpha~ (dlo <= 0 <= dhi)
   const float *g_lo, *g_hi;  // output target
   const float *gl, *gu;      // intermediate target: gradients of its lower / upper bounds ([T, H])
-  float *gsL, *gsU, *gtL, *gtU, *gD, *grho;
+  float *gsL, *gsU, *gtL, *gtU, *gD, *gdlo, *gdhi;
 };
 
 __device__ __forceinline__ float sgnf(float v) { return v > 0.f ? 1.f : (v < 0.f ? -1.f : 0.f); }
@@ -153,31 +156,40 @@ __global__ void __launch_bounds__(256, 1) mlp_chain_bwd_kernel(ChainBwdArgs a) {
     __syncthreads();
     block_gemm<CG>(Ab, maxw, Kw, Nw, a.m.W[k], false, Bt, maxw, Ls + a.soff[k], a.stot);
   }
-  // ---- G_{-1}: derivative of each row's bound w.r.t. lambda_{-1}; direct radius terms -------------
+  // ---- G_{-1}: derivative of each row's bound w.r.t. lambda_{-1}; direct terms of the box ends ------
+  // A lower bound takes min over Delta in [dlo, dhi] of M Delta = sum_m (M_m > 0 ? M_m dlo_m : M_m dhi_m),
+  // an upper bound the max (dhi where M_m > 0); at M_m = 0 the derivative is the mean of both sides.
   const int n = a.n;
   for (int e = threadIdx.x; e < kBwdRB * maxw; e += blockDim.x) Gb[e] = 0.f;
   __syncthreads();
   const float* Lm1 = Ls + a.soff[0];
   for (int m = threadIdx.x; m < n; m += blockDim.x) {
-    const float rho = a.radii[(long long)t * n + m];
-    float grho = 0.f;
+    const float dl = a.dlo[(long long)t * n + m], dh = a.dhi[(long long)t * n + m];
+    float gdl = 0.f, gdh = 0.f;
     for (int r = 0; r < nrows; ++r) {
       const int role = (row0 + r) % a.nroles;
       float G = 0.f;
       if (role != 2) {
         const float lam = Lm1[r * a.stot + m];
         const float M = output ? lam - Lm1[(r - role + 2) * a.stot + m] : lam;
-        // lower: -|M| rho, upper: +|M| rho
-        const float sg = role == 0 ? -1.f : 1.f;
-        G = sg * gw[r] * sgnf(M) * rho;
-        grho += sg * gw[r] * fabsf(M);
+        const float pos = role == 0 ? dl : dh, neg = role == 0 ? dh : dl;   // the end a positive M takes
+        G = gw[r] * (M > 0.f ? pos : (M < 0.f ? neg : 0.5f * (dl + dh)));
+        const float mp = fmaxf(M, 0.f), mn = fminf(M, 0.f);
+        if (role == 0) {
+          gdl = fmaf(gw[r], mp, gdl);
+          gdh = fmaf(gw[r], mn, gdh);
+        } else {
+          gdh = fmaf(gw[r], mp, gdh);
+          gdl = fmaf(gw[r], mn, gdl);
+        }
       }
       Gb[r * maxw + m] = G;
     }
     if (output)
       for (int r = 0; r < nrows; ++r)
         if ((row0 + r) % 3 == 2) Gb[r * maxw + m] = -(Gb[(r - 2) * maxw + m] + Gb[(r - 1) * maxw + m]);
-    atomicAdd(a.grho + (long long)t * n + m, grho);
+    atomicAdd(a.gdlo + (long long)t * n + m, gdl);
+    atomicAdd(a.gdhi + (long long)t * n + m, gdh);
   }
   __syncthreads();
   // ---- backward through the stages ----------------------------------------------------------------
@@ -354,25 +366,46 @@ __global__ void __launch_bounds__(256) bwd_gemm_kernel(int T, int K, int N, cons
   }
 }
 
-__global__ void gl_minus_gu_kernel(long long total, int width, int ld, int off, const float* gl, const float* gu,
-                                   float* out) {
+// (gl, gu) -> (gl + gu, gl - gu) in place: the layer-0 bounds' gradients split into the parts that meet
+// W_0 and |W_0| (l = z~ - e + W0+ dlo + W0- dhi, u = z~ + e + W0+ dhi + W0- dlo, W0+- = (W_0 +- |W_0|) / 2)
+__global__ void gl_gu_sum_diff_kernel(long long total, int width, int ld, int off, float* gl, float* gu) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     const long long t = e / width;
     const int j = (int)(e - t * width);
-    out[t * width + j] = gu[t * ld + off + j] - gl[t * ld + off + j];
+    const long long o = t * ld + off + j;
+    const float l = gl[o], u = gu[o];
+    gl[o] = l + u;
+    gu[o] = l - u;
   }
 }
 
-__global__ void split_alpha_kernel(int T, int n_x, int n_u, const float* ga, const float* grho, float* gx, float* gu,
-                                   float* gr) {
+// The box set's gradients from those of the displacement box's ends and of the nominal. Centred sets
+// (center NULL): dlo = -rho, dhi = rho. Off-centre sets: dlo = min(c - rho, a) - a and dhi = max(c + rho,
+// a) - a, so where c - rho < a (the nominal inside the box's lower side) dlo moves with c and against rho
+// and a, and likewise dhi where c + rho > a.
+__global__ void box_grad_kernel(int T, int n_x, int n_u, const float* ga, const float* gdlo, const float* gdhi,
+                                const float* center, const float* radii, const float* anom, float* gx, float* gu,
+                                float* gr, float* gc) {
   const int n = n_x + n_u;
   const long long total = (long long)T * n;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     const long long t = e / n;
     const int m = (int)(e - t * n);
-    if (m < n_x) gx[t * n_x + m] = ga[e];
-    else gu[t * n_u + m - n_x] = ga[e];
-    gr[e] = grho[e];
+    float g_a = ga[e], g_r, g_c = 0.f;
+    if (!center) {
+      g_r = gdhi[e] - gdlo[e];
+    } else {
+      const float c = center[e], r = radii[e], a = anom[e];
+      const float il = __fsub_rd(c, r) < a ? 1.f : 0.f, ih = __fadd_ru(c, r) > a ? 1.f : 0.f;
+      const float pl = il * gdlo[e], ph = ih * gdhi[e];
+      g_c = pl + ph;
+      g_r = ph - pl;
+      g_a -= g_c;
+      gc[e] = g_c;
+    }
+    if (m < n_x) gx[t * n_x + m] = g_a;
+    else gu[t * n_u + m - n_x] = g_a;
+    gr[e] = g_r;
   }
 }
 
@@ -386,8 +419,8 @@ size_t bwd_chain_smem(const Ctx& c, int target, int* stot_out) {
   return ((size_t)kBwdRB * stot + 2 * (size_t)kBwdRB * maxw + (size_t)kBwdKC * maxw + kBwdRB) * sizeof(float);
 }
 
-static leb_status launch_chain_bwd(const Ctx& c, int T, int target, const MlpWs& L, float* ws, const float* radii,
-                                   const float* g_lo, const float* g_hi, cudaStream_t s) {
+static leb_status launch_chain_bwd(const Ctx& c, int T, int target, const MlpWs& L, float* ws, const float* g_lo,
+                                   const float* g_hi, cudaStream_t s) {
   const MlpModel& m = c.mlp;
   ChainBwdArgs a{};
   a.m.L = m.L;
@@ -415,7 +448,8 @@ static leb_status launch_chain_bwd(const Ctx& c, int T, int target, const MlpWs&
   a.sU = ws + L.sU;
   a.tU = ws + L.tU;
   a.D = ws + L.D;
-  a.radii = radii;
+  a.dlo = ws + L.dlo;
+  a.dhi = ws + L.dhi;
   a.g_lo = g_lo;
   a.g_hi = g_hi;
   a.gl = ws + L.gl;
@@ -425,7 +459,8 @@ static leb_status launch_chain_bwd(const Ctx& c, int T, int target, const MlpWs&
   a.gtL = ws + L.gtL;
   a.gtU = ws + L.gtU;
   a.gD = ws + L.gD;
-  a.grho = ws + L.grho;
+  a.gdlo = ws + L.gdlo;
+  a.gdhi = ws + L.gdhi;
   const size_t smem = bwd_chain_smem(c, target, nullptr);
   dim3 grid(T, (a.rows_total + kBwdRB - 1) / kBwdRB);
   timer_begin(c, s, "mlp_chain_bwd_kernel");
@@ -444,8 +479,8 @@ static leb_status launch_chain_bwd(const Ctx& c, int T, int target, const MlpWs&
 }
 
 leb_status mlp_bounds_backward(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set,
-                               const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_rad, void* ws_base,
-                               int* flags, cudaStream_t s, bool saved) {
+                               const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_rad, float* g_ctr,
+                               void* ws_base, int* flags, cudaStream_t s, bool saved) {
   const MlpModel& m = c.mlp;
   // reduced-precision handles with a tensor-core adjoint: chains on the tensor cores, and the hidden
   // bounds recomputed by the tensor-core chains without their rounding inflation, i.e. the algorithm's
@@ -469,10 +504,10 @@ leb_status mlp_bounds_backward(Ctx& c, int T, const float* x_nom, const float* u
   const size_t TH = (size_t)T * L.H;
   for (size_t off : {L.gsL, L.gsU, L.gtL, L.gtU, L.gD, L.gz, L.gl, L.gu})
     if (cudaMemsetAsync(ws + off, 0, TH * sizeof(float), s) != cudaSuccess) return LEB_ERR_CUDA;
-  if (cudaMemsetAsync(ws + L.grho, 0, (size_t)T * n * sizeof(float), s) != cudaSuccess) return LEB_ERR_CUDA;
+  for (size_t off : {L.gdlo, L.gdhi})
+    if (cudaMemsetAsync(ws + off, 0, (size_t)T * n * sizeof(float), s) != cudaSuccess) return LEB_ERR_CUDA;
   auto chain = [&](int target, const float* glo, const float* ghi) {
-    return tc ? adj_tc_chain(c, T, target, L, ws, set->radii, glo, ghi, flags, s)
-              : launch_chain_bwd(c, T, target, L, ws, set->radii, glo, ghi, s);
+    return tc ? adj_tc_chain(c, T, target, L, ws, glo, ghi, flags, s) : launch_chain_bwd(c, T, target, L, ws, glo, ghi, s);
   };
   // 2. output chains
   st = chain(m.L - 1, g_rlo, g_rhi);
@@ -489,11 +524,16 @@ leb_status mlp_bounds_backward(Ctx& c, int T, const float* x_nom, const float* u
       st = chain(i, nullptr, nullptr);
       if (st != LEB_OK) return st;
     } else {
-      // layer 0: l = z~ - |W_0| rho, u = z~ + |W_0| rho  ->  d rho += |W_0|^T (g_u - g_l)
-      gl_minus_gu_kernel<<<blocks, 256, 0, s>>>((long long)T * width, width, L.H, L.hoff[0], ws + L.gl, ws + L.gu,
-                                                ws + L.gscr);
+      // layer 0: l = z~ - e + W0+ dlo + W0- dhi, u = z~ + e + W0+ dhi + W0- dlo (W0+- = (W_0 +- |W_0|) / 2)
+      //   -> d dlo += ((g_l + g_u) W_0 + (g_l - g_u) |W_0|) / 2, d dhi += ((g_l + g_u) W_0 - (g_l - g_u) |W_0|) / 2
+      gl_gu_sum_diff_kernel<<<blocks, 256, 0, s>>>((long long)T * width, width, L.H, L.hoff[0], ws + L.gl, ws + L.gu);
       dim3 grid((T + 63) / 64, (n + 63) / 64);
-      bwd_gemm_kernel<<<grid, 256, 0, s>>>(T, width, n, ws + L.gscr, width, m.W[0], 1, 1.f, nullptr, 0, ws + L.grho, n, 1);
+      const float* gs = ws + L.gl + L.hoff[0];
+      const float* gd = ws + L.gu + L.hoff[0];
+      bwd_gemm_kernel<<<grid, 256, 0, s>>>(T, width, n, gs, L.H, m.W[0], 0, 0.5f, nullptr, 0, ws + L.gdlo, n, 1);
+      bwd_gemm_kernel<<<grid, 256, 0, s>>>(T, width, n, gd, L.H, m.W[0], 1, 0.5f, nullptr, 0, ws + L.gdlo, n, 1);
+      bwd_gemm_kernel<<<grid, 256, 0, s>>>(T, width, n, gs, L.H, m.W[0], 0, 0.5f, nullptr, 0, ws + L.gdhi, n, 1);
+      bwd_gemm_kernel<<<grid, 256, 0, s>>>(T, width, n, gd, L.H, m.W[0], 1, -0.5f, nullptr, 0, ws + L.gdhi, n, 1);
     }
   }
   // 4. nominal pass backward: dz_{i-1} += (dz_i W_i) o D_{i-1}; d alpha = dz_0 W_0
@@ -507,7 +547,8 @@ leb_status mlp_bounds_backward(Ctx& c, int T, const float* x_nom, const float* u
     bwd_gemm_kernel<<<grid, 256, 0, s>>>(T, m.widths[1], n, ws + L.gz, L.H, m.W[0], 0, 1.f, nullptr, 0, ws + L.gscr, n, 0);
   }
   const int blocks = (int)std::min<long long>(((long long)T * n + 255) / 256, 148LL * 32);
-  split_alpha_kernel<<<blocks, 256, 0, s>>>(T, c.n_x, c.n_u, ws + L.gscr, ws + L.grho, g_x, g_u, g_rad);
+  box_grad_kernel<<<blocks, 256, 0, s>>>(T, c.n_x, c.n_u, ws + L.gscr, ws + L.gdlo, ws + L.gdhi, set->center,
+                                         set->radii, ws + L.anom, g_x, g_u, g_rad, g_ctr);
   return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
 }
 

@@ -6,8 +6,9 @@
 //   1. recomputes the chain forward:  lambda_{k-1} = (lambda_k o s_k) W_k,  k = target-1 .. 0,
 //      starting from lambda_{target-1} = rows of W_target, keeping each lambda_k (k >= 0) in a per-CTA
 //      scratch area (it stays in L2);
-//   2. forms G_{-1} = dr / d lambda_{-1} from -|M| rho (lower) and +|M| rho (upper), M = lambda_{-1}
-//      minus the Jacobian row of the same state for output rows, and the direct radius gradient;
+//   2. forms G_{-1} = dr / d lambda_{-1}: a lower bound takes min over the displacement box [dlo, dhi] of
+//      M Delta (M_m > 0 at dlo_m, M_m < 0 at dhi_m), an upper bound the max, M = lambda_{-1} minus the
+//      Jacobian row of the same state for output rows; and the direct gradients of the box's ends;
 //   3. runs the chain backward:  Ga_k = G_{k-1} W_k^T,  G_k = Ga_k o s_k + g tau_k,  summing per neuron
 //      over the chain rows d/ds_sel += Ga_k lambda_k, d/dtau_sel += g lambda_k (lower/upper rows) and
 //      d/dD += Ga_k lambda_k (Jacobian rows).
@@ -72,10 +73,10 @@ struct AdjTcArgs {
   int stot;                      // neurons per CTA scratch row block
   const float* W_target;         // FP32 [widths[target+1], widths[target]]
   const float *sL, *sU, *tL, *tU, *D;   // [T, H]
-  const float* radii;            // [T, n]
+  const float *dlo, *dhi;        // [T, n] the displacement box Delta = X - alpha~ (dlo <= 0 <= dhi)
   const float *g_lo, *g_hi;      // output target: [T, n_x]
   const float *gl, *gu;          // hidden target: [T, H]
-  float *gsL, *gsU, *gtL, *gtU, *gD, *grho;
+  float *gsL, *gsU, *gtL, *gtU, *gD, *gdlo, *gdhi;
   __half* scratch;               // gridDim.x x stot x 128 lambdas, FP16
   int* flags;
 };
@@ -443,7 +444,10 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       {
 #pragma unroll
         for (int u = 0; u < kAdjNU; ++u)
-          if (nrn0 + 256 * u < n) prefetch_l1(a.radii + (long long)t * n + nrn0 + 256 * u);
+          if (nrn0 + 256 * u < n) {
+            prefetch_l1(a.dlo + (long long)t * n + nrn0 + 256 * u);
+            prefetch_l1(a.dhi + (long long)t * n + nrn0 + 256 * u);
+          }
         if (!wait_acc()) return false;
         const int np = (n + 63) & ~63;
 #pragma unroll
@@ -451,9 +455,10 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
           const int j = nrn0 + 256 * u;
           if (j >= np) continue;
           const bool live = j < n;
-          const float rho = live ? a.radii[(long long)t * n + j] : 0.f;
+          const float dl = live ? a.dlo[(long long)t * n + j] : 0.f, dh = live ? a.dhi[(long long)t * n + j] : 0.f;
+          const float dm = 0.5f * (dl + dh);   // the derivative's value where M = 0 (mean of both sides)
           const uint32_t tl = t_lane + 256u * u;
-          float grho = 0.f;
+          float gdl = 0.f, gdh = 0.f;
 #pragma unroll 1
           for (int r0 = 0; r0 < 128; r0 += GS) {
             const int nch = min(NR, (128 - r0) >> 3);
@@ -474,9 +479,10 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
               // Rows past 128 (the last group) only hold zeros and are not stored.
               const float glo = r < 128 ? gw[r] * ginv : 0.f, ghi = r + 1 < 128 ? gw[r + 1] * ginv : 0.f;
               const float mlo = d[e], mhi = d[e + 1];
-              const float G0 = mlo > 0.f ? -glo * rho : (mlo < 0.f ? glo * rho : 0.f);
-              const float G1 = mhi > 0.f ? ghi * rho : (mhi < 0.f ? -ghi * rho : 0.f);
-              grho = fmaf(ghi, fabsf(mhi), fmaf(-glo, fabsf(mlo), grho));
+              const float G0 = glo * (mlo > 0.f ? dl : (mlo < 0.f ? dh : dm));
+              const float G1 = ghi * (mhi > 0.f ? dh : (mhi < 0.f ? dl : dm));
+              gdl = fmaf(glo, fmaxf(mlo, 0.f), fmaf(ghi, fminf(mhi, 0.f), gdl));
+              gdh = fmaf(glo, fminf(mlo, 0.f), fmaf(ghi, fmaxf(mhi, 0.f), gdh));
               v[e] = G0;
               v[e + 1] = G1;
               if (NR == 3) v[e + NR - 1] = -(G0 + G1);
@@ -485,7 +491,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
             for (int h = 0; h < NR; ++h)
               if (h < nch) put8(r0 + 8 * h, j, v + 8 * h);
           }
-          if (live && grho != 0.f) atomicAdd(a.grho + (long long)t * n + j, grho * gscale);
+          if (live && gdl != 0.f) atomicAdd(a.gdlo + (long long)t * n + j, gdl * gscale);
+          if (live && gdh != 0.f) atomicAdd(a.gdhi + (long long)t * n + j, gdh * gscale);
         }
         operand_ready();
       }
@@ -760,8 +767,8 @@ size_t adj_tc_scratch_floats(const Ctx& c) {
   return (size_t)c.sm_count * stot * 64;   // FP16: two per float
 }
 
-leb_status adj_tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, const float* radii,
-                        const float* g_lo, const float* g_hi, int* flags, cudaStream_t s) {
+leb_status adj_tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, const float* g_lo,
+                        const float* g_hi, int* flags, cudaStream_t s) {
   const MlpModel& m = c.mlp;
   AdjState* st = reinterpret_cast<AdjState*>(m.adj);
   if (!st) return LEB_ERR_UNSUPPORTED;
@@ -795,7 +802,8 @@ leb_status adj_tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* 
   a.tL = ws + L.tL;
   a.tU = ws + L.tU;
   a.D = ws + L.D;
-  a.radii = radii;
+  a.dlo = ws + L.dlo;
+  a.dhi = ws + L.dhi;
   a.g_lo = g_lo;
   a.g_hi = g_hi;
   a.gl = ws + L.gl;
@@ -805,7 +813,8 @@ leb_status adj_tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* 
   a.gtL = ws + L.gtL;
   a.gtU = ws + L.gtU;
   a.gD = ws + L.gD;
-  a.grho = ws + L.grho;
+  a.gdlo = ws + L.gdlo;
+  a.gdhi = ws + L.gdhi;
   a.scratch = reinterpret_cast<__half*>(ws + L.adj);
   a.flags = flags;
   const int items = T * a.tiles_per_t;

@@ -137,7 +137,7 @@ struct MlpWs {
   size_t winf;              // [T, H] tensor-core inflation weight per neuron (see crown_tc.cu)
   size_t ucon;              // [T, L-1] tensor-core inflation constant per layer (operand underflow)
   size_t gsL, gsU, gtL, gtU, gD, gz, gl, gu;  // [T, H] adjoint accumulators
-  size_t grho;              // [T, n] adjoint of the radii
+  size_t gdlo, gdhi;        // [T, n] adjoints of the displacement box's ends (dlo <= 0 <= dhi)
   size_t gscr;              // [T, max width] adjoint scratch
   size_t adj;               // tensor-core adjoint: per-CTA lambda store (0 floats for FP32 handles)
   size_t anom, dlo, dhi;    // [T, n] nominal alpha~ and displacement box Delta = X - alpha~
@@ -205,9 +205,10 @@ size_t mlp_workspace_floats(const Ctx& c, int T, MlpWs* layout, int n_gen = 0);
 leb_status mlp_bounds(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set, float* r_lo,
                       float* r_hi, float* A, float* B, const leb_options* opt, void* ws, int* flags, cudaStream_t s);
 // saved: the workspace holds the state of the forward call on the same inputs (skip its recompute)
+// g_ctr: [T, n] gradient of the set's centre (box sets with a centre; unused for centred sets)
 leb_status mlp_bounds_backward(Ctx& c, int T, const float* x_nom, const float* u_nom, const leb_set* set,
                                const float* g_rlo, const float* g_rhi, float* g_x, float* g_u, float* g_rad,
-                               void* ws, int* flags, cudaStream_t s, bool saved = false);
+                               float* g_ctr, void* ws, int* flags, cudaStream_t s, bool saved = false);
 leb_status mlp_prepare(Ctx& c);
 void mlp_release(Ctx& c);
 size_t simt_chain_smem(int maxw);
@@ -252,7 +253,7 @@ leb_status or_flags(int* dst, const int* src, cudaStream_t s);
 leb_status adj_tc_prepare(Ctx& c);
 void adj_tc_release(Ctx& c);
 size_t adj_tc_scratch_floats(const Ctx& c);
-leb_status adj_tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, const float* radii,
+leb_status adj_tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws,
                         const float* g_lo, const float* g_hi, int* flags, cudaStream_t s);
 
 }  // namespace leb

@@ -375,21 +375,23 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
 
 static leb_status bounds_backward(leb_handle h, const leb_batch* batch, int T, const float* x_nom,
                                   const float* u_nom, const leb_set* set, const float* g_rlo, const float* g_rhi,
-                                  float* g_x, float* g_u, float* g_radii, void* workspace, size_t ws_bytes,
-                                  int* dev_flags, void* stream, bool saved) {
+                                  float* g_x, float* g_u, float* g_radii, float* g_center, void* workspace,
+                                  size_t ws_bytes, int* dev_flags, void* stream, bool saved) {
   if (!h || !set || T < 0 || !dev_flags) return LEB_ERR_INVALID_ARG;
   h->timer.phase = 1;
   // every timestep's bound is independent of the others: a batch of trajectories of any horizons is the
   // same problem as its timesteps in a row; chains of uneven length are not supported by the adjoint
   if (batch && (batch->n_traj < 1 || !batch->traj_offsets)) return LEB_ERR_INVALID_ARG;
   if (batch && batch->traj_nquads) return LEB_ERR_UNSUPPORTED;
-  if (set->kind != LEB_SET_BOX || set->center) return LEB_ERR_UNSUPPORTED;
+  if (set->kind != LEB_SET_BOX) return LEB_ERR_UNSUPPORTED;
   if (T > 0 && (!x_nom || !u_nom || !set->radii || !g_rlo || !g_rhi || !g_x || !g_u || !g_radii))
     return LEB_ERR_INVALID_ARG;
+  // an off-centre box has a centre gradient: the caller must take it
+  if (set->center && T > 0 && !g_center) return LEB_ERR_INVALID_ARG;
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return LEB_ERR_WORKSPACE;
   if (h->kind == LEB_DYN_QUAD_CHAIN) {
-    // the adjoint differentiates the plain bound in the natural order
-    if (h->qk.inputs_first || h->qk.split_phi || h->qk.pieces) return LEB_ERR_UNSUPPORTED;
+    // the adjoint differentiates the plain bound in the natural order, for sets centred at the nominal
+    if (h->qk.inputs_first || h->qk.split_phi || h->qk.pieces || set->center) return LEB_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(dev_flags, 0, sizeof(int), s) != cudaSuccess) return LEB_ERR_CUDA;
     return pbh_bounds_backward(*h, T, x_nom, u_nom, set->radii, g_rlo, g_rhi, g_x, g_u, g_radii, dev_flags, s);
@@ -402,23 +404,31 @@ static leb_status bounds_backward(leb_handle h, const leb_batch* batch, int T, c
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(dev_flags, 0, sizeof(int), s) != cudaSuccess) return LEB_ERR_CUDA;
   if (T == 0) return LEB_OK;
-  return mlp_bounds_backward(*h, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, workspace, dev_flags, s,
+  return mlp_bounds_backward(*h, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, g_center, workspace, dev_flags, s,
                              saved);
 }
 
 leb_status leb_bounds_backward(leb_handle h, const leb_batch* batch, int T, const float* x_nom, const float* u_nom,
                                const leb_set* set, const float* g_rlo, const float* g_rhi, float* g_x, float* g_u,
                                float* g_radii, void* workspace, size_t ws_bytes, int* dev_flags, void* stream) {
-  return bounds_backward(h, batch, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, workspace, ws_bytes,
-                         dev_flags, stream, false);
+  return bounds_backward(h, batch, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, nullptr, workspace,
+                         ws_bytes, dev_flags, stream, false);
+}
+
+leb_status leb_bounds_backward_box(leb_handle h, const leb_batch* batch, int T, const float* x_nom,
+                                   const float* u_nom, const leb_set* set, const float* g_rlo, const float* g_rhi,
+                                   float* g_x, float* g_u, float* g_radii, float* g_center, void* workspace,
+                                   size_t ws_bytes, int* dev_flags, void* stream) {
+  return bounds_backward(h, batch, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, g_center, workspace,
+                         ws_bytes, dev_flags, stream, false);
 }
 
 leb_status leb_bounds_backward_saved(leb_handle h, const leb_batch* batch, int T, const float* x_nom,
                                      const float* u_nom, const leb_set* set, const float* g_rlo, const float* g_rhi,
                                      float* g_x, float* g_u, float* g_radii, void* workspace, size_t ws_bytes,
                                      int* dev_flags, void* stream) {
-  return bounds_backward(h, batch, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, workspace, ws_bytes,
-                         dev_flags, stream, true);
+  return bounds_backward(h, batch, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, nullptr, workspace,
+                         ws_bytes, dev_flags, stream, true);
 }
 
 // ---- nominal refinement (projected gradient descent on the PBH width) ----------------------------

@@ -66,7 +66,8 @@ size_t mlp_workspace_floats(const Ctx& c, int T, MlpWs* w, int n_gen) {
   w->gz = take(TH);
   w->gl = take(TH);
   w->gu = take(TH);
-  w->grho = take(Tn);
+  w->gdlo = take(Tn);
+  w->gdhi = take(Tn);
   w->gscr = take((size_t)T * maxw);
   w->adj = take(m.adj ? adj_tc_scratch_floats(c) : 0);
   w->anom = take(Tn);

@@ -173,3 +173,53 @@ def test_adjoint_takes_a_batch_of_ragged_trajectories():
     assert lib.leb_bounds_backward(h.h, binding.C.byref(bd), *args) == binding.LEB_ERR_UNSUPPORTED
     bad = binding.BatchDesc(0, offs.data_ptr(), None)
     assert lib.leb_bounds_backward(h.h, binding.C.byref(bad), *args) == binding.LEB_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+def test_off_centre_box_gradient(prec):
+    """leb_bounds_backward_box for boxes centred off the nominal (hulled with it): dL/d(x~, u~, radii,
+    centre) against the FP64 oracle's gradient (itself pinned by central differences). Half the
+    coordinates have the nominal inside the box, half outside it (that side's end is then the nominal).
+    Tolerance as for centred sets, rel = 1e-3 on FP32 handles; the reduced formats' operand rounding moves
+    these gradients further than the centred ones (measured worst 1.3e-3 = 2.6 u FP16, 1.6e-2 = 4.0 u BF16;
+    FP32 4.0e-5), so rel = 1e-3 + 6 u there. The centred call is unchanged: leb_bounds_backward refuses a
+    centre (no place for its gradient), and quad-chain handles take centred sets only."""
+    w = inputs.tanh_mlp(seed=4106, n_traj=1, N=4, widths=(64, 128, 128, 32))
+    rng = np.random.default_rng(9)
+    a = w.nominal().astype(np.float64)
+    scale = np.where(rng.uniform(size=a.shape) < 0.5, 0.5, 2.0) * rng.choice([-1.0, 1.0], a.shape)
+    c = (a + scale * w.radii).astype(np.float32)
+    h = binding.mlp(w.Ws, w.bs, w.act, w.residual, prec)
+    g_lo = rng.normal(size=(w.T, w.n_x)).astype(np.float32)
+    g_hi = rng.normal(size=(w.T, w.n_x)).astype(np.float32)
+    x, u, r, cc = _t(w.x_nom), _t(w.u_nom), _t(w.radii), _t(c)
+    gx, gu, gr, gc, fl = h.bounds_backward(x, u, r, _t(g_lo), _t(g_hi), center=cc)
+    torch.cuda.synchronize()
+    assert int(fl.item()) == 0
+    got_all = torch.cat([gx, gu, gr, gc], 1).cpu().numpy()
+    rel = 1e-3 if prec == "fp32" else 1e-3 + 6 * U_OP[prec]
+    worst = 0.0
+    for t in range(w.T):
+        ox, ou, orr, oc = crown.box_remainder_vjp(w.Ws, w.bs, w.act, w.x_nom[t], w.u_nom[t], w.radii[t], g_lo[t],
+                                                  g_hi[t], w.residual, center=c[t].astype(np.float64))
+        ref = np.concatenate([ox, ou, orr, oc])
+        got = got_all[t]
+        scale_t = np.abs(ref).max()
+        err = np.abs(got - ref)
+        worst = max(worst, float(np.max(err / (scale_t + np.abs(ref)))))
+        assert np.all(err <= rel * scale_t + rel * np.abs(ref)), (t, np.max(err / (scale_t + 1e-30)))
+    print(f"off-centre adjoint {prec}: worst |err| / (max|g| + |g|) = {worst:.2e}")
+    # the API's contract
+    lib = binding.lib()
+    sd = h.set_desc(radii=r, center=cc)
+    ws = h.workspace(w.T)
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    args = (w.T, x.data_ptr(), u.data_ptr(), binding.C.byref(sd), _t(g_lo).data_ptr(), _t(g_hi).data_ptr(),
+            gx.data_ptr(), gu.data_ptr(), gr.data_ptr())
+    assert lib.leb_bounds_backward(h.h, None, *args, ws.data_ptr(), ws.numel(), flags.data_ptr(), None) == \
+        binding.LEB_ERR_INVALID_ARG
+    q = inputs.planar_quad()
+    hq = binding.quad_chain(1, **q.params)
+    with pytest.raises(binding.LebError):
+        hq.bounds_backward(_t(q.x_nom), _t(q.u_nom), _t(q.radii), _t(np.ones((q.T, q.n_x))), _t(np.ones((q.T, q.n_x))),
+                           center=_t(np.concatenate([q.x_nom, q.u_nom], 1)))

@@ -209,6 +209,45 @@ def test_oracle_gradient_matches_finite_differences():
             assert fd == pytest.approx(grad[i], rel=2e-3, abs=2e-6)
 
 
+def test_oracle_gradient_off_centre_box_matches_finite_differences():
+    """The oracle's gradient for a box centred off the nominal, hulled with it, w.r.t. (x~, u~, radii,
+    centre) vs central differences (h = 1e-5, FP64). Half the coordinates have the nominal inside the box
+    (|c - a| = rho / 2), half outside it (|c - a| = 2 rho: that side of the hull is the nominal itself),
+    both far from the kinks at |c - a| = rho."""
+    w = inputs.tanh_mlp(n_traj=1, N=2, widths=(10, 16, 16, 6))
+    rng = np.random.default_rng(16)
+    t = 1
+    x, u, rad = (w.x_nom[t].astype(np.float64), w.u_nom[t].astype(np.float64), w.radii[t].astype(np.float64))
+    a = np.concatenate([x, u])
+    scale = np.where(np.arange(a.size) % 2 == 0, 0.5, 2.0) * rng.choice([-1.0, 1.0], a.size)
+    c = a + scale * rad
+    g_lo = rng.normal(size=6)
+    g_hi = rng.normal(size=6)
+    gx, gu, gr, gc = crown.box_remainder_vjp(w.Ws, w.bs, "tanh", x, u, rad, g_lo, g_hi, center=c)
+
+    def L(x_, u_, r_, c_):
+        lo, hi, _ = crown.box_remainder(w.Ws, w.bs, "tanh", x_, u_, r_, center=c_)
+        return float(g_lo @ lo + g_hi @ hi)
+
+    h = 1e-5
+    for vec, grad, which in ((x, gx, 0), (u, gu, 1), (rad, gr, 2), (c, gc, 3)):
+        for i in range(len(vec)):
+            e = np.zeros_like(vec)
+            e[i] = h
+            args_p = [x, u, rad, c]
+            args_m = [x, u, rad, c]
+            args_p[which] = vec + e
+            args_m[which] = vec - e
+            fd = (L(*args_p) - L(*args_m)) / (2 * h)
+            assert fd == pytest.approx(grad[i], rel=2e-3, abs=2e-6), (which, i)
+    # where the nominal lies outside the box, that side's end is the nominal: the centre and the radius move
+    # only the other end, so their gradients there are equal (both d/d(far end)) and the centre's is not 0
+    out = np.abs(c - a) > rad
+    assert np.all(np.abs(gc[out]) > 0)
+    far_sign = np.sign(c - a)[out]     # the far end is c + rho where c > a, c - rho where c < a
+    assert np.allclose(gr[out], far_sign * gc[out], rtol=1e-9, atol=1e-12)
+
+
 def test_proposer_gradients_and_adam_closed_form():
     rng = np.random.default_rng(16)
     Ws = [rng.normal(size=(7, 5)) * 0.4, rng.normal(size=(6, 7)) * 0.4, rng.normal(size=(4, 6)) * 0.4]
