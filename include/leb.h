@@ -173,8 +173,9 @@ leb_status leb_bounds(leb_handle h, const leb_batch* batch, int T, const float* 
                       const leb_options* opt, void* workspace, size_t ws_bytes, int* dev_flags, void* stream);
 
 /* ---- adjoint of the bounds (differentiable LEBs, Sec. IV-D) ------------------------------------ */
-/* Box sets centred at the nominal (set->center NULL; a box with a centre: leb_bounds_backward_box; other
- * sets: LEB_ERR_UNSUPPORTED, a centre without a centre gradient: LEB_ERR_INVALID_ARG). batch: NULL or
+/* Box sets centred at the nominal (set->center NULL; a box with a centre: leb_bounds_backward_box; a
+ * zonotope: leb_bounds_backward_zono; other sets: LEB_ERR_UNSUPPORTED, a centre without a centre
+ * gradient: LEB_ERR_INVALID_ARG). batch: NULL or
  * trajectories of any horizons (traj_offsets; each timestep's bound is independent, so the gradient is
  * that of the timesteps in a row); chains of uneven length (traj_nquads) return LEB_ERR_UNSUPPORTED.
  * Given g_rlo = dL/dr_lo and g_rhi = dL/dr_hi [T, n_x], writes g_x [T, n_x], g_u [T, n_u],
@@ -195,6 +196,17 @@ leb_status leb_bounds_backward_box(leb_handle h, const leb_batch* batch, int T, 
                                    const float* u_nom, const leb_set* set, const float* g_rlo, const float* g_rhi,
                                    float* g_x, float* g_u, float* g_radii, float* g_center, void* workspace,
                                    size_t ws_bytes, int* dev_flags, void* stream);
+/* The adjoint for zonotope sets taken as their interval hull (set->kind LEB_SET_ZONO, Eq. 21; the bound
+ * leb_bounds computes for that kind): the box of half-widths s_i = sum_g |G_ig| (rounded up) around
+ * set->center, or the nominal when it is NULL, hulled with the nominal, then Thms. 2-3 over that box.
+ * g_G [T, n, n_gen] (device, written) receives dL/dG = dL/ds_i sign(G_ig) (0 where G_ig = 0);
+ * g_center [T, n] as in leb_bounds_backward_box (required with a centre, may be NULL without one).
+ * MLP handles only (others: LEB_ERR_UNSUPPORTED); set->kind other than LEB_SET_ZONO, G NULL or
+ * n_gen < 1: LEB_ERR_INVALID_ARG. Workspace: leb_workspace_size. Otherwise as leb_bounds_backward. */
+leb_status leb_bounds_backward_zono(leb_handle h, const leb_batch* batch, int T, const float* x_nom,
+                                    const float* u_nom, const leb_set* set, const float* g_rlo, const float* g_rhi,
+                                    float* g_x, float* g_u, float* g_G, float* g_center, void* workspace,
+                                    size_t ws_bytes, int* dev_flags, void* stream);
 /* The same adjoint from the forward pass's saved state: the workspace must hold the state of the last
  * leb_bounds call on this handle with the same T, x_nom, u_nom and set (box, centred at the nominal,
  * no leb_batch), with no other call on that workspace in between. FP32 MLP handles skip the recompute

@@ -294,6 +294,27 @@ def box_remainder_vjp(Ws, bs, act, x_nom, u_nom, radii, g_lo, g_hi, residual=Tru
     return gx.numpy(), gu.numpy(), gr.numpy(), gc.numpy()
 
 
+def zono_hull_remainder_vjp(Ws, bs, act, x_nom, u_nom, G, g_lo, g_hi, residual=True, center=None):
+    """Gradient of sum(g_lo * r_lo + g_hi * r_hi) w.r.t. (x~, u~, G[, centre]) for a zonotope set taken as its
+    interval hull (Eq. 21): the box of half-widths sum_g |G_ig| around the centre (the nominal without one),
+    hulled with the nominal, then Thm. 3 over that box."""
+    Ws_t = [to_t(W) for W in Ws]
+    bs_t = [to_t(b) for b in bs]
+    x = to_t(x_nom).requires_grad_(True)
+    u = to_t(u_nom).requires_grad_(True)
+    Gt = to_t(G).requires_grad_(True)
+    c = None if center is None else to_t(center).requires_grad_(True)
+    a = torch.cat([x, u])
+    lo, hi = _box_hull(a, Gt.abs().sum(dim=1), c)
+    r_lo, r_hi, _, _ = remainder_bounds(Ws_t, bs_t, act, a, lo, hi, residual)
+    L = (to_t(g_lo) * r_lo).sum() + (to_t(g_hi) * r_hi).sum()
+    if c is None:
+        gx, gu, gG = torch.autograd.grad(L, [x, u, Gt])
+        return gx.numpy(), gu.numpy(), gG.numpy()
+    gx, gu, gG, gc = torch.autograd.grad(L, [x, u, Gt, c])
+    return gx.numpy(), gu.numpy(), gG.numpy(), gc.numpy()
+
+
 def zono_hull_nominal(nominal: torch.Tensor, c: torch.Tensor, G: torch.Tensor):
     """A zonotope that contains both c + G E and the nominal point: the segment from c to the nominal
     appended as one more generator, (c + a) / 2 + [G, (a - c) / 2] E (the set itself when c = a)."""

@@ -65,6 +65,7 @@ EXPORTS = [
     "leb_proposer_state_size", "leb_proposer_save_state", "leb_proposer_load_state", "leb_selftest_wait_timeout",
     "leb_selftest_set_wait_limit", "leb_proposer_calibrate", "leb_proposer_get_offset",
     "leb_set_partition_recentred", "leb_set_path_order_perm", "leb_bounds_backward_box",
+    "leb_bounds_backward_zono",
 ]
 
 
@@ -95,6 +96,8 @@ def lib():
         L.leb_bounds_backward_saved.argtypes = L.leb_bounds_backward.argtypes
         L.leb_bounds_backward_box.argtypes = [vp, C.POINTER(BatchDesc), i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp,
                                               vp, vp, vp, vp, sz, vp, vp]
+        L.leb_bounds_backward_zono.argtypes = [vp, C.POINTER(BatchDesc), i32, vp, vp, C.POINTER(SetDesc), vp, vp, vp,
+                                               vp, vp, vp, vp, sz, vp, vp]
         L.leb_zonotope_map.argtypes = [vp, vp, C.c_longlong, C.c_float, vp, vp, vp]
         L.leb_autotune.argtypes = [vp, i32, i32, i32, C.c_char_p, vp, sz, vp]
         L.leb_plan_string.argtypes = [vp, C.c_char_p, sz]
@@ -341,6 +344,28 @@ class Handle:
                  _ptr(g_rlo.contiguous()), _ptr(g_rhi.contiguous()),
                  _ptr(g_x), _ptr(g_u), _ptr(g_r), _ptr(ws), ws.numel(), _ptr(flags), _stream()), "leb_bounds_backward")
         return g_x, g_u, g_r, flags
+
+    def bounds_backward_zono(self, x_nom, u_nom, G, g_rlo, g_rhi, center=None, traj_offsets=None):
+        """dL/d(x~, u~, G[, center]) for a zonotope set taken as its interval hull
+        (leb_bounds_backward_zono). G [T, n, n_gen]; center [T, n] or None (the nominal). Returns
+        (g_x, g_u, g_G, g_center or None, flags)."""
+        dev = x_nom.device
+        T = int(x_nom.shape[0])
+        f32 = dict(device=dev, dtype=torch.float32)
+        G = G.contiguous()
+        g_x = torch.empty(T, self.n_x, **f32)
+        g_u = torch.empty(T, self.n_u, **f32)
+        g_G = torch.empty(G.shape, **f32)
+        g_c = None if center is None else torch.empty(T, self.n_x + self.n_u, **f32)
+        flags = torch.zeros(1, device=dev, dtype=torch.int32)
+        sd = self.set_desc(G=G, center=center)
+        ws = self.workspace(T, dev)
+        bd = self.batch_desc(traj_offsets)
+        check(lib().leb_bounds_backward_zono(self.h, None if bd is None else C.byref(bd), T, _ptr(x_nom), _ptr(u_nom),
+                                             C.byref(sd), _ptr(g_rlo.contiguous()), _ptr(g_rhi.contiguous()),
+                                             _ptr(g_x), _ptr(g_u), _ptr(g_G), _ptr(g_c), _ptr(ws), ws.numel(),
+                                             _ptr(flags), _stream()), "leb_bounds_backward_zono")
+        return g_x, g_u, g_G, g_c, flags
 
     def refine_nominal_pgd(self, x0, u0, radii, eps: float, lr: float, steps: int):
         """Projected gradient descent of every timestep's nominal point on the summed PBH width inside

@@ -409,6 +409,48 @@ __global__ void box_grad_kernel(int T, int n_x, int n_u, const float* ga, const 
   }
 }
 
+// The same for a zonotope set taken as its interval hull (LEB_SET_ZONO, Eq. 21): the box of half-widths
+// s_i = sum_g |G_ig| (rounded up, as the forward's set-to-box step takes them) around the centre (or the
+// nominal), hulled with the nominal; dL/dG_ig = dL/ds_i sign(G_ig). A warp per (timestep, input row).
+__global__ void zono_hull_grad_kernel(int T, int n_x, int n_u, int p, const float* ga, const float* gdlo,
+                                      const float* gdhi, const float* center, const float* G, const float* anom,
+                                      float* gx, float* gu, float* gG, float* gc) {
+  const int n = n_x + n_u;
+  const int lane = threadIdx.x & 31;
+  const long long rows = (long long)T * n;
+  for (long long e = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; e < rows;
+       e += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const float* Gr = G + e * p;
+    float sabs = 0.f;
+    for (int g = lane; g < p; g += 32) sabs = __fadd_ru(sabs, fabsf(Gr[g]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sabs = __fadd_ru(sabs, __shfl_xor_sync(0xffffffffu, sabs, o));
+    float g_a = ga[e], g_s, g_c = 0.f;
+    if (!center) {
+      g_s = gdhi[e] - gdlo[e];
+    } else {
+      const float c = center[e], a = anom[e];
+      const float il = __fsub_rd(c, sabs) < a ? 1.f : 0.f, ih = __fadd_ru(c, sabs) > a ? 1.f : 0.f;
+      const float pl = il * gdlo[e], ph = ih * gdhi[e];
+      g_c = pl + ph;
+      g_s = ph - pl;
+      g_a -= g_c;
+    }
+    float* gGr = gG + e * p;
+    for (int g = lane; g < p; g += 32) {
+      const float v = Gr[g];
+      gGr[g] = v > 0.f ? g_s : (v < 0.f ? -g_s : 0.f);
+    }
+    if (lane == 0) {
+      const long long t = e / n;
+      const int m = (int)(e - t * n);
+      if (m < n_x) gx[t * n_x + m] = g_a;
+      else gu[t * n_u + m - n_x] = g_a;
+      if (center) gc[e] = g_c;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------------------
 size_t bwd_chain_smem(const Ctx& c, int target, int* stot_out) {
   const MlpModel& m = c.mlp;
@@ -547,8 +589,14 @@ leb_status mlp_bounds_backward(Ctx& c, int T, const float* x_nom, const float* u
     bwd_gemm_kernel<<<grid, 256, 0, s>>>(T, m.widths[1], n, ws + L.gz, L.H, m.W[0], 0, 1.f, nullptr, 0, ws + L.gscr, n, 0);
   }
   const int blocks = (int)std::min<long long>(((long long)T * n + 255) / 256, 148LL * 32);
-  box_grad_kernel<<<blocks, 256, 0, s>>>(T, c.n_x, c.n_u, ws + L.gscr, ws + L.gdlo, ws + L.gdhi, set->center,
-                                         set->radii, ws + L.anom, g_x, g_u, g_rad, g_ctr);
+  if (set->kind == LEB_SET_ZONO) {   // g_rad is dL/dG [T, n, n_gen]
+    const int wblocks = (int)std::min<long long>(((long long)T * n + 7) / 8, 148LL * 32);
+    zono_hull_grad_kernel<<<wblocks, 256, 0, s>>>(T, c.n_x, c.n_u, set->n_gen, ws + L.gscr, ws + L.gdlo, ws + L.gdhi,
+                                                  set->center, set->G, ws + L.anom, g_x, g_u, g_rad, g_ctr);
+  } else {
+    box_grad_kernel<<<blocks, 256, 0, s>>>(T, c.n_x, c.n_u, ws + L.gscr, ws + L.gdlo, ws + L.gdhi, set->center,
+                                           set->radii, ws + L.anom, g_x, g_u, g_rad, g_ctr);
+  }
   return cudaGetLastError() == cudaSuccess ? LEB_OK : LEB_ERR_CUDA;
 }
 

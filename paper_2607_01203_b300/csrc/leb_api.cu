@@ -383,8 +383,12 @@ static leb_status bounds_backward(leb_handle h, const leb_batch* batch, int T, c
   // same problem as its timesteps in a row; chains of uneven length are not supported by the adjoint
   if (batch && (batch->n_traj < 1 || !batch->traj_offsets)) return LEB_ERR_INVALID_ARG;
   if (batch && batch->traj_nquads) return LEB_ERR_UNSUPPORTED;
-  if (set->kind != LEB_SET_BOX) return LEB_ERR_UNSUPPORTED;
-  if (T > 0 && (!x_nom || !u_nom || !set->radii || !g_rlo || !g_rhi || !g_x || !g_u || !g_radii))
+  // box sets; zonotope sets as their interval hull (MLP handles; g_radii is then dL/dG [T, n, n_gen])
+  if (set->kind != LEB_SET_BOX && set->kind != LEB_SET_ZONO) return LEB_ERR_UNSUPPORTED;
+  const bool zono = set->kind == LEB_SET_ZONO;
+  if (zono && (h->kind != LEB_DYN_MLP || saved)) return LEB_ERR_UNSUPPORTED;
+  if (T > 0 && (!x_nom || !u_nom || (zono ? (!set->G || set->n_gen < 1) : !set->radii) || !g_rlo || !g_rhi || !g_x ||
+                !g_u || !g_radii))
     return LEB_ERR_INVALID_ARG;
   // an off-centre box has a centre gradient: the caller must take it
   if (set->center && T > 0 && !g_center) return LEB_ERR_INVALID_ARG;
@@ -411,14 +415,25 @@ static leb_status bounds_backward(leb_handle h, const leb_batch* batch, int T, c
 leb_status leb_bounds_backward(leb_handle h, const leb_batch* batch, int T, const float* x_nom, const float* u_nom,
                                const leb_set* set, const float* g_rlo, const float* g_rhi, float* g_x, float* g_u,
                                float* g_radii, void* workspace, size_t ws_bytes, int* dev_flags, void* stream) {
+  if (set && set->kind != LEB_SET_BOX) return LEB_ERR_UNSUPPORTED;
   return bounds_backward(h, batch, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, nullptr, workspace,
                          ws_bytes, dev_flags, stream, false);
+}
+
+leb_status leb_bounds_backward_zono(leb_handle h, const leb_batch* batch, int T, const float* x_nom,
+                                    const float* u_nom, const leb_set* set, const float* g_rlo, const float* g_rhi,
+                                    float* g_x, float* g_u, float* g_G, float* g_center, void* workspace,
+                                    size_t ws_bytes, int* dev_flags, void* stream) {
+  if (!set || set->kind != LEB_SET_ZONO) return LEB_ERR_INVALID_ARG;
+  return bounds_backward(h, batch, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_G, g_center, workspace, ws_bytes,
+                         dev_flags, stream, false);
 }
 
 leb_status leb_bounds_backward_box(leb_handle h, const leb_batch* batch, int T, const float* x_nom,
                                    const float* u_nom, const leb_set* set, const float* g_rlo, const float* g_rhi,
                                    float* g_x, float* g_u, float* g_radii, float* g_center, void* workspace,
                                    size_t ws_bytes, int* dev_flags, void* stream) {
+  if (set && set->kind != LEB_SET_BOX) return LEB_ERR_UNSUPPORTED;
   return bounds_backward(h, batch, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, g_center, workspace,
                          ws_bytes, dev_flags, stream, false);
 }
@@ -427,6 +442,7 @@ leb_status leb_bounds_backward_saved(leb_handle h, const leb_batch* batch, int T
                                      const float* u_nom, const leb_set* set, const float* g_rlo, const float* g_rhi,
                                      float* g_x, float* g_u, float* g_radii, void* workspace, size_t ws_bytes,
                                      int* dev_flags, void* stream) {
+  if (set && set->kind != LEB_SET_BOX) return LEB_ERR_UNSUPPORTED;
   return bounds_backward(h, batch, T, x_nom, u_nom, set, g_rlo, g_rhi, g_x, g_u, g_radii, nullptr, workspace,
                          ws_bytes, dev_flags, stream, true);
 }

@@ -223,3 +223,73 @@ def test_off_centre_box_gradient(prec):
     with pytest.raises(binding.LebError):
         hq.bounds_backward(_t(q.x_nom), _t(q.u_nom), _t(q.radii), _t(np.ones((q.T, q.n_x))), _t(np.ones((q.T, q.n_x))),
                            center=_t(np.concatenate([q.x_nom, q.u_nom], 1)))
+
+
+@pytest.mark.parametrize("prec,n_gen,centred", [("fp32", 5, True), ("fp32", 37, False), ("fp16", 37, True),
+                                                ("fp16", 5, False), ("bf16", 37, False)])
+def test_zonotope_hull_gradient(prec, n_gen, centred):
+    """leb_bounds_backward_zono: the adjoint of the bound over a zonotope set's interval hull (Eq. 21),
+    dL/d(x~, u~, G[, centre]) against the FP64 oracle's gradient (pinned by central differences). G's
+    row l1 norms are the box workload's radii (so the hull is that box), 5 or 37 generators (a warp's
+    lanes and a ragged second pass), one entry per row set to 0; off-centre sets put the nominal inside
+    the hull in half the coordinates, outside in the rest. Tolerances as for box sets: dL/dG_ig is the
+    half-width gradient times sign(G_ig)."""
+    w = inputs.tanh_mlp(seed=4107, n_traj=1, N=4, widths=(64, 128, 128, 32))
+    rng = np.random.default_rng(10 + n_gen)
+    a = w.nominal().astype(np.float64)
+    share = rng.uniform(0.1, 1.0, size=(w.T, w.n, n_gen))
+    share[:, :, n_gen // 2] = 0.0
+    share /= share.sum(axis=2, keepdims=True)
+    G = (w.radii[:, :, None] * share * rng.choice([-1.0, 1.0], share.shape)).astype(np.float32)
+    rad = np.abs(G.astype(np.float64)).sum(axis=2)
+    c = None
+    if not centred:
+        scale = np.where(rng.uniform(size=a.shape) < 0.5, 0.5, 2.0) * rng.choice([-1.0, 1.0], a.shape)
+        c = (a + scale * rad).astype(np.float32)
+    h = binding.mlp(w.Ws, w.bs, w.act, w.residual, prec)
+    g_lo = rng.normal(size=(w.T, w.n_x)).astype(np.float32)
+    g_hi = rng.normal(size=(w.T, w.n_x)).astype(np.float32)
+    x, u = _t(w.x_nom), _t(w.u_nom)
+    gx, gu, gG, gc, fl = h.bounds_backward_zono(x, u, _t(G), _t(g_lo), _t(g_hi), center=None if c is None else _t(c))
+    torch.cuda.synchronize()
+    assert int(fl.item()) == 0
+    assert (gc is None) == centred
+    gG = gG.cpu().numpy()
+    assert np.all(gG[:, :, n_gen // 2] == 0.0)
+    parts = [gx, gu, torch.as_tensor(gG.reshape(w.T, -1))] + ([] if c is None else [gc])
+    got_all = torch.cat([p.cpu() for p in parts], 1).numpy()
+    rel = 1e-3 if prec == "fp32" else 1e-3 + 6 * U_OP[prec]
+    worst = 0.0
+    for t in range(w.T):
+        out = crown.zono_hull_remainder_vjp(w.Ws, w.bs, w.act, w.x_nom[t], w.u_nom[t], G[t].astype(np.float64),
+                                            g_lo[t], g_hi[t], w.residual,
+                                            center=None if c is None else c[t].astype(np.float64))
+        ref = np.concatenate([out[0], out[1], out[2].reshape(-1)] + ([] if c is None else [out[3]]))
+        got = got_all[t]
+        scale_t = np.abs(ref).max()
+        err = np.abs(got - ref)
+        worst = max(worst, float(np.max(err / (scale_t + np.abs(ref)))))
+        assert np.all(err <= rel * scale_t + rel * np.abs(ref)), (t, np.max(err / (scale_t + 1e-30)))
+    print(f"zonotope-hull adjoint {prec} n_gen={n_gen} centred={centred}: worst = {worst:.2e}")
+    # the API's contract: the box entry points refuse a zonotope, the zonotope one a box; quad chains none
+    lib = binding.lib()
+    sd = h.set_desc(G=_t(G))
+    ws = h.workspace(w.T)
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    gr = torch.empty(w.T, w.n, device="cuda")
+    args = (w.T, x.data_ptr(), u.data_ptr(), binding.C.byref(sd), _t(g_lo).data_ptr(), _t(g_hi).data_ptr(),
+            gx.data_ptr(), gu.data_ptr(), gr.data_ptr())
+    assert lib.leb_bounds_backward(h.h, None, *args, ws.data_ptr(), ws.numel(), flags.data_ptr(), None) == \
+        binding.LEB_ERR_UNSUPPORTED
+    assert lib.leb_bounds_backward_box(h.h, None, *args, None, ws.data_ptr(), ws.numel(), flags.data_ptr(),
+                                       None) == binding.LEB_ERR_UNSUPPORTED
+    sb = h.set_desc(radii=_t(w.radii))
+    args_b = (w.T, x.data_ptr(), u.data_ptr(), binding.C.byref(sb), _t(g_lo).data_ptr(), _t(g_hi).data_ptr(),
+              gx.data_ptr(), gu.data_ptr(), gr.data_ptr())
+    assert lib.leb_bounds_backward_zono(h.h, None, *args_b, None, ws.data_ptr(), ws.numel(), flags.data_ptr(),
+                                        None) == binding.LEB_ERR_INVALID_ARG
+    q = inputs.planar_quad()
+    hq = binding.quad_chain(1, **q.params)
+    with pytest.raises(binding.LebError):
+        hq.bounds_backward_zono(_t(q.x_nom), _t(q.u_nom), _t(np.full((q.T, q.n, 2), 0.01)),
+                                _t(np.ones((q.T, q.n_x))), _t(np.ones((q.T, q.n_x))))

@@ -248,6 +248,63 @@ def test_oracle_gradient_off_centre_box_matches_finite_differences():
     assert np.allclose(gr[out], far_sign * gc[out], rtol=1e-9, atol=1e-12)
 
 
+def test_oracle_gradient_zonotope_hull_matches_finite_differences():
+    """The oracle's gradient for a zonotope set taken as its interval hull (Eq. 21), w.r.t. (x~, u~, G,
+    centre), vs central differences of the box bound at radii sum_g |G_ig| (h = 1e-5, FP64); the centre
+    sits off the nominal, inside the box in half the coordinates and outside in the other half. Two
+    special cases: a diagonal G is the box of radii |G_ii| (the box gradient times sign(G_ii)), and a zero
+    generator entry gets no gradient."""
+    w = inputs.tanh_mlp(n_traj=1, N=2, widths=(10, 16, 16, 6))
+    rng = np.random.default_rng(18)
+    t = 1
+    x, u = w.x_nom[t].astype(np.float64), w.u_nom[t].astype(np.float64)
+    a = np.concatenate([x, u])
+    n, p = a.size, 5
+    G = rng.normal(size=(n, p)) * 0.02
+    G[3, 2] = 0.0
+    rad = np.abs(G).sum(axis=1)
+    scale = np.where(np.arange(n) % 2 == 0, 0.5, 2.0) * rng.choice([-1.0, 1.0], n)
+    c = a + scale * rad
+    g_lo = rng.normal(size=6)
+    g_hi = rng.normal(size=6)
+    gx, gu, gG, gc = crown.zono_hull_remainder_vjp(w.Ws, w.bs, "tanh", x, u, G, g_lo, g_hi, center=c)
+
+    def L(x_, u_, G_, c_):
+        lo, hi, _ = crown.box_remainder(w.Ws, w.bs, "tanh", x_, u_, np.abs(G_).sum(axis=1), center=c_)
+        return float(g_lo @ lo + g_hi @ hi)
+
+    h = 1e-5
+    for vec, grad, which in ((x, gx, 0), (u, gu, 1), (c, gc, 3)):
+        for i in range(len(vec)):
+            e = np.zeros_like(vec)
+            e[i] = h
+            args_p = [x, u, G, c]
+            args_m = [x, u, G, c]
+            args_p[which] = vec + e
+            args_m[which] = vec - e
+            fd = (L(*args_p) - L(*args_m)) / (2 * h)
+            assert fd == pytest.approx(grad[i], rel=2e-3, abs=2e-6), (which, i)
+    for (i, g) in ((0, 0), (1, 4), (5, 2), (n - 1, 3), (7, 1)):
+        Gp, Gm = G.copy(), G.copy()
+        Gp[i, g] += h
+        Gm[i, g] -= h
+        fd = (L(x, u, Gp, c) - L(x, u, Gm, c)) / (2 * h)
+        assert fd == pytest.approx(gG[i, g], rel=2e-3, abs=2e-6), (i, g)
+    assert gG[3, 2] == 0.0
+    # the row of dL/dG is dL/d(half-width) times sign(G): one magnitude per row
+    mag = np.abs(gG)
+    nz = G != 0
+    for i in range(n):
+        assert np.allclose(mag[i][nz[i]], mag[i][nz[i]].max(), rtol=1e-12, atol=0)
+    # a diagonal G is the box of radii |G_ii|
+    d = rng.normal(size=n) * 0.03
+    gx2, gu2, gG2 = crown.zono_hull_remainder_vjp(w.Ws, w.bs, "tanh", x, u, np.diag(d), g_lo, g_hi)
+    bx, bu, br = crown.box_remainder_vjp(w.Ws, w.bs, "tanh", x, u, np.abs(d), g_lo, g_hi)
+    assert np.allclose(gx2, bx, rtol=1e-12, atol=1e-14) and np.allclose(gu2, bu, rtol=1e-12, atol=1e-14)
+    assert np.allclose(np.diag(gG2), br * np.sign(d), rtol=1e-12, atol=1e-14)
+    assert np.all(gG2[~np.eye(n, dtype=bool)] == 0.0)
+
+
 def test_proposer_gradients_and_adam_closed_form():
     rng = np.random.default_rng(16)
     Ws = [rng.normal(size=(7, 5)) * 0.4, rng.normal(size=(6, 7)) * 0.4, rng.normal(size=(4, 6)) * 0.4]
