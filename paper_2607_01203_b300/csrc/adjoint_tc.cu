@@ -44,14 +44,14 @@
 
 namespace leb {
 
-constexpr int kAdjNU = 1;                           // neurons per epilogue thread (M-tiles m, m + 4 / kAdjNU)
+constexpr int kAdjNU = 1;                           // neurons per epilogue thread
 constexpr int kAdjEpiWarps = 16 / kAdjNU;           // M-tiles per thread set x 4 TMEM lane quarters
 constexpr int kAdjCtlWarps = 4;                     // warpgroup 0: TMA warp, MMA warp, two idle warps
 constexpr int kAdjThreads = 32 * (kAdjCtlWarps + kAdjEpiWarps);
 // Register split (setmaxnreg): warpgroup 0 keeps 32 registers a thread, the epilogue warpgroups take 112.
 // The increases draw on what the block was launched with, so the compiled kernel must have at least
 // kAdjRegsLaunchMin registers a thread (checked before any launch).
-constexpr int kAdjRegsCtl = 32, kAdjRegsEpi = 112;
+constexpr int kAdjRegsCtl = 48, kAdjRegsEpi = 104;
 constexpr int kAdjRegsLaunchMin = (128 * kAdjRegsCtl + 32 * kAdjEpiWarps * kAdjRegsEpi + kAdjThreads - 1) / kAdjThreads;
 constexpr int kAdjStages = 6;                       // weight-tile ring
 constexpr int kAdjATile = 128 * 64 * 2;             // 128 neurons x 64 K x 2 bytes
@@ -104,7 +104,12 @@ __device__ __forceinline__ uint32_t b_off8(int r0, int j) {
   return (uint32_t)((r0 >> 6) * kAdjLbo + (j >> 3) * 1024 + (j & 7) * 128 + ((((r0 & 63) >> 3) ^ (j & 7)) << 4));
 }
 
-__global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid_constant__ AdjTcArgs a) {
+// CTAs run in pairs (a cluster of 2) that stream the weight tiles together: tile kb of the sequence both
+// walk is loaded by CTA kb mod 2 and multicast to both, so each pair reads every weight tile from L2 once.
+// Both CTAs of a pair therefore walk the same number of items (the first CTA's count; a CTA past the
+// last item works on an item with no valid rows, which writes nothing outside its own scratch).
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
+    adjoint_tc_kernel(const __grid_constant__ AdjTcArgs a) {
   extern __shared__ uint8_t sraw[];
   // 1024-byte aligned base, as an offset from the shared array (so that every derived pointer keeps the
   // shared address space and its accesses compile to shared-memory instructions)
@@ -126,11 +131,16 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_items = a.T * a.tiles_per_t;
   const int target = a.target;
+  const uint32_t rank = cluster_ctarank();   // 0 or 1 in the pair
+  const uint16_t pair_mask = 3u;
+  // items of this CTA: blockIdx.x + j gridDim.x for j < n_pass (the pair's first CTA has the most)
+  const int first = (int)blockIdx.x & ~1;
+  const int n_pass = first < n_items ? (n_items - first + (int)gridDim.x - 1) / (int)gridDim.x : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kAdjStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&full[s], 1);    // this CTA's expect-tx; the bytes come from either CTA's load
+      mbar_init(&empty[s], 2);   // both CTAs' MMA warps have read the slot
     }
     mbar_init(a_full, kAdjEpiWarps);
     mbar_init(acc_full, 1);
@@ -142,6 +152,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
   if (warp == 1) tmem_alloc(&tmem_slot, 512);
   tc_fence_before();
   __syncthreads();
+  cluster_sync_all();   // the peer's barriers are initialised before any load or commit reaches them
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
@@ -171,7 +182,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       }
       uint32_t kb = 0;
       bool ok = true;
-      for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+      for (int pass = 0; pass < n_pass && ok; ++pass) {
         for (int s = 0; s < n_stages && ok; ++s) {
           int M, K;
           const CUtensorMap* map;
@@ -180,13 +191,15 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
           for (int kc = 0; kc < nK && ok; ++kc)
             for (int c = 0; c < nM; ++c, ++kb) {
               const int slot = (int)(kb % kAdjStages);
+              // the slot is free in both CTAs once both MMA warps have committed its previous tile
               if (kb >= (uint32_t)kAdjStages && !mbar_wait(&empty[slot], ((kb / kAdjStages) - 1) & 1u)) {
                 ok = false;
                 break;
               }
               if (*(volatile int*)&s_abort) { ok = false; break; }
               mbar_arrive_expect_tx(&full[slot], (uint32_t)kAdjATile);
-              tma_load_2d(ring + (size_t)slot * kAdjATile, map, kc * 64, c * 128, &full[slot]);
+              if ((kb & 1u) == rank)
+                tma_load_2d_mc(ring + (size_t)slot * kAdjATile, map, kc * 64, c * 128, &full[slot], pair_mask);
             }
         }
       }
@@ -194,9 +207,12 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
         s_abort = 1;
         atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
       }
-      // every issued load must land before the block exits
-      for (uint32_t j = (kb > (uint32_t)kAdjStages ? kb - kAdjStages : 0u); j < kb; ++j)
+      // every load into this CTA (its own and the peer's) must land, and every commit of the peer's MMA
+      // warp must have arrived here, before the block exits
+      for (uint32_t j = (kb > (uint32_t)kAdjStages ? kb - kAdjStages : 0u); j < kb; ++j) {
         mbar_wait(&full[j % kAdjStages], (j / kAdjStages) & 1u);
+        mbar_wait(&empty[j % kAdjStages], (j / kAdjStages) & 1u);
+      }
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -206,7 +222,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       const uint32_t idesc = idesc_f16_bmn(128, 128, a.fmt);
       uint32_t kb = 0, na = 0;
       bool ok = true;
-      for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+      for (int pass = 0; pass < n_pass && ok; ++pass) {
         for (int s = 0; s < n_stages && ok; ++s) {
           int M, K;
           const CUtensorMap* map;
@@ -215,6 +231,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
           if (!mbar_wait(a_full, na & 1u)) { ok = false; break; }
           ++na;
           tc_fence_after();
+          // K-chunk by K-chunk, each M-tile's 4 K-steps back to back into its accumulator (interleaving
+          // the M-tiles' MMAs was measured slower)
           for (int kc = 0; kc < nK && ok; ++kc)
             for (int c = 0; c < nM; ++c, ++kb) {
               const int slot = (int)(kb % kAdjStages);
@@ -226,7 +244,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
                 const uint64_t bd = sw128_mn_desc(b_base + (uint32_t)(kc * 8 + kk * 2) * 1024u, kAdjLbo, 1024u);
                 tc_mma_f16(tmem + (uint32_t)(c * 128), ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
               }
-              tc_commit(&empty[slot]);
+              tc_commit_mc(&empty[slot], pair_mask);   // frees the slot in both CTAs' accounting
             }
           tc_commit(acc_full);
         }
@@ -242,15 +260,16 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
   } else if (warp >= kAdjCtlWarps) {
     regs_inc<kAdjRegsEpi>();   // the epilogue warpgroups
     // ------------------------------------------------------------------ epilogue warps
-    // Each thread owns kAdjNU neurons: nrn[0] in M-tile mt and, with two, nrn[1] = nrn[0] + 256 in M-tile
-    // mt + 2 (same TMEM lane), worked on side by side. The code below is written for up to two; with one,
-    // every second-neuron branch is dead.
+    // Each thread owns one neuron, nrn0, in M-tile mt (TMEM lane quarter q, lane `lane`).
     const int q = warp & 3;                    // TMEM lane quarter
     const int mt = (warp - kAdjCtlWarps) >> 2;   // M-tile of the thread's first neuron
     const int nrn0 = mt * 128 + q * 32 + lane;
-    const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * 128);   // + 256 for nrn[1]
+    const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * 128);
     const int etid = threadIdx.x - 32 * kAdjCtlWarps;
+    // per-CTA lambda scratch, [16 row blocks][stot neurons][8 rows]: a warp's 32 neurons of one row block
+    // are 512 contiguous bytes
     __half* scr = a.scratch + (size_t)blockIdx.x * a.stot * 128;
+    const size_t rb_stride = (size_t)a.stot * 8;
     const int n = a.widths[0];
     const bool output = target == a.L - 1;
     uint32_t nacc = 0, nbar = 0;
@@ -309,132 +328,126 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
     // tile starts on a group, so the role of row r0 + e with r0 a multiple of 8 NR is e mod NR: a
     // compile-time constant in the unrolled loops. Rows past the tile's valid rows carry zero cotangents
     // and a zero first operand, so every value derived from them is zero.
+    static_assert(kAdjNU == 1, "the epilogue passes are written for one neuron a thread");
     auto run_item = [&](auto nr_c, int t, int row0, int nrows, const float* gw, float ginv, float gscale) -> bool {
       constexpr int NR = decltype(nr_c)::value;
       constexpr int GS = 8 * NR;                 // rows per group: whole groups of NR, whole 8-column loads
       const int Kt = a.widths[target];
       // ---- prologue: B = (W_target rows o s_{target-1}) (difference form for output rows) ----------
-      // Both neurons of the thread go through the rows together, and the W_target entries of the next
-      // 8-row chunk (the row groups it touches, at most 4) are loaded while a chunk is written.
+      // Rows in chunks of 8 NR (8 whole groups; every row of a group starts from the same W_target entry,
+      // that of the group's state), the next chunk's entries loaded while a chunk is written.
       {
         const int Kp = (Kt + 63) & ~63;
-        const int nu = (kAdjNU == 2 && nrn0 + 256 < Kp) ? 2 : (nrn0 < Kp ? 1 : 0);   // neurons of this thread in the layer
-        if (nu > 0) {
-          bool live[2];
-          float sl[2], su[2], dd[2];
-          const float* wcol[2];
+        if (nrn0 < Kp) {
+          const bool live = nrn0 < Kt;
+          const long long o = (long long)t * a.H + a.hoff[target - 1] + (live ? nrn0 : 0);
+          const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f, dd = live ? a.D[o] : 0.f;
+          const float* wcol = a.W_target + (live ? nrn0 : 0);
+          // W_target entries of the 8 groups of the chunk at row r0 (0 for a group past the valid rows)
+          auto wload = [&](int r0, float (&w)[GS / NR]) {
 #pragma unroll
-          for (int u = 0; u < kAdjNU; ++u) {
-            const int j = nrn0 + 256 * u;
-            live[u] = u < nu && j < Kt;
-            const long long o = (long long)t * a.H + a.hoff[target - 1] + (live[u] ? j : 0);
-            sl[u] = live[u] ? a.sL[o] : 0.f;
-            su[u] = live[u] ? a.sU[o] : 0.f;
-            dd[u] = live[u] ? a.D[o] : 0.f;
-            wcol[u] = a.W_target + (live[u] ? j : 0);
-          }
-          // W_target entries of the row groups rb / NR .. rb / NR + 3 (0 for a group past the valid rows)
-          auto wload = [&](int rb, float2 (&w)[4]) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const int g = rb / NR + i;
-              const bool grp = NR * g + NR - 1 < nrows;
-              const long long wo = (long long)(row0 / NR + g) * Kt;
-              w[i].x = (live[0] && grp) ? __ldg(wcol[0] + wo) : 0.f;
-              w[i].y = (live[1] && grp) ? __ldg(wcol[1] + wo) : 0.f;
+            for (int i = 0; i < GS / NR; ++i) {
+              const int r = r0 + NR * i;
+              w[i] = (live && r + NR - 1 < nrows) ? __ldg(wcol + (long long)((row0 + r) / NR) * Kt) : 0.f;
             }
           };
-          float2 wn[4];
+          float wn[GS / NR];
           wload(0, wn);
 #pragma unroll 1
-          for (int rb = 0; rb < 128; rb += 8) {
-            const float2 wc[4] = {wn[0], wn[1], wn[2], wn[3]};
-            if (rb + 8 < 128) wload(rb + 8, wn);
-            const int off = rb % NR;
-            const uint32_t lm = NR == 3 ? (0x49u << ((3 - off) % 3)) & 0xFFu : (off == 0 ? 0x55u : 0xAAu);
-            const uint32_t jm = NR == 3 ? (0x49u << ((5 - off) % 3)) & 0xFFu : 0u;
-            float v0[8], v1[8];
+          for (int r0 = 0; r0 < 128; r0 += GS) {
+            float wc[GS / NR];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const bool isL = (lm >> e) & 1u, isJ = (jm >> e) & 1u;
-              const int gi = (off + e) / NR;   // group of row rb + e, relative to rb / NR
-              const float2 lam = gi == 0 ? wc[0] : (gi == 1 ? wc[1] : (gi == 2 ? wc[2] : wc[3]));
-              const float jd0 = NR == 3 ? lam.x * dd[0] : 0.f, jd1 = NR == 3 ? lam.y * dd[1] : 0.f;
-              const bool useL0 = isL == !signbit(lam.x), useL1 = isL == !signbit(lam.y);
-              v0[e] = isJ ? jd0 : fmaf(lam.x, useL0 ? sl[0] : su[0], -jd0);
-              v1[e] = isJ ? jd1 : fmaf(lam.y, useL1 ? sl[1] : su[1], -jd1);
+            for (int i = 0; i < GS / NR; ++i) wc[i] = wn[i];
+            if (r0 + GS < 128) wload(r0 + GS, wn);
+            const int nch = min(NR, (128 - r0) >> 3);
+            float v[GS];
+#pragma unroll
+            for (int i = 0; i < GS / NR; ++i) {
+              const int e = NR * i;
+              const float w = wc[i];
+              const bool c = !signbit(w);
+              const float2 sv = make_float2(c ? sl : su, c ? su : sl);
+              if (NR == 3) {
+                const float jd = w * dd;
+                const float2 vp = __ffma2_rn(make_float2(w, w), sv, make_float2(-jd, -jd));
+                v[e] = vp.x;
+                v[e + 1] = vp.y;
+                v[e + 2] = jd;
+              } else {
+                const float2 vp = __fmul2_rn(make_float2(w, w), sv);
+                v[e] = vp.x;
+                v[e + 1] = vp.y;
+              }
             }
-            put8(rb, nrn0, v0);
-            if (nu > 1) put8(rb, nrn0 + 256, v1);
+#pragma unroll
+            for (int h = 0; h < NR; ++h)
+              if (h < nch) put8(r0 + 8 * h, nrn0, v + 8 * h);
           }
         }
         operand_ready();
       }
       // ---- forward stages k = target-1 .. 1 --------------------------------------------------------
+      // Rows in chunks of 8 NR as in the backward stages; a group's lower- and upper-bound rows as a pair.
       for (int k = target - 1; k >= 1; --k) {
         pf_vec(t, k - 1, false);
         if (!wait_acc()) return false;
         const int N = a.widths[k];             // neurons of hidden layer k-1 (rows of this product)
         const int Np = (N + 63) & ~63;
-#pragma unroll
-        for (int u = 0; u < kAdjNU; ++u) {
-          const int j = nrn0 + 256 * u;
-          if (j >= Np) continue;
-          const bool live = j < N;
-          const long long o = (long long)t * a.H + a.hoff[k - 1] + (live ? j : 0);
+        if (nrn0 < Np) {
+          const bool live = nrn0 < N;
+          const long long o = (long long)t * a.H + a.hoff[k - 1] + (live ? nrn0 : 0);
           const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f, dd = live ? a.D[o] : 0.f;
-          __half* lrow = scr + (size_t)(a.soff[k - 1] + (live ? j : 0)) * 128;
-          const uint32_t tl = t_lane + 256u * u;
+          __half* lcol = scr + (size_t)(a.soff[k - 1] + (live ? nrn0 : 0)) * 8;
 #pragma unroll 1
           for (int r0 = 0; r0 < 128; r0 += GS) {
             const int nch = min(NR, (128 - r0) >> 3);
             float d[GS];
 #pragma unroll
             for (int h = 0; h < NR; ++h) {
-              if (h < nch) tmem_ld8_nowait(tl + (uint32_t)(r0 + 8 * h), d + 8 * h);
+              if (h < nch) tmem_ld8_nowait(t_lane + (uint32_t)(r0 + 8 * h), d + 8 * h);
               else
 #pragma unroll
                 for (int e = 0; e < 8; ++e) d[8 * h + e] = 0.f;   // rows past the tile
             }
             tmem_wait_ld();
-            if (NR == 3)
-#pragma unroll
-              for (int e = 0; e < GS; e += NR) {
-                d[e] += d[e + 2];               // lambda of the lower row
-                d[e + 1] += d[e + 2];           // lambda of the upper row
-              }
-            // lambda is kept in FP16 for the backward pass, and the line choice (sign of lambda) is made
-            // on that stored value here and there alike
-            __half lh[GS];
-#pragma unroll
-            for (int e = 0; e < GS; ++e) lh[e] = __float2half_rn(d[e]);
             float v[GS];
 #pragma unroll
-            for (int e = 0; e < GS; e += NR) {
-              const bool nl = !(__half_as_ushort(lh[e]) & 0x8000u), nu_ = !(__half_as_ushort(lh[e + 1]) & 0x8000u);
+            for (int i = 0; i < GS / NR; ++i) {
+              const int e = NR * i;
+              float2 dp = make_float2(d[e], d[e + 1]);
+              if (NR == 3) dp = __fadd2_rn(dp, make_float2(d[e + 2], d[e + 2]));   // lambda = delta + lambda^J
+              d[e] = dp.x;
+              d[e + 1] = dp.y;
+              // the line choice (sign of lambda) is that of the FP16 value kept for the backward pass:
+              // rounding keeps the sign bit, so the FP32 sign bit decides alike
+              const bool cl = !signbit(dp.x), cu = !signbit(dp.y);
+              const float2 sv = make_float2(cl ? sl : su, cu ? su : sl);
               if (NR == 3) {
                 const float jd = d[e + 2] * dd;
-                v[e] = fmaf(d[e], nl ? sl : su, -jd);
-                v[e + 1] = fmaf(d[e + 1], nu_ ? su : sl, -jd);
-                v[e + NR - 1] = jd;
+                const float2 vp = __ffma2_rn(dp, sv, make_float2(-jd, -jd));
+                v[e] = vp.x;
+                v[e + 1] = vp.y;
+                v[e + 2] = jd;
               } else {
-                v[e] = d[e] * (nl ? sl : su);
-                v[e + 1] = d[e + 1] * (nu_ ? su : sl);
+                const float2 vp = __fmul2_rn(dp, sv);
+                v[e] = vp.x;
+                v[e + 1] = vp.y;
               }
             }
 #pragma unroll
             for (int h = 0; h < NR; ++h)
-              if (h < nch) put8(r0 + 8 * h, j, v + 8 * h);
+              if (h < nch) put8(r0 + 8 * h, nrn0, v + 8 * h);
+            // lambda is kept in FP16 for the backward pass
             if (live)
 #pragma unroll
               for (int h = 0; h < NR; ++h)
                 if (h < nch) {
                   uint4 q4;
-                  q4.x = (uint32_t)__half_as_ushort(lh[8 * h]) | ((uint32_t)__half_as_ushort(lh[8 * h + 1]) << 16);
-                  q4.y = (uint32_t)__half_as_ushort(lh[8 * h + 2]) | ((uint32_t)__half_as_ushort(lh[8 * h + 3]) << 16);
-                  q4.z = (uint32_t)__half_as_ushort(lh[8 * h + 4]) | ((uint32_t)__half_as_ushort(lh[8 * h + 5]) << 16);
-                  q4.w = (uint32_t)__half_as_ushort(lh[8 * h + 6]) | ((uint32_t)__half_as_ushort(lh[8 * h + 7]) << 16);
-                  *reinterpret_cast<uint4*>(lrow + r0 + 8 * h) = q4;
+                  q4.x = pack2(d[8 * h], d[8 * h + 1], 0);
+                  q4.y = pack2(d[8 * h + 2], d[8 * h + 3], 0);
+                  q4.z = pack2(d[8 * h + 4], d[8 * h + 5], 0);
+                  q4.w = pack2(d[8 * h + 6], d[8 * h + 7], 0);
+                  *reinterpret_cast<uint4*>(lcol + (size_t)((r0 >> 3) + h) * rb_stride) = q4;
                 }
           }
         }
@@ -497,150 +510,122 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
         operand_ready();
       }
       // ---- backward stages k = 0 .. target-1 -------------------------------------------------------
-      // The thread's neurons go side by side.
+      // Rows go in chunks of 8 NR (whole row groups and whole 8-row TMEM loads), so the role of every row
+      // is a compile-time constant; a group's lower- and upper-bound rows are worked on as a pair with
+      // packed FP32x2 arithmetic (.x the lower-bound row, .y the upper-bound row).
+      const float2 ginv2 = make_float2(ginv, ginv);
       for (int k = 0; k < target; ++k) {
         pf_vec(t, k, true);
         if (!wait_acc()) return false;
         const int N = a.widths[k + 1];            // neurons of hidden layer k
         const bool last = k == target - 1;
         const int Np = (N + 63) & ~63;
-        const int nu = (kAdjNU == 2 && nrn0 + 256 < Np) ? 2 : (nrn0 < Np ? 1 : 0);   // neurons of this thread in the layer
-        if (nu > 0) {
-          bool live[2];
-          long long o[2];
-          float sl[2], su[2], tlv[2], tu[2], dd[2];
-          const __half* lrow[2];
-          const float* wcol[2];
-#pragma unroll
-          for (int u = 0; u < kAdjNU; ++u) {
-            const int j = nrn0 + 256 * u;
-            live[u] = u < nu && j < N;
-            o[u] = (long long)t * a.H + a.hoff[k] + (live[u] ? j : 0);
-            sl[u] = live[u] ? a.sL[o[u]] : 0.f;
-            su[u] = live[u] ? a.sU[o[u]] : 0.f;
-            tlv[u] = live[u] ? a.tL[o[u]] : 0.f;
-            tu[u] = live[u] ? a.tU[o[u]] : 0.f;
-            dd[u] = live[u] ? a.D[o[u]] : 0.f;
-            lrow[u] = scr + (size_t)((last ? 0 : a.soff[k]) + (live[u] ? j : 0)) * 128;
-            wcol[u] = a.W_target + (live[u] ? j : 0);
-          }
-          const float2 dd2 = make_float2(dd[0], dd[1]);
-          float2 SL = make_float2(0.f, 0.f), SU = SL, TL = SL, TU = SL, GD = SL;
-          float2 wv = SL;   // lambda_{target-1} of the current row group (last stage), carried across chunks
-          // 16-row chunks; the roles of a chunk's rows as bit masks (bit e: row rb + e): Jacobian rows, and
-          // rows whose lower line is chosen when lambda >= 0 (lower-bound rows)
+        if (nrn0 < Np) {
+          const bool live = nrn0 < N;
+          const long long o = (long long)t * a.H + a.hoff[k] + (live ? nrn0 : 0);
+          const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f;
+          const float tl = live ? a.tL[o] : 0.f, tu = live ? a.tU[o] : 0.f, dd = live ? a.D[o] : 0.f;
+          const __half* lcol = scr + (size_t)((last ? 0 : a.soff[k]) + (live ? nrn0 : 0)) * 8;
+          const float* wcol = a.W_target + (live ? nrn0 : 0);
+          const float2 z2 = make_float2(0.f, 0.f);
+          float2 SL = z2, SU = z2, TL = z2, TU = z2;   // per-neuron sums over the rows choosing each line
+          float GD = 0.f;
 #pragma unroll 1
-          for (int rb = 0; rb < 128; rb += 16) {
-            const int off = rb % NR;       // role of row rb (tiles start on a row group)
-            // role-0 rows: e = -off mod NR (+ NR, ...); Jacobian rows (NR = 3): e = 2 - off mod 3 (+ 3, ...)
-            const uint32_t lm = NR == 3 ? (0x9249u << ((3 - off) % 3)) & 0xFFFFu : (off == 0 ? 0x5555u : 0xAAAAu);
-            const uint32_t jm = NR == 3 ? (0x9249u << ((5 - off) % 3)) & 0xFFFFu : 0u;
-            float ga0[16], ga1[16], l0[16], l1[16], g[16];
-            tmem_ld16_nowait(t_lane + (uint32_t)rb, ga0);
-            if (nu > 1) tmem_ld16_nowait(t_lane + 256u + (uint32_t)rb, ga1);
+          for (int r0 = 0; r0 < 128; r0 += GS) {
+            const int nch = min(NR, (128 - r0) >> 3);   // 8-row parts inside the tile
+            float x[GS], lam[GS], g[GS];
+#pragma unroll
+            for (int h = 0; h < NR; ++h) {
+              if (h < nch) tmem_ld8_nowait(t_lane + (uint32_t)(r0 + 8 * h), x + 8 * h);
+              else
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[8 * h + e] = 0.f;   // rows past the tile
+            }
             if (!last) {
 #pragma unroll
-              for (int e = 0; e < 16; e += 8) {
-                const uint4 v = *reinterpret_cast<const uint4*>(lrow[0] + rb + e);
-                const uint4 w = nu > 1 ? *reinterpret_cast<const uint4*>(lrow[1] + rb + e) : make_uint4(0u, 0u, 0u, 0u);
-                const uint32_t vv[4] = {v.x, v.y, v.z, v.w}, ww[4] = {w.x, w.y, w.z, w.w};
+              for (int h = 0; h < NR; ++h) {
+                const uint4 v = h < nch ? *reinterpret_cast<const uint4*>(lcol + (size_t)((r0 >> 3) + h) * rb_stride)
+                                        : make_uint4(0u, 0u, 0u, 0u);
+                const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                  const float2 a2 = __half22float2(*reinterpret_cast<const __half2*>(&vv[h]));
-                  const float2 b2 = __half22float2(*reinterpret_cast<const __half2*>(&ww[h]));
-                  l0[e + 2 * h] = a2.x; l0[e + 2 * h + 1] = a2.y;
-                  l1[e + 2 * h] = b2.x; l1[e + 2 * h + 1] = b2.y;
+                for (int q2 = 0; q2 < 4; ++q2) {
+                  const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&vv[q2]));
+                  lam[8 * h + 2 * q2] = f.x;
+                  lam[8 * h + 2 * q2 + 1] = f.y;
                 }
               }
             } else {
-              // lambda_{target-1}: the W_target row of each row's state, loaded at the group's first row
-              // (role 0) and carried to the group's other rows, also across chunks
+              // lambda_{target-1}: the W_target row of each group's state, the same for the group's rows
 #pragma unroll
-              for (int e = 0; e < 16; ++e) {
-                if ((lm >> e) & 1u) {
-                  const int r = rb + e;
-                  const bool grp = r + NR - 1 < nrows;
-                  const long long wo = (long long)((row0 + r) / NR) * Kt;
-                  wv.x = (live[0] && grp) ? __ldg(wcol[0] + wo) : 0.f;
-                  wv.y = (live[1] && grp) ? __ldg(wcol[1] + wo) : 0.f;
-                }
-                l0[e] = wv.x;
-                l1[e] = wv.y;
+              for (int i = 0; i < GS / NR; ++i) {
+                const int r = r0 + NR * i;
+                const float wv = (live && r + NR - 1 < nrows) ? __ldg(wcol + (long long)((row0 + r) / NR) * Kt) : 0.f;
+#pragma unroll
+                for (int h = 0; h < NR; ++h) lam[NR * i + h] = wv;
               }
             }
 #pragma unroll
-            for (int e = 0; e < 16; e += 4) {
-              const float4 v = *reinterpret_cast<const float4*>(gw + rb + e);
-              g[e] = v.x * ginv; g[e + 1] = v.y * ginv; g[e + 2] = v.z * ginv; g[e + 3] = v.w * ginv;
+            for (int h = 0; h < NR; ++h) {
+              float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+              if (h < nch) {
+                v0 = *reinterpret_cast<const float4*>(gw + r0 + 8 * h);
+                v1 = *reinterpret_cast<const float4*>(gw + r0 + 8 * h + 4);
+              }
+              g[8 * h] = v0.x; g[8 * h + 1] = v0.y; g[8 * h + 2] = v0.z; g[8 * h + 3] = v0.w;
+              g[8 * h + 4] = v1.x; g[8 * h + 5] = v1.y; g[8 * h + 6] = v1.z; g[8 * h + 7] = v1.w;
             }
             tmem_wait_ld();
-            if (nu < 2)
+            float Gv[GS];
 #pragma unroll
-              for (int e = 0; e < 16; ++e) ga1[e] = 0.f;
-            float G0[16], G1[16];
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const bool isJ = (jm >> e) & 1u, isL = (lm >> e) & 1u;
-              // scalar arithmetic: the two neurons' values sit in separate arrays, so packed FP32x2
-              // operations would first have to move them into register pairs
-              const float x0 = ga0[e], x1 = ga1[e], la = l0[e], lb = l1[e];
-              const float p10 = x0 * la, p11 = x1 * lb, p20 = g[e] * la, p21 = g[e] * lb;
-              // lower line chosen (sg) / upper line chosen (ng); both 0 on Jacobian rows. The choice is
-              // the sign bit of the stored lambda, as in the forward recompute.
-              const bool u0 = isL == !signbit(la), u1 = isL == !signbit(lb);
-              const float sg0 = !isJ && u0 ? 1.f : 0.f, sg1 = !isJ && u1 ? 1.f : 0.f;
-              const float ng0 = !isJ && !u0 ? 1.f : 0.f, ng1 = !isJ && !u1 ? 1.f : 0.f;
-              SL.x = fmaf(sg0, p10, SL.x);
-              SL.y = fmaf(sg1, p11, SL.y);
-              SU.x = fmaf(ng0, p10, SU.x);
-              SU.y = fmaf(ng1, p11, SU.y);
-              TL.x = fmaf(sg0, p20, TL.x);
-              TL.y = fmaf(sg1, p21, TL.y);
-              TU.x = fmaf(ng0, p20, TU.x);
-              TU.y = fmaf(ng1, p21, TU.y);
-              float2 G;
-              if (isJ) {
-                GD.x += p10;
-                GD.y += p11;
-                G = make_float2(x0 * dd2.x, x1 * dd2.y);
-              } else {
-                const float sv0 = u0 ? sl[0] : su[0], sv1 = u1 ? sl[1] : su[1];
-                const float tv0 = u0 ? tlv[0] : tu[0], tv1 = u1 ? tlv[1] : tu[1];
-                G = make_float2(fmaf(x0, sv0, g[e] * tv0), fmaf(x1, sv1, g[e] * tv1));
-              }
-              G0[e] = G.x;
-              G1[e] = G.y;
-            }
-            if (!last) {
-              put8(rb, nrn0, G0);
-              put8(rb + 8, nrn0, G0 + 8);
-              if (nu > 1) {
-                put8(rb, nrn0 + 256, G1);
-                put8(rb + 8, nrn0 + 256, G1 + 8);
+            for (int i = 0; i < GS / NR; ++i) {
+              const int e = NR * i;
+              const float2 xp = make_float2(x[e], x[e + 1]), lp = make_float2(lam[e], lam[e + 1]);
+              const float2 gp = __fmul2_rn(make_float2(g[e], g[e + 1]), ginv2);
+              const float2 p1 = __fmul2_rn(xp, lp), p2 = __fmul2_rn(gp, lp);
+              // the lower line is chosen on a lower-bound row where lambda >= 0 and on an upper-bound row
+              // where lambda < 0: the sign bit of the stored lambda, as in the forward recompute
+              const bool cl = !signbit(lp.x), cu = signbit(lp.y);
+              const float2 on = make_float2(cl ? 1.f : 0.f, cu ? 1.f : 0.f);
+              const float2 off = make_float2(cl ? 0.f : 1.f, cu ? 0.f : 1.f);
+              SL = __ffma2_rn(on, p1, SL);
+              SU = __ffma2_rn(off, p1, SU);
+              TL = __ffma2_rn(on, p2, TL);
+              TU = __ffma2_rn(off, p2, TU);
+              const float2 sv = make_float2(cl ? sl : su, cu ? sl : su), tv = make_float2(cl ? tl : tu, cu ? tl : tu);
+              const float2 G = __ffma2_rn(xp, sv, __fmul2_rn(gp, tv));
+              Gv[e] = G.x;
+              Gv[e + 1] = G.y;
+              if (NR == 3) {   // the Jacobian row
+                GD = fmaf(x[e + 2], lam[e + 2], GD);
+                Gv[e + 2] = x[e + 2] * dd;
               }
             }
+            if (!last)
+#pragma unroll
+              for (int h = 0; h < NR; ++h)
+                if (h < nch) put8(r0 + 8 * h, nrn0, Gv + 8 * h);
           }
-          const float gsl[2] = {SL.x, SL.y}, gsu[2] = {SU.x, SU.y}, gtl[2] = {TL.x, TL.y}, gtu[2] = {TU.x, TU.y};
-          const float gd[2] = {GD.x, GD.y};
-#pragma unroll
-          for (int u = 0; u < kAdjNU; ++u)
-            if (live[u]) {
-              if (gsl[u] != 0.f) atomicAdd(a.gsL + o[u], gsl[u] * gscale);
-              if (gsu[u] != 0.f) atomicAdd(a.gsU + o[u], gsu[u] * gscale);
-              if (gtl[u] != 0.f) atomicAdd(a.gtL + o[u], gtl[u] * gscale);
-              if (gtu[u] != 0.f) atomicAdd(a.gtU + o[u], gtu[u] * gscale);
-              if (gd[u] != 0.f) atomicAdd(a.gD + o[u], gd[u] * gscale);
-            }
+          if (live) {
+            const float gsl = SL.x + SL.y, gsu = SU.x + SU.y, gtl = TL.x + TL.y, gtu = TU.x + TU.y;
+            if (gsl != 0.f) atomicAdd(a.gsL + o, gsl * gscale);
+            if (gsu != 0.f) atomicAdd(a.gsU + o, gsu * gscale);
+            if (gtl != 0.f) atomicAdd(a.gtL + o, gtl * gscale);
+            if (gtu != 0.f) atomicAdd(a.gtU + o, gtu * gscale);
+            if (GD != 0.f) atomicAdd(a.gD + o, GD * gscale);
+          }
         }
         if (!last) operand_ready();
       }
       return true;
     };
 
-    for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
-      const int t = item / a.tiles_per_t, tile = item - t * a.tiles_per_t;
+    for (int pass = 0; pass < n_pass && ok; ++pass) {
+      const int item = (int)blockIdx.x + pass * (int)gridDim.x;
+      const bool dummy = item >= n_items;   // the pair's second CTA past the last item: no valid rows
+      const int ie = dummy ? n_items - 1 : item;
+      const int t = ie / a.tiles_per_t, tile = ie - t * a.tiles_per_t;
       const int row0 = tile * a.rows_per_tile;
-      const int nrows = min(a.rows_per_tile, a.rows_total - row0);   // valid rows of this tile
+      const int nrows = dummy ? 0 : min(a.rows_per_tile, a.rows_total - row0);   // valid rows of this tile
       // ---- row cotangents of the tile (0 past the valid rows) and their scale ----------------------
       float* gw = gws + gb * 128;
       if (etid < 128) {
@@ -679,6 +664,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync_all();   // neither CTA leaves while the other can still load into it or arrive on it
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem, 512);
 }
@@ -709,6 +695,7 @@ struct AdjState {
   uint16_t* W[kMaxLayers] = {};   // W_k rounded to the operand format, row-major [widths[k+1], widths[k]]
   CUtensorMap fwd[kMaxLayers];
   CUtensorMap bwd[kMaxLayers];
+  int max_pairs = 0;              // CTA pairs (clusters of 2) resident at once
 };
 
 bool encode(CUtensorMap* map, const void* ptr, int rows, int cols, int fmt) {
@@ -749,6 +736,18 @@ leb_status adj_tc_prepare(Ctx& c) {
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, adjoint_tc_kernel) != cudaSuccess) return LEB_ERR_CUDA;
   if (fa.numRegs < kAdjRegsLaunchMin) return LEB_ERR_UNSUPPORTED;
+  // a GPC with an odd number of free SMs leaves one of them out of every pair: size the grid by the pairs
+  // that fit at once, so that no pair waits for a second wave
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(c.sm_count & ~1));
+  cfg.blockDim = dim3(kAdjThreads);
+  cfg.dynamicSmemBytes = kAdjSmem;
+  int pairs = 0;
+  if (cudaOccupancyMaxActiveClusters(&pairs, (const void*)adjoint_tc_kernel, &cfg) != cudaSuccess || pairs < 1) {
+    (void)cudaGetLastError();
+    pairs = c.sm_count / 2;
+  }
+  st->max_pairs = pairs < c.sm_count / 2 ? pairs : c.sm_count / 2;
   return LEB_OK;
 }
 
@@ -818,8 +817,11 @@ leb_status adj_tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* 
   a.scratch = reinterpret_cast<__half*>(ws + L.adj);
   a.flags = flags;
   const int items = T * a.tiles_per_t;
-  const int grid = items < c.sm_count ? items : c.sm_count;
-  if (grid == 0) return LEB_OK;
+  if (items == 0) return LEB_OK;
+  // CTA pairs: an even grid of at most one CTA per SM (the per-CTA scratch holds sm_count CTAs)
+  const int max_grid = 2 * st->max_pairs;
+  if (max_grid < 2) return LEB_ERR_UNSUPPORTED;
+  const int grid = ((items + 1) & ~1) < max_grid ? ((items + 1) & ~1) : max_grid;
   timer_begin(c, s, "adjoint_tc_kernel");
   adjoint_tc_kernel<<<grid, kAdjThreads, kAdjSmem, s>>>(a);
   timer_end(c, s);
