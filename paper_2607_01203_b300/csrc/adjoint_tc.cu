@@ -104,12 +104,7 @@ __device__ __forceinline__ uint32_t b_off8(int r0, int j) {
   return (uint32_t)((r0 >> 6) * kAdjLbo + (j >> 3) * 1024 + (j & 7) * 128 + ((((r0 & 63) >> 3) ^ (j & 7)) << 4));
 }
 
-// CTAs run in pairs (a cluster of 2) that stream the weight tiles together: tile kb of the sequence both
-// walk is loaded by CTA kb mod 2 and multicast to both, so each pair reads every weight tile from L2 once.
-// Both CTAs of a pair therefore walk the same number of items (the first CTA's count; a CTA past the
-// last item works on an item with no valid rows, which writes nothing outside its own scratch).
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
-    adjoint_tc_kernel(const __grid_constant__ AdjTcArgs a) {
+__global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid_constant__ AdjTcArgs a) {
   extern __shared__ uint8_t sraw[];
   // 1024-byte aligned base, as an offset from the shared array (so that every derived pointer keeps the
   // shared address space and its accesses compile to shared-memory instructions)
@@ -131,16 +126,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_items = a.T * a.tiles_per_t;
   const int target = a.target;
-  const uint32_t rank = cluster_ctarank();   // 0 or 1 in the pair
-  const uint16_t pair_mask = 3u;
-  // items of this CTA: blockIdx.x + j gridDim.x for j < n_pass (the pair's first CTA has the most)
-  const int first = (int)blockIdx.x & ~1;
-  const int n_pass = first < n_items ? (n_items - first + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  // items of this CTA: blockIdx.x + j gridDim.x for j < n_pass
+  const int n_pass = (int)blockIdx.x < n_items ? (n_items - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kAdjStages; ++s) {
-      mbar_init(&full[s], 1);    // this CTA's expect-tx; the bytes come from either CTA's load
-      mbar_init(&empty[s], 2);   // both CTAs' MMA warps have read the slot
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
     }
     mbar_init(a_full, kAdjEpiWarps);
     mbar_init(acc_full, 1);
@@ -152,7 +144,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
   if (warp == 1) tmem_alloc(&tmem_slot, 512);
   tc_fence_before();
   __syncthreads();
-  cluster_sync_all();   // the peer's barriers are initialised before any load or commit reaches them
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
@@ -191,15 +182,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
           for (int kc = 0; kc < nK && ok; ++kc)
             for (int c = 0; c < nM; ++c, ++kb) {
               const int slot = (int)(kb % kAdjStages);
-              // the slot is free in both CTAs once both MMA warps have committed its previous tile
               if (kb >= (uint32_t)kAdjStages && !mbar_wait(&empty[slot], ((kb / kAdjStages) - 1) & 1u)) {
                 ok = false;
                 break;
               }
               if (*(volatile int*)&s_abort) { ok = false; break; }
               mbar_arrive_expect_tx(&full[slot], (uint32_t)kAdjATile);
-              if ((kb & 1u) == rank)
-                tma_load_2d_mc(ring + (size_t)slot * kAdjATile, map, kc * 64, c * 128, &full[slot], pair_mask);
+              tma_load_2d(ring + (size_t)slot * kAdjATile, map, kc * 64, c * 128, &full[slot]);
             }
         }
       }
@@ -207,12 +196,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
         s_abort = 1;
         atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
       }
-      // every load into this CTA (its own and the peer's) must land, and every commit of the peer's MMA
-      // warp must have arrived here, before the block exits
-      for (uint32_t j = (kb > (uint32_t)kAdjStages ? kb - kAdjStages : 0u); j < kb; ++j) {
+      // every issued load must land before the block exits
+      for (uint32_t j = (kb > (uint32_t)kAdjStages ? kb - kAdjStages : 0u); j < kb; ++j)
         mbar_wait(&full[j % kAdjStages], (j / kAdjStages) & 1u);
-        mbar_wait(&empty[j % kAdjStages], (j / kAdjStages) & 1u);
-      }
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -244,7 +230,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
                 const uint64_t bd = sw128_mn_desc(b_base + (uint32_t)(kc * 8 + kk * 2) * 1024u, kAdjLbo, 1024u);
                 tc_mma_f16(tmem + (uint32_t)(c * 128), ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
               }
-              tc_commit_mc(&empty[slot], pair_mask);   // frees the slot in both CTAs' accounting
+              tc_commit(&empty[slot]);
             }
           tc_commit(acc_full);
         }
@@ -621,11 +607,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
 
     for (int pass = 0; pass < n_pass && ok; ++pass) {
       const int item = (int)blockIdx.x + pass * (int)gridDim.x;
-      const bool dummy = item >= n_items;   // the pair's second CTA past the last item: no valid rows
-      const int ie = dummy ? n_items - 1 : item;
-      const int t = ie / a.tiles_per_t, tile = ie - t * a.tiles_per_t;
+      const int t = item / a.tiles_per_t, tile = item - t * a.tiles_per_t;
       const int row0 = tile * a.rows_per_tile;
-      const int nrows = dummy ? 0 : min(a.rows_per_tile, a.rows_total - row0);   // valid rows of this tile
+      const int nrows = min(a.rows_per_tile, a.rows_total - row0);   // valid rows of this tile
       // ---- row cotangents of the tile (0 past the valid rows) and their scale ----------------------
       float* gw = gws + gb * 128;
       if (etid < 128) {
@@ -664,7 +648,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
-  cluster_sync_all();   // neither CTA leaves while the other can still load into it or arrive on it
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem, 512);
 }
@@ -695,7 +678,6 @@ struct AdjState {
   uint16_t* W[kMaxLayers] = {};   // W_k rounded to the operand format, row-major [widths[k+1], widths[k]]
   CUtensorMap fwd[kMaxLayers];
   CUtensorMap bwd[kMaxLayers];
-  int max_pairs = 0;              // CTA pairs (clusters of 2) resident at once
 };
 
 bool encode(CUtensorMap* map, const void* ptr, int rows, int cols, int fmt) {
@@ -736,18 +718,6 @@ leb_status adj_tc_prepare(Ctx& c) {
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, adjoint_tc_kernel) != cudaSuccess) return LEB_ERR_CUDA;
   if (fa.numRegs < kAdjRegsLaunchMin) return LEB_ERR_UNSUPPORTED;
-  // a GPC with an odd number of free SMs leaves one of them out of every pair: size the grid by the pairs
-  // that fit at once, so that no pair waits for a second wave
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(c.sm_count & ~1));
-  cfg.blockDim = dim3(kAdjThreads);
-  cfg.dynamicSmemBytes = kAdjSmem;
-  int pairs = 0;
-  if (cudaOccupancyMaxActiveClusters(&pairs, (const void*)adjoint_tc_kernel, &cfg) != cudaSuccess || pairs < 1) {
-    (void)cudaGetLastError();
-    pairs = c.sm_count / 2;
-  }
-  st->max_pairs = pairs < c.sm_count / 2 ? pairs : c.sm_count / 2;
   return LEB_OK;
 }
 
@@ -818,10 +788,7 @@ leb_status adj_tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* 
   a.flags = flags;
   const int items = T * a.tiles_per_t;
   if (items == 0) return LEB_OK;
-  // CTA pairs: an even grid of at most one CTA per SM (the per-CTA scratch holds sm_count CTAs)
-  const int max_grid = 2 * st->max_pairs;
-  if (max_grid < 2) return LEB_ERR_UNSUPPORTED;
-  const int grid = ((items + 1) & ~1) < max_grid ? ((items + 1) & ~1) : max_grid;
+  const int grid = items < c.sm_count ? items : c.sm_count;   // the per-CTA scratch holds sm_count CTAs
   timer_begin(c, s, "adjoint_tc_kernel");
   adjoint_tc_kernel<<<grid, kAdjThreads, kAdjSmem, s>>>(a);
   timer_end(c, s);
