@@ -51,7 +51,7 @@ constexpr int kAdjThreads = 32 * (kAdjCtlWarps + kAdjEpiWarps);
 // Register split (setmaxnreg): warpgroup 0 keeps 32 registers a thread, the epilogue warpgroups take 112.
 // The increases draw on what the block was launched with, so the compiled kernel must have at least
 // kAdjRegsLaunchMin registers a thread (checked before any launch).
-constexpr int kAdjRegsCtl = 48, kAdjRegsEpi = 104;
+constexpr int kAdjRegsCtl = 32, kAdjRegsEpi = 112;
 constexpr int kAdjRegsLaunchMin = (128 * kAdjRegsCtl + 32 * kAdjEpiWarps * kAdjRegsEpi + kAdjThreads - 1) / kAdjThreads;
 constexpr int kAdjStages = 6;                       // weight-tile ring
 constexpr int kAdjATile = 128 * 64 * 2;             // 128 neurons x 64 K x 2 bytes
@@ -516,81 +516,97 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
           const float2 z2 = make_float2(0.f, 0.f);
           float2 SL = z2, SU = z2, TL = z2, TU = z2;   // per-neuron sums over the rows choosing each line
           float GD = 0.f;
-#pragma unroll 1
-          for (int r0 = 0; r0 < 128; r0 += GS) {
-            const int nch = min(NR, (128 - r0) >> 3);   // 8-row parts inside the tile
-            float x[GS], lam[GS], g[GS];
-#pragma unroll
-            for (int h = 0; h < NR; ++h) {
-              if (h < nch) tmem_ld8_nowait(t_lane + (uint32_t)(r0 + 8 * h), x + 8 * h);
-              else
-#pragma unroll
-                for (int e = 0; e < 8; ++e) x[8 * h + e] = 0.f;   // rows past the tile
-            }
-            if (!last) {
-#pragma unroll
-              for (int h = 0; h < NR; ++h) {
-                const uint4 v = h < nch ? *reinterpret_cast<const uint4*>(lcol + (size_t)((r0 >> 3) + h) * rb_stride)
-                                        : make_uint4(0u, 0u, 0u, 0u);
-                const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int q2 = 0; q2 < 4; ++q2) {
-                  const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&vv[q2]));
-                  lam[8 * h + 2 * q2] = f.x;
-                  lam[8 * h + 2 * q2 + 1] = f.y;
+          // the chunk loop, compiled apart for the last stage (lambda = W_target entries) and the others
+          auto chunks = [&](auto last_c) {
+            constexpr bool LAST = decltype(last_c)::value;
+            // the chunk's stored lambdas (or W_target entries, last stage): loaded one chunk ahead for
+            // two-role rows, at the chunk itself for three-role rows (measured faster each way)
+            constexpr bool kAhead = NR == 2;
+            uint4 lnx[NR];
+            float wnx[GS / NR];
+            auto lam_load = [&](int r0) {
+              const int nch = min(NR, (128 - r0) >> 3);
+              if (!LAST) {
+  #pragma unroll
+                for (int h = 0; h < NR; ++h)
+                  lnx[h] = h < nch ? *reinterpret_cast<const uint4*>(lcol + (size_t)((r0 >> 3) + h) * rb_stride)
+                                   : make_uint4(0u, 0u, 0u, 0u);
+              } else {
+                // lambda_{target-1}: the W_target row of each group's state, the same for the group's rows
+  #pragma unroll
+                for (int i = 0; i < GS / NR; ++i) {
+                  const int r = r0 + NR * i;
+                  wnx[i] = (live && r + NR - 1 < nrows) ? __ldg(wcol + (long long)((row0 + r) / NR) * Kt) : 0.f;
                 }
               }
-            } else {
-              // lambda_{target-1}: the W_target row of each group's state, the same for the group's rows
-#pragma unroll
+            };
+            if (kAhead) lam_load(0);
+  #pragma unroll 1
+            for (int r0 = 0; r0 < 128; r0 += GS) {
+              const int nch = min(NR, (128 - r0) >> 3);   // 8-row parts inside the tile
+              float x[GS];
+              if (!kAhead) lam_load(r0);
+  #pragma unroll
+              for (int h = 0; h < NR; ++h) {
+                if (h < nch) tmem_ld8_nowait(t_lane + (uint32_t)(r0 + 8 * h), x + 8 * h);
+                else
+  #pragma unroll
+                  for (int e = 0; e < 8; ++e) x[8 * h + e] = 0.f;   // rows past the tile
+              }
+              // this chunk's lambdas: FP16 pairs (rows 2m, 2m+1 of the chunk in word m), or the group entries
+              uint32_t lw[4 * NR];
+              float wc[GS / NR];
+  #pragma unroll
+              for (int h = 0; h < NR; ++h) {
+                lw[4 * h] = lnx[h].x;
+                lw[4 * h + 1] = lnx[h].y;
+                lw[4 * h + 2] = lnx[h].z;
+                lw[4 * h + 3] = lnx[h].w;
+              }
+  #pragma unroll
+              for (int i = 0; i < GS / NR; ++i) wc[i] = wnx[i];
+              auto lam = [&](int e) -> float {
+                if (LAST) return wc[e / NR];
+                const __half2 hv = *reinterpret_cast<const __half2*>(&lw[e >> 1]);
+                return (e & 1) ? __high2float(hv) : __low2float(hv);
+              };
+              if (kAhead && r0 + GS < 128) lam_load(r0 + GS);
+              tmem_wait_ld();
+              float Gv[GS];
+  #pragma unroll
               for (int i = 0; i < GS / NR; ++i) {
-                const int r = r0 + NR * i;
-                const float wv = (live && r + NR - 1 < nrows) ? __ldg(wcol + (long long)((row0 + r) / NR) * Kt) : 0.f;
-#pragma unroll
-                for (int h = 0; h < NR; ++h) lam[NR * i + h] = wv;
+                const int e = NR * i;
+                const float2 xp = make_float2(x[e], x[e + 1]), lp = make_float2(lam(e), lam(e + 1));
+                // row cotangents from shared memory (0 for rows past the tile)
+                const float g0 = r0 + e < 128 ? gw[r0 + e] : 0.f, g1 = r0 + e + 1 < 128 ? gw[r0 + e + 1] : 0.f;
+                const float2 gp = __fmul2_rn(make_float2(g0, g1), ginv2);
+                const float2 p1 = __fmul2_rn(xp, lp), p2 = __fmul2_rn(gp, lp);
+                // the lower line is chosen on a lower-bound row where lambda >= 0 and on an upper-bound row
+                // where lambda < 0: the sign bit of the stored lambda, as in the forward recompute
+                const bool cl = !signbit(lp.x), cu = signbit(lp.y);
+                const float2 on = make_float2(cl ? 1.f : 0.f, cu ? 1.f : 0.f);
+                const float2 off = make_float2(cl ? 0.f : 1.f, cu ? 0.f : 1.f);
+                SL = __ffma2_rn(on, p1, SL);
+                SU = __ffma2_rn(off, p1, SU);
+                TL = __ffma2_rn(on, p2, TL);
+                TU = __ffma2_rn(off, p2, TU);
+                const float2 sv = make_float2(cl ? sl : su, cu ? sl : su), tv = make_float2(cl ? tl : tu, cu ? tl : tu);
+                const float2 G = __ffma2_rn(xp, sv, __fmul2_rn(gp, tv));
+                Gv[e] = G.x;
+                Gv[e + 1] = G.y;
+                if (NR == 3) {   // the Jacobian row
+                  GD = fmaf(x[e + 2], lam(e + 2), GD);
+                  Gv[e + 2] = x[e + 2] * dd;
+                }
               }
+              if (!last)
+  #pragma unroll
+                for (int h = 0; h < NR; ++h)
+                  if (h < nch) put8(r0 + 8 * h, nrn0, Gv + 8 * h);
             }
-#pragma unroll
-            for (int h = 0; h < NR; ++h) {
-              float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-              if (h < nch) {
-                v0 = *reinterpret_cast<const float4*>(gw + r0 + 8 * h);
-                v1 = *reinterpret_cast<const float4*>(gw + r0 + 8 * h + 4);
-              }
-              g[8 * h] = v0.x; g[8 * h + 1] = v0.y; g[8 * h + 2] = v0.z; g[8 * h + 3] = v0.w;
-              g[8 * h + 4] = v1.x; g[8 * h + 5] = v1.y; g[8 * h + 6] = v1.z; g[8 * h + 7] = v1.w;
-            }
-            tmem_wait_ld();
-            float Gv[GS];
-#pragma unroll
-            for (int i = 0; i < GS / NR; ++i) {
-              const int e = NR * i;
-              const float2 xp = make_float2(x[e], x[e + 1]), lp = make_float2(lam[e], lam[e + 1]);
-              const float2 gp = __fmul2_rn(make_float2(g[e], g[e + 1]), ginv2);
-              const float2 p1 = __fmul2_rn(xp, lp), p2 = __fmul2_rn(gp, lp);
-              // the lower line is chosen on a lower-bound row where lambda >= 0 and on an upper-bound row
-              // where lambda < 0: the sign bit of the stored lambda, as in the forward recompute
-              const bool cl = !signbit(lp.x), cu = signbit(lp.y);
-              const float2 on = make_float2(cl ? 1.f : 0.f, cu ? 1.f : 0.f);
-              const float2 off = make_float2(cl ? 0.f : 1.f, cu ? 0.f : 1.f);
-              SL = __ffma2_rn(on, p1, SL);
-              SU = __ffma2_rn(off, p1, SU);
-              TL = __ffma2_rn(on, p2, TL);
-              TU = __ffma2_rn(off, p2, TU);
-              const float2 sv = make_float2(cl ? sl : su, cu ? sl : su), tv = make_float2(cl ? tl : tu, cu ? tl : tu);
-              const float2 G = __ffma2_rn(xp, sv, __fmul2_rn(gp, tv));
-              Gv[e] = G.x;
-              Gv[e + 1] = G.y;
-              if (NR == 3) {   // the Jacobian row
-                GD = fmaf(x[e + 2], lam[e + 2], GD);
-                Gv[e + 2] = x[e + 2] * dd;
-              }
-            }
-            if (!last)
-#pragma unroll
-              for (int h = 0; h < NR; ++h)
-                if (h < nch) put8(r0 + 8 * h, nrn0, Gv + 8 * h);
-          }
+          };
+          if (last) chunks(std::true_type());
+          else chunks(std::false_type());
           if (live) {
             const float gsl = SL.x + SL.y, gsu = SU.x + SU.y, gtl = TL.x + TL.y, gtu = TU.x + TU.y;
             if (gsl != 0.f) atomicAdd(a.gsL + o, gsl * gscale);
