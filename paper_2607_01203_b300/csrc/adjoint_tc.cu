@@ -51,12 +51,12 @@ constexpr int kAdjThreads = 32 * (kAdjCtlWarps + kAdjEpiWarps);
 // Register split (setmaxnreg): warpgroup 0 keeps 32 registers a thread, the epilogue warpgroups take 112.
 // The increases draw on what the block was launched with, so the compiled kernel must have at least
 // kAdjRegsLaunchMin registers a thread (checked before any launch).
-constexpr int kAdjRegsCtl = 32, kAdjRegsEpi = 112;
+constexpr int kAdjRegsCtl = 40, kAdjRegsEpi = 104;
 constexpr int kAdjRegsLaunchMin = (128 * kAdjRegsCtl + 32 * kAdjEpiWarps * kAdjRegsEpi + kAdjThreads - 1) / kAdjThreads;
 constexpr int kAdjStages = 6;                       // weight-tile ring
 constexpr int kAdjATile = 128 * 64 * 2;             // 128 neurons x 64 K x 2 bytes
 constexpr int kAdjBRegion = 128 * 512 * 2;          // 128 rows x K <= 512 x 2 bytes
-constexpr int kAdjSmall = 1024 + 32 + 16 * 8;   // row cotangents, their scale, barriers
+constexpr int kAdjSmall = 1024 + 32 + 24 * 8;   // row cotangents [2 items][128], their scales, barriers
 constexpr int kAdjSmem = 1024 + kAdjBRegion + kAdjStages * kAdjATile + kAdjSmall;
 static_assert(kAdjSmem <= 227 * 1024, "adjoint tensor-core shared memory");
 
@@ -69,15 +69,15 @@ struct AdjTcArgs {
   int T, target, nroles, rows_total, rows_per_tile, tiles_per_t;
   int H;
   int hoff[kMaxLayers];
-  int soff[kMaxLayers];          // scratch offset (in neurons) of lambda_k, k = 0 .. target-2
-  int stot;                      // neurons per CTA scratch row block
+  int soff[kMaxLayers];          // scratch offset (in this CTA's neurons) of lambda_k, k = 0 .. target-2
+  int stot;                      // neurons per CTA scratch row block (each CTA holds 128 of every 256)
   const float* W_target;         // FP32 [widths[target+1], widths[target]]
   const float *sL, *sU, *tL, *tU, *D;   // [T, H]
   const float *dlo, *dhi;        // [T, n] the displacement box Delta = X - alpha~ (dlo <= 0 <= dhi)
   const float *g_lo, *g_hi;      // output target: [T, n_x]
   const float *gl, *gu;          // hidden target: [T, H]
   float *gsL, *gsU, *gtL, *gtU, *gD, *gdlo, *gdhi;
-  __half* scratch;               // gridDim.x x stot x 128 lambdas, FP16
+  __half* scratch;               // gridDim.x x stot x 256 lambdas, FP16
   int* flags;
 };
 
@@ -104,19 +104,28 @@ __device__ __forceinline__ uint32_t b_off8(int r0, int j) {
   return (uint32_t)((r0 >> 6) * kAdjLbo + (j >> 3) * 1024 + (j & 7) * 128 + ((((r0 & 63) >> 3) ^ (j & 7)) << 4));
 }
 
-__global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid_constant__ AdjTcArgs a) {
+// CTAs work in pairs (a cluster of 2) whose tensor cores act as one (.cta_group::2): a pass of a pair
+// takes two items, one per CTA, whose 2 x 128 rows are the N = 256 columns of every product; each CTA
+// holds its own item's per-row operand and half of every 256-neuron weight tile (neurons 128 r .. 128 r
+// + 127 of it, r the CTA's rank), so the pair streams each weight tile once for 256 rows. CTA 0 issues
+// the MMAs; each CTA's TMEM holds its 128 neurons of a tile for both items' rows. An epilogue thread owns
+// one neuron and the rows of one item, and writes the next operand's rows into the CTA that holds that
+// item (its own or the peer's shared memory). Both CTAs walk the same number of passes (a CTA past the
+// last item works on an item with no valid rows, which writes nothing outside its own scratch).
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
+    adjoint_tc_kernel(const __grid_constant__ AdjTcArgs a) {
   extern __shared__ uint8_t sraw[];
   // 1024-byte aligned base, as an offset from the shared array (so that every derived pointer keeps the
   // shared address space and its accesses compile to shared-memory instructions)
   uint8_t* base = sraw + ((1024u - (smem_u32(sraw) & 1023u)) & 1023u);
   uint8_t* Bop = base;                                   // per-row operand
   uint8_t* ring = base + kAdjBRegion;                    // weight tiles
-  float* gws = reinterpret_cast<float*>(ring + kAdjStages * kAdjATile);   // [2][128] row cotangents
-  float* wmax = gws + 256;                                                 // [2][4] per-warp max |g|
+  float* gws = reinterpret_cast<float*>(ring + kAdjStages * kAdjATile);   // [2 items][128] row cotangents
+  float* wmax = gws + 256;                                                 // [2 items][4] per-warp max |g|
   uint64_t* bars = reinterpret_cast<uint64_t*>(wmax + 8);
-  uint64_t* full = bars;                      // [kAdjStages]
-  uint64_t* empty = bars + kAdjStages;        // [kAdjStages]
-  uint64_t* a_full = bars + 2 * kAdjStages;   // operand written by the epilogue
+  uint64_t* full = bars;                      // [kAdjStages] (CTA 0) both CTAs' weight halves landed
+  uint64_t* empty = bars + kAdjStages;        // [kAdjStages] the pair's MMAs have read the slot
+  uint64_t* a_full = bars + 3 * kAdjStages;   // (CTA 0) both CTAs' operands written by their epilogues
   uint64_t* acc_full = a_full + 1;            // accumulators complete
   uint64_t* drain = acc_full + 1;
   uint64_t* ebar = drain + 1;                 // epilogue-warps barrier
@@ -126,24 +135,29 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_items = a.T * a.tiles_per_t;
   const int target = a.target;
-  // items of this CTA: blockIdx.x + j gridDim.x for j < n_pass
-  const int n_pass = (int)blockIdx.x < n_items ? (n_items - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  const uint32_t rank = cluster_ctarank();   // 0 or 1 in the pair
+  // pass j of pair P takes items 2 (P + j n_pairs) + h, h = 0, 1 (item h's rows live in CTA h)
+  const int P = (int)blockIdx.x >> 1, n_pairs = (int)gridDim.x >> 1;
+  const int n_pass = 2 * P < n_items ? (n_items - 2 * P + 2 * n_pairs - 1) / (2 * n_pairs) : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kAdjStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(a_full, kAdjEpiWarps);
+    mbar_init(a_full, 2 * kAdjEpiWarps);   // both CTAs' epilogue warps
     mbar_init(acc_full, 1);
     mbar_init(drain, 1);
     mbar_init(ebar, kAdjEpiWarps);
     mbar_fence_init();
     s_abort = 0;
   }
-  if (warp == 1) tmem_alloc(&tmem_slot, 512);
+  __syncthreads();
+  cluster_sync_all();   // the peer's barriers are initialised before any arrival reaches them
+  if (warp == 1) tmem_alloc_pair(&tmem_slot, 512);
   tc_fence_before();
   __syncthreads();
+  cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
@@ -173,22 +187,24 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       }
       uint32_t kb = 0;
       bool ok = true;
+      const uint32_t full0 = cluster_addr(full, 0u);   // both halves of a tile complete on CTA 0's barrier
       for (int pass = 0; pass < n_pass && ok; ++pass) {
         for (int s = 0; s < n_stages && ok; ++s) {
           int M, K;
           const CUtensorMap* map;
           stage_shape(s, M, K, map);
-          const int nM = (M + 127) / 128, nK = (K + 63) / 64;
+          const int nM = (M + 255) / 256, nK = (K + 63) / 64;   // 256-neuron tiles, this CTA's half of each
           for (int kc = 0; kc < nK && ok; ++kc)
             for (int c = 0; c < nM; ++c, ++kb) {
               const int slot = (int)(kb % kAdjStages);
-              if (kb >= (uint32_t)kAdjStages && !mbar_wait(&empty[slot], ((kb / kAdjStages) - 1) & 1u)) {
+              if (kb >= (uint32_t)kAdjStages && !mbar_wait_spin<false>(&empty[slot], ((kb / kAdjStages) - 1) & 1u)) {
                 ok = false;
                 break;
               }
               if (*(volatile int*)&s_abort) { ok = false; break; }
-              mbar_arrive_expect_tx(&full[slot], (uint32_t)kAdjATile);
-              tma_load_2d(ring + (size_t)slot * kAdjATile, map, kc * 64, c * 128, &full[slot]);
+              if (rank == 0) mbar_arrive_expect_tx(&full[slot], 2u * (uint32_t)kAdjATile);
+              tma_load_2d_pair(ring + (size_t)slot * kAdjATile, map, kc * 64, c * 256 + (int)rank * 128,
+                               full0 + (uint32_t)slot * 8u);
             }
         }
       }
@@ -196,16 +212,17 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
         s_abort = 1;
         atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
       }
-      // every issued load must land before the block exits
+      // the last tiles' MMAs (which read this CTA's loads) must have completed and their commits arrived
+      // here before the block exits
       for (uint32_t j = (kb > (uint32_t)kAdjStages ? kb - kAdjStages : 0u); j < kb; ++j)
-        mbar_wait(&full[j % kAdjStages], (j / kAdjStages) & 1u);
+        mbar_wait(&empty[j % kAdjStages], (j / kAdjStages) & 1u);
     }
     __syncwarp();
   } else if (warp == 1) {
-    // ------------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    if (lane == 0 && rank == 0) {
+      // ---------------------------------------------------------------- MMA issuer of the pair (CTA 0)
       const uint32_t ring_base = smem_u32(ring), b_base = smem_u32(Bop);
-      const uint32_t idesc = idesc_f16_bmn(128, 128, a.fmt);
+      const uint32_t idesc = idesc_f16_bmn(256, 256, a.fmt);
       uint32_t kb = 0, na = 0;
       bool ok = true;
       for (int pass = 0; pass < n_pass && ok; ++pass) {
@@ -213,53 +230,65 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
           int M, K;
           const CUtensorMap* map;
           stage_shape(s, M, K, map);
-          const int nM = (M + 127) / 128, nK = (K + 63) / 64;
-          if (!mbar_wait(a_full, na & 1u)) { ok = false; break; }
+          const int nM = (M + 255) / 256, nK = (K + 63) / 64;
+          // both CTAs' epilogues have written their operand (the peer's arrive from its CTA)
+          if (!mbar_wait_cluster(a_full, na & 1u)) { ok = false; break; }
           ++na;
           tc_fence_after();
-          // K-chunk by K-chunk, each M-tile's 4 K-steps back to back into its accumulator (interleaving
-          // the M-tiles' MMAs was measured slower)
+          // K-chunk by K-chunk, each tile's 4 K-steps back to back into its accumulator
           for (int kc = 0; kc < nK && ok; ++kc)
             for (int c = 0; c < nM; ++c, ++kb) {
               const int slot = (int)(kb % kAdjStages);
-              if (!mbar_wait(&full[slot], (kb / kAdjStages) & 1u)) { ok = false; break; }
+              if (!mbar_wait_spin<true>(&full[slot], (kb / kAdjStages) & 1u)) {   // both CTAs' halves
+                ok = false;
+                break;
+              }
               tc_fence_after();
 #pragma unroll
               for (int kk = 0; kk < 4; ++kk) {
                 const uint64_t ad = sw128_desc(ring_base + slot * kAdjATile + kk * 32);
                 const uint64_t bd = sw128_mn_desc(b_base + (uint32_t)(kc * 8 + kk * 2) * 1024u, kAdjLbo, 1024u);
-                tc_mma_f16(tmem + (uint32_t)(c * 128), ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                tc_mma_f16_pair(tmem + (uint32_t)(c * 256), ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
               }
-              tc_commit(&empty[slot]);
+              tc_commit_pair(&empty[slot], 3u);   // frees the slot in both CTAs
             }
-          tc_commit(acc_full);
+          tc_commit_pair(acc_full, 3u);
         }
       }
       if (!ok) {
         s_abort = 1;
         atomicOr(a.flags, LEB_ASYNC_TIMEOUT);
       }
-      tc_commit(drain);
+      tc_commit_pair(drain, 1u);
       mbar_wait(drain, 0);
     }
     __syncwarp();
   } else if (warp >= kAdjCtlWarps) {
     regs_inc<kAdjRegsEpi>();   // the epilogue warpgroups
     // ------------------------------------------------------------------ epilogue warps
-    // Each thread owns one neuron, nrn0, in M-tile mt (TMEM lane quarter q, lane `lane`).
-    const int q = warp & 3;                    // TMEM lane quarter
-    const int mt = (warp - kAdjCtlWarps) >> 2;   // M-tile of the thread's first neuron
-    const int nrn0 = mt * 128 + q * 32 + lane;
-    const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * 128);
+    // Each thread owns one neuron of 256-neuron tile pt, nrn0 = 256 pt + 128 rank + 32 q + lane (its
+    // index among this CTA's neurons: jl0 = 128 pt + 32 q + lane), for the rows of item hh (TMEM columns
+    // 256 pt + 128 hh ..); the prologue instead gives thread etid neuron etid of this CTA's own item.
+    const int ew = warp - kAdjCtlWarps;
+    const int q = ew & 3;                      // TMEM lane quarter
+    const int pt = (ew >> 2) & 1;              // 256-neuron tile
+    const int hh = ew >> 3;                    // the item whose rows the thread works on
+    const int nrn0 = pt * 256 + (int)rank * 128 + q * 32 + lane;
+    const int jl0 = pt * 128 + q * 32 + lane;
+    const uint32_t t_lane = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(pt * 256 + hh * 128);
     const int etid = threadIdx.x - 32 * kAdjCtlWarps;
-    // per-CTA lambda scratch, [16 row blocks][stot neurons][8 rows]: a warp's 32 neurons of one row block
-    // are 512 contiguous bytes
-    __half* scr = a.scratch + (size_t)blockIdx.x * a.stot * 128;
+    // per-CTA lambda scratch, [2 items x 16 row blocks][stot neurons of this CTA][8 rows]: a warp's 32
+    // neurons of one row block are 512 contiguous bytes
+    __half* scr = a.scratch + (size_t)blockIdx.x * a.stot * 256;
     const size_t rb_stride = (size_t)a.stot * 8;
+    __half* scr_item = scr + (size_t)hh * 16 * rb_stride;
+    // item hh's operand lives in CTA hh; operand-written arrivals go to CTA 0's barrier
+    const bool own_rows = hh == (int)rank;
+    const uint32_t bop_item = cluster_addr(Bop, (uint32_t)hh);
+    const uint32_t a_full0 = cluster_addr(a_full, 0u);
     const int n = a.widths[0];
     const bool output = target == a.L - 1;
     uint32_t nacc = 0, nbar = 0;
-    int gb = 0;
     bool ok = true;
     auto epi_sync = [&]() -> bool {
       __syncwarp();
@@ -270,9 +299,9 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
     };
     auto operand_ready = [&]() {
       tc_fence_before();
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(a_full);
+      fence_proxy_async_all();   // this thread's operand writes, here and in the peer, to the async proxy
+      __syncwarp();                // the warp's writes before lane 0's release at cluster scope
+      if (lane == 0) mbar_arrive_cluster(a_full0);
     };
     auto wait_acc = [&]() -> bool {
       if (!mbar_wait_warp(acc_full, nacc & 1u)) return false;
@@ -280,14 +309,22 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       tc_fence_after();
       return true;
     };
-    // 8 consecutive rows r0 .. r0 + 7 of neuron j into the operand (one 16-byte store)
-    auto put8 = [&](int r0, int j, const float* v) {
+    // 8 consecutive rows r0 .. r0 + 7 of neuron j into an operand (one 16-byte store): this CTA's own
+    // (prologue), or that of the thread's item (the peer's when the item's rows live there)
+    auto pack8 = [&](const float* v) {
       uint4 q;
       q.x = pack2(v[0], v[1], a.fmt);
       q.y = pack2(v[2], v[3], a.fmt);
       q.z = pack2(v[4], v[5], a.fmt);
       q.w = pack2(v[6], v[7], a.fmt);
-      *reinterpret_cast<uint4*>(Bop + b_off8(r0, j)) = q;
+      return q;
+    };
+    auto put8_own = [&](int r0, int j, const float* v) {
+      *reinterpret_cast<uint4*>(Bop + b_off8(r0, j)) = pack8(v);
+    };
+    auto put8 = [&](int r0, int j, const float* v) {
+      if (own_rows) *reinterpret_cast<uint4*>(Bop + b_off8(r0, j)) = pack8(v);
+      else st_cluster_v4(bop_item + b_off8(r0, j), pack8(v));
     };
 
     // Pulls the thread's neurons' entries of hidden layer hl's vectors (sL, sU, D and, with taus,
@@ -315,7 +352,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
     // compile-time constant in the unrolled loops. Rows past the tile's valid rows carry zero cotangents
     // and a zero first operand, so every value derived from them is zero.
     static_assert(kAdjNU == 1, "the epilogue passes are written for one neuron a thread");
-    auto run_item = [&](auto nr_c, int t, int row0, int nrows, const float* gw, float ginv, float gscale) -> bool {
+    auto run_item = [&](auto nr_c, int t, int row0, int nrows, const float* gw, float ginv, float gscale, int t_own,
+                        int row0_own, int nrows_own) -> bool {
       constexpr int NR = decltype(nr_c)::value;
       constexpr int GS = 8 * NR;                 // rows per group: whole groups of NR, whole 8-column loads
       const int Kt = a.widths[target];
@@ -324,17 +362,18 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
       // that of the group's state), the next chunk's entries loaded while a chunk is written.
       {
         const int Kp = (Kt + 63) & ~63;
-        if (nrn0 < Kp) {
-          const bool live = nrn0 < Kt;
-          const long long o = (long long)t * a.H + a.hoff[target - 1] + (live ? nrn0 : 0);
+        const int jp = etid;   // neuron of this CTA's own item's operand
+        if (jp < Kp) {
+          const bool live = jp < Kt;
+          const long long o = (long long)t_own * a.H + a.hoff[target - 1] + (live ? jp : 0);
           const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f, dd = live ? a.D[o] : 0.f;
-          const float* wcol = a.W_target + (live ? nrn0 : 0);
+          const float* wcol = a.W_target + (live ? jp : 0);
           // W_target entries of the 8 groups of the chunk at row r0 (0 for a group past the valid rows)
           auto wload = [&](int r0, float (&w)[GS / NR]) {
 #pragma unroll
             for (int i = 0; i < GS / NR; ++i) {
               const int r = r0 + NR * i;
-              w[i] = (live && r + NR - 1 < nrows) ? __ldg(wcol + (long long)((row0 + r) / NR) * Kt) : 0.f;
+              w[i] = (live && r + NR - 1 < nrows_own) ? __ldg(wcol + (long long)((row0_own + r) / NR) * Kt) : 0.f;
             }
           };
           float wn[GS / NR];
@@ -367,7 +406,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
             }
 #pragma unroll
             for (int h = 0; h < NR; ++h)
-              if (h < nch) put8(r0 + 8 * h, nrn0, v + 8 * h);
+              if (h < nch) put8_own(r0 + 8 * h, jp, v + 8 * h);
           }
         }
         operand_ready();
@@ -383,7 +422,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
           const bool live = nrn0 < N;
           const long long o = (long long)t * a.H + a.hoff[k - 1] + (live ? nrn0 : 0);
           const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f, dd = live ? a.D[o] : 0.f;
-          __half* lcol = scr + (size_t)(a.soff[k - 1] + (live ? nrn0 : 0)) * 8;
+          __half* lcol = scr_item + (size_t)(a.soff[k - 1] + (live ? jl0 : 0)) * 8;
 #pragma unroll 1
           for (int r0 = 0; r0 < 128; r0 += GS) {
             const int nch = min(NR, (128 - r0) >> 3);
@@ -511,7 +550,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
           const long long o = (long long)t * a.H + a.hoff[k] + (live ? nrn0 : 0);
           const float sl = live ? a.sL[o] : 0.f, su = live ? a.sU[o] : 0.f;
           const float tl = live ? a.tL[o] : 0.f, tu = live ? a.tU[o] : 0.f, dd = live ? a.D[o] : 0.f;
-          const __half* lcol = scr + (size_t)((last ? 0 : a.soff[k]) + (live ? nrn0 : 0)) * 8;
+          const __half* lcol = scr_item + (size_t)((last ? 0 : a.soff[k]) + (live ? jl0 : 0)) * 8;
           const float* wcol = a.W_target + (live ? nrn0 : 0);
           const float2 z2 = make_float2(0.f, 0.f);
           float2 SL = z2, SU = z2, TL = z2, TU = z2;   // per-neuron sums over the rows choosing each line
@@ -622,16 +661,25 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
     };
 
     for (int pass = 0; pass < n_pass && ok; ++pass) {
-      const int item = (int)blockIdx.x + pass * (int)gridDim.x;
-      const int t = item / a.tiles_per_t, tile = item - t * a.tiles_per_t;
-      const int row0 = tile * a.rows_per_tile;
-      const int nrows = min(a.rows_per_tile, a.rows_total - row0);   // valid rows of this tile
-      // ---- row cotangents of the tile (0 past the valid rows) and their scale ----------------------
-      float* gw = gws + gb * 128;
-      if (etid < 128) {
+      // the pass's two items (item h's rows live in CTA h); one past the last item has no valid rows
+      int it_t[2], it_row0[2], it_nrows[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int item = 2 * (P + pass * n_pairs) + h;
+        const bool dummy = item >= n_items;
+        const int ie = dummy ? n_items - 1 : item;
+        it_t[h] = ie / a.tiles_per_t;
+        it_row0[h] = (ie - it_t[h] * a.tiles_per_t) * a.rows_per_tile;
+        it_nrows[h] = dummy ? 0 : min(a.rows_per_tile, a.rows_total - it_row0[h]);   // valid rows of the tile
+      }
+      // ---- row cotangents of both tiles (0 past the valid rows) and their scales --------------------
+      if (pass > 0 && !epi_sync()) { ok = false; break; }   // every warp is done with the last pass's
+      if (etid < 256) {
+        const int h = etid >> 7, e = etid & 127;
+        const int t = h ? it_t[1] : it_t[0];
         float g = 0.f;
-        if (etid < nrows) {
-          const int grow = row0 + etid, role = grow % a.nroles, idx = grow / a.nroles;
+        if (e < (h ? it_nrows[1] : it_nrows[0])) {
+          const int grow = (h ? it_row0[1] : it_row0[0]) + e, role = grow % a.nroles, idx = grow / a.nroles;
           if (output) {
             const int nx = a.widths[a.L];
             g = role == 0 ? a.g_lo[(long long)t * nx + idx] : (role == 1 ? a.g_hi[(long long)t * nx + idx] : 0.f);
@@ -640,19 +688,23 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
             g = role == 0 ? a.gl[o] : a.gu[o];
           }
         }
-        gw[etid] = g;
+        gws[etid] = g;
         float m = fabsf(g);
 #pragma unroll
         for (int dlt = 16; dlt > 0; dlt >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, dlt));
-        if (lane == 0) wmax[gb * 4 + (etid >> 5)] = m;
+        if (lane == 0) wmax[etid >> 5] = m;   // [item][warp of 32 rows]
       }
       if (!epi_sync()) { ok = false; break; }
-      const float gmax = fmaxf(fmaxf(wmax[gb * 4], wmax[gb * 4 + 1]), fmaxf(wmax[gb * 4 + 2], wmax[gb * 4 + 3]));
+      const float* wm = wmax + hh * 4;
+      const float gmax = fmaxf(fmaxf(wm[0], wm[1]), fmaxf(wm[2], wm[3]));
       const float gscale = (gmax > 0.f && isfinite(gmax)) ? gmax : 1.f;
       const float ginv = 1.f / gscale;
-      gb ^= 1;
-      ok = output ? run_item(std::integral_constant<int, 3>(), t, row0, nrows, gw, ginv, gscale)
-                  : run_item(std::integral_constant<int, 2>(), t, row0, nrows, gw, ginv, gscale);
+      const float* gw = gws + hh * 128;
+      const int tm = hh ? it_t[1] : it_t[0], r0m = hh ? it_row0[1] : it_row0[0], nm = hh ? it_nrows[1] : it_nrows[0];
+      const int to = rank ? it_t[1] : it_t[0], r0o = rank ? it_row0[1] : it_row0[0];
+      const int no = rank ? it_nrows[1] : it_nrows[0];
+      ok = output ? run_item(std::integral_constant<int, 3>(), tm, r0m, nm, gw, ginv, gscale, to, r0o, no)
+                  : run_item(std::integral_constant<int, 2>(), tm, r0m, nm, gw, ginv, gscale, to, r0o, no);
       if (!ok) break;
       tc_fence_before();
       if (*(volatile int*)&s_abort) ok = false;
@@ -664,8 +716,9 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const __grid
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync_all();   // neither CTA leaves while the other can still write into it or arrive on it
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tmem, 512);
+  if (warp == 1) tmem_dealloc_pair(tmem, 512);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -694,6 +747,7 @@ struct AdjState {
   uint16_t* W[kMaxLayers] = {};   // W_k rounded to the operand format, row-major [widths[k+1], widths[k]]
   CUtensorMap fwd[kMaxLayers];
   CUtensorMap bwd[kMaxLayers];
+  int max_pairs = 0;              // CTA pairs resident at once
 };
 
 bool encode(CUtensorMap* map, const void* ptr, int rows, int cols, int fmt) {
@@ -734,6 +788,19 @@ leb_status adj_tc_prepare(Ctx& c) {
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, adjoint_tc_kernel) != cudaSuccess) return LEB_ERR_CUDA;
   if (fa.numRegs < kAdjRegsLaunchMin) return LEB_ERR_UNSUPPORTED;
+  // a GPC with an odd number of free SMs leaves one of them out of every pair: size the grid by the pairs
+  // that fit at once, so that no pair waits for a second wave
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(c.sm_count & ~1));
+  cfg.blockDim = dim3(kAdjThreads);
+  cfg.dynamicSmemBytes = kAdjSmem;
+  int pairs = 0;
+  if (cudaOccupancyMaxActiveClusters(&pairs, (const void*)adjoint_tc_kernel, &cfg) != cudaSuccess || pairs < 1) {
+    (void)cudaGetLastError();
+    pairs = c.sm_count / 2;
+  }
+  st->max_pairs = pairs < c.sm_count / 2 ? pairs : c.sm_count / 2;
+  if (st->max_pairs < 1) return LEB_ERR_UNSUPPORTED;
   return LEB_OK;
 }
 
@@ -748,8 +815,9 @@ void adj_tc_release(Ctx& c) {
 size_t adj_tc_scratch_floats(const Ctx& c) {
   const MlpModel& m = c.mlp;
   size_t stot = 0;
-  for (int k = 0; k + 2 < m.L; ++k) stot += m.widths[k + 1];   // lambda_0 .. lambda_{L-3}
-  return (size_t)c.sm_count * stot * 64;   // FP16: two per float
+  // lambda_0 .. lambda_{L-3}: each CTA of a pair holds 128 of every 256 neurons, for 256 rows
+  for (int k = 0; k + 2 < m.L; ++k) stot += (size_t)((m.widths[k + 1] + 255) / 256) * 128;
+  return (size_t)c.sm_count * stot * 128;   // FP16: two per float
 }
 
 leb_status adj_tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* ws, const float* g_lo,
@@ -776,9 +844,9 @@ leb_status adj_tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* 
   a.H = L.H;
   for (int i = 0; i + 1 < m.L; ++i) a.hoff[i] = L.hoff[i];
   int o = 0;
-  for (int k = 0; k + 2 <= target; ++k) {
+  for (int k = 0; k + 2 <= target; ++k) {   // this CTA's 128 of every 256 neurons
     a.soff[k] = o;
-    o += m.widths[k + 1];
+    o += ((m.widths[k + 1] + 255) / 256) * 128;
   }
   a.stot = o > 0 ? o : 1;
   a.W_target = m.W[target];
@@ -804,7 +872,11 @@ leb_status adj_tc_chain(const Ctx& c, int T, int target, const MlpWs& L, float* 
   a.flags = flags;
   const int items = T * a.tiles_per_t;
   if (items == 0) return LEB_OK;
-  const int grid = items < c.sm_count ? items : c.sm_count;   // the per-CTA scratch holds sm_count CTAs
+  // CTA pairs, each taking two items a pass: an even grid of at most the resident pairs (the per-CTA
+  // scratch holds sm_count CTAs)
+  const int max_grid = 2 * st->max_pairs;
+  const int want = 2 * ((items + 1) / 2);
+  const int grid = want < max_grid ? want : max_grid;
   timer_begin(c, s, "adjoint_tc_kernel");
   adjoint_tc_kernel<<<grid, kAdjThreads, kAdjSmem, s>>>(a);
   timer_end(c, s);

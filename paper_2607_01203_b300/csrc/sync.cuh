@@ -70,6 +70,53 @@ __device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, un
   }
 }
 
+// Waits that poll without suspending (bounded like the others), for the single threads that hand weight
+// tiles from TMA to the tensor cores: a suspended thread resumes some time after the phase completes, a
+// delay that a chain of such hand-offs would pay on every tile. The cluster form acquires at cluster
+// scope, for phases completed by arrivals from another CTA of the cluster.
+__device__ __forceinline__ bool mbar_try_wait_cl(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+template <bool kCluster>
+__device__ __forceinline__ bool mbar_wait_spin(uint64_t* bar, uint32_t parity) {
+  auto test = [&]() { return kCluster ? mbar_try_wait_cl(bar, parity) : mbar_try_wait(bar, parity); };
+  if (test()) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (test()) return true;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+// A sleeping wait with acquire at cluster scope (phases completed from another CTA of the cluster).
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait_cl(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait_cluster(bar, parity, kWaitSleepNs)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
 // The kernels' wait: the same, with the library's limit.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return mbar_wait_for(bar, parity, kWaitLimitNs);
