@@ -59,7 +59,7 @@ DRAM_BYTES_PER_TS_LAUNCH = {
     "pbh": (971_229_440 + 433_273_856) / 3200,
     "crown": (8_657_152 + 14_076_160 + 17_191_424 + 6_146_304) / (3 * 400),   # crown_tc_kernel, its 3 launches
     # 2 tight crown_tc_kernel + 3 adjoint_tc_kernel launches
-    "backward": (7_844_096 + 12_432_640 + 29_544_704 + 1_859_584 + 20_458_240 + 768 + 12_218_368) / (5 * 400),
+    "backward": (7_812_352 + 12_453_632 + 29_526_784 + 2_761_472 + 20_472_576 + 768 + 12_058_880) / (5 * 400),
     # pbh_sys_kernel<true>, captured at the bench's own size (12800 timesteps of the 168-state coupled
     # system)
     "pbh_sys": (39_297_792 + 1_901_738_000) / 12800,
