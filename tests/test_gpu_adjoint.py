@@ -87,6 +87,34 @@ def test_tensor_core_adjoint_workload_many_tiles_per_cta(prec):
     check(w, [0, 7, 33, 60, 99], prec=prec, rel=1e-3 + 4 * U_OP[prec])
 
 
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_tensor_core_adjoint_pairs_odd_item_count(prec):
+    """The tensor-core adjoint runs on CTA pairs that take two tiles a pass: 301 timesteps of a net with
+    one tile per timestep for every target (32 outputs: 96 of 126 rows; 64 hidden neurons: 128 rows) give
+    an odd tile count, several passes per pair and a pair whose last pass has a tile past the end (it
+    must write nothing). The gradient of the whole batch at sampled timesteps, the last included, against
+    the oracle."""
+    w = inputs.tanh_mlp(seed=4108, n_traj=1, N=301, widths=(64, 64, 64, 32))
+    assert w.T == 301
+    h = binding.mlp(w.Ws, w.bs, w.act, w.residual, prec)
+    rng = np.random.default_rng(21)
+    g_lo = rng.normal(size=(w.T, w.n_x)).astype(np.float32)
+    g_hi = rng.normal(size=(w.T, w.n_x)).astype(np.float32)
+    gx, gu, gr, fl = h.bounds_backward(_t(w.x_nom), _t(w.u_nom), _t(w.radii), _t(g_lo), _t(g_hi))
+    torch.cuda.synchronize()
+    assert int(fl.item()) == 0
+    got_all = torch.cat([gx, gu, gr], 1).cpu().numpy()
+    assert np.all(np.isfinite(got_all))
+    rel = 1e-3 + 4 * U_OP[prec]
+    for t in (0, 1, 147, 148, 149, 296, 299, 300):
+        ox, ou, orr = crown.box_remainder_vjp(w.Ws, w.bs, w.act, w.x_nom[t], w.u_nom[t], w.radii[t], g_lo[t],
+                                              g_hi[t], w.residual)
+        ref = np.concatenate([ox, ou, orr])
+        err = np.abs(got_all[t] - ref)
+        scale_t = np.abs(ref).max()
+        assert np.all(err <= rel * scale_t + rel * np.abs(ref)), (t, np.max(err / (scale_t + 1e-30)))
+
+
 def test_tensor_core_adjoint_uneven_widths():
     """Widths that leave partial M-tiles, a partial K-block of the inputs and a partial output tile (96
     inputs, 192 and 128 hidden, 40 outputs: 120 of the tile's 126 rows)."""
