@@ -2,7 +2,7 @@
 // part of the reverse pass for reduced-precision (FP16 / BF16) handles.
 //
 // For one back-substitution target (the output rows, or the lower/upper rows of hidden layer `target`)
-// and 128 chain rows of one timestep, a CTA
+// and 128 chain rows of one timestep (an item; a pair of CTAs takes two items at a time, below), the kernel
 //   1. recomputes the chain forward:  lambda_{k-1} = (lambda_k o s_k) W_k,  k = target-1 .. 0,
 //      starting from lambda_{target-1} = rows of W_target, keeping each lambda_k (k >= 0) in a per-CTA
 //      scratch area (it stays in L2);
@@ -17,12 +17,15 @@
 //
 // Layout (transposed with respect to the forward chain kernel): the products are computed as
 //   lambda_{k-1}^T = W_k^T (lambda_k o s_k)^T   and   Ga_k^T = W_k G_{k-1}^T,
-// so the weights are the streamed A operand (128 neurons x 64 K tiles by TMA, a ring of kAdjStages) and
-// the per-row operand is the resident B operand (128 rows x K, K-major, 128-byte swizzle). TMEM holds
-// D[neuron][row]: lane = neuron inside an M-tile of 128, column = 128 * M-tile + row. Every epilogue
-// thread owns one neuron (16 epilogue warps: 4 M-tiles x 4 TMEM lane quarters, four per SM
-// sub-partition, with most of warpgroup 0's registers handed to them by setmaxnreg), so every sum over
-// chain rows is a register sum, and the role of a row (lower, upper, Jacobian) is the same across a warp.
+// so the weights are the streamed A operand and the per-row operand is the resident B operand (MN-major,
+// 128-byte swizzle). CTAs work in pairs whose tensor cores act as one (.cta_group::2): M = 256 neurons
+// (each CTA loads its 128 of every 256-neuron weight tile by TMA, a ring of kAdjStages) by N = 256 rows
+// (each CTA holds its own item's 128 rows of B). Each CTA's TMEM holds D[neuron][row] for its 128
+// neurons of a tile: lane = neuron, column = 256 * tile + 128 * item + row. Every epilogue thread owns
+// one neuron and one item's rows (16 epilogue warps: 2 tiles x 4 TMEM lane quarters x 2 items, with
+// most of warpgroup 0's registers handed to them by setmaxnreg), so every sum over chain rows is a
+// register sum and the role of a row (lower, upper, Jacobian) is the same across a warp; the next
+// operand's rows go to the CTA that holds their item (the peer's shared memory for half the warps).
 //
 // Output rows are carried in difference form: the lower and upper rows hold delta = lambda - lambda^J
 // (their operand lambda o s_sel - lambda^J o sigma'(z~) is formed in FP32 from the row and the Jacobian
