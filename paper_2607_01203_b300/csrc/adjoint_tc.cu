@@ -224,7 +224,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
   } else if (warp == 1) {
     if (lane == 0 && rank == 0) {
       // ---------------------------------------------------------------- MMA issuer of the pair (CTA 0)
-      const uint32_t ring_base = smem_u32(ring), b_base = smem_u32(Bop);
+      // descriptors built once and advanced by the byte offset >> 4 (their start-address field is addr >> 4
+      // in the low 14 bits, which shared-memory addresses never carry out of)
+      const uint64_t a_desc0 = sw128_desc(smem_u32(ring));
+      const uint64_t b_desc0 = sw128_mn_desc(smem_u32(Bop), kAdjLbo, 1024u);
       const uint32_t idesc = idesc_f16_bmn(256, 256, a.fmt);
       uint32_t kb = 0, na = 0;
       bool ok = true;
@@ -247,12 +250,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
                 break;
               }
               tc_fence_after();
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t ad = sw128_desc(ring_base + slot * kAdjATile + kk * 32);
-                const uint64_t bd = sw128_mn_desc(b_base + (uint32_t)(kc * 8 + kk * 2) * 1024u, kAdjLbo, 1024u);
-                tc_mma_f16_pair(tmem + (uint32_t)(c * 256), ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-              }
+              // K step kk: 32 bytes further in the weight tile's rows, two 1 KB neuron groups further in B
+              const uint64_t ad = a_desc0 + (uint64_t)(slot * (kAdjATile >> 4));
+              const uint64_t bd = b_desc0 + (uint64_t)(kc * (8 * 1024 >> 4));
+              const uint32_t d_tmem = tmem + (uint32_t)(c * 256);
+              tc_mma_f16_pair(d_tmem, ad, bd, idesc, kc > 0 ? 1u : 0u);
+              tc_mma_f16_pair(d_tmem, ad + 2, bd + 128, idesc, 1u);
+              tc_mma_f16_pair(d_tmem, ad + 4, bd + 256, idesc, 1u);
+              tc_mma_f16_pair(d_tmem, ad + 6, bd + 384, idesc, 1u);
               tc_commit_pair(&empty[slot], 3u);   // frees the slot in both CTAs
             }
           tc_commit_pair(acc_full, 3u);

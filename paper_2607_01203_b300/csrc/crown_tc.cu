@@ -324,7 +324,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      const uint32_t a_base = smem_u32(Asm), b_base = smem_u32(Bsm);
+      // Operand descriptors are built once and advanced by adding the byte offset >> 4: their start-address
+      // field is addr >> 4 in the low 14 bits, which shared-memory addresses (< 256 KB) never carry out of.
+      // This thread shares its sub-partition with three epilogue warps, so every instruction it saves
+      // between MMAs is time the tensor core does not wait.
+      const uint64_t a_desc0 = sw128_desc(smem_u32(Asm)), b_desc0 = sw128_desc(smem_u32(Bsm));
       uint32_t kb = 0, jc = 0, rpar = 0, fpar = 0, used = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
@@ -333,6 +337,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
           for (int h = 0; h < nh && ok; ++h, ++jc) {
             const int nc = job_nc(k, h);
             const uint32_t hb = jc & 1u;
+            const uint32_t idesc = idesc_f16(128, nc, FMT);
+            const uint32_t d_tmem = tmem + hb * 256u;
             if ((used >> hb) & 1u) {
               if (!mbar_wait(&acc_free[hb], (fpar >> hb) & 1u)) { ok = false; break; }
               fpar ^= 1u << hb;
@@ -349,13 +355,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) crown_tc_kernel(const __grid_co
                 const int s = (int)(kb % kTcNSB);
                 if (!mbar_wait(&b_full[s], (kb / kTcNSB) & 1u)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t idesc = idesc_f16(128, nc, FMT);
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                  const uint64_t ad = sw128_desc(a_base + kc * 16384 + kk * 32);
-                  const uint64_t bd = sw128_desc(b_base + s * kTcBStage + kk * 32);
-                  tc_mma_f16(tmem + hb * 256u, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-                }
+                const uint64_t ad = a_desc0 + (uint64_t)(kc * (16384 >> 4));
+                const uint64_t bd = b_desc0 + (uint64_t)(s * (kTcBStage >> 4));
+                // K step kk: 32 bytes further in the 128-byte swizzled rows
+                tc_mma_f16(d_tmem, ad, bd, idesc, kc > 0 ? 1u : 0u);
+                tc_mma_f16(d_tmem, ad + 2, bd + 2, idesc, 1u);
+                tc_mma_f16(d_tmem, ad + 4, bd + 4, idesc, 1u);
+                tc_mma_f16(d_tmem, ad + 6, bd + 6, idesc, 1u);
                 tc_commit(&b_empty[s]);
                 ++kb;
               }
