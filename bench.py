@@ -57,9 +57,9 @@ DRAM_BYTES_PER_TS_LAUNCH = {
     # pbh_zono_tma_kernel<0> (the plain instance), one launch at T = 3200 (64 x 50), whose 486 MB of A/B
     # writes exceed the L2 (the last ~53 MB of them are still in L2 when the launch ends)
     "pbh": (971_229_440 + 433_273_856) / 3200,
-    "crown": (8_657_152 + 14_076_160 + 17_191_424 + 6_146_304) / (3 * 400),   # crown_tc_kernel, its 3 launches
+    "crown": (8_640_768 + 14_077_952 + 17_200_128 + 5_396_480) / (3 * 400),   # crown_tc_kernel, its 3 launches
     # 2 tight crown_tc_kernel + 3 adjoint_tc_kernel launches
-    "backward": (7_812_352 + 12_453_632 + 29_526_784 + 2_761_472 + 20_472_576 + 768 + 12_058_880) / (5 * 400),
+    "backward": (7_814_400 + 12_471_296 + 29_554_944 + 2_693_376 + 20_472_576 + 256 + 12_047_872) / (5 * 400),
     # pbh_sys_kernel<true>, captured at the bench's own size (12800 timesteps of the 168-state coupled
     # system)
     "pbh_sys": (39_297_792 + 1_901_738_000) / 12800,
