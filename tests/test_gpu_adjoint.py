@@ -115,6 +115,14 @@ def test_tensor_core_adjoint_pairs_odd_item_count(prec):
         assert np.all(err <= rel * scale_t + rel * np.abs(ref)), (t, np.max(err / (scale_t + 1e-30)))
 
 
+def test_tensor_core_adjoint_full_network_one_timestep():
+    """One timestep of the full network: 4 output tiles and 8 tiles per hidden target, so the CTA pairs'
+    grid shrinks to two or four CTAs and every pass has both of its tiles."""
+    w = inputs.tanh_mlp(n_traj=1, N=1)
+    assert w.T == 1
+    check(w, [0], prec="fp16", rel=1e-3 + 4 * U_OP["fp16"])
+
+
 def test_tensor_core_adjoint_uneven_widths():
     """Widths that leave partial M-tiles, a partial K-block of the inputs and a partial output tile (96
     inputs, 192 and 128 hidden, 40 outputs: 120 of the tile's 126 rows)."""
