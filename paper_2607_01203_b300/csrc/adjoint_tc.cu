@@ -59,7 +59,8 @@ constexpr int kAdjRegsLaunchMin = (128 * kAdjRegsCtl + 32 * kAdjEpiWarps * kAdjR
 constexpr int kAdjStages = 6;                       // weight-tile ring
 constexpr int kAdjATile = 128 * 64 * 2;             // 128 neurons x 64 K x 2 bytes
 constexpr int kAdjBRegion = 128 * 512 * 2;          // 128 rows x K <= 512 x 2 bytes
-constexpr int kAdjSmall = 1024 + 32 + 24 * 8;   // row cotangents [2 items][128], their scales, barriers
+constexpr int kAdjBars = 2 * kAdjStages + 6;   // full, empty, a_full[2], acc_full[2], drain, ebar
+constexpr int kAdjSmall = 1024 + 32 + kAdjBars * 8;   // row cotangents [2 items][128], their scales, barriers
 constexpr int kAdjSmem = 1024 + kAdjBRegion + kAdjStages * kAdjATile + kAdjSmall;
 static_assert(kAdjSmem <= 227 * 1024, "adjoint tensor-core shared memory");
 
@@ -115,6 +116,11 @@ __device__ __forceinline__ uint32_t b_off8(int r0, int j) {
 // one neuron and the rows of one item, and writes the next operand's rows into the CTA that holds that
 // item (its own or the peer's shared memory). Both CTAs walk the same number of passes (a CTA past the
 // last item works on an item with no valid rows, which writes nothing outside its own scratch).
+// A stage's MMAs go K-half by K-half (operand neurons 0-255, then 256-511), in each over the tiles in
+// turn, and are committed twice: once tile 0 is complete and K-half 0 read for the last time, and once
+// all are done. The epilogue warps of tile h wait for their commit and release K-half h of the next
+// operand, so tile 0's epilogue runs under the stage's last MMAs and the next stage's first MMAs run
+// under tile 1's epilogue.
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
     adjoint_tc_kernel(const __grid_constant__ AdjTcArgs a) {
   extern __shared__ uint8_t sraw[];
@@ -128,9 +134,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(wmax + 8);
   uint64_t* full = bars;                      // [kAdjStages] (CTA 0) both CTAs' weight halves landed
   uint64_t* empty = bars + kAdjStages;        // [kAdjStages] the pair's MMAs have read the slot
-  uint64_t* a_full = bars + 3 * kAdjStages;   // (CTA 0) both CTAs' operands written by their epilogues
-  uint64_t* acc_full = a_full + 1;            // accumulators complete
-  uint64_t* drain = acc_full + 1;
+  // (CTA 0) [2]: K-half h of both CTAs' operands written (operand neurons 256 h ..) and accumulator tile h
+  // read, by the epilogue warps of tile h
+  uint64_t* a_full = bars + 2 * kAdjStages;
+  // [2]: accumulator tile 0 complete and every MMA reading K-half 0 of the operand done; all MMAs done
+  uint64_t* acc_full = a_full + 2;
+  uint64_t* drain = acc_full + 2;
   uint64_t* ebar = drain + 1;                 // epilogue-warps barrier
   __shared__ uint32_t tmem_slot;
   __shared__ int s_abort;
@@ -148,8 +157,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(a_full, 2 * kAdjEpiWarps);   // both CTAs' epilogue warps
-    mbar_init(acc_full, 1);
+    mbar_init(&a_full[0], kAdjEpiWarps);   // the tile's 8 epilogue warps in each CTA
+    mbar_init(&a_full[1], kAdjEpiWarps);
+    mbar_init(&acc_full[0], 1);
+    mbar_init(&acc_full[1], 1);
     mbar_init(drain, 1);
     mbar_init(ebar, kAdjEpiWarps);
     mbar_fence_init();
@@ -197,18 +208,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
           const CUtensorMap* map;
           stage_shape(s, M, K, map);
           const int nM = (M + 255) / 256, nK = (K + 63) / 64;   // 256-neuron tiles, this CTA's half of each
-          for (int kc = 0; kc < nK && ok; ++kc)
-            for (int c = 0; c < nM; ++c, ++kb) {
-              const int slot = (int)(kb % kAdjStages);
-              if (kb >= (uint32_t)kAdjStages && !mbar_wait_spin<false>(&empty[slot], ((kb / kAdjStages) - 1) & 1u)) {
-                ok = false;
-                break;
+          // the MMAs' order: K-half by K-half, in each the tiles in turn, in each tile its K-chunks
+          for (int kh = 0; kh < 2 && ok; ++kh)
+            for (int c = 0; c < nM && ok; ++c)
+              for (int kc = 4 * kh; kc < min(nK, 4 * kh + 4); ++kc, ++kb) {
+                const int slot = (int)(kb % kAdjStages);
+                if (kb >= (uint32_t)kAdjStages &&
+                    !mbar_wait_spin<false>(&empty[slot], ((kb / kAdjStages) - 1) & 1u)) {
+                  ok = false;
+                  break;
+                }
+                if (*(volatile int*)&s_abort) { ok = false; break; }
+                if (rank == 0) mbar_arrive_expect_tx(&full[slot], 2u * (uint32_t)kAdjATile);
+                tma_load_2d_pair(ring + (size_t)slot * kAdjATile, map, kc * 64, c * 256 + (int)rank * 128,
+                                 full0 + (uint32_t)slot * 8u);
               }
-              if (*(volatile int*)&s_abort) { ok = false; break; }
-              if (rank == 0) mbar_arrive_expect_tx(&full[slot], 2u * (uint32_t)kAdjATile);
-              tma_load_2d_pair(ring + (size_t)slot * kAdjATile, map, kc * 64, c * 256 + (int)rank * 128,
-                               full0 + (uint32_t)slot * 8u);
-            }
         }
       }
       if (!ok) {
@@ -231,36 +245,44 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
       const uint32_t idesc = idesc_f16_bmn(256, 256, a.fmt);
       uint32_t kb = 0, na = 0;
       bool ok = true;
+      // the MMAs of tile c over K-chunks kc = 4 kh .. of K-half kh, each chunk's 4 K-steps back to back
+      auto issue = [&](int c, int kh, int nK) -> bool {
+        for (int kc = 4 * kh; kc < min(nK, 4 * kh + 4); ++kc, ++kb) {
+          const int slot = (int)(kb % kAdjStages);
+          if (!mbar_wait_spin<true>(&full[slot], (kb / kAdjStages) & 1u)) return false;   // both CTAs' halves
+          tc_fence_after();
+          // K step kk: 32 bytes further in the weight tile's rows, two 1 KB neuron groups further in B
+          const uint64_t ad = a_desc0 + (uint64_t)(slot * (kAdjATile >> 4));
+          const uint64_t bd = b_desc0 + (uint64_t)(kc * (8 * 1024 >> 4));
+          const uint32_t d_tmem = tmem + (uint32_t)(c * 256);
+          tc_mma_f16_pair(d_tmem, ad, bd, idesc, kc > 0 ? 1u : 0u);
+          tc_mma_f16_pair(d_tmem, ad + 2, bd + 128, idesc, 1u);
+          tc_mma_f16_pair(d_tmem, ad + 4, bd + 256, idesc, 1u);
+          tc_mma_f16_pair(d_tmem, ad + 6, bd + 384, idesc, 1u);
+          tc_commit_pair(&empty[slot], 3u);   // frees the slot in both CTAs
+        }
+        return true;
+      };
       for (int pass = 0; pass < n_pass && ok; ++pass) {
         for (int s = 0; s < n_stages && ok; ++s) {
           int M, K;
           const CUtensorMap* map;
           stage_shape(s, M, K, map);
           const int nM = (M + 255) / 256, nK = (K + 63) / 64;
-          // both CTAs' epilogues have written their operand (the peer's arrive from its CTA)
-          if (!mbar_wait_cluster(a_full, na & 1u)) { ok = false; break; }
+          // Tile 0 over K-half 0 needs only the warps of the last stage's tile 0 (or the prologue) to be done
+          // (they wrote K-half 0 and read accumulator tile 0); the rest waits for those of tile 1 as well.
+          // Tile 0 completes, and K-half 0 is read for the last time, before tile 1 over K-half 1, so the
+          // warps of tile 0 start their epilogue while those MMAs run (the peer's arrivals come from its CTA).
+          if (!mbar_wait_cluster(&a_full[0], na & 1u)) { ok = false; break; }
+          tc_fence_after();
+          if (!issue(0, 0, nK)) { ok = false; break; }
+          if (!mbar_wait_cluster(&a_full[1], na & 1u)) { ok = false; break; }
           ++na;
           tc_fence_after();
-          // K-chunk by K-chunk, each tile's 4 K-steps back to back into its accumulator
-          for (int kc = 0; kc < nK && ok; ++kc)
-            for (int c = 0; c < nM; ++c, ++kb) {
-              const int slot = (int)(kb % kAdjStages);
-              if (!mbar_wait_spin<true>(&full[slot], (kb / kAdjStages) & 1u)) {   // both CTAs' halves
-                ok = false;
-                break;
-              }
-              tc_fence_after();
-              // K step kk: 32 bytes further in the weight tile's rows, two 1 KB neuron groups further in B
-              const uint64_t ad = a_desc0 + (uint64_t)(slot * (kAdjATile >> 4));
-              const uint64_t bd = b_desc0 + (uint64_t)(kc * (8 * 1024 >> 4));
-              const uint32_t d_tmem = tmem + (uint32_t)(c * 256);
-              tc_mma_f16_pair(d_tmem, ad, bd, idesc, kc > 0 ? 1u : 0u);
-              tc_mma_f16_pair(d_tmem, ad + 2, bd + 128, idesc, 1u);
-              tc_mma_f16_pair(d_tmem, ad + 4, bd + 256, idesc, 1u);
-              tc_mma_f16_pair(d_tmem, ad + 6, bd + 384, idesc, 1u);
-              tc_commit_pair(&empty[slot], 3u);   // frees the slot in both CTAs
-            }
-          tc_commit_pair(acc_full, 3u);
+          if ((nM > 1 && !issue(1, 0, nK)) || !issue(0, 1, nK)) { ok = false; break; }
+          tc_commit_pair(&acc_full[0], 3u);
+          if (nM > 1 && !issue(1, 1, nK)) { ok = false; break; }
+          tc_commit_pair(&acc_full[1], 3u);
         }
       }
       if (!ok) {
@@ -276,7 +298,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
     // ------------------------------------------------------------------ epilogue warps
     // Each thread owns one neuron of 256-neuron tile pt, nrn0 = 256 pt + 128 rank + 32 q + lane (its
     // index among this CTA's neurons: jl0 = 128 pt + 32 q + lane), for the rows of item hh (TMEM columns
-    // 256 pt + 128 hh ..); the prologue instead gives thread etid neuron etid of this CTA's own item.
+    // 256 pt + 128 hh ..); in the prologue it instead owns neuron 256 pt + 128 hh + 32 q + lane of this
+    // CTA's own item, so that the warps of tile pt write K-half pt there too.
     const int ew = warp - kAdjCtlWarps;
     const int q = ew & 3;                      // TMEM lane quarter
     const int pt = (ew >> 2) & 1;              // 256-neuron tile
@@ -290,10 +313,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
     __half* scr = a.scratch + (size_t)blockIdx.x * a.stot * 256;
     const size_t rb_stride = (size_t)a.stot * 8;
     __half* scr_item = scr + (size_t)hh * 16 * rb_stride;
-    // item hh's operand lives in CTA hh; operand-written arrivals go to CTA 0's barrier
+    // item hh's operand lives in CTA hh; the warps of tile pt write K-half pt of the next operand (its
+    // neurons 256 pt ..), and their arrivals go to CTA 0's barrier of that half
     const bool own_rows = hh == (int)rank;
     const uint32_t bop_item = cluster_addr(Bop, (uint32_t)hh);
-    const uint32_t a_full0 = cluster_addr(a_full, 0u);
+    const uint32_t a_full0 = cluster_addr(&a_full[pt], 0u);
     const int n = a.widths[0];
     const bool output = target == a.L - 1;
     uint32_t nacc = 0, nbar = 0;
@@ -311,8 +335,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
       __syncwarp();                // the warp's writes before lane 0's release at cluster scope
       if (lane == 0) mbar_arrive_cluster(a_full0);
     };
-    auto wait_acc = [&]() -> bool {
-      if (!mbar_wait_warp(acc_full, nacc & 1u)) return false;
+    auto wait_acc = [&]() -> bool {   // accumulator tile pt complete (and, for tile 0, K-half 0 read)
+      if (!mbar_wait_warp(&acc_full[pt], nacc & 1u)) return false;
       ++nacc;
       tc_fence_after();
       return true;
@@ -370,7 +394,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
       // that of the group's state), the next chunk's entries loaded while a chunk is written.
       {
         const int Kp = (Kt + 63) & ~63;
-        const int jp = etid;   // neuron of this CTA's own item's operand
+        const int jp = pt * 256 + hh * 128 + q * 32 + lane;   // neuron of this CTA's own item's operand
         if (jp < Kp) {
           const bool live = jp < Kt;
           const long long o = (long long)t_own * a.H + a.hoff[target - 1] + (live ? jp : 0);
