@@ -59,7 +59,7 @@ DRAM_BYTES_PER_TS_LAUNCH = {
     "pbh": (971_229_440 + 433_273_856) / 3200,
     "crown": (8_640_768 + 14_077_952 + 17_200_128 + 5_396_480) / (3 * 400),   # crown_tc_kernel, its 3 launches
     # 2 tight crown_tc_kernel + 3 adjoint_tc_kernel launches
-    "backward": (7_814_400 + 12_471_296 + 29_554_944 + 2_693_376 + 20_472_576 + 256 + 12_047_872) / (5 * 400),
+    "backward": (7_811_840 + 12_432_896 + 29_577_984 + 2_233_088 + 20_483_072 + 256 + 12_216_320) / (5 * 400),
     # pbh_sys_kernel<true>, captured at the bench's own size (12800 timesteps of the 168-state coupled
     # system)
     "pbh_sys": (39_297_792 + 1_901_738_000) / 12800,
