@@ -384,7 +384,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
     // compile-time constant in the unrolled loops. Rows past the tile's valid rows carry zero cotangents
     // and a zero first operand, so every value derived from them is zero.
     static_assert(kAdjNU == 1, "the epilogue passes are written for one neuron a thread");
-    auto run_item = [&](auto nr_c, int t, int row0, int nrows, const float* gw, float ginv, float gscale, int t_own,
+    // cot(ginv, gscale) loads the pass's row cotangents into gw (a barrier of all epilogue warps): called
+    // only before G_{-1}, their first use, so that a pass's prologue and forward stages need no barrier of
+    // all warps and the warps of tile 0 start them while those of tile 1 finish the last pass
+    auto run_item = [&](auto nr_c, int t, int row0, int nrows, const float* gw, auto&& cot, int t_own,
                         int row0_own, int nrows_own) -> bool {
       constexpr int NR = decltype(nr_c)::value;
       constexpr int GS = 8 * NR;                 // rows per group: whole groups of NR, whole 8-column loads
@@ -511,6 +514,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
         operand_ready();
       }
       // ---- G_{-1} from lambda_{-1} (neurons = inputs m < n) --------------------------------------------
+      float ginv, gscale;
+      if (!cot(ginv, gscale)) return false;
       {
 #pragma unroll
         for (int u = 0; u < kAdjNU; ++u)
@@ -705,38 +710,41 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kAdjThreads, 1)
         it_nrows[h] = dummy ? 0 : min(a.rows_per_tile, a.rows_total - it_row0[h]);   // valid rows of the tile
       }
       // ---- row cotangents of both tiles (0 past the valid rows) and their scales --------------------
-      if (pass > 0 && !epi_sync()) { ok = false; break; }   // every warp is done with the last pass's
-      if (etid < 256) {
-        const int h = etid >> 7, e = etid & 127;
-        const int t = h ? it_t[1] : it_t[0];
-        float g = 0.f;
-        if (e < (h ? it_nrows[1] : it_nrows[0])) {
-          const int grow = (h ? it_row0[1] : it_row0[0]) + e, role = grow % a.nroles, idx = grow / a.nroles;
-          if (output) {
-            const int nx = a.widths[a.L];
-            g = role == 0 ? a.g_lo[(long long)t * nx + idx] : (role == 1 ? a.g_hi[(long long)t * nx + idx] : 0.f);
-          } else {
-            const long long o = (long long)t * a.H + a.hoff[target] + idx;
-            g = role == 0 ? a.gl[o] : a.gu[o];
+      auto cotangents = [&](float& ginv, float& gscale) -> bool {
+        if (!epi_sync()) return false;   // every warp is done with the last pass's (read from G_{-1} on)
+        if (etid < 256) {
+          const int h = etid >> 7, e = etid & 127;
+          const int t = h ? it_t[1] : it_t[0];
+          float g = 0.f;
+          if (e < (h ? it_nrows[1] : it_nrows[0])) {
+            const int grow = (h ? it_row0[1] : it_row0[0]) + e, role = grow % a.nroles, idx = grow / a.nroles;
+            if (output) {
+              const int nx = a.widths[a.L];
+              g = role == 0 ? a.g_lo[(long long)t * nx + idx] : (role == 1 ? a.g_hi[(long long)t * nx + idx] : 0.f);
+            } else {
+              const long long o = (long long)t * a.H + a.hoff[target] + idx;
+              g = role == 0 ? a.gl[o] : a.gu[o];
+            }
           }
-        }
-        gws[etid] = g;
-        float m = fabsf(g);
+          gws[etid] = g;
+          float m = fabsf(g);
 #pragma unroll
-        for (int dlt = 16; dlt > 0; dlt >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, dlt));
-        if (lane == 0) wmax[etid >> 5] = m;   // [item][warp of 32 rows]
-      }
-      if (!epi_sync()) { ok = false; break; }
-      const float* wm = wmax + hh * 4;
-      const float gmax = fmaxf(fmaxf(wm[0], wm[1]), fmaxf(wm[2], wm[3]));
-      const float gscale = (gmax > 0.f && isfinite(gmax)) ? gmax : 1.f;
-      const float ginv = 1.f / gscale;
+          for (int dlt = 16; dlt > 0; dlt >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, dlt));
+          if (lane == 0) wmax[etid >> 5] = m;   // [item][warp of 32 rows]
+        }
+        if (!epi_sync()) return false;
+        const float* wm = wmax + hh * 4;
+        const float gmax = fmaxf(fmaxf(wm[0], wm[1]), fmaxf(wm[2], wm[3]));
+        gscale = (gmax > 0.f && isfinite(gmax)) ? gmax : 1.f;
+        ginv = 1.f / gscale;
+        return true;
+      };
       const float* gw = gws + hh * 128;
       const int tm = hh ? it_t[1] : it_t[0], r0m = hh ? it_row0[1] : it_row0[0], nm = hh ? it_nrows[1] : it_nrows[0];
       const int to = rank ? it_t[1] : it_t[0], r0o = rank ? it_row0[1] : it_row0[0];
       const int no = rank ? it_nrows[1] : it_nrows[0];
-      ok = output ? run_item(std::integral_constant<int, 3>(), tm, r0m, nm, gw, ginv, gscale, to, r0o, no)
-                  : run_item(std::integral_constant<int, 2>(), tm, r0m, nm, gw, ginv, gscale, to, r0o, no);
+      ok = output ? run_item(std::integral_constant<int, 3>(), tm, r0m, nm, gw, cotangents, to, r0o, no)
+                  : run_item(std::integral_constant<int, 2>(), tm, r0m, nm, gw, cotangents, to, r0o, no);
       if (!ok) break;
       tc_fence_before();
       if (*(volatile int*)&s_abort) ok = false;
