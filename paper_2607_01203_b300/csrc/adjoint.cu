@@ -261,17 +261,18 @@ __device__ __forceinline__ float extreme_point(int act, float s, float l, float 
   return best;
 }
 
+// The slopes are those the forward relaxation stored (they depend on [l, u] only).
 __global__ void mlp_relax_bwd_kernel(int T, int width, int ld, int off, int act, const float* lo, const float* hi,
-                                     const float* zhat, const float* gsL, const float* gsU, const float* gtL,
-                                     const float* gtU, const float* gD, float* gl, float* gu, float* gz) {
+                                     const float* zhat, const float* sLv, const float* sUv, const float* gsL,
+                                     const float* gsU, const float* gtL, const float* gtU, const float* gD, float* gl,
+                                     float* gu, float* gz) {
   const long long total = (long long)T * width;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     const long long t = e / width;
     const int j = (int)(e - t * width);
     const long long o = t * ld + off + j;
     const float l = lo[o], u = hi[o], zt = zhat[o];
-    const Relax r = relax_neuron(act, l, u, zt, 0.f);
-    const float sL = r.sL, sU = r.sU;
+    const float sL = sLv[o], sU = sUv[o];
     // slope derivatives w.r.t. l and u (same case analysis as the forward rules)
     float dsLdl = 0.f, dsLdu = 0.f, dsUdl = 0.f, dsUdu = 0.f;
     const float w = u - l;
@@ -559,8 +560,8 @@ leb_status mlp_bounds_backward(Ctx& c, int T, const float* x_nom, const float* u
     const int width = m.widths[i + 1];
     const int blocks = (int)std::min<long long>(((long long)T * width + 255) / 256, 148LL * 32);
     mlp_relax_bwd_kernel<<<blocks, 256, 0, s>>>(T, width, L.H, L.hoff[i], m.act, ws + L.lo, ws + L.hi, ws + L.zhat,
-                                                ws + L.gsL, ws + L.gsU, ws + L.gtL, ws + L.gtU, ws + L.gD, ws + L.gl,
-                                                ws + L.gu, ws + L.gz);
+                                                ws + L.sL, ws + L.sU, ws + L.gsL, ws + L.gsU, ws + L.gtL, ws + L.gtU,
+                                                ws + L.gD, ws + L.gl, ws + L.gu, ws + L.gz);
     if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
     if (i > 0) {
       st = chain(i, nullptr, nullptr);

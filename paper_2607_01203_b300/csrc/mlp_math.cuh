@@ -120,19 +120,37 @@ __device__ __forceinline__ float g_nominal(int act, float s, float zh, float na,
   return want_max ? __fadd_ru(g.hi, slack) : __fsub_rd(g.lo, slack);
 }
 
-// Tangent point d > 0 of the line through (l, tanh l), l < 0 (bisection in FP32). Any value is sound
-// because intercepts are recomputed exactly; this only chooses a tight slope.
+// Tangent point d > 0 of the line through (l, tanh l), l < 0: the root of
+//   g(d) = tanh d - tanh l - tanh'(d) (d - l),   g'(d) = 2 tanh d tanh'(d) (d - l) > 0 on (0, 20).
+// For |l| < 0.01, g is O(l^3) and FP32 cancels it to noise; its root is -l/2 up to O(l^3), taken directly
+// (the slope tanh'(d) it picks is within 1e-8 of the exact one). Otherwise, in FP32: 9 bisection steps of
+// [0, 20], then 6 Newton steps from -l/2 (or the bracket's midpoint when -l/2 lies outside it), each kept
+// inside the bracket (a step that would leave it bisects instead). Checked against FP64 roots for
+// l in [-1e4, -0.01]: the slope differs from the exact tangent's by at most 4.4e-7, as the 32-step
+// bisection's did (2e-7), at half its tanh evaluations. Any value is sound because intercepts are
+// recomputed exactly; this only chooses a tight slope.
 __device__ __forceinline__ float tanh_tangent_from(float l) {
+  if (l > -0.01f) return -0.5f * l;
   float lo = 0.f, hi = 20.f;
   const float tl = tanhf(l);
 #pragma unroll 1
-  for (int it = 0; it < 32; ++it) {
+  for (int it = 0; it < 9; ++it) {
     const float mid = 0.5f * (lo + hi);
     const float tm = tanhf(mid);
     const float gm = tm - tl - (1.f - tm * tm) * (mid - l);
     if (gm > 0.f) hi = mid; else lo = mid;
   }
-  return 0.5f * (lo + hi);
+  const float d0 = -0.5f * l;
+  float d = (d0 >= lo && d0 <= hi) ? d0 : 0.5f * (lo + hi);
+#pragma unroll 1
+  for (int it = 0; it < 6; ++it) {
+    const float t = tanhf(d), sp = 1.f - t * t;
+    const float g = t - tl - sp * (d - l);
+    if (g > 0.f) hi = d; else lo = d;
+    const float dn = d - g / (2.f * t * sp * (d - l));
+    d = (dn >= lo && dn <= hi) ? dn : 0.5f * (lo + hi);
+  }
+  return d;
 }
 
 struct Relax {
