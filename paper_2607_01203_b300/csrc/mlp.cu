@@ -210,6 +210,7 @@ struct NomArgs {
   float gam;            // gamma for the blocked dot product (chunk + chunk count + bias)
   int act;
   int first;
+  int no_v1;            // v1 (and v2) not wanted: bounds recomputed without rounding inflation
 };
 
 constexpr int kNomBT = 64, kNomBN = 64;
@@ -219,10 +220,13 @@ __device__ __forceinline__ float2 abs2(float2 v) { return make_float2(fabsf(v.x)
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 
 // FIRST: the first hidden layer (its bounds over the displacement box come out of this pass too);
-// V2: the reduced-precision operand term v2 = |W - W~| abar is wanted (tensor-core handles). Both are
-// template parameters so that the unused accumulators take no registers.
-template <bool FIRST, bool V2>
+// V2: the reduced-precision operand term v2 = |W - W~| abar is wanted (tensor-core handles); V1: v1 =
+// |W| abar is wanted (not for bounds recomputed without rounding inflation, whose nominal, radius and
+// first-layer bounds are the same either way). The flags are template parameters so that the unused
+// accumulators take no registers.
+template <bool FIRST, bool V2, bool V1>
 __global__ void __launch_bounds__(256) mlp_nominal_kernel(NomArgs a) {
+  static_assert(V1 || !V2, "v2 comes with v1");
   __shared__ __align__(16) float s_in[kKC][kNomBT + 4];
   __shared__ __align__(16) float s_q[kKC][kNomBT + 4];
   __shared__ __align__(16) float s_ab[kKC][kNomBT + 4];
@@ -258,35 +262,40 @@ __global__ void __launch_bounds__(256) mlp_nominal_kernel(NomArgs a) {
         if (FIRST) {
           dl = a.dlo[o];
           dh = a.dhi[o];
-          ab = fmaxf(fabsf(dl), fabsf(dh));
-        } else {
+          if (V1) ab = fmaxf(fabsf(dl), fabsf(dh));
+        } else if (V1) {
           ab = a.abar[o];
         }
       }
       s_in[kk][tt] = x;
       s_q[kk][tt] = q;
-      s_ab[kk][tt] = ab;
-      s_dl[kk][tt] = dl;
-      s_dh[kk][tt] = dh;
+      if (V1) s_ab[kk][tt] = ab;
+      if (FIRST) {
+        s_dl[kk][tt] = dl;
+        s_dh[kk][tt] = dh;
+      }
     }
     for (int e = threadIdx.x; e < kKC * kNomBN; e += 256) {
       const int cc = e / kKC, kk = e - cc * kKC;
       const int c = c0 + cc, k = k0 + kk;
       const float w = (c < a.N && k < a.K) ? a.W[(long long)c * a.K + k] : 0.f;
       s_w[kk][cc] = w;
-      float we = 0.f;
-      if (a.op_fmt == 0) we = fabsf(w - __half2float(__float2half_rn(w)));
-      else if (a.op_fmt == 1) we = fabsf(w - __bfloat162float(__float2bfloat16_rn(w)));
-      s_we[kk][cc] = we;
+      if (V2) {
+        float we = 0.f;
+        if (a.op_fmt == 0) we = fabsf(w - __half2float(__float2half_rn(w)));
+        else if (a.op_fmt == 1) we = fabsf(w - __bfloat162float(__float2bfloat16_rn(w)));
+        s_we[kk][cc] = we;
+      }
     }
     __syncthreads();
 #pragma unroll 2
     for (int kk = 0; kk < kKC; ++kk) {
       const float4 w4 = *reinterpret_cast<const float4*>(&s_w[kk][4 * tx]);
-      const float4 e4 = *reinterpret_cast<const float4*>(&s_we[kk][4 * tx]);
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 e4 = V2 ? *reinterpret_cast<const float4*>(&s_we[kk][4 * tx]) : z4;
       const float4 x4 = *reinterpret_cast<const float4*>(&s_in[kk][4 * ty]);
       const float4 q4 = *reinterpret_cast<const float4*>(&s_q[kk][4 * ty]);
-      const float4 a4 = *reinterpret_cast<const float4*>(&s_ab[kk][4 * ty]);
+      const float4 a4 = V1 ? *reinterpret_cast<const float4*>(&s_ab[kk][4 * ty]) : z4;
       const float2 w2[2] = {make_float2(w4.x, w4.y), make_float2(w4.z, w4.w)};
       const float2 wa2[2] = {abs2(w2[0]), abs2(w2[1])};
       const float2 we2[2] = {make_float2(e4.x, e4.y), make_float2(e4.z, e4.w)};
@@ -306,7 +315,7 @@ __global__ void __launch_bounds__(256) mlp_nominal_kernel(NomArgs a) {
           sum[i][j] = t1;
           cmp[i][j] = __fadd2_rn(cmp[i][j], __fadd2_rn(pe, se));
           err[i][j] = __ffma2_ru(wa2[j], dup2(q[i]), err[i][j]);
-          vv[i][j] = __ffma2_ru(wa2[j], dup2(ab[i]), vv[i][j]);
+          if (V1) vv[i][j] = __ffma2_ru(wa2[j], dup2(ab[i]), vv[i][j]);
           if (V2) vw[i][j] = __ffma2_ru(we2[j], dup2(ab[i]), vw[i][j]);
         }
       if (FIRST) {
@@ -352,7 +361,7 @@ __global__ void __launch_bounds__(256) mlp_nominal_kernel(NomArgs a) {
       const long long o = (long long)t * a.ld_out + c;
       a.zhat[o] = zh;
       a.zrad[o] = e;
-      a.v1[o] = v1;
+      if (V1) a.v1[o] = v1;
       if (V2) a.v2[o] = v2;
       if (FIRST) {
         a.lo[o] = __fadd_rd(__fsub_rd(zh, e), bl);
@@ -864,12 +873,15 @@ leb_status launch_simt_chain(const Ctx& c, const ChainArgs& a, cudaStream_t s) {
 
 static void launch_nominal(const NomArgs& na, dim3 grid, cudaStream_t s) {
   const bool v2 = na.v2 != nullptr;
-  if (na.first) {
-    if (v2) mlp_nominal_kernel<true, true><<<grid, 256, 0, s>>>(na);
-    else mlp_nominal_kernel<true, false><<<grid, 256, 0, s>>>(na);
+  if (na.no_v1) {
+    if (na.first) mlp_nominal_kernel<true, false, false><<<grid, 256, 0, s>>>(na);
+    else mlp_nominal_kernel<false, false, false><<<grid, 256, 0, s>>>(na);
+  } else if (na.first) {
+    if (v2) mlp_nominal_kernel<true, true, true><<<grid, 256, 0, s>>>(na);
+    else mlp_nominal_kernel<true, false, true><<<grid, 256, 0, s>>>(na);
   } else {
-    if (v2) mlp_nominal_kernel<false, true><<<grid, 256, 0, s>>>(na);
-    else mlp_nominal_kernel<false, false><<<grid, 256, 0, s>>>(na);
+    if (v2) mlp_nominal_kernel<false, true, true><<<grid, 256, 0, s>>>(na);
+    else mlp_nominal_kernel<false, false, true><<<grid, 256, 0, s>>>(na);
   }
 }
 
@@ -881,9 +893,10 @@ leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_
   const bool zexact = set->kind == LEB_SET_ZONO_EXACT;
   mlp_workspace_floats(c, T, &L, zexact && tc ? set->n_gen : 0);
   float* ws = (float*)((char*)ws_base + 256);
+  // inflation weights of the tensor-core chains (none for bounds recomputed without inflation)
   auto tcw = [&](int layer) {
     TcWeights w{};
-    if (!tc) return w;
+    if (!tc || tight) return w;
     const float uop = m.prec == LEB_PREC_FP16 ? 4.8828125e-04f : 3.90625e-03f;  // 2^-11 / 2^-8
     const float g = gamma_tc(m.widths[layer + 1]);
     w.winf = ws + L.winf;
@@ -928,7 +941,9 @@ leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_
     na.hhat = ws + L.hhat + L.hoff[i];
     na.hrad = ws + L.hrad + L.hoff[i];
     na.v1 = ws + L.v1 + L.hoff[i];
-    na.v2 = m.prec == LEB_PREC_FP32 ? nullptr : ws + L.v2 + L.hoff[i];
+    // bounds recomputed without inflation (tight) read neither v1 nor v2
+    na.no_v1 = tight ? 1 : 0;
+    na.v2 = m.prec == LEB_PREC_FP32 || tight ? nullptr : ws + L.v2 + L.hoff[i];
     na.op_fmt = m.prec == LEB_PREC_FP16 ? 0 : (m.prec == LEB_PREC_BF16 ? 1 : -1);
     na.lo = ws + L.lo + L.hoff[i];
     na.hi = ws + L.hi + L.hoff[i];
@@ -956,7 +971,7 @@ leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_
       mlp_relax_kernel<<<blocks, 256, 0, s>>>(T, na.N, L.H, L.hoff[0], m.act, ws + L.lo, ws + L.hi, ws + L.zhat,
                                               ws + L.zrad, nullptr, ws + L.sL, ws + L.tL, ws + L.sU, ws + L.tU,
                                               ws + L.D, ws + L.abar, ws + L.loss, ws + L.v1, ws + L.v2, tcw(0), 0);
-      if (tc) tc_ucon_kernel<<<T, 32, 0, s>>>(T, na.N, L.H, L.hoff[0], ws + L.v1, tcw(0), 0);
+      if (tc && !tight) tc_ucon_kernel<<<T, 32, 0, s>>>(T, na.N, L.H, L.hoff[0], ws + L.v1, tcw(0), 0);
       if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
       continue;
     }
@@ -979,7 +994,7 @@ leb_status mlp_forward_hidden(Ctx& c, int T, const float* x_nom, const float* u_
     mlp_relax_kernel<<<blocks, 256, 0, s>>>(T, na.N, L.H, L.hoff[i], m.act, ws + L.lo, ws + L.hi, ws + L.zhat,
                                             ws + L.zrad, ws + L.bslack, ws + L.sL, ws + L.tL, ws + L.sU, ws + L.tU,
                                             ws + L.D, ws + L.abar, ws + L.loss, ws + L.v1, ws + L.v2, tcw(i), i);
-    if (tc) tc_ucon_kernel<<<T, 32, 0, s>>>(T, na.N, L.H, L.hoff[i], ws + L.v1, tcw(i), i);
+    if (tc && !tight) tc_ucon_kernel<<<T, 32, 0, s>>>(T, na.N, L.H, L.hoff[i], ws + L.v1, tcw(i), i);
     if (cudaGetLastError() != cudaSuccess) return LEB_ERR_CUDA;
   }
   return LEB_OK;
