@@ -57,9 +57,9 @@ DRAM_BYTES_PER_TS_LAUNCH = {
     # pbh_zono_tma_kernel<0> (the plain instance), one launch at T = 3200 (64 x 50), whose 486 MB of A/B
     # writes exceed the L2 (the last ~53 MB of them are still in L2 when the launch ends)
     "pbh": (971_229_440 + 433_273_856) / 3200,
-    "crown": (8_640_768 + 14_077_952 + 17_200_128 + 5_396_480) / (3 * 400),   # crown_tc_kernel, its 3 launches
+    "crown": (8_680_192 + 14_075_136 + 17_189_120 + 5_723_136) / (3 * 400),   # crown_tc_kernel, its 3 launches
     # 2 tight crown_tc_kernel + 3 adjoint_tc_kernel launches
-    "backward": (7_811_840 + 12_432_896 + 29_577_984 + 2_233_088 + 20_483_072 + 256 + 12_216_320) / (5 * 400),
+    "backward": (7_813_888 + 12_442_112 + 29_537_792 + 2_031_616 + 20_539_136 + 12_056_320) / (5 * 400),
     # pbh_sys_kernel<true>, captured at the bench's own size (12800 timesteps of the 168-state coupled
     # system)
     "pbh_sys": (39_297_792 + 1_901_738_000) / 12800,
